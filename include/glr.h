@@ -1,0 +1,208 @@
+/*
+ * glr.h -- C ABI of the GB300 global low-rank (GLR) denoising library.
+ *
+ * The library implements the hot path of "Large-scale Global Low-rank
+ * Optimization for Computational Compressed Imaging" (Li et al., 2023):
+ * key-patch selection from corners of the edge map (Section 2, Eq. 2-3),
+ * global patch matching with a running top-K (Section 2, Eq. 1 made global,
+ * Eq. 4 computed as a dense contraction), grouping R~_i x and the WNNM
+ * low-rank step (Eq. 5), aggregation, and the GAP projection for the coded
+ * aperture model y = sum_t A_t x_t (Eq. 6, Eq. 8).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All array arguments are DEVICE pointers owned by the caller, except
+ *    where an argument is documented as a host pointer.  The library never
+ *    allocates or frees device memory; scratch space is the caller's
+ *    workspace `ws` of `ws_bytes` bytes (query the size with
+ *    glr_workspace_size; the base must be 256-byte aligned).
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL = the legacy default stream).  Arguments are validated on the host
+ *    before anything is launched; on an error nothing is launched and the
+ *    status code says why.  Nothing aborts, exits or traps.
+ *  - Device-side conditions (a bounded wait that expired, a group whose SVD
+ *    did not converge, a key whose candidate list had to be rebuilt) are
+ *    recorded as bits and counters in a status block at the start of the
+ *    workspace; read it with glr_poll_status after the stream is done.
+ *  - Images: x is float32 [n_img][C][H][W], row-major.  A patch is P x P x C;
+ *    its vector index is ch*P*P + dr*P + dc.  Patch positions are the
+ *    Hq x Wq = (H-P+1) x (W-P+1) top-left corners (the valid positions of the
+ *    Conv2d heat map in Section 2); a position id is q = r*Wq + c.
+ *  - Keys, groups and matches are per image: keys int32 [n_img][N],
+ *    idx int32 [n_img][N][K], dist float32 [n_img][N][K],
+ *    groups float32 [n_img][N][K][C*P*P].
+ */
+#ifndef GLR_H_
+#define GLR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t glr_status;
+enum {
+  GLR_OK = 0,
+  GLR_EINVAL = 1,    /* an argument is out of range or a pointer is NULL/misaligned */
+  GLR_ECUDA = 2,     /* a CUDA runtime call failed (launch error, bad stream, ...) */
+  GLR_ENOMEM = 3,    /* the workspace is smaller than glr_workspace_size() */
+  GLR_ETIMEDOUT = 4, /* a bounded device-side wait expired (status bit set) */
+  GLR_ENOTSUP = 5,   /* the shape / mode is valid but not supported by this build */
+  GLR_EDEVICE = 6    /* a device-side error bit is set in the status block */
+};
+
+/* Status-block bits (glr_poll_status, `bits`). */
+enum {
+  GLR_DEV_TIMEOUT = 1u << 0,       /* an mbarrier / flag wait hit its iteration cap */
+  GLR_DEV_NONFINITE = 1u << 1,     /* NaN or Inf met in an input */
+  GLR_DEV_SVD_NOCONV = 1u << 2,    /* a Jacobi SVD reached its sweep cap */
+  GLR_DEV_CAND_OVERFLOW = 1u << 3  /* a candidate buffer overflowed (result still exact, slower) */
+};
+
+/* A batch of equally sized images searched independently. */
+typedef struct glr_images {
+  int32_t n_img; /* number of images (video frames, MSFA images, ...) */
+  int32_t C;     /* channels per image (1 for SCI frames) */
+  int32_t H, W;  /* image size */
+  int32_t P;     /* patch side; 1 <= P <= min(H, W) */
+} glr_images;
+
+/* Contraction used by glr_match_topk. */
+enum {
+  GLR_MATCH_FP32 = 0, /* plain form: FP32 FMA on the CUDA cores */
+  GLR_MATCH_BF16 = 1  /* chosen form: BF16 tcgen05.mma into TMEM, FP32 accumulate, FP32 re-rank */
+};
+
+typedef struct glr_match_opts {
+  int32_t mode;   /* GLR_MATCH_* */
+  int32_t k_over; /* candidates kept per key and position split before the exact
+                     FP32 re-rank; 0 = default (K+16 for FP32, 2K for BF16) */
+  int32_t splits; /* position splits per key tile; 0 = automatic */
+  int32_t reserved[5];
+} glr_match_opts;
+
+/* Operation codes for glr_workspace_size. */
+enum { GLR_OP_SELECT = 1, GLR_OP_MATCH = 2, GLR_OP_LOWRANK = 3, GLR_OP_AGGREGATE = 4 };
+
+/*
+ * Workspace bytes needed by one operation.  `opts` is used by GLR_OP_MATCH
+ * only and may be NULL (defaults).  Returns 0 for invalid arguments.
+ */
+size_t glr_workspace_size(int32_t op, const glr_images* im, int32_t N, int32_t K,
+                          const glr_match_opts* opts);
+
+/*
+ * Key (exemplar) patch selection -- Section 2: "exemplar patches centred on
+ * corner points of the averaged edge map", edge maps of Eq. 2 with the
+ * threshold function of Eq. 3.
+ *
+ *   x        [n_img][C][H][W] float32, the current estimate.
+ *   edge_th  the threshold th of Eq. 3 (applied to Sobel output).
+ *   N        keys per image, 1 <= N <= Hq*Wq.
+ *   keys     out, int32 [n_img][N]: position ids in rank order -- corners by
+ *            descending integer Harris response (k = 1/25) of the summed
+ *            signed edge maps, ties by pixel id, mapped to the patch whose
+ *            top-left is (r - P/2, c - P/2) clamped, duplicates dropped;
+ *            then a row-major uniform grid of stride max(1, isqrt(Hq*Wq/N))
+ *            fills the remaining slots.
+ *   n_found  out, int32 [n_img]: number of valid keys (= N).
+ *   n_corner out (may be NULL), int32 [n_img]: keys that came from corners.
+ * Result is bit-exact given the edge maps (integer arithmetic after Eq. 3).
+ */
+glr_status glr_select_keys(const float* x, const glr_images* im, float edge_th, int32_t N,
+                           int32_t* keys, int32_t* n_found, int32_t* n_corner, void* ws,
+                           size_t ws_bytes, void* stream);
+
+/*
+ * Global matching -- Section 2 (Eq. 1 over the entire image; the heat map of
+ * Eq. 4 computed as ||p||^2 - 2<p,q> + ||q||^2 for every key p and every
+ * position q of the same image, fused with a running per-key top-K so the
+ * heat map never reaches memory).
+ *
+ *   keys     int32 [n_img][N] position ids (from glr_select_keys or the caller).
+ *   n_found  int32 [n_img] valid keys per image (<= N); rows beyond are not written.
+ *   K        matches per key, 1 <= K <= 128, K <= Hq*Wq.
+ *   idx      out, int32 [n_img][N][K]: the K positions with the smallest
+ *            squared L2 distance, ordered by (distance, position id); the key
+ *            itself is included (distance 0).
+ *   dist     out (may be NULL), float32 [n_img][N][K]: those distances,
+ *            recomputed directly as sum((p - q)^2) in FP32.
+ */
+glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* keys,
+                          const int32_t* n_found, int32_t N, int32_t K,
+                          const glr_match_opts* opts, int32_t* idx, float* dist, void* ws,
+                          size_t ws_bytes, void* stream);
+
+/*
+ * Grouping and low-rank step -- Eq. 5 (R~_i x) solved by WNNM (Section 2).
+ * For every key the K matched patches form Y (d x K, d = C*P*P); with
+ * Y = U S V^T, sigma_hat_i = sqrt(max(s_i^2 - K sigma_w^2, 0)),
+ * tau_i = c_wnnm sigma_w^2 / (sigma_hat_i + 1e-8), s'_i = max(s_i - tau_i, 0),
+ * the output is X^ = U diag(s') V^T.  The SVD is a one-sided Jacobi in FP32.
+ *
+ *   idx      int32 [n_img][N][K] matches (from glr_match_topk).
+ *   groups   out, float32 [n_img][N][K][d]: row j = column j of X^.
+ *   rank     out (may be NULL), int32 [n_img][N]: number of s'_i > 0.
+ * Limits of this build: d <= 64 and K <= 64 (GLR_ENOTSUP otherwise).
+ */
+glr_status glr_lowrank_groups(const float* x, const glr_images* im, const int32_t* idx,
+                              const int32_t* n_found, int32_t N, int32_t K, float sigma_w,
+                              float c_wnnm, float* groups, int32_t* rank, void* ws,
+                              size_t ws_bytes, void* stream);
+
+/*
+ * Aggregation: every group column is added back at its patch position with
+ * weight 1 and overlapping estimates are averaged; pixels no patch covers
+ * keep x_in.  v_out must not alias groups; it may alias x_in.
+ *   groups float32 [n_img][N][K][d], idx int32 [n_img][N][K],
+ *   x_in, v_out float32 [n_img][C][H][W].
+ */
+glr_status glr_aggregate(const float* groups, const int32_t* idx, const int32_t* n_found,
+                         const glr_images* im, int32_t N, int32_t K, const float* x_in,
+                         float* v_out, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * GAP projection for y = sum_t A_t x_t (Eq. 6 for video SCI; Eq. 8 for an
+ * MSFA with orthogonal masks, Eq. 9, where R == 1):
+ *   R = sum_t A_t^2 (0 -> 1),  x_t = v_t + A_t (y - sum_s A_s v_s) / R.
+ * With accelerate != 0 (accelerated GAP): y_acc += y - sum_s A_s v_s and y_acc
+ * replaces y in the update.  v == NULL means v = 0, which gives the usual
+ * start x0 = Phi^T (y / R).
+ *
+ *   y      float32 [G][H][W]          measurements
+ *   masks  float32 [T][H][W] per group, at element stride mask_group_stride
+ *          between groups (0 = one mask set shared by all groups)
+ *   v, x_out float32 [G][T][H][W]; x_out may alias v.
+ *   y_acc  float32 [G][H][W], in/out, required iff accelerate != 0.
+ */
+glr_status glr_gap_step(const float* y, const float* masks, int64_t mask_group_stride,
+                        const float* v, int32_t G, int32_t T, int32_t H, int32_t W,
+                        int32_t accelerate, float* y_acc, float* x_out, void* stream);
+
+/*
+ * Reads the status block of a workspace used by an earlier call (blocks on
+ * `stream`).  bits = OR of GLR_DEV_*; counters (may be NULL) receives 4
+ * uint32 values: [0] keys whose candidate buffer overflowed, [1] groups whose
+ * SVD hit the sweep cap, [2] total Jacobi sweeps, [3] groups processed.
+ * Returns GLR_EDEVICE if any error bit (timeout, non-finite) is set.
+ * Pass reset != 0 to clear the block afterwards.
+ */
+glr_status glr_poll_status(const void* ws, uint32_t* bits, uint32_t* counters, int32_t reset,
+                           void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* glr_status_string(glr_status s);
+
+/* Number of kernels this library has launched in this process (all devices). */
+uint64_t glr_launch_count(void);
+
+/* Version string of the library build. */
+const char* glr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLR_H_ */

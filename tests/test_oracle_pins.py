@@ -1,0 +1,380 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: closed forms
+worked by hand, invariants, special cases that reduce to a textbook result,
+an independent library algorithm (k-d tree nearest neighbours), and brute
+force on tiny inputs.  A dropped term, a flipped sign, a wrong index or a
+transposed operand in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import glr_oracle as O
+from paper_2301_03047_gb300 import synth
+
+# ---------------------------------------------------------------------------
+# Eq. 2 / Eq. 3: Sobel and binary edge maps
+# ---------------------------------------------------------------------------
+
+
+def test_sobel_ramp_closed_form():
+    """A ramp x = a*c + b*r gives g_h = 8a, g_v = 8b inside; 4a / 4b on replicated borders."""
+    a, b = 0.0625, -0.03125
+    H, W = 9, 11
+    r = np.arange(H)[:, None]
+    c = np.arange(W)[None, :]
+    img = a * c + b * r
+    gh, gv = O.sobel(img)
+    assert np.allclose(gh[:, 1:-1], 8 * a) and np.allclose(gh[:, 0], 4 * a) and np.allclose(gh[:, -1], 4 * a)
+    assert np.allclose(gv[1:-1, :], 8 * b) and np.allclose(gv[0, :], 4 * b) and np.allclose(gv[-1, :], 4 * b)
+
+
+def test_edge_maps_signs_reading_a1():
+    """A rising step in x lights only h+, a falling one only h-, and likewise for v (reading A1)."""
+    img = np.zeros((6, 8))
+    img[:, 4:] = 1.0  # rising left->right
+    m = O.edge_maps(img, 0.1)
+    assert m["h+"][:, 3:5].all() and m["h+"].sum() == 12
+    assert m["h-"].sum() == 0 and m["v+"].sum() == 0 and m["v-"].sum() == 0
+    m2 = O.edge_maps(1.0 - img, 0.1)
+    assert m2["h-"].sum() == 12 and m2["h+"].sum() == 0
+    m3 = O.edge_maps(img.T.copy(), 0.1)  # rising top->bottom
+    assert m3["v+"].sum() == 12 and m3["v-"].sum() == 0 and m3["h+"].sum() == 0
+
+
+def test_threshold_is_strict():
+    """Eq. 3: T(z) = 1 only for z > th; z == th gives 0."""
+    z = np.array([0.09, 0.1, 0.11])
+    assert list(O.threshold(z, 0.1)) == [0, 0, 1]
+
+
+def test_golden_edge_fixture():
+    """Hand-worked Sobel / edge maps of a 5x5 image (tests/golden/edges_5x5.txt)."""
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "edges_5x5.txt")
+    blocks = {}
+    cur = None
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.endswith(":"):
+            cur = line[:-1]
+            blocks[cur] = []
+        else:
+            blocks[cur].append([float(t) for t in line.split()])
+    img = np.array(blocks["image"])
+    gh, gv = O.sobel(img)
+    assert np.array_equal(gh, np.array(blocks["g_h"]))
+    assert np.array_equal(gv, np.array(blocks["g_v"]))
+    m = O.edge_maps(img, blocks["th"][0][0])
+    for k in ("h+", "h-", "v+", "v-"):
+        assert np.array_equal(m[k], np.array(blocks[k], dtype=np.uint8)), k
+    assert np.array_equal(O.edge_sum(img[None], blocks["th"][0][0]), np.array(blocks["S"], dtype=np.int64))
+
+
+def test_edge_sum_or_over_channels():
+    img = np.zeros((2, 6, 8))
+    img[0, :, 4:] = 1.0
+    img[1, :, 4:] = 1.0
+    s2 = O.edge_sum(img, 0.1)
+    s1 = O.edge_sum(img[:1], 0.1)
+    assert np.array_equal(s1, s2)
+
+
+# ---------------------------------------------------------------------------
+# Corner detection (reading A3)
+# ---------------------------------------------------------------------------
+
+
+def test_harris_flat_and_straight_edge():
+    """Flat maps give R = 0; a straight full-height edge gives R <= 0 everywhere (no corner)."""
+    assert np.all(O.corner_response(np.zeros((12, 12), dtype=np.int64)) == 0)
+    S = np.zeros((16, 16), dtype=np.int64)
+    S[:, 7:9] = 2
+    R = O.corner_response(S)
+    assert R.max() <= 0 and R.min() < 0
+
+
+def test_harris_rectangle_corners():
+    """The four strongest NMS corners of a filled rectangle are its four corner pixels."""
+    img = np.zeros((40, 40))
+    img[10:30, 12:28] = 1.0
+    S = O.edge_sum(img[None], 0.1)
+    R = O.corner_response(S)
+    keep = O.nms3(R)
+    rr, cc = np.nonzero(keep)
+    order = np.lexsort((rr * 40 + cc, -R[rr, cc]))[:4]
+    got = sorted((int(rr[i]), int(cc[i])) for i in order)
+    assert got == [(10, 12), (10, 27), (29, 12), (29, 27)]
+
+
+def test_nms_plateau_tie_break():
+    """A plateau keeps only its lowest-index pixel; strict maxima survive; R <= 0 never does."""
+    R = np.zeros((5, 6), dtype=np.int64)
+    R[1, 1] = R[1, 2] = R[2, 1] = R[2, 2] = 7  # 2x2 plateau
+    R[3, 4] = 9
+    R[4, 0] = -3
+    keep = O.nms3(R)
+    assert set(zip(*np.nonzero(keep))) == {(1, 1), (3, 4)}
+
+
+def test_select_keys_grid_fill_closed_form():
+    """No edges -> all keys come from the row-major grid of stride isqrt(Hq*Wq // N) (A5)."""
+    x = np.full((1, 20, 20), 0.3)
+    P, N = 4, 10
+    keys, nc = O.select_keys(x, P, N, 0.1)
+    Hq = Wq = 17
+    s = math.isqrt(Hq * Wq // N)
+    assert s == 5 and nc == 0
+    expect = [gr * Wq + gc for gr in range(0, Hq, s) for gc in range(0, Wq, s)][:N]
+    assert list(keys) == expect
+
+
+def test_select_keys_clamp_and_dedupe():
+    """Corners near the border clamp to the same top-left patch; later duplicates are dropped (A4)."""
+    img = np.zeros((1, 24, 24))
+    img[0, 1:12, 1:12] = 1.0  # corner pixels (1,1),(1,11),(11,1),(11,11)
+    P, N = 8, 6
+    keys, nc = O.select_keys(img, P, N, 0.1)
+    Wq = 24 - P + 1
+    # corner (1,1) -> top-left (max(1-4,0), max(1-4,0)) = (0,0); (1,11) -> (0,7); (11,1) -> (7,0); (11,11) -> (7,7)
+    corner_tl = {0 * Wq + 0, 0 * Wq + 7, 7 * Wq + 0, 7 * Wq + 7}
+    assert set(int(k) for k in keys[:nc]) <= corner_tl | set(range(Wq * Wq))
+    assert {0, 7, 7 * Wq, 7 * Wq + 7} <= set(int(k) for k in keys[:nc])
+    assert len(set(int(k) for k in keys)) == N
+    # Two corners 1 px apart near the origin clamp to the same patch.
+    img2 = np.zeros((1, 24, 24))
+    img2[0, 2:20, 2:20] = 1.0
+    img2[0, 2:4, 2:4] = 0.5
+    k2, nc2 = O.select_keys(img2, P, 20, 0.1)
+    assert len(set(int(k) for k in k2)) == 20
+
+
+# ---------------------------------------------------------------------------
+# Global matching (Eq. 1 over the whole image)
+# ---------------------------------------------------------------------------
+
+
+def test_topk_ramp_closed_form():
+    """On x = a*c every pixel of two patches differs by a*dc, so d = P^2 a^2 dc^2 exactly:
+    the ranking is (|dc|, id)."""
+    a = 0.25
+    H, W, P, K = 12, 14, 3, 20
+    img = (a * np.arange(W)[None, :] * np.ones((H, 1)))[None]
+    Hq, Wq = H - P + 1, W - P + 1
+    key = 4 * Wq + 5
+    idx, dist = O.match_topk(img, P, np.array([key]), K)
+    ids = np.arange(Hq * Wq)
+    dc = np.abs(ids % Wq - 5)
+    expect = ids[np.lexsort((ids, dc))][:K]
+    assert list(idx[0]) == list(expect)
+    assert np.allclose(dist[0], P * P * a * a * dc[expect] ** 2)
+
+
+def test_topk_planted_copies():
+    """Exact copies of the key patch have distance 0 and come first, in id order."""
+    rng = synth.rng_for("planted")
+    H, W, P = 20, 22, 4
+    img = rng.random((1, H, W))
+    Wq = W - P + 1
+    src = (3, 5)
+    for r, c in [(12, 1), (0, 15), (15, 16)]:
+        img[0, r : r + P, c : c + P] = img[0, src[0] : src[0] + P, src[1] : src[1] + P]
+    key = src[0] * Wq + src[1]
+    idx, dist = O.match_topk(img, P, np.array([key]), 6)
+    want = sorted([key, 12 * Wq + 1, 0 * Wq + 15, 15 * Wq + 16])
+    assert list(idx[0][:4]) == want and np.all(dist[0][:4] == 0) and np.all(dist[0][4:] > 0)
+
+
+def test_topk_constant_image_ties_by_id():
+    img = np.full((1, 10, 10), 0.5)
+    idx, dist = O.match_topk(img, 3, np.array([17, 40]), 7)
+    assert np.all(dist == 0) and list(idx[0]) == list(range(7)) and list(idx[1]) == list(range(7))
+
+
+def test_topk_matches_kdtree_where_separated():
+    """An independent exact nearest-neighbour search (scipy k-d tree) agrees wherever
+    the K-th and (K+1)-th distances are separated."""
+    spatial = pytest.importorskip("scipy.spatial")
+    rng = synth.rng_for("kdtree")
+    img = rng.random((1, 18, 17))
+    P, K = 4, 9
+    Q = O.patch_matrix(img, P)
+    keys = np.array([0, 31, 77, 130, Q.shape[0] - 1])
+    idx, dist = O.match_topk(img, P, keys, K)
+    tree = spatial.cKDTree(Q)
+    for i, k in enumerate(keys):
+        dd, ii = tree.query(Q[k], k=K + 1)
+        if dd[K] ** 2 - dd[K - 1] ** 2 > 1e-9:
+            assert set(ii[:K]) == set(idx[i])
+        assert np.allclose(np.sqrt(dist[i]), dd[:K], atol=1e-12)
+
+
+def test_patch_matrix_layout():
+    """Patch vector index = ch*P*P + dr*P + dc at position id r*Wq + c."""
+    x = np.arange(2 * 5 * 6, dtype=np.float64).reshape(2, 5, 6)
+    P = 2
+    Q = O.patch_matrix(x, P)
+    Wq = 5
+    q = 2 * Wq + 3
+    assert Q.shape == (4 * 5, 8)
+    assert Q[q, 1 * 4 + 1 * 2 + 0] == x[1, 3, 3] and Q[q, 0 * 4 + 0 * 2 + 1] == x[0, 2, 4]
+
+
+# ---------------------------------------------------------------------------
+# WNNM (Eq. 5, reading A9)
+# ---------------------------------------------------------------------------
+
+
+def test_wnnm_zero_noise_is_identity():
+    rng = synth.rng_for("wnnm-id")
+    Y = rng.random((16, 8))
+    X, r, s, s2 = O.wnnm(Y, 0.0, 2 * math.sqrt(8))
+    assert np.allclose(X, Y, atol=1e-12) and r == 8
+
+
+def test_wnnm_rank_one_closed_form():
+    """Y = sigma u v^T: X^ = (s'/sigma) Y with s' = sigma - C sw^2 / (sqrt(sigma^2 - K sw^2) + eps)."""
+    rng = synth.rng_for("wnnm-r1")
+    d, K = 12, 6
+    u = rng.standard_normal(d)
+    u /= np.linalg.norm(u)
+    v = rng.standard_normal(K)
+    v /= np.linalg.norm(v)
+    sigma, sw, C = 3.0, 0.2, 2 * math.sqrt(K)
+    X, r, s, s2 = O.wnnm(sigma * np.outer(u, v), sw, C)
+    s_new = sigma - C * sw * sw / (math.sqrt(sigma * sigma - K * sw * sw) + 1e-16)
+    assert r == 1 and abs(s2[0] - s_new) < 1e-12
+    assert np.allclose(X, (s_new / sigma) * sigma * np.outer(u, v), atol=1e-12)
+
+
+def test_wnnm_two_by_two_singular_values():
+    """[[3,0],[4,5]] has Y^T Y = [[25,20],[20,25]] -> singular values sqrt(45), sqrt(5)."""
+    _, _, s, _ = O.wnnm(np.array([[3.0, 0.0], [4.0, 5.0]]), 0.0, 1.0)
+    assert np.allclose(s, [math.sqrt(45), math.sqrt(5)], atol=1e-13)
+
+
+def test_wnnm_orthogonal_columns_closed_form():
+    """Orthogonal columns of norms s_i: X^ scales column i by s'_i / s_i (a textbook diagonal case)."""
+    rng = synth.rng_for("wnnm-orth")
+    d, K = 10, 4
+    Qm, _ = np.linalg.qr(rng.standard_normal((d, K)))
+    s = np.array([5.0, 2.0, 0.9, 0.3])
+    Y = Qm * s
+    sw, C = 0.25, 2 * math.sqrt(K)
+    X, r, _, s2 = O.wnnm(Y, sw, C)
+    sh = np.sqrt(np.maximum(s * s - K * sw * sw, 0))
+    sp = np.maximum(s - C * sw * sw / (sh + 1e-16), 0)
+    assert np.allclose(X, Qm * sp, atol=1e-12) and r == int((sp > 0).sum())
+    assert sp[-1] == 0.0  # s^2 < K sw^2 -> sigma_hat = 0 -> the component is removed
+
+
+def test_wnnm_noise_only_group_vanishes():
+    rng = synth.rng_for("wnnm-noise")
+    Y = rng.standard_normal((8, 8)) * 1e-3
+    X, r, _, _ = O.wnnm(Y, 1.0, 2 * math.sqrt(8))
+    assert r == 0 and np.all(X == 0)
+
+
+def test_wnnm_recovers_noiseless_low_rank():
+    rng = synth.rng_for("wnnm-lr")
+    Y = rng.standard_normal((64, 3)) @ rng.standard_normal((3, 40))
+    X, r, _, _ = O.wnnm(Y, 1e-7, 2 * math.sqrt(40))
+    assert r >= 3 and np.linalg.norm(X - Y) / np.linalg.norm(Y) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Aggregation (reading A10)
+# ---------------------------------------------------------------------------
+
+
+def test_aggregate_identity_denoiser_returns_input():
+    rng = synth.rng_for("agg-id")
+    x = rng.random((2, 9, 10))
+    P = 3
+    Q = O.patch_matrix(x, P)
+    idx = rng.integers(0, Q.shape[0], size=(5, 4))
+    v = O.aggregate(O.gather_groups(x, P, idx, Q), idx, x, P)
+    assert np.allclose(v, x, atol=1e-14)
+
+
+def test_aggregate_hand_worked_overlap():
+    """Two 2x2 patches on a 3x4 image overlapping in one column; hand-computed average."""
+    x = np.full((1, 3, 4), 9.0)
+    P = 2
+    Wq = 3
+    idx = np.array([[0 * Wq + 0], [0 * Wq + 1]])  # top-left (0,0) and (0,1)
+    g = np.array([[[1.0, 2.0, 3.0, 4.0]], [[10.0, 20.0, 30.0, 40.0]]])  # rows (0,0),(0,1),(1,0),(1,1)
+    v = O.aggregate(g, idx, x, P)
+    want = np.array([[1.0, (2 + 10) / 2, 20.0, 9.0], [3.0, (4 + 30) / 2, 40.0, 9.0], [9.0, 9.0, 9.0, 9.0]])
+    assert np.allclose(v[0], want)
+
+
+# ---------------------------------------------------------------------------
+# GAP projection (Eq. 6 / Eq. 8)
+# ---------------------------------------------------------------------------
+
+
+def test_gap_projection_is_consistent():
+    """Phi(x) = y wherever some mask is non-zero; untouched where all masks are zero."""
+    rng = synth.rng_for("gap")
+    T, H, W = 4, 7, 9
+    A = (rng.random((T, H, W)) < 0.5).astype(float)
+    A[:, 0, 0] = 0.0
+    y = rng.random((H, W))
+    v = rng.random((T, H, W))
+    x, _ = O.gap_project(y, A, v)
+    phi = (A * x).sum(0)
+    cov = A.sum(0) > 0
+    assert np.allclose(phi[cov], y[cov], atol=1e-13)
+    assert np.allclose(x[:, 0, 0], v[:, 0, 0])
+
+
+def test_gap_fixed_point_and_init():
+    rng = synth.rng_for("gap2")
+    T, H, W = 3, 5, 6
+    A = rng.random((T, H, W))
+    v = rng.random((T, H, W))
+    y = (A * v).sum(0)
+    x, _ = O.gap_project(y, A, v)
+    assert np.allclose(x, v, atol=1e-14)
+    x0 = O.gap_init(y, A)
+    R = (A * A).sum(0)
+    assert np.allclose(x0, A * (y / R)[None])
+    # one pixel by hand: masks (1, 0, 1), y = 6 -> R = 2 -> x0 = (3, 0, 3)
+    A1 = np.array([1.0, 0.0, 1.0]).reshape(3, 1, 1)
+    assert np.allclose(O.gap_init(np.array([[6.0]]), A1).ravel(), [3.0, 0.0, 3.0])
+
+
+def test_gap_accelerated_accumulates_residual():
+    rng = synth.rng_for("gap3")
+    T, H, W = 2, 3, 3
+    A = (rng.random((T, H, W)) < 0.5).astype(float) + 0.5
+    v = rng.random((T, H, W))
+    y = rng.random((H, W))
+    yacc0 = y.copy()
+    x, yacc = O.gap_project(y, A, v, yacc0)
+    assert np.allclose(yacc, y + (y - (A * v).sum(0)))
+    assert np.allclose((A * x).sum(0), yacc)
+
+
+def test_msfa_orthogonal_masks_give_unit_normaliser():
+    """Eq. 9: orthogonal binary masks that tile the plane give R = 1 everywhere."""
+    H = W = 8
+    A = np.zeros((16, H, W))
+    for b in range(16):
+        A[b, (b // 4)::4, (b % 4)::4] = 1.0
+    assert np.all(O.gap_normaliser(A) == 1.0)
+    for i in range(16):
+        for j in range(i + 1, 16):
+            assert not np.any(A[i] * A[j])
+
+
+def test_psnr():
+    a = np.zeros((2, 4, 4))
+    b = np.full((2, 4, 4), 0.1)
+    assert abs(O.psnr(a, b) - 20.0) < 1e-12
