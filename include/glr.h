@@ -58,7 +58,8 @@ enum {
   GLR_DEV_TIMEOUT = 1u << 0,       /* an mbarrier / flag wait hit its iteration cap */
   GLR_DEV_NONFINITE = 1u << 1,     /* NaN or Inf met in an input */
   GLR_DEV_SVD_NOCONV = 1u << 2,    /* a Jacobi SVD reached its sweep cap */
-  GLR_DEV_CAND_OVERFLOW = 1u << 3  /* a candidate buffer overflowed (result still exact, slower) */
+  GLR_DEV_CAND_OVERFLOW = 1u << 3, /* a candidate buffer overflowed (result still exact, slower) */
+  GLR_DEV_BAD_INDEX = 1u << 4      /* a key / match position id was outside 0..Hq*Wq-1 (entry skipped) */
 };
 
 /* A batch of equally sized images searched independently. */
@@ -186,7 +187,7 @@ glr_status glr_gap_step(const float* y, const float* masks, int64_t mask_group_s
  * `stream`).  bits = OR of GLR_DEV_*; counters (may be NULL) receives 4
  * uint32 values: [0] keys whose candidate buffer overflowed, [1] groups whose
  * SVD hit the sweep cap, [2] total Jacobi sweeps, [3] groups processed.
- * Returns GLR_EDEVICE if any error bit (timeout, non-finite) is set.
+ * Returns GLR_EDEVICE if any error bit (timeout, non-finite, bad index) is set.
  * Pass reset != 0 to clear the block afterwards.
  */
 glr_status glr_poll_status(const void* ws, uint32_t* bits, uint32_t* counters, int32_t reset,
@@ -197,6 +198,18 @@ const char* glr_status_string(glr_status s);
 
 /* Number of kernels this library has launched in this process (all devices). */
 uint64_t glr_launch_count(void);
+
+/*
+ * Per-kernel timing: when enabled, the library records a CUDA event pair on
+ * the launch stream around every kernel it launches (do not enable while a
+ * stream is being captured into a CUDA graph).  glr_profile_collect waits for
+ * the recorded events, sums the durations per kernel name since the previous
+ * collect and clears the record.  names receives `cap` NUL-terminated strings
+ * of 48 bytes each; total_ms and launches receive `cap` values.  Returns the
+ * number of distinct kernels written (<= cap), or -1 on a CUDA error.
+ */
+glr_status glr_profile_enable(int32_t on);
+int32_t glr_profile_collect(char* names, float* total_ms, int32_t* launches, int32_t cap);
 
 /* Version string of the library build. */
 const char* glr_version(void);

@@ -1,0 +1,62 @@
+// Launch functions of the GLR kernels (host side), one translation unit per step.
+#pragma once
+
+#include <algorithm>
+#include <type_traits>
+
+#include "glr_common.cuh"
+
+namespace glr {
+
+// ---- GAP projection (k_gap.cu)
+glr_status launch_gap_step(const float* y, const float* masks, long long mstride, const float* v, int G, int T,
+                           long long HW, int accelerate, float* y_acc, float* x_out, cudaStream_t s);
+
+// ---- key selection (k_select.cu)
+struct SelectWs {
+  size_t S_off, R_off, cand_off, cnt_off, bitmap_off, total;
+};
+SelectWs select_ws_layout(const glr_images& im, int N);
+glr_status launch_select(const float* x, const glr_images& im, float th, int N, int32_t* keys, int32_t* n_found,
+                         int32_t* n_corner, char* ws, const SelectWs& L, cudaStream_t s);
+
+// ---- matching (k_match.cu, k_match_tc.cu)
+struct MatchPlan {
+  int mode;
+  int K, Kp;            // matches, candidates kept per stream
+  int cap;              // stream compaction trigger (entries; buffers hold cap + 32)
+  int splits;           // position splits per key tile
+  int subs;             // streams per key and split (column halves inside a tile)
+  int streams_per_key;  // splits * subs
+  int key_tile;         // keys per CTA
+  int Npad;             // N rounded up to key_tile
+  int pos_tile;         // positions per scorer tile
+  int pos_tiles;        // position tiles per image
+  int tiles_per_split;
+  int dk;               // BF16 operand row length (elements)
+  long long npos_pad;   // BF16 position rows per image (pos_tiles * pos_tile)
+  size_t mean_off, qn_off, keyv_off, buf_off, bufcnt_off, qpack_off, kpack_off, total;
+};
+MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o);
+glr_status launch_match(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found, int N,
+                        const MatchPlan& plan, int32_t* idx, float* dist, char* ws, cudaStream_t s);
+// tensor-core scorer (k_match_tc.cu); returns GLR_ENOTSUP when the shape is not covered
+glr_status launch_match_tc(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found,
+                           int N, const MatchPlan& plan, char* ws, cudaStream_t s);
+
+// ---- low-rank step (k_lowrank.cu)
+glr_status launch_gather(const float* x, const glr_images& im, const int32_t* idx, const int32_t* n_found, int N,
+                         int K, float* groups, StatusBlock* st, cudaStream_t s);
+glr_status launch_wnnm(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
+                       float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
+
+// ---- aggregation (k_aggregate.cu)
+struct AggWs {
+  size_t num_off, cnt_off, total;
+};
+AggWs agg_ws_layout(const glr_images& im);
+glr_status launch_aggregate(const float* groups, const int32_t* idx, const int32_t* n_found, const glr_images& im,
+                            int N, int K, const float* x_in, float* v_out, char* ws, const AggWs& L,
+                            cudaStream_t s);
+
+}  // namespace glr

@@ -1,0 +1,110 @@
+// Aggregation: the low-rank patch estimates go back to their positions and
+// overlapping estimates are averaged (weight 1); uncovered pixels keep x_in.
+//
+//  k_scatter    one warp per matched patch (group row); lanes add its d values
+//               into the numerator planes with FP32 atomics (L2-resident), and
+//               lane 0 adds 1 to the integer count of that patch position.
+//  k_normalise  32x32 pixel tiles: den = P x P box sum of the position counts
+//               (separable, in shared memory), v = num / den or x_in.
+#include "glr_kernels.cuh"
+
+namespace glr {
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_scatter(const float* __restrict__ groups, const int32_t* __restrict__ idx,
+                                                 const int32_t* __restrict__ n_found, int n_img, int C, int H, int W,
+                                                 int P, int N, int K, float* __restrict__ num,
+                                                 int* __restrict__ cnt, StatusBlock* st) {
+  const int d = C * P * P;
+  const int Wq = W - P + 1, Hq = H - P + 1;
+  const long long rows = (long long)n_img * N * K;
+  const int lane = threadIdx.x & 31;
+  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < rows;
+       row += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const long long f = row / ((long long)N * K);
+    const int k = (int)((row - f * (long long)N * K) / K);
+    if (k >= min(n_found[f], N)) continue;
+    const int q = idx[row];
+    if ((unsigned)q >= (unsigned)(Wq * Hq)) {
+      if (lane == 0) status_set(st, GLR_DEV_BAD_INDEX);
+      continue;
+    }
+    const int r = q / Wq, c = q - (q / Wq) * Wq;
+    const float* src = groups + row * d;
+    for (int e = lane; e < d; e += 32) {
+      const int ch = e / (P * P), rr = (e / P) % P, cc = e % P;
+      atomicAdd(num + ((f * C + ch) * H + r + rr) * (long long)W + c + cc, __ldg(src + e));
+    }
+    if (lane == 0) atomicAdd(cnt + f * (long long)Hq * Wq + q, 1);
+  }
+}
+
+constexpr int AT = 32;
+
+__global__ void __launch_bounds__(256) k_normalise(const float* __restrict__ num, const int* __restrict__ cnt,
+                                                   const float* x_in, float* v_out, int C, int H, int W, int P) {
+  // counts of positions that cover the tile: rows r0-P+1 .. r0+AT-1
+  __shared__ int cs[AT + 16][AT + 16];
+  __shared__ int hs[AT + 16][AT];
+  const int Hq = H - P + 1, Wq = W - P + 1;
+  const int f = blockIdx.z;
+  const int r0 = blockIdx.y * AT, c0 = blockIdx.x * AT;
+  const int tid = threadIdx.x;
+  const int ext = AT + P - 1;
+  const int* cf = cnt + (long long)f * Hq * Wq;
+  for (int i = tid; i < ext * ext; i += 256) {
+    const int a = i / ext, b = i % ext;
+    const int pr = r0 - (P - 1) + a, pc = c0 - (P - 1) + b;
+    cs[a][b] = (pr >= 0 && pr < Hq && pc >= 0 && pc < Wq) ? cf[(long long)pr * Wq + pc] : 0;
+  }
+  __syncthreads();
+  for (int i = tid; i < ext * AT; i += 256) {
+    const int a = i / AT, b = i % AT;
+    int s = 0;
+    for (int t = 0; t < P; ++t) s += cs[a][b + t];
+    hs[a][b] = s;
+  }
+  __syncthreads();
+  for (int i = tid; i < AT * AT; i += 256) {
+    const int a = i / AT, b = i % AT;
+    const int rr = r0 + a, cc = c0 + b;
+    if (rr >= H || cc >= W) continue;
+    int den = 0;
+    for (int t = 0; t < P; ++t) den += hs[a + t][b];
+    for (int ch = 0; ch < C; ++ch) {
+      const long long o = (((long long)f * C + ch) * H + rr) * W + cc;
+      v_out[o] = den > 0 ? num[o] / (float)den : x_in[o];
+    }
+  }
+}
+
+}  // namespace
+
+AggWs agg_ws_layout(const glr_images& im) {
+  WsLayout L;
+  AggWs w;
+  w.num_off = L.take((size_t)im.n_img * im.C * im.H * im.W * 4);
+  w.cnt_off = L.take((size_t)im.n_img * (im.H - im.P + 1) * (im.W - im.P + 1) * 4);
+  w.total = L.off;
+  return w;
+}
+
+glr_status launch_aggregate(const float* groups, const int32_t* idx, const int32_t* n_found, const glr_images& im,
+                            int N, int K, const float* x_in, float* v_out, char* ws, const AggWs& L,
+                            cudaStream_t s) {
+  float* num = reinterpret_cast<float*>(ws + L.num_off);
+  int* cnt = reinterpret_cast<int*>(ws + L.cnt_off);
+  const size_t num_b = (size_t)im.n_img * im.C * im.H * im.W * 4;
+  const size_t cnt_b = (size_t)im.n_img * (im.H - im.P + 1) * (im.W - im.P + 1) * 4;
+  if (cudaMemsetAsync(num, 0, num_b, s) != cudaSuccess) return GLR_ECUDA;
+  if (cudaMemsetAsync(cnt, 0, cnt_b, s) != cudaSuccess) return GLR_ECUDA;
+  const long long rows = (long long)im.n_img * N * K;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(rows * 32, 256), 152LL * 32));
+  GLR_LAUNCH("k_scatter", s, k_scatter<<<blocks, 256, 0, s>>>(groups, idx, n_found, im.n_img, im.C, im.H, im.W, im.P, N, K, num, cnt, reinterpret_cast<StatusBlock*>(ws)));
+  dim3 g((unsigned)ceil_div(im.W, AT), (unsigned)ceil_div(im.H, AT), (unsigned)im.n_img);
+  GLR_LAUNCH("k_normalise", s, k_normalise<<<g, 256, 0, s>>>(num, cnt, x_in, v_out, im.C, im.H, im.W, im.P));
+  return GLR_OK;
+}
+
+}  // namespace glr

@@ -1,0 +1,85 @@
+// GAP projection for y = sum_t A_t x_t (Eq. 6; Eq. 8 with orthogonal masks, Eq. 9).
+//   R = sum_t A_t^2 (0 -> 1), x_t = v_t + A_t (y - sum_s A_s v_s) / R
+// One thread per pixel (4 pixels with float4 when the plane size allows);
+// HBM-bound: reads y, T masks, T estimates and writes T outputs.
+#include "glr_kernels.cuh"
+
+namespace glr {
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_gap_step(const float* __restrict__ y, const float* __restrict__ masks,
+                                                  long long mstride, const float* v, int G, int T,
+                                                  long long HW, int accelerate, float* y_acc, float* x_out) {
+  using V = typename std::conditional<VEC, float4, float>::type;
+  constexpr int L = VEC ? 4 : 1;
+  const long long nvec = HW / L;
+  const long long total = (long long)G * nvec;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long g = i / nvec, p = i - g * nvec;
+    const V* yv = reinterpret_cast<const V*>(y + g * HW) + p;
+    const float* mg = masks + g * mstride;
+    float R[L], phi[L], yy[L];
+    {
+      V t = __ldg(yv);
+      const float* tp = reinterpret_cast<const float*>(&t);
+#pragma unroll
+      for (int l = 0; l < L; ++l) { yy[l] = tp[l]; R[l] = 0.f; phi[l] = 0.f; }
+    }
+    for (int t = 0; t < T; ++t) {
+      V a = __ldg(reinterpret_cast<const V*>(mg + (long long)t * HW) + p);
+      const float* ap = reinterpret_cast<const float*>(&a);
+      V vv;
+      float* vp = reinterpret_cast<float*>(&vv);
+      if (v) vv = *(reinterpret_cast<const V*>(v + (g * T + t) * HW) + p);
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        R[l] = fmaf(ap[l], ap[l], R[l]);
+        if (v) phi[l] = fmaf(ap[l], vp[l], phi[l]);
+      }
+    }
+    float coef[L];
+    if (accelerate) {
+      V* yap = reinterpret_cast<V*>(y_acc + g * HW) + p;
+      V ya = *yap;
+      float* yp = reinterpret_cast<float*>(&ya);
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        yp[l] = yp[l] + (yy[l] - phi[l]);
+        yy[l] = yp[l];
+      }
+      *yap = ya;
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) coef[l] = (yy[l] - phi[l]) / (R[l] == 0.f ? 1.f : R[l]);
+    for (int t = 0; t < T; ++t) {
+      V a = __ldg(reinterpret_cast<const V*>(mg + (long long)t * HW) + p);
+      const float* ap = reinterpret_cast<const float*>(&a);
+      V vv;
+      float* vp = reinterpret_cast<float*>(&vv);
+      if (v) vv = *(reinterpret_cast<const V*>(v + (g * T + t) * HW) + p);
+      V o;
+      float* op = reinterpret_cast<float*>(&o);
+#pragma unroll
+      for (int l = 0; l < L; ++l) op[l] = fmaf(ap[l], coef[l], v ? vp[l] : 0.f);
+      *(reinterpret_cast<V*>(x_out + (g * T + t) * HW) + p) = o;
+    }
+  }
+}
+
+glr_status launch_gap_step(const float* y, const float* masks, long long mstride, const float* v, int G, int T,
+                           long long HW, int accelerate, float* y_acc, float* x_out, cudaStream_t s) {
+  const bool vec = (HW % 4 == 0) && ((uintptr_t)y % 16 == 0) && ((uintptr_t)masks % 16 == 0) &&
+                   (mstride % 4 == 0) && (!v || (uintptr_t)v % 16 == 0) && ((uintptr_t)x_out % 16 == 0) &&
+                   (!y_acc || (uintptr_t)y_acc % 16 == 0);
+  const long long work = (long long)G * (vec ? HW / 4 : HW);
+  int blocks = (int)std::min<long long>(ceil_div(work, 256), 152LL * 16);
+  if (blocks < 1) blocks = 1;
+  if (vec)
+    GLR_LAUNCH("k_gap_step", s, k_gap_step<true><<<blocks, 256, 0, s>>>(y, masks, mstride, v, G, T, HW, accelerate, y_acc, x_out));
+  else
+    GLR_LAUNCH("k_gap_step", s, k_gap_step<false><<<blocks, 256, 0, s>>>(y, masks, mstride, v, G, T, HW, accelerate, y_acc, x_out));
+  return GLR_OK;
+}
+
+}  // namespace glr

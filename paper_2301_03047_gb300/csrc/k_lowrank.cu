@@ -1,0 +1,249 @@
+// Grouping R~_i x and the WNNM low-rank step of Eq. 5.
+//
+//  k_gather      groups[f][k][j][:] = patch at idx[f][k][j] (vector order
+//                ch, dr, dc).  One thread per 4 output floats: coalesced 16-byte
+//                stores; loads hit the L2-resident image.  HBM-write bound.
+//  k_jacobi_wnnm one warp per group Y (d x K).  One-sided Jacobi (Hestenes)
+//                SVD in FP32 with the columns held in registers: lane L owns two
+//                columns; the K/2 lanes rotate their column pairs in parallel and
+//                then pass columns along a circle (round-robin tournament
+//                ordering) with two warp shuffles per element, so every pair
+//                meets once per sweep.  Rotation angles use the stable
+//                formulas of Rutishauser (t = sign(z)/(|z| + sqrt(1 + z^2))).
+//                Sweeps stop when no pair has |a.b| > tol sqrt(|a|^2 |b|^2).
+//                With W = Y V (columns w_i = s_i u_i) the WNNM estimate is
+//                X^ = U diag(s') V^T = sum_i (s'_i / s_i^3) w_i (w_i^T Y),
+//                formed from the active w_i staged in shared memory and the
+//                original Y re-read from the group buffer.
+#include "glr_kernels.cuh"
+
+namespace glr {
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_gather(const float* __restrict__ x, int n_img, int C, int H, int W, int P,
+                                                const int32_t* __restrict__ idx, const int32_t* __restrict__ n_found,
+                                                int N, int K, float* __restrict__ groups, StatusBlock* st) {
+  const int d = C * P * P;
+  const int Wq = W - P + 1;
+  const int q4 = d / 4;  // d % 4 == 0 on this path
+  const long long per_img = (long long)N * K * q4;
+  const long long total = (long long)n_img * per_img;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / per_img;
+    const long long rem = i - f * per_img;
+    const long long gj = rem / q4;  // k*K + j
+    const int e0 = (int)(rem - gj * q4) * 4;
+    const int k = (int)(gj / K);
+    if (k >= min(n_found[f], N)) continue;
+    const int q = idx[f * (long long)N * K + gj];
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if ((unsigned)q >= (unsigned)(Wq * (H - P + 1))) {
+      if (e0 == 0) status_set(st, GLR_DEV_BAD_INDEX);
+      reinterpret_cast<float4*>(groups)[(f * (long long)N * K + gj) * q4 + e0 / 4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const int r = q / Wq, c = q - (q / Wq) * Wq;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = e0 + t;
+      const int ch = e / (P * P), rr = (e / P) % P, cc = e % P;
+      v[t] = __ldg(x + (((long long)f * C + ch) * H + r + rr) * W + c + cc);
+    }
+    reinterpret_cast<float4*>(groups)[(f * (long long)N * K + gj) * q4 + e0 / 4] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+template <int DMAX>
+__device__ __forceinline__ void jacobi_pair(float (&a)[DMAX], float (&b)[DMAX], float tol, bool active, bool& rotated) {
+  float alpha = 0.f, beta = 0.f, gamma = 0.f;
+#pragma unroll
+  for (int r = 0; r < DMAX; ++r) {
+    alpha = fmaf(a[r], a[r], alpha);
+    beta = fmaf(b[r], b[r], beta);
+    gamma = fmaf(a[r], b[r], gamma);
+  }
+  if (active && fabsf(gamma) > tol * sqrtf(alpha * beta) && gamma != 0.f) {
+    const float zeta = (beta - alpha) / (2.f * gamma);
+    const float az = fabsf(zeta);
+    float t = (az < 1e18f) ? 1.f / (az + sqrtf(1.f + zeta * zeta)) : 0.5f / az;
+    t = copysignf(t, zeta);
+    const float cs = rsqrtf(1.f + t * t);
+    const float sn = cs * t;
+#pragma unroll
+    for (int r = 0; r < DMAX; ++r) {
+      const float ar = a[r], br = b[r];
+      a[r] = cs * ar - sn * br;
+      b[r] = sn * ar + cs * br;
+    }
+    rotated = true;
+  }
+}
+
+// DMAX rows per column, KMAX <= 64 columns, one warp per group, WARPS groups per CTA.
+template <int DMAX, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_jacobi_wnnm(int n_img, int d, int N, int K,
+                                                            const int32_t* __restrict__ n_found, float sigma_w,
+                                                            float c_wnnm, float tol, int max_sweeps,
+                                                            float* __restrict__ groups, int32_t* __restrict__ rank,
+                                                            StatusBlock* st) {
+  extern __shared__ float wsm[];  // [WARPS][64][DMAX]: active columns of W
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float* Ws = wsm + (size_t)wid * 64 * DMAX;
+  const long long ngroups = (long long)n_img * N;
+  const int m = (K + 1) / 2;  // lanes holding a column pair
+  const bool live = lane < m;
+  for (long long g = blockIdx.x * (long long)WARPS + wid; g < ngroups; g += (long long)gridDim.x * WARPS) {
+    const int f = (int)(g / N), k = (int)(g - (long long)f * N);
+    if (k >= min(n_found[f], N)) continue;
+    float* Y = groups + g * (long long)K * d;
+    float a[DMAX], b[DMAX];
+    const int ja = 2 * lane, jb = 2 * lane + 1;
+#pragma unroll
+    for (int r = 0; r < DMAX; ++r) {
+      a[r] = (live && r < d) ? Y[(long long)ja * d + r] : 0.f;
+      b[r] = (live && jb < K && r < d) ? Y[(long long)jb * d + r] : 0.f;
+    }
+    // non-finite input: leave the group unchanged and flag it
+    float s0 = 0.f;
+#pragma unroll
+    for (int r = 0; r < DMAX; ++r) s0 += a[r] + b[r];
+    if (__any_sync(0xffffffffu, !isfinite(s0))) {
+      if (lane == 0) status_set(st, GLR_DEV_NONFINITE);
+      if (rank && lane == 0) rank[g] = -1;
+      continue;
+    }
+    int sweep = 0;
+    bool converged = (m < 1);
+    while (!converged && sweep < max_sweeps) {
+      bool rotated = false;
+      for (int round = 0; round < 2 * m - 1; ++round) {
+        jacobi_pair<DMAX>(a, b, tol, live, rotated);
+        if (m > 1) {
+          // circle rotation: slot top[0] stays; top[1] <- bot[0]; top[k] <- top[k-1];
+          // bot[m-1] <- top[m-1]; bot[k] <- bot[k+1]
+#pragma unroll
+          for (int r = 0; r < DMAX; ++r) {
+            const float up_src = (lane == 0) ? b[r] : a[r];
+            const float t_in = __shfl_up_sync(0xffffffffu, up_src, 1);
+            const float b_in = __shfl_down_sync(0xffffffffu, b[r], 1);
+            const float na = (lane == 0) ? a[r] : t_in;
+            const float nb = (lane == m - 1) ? a[r] : b_in;
+            a[r] = na;
+            b[r] = nb;
+          }
+        }
+      }
+      ++sweep;
+      converged = !__any_sync(0xffffffffu, rotated);
+    }
+    if (!converged && lane == 0) {
+      atomicAdd(&st->svd_noconv, 1u);
+      status_set(st, GLR_DEV_SVD_NOCONV);
+    }
+    if (lane == 0) {
+      atomicAdd(&st->sweeps, (unsigned)sweep);
+      atomicAdd(&st->groups, 1u);
+    }
+    // singular values and WNNM shrinkage (reading: tau_i = C sw^2 / (sigma_hat_i + eps))
+    float na2 = 0.f, nb2 = 0.f;
+#pragma unroll
+    for (int r = 0; r < DMAX; ++r) {
+      na2 = fmaf(a[r], a[r], na2);
+      nb2 = fmaf(b[r], b[r], nb2);
+    }
+    const float sw2 = sigma_w * sigma_w;
+    float coef_a = 0.f, coef_b = 0.f;
+    {
+      const float sa = sqrtf(na2), sb = sqrtf(nb2);
+      const float ha = sqrtf(fmaxf(na2 - (float)K * sw2, 0.f)), hb = sqrtf(fmaxf(nb2 - (float)K * sw2, 0.f));
+      const float pa = fmaxf(sa - c_wnnm * sw2 / (ha + 1e-8f), 0.f);
+      const float pb = fmaxf(sb - c_wnnm * sw2 / (hb + 1e-8f), 0.f);
+      if (live && pa > 0.f && sa > 0.f) coef_a = pa / (sa * na2);
+      if (live && pb > 0.f && sb > 0.f) coef_b = pb / (sb * nb2);
+    }
+    const unsigned act_a = __ballot_sync(0xffffffffu, coef_a != 0.f);
+    const unsigned act_b = __ballot_sync(0xffffffffu, coef_b != 0.f);
+    const int ra = __popc(act_a), rb = __popc(act_b);
+    const int rnk = ra + rb;
+    if (rank && lane == 0) rank[g] = rnk;
+    // stage the active columns w_i into shared memory (compacted) with coefficients
+    __shared__ float coef_s[WARPS][64];
+    {
+      const int pa = __popc(act_a & ((1u << lane) - 1u));
+      const int pb = ra + __popc(act_b & ((1u << lane) - 1u));
+      if (coef_a != 0.f) {
+#pragma unroll
+        for (int r = 0; r < DMAX; ++r) Ws[pa * DMAX + r] = a[r];
+        coef_s[wid][pa] = coef_a;
+      }
+      if (coef_b != 0.f) {
+#pragma unroll
+        for (int r = 0; r < DMAX; ++r) Ws[pb * DMAX + r] = b[r];
+        coef_s[wid][pb] = coef_b;
+      }
+    }
+    __syncwarp();
+    // X^ columns j = 2 lane, 2 lane + 1: x^_j = sum_i coef_i w_i (w_i . y_j)
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const int j = 2 * lane + h;
+      const bool own = live && j < K;
+      float y[DMAX], o[DMAX];
+#pragma unroll
+      for (int r = 0; r < DMAX; ++r) {
+        y[r] = (own && r < d) ? Y[(long long)j * d + r] : 0.f;
+        o[r] = 0.f;
+      }
+      for (int i = 0; i < rnk; ++i) {
+        const float* w = Ws + i * DMAX;
+        float z = 0.f;
+#pragma unroll
+        for (int r = 0; r < DMAX; ++r) z = fmaf(w[r], y[r], z);
+        z *= coef_s[wid][i];
+#pragma unroll
+        for (int r = 0; r < DMAX; ++r) o[r] = fmaf(z, w[r], o[r]);
+      }
+      __syncwarp();
+      if (own) {
+#pragma unroll
+        for (int r = 0; r < DMAX; ++r)
+          if (r < d) Y[(long long)j * d + r] = o[r];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+glr_status launch_gather(const float* x, const glr_images& im, const int32_t* idx, const int32_t* n_found, int N,
+                         int K, float* groups, StatusBlock* st, cudaStream_t s) {
+  const int d = im.C * im.P * im.P;
+  if (d % 4 != 0) return GLR_ENOTSUP;
+  const long long total = (long long)im.n_img * N * K * (d / 4);
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+  GLR_LAUNCH("k_gather", s, k_gather<<<blocks, 256, 0, s>>>(x, im.n_img, im.C, im.H, im.W, im.P, idx, n_found, N, K, groups, st));
+  return GLR_OK;
+}
+
+glr_status launch_wnnm(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
+                       float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s) {
+  const int d = im.C * im.P * im.P;
+  if (d > 64 || K > 64 || K < 1) return GLR_ENOTSUP;
+  constexpr int WARPS = 4;
+  constexpr int DMAX = 64;
+  const size_t smem = (size_t)WARPS * 64 * DMAX * sizeof(float);
+  if (cudaFuncSetAttribute(k_jacobi_wnnm<DMAX, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return GLR_ECUDA;
+  const long long ngroups = (long long)im.n_img * N;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(ngroups, WARPS), 152LL * 64));
+  const float tol = 2e-6f;
+  GLR_LAUNCH("k_jacobi_wnnm", s, k_jacobi_wnnm<DMAX, WARPS><<<blocks, WARPS * 32, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, 30,
+                                                             groups, rank, st));
+  return GLR_OK;
+}
+
+}  // namespace glr

@@ -1,0 +1,431 @@
+// Global patch matching (Section 2: the search covers every position of the
+// image; the similarity is the squared L2 distance of Eq. 1, evaluated as
+// ||p||^2 - 2<p,q> + ||q||^2 for all key/position pairs, i.e. the Conv2d
+// heat map of Eq. 4 on intensities) fused with a running per-key top-K.
+//
+// Pipeline of glr_match_topk:
+//   k_image_mean   mean of each image (values are shifted by it before the
+//                  expanded form; distances are unchanged, cancellation shrinks)
+//   k_patch_norms  ||q - mu||^2 for every position
+//   k_key_vectors  shifted key patches, [img][key][d]
+//   scorer         FP32 (k_match_fp32, below) or BF16 tcgen05 (k_match_tc.cu):
+//                  scores of 128 keys x all positions of a split, pushed
+//                  through the running top-K' streams (topk_stream.cuh)
+//   k_rerank       per key: exact FP32 sum((p-q)^2) of every kept candidate,
+//                  sort by (distance, id), emit the K best.
+#include "glr_kernels.cuh"
+#include "topk_stream.cuh"
+
+namespace glr {
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_image_mean(const float* __restrict__ x, long long n_per_img,
+                                                    float* __restrict__ mean) {
+  __shared__ double red[256];
+  const float* xf = x + blockIdx.x * n_per_img;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n_per_img; i += 256) s += (double)xf[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) mean[blockIdx.x] = (float)(red[0] / (double)n_per_img);
+}
+
+__global__ void __launch_bounds__(256) k_patch_norms(const float* __restrict__ x, const float* __restrict__ mean,
+                                                     int n_img, int C, int H, int W, int P, float* __restrict__ qn) {
+  const int Hq = H - P + 1, Wq = W - P + 1;
+  const long long npos = (long long)Hq * Wq;
+  const long long total = (long long)n_img * npos;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / npos;
+    const int q = (int)(i - f * npos);
+    const int r = q / Wq, c = q - (q / Wq) * Wq;
+    const float mu = mean[f];
+    float s = 0.f;
+    for (int ch = 0; ch < C; ++ch)
+      for (int dr = 0; dr < P; ++dr) {
+        const float* row = x + (((long long)f * C + ch) * H + r + dr) * W + c;
+        for (int dc = 0; dc < P; ++dc) {
+          const float v = __ldg(row + dc) - mu;
+          s = fmaf(v, v, s);
+        }
+      }
+    qn[i] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_key_vectors(const float* __restrict__ x, const float* __restrict__ mean,
+                                                     const int32_t* __restrict__ keys,
+                                                     const int32_t* __restrict__ n_found, int n_img, int C, int H,
+                                                     int W, int P, int N, int Npad, float* __restrict__ keyv,
+                                                     StatusBlock* st) {
+  const int d = C * P * P;
+  const int Wq = W - P + 1;
+  const long long total = (long long)n_img * Npad * d;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long fk = i / d;
+    const int e = (int)(i - fk * d);
+    const int f = (int)(fk / Npad), k = (int)(fk - (long long)f * Npad);
+    float v = 0.f;
+    const int q = k < min(n_found[f], N) ? keys[(long long)f * N + k] : -1;
+    if ((unsigned)q >= (unsigned)(Wq * (H - P + 1))) {
+      if (q != -1 && e == 0) status_set(st, GLR_DEV_BAD_INDEX);
+    } else {
+      const int r = q / Wq, c = q - (q / Wq) * Wq;
+      const int ch = e / (P * P), dr = (e / P) % P, dc = e % P;
+      v = __ldg(x + (((long long)f * C + ch) * H + r + dr) * W + c + dc) - mean[f];
+    }
+    keyv[i] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 scorer: 128 keys x 128 positions per tile, 256 threads, 8x8 per thread.
+// A position tile is one row r of the position grid, columns c0..c0+127; its
+// patches are read from a C x P x (128+P-1) strip of the image, so no patch
+// matrix is materialised.  Thread (ty, tx) owns keys 8ty..8ty+7 and positions
+// 8tx..8tx+7; for each (channel, patch row) it loads a 16-float window of the
+// strip once and reuses it for the P column offsets.
+// ---------------------------------------------------------------------------
+constexpr int FT = 128;     // keys and positions per tile
+constexpr int SC_LD = 132;  // score tile row stride (conflict-free LDS.128 by row owners)
+
+template <int P>
+__global__ void __launch_bounds__(256, 2)
+    k_match_fp32(const float* __restrict__ x, const float* __restrict__ mean, const float* __restrict__ qn,
+                 const float* __restrict__ keyv, const int32_t* __restrict__ n_found, int C, int H, int W, int Npad,
+                 int splits, int tiles_per_split, StreamCfg cfg, uint2* __restrict__ bufs,
+                 int* __restrict__ buf_cnt) {
+  extern __shared__ __align__(16) float smem[];
+  const int d = C * P * P;
+  float* As = smem;                         // [d][FT]
+  float* strip = As + d * FT;               // [C][P][FT + 8]
+  float* Sc = strip + C * P * (FT + 8);     // [FT][SC_LD]
+  float* pn = Sc + FT * SC_LD;              // [FT]
+  unsigned* hist = reinterpret_cast<unsigned*>(pn + FT);  // [8][256]
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int kt = blockIdx.x, f = blockIdx.y, split = blockIdx.z;
+  const int Hq = H - P + 1, Wq = W - P + 1;
+  const int tpr = (Wq + FT - 1) / FT;
+  const int ntiles = Hq * tpr;
+  const int nf = min(n_found[f], Npad);
+  const float mu = mean[f];
+
+  // key tile, transposed: As[e][i]
+  const float* kv = keyv + ((long long)f * Npad + (long long)kt * FT) * d;
+  for (int i = tid; i < d * FT; i += 256) {
+    const int key = i / d, e = i - (i / d) * d;
+    As[e * FT + key] = kv[(long long)key * d + e];
+  }
+  __syncthreads();
+  if (tid < FT) {
+    float s = 0.f;
+    for (int e = 0; e < d; ++e) s = fmaf(As[e * FT + tid], As[e * FT + tid], s);
+    pn[tid] = s;
+  }
+  // stream owned by this thread: row = 32 (wid % 4) + lane, column half h = wid / 4
+  const int row = 32 * (wid & 3) + lane;
+  const int h = wid >> 2;
+  const int key = kt * FT + row;
+  const long long stream = (((long long)f * Npad + key) * splits + split) * 2 + h;
+  uint2* mybuf = bufs + stream * (cfg.cap + 32);
+  float tau = (key < nf) ? INFINITY : -INFINITY;
+  int cnt = 0;
+  unsigned* whist = hist + wid * 256;
+
+  const int ty = tid >> 4, tx = tid & 15;
+  const int t_begin = split * tiles_per_split;
+  const int t_end = min(ntiles, t_begin + tiles_per_split);
+  for (int t = t_begin; t < t_end; ++t) {
+    const int r = t / tpr, c0 = (t - (t / tpr) * tpr) * FT;
+    __syncthreads();  // previous tile fully consumed
+    for (int i = tid; i < C * P * (FT + 8); i += 256) {
+      const int cr = i / (FT + 8), j = i - (i / (FT + 8)) * (FT + 8);
+      const int ch = cr / P, dr = cr - (cr / P) * P;
+      const int cc = c0 + j;
+      strip[i] = (cc < W) ? __ldg(x + (((long long)f * C + ch) * H + r + dr) * W + cc) - mu : 0.f;
+    }
+    __syncthreads();
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int ch = 0; ch < C; ++ch) {
+#pragma unroll
+      for (int dr = 0; dr < P; ++dr) {
+        float w[16];
+        const float4* sp = reinterpret_cast<const float4*>(strip + (ch * P + dr) * (FT + 8) + tx * 8);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float4 t4 = sp[v];
+          w[4 * v] = t4.x;
+          w[4 * v + 1] = t4.y;
+          w[4 * v + 2] = t4.z;
+          w[4 * v + 3] = t4.w;
+        }
+#pragma unroll
+        for (int dc = 0; dc < P; ++dc) {
+          const float4* ap = reinterpret_cast<const float4*>(As + ((ch * P + dr) * P + dc) * FT + ty * 8);
+          const float4 a0 = ap[0], a1 = ap[1];
+          const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], w[j + dc], acc[i][j]);
+        }
+      }
+    }
+    // scores s = ||p||^2 + ||q||^2 - 2 <p,q>; missing positions -> +inf
+    {
+      float qv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int cc = c0 + tx * 8 + j;
+        qv[j] = (cc < Wq) ? __ldg(qn + (long long)f * Hq * Wq + (long long)r * Wq + cc) : INFINITY;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float pi = pn[ty * 8 + i];
+        float o[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[j] = fmaf(-2.f, acc[i][j], pi + qv[j]);
+        float4* dst = reinterpret_cast<float4*>(Sc + (ty * 8 + i) * SC_LD + tx * 8);
+        dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+      }
+    }
+    __syncthreads();
+    // row owners push their half row in two 32-column chunks
+    const int qbase = r * Wq + c0;
+#pragma unroll 1
+    for (int ch2 = 0; ch2 < 2; ++ch2) {
+      const int col0 = h * 64 + ch2 * 32;
+      const int nvalid = max(0, min(32, Wq - (c0 + col0)));
+      float s[32];
+      const float4* src = reinterpret_cast<const float4*>(Sc + row * SC_LD + col0);
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const float4 t4 = src[v];
+        s[4 * v] = t4.x;
+        s[4 * v + 1] = t4.y;
+        s[4 * v + 2] = t4.z;
+        s[4 * v + 3] = t4.w;
+      }
+      stream_push<32>(s, qbase + col0, nvalid, tau, cnt, mybuf, cfg, whist);
+    }
+  }
+  stream_finish(tau, cnt, mybuf, cfg, whist);
+  buf_cnt[stream] = (key < nf) ? cnt : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Exact re-rank: one warp per key.  Candidates of every stream of the key are
+// scored with the direct FP32 sum((p - q)^2) (fixed order over the vector
+// index), then sorted by (distance, position id) with a bitonic sort in shared
+// memory; the first K are written.
+// ---------------------------------------------------------------------------
+constexpr int RR_WARPS = 4;
+constexpr int kRerankMaxList = 2048;  // candidates of one key held by the re-rank (pow2)
+
+__global__ void __launch_bounds__(RR_WARPS * 32)
+    k_rerank(const float* __restrict__ x, const int32_t* __restrict__ keys, const int32_t* __restrict__ n_found,
+             int n_img, int C, int H, int W, int P, int N, int Npad, int K, int streams_per_key, int cap_slots,
+             int kp, int pow2, const uint2* __restrict__ bufs, const int* __restrict__ buf_cnt,
+             int32_t* __restrict__ idx, float* __restrict__ dist) {
+  extern __shared__ unsigned long long rr_smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int d = C * P * P;
+  const int Wq = W - P + 1;
+  unsigned long long* list = rr_smem + (size_t)wid * pow2;
+  float* pv = reinterpret_cast<float*>(rr_smem + (size_t)RR_WARPS * pow2) + wid * 64 * 4;  // up to d = 256
+  const long long nkeys = (long long)n_img * N;
+  for (long long gk = blockIdx.x * (long long)RR_WARPS + wid; gk < nkeys; gk += (long long)gridDim.x * RR_WARPS) {
+    const int f = (int)(gk / N), k = (int)(gk - (long long)f * N);
+    if (k >= min(n_found[f], N)) continue;
+    const int kq = keys[gk];
+    if ((unsigned)kq >= (unsigned)(Wq * (H - P + 1))) continue;  // flagged by k_key_vectors
+    const int kr = kq / Wq, kc = kq - (kq / Wq) * Wq;
+    for (int e = lane; e < d; e += 32) {
+      const int ch = e / (P * P), dr = (e / P) % P, dc = e % P;
+      pv[e] = __ldg(x + (((long long)f * C + ch) * H + kr + dr) * W + kc + dc);
+    }
+    // gather candidate ids
+    int total = 0;
+    const long long s0 = ((long long)f * Npad + k) * streams_per_key;
+    for (int sidx = 0; sidx < streams_per_key; ++sidx) {
+      const int n = min(buf_cnt[s0 + sidx], kp);
+      const uint2* b = bufs + (s0 + sidx) * cap_slots;
+      for (int i = lane; i < n; i += 32) list[total + i] = b[i].y;
+      total += n;
+    }
+    for (int i = total + lane; i < pow2; i += 32) list[i] = ~0ull;
+    __syncwarp();
+    // exact distances
+    for (int i = lane; i < total; i += 32) {
+      const int q = (int)list[i];
+      const int r = q / Wq, c = q - (q / Wq) * Wq;
+      float acc = 0.f;
+      for (int ch = 0; ch < C; ++ch)
+        for (int dr = 0; dr < P; ++dr) {
+          const float* rowp = x + (((long long)f * C + ch) * H + r + dr) * W + c;
+          const float* pp = pv + (ch * P + dr) * P;
+          for (int dc = 0; dc < P; ++dc) {
+            const float df = pp[dc] - __ldg(rowp + dc);
+            acc = fmaf(df, df, acc);
+          }
+        }
+      list[i] = ((unsigned long long)float_order_key(acc) << 32) | (unsigned)q;
+    }
+    __syncwarp();
+    for (int kk = 2; kk <= pow2; kk <<= 1) {
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < pow2; i += 32) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const bool up = (i & kk) == 0;
+            const unsigned long long a = list[i], b = list[ixj];
+            if ((a > b) == up) {
+              list[i] = b;
+              list[ixj] = a;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    for (int i = lane; i < K; i += 32) {
+      const unsigned long long e = list[i];
+      idx[gk * K + i] = (int32_t)(e & 0xffffffffu);
+      if (dist) dist[gk * K + i] = float_from_order_key((uint32_t)(e >> 32));
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o) {
+  MatchPlan pl{};
+  pl.mode = o ? o->mode : GLR_MATCH_FP32;
+  pl.K = K;
+  pl.Kp = (o && o->k_over > 0) ? o->k_over : (pl.mode == GLR_MATCH_BF16 ? 2 * K : K + 16);
+  pl.Kp = std::max(pl.Kp, K);
+  pl.cap = std::max(4 * pl.Kp, 256);
+  pl.cap = (int)ceil_div(pl.cap, 32) * 32;
+  pl.subs = 2;
+  pl.key_tile = FT;
+  pl.Npad = (int)(ceil_div(N, FT) * FT);
+  const int Hq = im.H - im.P + 1, Wq = im.W - im.P + 1;
+  const int ktiles = pl.Npad / FT;
+  if (pl.mode == GLR_MATCH_BF16) {
+    pl.pos_tile = 256;
+    pl.pos_tiles = (int)ceil_div((long long)Hq * Wq, pl.pos_tile);
+  } else {
+    pl.pos_tile = FT;
+    pl.pos_tiles = Hq * (int)ceil_div(Wq, FT);
+  }
+  int splits = (o && o->splits > 0) ? o->splits : (int)ceil_div(4 * 152, (long long)ktiles * im.n_img);
+  // the exact re-rank holds every stream's candidates of one key in shared memory
+  const int max_splits = std::max(1, kRerankMaxList / (pl.subs * pl.Kp));
+  splits = std::max(1, std::min({splits, pl.pos_tiles, max_splits}));
+  pl.tiles_per_split = (int)ceil_div(pl.pos_tiles, splits);
+  pl.splits = (int)ceil_div(pl.pos_tiles, pl.tiles_per_split);
+  pl.streams_per_key = pl.splits * pl.subs;
+  const int d = im.C * im.P * im.P;
+  const long long npos = (long long)Hq * Wq;
+  WsLayout L;
+  pl.mean_off = L.take((size_t)im.n_img * 4);
+  pl.qn_off = L.take((size_t)im.n_img * npos * 4);
+  pl.keyv_off = L.take((size_t)im.n_img * pl.Npad * d * 4);
+  const long long nstreams = (long long)im.n_img * pl.Npad * pl.streams_per_key;
+  pl.buf_off = L.take((size_t)nstreams * (pl.cap + 32) * 8);
+  pl.bufcnt_off = L.take((size_t)nstreams * 4);
+  if (pl.mode == GLR_MATCH_BF16) {
+    // BF16 operands: positions [img][npos_pad][dk] and keys [img][Npad][dk], dk = d + 16 (norm columns)
+    const int dk = d + 16;
+    pl.dk = dk;
+    pl.npos_pad = (long long)pl.pos_tiles * pl.pos_tile;
+    pl.qpack_off = L.take((size_t)im.n_img * pl.npos_pad * dk * 2);
+    pl.kpack_off = L.take((size_t)im.n_img * pl.Npad * dk * 2);
+  }
+  pl.total = L.off;
+  return pl;
+}
+
+glr_status launch_match(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found, int N,
+                        const MatchPlan& pl, int32_t* idx, float* dist, char* ws, cudaStream_t s) {
+  const int Hq = im.H - im.P + 1, Wq = im.W - im.P + 1;
+  const long long npos = (long long)Hq * Wq;
+  const int d = im.C * im.P * im.P;
+  float* mean = reinterpret_cast<float*>(ws + pl.mean_off);
+  float* qn = reinterpret_cast<float*>(ws + pl.qn_off);
+  float* keyv = reinterpret_cast<float*>(ws + pl.keyv_off);
+  uint2* bufs = reinterpret_cast<uint2*>(ws + pl.buf_off);
+  int* bufcnt = reinterpret_cast<int*>(ws + pl.bufcnt_off);
+  const long long HW = (long long)im.H * im.W;
+  GLR_LAUNCH("k_image_mean", s, k_image_mean<<<im.n_img, 256, 0, s>>>(x, (long long)im.C * HW, mean));
+  {
+    const long long total = (long long)im.n_img * npos;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+    GLR_LAUNCH("k_patch_norms", s, k_patch_norms<<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, qn));
+  }
+  {
+    const long long total = (long long)im.n_img * pl.Npad * d;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+    GLR_LAUNCH("k_key_vectors", s, k_key_vectors<<<blocks, 256, 0, s>>>(x, mean, keys, n_found, im.n_img, im.C, im.H, im.W, im.P, N, pl.Npad,
+                                        keyv, reinterpret_cast<StatusBlock*>(ws)));
+  }
+  StreamCfg cfg{pl.cap, pl.Kp};
+  if (pl.mode == GLR_MATCH_BF16) {
+    const glr_status st = launch_match_tc(x, im, keys, n_found, N, pl, ws, s);
+    if (st != GLR_OK) return st;
+  } else {
+    const size_t smem = (size_t)(d * FT + im.C * im.P * (FT + 8) + FT * SC_LD + FT) * 4 + 8 * 256 * 4;
+    if (smem > 227 * 1024) return GLR_ENOTSUP;
+    dim3 grid((unsigned)(pl.Npad / FT), (unsigned)im.n_img, (unsigned)pl.splits);
+#define GLR_FP32_CASE(PP)                                                                                    \
+  case PP: {                                                                                                 \
+    if (cudaFuncSetAttribute(k_match_fp32<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=     \
+        cudaSuccess)                                                                                         \
+      return GLR_ECUDA;                                                                                      \
+    GLR_LAUNCH("k_match_fp32", s,                                                                           \
+               k_match_fp32<PP><<<grid, 256, smem, s>>>(x, mean, qn, keyv, n_found, im.C, im.H, im.W, pl.Npad,  \
+                                                        pl.splits, pl.tiles_per_split, cfg, bufs, bufcnt));     \
+  } break;
+    switch (im.P) {
+      GLR_FP32_CASE(2)
+      GLR_FP32_CASE(3)
+      GLR_FP32_CASE(4)
+      GLR_FP32_CASE(5)
+      GLR_FP32_CASE(6)
+      GLR_FP32_CASE(7)
+      GLR_FP32_CASE(8)
+      default:
+        return GLR_ENOTSUP;
+    }
+#undef GLR_FP32_CASE
+  }
+  {
+    int pow2 = 32;
+    while (pow2 < pl.streams_per_key * pl.Kp) pow2 <<= 1;
+    const size_t smem = (size_t)RR_WARPS * pow2 * 8 + (size_t)RR_WARPS * 256 * 4;
+    if (smem > 227 * 1024 || d > 256) return GLR_ENOTSUP;
+    if (cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return GLR_ECUDA;
+    const long long nkeys = (long long)im.n_img * N;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, RR_WARPS), 152LL * 16));
+    GLR_LAUNCH("k_rerank", s, k_rerank<<<blocks, RR_WARPS * 32, smem, s>>>(x, keys, n_found, im.n_img, im.C, im.H, im.W, im.P, N, pl.Npad,
+                                                 pl.K, pl.streams_per_key, pl.cap + 32, pl.Kp, pow2, bufs, bufcnt,
+                                                 idx, dist));
+  }
+  return GLR_OK;
+}
+
+}  // namespace glr

@@ -1,0 +1,284 @@
+"""Python binding of the GLR C ABI (include/glr.h).
+
+Argument marshalling only: tensors become device pointers, the current torch
+CUDA stream becomes the cudaStream_t, and every step runs in libglr.so.
+There is no CPU fallback; a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+
+
+class GlrError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        lib = L.load()
+        super().__init__(f"{fn}: {lib.glr_status_string(code).decode()}")
+        self.code = code
+
+
+def _check(fn: str, code: int) -> None:
+    if code != L.GLR_OK:
+        raise GlrError(fn, code)
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensors must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream: torch.cuda.Stream | None = None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def images(n_img: int, C: int, H: int, W: int, P: int) -> L.GlrImages:
+    return L.GlrImages(n_img, C, H, W, P)
+
+
+def images_of(x: torch.Tensor, P: int) -> L.GlrImages:
+    n, C, H, W = x.shape
+    return images(n, C, H, W, P)
+
+
+def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0) -> L.GlrMatchOpts:
+    m = {"fp32": L.GLR_MATCH_FP32, "bf16": L.GLR_MATCH_BF16}.get(mode, mode)
+    o = L.GlrMatchOpts()
+    o.mode, o.k_over, o.splits = int(m), int(k_over), int(splits)
+    return o
+
+
+def workspace_size(op: int, im: L.GlrImages, N: int = 1, K: int = 1, opts: L.GlrMatchOpts | None = None) -> int:
+    lib = L.load()
+    n = lib.glr_workspace_size(op, ctypes.byref(im), N, K, ctypes.byref(opts) if opts is not None else None)
+    if n == 0:
+        raise GlrError("glr_workspace_size", L.GLR_EINVAL)
+    return int(n)
+
+
+def workspace(op: int, im: L.GlrImages, N: int = 1, K: int = 1, opts=None, device="cuda") -> torch.Tensor:
+    n = workspace_size(op, im, N, K, opts)
+    return torch.empty(n + 256, dtype=torch.uint8, device=device)
+
+
+def _ws(ws: torch.Tensor) -> tuple[int, int]:
+    p = ws.data_ptr()
+    off = (-p) % 256
+    return p + off, ws.numel() - off
+
+
+def select_keys(x, P, N, edge_th=0.1, *, keys=None, n_found=None, n_corner=None, ws=None, stream=None):
+    """Corner-based key selection (Section 2, Eq. 2-3).  x: [n_img][C][H][W] float32."""
+    lib = L.load()
+    im = images_of(x, P)
+    dev = x.device
+    if keys is None:
+        keys = torch.empty((x.shape[0], N), dtype=torch.int32, device=dev)
+    if n_found is None:
+        n_found = torch.empty(x.shape[0], dtype=torch.int32, device=dev)
+    if n_corner is None:
+        n_corner = torch.empty(x.shape[0], dtype=torch.int32, device=dev)
+    if ws is None:
+        ws = workspace(L.GLR_OP_SELECT, im, N, 1, None, dev)
+    wp, wn = _ws(ws)
+    _check("glr_select_keys", lib.glr_select_keys(_ptr(x), ctypes.byref(im), float(edge_th), int(N), _ptr(keys),
+                                                  _ptr(n_found), _ptr(n_corner), wp, wn, _stream(stream)))
+    return keys, n_found, n_corner
+
+
+def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, idx=None, dist=None, ws=None,
+               stream=None):
+    """Global matching with a fused running top-K (Eq. 1 over the whole image, Eq. 4 as a contraction)."""
+    lib = L.load()
+    im = images_of(x, P)
+    N = keys.shape[1]
+    o = match_opts(mode, k_over, splits)
+    dev = x.device
+    if idx is None:
+        idx = torch.empty((x.shape[0], N, K), dtype=torch.int32, device=dev)
+    if dist is None:
+        dist = torch.empty((x.shape[0], N, K), dtype=torch.float32, device=dev)
+    if ws is None:
+        ws = workspace(L.GLR_OP_MATCH, im, N, K, o, dev)
+    wp, wn = _ws(ws)
+    _check("glr_match_topk", lib.glr_match_topk(_ptr(x), ctypes.byref(im), _ptr(keys), _ptr(n_found), int(N), int(K),
+                                                ctypes.byref(o), _ptr(idx), _ptr(dist), wp, wn, _stream(stream)))
+    return idx, dist
+
+
+def lowrank_groups(x, P, idx, n_found, sigma_w, c_wnnm, *, groups=None, rank=None, ws=None, stream=None):
+    """R~_i x and the WNNM step of Eq. 5; returns (groups [n][N][K][d] = X^, rank [n][N])."""
+    lib = L.load()
+    im = images_of(x, P)
+    n, N, K = idx.shape
+    d = x.shape[1] * P * P
+    dev = x.device
+    if groups is None:
+        groups = torch.empty((n, N, K, d), dtype=torch.float32, device=dev)
+    if rank is None:
+        rank = torch.empty((n, N), dtype=torch.int32, device=dev)
+    if ws is None:
+        ws = workspace(L.GLR_OP_LOWRANK, im, N, K, None, dev)
+    wp, wn = _ws(ws)
+    _check("glr_lowrank_groups", lib.glr_lowrank_groups(_ptr(x), ctypes.byref(im), _ptr(idx), _ptr(n_found), int(N),
+                                                        int(K), float(sigma_w), float(c_wnnm), _ptr(groups),
+                                                        _ptr(rank), wp, wn, _stream(stream)))
+    return groups, rank
+
+
+def aggregate(groups, idx, n_found, x, P, *, out=None, ws=None, stream=None):
+    """Average the group estimates back into the image (weight 1; uncovered pixels keep x)."""
+    lib = L.load()
+    im = images_of(x, P)
+    n, N, K = idx.shape
+    if out is None:
+        out = torch.empty_like(x)
+    if ws is None:
+        ws = workspace(L.GLR_OP_AGGREGATE, im, N, K, None, x.device)
+    wp, wn = _ws(ws)
+    _check("glr_aggregate", lib.glr_aggregate(_ptr(groups), _ptr(idx), _ptr(n_found), ctypes.byref(im), int(N),
+                                              int(K), _ptr(x), _ptr(out), wp, wn, _stream(stream)))
+    return out
+
+
+def gap_step(y, masks, v=None, *, accelerate=False, y_acc=None, out=None, stream=None):
+    """GAP projection (Eq. 6 / Eq. 8).  y: [G][H][W]; masks: [T][H][W] (shared) or [G][T][H][W];
+    v, out: [G][T][H][W].  v=None gives x0 = Phi^T(y/R)."""
+    lib = L.load()
+    G, H, W = y.shape
+    if masks.dim() == 3:
+        T = masks.shape[0]
+        mstride = 0
+    else:
+        T = masks.shape[1]
+        mstride = T * H * W
+    if out is None:
+        out = torch.empty((G, T, H, W), dtype=torch.float32, device=y.device)
+    _check("glr_gap_step", lib.glr_gap_step(_ptr(y), _ptr(masks), int(mstride), _ptr(v), G, T, H, W,
+                                            1 if accelerate else 0, _ptr(y_acc), _ptr(out), _stream(stream)))
+    return out
+
+
+def poll_status(ws, reset=False, stream=None):
+    """(bits, [cand_overflow, svd_noconv, sweeps, groups]) of the last call that used ws."""
+    lib = L.load()
+    wp, _ = _ws(ws)
+    bits = ctypes.c_uint32(0)
+    cnt = (ctypes.c_uint32 * 4)()
+    code = lib.glr_poll_status(wp, ctypes.byref(bits), cnt, 1 if reset else 0, _stream(stream))
+    if code not in (L.GLR_OK, L.GLR_EDEVICE):
+        raise GlrError("glr_poll_status", code)
+    return int(bits.value), [int(c) for c in cnt]
+
+
+def launch_count() -> int:
+    return int(L.load().glr_launch_count())
+
+
+def profile_enable(on: bool = True) -> None:
+    _check("glr_profile_enable", L.load().glr_profile_enable(1 if on else 0))
+
+
+def profile_collect(cap: int = 64) -> dict[str, tuple[float, int]]:
+    """{kernel name: (total ms, launches)} recorded since the previous collect."""
+    lib = L.load()
+    names = ctypes.create_string_buffer(48 * cap)
+    ms = (ctypes.c_float * cap)()
+    cnt = (ctypes.c_int32 * cap)()
+    n = lib.glr_profile_collect(names, ms, cnt, cap)
+    if n < 0:
+        raise GlrError("glr_profile_collect", L.GLR_ECUDA)
+    out = {}
+    for i in range(n):
+        nm = names.raw[48 * i : 48 * i + 48].split(b"\0", 1)[0].decode()
+        out[nm] = (float(ms[i]), int(cnt[i]))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# A reusable GLR iteration: every buffer allocated once, so repeated steps
+# launch kernels only (graph-capturable).
+# ---------------------------------------------------------------------------
+@dataclass
+class GlrShape:
+    n_img: int
+    C: int
+    H: int
+    W: int
+    P: int
+    N: int
+    K: int
+
+
+class GlrDenoiser:
+    """Select -> match -> low-rank -> aggregate on fixed-size images, with preallocated buffers."""
+
+    def __init__(self, shape: GlrShape, mode: str = "bf16", edge_th: float = 0.1, k_over: int = 0, splits: int = 0,
+                 device="cuda"):
+        s = shape
+        self.shape, self.mode, self.edge_th = s, mode, edge_th
+        self.opts = match_opts(mode, k_over, splits)
+        self.k_over, self.splits = k_over, splits
+        im = images(s.n_img, s.C, s.H, s.W, s.P)
+        dev = torch.device(device)
+        d = s.C * s.P * s.P
+        self.keys = torch.empty((s.n_img, s.N), dtype=torch.int32, device=dev)
+        self.n_found = torch.empty(s.n_img, dtype=torch.int32, device=dev)
+        self.n_corner = torch.empty(s.n_img, dtype=torch.int32, device=dev)
+        self.idx = torch.empty((s.n_img, s.N, s.K), dtype=torch.int32, device=dev)
+        self.dist = torch.empty((s.n_img, s.N, s.K), dtype=torch.float32, device=dev)
+        self.groups = torch.empty((s.n_img, s.N, s.K, d), dtype=torch.float32, device=dev)
+        self.rank = torch.empty((s.n_img, s.N), dtype=torch.int32, device=dev)
+        self.ws_select = workspace(L.GLR_OP_SELECT, im, s.N, s.K, None, dev)
+        self.ws_match = workspace(L.GLR_OP_MATCH, im, s.N, s.K, self.opts, dev)
+        self.ws_lowrank = workspace(L.GLR_OP_LOWRANK, im, s.N, s.K, None, dev)
+        self.ws_agg = workspace(L.GLR_OP_AGGREGATE, im, s.N, s.K, None, dev)
+
+    def __call__(self, x: torch.Tensor, sigma_w: float, c_wnnm: float, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+        s = self.shape
+        select_keys(x, s.P, s.N, self.edge_th, keys=self.keys, n_found=self.n_found, n_corner=self.n_corner,
+                    ws=self.ws_select, stream=stream)
+        match_topk(x, s.P, self.keys, self.n_found, s.K, self.mode, k_over=self.k_over, splits=self.splits,
+                   idx=self.idx, dist=self.dist, ws=self.ws_match, stream=stream)
+        lowrank_groups(x, s.P, self.idx, self.n_found, sigma_w, c_wnnm, groups=self.groups, rank=self.rank,
+                       ws=self.ws_lowrank, stream=stream)
+        return aggregate(self.groups, self.idx, self.n_found, x, s.P, out=out, ws=self.ws_agg, stream=stream)
+
+
+class SciReconstructor:
+    """GAP + GLR for one video snapshot y = sum_t M_t x_t (Eq. 6); frames are the images."""
+
+    def __init__(self, T, H, W, P, N, K, mode="bf16", edge_th=0.1, accelerate=False, k_over=0, splits=0,
+                 device="cuda"):
+        self.T, self.H, self.W = T, H, W
+        self.den = GlrDenoiser(GlrShape(T, 1, H, W, P, N, K), mode, edge_th, k_over, splits, device)
+        self.accelerate = accelerate
+        self.x = torch.empty((1, T, H, W), dtype=torch.float32, device=device)
+        self.v = torch.empty_like(self.x)
+        self.y_acc = torch.empty((1, H, W), dtype=torch.float32, device=device)
+
+    def start(self, y: torch.Tensor, masks: torch.Tensor) -> torch.Tensor:
+        """x0 = Phi^T(y/R)."""
+        self.y, self.masks = y.view(1, self.H, self.W), masks
+        if self.accelerate:
+            self.y_acc.copy_(self.y)
+        gap_step(self.y, masks, None, out=self.x)
+        return self.x
+
+    def step(self, sigma_w: float, c_wnnm: float, stream=None) -> torch.Tensor:
+        """One GAP iteration: v = D(x); x = project(v)."""
+        xi = self.x.view(self.T, 1, self.H, self.W)
+        self.den(xi, sigma_w, c_wnnm, out=self.v.view(self.T, 1, self.H, self.W), stream=stream)
+        gap_step(self.y, self.masks, self.v, accelerate=self.accelerate, y_acc=self.y_acc if self.accelerate else None,
+                 out=self.x, stream=stream)
+        return self.x

@@ -1,0 +1,284 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, step by step.
+
+Every test feeds both sides the same seeded input (teacher forcing) and
+compares element by element:
+  * key selection: bit-exact (integer arithmetic after the edge maps; inputs
+    are 8-bit quantised so the FP32 Sobel sums are exact);
+  * matching: indices bit-exact wherever the oracle's distances are separated
+    by more than TAU_SEP, otherwise the GPU set must be a valid top-K within
+    TAU_SEP; distances within 2e-5 relative;
+  * low-rank step: X^ within 2e-4 * ||Y||_F / sqrt(dK) RMS and 1e-3 max
+    (FP32 one-sided Jacobi vs FP64 LAPACK);
+  * aggregation and GAP: within 1e-5 relative / 1e-6 absolute.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import glr_oracle as O  # noqa: E402
+from paper_2301_03047_gb300 import glr, synth  # noqa: E402
+
+TAU_SEP = 1e-4
+
+
+def cuda(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def scene(tag, F, H, W, quant=True, C=1):
+    rng = synth.rng_for(tag)
+    fr = synth.textured_frames(rng, F * C, H, W).reshape(F, C, H, W)
+    return synth.quantize8(fr) if quant else fr
+
+
+# ---------------------------------------------------------------------------
+# GAP projection
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("accelerate", [False, True])
+@pytest.mark.parametrize("HW", [(37, 53), (64, 64)])
+def test_gap_step_matches_oracle(accelerate, HW):
+    H, W = HW
+    rng = synth.rng_for("gap-gpu", H)
+    T = 5
+    A = (rng.random((T, H, W)) < 0.5).astype(np.float32)
+    A[:, 0, :3] = 0.0
+    y = rng.random((1, H, W)).astype(np.float32)
+    v = rng.random((1, T, H, W)).astype(np.float32)
+    yacc = rng.random((1, H, W)).astype(np.float32)
+    ya = cuda(yacc)
+    x = glr.gap_step(cuda(y), cuda(A), cuda(v), accelerate=accelerate, y_acc=ya if accelerate else None)
+    torch.cuda.synchronize()
+    xo, yo = O.gap_project(y[0], A, v[0], yacc[0] if accelerate else None)
+    np.testing.assert_allclose(x.cpu().numpy()[0], xo, rtol=1e-5, atol=1e-6)
+    if accelerate:
+        np.testing.assert_allclose(ya.cpu().numpy()[0], yo, rtol=1e-5, atol=1e-6)
+    x0 = glr.gap_step(cuda(y), cuda(A), None)
+    np.testing.assert_allclose(x0.cpu().numpy()[0], O.gap_init(y[0], A), rtol=1e-6, atol=1e-7)
+
+
+def test_gap_step_per_group_masks_and_alias():
+    rng = synth.rng_for("gap-groups")
+    G, T, H, W = 3, 4, 16, 20
+    A = rng.random((G, T, H, W)).astype(np.float32)
+    y = rng.random((G, H, W)).astype(np.float32)
+    v = rng.random((G, T, H, W)).astype(np.float32)
+    vt = cuda(v)
+    glr.gap_step(cuda(y), cuda(A), vt, out=vt)  # in place
+    torch.cuda.synchronize()
+    for g in range(G):
+        xo, _ = O.gap_project(y[g], A[g], v[g])
+        np.testing.assert_allclose(vt.cpu().numpy()[g], xo, rtol=1e-5, atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Key selection (bit-exact)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize(
+    "case",
+    [
+        ("scene", 3, 1, 96, 130, 8, 200),  # several Harris tiles, ragged edge
+        ("scene-many", 2, 1, 64, 64, 8, 1200),  # N above the number of corners -> grid fill
+        ("scene-P5", 2, 1, 70, 45, 5, 60),
+        ("msfa", 2, 3, 48, 40, 6, 80),  # multi-channel edge maps OR-ed over channels
+    ],
+)
+def test_select_keys_bit_exact(case):
+    tag, F, C, H, W, P, N = case
+    x = scene(tag, F, H, W, C=C)
+    keys, nf, nc = glr.select_keys(cuda(x), P, N, 0.1)
+    torch.cuda.synchronize()
+    keys, nf, nc = keys.cpu().numpy(), nf.cpu().numpy(), nc.cpu().numpy()
+    for f in range(F):
+        ok, onc = O.select_keys(x[f], P, N, 0.1)
+        assert nf[f] == N
+        assert nc[f] == onc
+        np.testing.assert_array_equal(keys[f], ok)
+
+
+def test_select_keys_flat_and_rectangles():
+    H, W, P = 40, 44, 8
+    flat = np.full((1, 1, H, W), 0.25, np.float32)
+    rect = np.zeros((1, 1, H, W), np.float32)
+    rect[0, 0, 1:12, 1:12] = 1.0  # corners that clamp onto the same patches
+    rect[0, 0, 20:39, 25:43] = 0.5
+    for x, N in ((flat, 17), (rect, 30), (rect, 3)):
+        keys, nf, nc = glr.select_keys(cuda(x), P, N, 0.1)
+        ok, onc = O.select_keys(x[0], P, N, 0.1)
+        assert int(nc.cpu()[0]) == onc
+        np.testing.assert_array_equal(keys.cpu().numpy()[0], ok)
+
+
+def test_select_keys_single_position():
+    """Degenerate size: the image is exactly one patch (Hq = Wq = 1)."""
+    x = scene("one", 1, 8, 8)
+    keys, nf, nc = glr.select_keys(cuda(x), 8, 1, 0.1)
+    assert keys.cpu().numpy().tolist() == [[0]]
+
+
+# ---------------------------------------------------------------------------
+# Matching
+# ---------------------------------------------------------------------------
+def check_topk(x, P, keys, K, idx_gpu, dist_gpu, n_found=None, tau=TAU_SEP):
+    F = x.shape[0]
+    nbad_sep = 0
+    for f in range(F):
+        Q = O.patch_matrix(x[f], P)
+        nf = keys.shape[1] if n_found is None else n_found[f]
+        for i in range(nf):
+            d_all = O.all_distances(x[f], P, keys[f, i], Q)
+            order = np.lexsort((np.arange(len(d_all)), d_all))
+            ds = d_all[order]
+            g_idx = idx_gpu[f, i]
+            # distances reported are the exact ones of the reported ids
+            np.testing.assert_allclose(dist_gpu[f, i], d_all[g_idx], rtol=2e-5, atol=2e-6)
+            # ranks: GPU distances are a valid sorted top-K within tau
+            assert np.all(np.diff(dist_gpu[f, i]) >= -tau)
+            assert np.all(d_all[g_idx] <= ds[K - 1] + tau)
+            assert len(set(g_idx.tolist())) == K
+            # bit-exact where separated
+            for j in range(K):
+                lo = ds[j] - ds[j - 1] if j > 0 else np.inf
+                hi = ds[j + 1] - ds[j] if j + 1 < len(ds) else np.inf
+                if lo > tau and hi > tau:
+                    if g_idx[j] != order[j]:
+                        nbad_sep += 1
+    assert nbad_sep == 0
+
+
+@pytest.mark.parametrize(
+    "case",
+    [
+        ("m1", 2, 1, 60, 150, 8, 130, 40),  # 2 key tiles (ragged), 2 column tiles per row (ragged)
+        ("m2", 1, 1, 37, 41, 4, 50, 9),
+        ("m3", 2, 2, 30, 33, 5, 20, 12),  # multi-channel
+        ("m4", 1, 1, 24, 26, 3, 300, 128),  # K at its maximum
+    ],
+)
+@pytest.mark.parametrize("splits", [0, 3])
+def test_match_fp32_parity(case, splits):
+    tag, F, C, H, W, P, N, K = case
+    x = scene(tag, F, H, W, quant=False, C=C)
+    rng = synth.rng_for(tag + "keys")
+    npos = (H - P + 1) * (W - P + 1)
+    keys = np.stack([rng.choice(npos, size=N, replace=False) for _ in range(F)]).astype(np.int32)
+    nf = np.full(F, N, np.int32)
+    idx, dist = glr.match_topk(cuda(x), P, cuda(keys, torch.int32), cuda(nf, torch.int32), K, "fp32", splits=splits)
+    torch.cuda.synchronize()
+    check_topk(x, P, keys, K, idx.cpu().numpy(), dist.cpu().numpy())
+
+
+def test_match_planted_copies_and_constant():
+    H, W, P, K = 40, 50, 8, 6
+    rng = synth.rng_for("planted-gpu")
+    x = rng.random((2, 1, H, W)).astype(np.float32)
+    Wq = W - P + 1
+    src = (5, 7)
+    spots = [(20, 3), (0, 30), (31, 40)]
+    for r, c in spots:
+        x[0, 0, r : r + P, c : c + P] = x[0, 0, src[0] : src[0] + P, src[1] : src[1] + P]
+    x[1] = 0.5  # constant image: every distance is 0, ties by id
+    keys = np.array([[src[0] * Wq + src[1]], [77]], np.int32)
+    idx, dist = glr.match_topk(cuda(x), P, cuda(keys, torch.int32), cuda(np.array([1, 1], np.int32), torch.int32), K)
+    idx = idx.cpu().numpy()
+    want = sorted([src[0] * Wq + src[1]] + [r * Wq + c for r, c in spots])
+    assert idx[0, 0, :4].tolist() == want
+    assert np.all(dist.cpu().numpy()[0, 0, :4] == 0)
+    assert idx[1, 0].tolist() == list(range(K))
+
+
+def test_match_n_found_masks_rows():
+    x = scene("nf", 2, 30, 30, quant=False)
+    P, N, K = 6, 20, 5
+    keys = np.tile(np.arange(N, dtype=np.int32) * 7, (2, 1))
+    nf = np.array([20, 9], np.int32)
+    idx = torch.full((2, N, K), -7, dtype=torch.int32, device="cuda")
+    glr.match_topk(cuda(x), P, cuda(keys, torch.int32), cuda(nf, torch.int32), K, idx=idx)
+    idx = idx.cpu().numpy()
+    assert np.all(idx[1, 9:] == -7) and np.all(idx[1, :9] >= 0) and np.all(idx[0] >= 0)
+
+
+# ---------------------------------------------------------------------------
+# Low-rank step (teacher-forced idx)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", [("l1", 2, 1, 40, 44, 8, 30, 40, 0.3), ("l2", 1, 1, 30, 30, 8, 20, 64, 0.1),
+                                  ("l3", 1, 1, 25, 27, 4, 15, 7, 0.05), ("l4", 1, 1, 30, 30, 8, 10, 64, 0.0)])
+def test_lowrank_parity(case):
+    tag, F, C, H, W, P, N, K, sw = case
+    x = scene(tag, F, H, W, quant=False, C=C)
+    rng = synth.rng_for(tag + "idx")
+    npos = (H - P + 1) * (W - P + 1)
+    idx = rng.integers(0, npos, size=(F, N, K)).astype(np.int32)
+    nf = np.full(F, N, np.int32)
+    cw = 2 * math.sqrt(K)
+    groups, rank = glr.lowrank_groups(cuda(x), P, cuda(idx, torch.int32), cuda(nf, torch.int32), sw, cw)
+    torch.cuda.synchronize()
+    g = groups.cpu().numpy()
+    rk = rank.cpu().numpy()
+    d = C * P * P
+    for f in range(F):
+        Y = O.gather_groups(x[f], P, idx[f])
+        Xo, ro = O.lowrank_groups(Y, sw, cw, eps=1e-8)
+        for i in range(N):
+            scale = np.linalg.norm(Y[i]) / math.sqrt(d * K)
+            err = g[f, i] - Xo[i]
+            assert np.sqrt(np.mean(err**2)) <= 2e-4 * max(scale, 1e-3), (f, i)
+            assert np.abs(err).max() <= 1e-3 * max(np.abs(Y[i]).max(), 1e-3)
+            assert abs(int(rk[f, i]) - int(ro[i])) <= 1
+
+
+def test_lowrank_noiseless_low_rank_recovery():
+    """Groups of exactly rank 2 are returned unchanged (up to FP32) for a tiny sigma_w."""
+    H, W, P, K = 20, 20, 8, 32
+    rr = np.arange(H)[:, None] / H
+    cc = np.arange(W)[None, :] / W
+    x = (0.3 + 0.2 * rr + 0.1 * cc + 0.05 * rr * cc).astype(np.float32)[None, None]
+    rng = synth.rng_for("lr-rec")
+    idx = rng.integers(0, (H - P + 1) ** 2, size=(1, 5, K)).astype(np.int32)
+    groups, rank = glr.lowrank_groups(cuda(x), P, cuda(idx, torch.int32), cuda(np.array([5], np.int32), torch.int32), 1e-5, 2 * math.sqrt(K))
+    Y = O.gather_groups(x[0], P, idx[0])
+    g = groups.cpu().numpy()[0]
+    assert np.linalg.norm(g - Y) / np.linalg.norm(Y) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Aggregation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", [("a1", 2, 1, 33, 47, 8, 25, 10), ("a2", 1, 3, 20, 21, 4, 12, 6)])
+def test_aggregate_parity(case):
+    tag, F, C, H, W, P, N, K = case
+    rng = synth.rng_for(tag)
+    x = rng.random((F, C, H, W)).astype(np.float32)
+    npos = (H - P + 1) * (W - P + 1)
+    idx = rng.integers(0, npos, size=(F, N, K)).astype(np.int32)
+    g = rng.random((F, N, K, C * P * P)).astype(np.float32)
+    nf = np.full(F, N, np.int32)
+    v = glr.aggregate(cuda(g), cuda(idx, torch.int32), cuda(nf, torch.int32), cuda(x), P)
+    torch.cuda.synchronize()
+    for f in range(F):
+        vo = O.aggregate(g[f], idx[f], x[f], P)
+        np.testing.assert_allclose(v.cpu().numpy()[f], vo, rtol=1e-5, atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Device status, workspace errors
+# ---------------------------------------------------------------------------
+def test_nonfinite_input_is_flagged():
+    x = scene("nan", 1, 24, 24, quant=False)
+    x[0, 0, 3, 3] = np.nan
+    idx = np.zeros((1, 2, 8), np.int32)
+    ws = glr.workspace(glr.L.GLR_OP_LOWRANK, glr.images(1, 1, 24, 24, 8))
+    glr.lowrank_groups(cuda(x), 8, cuda(idx, torch.int32), cuda(np.array([2], np.int32), torch.int32), 0.1, 4.0, ws=ws)
+    bits, cnt = glr.poll_status(ws)
+    assert bits & glr.L.GLR_DEV_NONFINITE
+
+
+def test_workspace_too_small():
+    x = cuda(scene("ws", 1, 32, 32))
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(glr.GlrError) as e:
+        glr.select_keys(x, 8, 10, ws=ws)
+    assert e.value.code == glr.L.GLR_ENOMEM
