@@ -137,6 +137,18 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
                           size_t ws_bytes, void* stream);
 
 /*
+ * Testing aid for the BF16 tensor-core scorer: runs glr_match_topk in
+ * GLR_MATCH_BF16 mode (no idx / dist output) and also writes the raw scores
+ * ||p~ - q~||^2 of every key against the first 256 positions of its image,
+ * float32 [n_img][ceil(N/128)*128][256], to `scores` (device).  p~, q~ are the
+ * mean-shifted patches rounded to BF16.  The paper has no counterpart; this
+ * exists to check the tensor-core operand layout against a host computation.
+ */
+glr_status glr_debug_match_scores(const float* x, const glr_images* im, const int32_t* keys,
+                                  const int32_t* n_found, int32_t N, int32_t K, float* scores, void* ws,
+                                  size_t ws_bytes, void* stream);
+
+/*
  * Grouping and low-rank step -- Eq. 5 (R~_i x) solved by WNNM (Section 2).
  * For every key the K matched patches form Y (d x K, d = C*P*P); with
  * Y = U S V^T, sigma_hat_i = sqrt(max(s_i^2 - K sigma_w^2, 0)),

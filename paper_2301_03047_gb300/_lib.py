@@ -33,6 +33,7 @@ PROTOTYPES = {
     "glr_workspace_size": (c_size_t, [c_int32, ctypes.POINTER(GlrImages), c_int32, c_int32, ctypes.POINTER(GlrMatchOpts)]),
     "glr_select_keys": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_float, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_match_topk": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, ctypes.POINTER(GlrMatchOpts), c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "glr_debug_match_scores": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_lowrank_groups": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_aggregate": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(GlrImages), c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_gap_step": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),

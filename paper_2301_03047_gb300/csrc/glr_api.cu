@@ -166,7 +166,7 @@ glr_status glr_select_keys(const float* x, const glr_images* im, float edge_th, 
 glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* keys, const int32_t* n_found,
                           int32_t N, int32_t K, const glr_match_opts* opts, int32_t* idx, float* dist, void* ws,
                           size_t ws_bytes, void* stream) {
-  if (!images_ok(im) || !x || !keys || !n_found || !idx) return GLR_EINVAL;
+  if (!images_ok(im) || !x || !keys || !n_found || (!idx && !g_tc_dump)) return GLR_EINVAL;
   const long long npos = npos_of(im);
   if (N < 1 || K < 1 || K > npos) return GLR_EINVAL;
   if (K > 128) return GLR_ENOTSUP;
@@ -178,6 +178,18 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
   glr_status st = begin_ws(ws, ws_bytes, pl.total, s);
   if (st != GLR_OK) return st;
   return launch_match(x, *im, keys, n_found, N, pl, idx, dist, (char*)ws, s);
+}
+
+glr_status glr_debug_match_scores(const float* x, const glr_images* im, const int32_t* keys,
+                                  const int32_t* n_found, int32_t N, int32_t K, float* scores, void* ws,
+                                  size_t ws_bytes, void* stream) {
+  if (!scores) return GLR_EINVAL;
+  glr_match_opts o{};
+  o.mode = GLR_MATCH_BF16;
+  g_tc_dump = scores;
+  glr_status st = glr_match_topk(x, im, keys, n_found, N, K, &o, nullptr, nullptr, ws, ws_bytes, stream);
+  g_tc_dump = nullptr;
+  return st;
 }
 
 glr_status glr_lowrank_groups(const float* x, const glr_images* im, const int32_t* idx, const int32_t* n_found,

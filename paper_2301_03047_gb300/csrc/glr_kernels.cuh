@@ -43,6 +43,9 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
 // tensor-core scorer (k_match_tc.cu); returns GLR_ENOTSUP when the shape is not covered
 glr_status launch_match_tc(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found,
                            int N, const MatchPlan& plan, char* ws, cudaStream_t s);
+// testing aid: when set, the tensor-core scorer also writes the raw scores of the
+// first position tile, [n_img][Npad][256] float32, to this device buffer
+extern float* g_tc_dump;
 
 // ---- low-rank step (k_lowrank.cu)
 glr_status launch_gather(const float* x, const glr_images& im, const int32_t* idx, const int32_t* n_found, int N,

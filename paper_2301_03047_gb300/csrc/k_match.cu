@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
     }
     for (int i = lane; i < K; i += 32) {
       const unsigned long long e = list[i];
-      idx[gk * K + i] = (int32_t)(e & 0xffffffffu);
+      if (idx) idx[gk * K + i] = (int32_t)(e & 0xffffffffu);
       if (dist) dist[gk * K + i] = float_from_order_key((uint32_t)(e >> 32));
     }
     __syncwarp();
@@ -349,7 +349,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   pl.bufcnt_off = L.take((size_t)nstreams * 4);
   if (pl.mode == GLR_MATCH_BF16) {
     // BF16 operands: positions [img][npos_pad][dk] and keys [img][Npad][dk], dk = d + 16 (norm columns)
-    const int dk = d + 16;
+    const int dk = 64 + 16;  // patch columns padded to 64, plus the norm columns
     pl.dk = dk;
     pl.npos_pad = (long long)pl.pos_tiles * pl.pos_tile;
     pl.qpack_off = L.take((size_t)im.n_img * pl.npos_pad * dk * 2);

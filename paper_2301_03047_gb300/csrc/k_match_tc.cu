@@ -1,11 +1,492 @@
-// BF16 tensor-core scorer for glr_match_topk (tcgen05.mma into TMEM, TMA-fed).
+// BF16 tensor-core scorer for glr_match_topk: the heat map of Eq. 4 evaluated
+// as a dense contraction on the 5th-generation tensor cores (tcgen05.mma,
+// accumulators in tensor memory), operands staged by TMA, fused with the
+// running per-key top-K' of topk_stream.cuh so no score reaches HBM.
+//
+// Operands (packed once per call by k_pack_keys / k_pack_positions):
+//   A (keys)      row = [-2 p~ (d bf16, zero-padded to 64) | 1 1 1 pn_hi pn_mid pn_lo 0..]
+//   B (positions) row = [   q~ (d bf16, zero-padded to 64) | qn_hi qn_mid qn_lo 1 1 1 0..]
+// where p~, q~ are the mean-shifted patches rounded to BF16 and pn, qn their
+// squared norms computed in FP32 from the rounded values, split into three
+// BF16 terms.  One 128 x 256 x 80 product therefore gives, per key/position,
+// ||p~||^2 + ||q~||^2 - 2<p~,q~> = ||p~ - q~||^2 up to FP32 accumulation:
+// the exact distance of the BF16-rounded patches.  Candidates are re-ranked
+// with the exact FP32 distance afterwards (k_rerank).
+//
+// CTA = 128 keys x one split of the positions, 320 threads:
+//   warp 0      TMA producer (one thread): key tile once, then position tiles
+//               into a 4-stage ring (SW128 for the 64 patch columns, SW32 for
+//               the 16 norm columns)
+//   warp 1      TMEM allocator (512 columns = two 128x256 FP32 accumulators)
+//               and MMA issuer (one thread): 4 x K16 + 1 x K16 per tile
+//   warps 2-9   epilogue: tcgen05.ld 32 lanes x 32 columns, push into the
+//               per-row top-K' stream; warps w and w+4 share a TMEM lane
+//               quadrant and take one column half each
+// Every mbarrier wait is bounded (1 s of %globaltimer): on expiry the CTA sets
+// GLR_DEV_TIMEOUT and an abort flag, every role leaves its loop, in-flight TMA
+// loads and MMAs are waited for (bounded) and TMEM is freed before exit.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include "glr_kernels.cuh"
+#include "topk_stream.cuh"
 
 namespace glr {
 
-glr_status launch_match_tc(const float*, const glr_images&, const int32_t*, const int32_t*, int, const MatchPlan&,
-                           char*, cudaStream_t) {
-  return GLR_ENOTSUP;
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_N = 256;
+constexpr int TC_STAGES = 4;
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = 64 + TC_EPI_WARPS * 32;
+constexpr int DK_MAIN = 64;  // patch columns (bf16), one 128-byte swizzle row
+constexpr int DK_AUX = 16;   // norm columns (bf16), one 32-byte swizzle row
+constexpr uint32_t A_MAIN_BYTES = TC_M * DK_MAIN * 2;  // 16384
+constexpr uint32_t A_AUX_BYTES = TC_M * DK_AUX * 2;    // 4096
+constexpr uint32_t B_MAIN_BYTES = TC_N * DK_MAIN * 2;  // 32768
+constexpr uint32_t B_AUX_BYTES = TC_N * DK_AUX * 2;    // 8192
+constexpr uint32_t OFF_A_MAIN = 0;
+constexpr uint32_t OFF_A_AUX = OFF_A_MAIN + A_MAIN_BYTES;
+constexpr uint32_t OFF_B_MAIN = OFF_A_AUX + A_AUX_BYTES;
+constexpr uint32_t OFF_B_AUX = OFF_B_MAIN + TC_STAGES * B_MAIN_BYTES;
+constexpr uint32_t OFF_BAR = OFF_B_AUX + TC_STAGES * B_AUX_BYTES;  // 8-byte barriers
+constexpr int NBAR = 2 * TC_STAGES + 4 + 2;                        // full, empty, tmem_full x2, tmem_empty x2, a_full, mma_done
+constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;                  // tmem base, abort flag
+constexpr uint32_t OFF_HIST = (OFF_MISC + 64 + 15) / 16 * 16;
+constexpr uint32_t TC_SMEM = OFF_HIST + TC_EPI_WARPS * 256 * 4 + 1024;  // + alignment slack
+constexpr unsigned long long kWaitNs = 1000000000ull;                   // 1 s
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait.  Returns false if the CTA aborted or this wait timed out (then
+// it raises the abort flag and the device status bit).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, StatusBlock* st,
+                                          bool honour_abort = true) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0) {
+      if (honour_abort && *abort) return false;
+      if (globaltimer() - t0 > kWaitNs) {
+        *abort = 1;
+        status_set(st, GLR_DEV_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor (K-major operand, swizzled): start address,
+// leading / stride byte offsets (>> 4), descriptor version 1, layout type.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo_bytes, uint32_t layout) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;  // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)layout << 61;
+  return d;
+}
+constexpr uint32_t LAYOUT_SW128 = 2, LAYOUT_SW32 = 6;
+
+// Instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, N, M.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ------------------------------------------------------------------- kernels
+__device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+// Positions: thread per position; writes 64 + 16 bf16.
+__global__ void __launch_bounds__(256) k_pack_positions(const float* __restrict__ x, const float* __restrict__ mean,
+                                                        int n_img, int C, int H, int W, int P, long long npos_pad,
+                                                        __nv_bfloat16* __restrict__ qmain,
+                                                        __nv_bfloat16* __restrict__ qaux) {
+  const int Hq = H - P + 1, Wq = W - P + 1;
+  const long long npos = (long long)Hq * Wq;
+  const int d = C * P * P;
+  const long long total = (long long)n_img * npos_pad;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / npos_pad;
+    const long long q = i - f * npos_pad;
+    __align__(16) __nv_bfloat16 row[DK_MAIN];
+    __align__(16) __nv_bfloat16 aux[DK_AUX];
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
+#pragma unroll
+    for (int e = 0; e < DK_AUX; ++e) aux[e] = z;
+    if (q < npos) {
+      const int r = (int)(q / Wq), c = (int)(q - (q / Wq) * Wq);
+      const float mu = mean[f];
+      float nrm = 0.f;
+#pragma unroll 8
+      for (int e = 0; e < DK_MAIN; ++e) {
+        float v = 0.f;
+        if (e < d) {
+          const int ch = e / (P * P), dr = (e / P) % P, dc = e % P;
+          v = __ldg(x + (((long long)f * C + ch) * H + r + dr) * W + c + dc) - mu;
+        }
+        row[e] = __float2bfloat16_rn(v);
+        const float rv = __bfloat162float(row[e]);
+        nrm = fmaf(rv, rv, nrm);
+      }
+      split3(nrm, aux[0], aux[1], aux[2]);
+      aux[3] = aux[4] = aux[5] = one;
+    } else {
+#pragma unroll
+      for (int e = 0; e < DK_MAIN; ++e) row[e] = z;
+    }
+    uint4* dst = reinterpret_cast<uint4*>(qmain + i * DK_MAIN);
+    const uint4* src = reinterpret_cast<const uint4*>(row);
+#pragma unroll
+    for (int k = 0; k < DK_MAIN / 8; ++k) dst[k] = src[k];
+    uint4* dsta = reinterpret_cast<uint4*>(qaux + i * DK_AUX);
+    const uint4* srca = reinterpret_cast<const uint4*>(aux);
+    dsta[0] = srca[0];
+    dsta[1] = srca[1];
+  }
+}
+
+// Keys: thread per key slot of the padded key array.
+__global__ void __launch_bounds__(256) k_pack_keys(const float* __restrict__ keyv, int n_keys_total, int d,
+                                                   __nv_bfloat16* __restrict__ kmain,
+                                                   __nv_bfloat16* __restrict__ kaux) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_keys_total; i += gridDim.x * blockDim.x) {
+    __align__(16) __nv_bfloat16 row[DK_MAIN];
+    __align__(16) __nv_bfloat16 aux[DK_AUX];
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
+    float nrm = 0.f;
+#pragma unroll 8
+    for (int e = 0; e < DK_MAIN; ++e) {
+      const float v = e < d ? keyv[(long long)i * d + e] : 0.f;
+      const __nv_bfloat16 b = __float2bfloat16_rn(v);
+      const float rv = __bfloat162float(b);
+      nrm = fmaf(rv, rv, nrm);
+      row[e] = __float2bfloat16_rn(-2.f * rv);  // exact: scaling by -2
+    }
+#pragma unroll
+    for (int e = 0; e < DK_AUX; ++e) aux[e] = z;
+    aux[0] = aux[1] = aux[2] = one;
+    split3(nrm, aux[3], aux[4], aux[5]);
+    uint4* dst = reinterpret_cast<uint4*>(kmain + (long long)i * DK_MAIN);
+    const uint4* src = reinterpret_cast<const uint4*>(row);
+#pragma unroll
+    for (int k = 0; k < DK_MAIN / 8; ++k) dst[k] = src[k];
+    uint4* dsta = reinterpret_cast<uint4*>(kaux + (long long)i * DK_AUX);
+    const uint4* srca = reinterpret_cast<const uint4*>(aux);
+    dsta[0] = srca[0];
+    dsta[1] = srca[1];
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_match_tc(const __grid_constant__ CUtensorMap tm_qmain, const __grid_constant__ CUtensorMap tm_qaux,
+               const __grid_constant__ CUtensorMap tm_kmain, const __grid_constant__ CUtensorMap tm_kaux,
+               const int32_t* __restrict__ n_found, int Npad, long long npos, long long npos_pad, int splits,
+               int tiles_per_split, int ntiles, StreamCfg cfg, uint2* __restrict__ bufs, int* __restrict__ buf_cnt,
+               StatusBlock* st, float* __restrict__ dump) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + TC_STAGES;
+  uint64_t* tfull = bars + 2 * TC_STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* a_full = tempty + 2;
+  uint64_t* mma_done = a_full + 1;
+  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(smem + OFF_MISC);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
+  unsigned* hist = reinterpret_cast<unsigned*>(smem + OFF_HIST);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kt = blockIdx.x, f = blockIdx.y, split = blockIdx.z;
+  const int t_begin = split * tiles_per_split;
+  const int t_end = min(ntiles, t_begin + tiles_per_split);
+  const int nt = max(0, t_end - t_begin);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);
+      mbar_init(tempty + b, TC_EPI_WARPS);
+    }
+    mbar_init(a_full, 1);
+    mbar_init(mma_done, 1);
+    *abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_base_s, 512);
+    tmem_relinquish();
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_base_s;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- producer
+      mbar_arrive_expect_tx(a_full, A_MAIN_BYTES + A_AUX_BYTES);
+      const int arow = f * Npad + kt * TC_M;
+      tma_load_2d(&tm_kmain, a_full, smem + OFF_A_MAIN, 0, arow);
+      tma_load_2d(&tm_kaux, a_full, smem + OFF_A_AUX, 0, arow);
+      int issued = 0;
+      for (int i = 0; i < nt; ++i) {
+        const int s = i % TC_STAGES;
+        const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
+        if (!mbar_wait(empty + s, ph ^ 1u, abort_s, st)) break;
+        mbar_arrive_expect_tx(full + s, B_MAIN_BYTES + B_AUX_BYTES);
+        const int brow = (int)(f * npos_pad + (long long)(t_begin + i) * TC_N);
+        tma_load_2d(&tm_qmain, full + s, smem + OFF_B_MAIN + s * B_MAIN_BYTES, 0, brow);
+        tma_load_2d(&tm_qaux, full + s, smem + OFF_B_AUX + s * B_AUX_BYTES, 0, brow);
+        issued = i + 1;
+      }
+      // teardown: every issued copy has landed before the CTA may exit
+      mbar_wait(a_full, 0, abort_s, st, false);
+      for (int i = max(0, issued - TC_STAGES); i < issued; ++i)
+        mbar_wait(full + (i % TC_STAGES), (uint32_t)(i / TC_STAGES) & 1u, abort_s, st, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // --------------------------------------------------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+      const uint32_t a_main = smem_u32(smem + OFF_A_MAIN), a_aux = smem_u32(smem + OFF_A_AUX);
+      bool ok = mbar_wait(a_full, 0, abort_s, st);
+      tc_fence_after();
+      for (int i = 0; ok && i < nt; ++i) {
+        const int s = i % TC_STAGES;
+        const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
+        const int b = i & 1;
+        const uint32_t bph = (uint32_t)(i >> 1) & 1u;
+        if (!mbar_wait(full + s, ph, abort_s, st)) break;
+        if (!mbar_wait(tempty + b, bph ^ 1u, abort_s, st)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * TC_N);
+        const uint32_t b_main = smem_u32(smem + OFF_B_MAIN + s * B_MAIN_BYTES);
+        const uint32_t b_aux = smem_u32(smem + OFF_B_AUX + s * B_AUX_BYTES);
+#pragma unroll
+        for (int k = 0; k < DK_MAIN / 16; ++k)
+          mma_bf16(d_tmem, smem_desc(a_main + 32 * k, 1024, LAYOUT_SW128), smem_desc(b_main + 32 * k, 1024, LAYOUT_SW128),
+                   idesc, k > 0 ? 1u : 0u);
+        mma_bf16(d_tmem, smem_desc(a_aux, 256, LAYOUT_SW32), smem_desc(b_aux, 256, LAYOUT_SW32), idesc, 1u);
+        mma_commit(empty + s);
+        mma_commit(tfull + b);
+      }
+      // teardown: all issued MMAs have completed
+      mma_commit(mma_done);
+      mbar_wait(mma_done, 0, abort_s, st, false);
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    const int e = warp - 2;
+    const int quad = warp & 3;
+    const int h = e >> 2;
+    const int row = 32 * quad + lane;
+    const int key = kt * TC_M + row;
+    const int nf = min(n_found[f], Npad);
+    const long long stream = (((long long)f * Npad + key) * splits + split) * 2 + h;
+    uint2* mybuf = bufs + stream * (cfg.cap + 32);
+    float tau = (key < nf) ? INFINITY : -INFINITY;
+    int cnt = 0;
+    unsigned* whist = hist + e * 256;
+    for (int i = 0; i < nt; ++i) {
+      const int b = i & 1;
+      const uint32_t bph = (uint32_t)(i >> 1) & 1u;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull + b, bph, abort_s, st));
+      if (!ok) break;
+      tc_fence_after();
+      const long long tile_q0 = (long long)(t_begin + i) * TC_N;
+#pragma unroll 1
+      for (int c = 0; c < 4; ++c) {
+        const int col = h * 128 + c * 32;
+        const uint32_t taddr = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + col);
+        float v[32];
+        tmem_ld_32x32(taddr, v);
+        const long long q0 = tile_q0 + col;
+        const int nvalid = (int)max(0LL, min(32LL, npos - q0));
+        if (dump != nullptr && i == 0 && t_begin == 0) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) dump[((long long)f * Npad + key) * TC_N + col + j] = v[j];
+        }
+        stream_push<32>(v, (int)q0, nvalid, tau, cnt, mybuf, cfg, whist);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty + b);
+    }
+    stream_finish(tau, cnt, mybuf, cfg, whist);
+    buf_cnt[stream] = (key < nf) ? cnt : 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 512);
+  }
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, void* base, uint64_t rows, uint32_t cols, uint32_t box_rows, CUtensorMapSwizzle sw) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  const cuuint32_t box[2] = {cols, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+extern float* g_tc_dump;
+
+glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int32_t* n_found, const MatchPlan& pl,
+                                char* ws, float* dump, cudaStream_t s) {
+  const int d = im.C * im.P * im.P;
+  if (d > DK_MAIN) return GLR_ENOTSUP;
+  const float* mean = reinterpret_cast<const float*>(ws + pl.mean_off);
+  const float* keyv = reinterpret_cast<const float*>(ws + pl.keyv_off);
+  uint2* bufs = reinterpret_cast<uint2*>(ws + pl.buf_off);
+  int* bufcnt = reinterpret_cast<int*>(ws + pl.bufcnt_off);
+  StatusBlock* st = reinterpret_cast<StatusBlock*>(ws);
+  __nv_bfloat16* qmain = reinterpret_cast<__nv_bfloat16*>(ws + pl.qpack_off);
+  __nv_bfloat16* qaux = qmain + (size_t)im.n_img * pl.npos_pad * DK_MAIN;
+  __nv_bfloat16* kmain = reinterpret_cast<__nv_bfloat16*>(ws + pl.kpack_off);
+  __nv_bfloat16* kaux = kmain + (size_t)im.n_img * pl.Npad * DK_MAIN;
+  {
+    const long long total = (long long)im.n_img * pl.npos_pad;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+    GLR_LAUNCH("k_pack_positions", s,
+               k_pack_positions<<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, pl.npos_pad, qmain,
+                                                       qaux));
+  }
+  {
+    const int nk = im.n_img * pl.Npad;
+    const int blocks = (int)std::max<long long>(1, ceil_div(nk, 256));
+    GLR_LAUNCH("k_pack_keys", s, k_pack_keys<<<blocks, 256, 0, s>>>(keyv, nk, d, kmain, kaux));
+  }
+  CUtensorMap tq, tqa, tk, tka;
+  const uint64_t qrows = (uint64_t)im.n_img * pl.npos_pad, krows = (uint64_t)im.n_img * pl.Npad;
+  if (!make_map(&tq, qmain, qrows, DK_MAIN, TC_N, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !make_map(&tqa, qaux, qrows, DK_AUX, TC_N, CU_TENSOR_MAP_SWIZZLE_32B) ||
+      !make_map(&tk, kmain, krows, DK_MAIN, TC_M, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !make_map(&tka, kaux, krows, DK_AUX, TC_M, CU_TENSOR_MAP_SWIZZLE_32B))
+    return GLR_ECUDA;
+  if (cudaFuncSetAttribute(k_match_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) != cudaSuccess)
+    return GLR_ECUDA;
+  const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
+  const StreamCfg cfg{pl.cap, pl.Kp};
+  dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
+  GLR_LAUNCH("k_match_tc", s,
+             k_match_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
+                                                          pl.splits, pl.tiles_per_split, pl.pos_tiles, cfg, bufs,
+                                                          bufcnt, st, dump));
+  return GLR_OK;
+}
+
+glr_status launch_match_tc(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found, int N,
+                           const MatchPlan& pl, char* ws, cudaStream_t s) {
+  (void)keys;
+  (void)N;
+  return launch_match_tc_impl(x, im, n_found, pl, ws, g_tc_dump, s);
+}
+
+float* g_tc_dump = nullptr;
 
 }  // namespace glr

@@ -32,7 +32,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // Compact the buffer of lane L to its kp smallest (key, id) entries.  All 32 lanes call.
-__device__ __noinline__ void stream_compact(int L, float& tau, int& cnt, uint2* buf, int kp, unsigned* hist) {
+static __device__ __noinline__ void stream_compact(int L, float& tau, int& cnt, uint2* buf, int kp, unsigned* hist) {
   const int lane = threadIdx.x & 31;
   const int n = __shfl_sync(0xffffffffu, cnt, L);
   uint2* b = reinterpret_cast<uint2*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(buf), L));

@@ -115,6 +115,21 @@ def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, idx=N
     return idx, dist
 
 
+def debug_match_scores(x, P, keys, n_found, K, *, ws=None, stream=None):
+    """Raw BF16 tensor-core scores of every key against the first 256 positions (testing aid)."""
+    lib = L.load()
+    im = images_of(x, P)
+    N = keys.shape[1]
+    npad = (N + 127) // 128 * 128
+    scores = torch.full((x.shape[0], npad, 256), float("nan"), dtype=torch.float32, device=x.device)
+    if ws is None:
+        ws = workspace(L.GLR_OP_MATCH, im, N, K, match_opts("bf16"), x.device)
+    wp, wn = _ws(ws)
+    _check("glr_debug_match_scores", lib.glr_debug_match_scores(_ptr(x), ctypes.byref(im), _ptr(keys), _ptr(n_found),
+                                                                int(N), int(K), _ptr(scores), wp, wn, _stream(stream)))
+    return scores
+
+
 def lowrank_groups(x, P, idx, n_found, sigma_w, c_wnnm, *, groups=None, rank=None, ws=None, stream=None):
     """R~_i x and the WNNM step of Eq. 5; returns (groups [n][N][K][d] = X^, rank [n][N])."""
     lib = L.load()
