@@ -271,6 +271,19 @@ def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict) -
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+def workload(name: str):
+    """The timed workload: 16 x 512^2 (the headline); smaller cases for profiling captures."""
+    from paper_2301_03047_gb300 import synth
+
+    if name == "sci16":
+        return synth.SCI_LARGE
+    if name == "sci4":  # profiling case: same frame size, 4 frames (operands still larger than L2)
+        return synth.scaled(synth.SCI_LARGE, T=4, name="sci_4x512x512_P8_N4096_K64")
+    if name == "sci8":
+        return synth.SCI_SMALL
+    raise ValueError(name)
+
+
 def run_glr(args) -> None:
     import numpy as np
     import torch
@@ -285,7 +298,7 @@ def run_glr(args) -> None:
     from oracle import glr_oracle as O  # only for PSNR bookkeeping of the result (no compute on the path)
     from paper_2301_03047_gb300 import glr, synth
 
-    cfg = synth.SCI_LARGE
+    cfg = workload(args.workload)
     prob = synth.sci_problem(cfg)
     y = torch.from_numpy(prob.y).to(dev)
     masks = torch.from_numpy(prob.masks).to(dev)
@@ -414,6 +427,7 @@ def run_glr(args) -> None:
         "psnr_db": round(head["psnr"], 3),
         "gpu_launches": launches,
         "kernels": kernels,
+        "svd_sweeps_per_group": round(sweeps, 2),
         "roofline": rl,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -481,6 +495,8 @@ def main() -> None:
     ap.add_argument("--impl", default="glr", choices=["glr", "reference"])
     ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--oracle-keys", type=int, default=96)
+    ap.add_argument("--workload", default="sci16", choices=["sci16", "sci4", "sci8"],
+                    help="sci16 = the headline workload; sci4 / sci8 are smaller cases for profiling")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

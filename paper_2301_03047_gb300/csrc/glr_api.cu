@@ -173,7 +173,7 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
   if (opts && opts->mode != GLR_MATCH_FP32 && opts->mode != GLR_MATCH_BF16) return GLR_EINVAL;
   if (opts && (opts->k_over < 0 || opts->splits < 0 || (opts->k_over > 0 && opts->k_over < K))) return GLR_EINVAL;
   const MatchPlan pl = match_plan(*im, N, K, opts);
-  if (pl.Kp > 512) return GLR_ENOTSUP;
+  if (pl.Kp > 256 || pl.Kp >= pl.cap) return GLR_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
   glr_status st = begin_ws(ws, ws_bytes, pl.total, s);
   if (st != GLR_OK) return st;

@@ -55,35 +55,46 @@ __global__ void __launch_bounds__(256) k_gather(const float* __restrict__ x, int
   }
 }
 
+// One Jacobi rotation of the column pair (a, b) held by this lane.  alpha / beta
+// are the tracked squared norms of a / b (updated exactly as the rotation
+// changes them: alpha - t gamma, beta + t gamma); only gamma = a.b is summed.
 template <int DMAX>
-__device__ __forceinline__ void jacobi_pair(float (&a)[DMAX], float (&b)[DMAX], float tol, bool active, bool& rotated) {
-  float alpha = 0.f, beta = 0.f, gamma = 0.f;
+__device__ __forceinline__ void jacobi_pair(float (&a)[DMAX], float (&b)[DMAX], float& alpha, float& beta, float tol,
+                                            bool active, bool& rotated) {
+  float ga[4] = {0.f, 0.f, 0.f, 0.f};  // four partial sums shorten the dependency chain
 #pragma unroll
-  for (int r = 0; r < DMAX; ++r) {
-    alpha = fmaf(a[r], a[r], alpha);
-    beta = fmaf(b[r], b[r], beta);
-    gamma = fmaf(a[r], b[r], gamma);
-  }
+  for (int r = 0; r < DMAX; ++r) ga[r & 3] = fmaf(a[r], b[r], ga[r & 3]);
+  const float gamma = (ga[0] + ga[1]) + (ga[2] + ga[3]);
   if (active && fabsf(gamma) > tol * sqrtf(alpha * beta) && gamma != 0.f) {
-    const float zeta = (beta - alpha) / (2.f * gamma);
+    const float zeta = __fdividef(beta - alpha, 2.f * gamma);
     const float az = fabsf(zeta);
-    float t = (az < 1e18f) ? 1.f / (az + sqrtf(1.f + zeta * zeta)) : 0.5f / az;
+    float t = (az < 1e18f) ? __frcp_rn(az + sqrtf(fmaf(zeta, zeta, 1.f))) : __fdividef(0.5f, az);
     t = copysignf(t, zeta);
-    const float cs = rsqrtf(1.f + t * t);
+    const float cs = rsqrtf(fmaf(t, t, 1.f));
     const float sn = cs * t;
 #pragma unroll
     for (int r = 0; r < DMAX; ++r) {
       const float ar = a[r], br = b[r];
-      a[r] = cs * ar - sn * br;
-      b[r] = sn * ar + cs * br;
+      a[r] = fmaf(cs, ar, -sn * br);
+      b[r] = fmaf(sn, ar, cs * br);
     }
+    alpha = fmaf(-t, gamma, alpha);
+    beta = fmaf(t, gamma, beta);
     rotated = true;
   }
 }
 
+template <int DMAX>
+__device__ __forceinline__ float sq_norm(const float (&a)[DMAX]) {
+  float p[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int r = 0; r < DMAX; ++r) p[r & 3] = fmaf(a[r], a[r], p[r & 3]);
+  return (p[0] + p[1]) + (p[2] + p[3]);
+}
+
 // DMAX rows per column, KMAX <= 64 columns, one warp per group, WARPS groups per CTA.
 template <int DMAX, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_jacobi_wnnm(int n_img, int d, int N, int K,
+__global__ void __launch_bounds__(WARPS * 32, 2) k_jacobi_wnnm(int n_img, int d, int N, int K,
                                                             const int32_t* __restrict__ n_found, float sigma_w,
                                                             float c_wnnm, float tol, int max_sweeps,
                                                             float* __restrict__ groups, int32_t* __restrict__ rank,
@@ -118,11 +129,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_jacobi_wnnm(int n_img, int d, in
     bool converged = (m < 1);
     while (!converged && sweep < max_sweeps) {
       bool rotated = false;
+      // exact norms once per sweep; tracked through the rotations within it
+      float alpha = sq_norm<DMAX>(a), beta = sq_norm<DMAX>(b);
       for (int round = 0; round < 2 * m - 1; ++round) {
-        jacobi_pair<DMAX>(a, b, tol, live, rotated);
+        jacobi_pair<DMAX>(a, b, alpha, beta, tol, live, rotated);
         if (m > 1) {
           // circle rotation: slot top[0] stays; top[1] <- bot[0]; top[k] <- top[k-1];
-          // bot[m-1] <- top[m-1]; bot[k] <- bot[k+1]
+          // bot[m-1] <- top[m-1]; bot[k] <- bot[k+1]  (columns move with their norms)
 #pragma unroll
           for (int r = 0; r < DMAX; ++r) {
             const float up_src = (lane == 0) ? b[r] : a[r];
@@ -133,6 +146,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_jacobi_wnnm(int n_img, int d, in
             a[r] = na;
             b[r] = nb;
           }
+          const float up_n = (lane == 0) ? beta : alpha;
+          const float tn = __shfl_up_sync(0xffffffffu, up_n, 1);
+          const float bn = __shfl_down_sync(0xffffffffu, beta, 1);
+          const float nal = (lane == 0) ? alpha : tn;
+          const float nbe = (lane == m - 1) ? alpha : bn;
+          alpha = nal;
+          beta = nbe;
         }
       }
       ++sweep;
@@ -190,26 +210,26 @@ __global__ void __launch_bounds__(WARPS * 32) k_jacobi_wnnm(int n_img, int d, in
     for (int h = 0; h < 2; ++h) {
       const int j = 2 * lane + h;
       const bool own = live && j < K;
-      float y[DMAX], o[DMAX];
+      // a / b are free once W is staged: reuse them as y_j and x^_j
 #pragma unroll
       for (int r = 0; r < DMAX; ++r) {
-        y[r] = (own && r < d) ? Y[(long long)j * d + r] : 0.f;
-        o[r] = 0.f;
+        a[r] = (own && r < d) ? Y[(long long)j * d + r] : 0.f;
+        b[r] = 0.f;
       }
       for (int i = 0; i < rnk; ++i) {
         const float* w = Ws + i * DMAX;
-        float z = 0.f;
+        float zp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int r = 0; r < DMAX; ++r) z = fmaf(w[r], y[r], z);
-        z *= coef_s[wid][i];
+        for (int r = 0; r < DMAX; ++r) zp[r & 3] = fmaf(w[r], a[r], zp[r & 3]);
+        const float z = ((zp[0] + zp[1]) + (zp[2] + zp[3])) * coef_s[wid][i];
 #pragma unroll
-        for (int r = 0; r < DMAX; ++r) o[r] = fmaf(z, w[r], o[r]);
+        for (int r = 0; r < DMAX; ++r) b[r] = fmaf(z, w[r], b[r]);
       }
       __syncwarp();
       if (own) {
 #pragma unroll
         for (int r = 0; r < DMAX; ++r)
-          if (r < d) Y[(long long)j * d + r] = o[r];
+          if (r < d) Y[(long long)j * d + r] = b[r];
       }
     }
     __syncwarp();
@@ -240,7 +260,7 @@ glr_status launch_wnnm(const glr_images& im, const int32_t* n_found, int N, int 
     return GLR_ECUDA;
   const long long ngroups = (long long)im.n_img * N;
   const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(ngroups, WARPS), 152LL * 64));
-  const float tol = 2e-6f;
+  const float tol = 1e-5f;
   GLR_LAUNCH("k_jacobi_wnnm", s, k_jacobi_wnnm<DMAX, WARPS><<<blocks, WARPS * 32, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, 30,
                                                              groups, rank, st));
   return GLR_OK;

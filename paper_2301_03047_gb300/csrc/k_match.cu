@@ -218,7 +218,10 @@ __global__ void __launch_bounds__(256, 2)
         s[4 * v + 2] = t4.z;
         s[4 * v + 3] = t4.w;
       }
-      stream_push<32>(s, qbase + col0, nvalid, tau, cnt, mybuf, cfg, whist);
+      const unsigned rows = stream_filter(s, nvalid, tau);
+      if (rows)
+        stream_append(rows, Sc + (32 * (wid & 3)) * SC_LD + col0, SC_LD, qbase + col0, nvalid, tau, cnt, mybuf, cfg,
+                      whist);
     }
   }
   stream_finish(tau, cnt, mybuf, cfg, whist);
@@ -317,8 +320,8 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   pl.K = K;
   pl.Kp = (o && o->k_over > 0) ? o->k_over : (pl.mode == GLR_MATCH_BF16 ? 2 * K : K + 16);
   pl.Kp = std::max(pl.Kp, K);
-  pl.cap = std::max(4 * pl.Kp, 256);
-  pl.cap = (int)ceil_div(pl.cap, 32) * 32;
+  pl.cap = std::min(std::max(4 * pl.Kp, 256), kStreamMaxEntries - 32);
+  pl.cap = (int)(pl.cap / 32) * 32;
   pl.subs = 2;
   pl.key_tile = FT;
   pl.Npad = (int)(ceil_div(N, FT) * FT);

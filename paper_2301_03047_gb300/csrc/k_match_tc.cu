@@ -54,7 +54,10 @@ constexpr uint32_t OFF_BAR = OFF_B_AUX + TC_STAGES * B_AUX_BYTES;  // 8-byte bar
 constexpr int NBAR = 2 * TC_STAGES + 4 + 2;                        // full, empty, tmem_full x2, tmem_empty x2, a_full, mma_done
 constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;                  // tmem base, abort flag
 constexpr uint32_t OFF_HIST = (OFF_MISC + 64 + 15) / 16 * 16;
-constexpr uint32_t TC_SMEM = OFF_HIST + TC_EPI_WARPS * 256 * 4 + 1024;  // + alignment slack
+constexpr int TILE_LD = 33;  // per-warp 32 x 32 score tile for the row-wise append
+constexpr uint32_t OFF_TILE = OFF_HIST + TC_EPI_WARPS * 256 * 4;
+constexpr uint32_t TC_SMEM = OFF_TILE + TC_EPI_WARPS * 32 * TILE_LD * 4 + 1024;  // + alignment slack
+static_assert(TC_SMEM <= 232448, "shared memory budget");
 constexpr unsigned long long kWaitNs = 1000000000ull;                   // 1 s
 
 // ---------------------------------------------------------------- PTX helpers
@@ -130,21 +133,18 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 32 lanes x 32 consecutive FP32 columns; the destination registers are valid after tmem_ld_wait().
+__device__ __forceinline__ void tmem_ld_32x32_nowait(uint32_t taddr, float (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
       "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
+        "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15]), "=f"(v[16]),
+        "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]), "=f"(v[22]), "=f"(v[23]), "=f"(v[24]),
+        "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
-
 // Shared-memory matrix descriptor (K-major operand, swizzled): start address,
 // leading / stride byte offsets (>> 4), descriptor version 1, layout type.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo_bytes, uint32_t layout) {
@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(smem + OFF_MISC);
   volatile int* abort_s = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
   unsigned* hist = reinterpret_cast<unsigned*>(smem + OFF_HIST);
+  float* tiles = reinterpret_cast<float*>(smem + OFF_TILE);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kt = blockIdx.x, f = blockIdx.y, split = blockIdx.z;
@@ -367,6 +368,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     float tau = (key < nf) ? INFINITY : -INFINITY;
     int cnt = 0;
     unsigned* whist = hist + e * 256;
+    float* wtile = tiles + e * 32 * TILE_LD;
     for (int i = 0; i < nt; ++i) {
       const int b = i & 1;
       const uint32_t bph = (uint32_t)(i >> 1) & 1u;
@@ -374,23 +376,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) break;
       tc_fence_after();
       const long long tile_q0 = (long long)(t_begin + i) * TC_N;
-#pragma unroll 1
+      float v[4][32];
+      {
+        const uint32_t taddr = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128);
+        tmem_ld_32x32_nowait(taddr, v[0]);
+        tmem_ld_32x32_nowait(taddr + 32, v[1]);
+        tmem_ld_32x32_nowait(taddr + 64, v[2]);
+        tmem_ld_32x32_nowait(taddr + 96, v[3]);
+        tmem_ld_wait();
+      }
+      // the accumulator is in registers: hand the TMEM buffer back to the MMA warp
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty + b);
+#pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int col = h * 128 + c * 32;
-        const uint32_t taddr = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + col);
-        float v[32];
-        tmem_ld_32x32(taddr, v);
         const long long q0 = tile_q0 + col;
         const int nvalid = (int)max(0LL, min(32LL, npos - q0));
         if (dump != nullptr && i == 0 && t_begin == 0) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) dump[((long long)f * Npad + key) * TC_N + col + j] = v[j];
+          for (int j = 0; j < 32; ++j) dump[((long long)f * Npad + key) * TC_N + col + j] = v[c][j];
         }
-        stream_push<32>(v, (int)q0, nvalid, tau, cnt, mybuf, cfg, whist);
+        const unsigned rows = stream_filter(v[c], nvalid, tau);
+        if (rows) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) wtile[lane * TILE_LD + j] = v[c][j];
+          __syncwarp();
+          stream_append(rows, wtile, TILE_LD, (int)q0, nvalid, tau, cnt, mybuf, cfg, whist);
+        }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty + b);
     }
     stream_finish(tau, cnt, mybuf, cfg, whist);
     buf_cnt[stream] = (key < nf) ? cnt : 0;

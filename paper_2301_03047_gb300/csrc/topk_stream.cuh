@@ -1,19 +1,23 @@
 // Running per-key top-K' over a stream of scores, shared by the FP32 and the
-// tensor-core scorers.  Each lane of a warp owns one key row; the 32 lanes
-// push 32-column chunks of their rows in lock step.
+// tensor-core scorers.  A warp serves 32 key rows; lane r holds the state of
+// row r: a threshold tau and a candidate buffer (global memory, cap + 32
+// entries of {order-preserving score bits, position id}).
 //
-//   * A lane keeps a threshold tau and a candidate buffer (global memory,
-//     cap + 32 entries of {order-preserving score bits, position id}).
-//     A score s < tau is appended; a chunk whose minimum is >= tau for every
-//     lane costs one min-reduction and a warp vote.
-//   * When a lane's buffer holds more than cap entries the whole warp
-//     compacts it: a 4-pass 8-bit radix select finds the K'-th smallest
-//     score, entries below it are kept, and among entries equal to it the
-//     earliest (= smallest position ids, since a stream is scanned in
-//     increasing id order) fill the remaining slots.  tau becomes the K'-th
-//     smallest score; later equal scores have larger ids and lose the tie.
-//   * The buffer therefore always contains the K' smallest (score, id) pairs
-//     seen so far, plus at most cap + 32 - K' others.
+// One 32-column chunk is pushed in two steps:
+//   1. filter   each lane takes the minimum of its row's 32 scores (in
+//               registers) and compares it with its tau: one instruction per
+//               score, and a warp vote gives the rows that have a candidate.
+//   2. append   for each such row the warp reads the row from a shared-memory
+//               tile (lane = column), votes on s < tau and appends the
+//               candidates in position order with one coalesced store.
+// When a buffer holds more than cap entries the warp compacts it: the new
+// threshold is a pivot drawn from 32 sorted samples such that at least K'
+// entries lie below it (entries >= pivot are dropped), or, if the sample
+// misses, the exact K'-th smallest found by a 4-pass radix select.  The
+// buffer therefore always holds every entry that can still be among the K'
+// smallest (score, id) pairs of the stream.  At the end of the stream an
+// exact compaction leaves exactly the K' smallest, ties by smaller id
+// (entries are appended in increasing id order).
 #pragma once
 
 #include "glr_common.cuh"
@@ -22,8 +26,11 @@ namespace glr {
 
 struct StreamCfg {
   int cap;  // compaction trigger (entries)
-  int kp;   // entries kept by a compaction
+  int kp;   // entries kept per stream
 };
+
+constexpr int kStreamSlots = 17;                      // buffer entries per lane of the compacting warp
+constexpr int kStreamMaxEntries = 32 * kStreamSlots;  // cap + 32 <= 544
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -31,23 +38,28 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-// Compact the buffer of lane L to its kp smallest (key, id) entries.  All 32 lanes call.
-static __device__ __noinline__ void stream_compact(int L, float& tau, int& cnt, uint2* buf, int kp, unsigned* hist) {
+// Exact: keep the kp smallest (key, buffer order) entries of b[0..n).  Returns the new count;
+// *tau_key receives the kp-th smallest key.  Warp-collective (uniform arguments).
+static __device__ __noinline__ int compact_exact(uint2* b, int n, int kp, unsigned* hist, uint32_t* tau_key) {
   const int lane = threadIdx.x & 31;
-  const int n = __shfl_sync(0xffffffffu, cnt, L);
-  uint2* b = reinterpret_cast<uint2*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(buf), L));
-  __syncwarp();
-  if (n <= kp) return;
+  uint2 e[kStreamSlots];
+#pragma unroll
+  for (int i = 0; i < kStreamSlots; ++i) {
+    const int j = lane + 32 * i;
+    e[i] = (j < n) ? b[j] : make_uint2(0xffffffffu, 0u);
+  }
   uint32_t prefix = 0, pmask = 0;
   int k = kp;  // 1-based rank of the wanted element among those matching the prefix
+#pragma unroll 1
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = 24 - 8 * pass;
 #pragma unroll
     for (int i = 0; i < 8; ++i) hist[lane * 8 + i] = 0;
     __syncwarp();
-    for (int i = lane; i < n; i += 32) {
-      const uint32_t key = b[i].x;
-      if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+#pragma unroll
+    for (int i = 0; i < kStreamSlots; ++i) {
+      const int j = lane + 32 * i;
+      if (j < n && (e[i].x & pmask) == prefix) atomicAdd(&hist[(e[i].x >> shift) & 255u], 1u);
     }
     __syncwarp();
     int loc[8];
@@ -86,70 +98,140 @@ static __device__ __noinline__ void stream_compact(int L, float& tau, int& cnt, 
     pmask |= 255u << shift;
     __syncwarp();
   }
-  const uint32_t T = prefix;  // kp-th smallest key; keep k entries equal to T
+  const uint32_t T = prefix;
   int out = 0, ties = 0;
   const unsigned lt_mask = lanemask_lt();
-  for (int base = 0; base < n; base += 32) {
-    const int i = base + lane;
-    uint2 e = make_uint2(0xffffffffu, 0u);
-    if (i < n) e = b[i];
-    const bool lt = (i < n) && e.x < T;
-    const bool eq = (i < n) && e.x == T;
+#pragma unroll
+  for (int i = 0; i < kStreamSlots; ++i) {
+    const int j = lane + 32 * i;
+    const bool lt = (j < n) && e[i].x < T;
+    const bool eq = (j < n) && e[i].x == T;
     const unsigned eqm = __ballot_sync(0xffffffffu, eq);
     const int tie_rank = ties + __popc(eqm & lt_mask);
     const bool keep = lt || (eq && tie_rank < k);
     const unsigned km = __ballot_sync(0xffffffffu, keep);
-    __syncwarp();
-    if (keep) b[out + __popc(km & lt_mask)] = e;
+    if (keep) b[out + __popc(km & lt_mask)] = e[i];
     out += __popc(km);
     ties += __popc(eqm);
-    __syncwarp();
   }
-  if (lane == L) {
-    cnt = out;
-    tau = float_from_order_key(T);
+  __syncwarp();
+  *tau_key = T;
+  return out;
+}
+
+// Mid-stream: drop every entry at or above a pivot that leaves between kp and
+// cap - 32 entries; falls back to the exact selection.  Warp-collective.
+static __device__ __noinline__ int compact_pivot(uint2* b, int n, int kp, int cap, unsigned* hist, float* tau) {
+  const int lane = threadIdx.x & 31;
+  // 32 samples spread over the buffer, sorted across the warp (bitonic, ascending)
+  uint32_t smp = b[(int)(((long long)lane * n) >> 5)].x;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint32_t o = __shfl_xor_sync(0xffffffffu, smp, j);
+      const bool up = ((lane & k) == 0);
+      const bool lower = ((lane & j) == 0);
+      smp = (lower == up) ? min(smp, o) : max(smp, o);
+    }
+  }
+  const int target = kp + (cap - kp) / 4;
+  const int pidx = min(31, max(0, (int)(((long long)target * 32) / n)));
+  const uint32_t pivot = __shfl_sync(0xffffffffu, smp, pidx);
+  uint2 e[kStreamSlots];
+  int below = 0;
+#pragma unroll
+  for (int i = 0; i < kStreamSlots; ++i) {
+    const int j = lane + 32 * i;
+    e[i] = (j < n) ? b[j] : make_uint2(0xffffffffu, 0u);
+    below += (j < n && e[i].x < pivot) ? 1 : 0;
+  }
+  below = __reduce_add_sync(0xffffffffu, below);
+  if (below < kp || below > cap - 32) {
+    uint32_t T;
+    const int out = compact_exact(b, n, kp, hist, &T);
+    *tau = float_from_order_key(T);
+    return out;
+  }
+  int out = 0;
+  const unsigned lt_mask = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < kStreamSlots; ++i) {
+    const int j = lane + 32 * i;
+    const bool keep = (j < n) && e[i].x < pivot;
+    const unsigned km = __ballot_sync(0xffffffffu, keep);
+    if (keep) b[out + __popc(km & lt_mask)] = e[i];
+    out += __popc(km);
+  }
+  __syncwarp();
+  *tau = float_from_order_key(pivot);
+  return out;
+}
+
+// Step 1 of a chunk push: rows (bit r = lane r) whose 32 scores contain one
+// below their tau.  s = this lane's row scores, column j = position q0 + j;
+// columns j >= nvalid do not exist.
+__device__ __forceinline__ unsigned stream_filter(const float (&s)[32], int nvalid, float tau) {
+  float m = s[0];
+  if (nvalid < 32) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) m = fminf(m, j < nvalid ? s[j] : INFINITY);
+    if (nvalid <= 0) m = INFINITY;
+  } else {
+#pragma unroll
+    for (int j = 1; j < 32; ++j) m = fminf(m, s[j]);
+  }
+  return __ballot_sync(0xffffffffu, m < tau);
+}
+
+// Step 2: append the candidates of the selected rows.  tile holds the same
+// 32 x 32 scores in shared memory, row r at tile + r * ld (lane = column).
+// tau / cnt / row_buf belong to this lane's row.
+__device__ __forceinline__ void stream_append(unsigned rows, const float* tile, int ld, int q0, int nvalid,
+                                              float& tau, int& cnt, uint2* row_buf, const StreamCfg& cfg,
+                                              unsigned* hist) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = lanemask_lt();
+  while (rows) {
+    const int r = __ffs(rows) - 1;
+    rows &= rows - 1;
+    const float t_r = __shfl_sync(0xffffffffu, tau, r);
+    int c_r = __shfl_sync(0xffffffffu, cnt, r);
+    uint2* b_r = reinterpret_cast<uint2*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(row_buf), r));
+    const float v = tile[r * ld + lane];
+    const bool c = (lane < nvalid) && v < t_r;
+    const unsigned bal = __ballot_sync(0xffffffffu, c);
+    if (c) b_r[c_r + __popc(bal & lt_mask)] = make_uint2(float_order_key(v), (unsigned)(q0 + lane));
+    c_r += __popc(bal);
+    float nt = t_r;
+    if (c_r > cfg.cap) {
+      __syncwarp();
+      c_r = compact_pivot(b_r, c_r, cfg.kp, cfg.cap, hist, &nt);
+    }
+    if (lane == r) {
+      cnt = c_r;
+      tau = nt;
+    }
   }
   __syncwarp();
 }
 
-// Push one 32-column chunk of this lane's row: s[j] is the score of position q0 + j,
-// columns j >= nvalid do not exist.  All 32 lanes call with the same q0 / nvalid.
-template <int NC>
-__device__ __forceinline__ void stream_push(const float (&s)[NC], int q0, int nvalid, float& tau, int& cnt,
-                                            uint2* buf, const StreamCfg& cfg, unsigned* hist) {
-  float m = INFINITY;
-#pragma unroll
-  for (int j = 0; j < NC; ++j) m = fminf(m, j < nvalid ? s[j] : INFINITY);
-  const bool any = m < tau;
-  if (__any_sync(0xffffffffu, any)) {
-    if (any) {
-#pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        if (j < nvalid && s[j] < tau) {
-          buf[cnt] = make_uint2(float_order_key(s[j]), (unsigned)(q0 + j));
-          ++cnt;
-        }
-      }
-    }
-    __syncwarp();
-    unsigned need = __ballot_sync(0xffffffffu, cnt > cfg.cap);
-    while (need) {
-      const int L = __ffs(need) - 1;
-      need &= need - 1;
-      stream_compact(L, tau, cnt, buf, cfg.kp, hist);
-    }
-  }
-}
-
-// End of a stream: bring every buffer down to kp entries.
-__device__ __forceinline__ void stream_finish(float& tau, int& cnt, uint2* buf, const StreamCfg& cfg,
+// End of a stream: every buffer keeps exactly its min(cnt, kp) smallest entries.
+__device__ __forceinline__ void stream_finish(float& tau, int& cnt, uint2* row_buf, const StreamCfg& cfg,
                                               unsigned* hist) {
   __syncwarp();
   unsigned need = __ballot_sync(0xffffffffu, cnt > cfg.kp);
   while (need) {
-    const int L = __ffs(need) - 1;
+    const int r = __ffs(need) - 1;
     need &= need - 1;
-    stream_compact(L, tau, cnt, buf, cfg.kp, hist);
+    const int c_r = __shfl_sync(0xffffffffu, cnt, r);
+    uint2* b_r = reinterpret_cast<uint2*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(row_buf), r));
+    uint32_t T;
+    const int out = compact_exact(b_r, c_r, cfg.kp, hist, &T);
+    if ((threadIdx.x & 31) == r) {
+      cnt = out;
+      tau = float_from_order_key(T);
+    }
   }
 }
 
