@@ -310,6 +310,7 @@ def run_glr(args) -> None:
     prof = None
     clocks_summary = None
     sweeps = 0.0
+    stream_stats = None
     launches = 0
     for form in forms:
         rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=form, edge_th=cfg.edge_th,
@@ -352,6 +353,9 @@ def run_glr(args) -> None:
             glr.profile_enable(False)
             bits, cnt = glr.poll_status(rec.den.ws_lowrank)
             sweeps = cnt[2] / max(cnt[3], 1)
+            _, mcnt = glr.poll_status(rec.den.ws_match)
+            stream_stats = {"appends_per_key": round(mcnt[4] / (cfg.T * cfg.N), 1),
+                            "compactions_per_key": round(mcnt[5] / (cfg.T * cfg.N), 2)}
         x = rec.x.cpu().numpy()[0]
         results[form] = {"total_s": total_s, "ms_per_step": total_s / args.steps * 1e3, "step_ms": step_ms,
                          "psnr": O.psnr_framewise(x, prob.truth), "iters": k}
@@ -428,6 +432,7 @@ def run_glr(args) -> None:
         "gpu_launches": launches,
         "kernels": kernels,
         "svd_sweeps_per_group": round(sweeps, 2),
+        "topk_streams": stream_stats,
         "roofline": rl,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -79,9 +79,11 @@ enum {
 typedef struct glr_match_opts {
   int32_t mode;   /* GLR_MATCH_* */
   int32_t k_over; /* candidates kept per key and position split before the exact
-                     FP32 re-rank; 0 = default (K+16 for FP32, 2K for BF16) */
+                     FP32 re-rank; 0 = default (K+16) */
   int32_t splits; /* position splits per key tile; 0 = automatic */
-  int32_t reserved[5];
+  int32_t cap;    /* candidates a top-K stream may hold before it compacts
+                     (> k_over, <= 512); 0 = automatic */
+  int32_t reserved[4];
 } glr_match_opts;
 
 /* Operation codes for glr_workspace_size. */
@@ -196,9 +198,11 @@ glr_status glr_gap_step(const float* y, const float* masks, int64_t mask_group_s
 
 /*
  * Reads the status block of a workspace used by an earlier call (blocks on
- * `stream`).  bits = OR of GLR_DEV_*; counters (may be NULL) receives 4
+ * `stream`).  bits = OR of GLR_DEV_*; counters (may be NULL) receives 6
  * uint32 values: [0] keys whose candidate buffer overflowed, [1] groups whose
- * SVD hit the sweep cap, [2] total Jacobi sweeps, [3] groups processed.
+ * SVD hit the sweep cap, [2] total Jacobi sweeps, [3] groups processed,
+ * [4] candidates appended by the matching top-K streams (saturating),
+ * [5] top-K stream compactions (saturating).
  * Returns GLR_EDEVICE if any error bit (timeout, non-finite, bad index) is set.
  * Pass reset != 0 to clear the block afterwards.
  */

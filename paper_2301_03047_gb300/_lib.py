@@ -25,7 +25,7 @@ class GlrImages(ctypes.Structure):
 
 
 class GlrMatchOpts(ctypes.Structure):
-    _fields_ = [("mode", c_int32), ("k_over", c_int32), ("splits", c_int32), ("reserved", c_int32 * 5)]
+    _fields_ = [("mode", c_int32), ("k_over", c_int32), ("splits", c_int32), ("cap", c_int32), ("reserved", c_int32 * 4)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/glr.h

@@ -171,7 +171,9 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
   if (N < 1 || K < 1 || K > npos) return GLR_EINVAL;
   if (K > 128) return GLR_ENOTSUP;
   if (opts && opts->mode != GLR_MATCH_FP32 && opts->mode != GLR_MATCH_BF16) return GLR_EINVAL;
-  if (opts && (opts->k_over < 0 || opts->splits < 0 || (opts->k_over > 0 && opts->k_over < K))) return GLR_EINVAL;
+  if (opts && (opts->k_over < 0 || opts->splits < 0 || opts->cap < 0 || (opts->k_over > 0 && opts->k_over < K)))
+    return GLR_EINVAL;
+  if (opts && opts->cap > 512) return GLR_ENOTSUP;
   const MatchPlan pl = match_plan(*im, N, K, opts);
   if (pl.Kp > 256 || pl.Kp >= pl.cap) return GLR_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
@@ -245,6 +247,8 @@ glr_status glr_poll_status(const void* ws, uint32_t* bits, uint32_t* counters, i
     counters[1] = h.svd_noconv;
     counters[2] = h.sweeps;
     counters[3] = h.groups;
+    counters[4] = (uint32_t)std::min<unsigned long long>(h.cand_appends, 0xffffffffull);
+    counters[5] = (uint32_t)std::min<unsigned long long>(h.compactions, 0xffffffffull);
   }
   if (reset) {
     if (cudaMemsetAsync(const_cast<void*>(ws), 0, sizeof(StatusBlock), s) != cudaSuccess) return GLR_ECUDA;

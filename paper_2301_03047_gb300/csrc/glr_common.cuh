@@ -17,7 +17,10 @@ struct StatusBlock {
   uint32_t svd_noconv;     // groups that reached the sweep cap
   uint32_t sweeps;         // total Jacobi sweeps
   uint32_t groups;         // groups processed
-  uint32_t pad[59];
+  uint32_t pad0;
+  unsigned long long cand_appends;  // candidates appended by the top-K streams
+  unsigned long long compactions;   // stream compactions
+  uint32_t pad[54];
 };
 static_assert(sizeof(StatusBlock) == 256, "status block is 256 bytes");
 

@@ -35,7 +35,7 @@ struct MatchPlan {
   int tiles_per_split;
   int dk;               // BF16 operand row length (elements)
   long long npos_pad;   // BF16 position rows per image (pos_tiles * pos_tile)
-  size_t mean_off, qn_off, keyv_off, buf_off, bufcnt_off, qpack_off, kpack_off, total;
+  size_t mean_off, qn_off, keyv_off, buf_off, bufcnt_off, taugl_off, qpack_off, kpack_off, total;
 };
 MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o);
 glr_status launch_match(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found, int N,

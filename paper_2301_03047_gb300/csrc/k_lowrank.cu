@@ -5,10 +5,10 @@
 //                stores; loads hit the L2-resident image.  HBM-write bound.
 //  k_jacobi_wnnm one warp per group Y (d x K).  One-sided Jacobi (Hestenes)
 //                SVD in FP32 with the columns held in registers: lane L owns two
-//                columns; the K/2 lanes rotate their column pairs in parallel and
-//                then pass columns along a circle (round-robin tournament
-//                ordering) with two warp shuffles per element, so every pair
-//                meets once per sweep.  Rotation angles use the stable
+//                column slots (zero beyond K); the 32 lanes rotate their pairs in
+//                parallel and re-pair by a recursive-halving ordering (cyclic
+//                shifts within lane groups, one shuffle per element), so every
+//                pair meets once per sweep.  Rotation angles use the stable
 //                formulas of Rutishauser (t = sign(z)/(|z| + sqrt(1 + z^2))).
 //                Sweeps stop when no pair has |a.b| > tol sqrt(|a|^2 |b|^2).
 //                With W = Y V (columns w_i = s_i u_i) the WNNM estimate is
@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_jacobi_wnnm(int n_img, int d,
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float* Ws = wsm + (size_t)wid * 64 * DMAX;
   const long long ngroups = (long long)n_img * N;
-  const int m = (K + 1) / 2;  // lanes holding a column pair
-  const bool live = lane < m;
+  const int m = (K + 1) / 2;  // lanes holding at least one real column; the other slots are zero
+  const bool live = true;     // zero columns never rotate (their inner products vanish)
   for (long long g = blockIdx.x * (long long)WARPS + wid; g < ngroups; g += (long long)gridDim.x * WARPS) {
     const int f = (int)(g / N), k = (int)(g - (long long)f * N);
     if (k >= min(n_found[f], N)) continue;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_jacobi_wnnm(int n_img, int d,
     const int ja = 2 * lane, jb = 2 * lane + 1;
 #pragma unroll
     for (int r = 0; r < DMAX; ++r) {
-      a[r] = (live && r < d) ? Y[(long long)ja * d + r] : 0.f;
+      a[r] = (ja < K && r < d) ? Y[(long long)ja * d + r] : 0.f;
       b[r] = (live && jb < K && r < d) ? Y[(long long)jb * d + r] : 0.f;
     }
     // non-finite input: leave the group unchanged and flag it
@@ -127,32 +127,43 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_jacobi_wnnm(int n_img, int d,
     }
     int sweep = 0;
     bool converged = (m < 1);
+    // Parallel ordering by recursive halving (32 lanes, 64 column slots): at a
+    // level with lane groups of size g, the B columns shift cyclically inside
+    // each group for g rounds, so every A meets every B of its group; then each
+    // group of 2g lanes regroups into A-A pairs (first half) and B-B pairs
+    // (second half) for the next level.  Levels g = 32, 16, ..., 1 give
+    // 63 rounds covering all 2016 pairs; a shift costs one shuffle per element.
     while (!converged && sweep < max_sweeps) {
       bool rotated = false;
       // exact norms once per sweep; tracked through the rotations within it
       float alpha = sq_norm<DMAX>(a), beta = sq_norm<DMAX>(b);
-      for (int round = 0; round < 2 * m - 1; ++round) {
-        jacobi_pair<DMAX>(a, b, alpha, beta, tol, live, rotated);
-        if (m > 1) {
-          // circle rotation: slot top[0] stays; top[1] <- bot[0]; top[k] <- top[k-1];
-          // bot[m-1] <- top[m-1]; bot[k] <- bot[k+1]  (columns move with their norms)
+#pragma unroll 1
+      for (int g = 32; g >= 1; g >>= 1) {
+        if (g < 32) {
+          const bool first = (lane & g) == 0;
 #pragma unroll
           for (int r = 0; r < DMAX; ++r) {
-            const float up_src = (lane == 0) ? b[r] : a[r];
-            const float t_in = __shfl_up_sync(0xffffffffu, up_src, 1);
-            const float b_in = __shfl_down_sync(0xffffffffu, b[r], 1);
-            const float na = (lane == 0) ? a[r] : t_in;
-            const float nb = (lane == m - 1) ? a[r] : b_in;
-            a[r] = na;
-            b[r] = nb;
+            const float recv = __shfl_xor_sync(0xffffffffu, first ? b[r] : a[r], g);
+            if (first)
+              b[r] = recv;
+            else
+              a[r] = recv;
           }
-          const float up_n = (lane == 0) ? beta : alpha;
-          const float tn = __shfl_up_sync(0xffffffffu, up_n, 1);
-          const float bn = __shfl_down_sync(0xffffffffu, beta, 1);
-          const float nal = (lane == 0) ? alpha : tn;
-          const float nbe = (lane == m - 1) ? alpha : bn;
-          alpha = nal;
-          beta = nbe;
+          const float rn = __shfl_xor_sync(0xffffffffu, first ? beta : alpha, g);
+          if (first)
+            beta = rn;
+          else
+            alpha = rn;
+        }
+        const int src = (lane & ~(g - 1)) | ((lane + 1) & (g - 1));
+#pragma unroll 1
+        for (int rd = 0; rd < g; ++rd) {
+          jacobi_pair<DMAX>(a, b, alpha, beta, tol, live, rotated);
+          if (rd + 1 < g) {
+#pragma unroll
+            for (int r = 0; r < DMAX; ++r) b[r] = __shfl_sync(0xffffffffu, b[r], src);
+            beta = __shfl_sync(0xffffffffu, beta, src);
+          }
         }
       }
       ++sweep;

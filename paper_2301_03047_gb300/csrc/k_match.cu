@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256, 2)
     k_match_fp32(const float* __restrict__ x, const float* __restrict__ mean, const float* __restrict__ qn,
                  const float* __restrict__ keyv, const int32_t* __restrict__ n_found, int C, int H, int W, int Npad,
                  int splits, int tiles_per_split, StreamCfg cfg, uint2* __restrict__ bufs,
-                 int* __restrict__ buf_cnt) {
+                 int* __restrict__ buf_cnt, uint32_t* __restrict__ tau_gl, StatusBlock* st) {
   extern __shared__ __align__(16) float smem[];
   const int d = C * P * P;
   float* As = smem;                         // [d][FT]
@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(256, 2)
   float* Sc = strip + C * P * (FT + 8);     // [FT][SC_LD]
   float* pn = Sc + FT * SC_LD;              // [FT]
   unsigned* hist = reinterpret_cast<unsigned*>(pn + FT);  // [8][256]
+  uint32_t* tau_sh = hist + 8 * 256;                        // [FT] published thresholds of the tile's rows
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int kt = blockIdx.x, f = blockIdx.y, split = blockIdx.z;
   const int Hq = H - P + 1, Wq = W - P + 1;
@@ -128,6 +129,7 @@ __global__ void __launch_bounds__(256, 2)
     float s = 0.f;
     for (int e = 0; e < d; ++e) s = fmaf(As[e * FT + tid], As[e * FT + tid], s);
     pn[tid] = s;
+    tau_sh[tid] = 0xffffffffu;
   }
   // stream owned by this thread: row = 32 (wid % 4) + lane, column half h = wid / 4
   const int row = 32 * (wid & 3) + lane;
@@ -137,7 +139,10 @@ __global__ void __launch_bounds__(256, 2)
   uint2* mybuf = bufs + stream * (cfg.cap + 32);
   float tau = (key < nf) ? INFINITY : -INFINITY;
   int cnt = 0;
+  uint2 stats = make_uint2(0u, 0u);
   unsigned* whist = hist + wid * 256;
+  uint32_t* pub_sh = tau_sh + 32 * (wid & 3);
+  uint32_t* pub_gl = tau_gl + (long long)f * Npad + (long long)kt * FT + 32 * (wid & 3);
 
   const int ty = tid >> 4, tx = tid & 15;
   const int t_begin = split * tiles_per_split;
@@ -204,6 +209,7 @@ __global__ void __launch_bounds__(256, 2)
     __syncthreads();
     // row owners push their half row in two 32-column chunks
     const int qbase = r * Wq + c0;
+    const uint32_t gl = *reinterpret_cast<volatile uint32_t*>(pub_gl + lane);
 #pragma unroll 1
     for (int ch2 = 0; ch2 < 2; ++ch2) {
       const int col0 = h * 64 + ch2 * 32;
@@ -218,13 +224,15 @@ __global__ void __launch_bounds__(256, 2)
         s[4 * v + 2] = t4.z;
         s[4 * v + 3] = t4.w;
       }
-      const unsigned rows = stream_filter(s, nvalid, tau);
+      const float te = stream_tau_eff(tau, *reinterpret_cast<volatile uint32_t*>(pub_sh + lane), gl);
+      const unsigned rows = stream_filter(s, nvalid, te);
       if (rows)
-        stream_append(rows, Sc + (32 * (wid & 3)) * SC_LD + col0, SC_LD, qbase + col0, nvalid, tau, cnt, mybuf, cfg,
-                      whist);
+        stream_append(rows, Sc + (32 * (wid & 3)) * SC_LD + col0, SC_LD, qbase + col0, nvalid, te, tau, cnt, mybuf,
+                      cfg, whist, pub_sh, pub_gl, stats);
     }
   }
   stream_finish(tau, cnt, mybuf, cfg, whist);
+  stream_stats_flush(stats, st);
   buf_cnt[stream] = (key < nf) ? cnt : 0;
 }
 
@@ -247,7 +255,7 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
   const int d = C * P * P;
   const int Wq = W - P + 1;
   unsigned long long* list = rr_smem + (size_t)wid * pow2;
-  float* pv = reinterpret_cast<float*>(rr_smem + (size_t)RR_WARPS * pow2) + wid * 64 * 4;  // up to d = 256
+  float* pv = reinterpret_cast<float*>(rr_smem + (size_t)RR_WARPS * pow2) + wid * 512;  // key patch (d <= 256) + 256 counters
   const long long nkeys = (long long)n_img * N;
   for (long long gk = blockIdx.x * (long long)RR_WARPS + wid; gk < nkeys; gk += (long long)gridDim.x * RR_WARPS) {
     const int f = (int)(gk / N), k = (int)(gk - (long long)f * N);
@@ -268,9 +276,8 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
       for (int i = lane; i < n; i += 32) list[total + i] = b[i].y;
       total += n;
     }
-    for (int i = total + lane; i < pow2; i += 32) list[i] = ~0ull;
     __syncwarp();
-    // exact distances
+    // exact FP32 distances, summed in a fixed order over the vector index
     for (int i = lane; i < total; i += 32) {
       const int q = (int)list[i];
       const int r = q / Wq, c = q - (q / Wq) * Wq;
@@ -287,9 +294,81 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
       list[i] = ((unsigned long long)float_order_key(acc) << 32) | (unsigned)q;
     }
     __syncwarp();
-    for (int kk = 2; kk <= pow2; kk <<= 1) {
+    // select the K smallest (distance, id) pairs with an MSB radix select over the
+    // 64-bit keys, then sort those K (bitonic); ties in distance go to smaller ids
+    unsigned long long T = ~0ull;
+    if (total > K) {
+      unsigned* hist = reinterpret_cast<unsigned*>(pv + 256);  // 256 counters after the key patch
+      unsigned long long prefix = 0, pmask = 0;
+      int rank = K;  // 1-based rank of the wanted key among those matching the prefix
+      for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 56 - 8 * pass;
+        for (int i = lane; i < 256; i += 32) hist[i] = 0;
+        __syncwarp();
+        for (int i = lane; i < total; i += 32) {
+          const unsigned long long e = list[i];
+          if ((e & pmask) == prefix) atomicAdd(&hist[(e >> shift) & 255u], 1u);
+        }
+        __syncwarp();
+        int loc[8], sum = 0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          loc[t] = (int)hist[lane * 8 + t];
+          sum += loc[t];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int yv = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += yv;
+        }
+        const int excl = incl - sum;
+        const int owner = __ffs(__ballot_sync(0xffffffffu, excl < rank && rank <= incl)) - 1;
+        int sel = 0, before = 0;
+        if (lane == owner) {
+          int c = excl;
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            if (c + loc[t] >= rank) {
+              sel = lane * 8 + t;
+              before = c;
+              break;
+            }
+            c += loc[t];
+          }
+        }
+        sel = __shfl_sync(0xffffffffu, sel, owner);
+        before = __shfl_sync(0xffffffffu, before, owner);
+        rank -= before;
+        prefix |= (unsigned long long)sel << shift;
+        pmask |= 255ull << shift;
+        __syncwarp();
+      }
+      T = prefix;  // keys are unique (ids differ): exactly K entries are <= T
+    }
+    // compact the selected entries to the front, then sort them
+    {
+      int out = 0;
+      const unsigned ltm = (1u << lane) - 1u;
+      for (int base = 0; base < total; base += 32) {
+        const int i = base + lane;
+        const unsigned long long e = i < total ? list[i] : ~0ull;
+        const bool keep = i < total && e <= T;
+        const unsigned km = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (keep) list[out + __popc(km & ltm)] = e;
+        out += __popc(km);
+        __syncwarp();
+      }
+      total = out;
+    }
+    int p2 = 32;
+    while (p2 < total) p2 <<= 1;
+    for (int i = total + lane; i < p2; i += 32) list[i] = ~0ull;
+    __syncwarp();
+    for (int kk = 2; kk <= p2; kk <<= 1) {
       for (int j = kk >> 1; j > 0; j >>= 1) {
-        for (int i = lane; i < pow2; i += 32) {
+        for (int i = lane; i < p2; i += 32) {
           const int ixj = i ^ j;
           if (ixj > i) {
             const bool up = (i & kk) == 0;
@@ -318,9 +397,10 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   MatchPlan pl{};
   pl.mode = o ? o->mode : GLR_MATCH_FP32;
   pl.K = K;
-  pl.Kp = (o && o->k_over > 0) ? o->k_over : (pl.mode == GLR_MATCH_BF16 ? 2 * K : K + 16);
+  pl.Kp = (o && o->k_over > 0) ? o->k_over : K + 16;
   pl.Kp = std::max(pl.Kp, K);
-  pl.cap = std::min(std::max(4 * pl.Kp, 256), kStreamMaxEntries - 32);
+  // a small compaction trigger publishes a first threshold early; each compaction keeps ~Kp + (cap - Kp) / 4
+  pl.cap = (o && o->cap > 0) ? o->cap : std::min(std::max(2 * pl.Kp + 64, 256), kStreamMaxEntries - 32);
   pl.cap = (int)(pl.cap / 32) * 32;
   pl.subs = 2;
   pl.key_tile = FT;
@@ -334,7 +414,9 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
     pl.pos_tile = FT;
     pl.pos_tiles = Hq * (int)ceil_div(Wq, FT);
   }
-  int splits = (o && o->splits > 0) ? o->splits : (int)ceil_div(4 * 152, (long long)ktiles * im.n_img);
+  // fewer splits mean fewer streams per key (less re-rank work and threshold learning):
+  // split the positions only when key tiles alone would leave SMs idle
+  int splits = (o && o->splits > 0) ? o->splits : (int)ceil_div(152, (long long)ktiles * im.n_img);
   // the exact re-rank holds every stream's candidates of one key in shared memory
   const int max_splits = std::max(1, kRerankMaxList / (pl.subs * pl.Kp));
   splits = std::max(1, std::min({splits, pl.pos_tiles, max_splits}));
@@ -350,6 +432,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   const long long nstreams = (long long)im.n_img * pl.Npad * pl.streams_per_key;
   pl.buf_off = L.take((size_t)nstreams * (pl.cap + 32) * 8);
   pl.bufcnt_off = L.take((size_t)nstreams * 4);
+  pl.taugl_off = L.take((size_t)im.n_img * pl.Npad * 4);
   if (pl.mode == GLR_MATCH_BF16) {
     // BF16 operands: positions [img][npos_pad][dk] and keys [img][Npad][dk], dk = d + 16 (norm columns)
     const int dk = 64 + 16;  // patch columns padded to 64, plus the norm columns
@@ -373,6 +456,8 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
   uint2* bufs = reinterpret_cast<uint2*>(ws + pl.buf_off);
   int* bufcnt = reinterpret_cast<int*>(ws + pl.bufcnt_off);
   const long long HW = (long long)im.H * im.W;
+  uint32_t* taugl = reinterpret_cast<uint32_t*>(ws + pl.taugl_off);
+  if (cudaMemsetAsync(taugl, 0xff, (size_t)im.n_img * pl.Npad * 4, s) != cudaSuccess) return GLR_ECUDA;
   GLR_LAUNCH("k_image_mean", s, k_image_mean<<<im.n_img, 256, 0, s>>>(x, (long long)im.C * HW, mean));
   {
     const long long total = (long long)im.n_img * npos;
@@ -390,7 +475,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     const glr_status st = launch_match_tc(x, im, keys, n_found, N, pl, ws, s);
     if (st != GLR_OK) return st;
   } else {
-    const size_t smem = (size_t)(d * FT + im.C * im.P * (FT + 8) + FT * SC_LD + FT) * 4 + 8 * 256 * 4;
+    const size_t smem = (size_t)(d * FT + im.C * im.P * (FT + 8) + FT * SC_LD + FT) * 4 + 8 * 256 * 4 + FT * 4;
     if (smem > 227 * 1024) return GLR_ENOTSUP;
     dim3 grid((unsigned)(pl.Npad / FT), (unsigned)im.n_img, (unsigned)pl.splits);
 #define GLR_FP32_CASE(PP)                                                                                    \
@@ -400,7 +485,8 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
       return GLR_ECUDA;                                                                                      \
     GLR_LAUNCH("k_match_fp32", s,                                                                           \
                k_match_fp32<PP><<<grid, 256, smem, s>>>(x, mean, qn, keyv, n_found, im.C, im.H, im.W, pl.Npad,  \
-                                                        pl.splits, pl.tiles_per_split, cfg, bufs, bufcnt));     \
+                                                        pl.splits, pl.tiles_per_split, cfg, bufs, bufcnt, taugl,   \
+                                                        reinterpret_cast<StatusBlock*>(ws)));                      \
   } break;
     switch (im.P) {
       GLR_FP32_CASE(2)
@@ -418,7 +504,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
   {
     int pow2 = 32;
     while (pow2 < pl.streams_per_key * pl.Kp) pow2 <<= 1;
-    const size_t smem = (size_t)RR_WARPS * pow2 * 8 + (size_t)RR_WARPS * 256 * 4;
+    const size_t smem = (size_t)RR_WARPS * pow2 * 8 + (size_t)RR_WARPS * 512 * 4;
     if (smem > 227 * 1024 || d > 256) return GLR_ENOTSUP;
     if (cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return GLR_ECUDA;

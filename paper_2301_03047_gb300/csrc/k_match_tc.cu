@@ -56,7 +56,8 @@ constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;                  // tmem base,
 constexpr uint32_t OFF_HIST = (OFF_MISC + 64 + 15) / 16 * 16;
 constexpr int TILE_LD = 33;  // per-warp 32 x 32 score tile for the row-wise append
 constexpr uint32_t OFF_TILE = OFF_HIST + TC_EPI_WARPS * 256 * 4;
-constexpr uint32_t TC_SMEM = OFF_TILE + TC_EPI_WARPS * 32 * TILE_LD * 4 + 1024;  // + alignment slack
+constexpr uint32_t OFF_TAU = OFF_TILE + TC_EPI_WARPS * 32 * TILE_LD * 4;  // published thresholds of the 128 rows
+constexpr uint32_t TC_SMEM = OFF_TAU + TC_M * 4 + 1024;                   // + alignment slack
 static_assert(TC_SMEM <= 232448, "shared memory budget");
 constexpr unsigned long long kWaitNs = 1000000000ull;                   // 1 s
 
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                const __grid_constant__ CUtensorMap tm_kmain, const __grid_constant__ CUtensorMap tm_kaux,
                const int32_t* __restrict__ n_found, int Npad, long long npos, long long npos_pad, int splits,
                int tiles_per_split, int ntiles, StreamCfg cfg, uint2* __restrict__ bufs, int* __restrict__ buf_cnt,
-               StatusBlock* st, float* __restrict__ dump) {
+               uint32_t* __restrict__ tau_gl, StatusBlock* st, float* __restrict__ dump) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
@@ -272,6 +273,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   volatile int* abort_s = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
   unsigned* hist = reinterpret_cast<unsigned*>(smem + OFF_HIST);
   float* tiles = reinterpret_cast<float*>(smem + OFF_TILE);
+  uint32_t* tau_sh = reinterpret_cast<uint32_t*>(smem + OFF_TAU);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kt = blockIdx.x, f = blockIdx.y, split = blockIdx.z;
@@ -291,6 +293,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     mbar_init(a_full, 1);
     mbar_init(mma_done, 1);
     *abort_s = 0;
+    for (int i = 0; i < TC_M; ++i) tau_sh[i] = 0xffffffffu;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -367,8 +370,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint2* mybuf = bufs + stream * (cfg.cap + 32);
     float tau = (key < nf) ? INFINITY : -INFINITY;
     int cnt = 0;
+    uint32_t gl_next = 0xffffffffu;  // published bound of other CTAs, loaded one tile ahead
+    uint2 stats = make_uint2(0u, 0u);
     unsigned* whist = hist + e * 256;
     float* wtile = tiles + e * 32 * TILE_LD;
+    uint32_t* pub_sh = tau_sh + 32 * quad;
+    uint32_t* pub_gl = tau_gl + (long long)f * Npad + (long long)kt * TC_M + 32 * quad;
     for (int i = 0; i < nt; ++i) {
       const int b = i & 1;
       const uint32_t bph = (uint32_t)(i >> 1) & 1u;
@@ -376,6 +383,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) break;
       tc_fence_after();
       const long long tile_q0 = (long long)(t_begin + i) * TC_N;
+      const uint32_t gl = gl_next;
+      gl_next = *reinterpret_cast<volatile uint32_t*>(pub_gl + lane);
       float v[4][32];
       {
         const uint32_t taddr = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128);
@@ -398,16 +407,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) dump[((long long)f * Npad + key) * TC_N + col + j] = v[c][j];
         }
-        const unsigned rows = stream_filter(v[c], nvalid, tau);
+        const float te = stream_tau_eff(tau, *reinterpret_cast<volatile uint32_t*>(pub_sh + lane), gl);
+        const unsigned rows = stream_filter(v[c], nvalid, te);
         if (rows) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) wtile[lane * TILE_LD + j] = v[c][j];
           __syncwarp();
-          stream_append(rows, wtile, TILE_LD, (int)q0, nvalid, tau, cnt, mybuf, cfg, whist);
+          stream_append(rows, wtile, TILE_LD, (int)q0, nvalid, te, tau, cnt, mybuf, cfg, whist, pub_sh, pub_gl, stats);
         }
       }
     }
     stream_finish(tau, cnt, mybuf, cfg, whist);
+    stream_stats_flush(stats, st);
     buf_cnt[stream] = (key < nf) ? cnt : 0;
   }
   tc_fence_before();
@@ -459,6 +470,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   const float* keyv = reinterpret_cast<const float*>(ws + pl.keyv_off);
   uint2* bufs = reinterpret_cast<uint2*>(ws + pl.buf_off);
   int* bufcnt = reinterpret_cast<int*>(ws + pl.bufcnt_off);
+  uint32_t* taugl = reinterpret_cast<uint32_t*>(ws + pl.taugl_off);
   StatusBlock* st = reinterpret_cast<StatusBlock*>(ws);
   __nv_bfloat16* qmain = reinterpret_cast<__nv_bfloat16*>(ws + pl.qpack_off);
   __nv_bfloat16* qaux = qmain + (size_t)im.n_img * pl.npos_pad * DK_MAIN;
@@ -491,7 +503,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   GLR_LAUNCH("k_match_tc", s,
              k_match_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
                                                           pl.splits, pl.tiles_per_split, pl.pos_tiles, cfg, bufs,
-                                                          bufcnt, st, dump));
+                                                          bufcnt, taugl, st, dump));
   return GLR_OK;
 }
 

@@ -18,6 +18,14 @@
 // smallest (score, id) pairs of the stream.  At the end of the stream an
 // exact compaction leaves exactly the K' smallest, ties by smaller id
 // (entries are appended in increasing id order).
+//
+// Several streams serve one key (column halves of a tile, position splits).
+// A compaction that leaves at least K' entries strictly below a value v
+// publishes v (atomic min, in shared memory for the streams of one CTA and in
+// global memory across CTAs): at least K' scores of the key lie below v, so
+// no score >= v can be among its K' smallest, and every stream of the key
+// filters against min(own threshold, published value).  The union of the
+// streams of a key therefore still contains its K' smallest scores.
 #pragma once
 
 #include "glr_common.cuh"
@@ -119,83 +127,119 @@ static __device__ __noinline__ int compact_exact(uint2* b, int n, int kp, unsign
   return out;
 }
 
-// Mid-stream: drop every entry at or above a pivot that leaves between kp and
-// cap - 32 entries; falls back to the exact selection.  Warp-collective.
-static __device__ __noinline__ int compact_pivot(uint2* b, int n, int kp, int cap, unsigned* hist, float* tau) {
+// Mid-stream compaction of b[0..n) (warp-collective).  Entries >= te_key (the
+// effective threshold) are dropped first; if that is not enough, a pivot from
+// 32 sorted samples that leaves between kp and cap - 32 entries strictly
+// below it becomes the new threshold, else the exact kp-th smallest.
+// Returns the new count; *tau_own gets the stream's new threshold and
+// *pub the value to publish (0xffffffff = nothing).
+static __device__ __noinline__ int compact_mid(uint2* b, int n, int kp, int cap, uint32_t te_key, unsigned* hist,
+                                               float* tau_own, uint32_t* pub) {
   const int lane = threadIdx.x & 31;
-  // 32 samples spread over the buffer, sorted across the warp (bitonic, ascending)
-  uint32_t smp = b[(int)(((long long)lane * n) >> 5)].x;
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const uint32_t o = __shfl_xor_sync(0xffffffffu, smp, j);
-      const bool up = ((lane & k) == 0);
-      const bool lower = ((lane & j) == 0);
-      smp = (lower == up) ? min(smp, o) : max(smp, o);
-    }
-  }
-  const int target = kp + (cap - kp) / 4;
-  const int pidx = min(31, max(0, (int)(((long long)target * 32) / n)));
-  const uint32_t pivot = __shfl_sync(0xffffffffu, smp, pidx);
+  const unsigned lt_mask = lanemask_lt();
   uint2 e[kStreamSlots];
-  int below = 0;
+  int below_te = 0;
 #pragma unroll
   for (int i = 0; i < kStreamSlots; ++i) {
     const int j = lane + 32 * i;
     e[i] = (j < n) ? b[j] : make_uint2(0xffffffffu, 0u);
-    below += (j < n && e[i].x < pivot) ? 1 : 0;
+    below_te += (j < n && e[i].x < te_key) ? 1 : 0;
   }
-  below = __reduce_add_sync(0xffffffffu, below);
-  if (below < kp || below > cap - 32) {
-    uint32_t T;
-    const int out = compact_exact(b, n, kp, hist, &T);
-    *tau = float_from_order_key(T);
-    return out;
+  below_te = __reduce_add_sync(0xffffffffu, below_te);
+  uint32_t cut = te_key;
+  *pub = 0xffffffffu;
+  if (below_te > (cap + kp) / 2) {
+    // 32 samples spread over the buffer, sorted across the warp (bitonic, ascending)
+    uint32_t smp = b[(int)(((long long)lane * n) >> 5)].x;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const uint32_t o = __shfl_xor_sync(0xffffffffu, smp, j);
+        const bool up = ((lane & k) == 0);
+        const bool lower = ((lane & j) == 0);
+        smp = (lower == up) ? min(smp, o) : max(smp, o);
+      }
+    }
+    const int target = kp + (cap - kp) / 4;
+    const int pidx = min(31, max(0, (int)(((long long)target * 32) / n)));
+    const uint32_t pivot = min(__shfl_sync(0xffffffffu, smp, pidx), te_key);
+    int below = 0;
+#pragma unroll
+    for (int i = 0; i < kStreamSlots; ++i) below += (lane + 32 * i < n && e[i].x < pivot) ? 1 : 0;
+    below = __reduce_add_sync(0xffffffffu, below);
+    if (below < kp || below > cap - 32) {
+      uint32_t T;
+      const int out = compact_exact(b, n, kp, hist, &T);
+      *tau_own = float_from_order_key(T);
+      *pub = T + 1u;  // the kp kept entries are <= T: at least kp scores lie strictly below T + 1
+      return out;
+    }
+    cut = pivot;
+    *pub = pivot;
+    *tau_own = float_from_order_key(pivot);
   }
   int out = 0;
-  const unsigned lt_mask = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < kStreamSlots; ++i) {
     const int j = lane + 32 * i;
-    const bool keep = (j < n) && e[i].x < pivot;
+    const bool keep = (j < n) && e[i].x < cut;
     const unsigned km = __ballot_sync(0xffffffffu, keep);
     if (keep) b[out + __popc(km & lt_mask)] = e[i];
     out += __popc(km);
   }
   __syncwarp();
-  *tau = float_from_order_key(pivot);
   return out;
+}
+
+// Per-warp counters (appends, compactions) go to the status block once per stream.
+__device__ __forceinline__ void stream_stats_flush(const uint2& stats, StatusBlock* st) {
+  if ((threadIdx.x & 31) == 0 && st != nullptr) {
+    atomicAdd(&st->cand_appends, (unsigned long long)stats.x);
+    atomicAdd(&st->compactions, (unsigned long long)stats.y);
+  }
+}
+
+// Effective threshold of this lane's row: own threshold and the published bounds.
+__device__ __forceinline__ float stream_tau_eff(float tau_own, uint32_t pub_shared, uint32_t pub_global) {
+  return fminf(tau_own, float_from_order_key(min(pub_shared, pub_global)));  // 0xffffffff decodes to NaN: ignored
 }
 
 // Step 1 of a chunk push: rows (bit r = lane r) whose 32 scores contain one
 // below their tau.  s = this lane's row scores, column j = position q0 + j;
 // columns j >= nvalid do not exist.
 __device__ __forceinline__ unsigned stream_filter(const float (&s)[32], int nvalid, float tau) {
-  float m = s[0];
+  // tree-shaped minimum: depth 5 instead of a 31-long dependency chain
+  float m[16];
   if (nvalid < 32) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) m = fminf(m, j < nvalid ? s[j] : INFINITY);
-    if (nvalid <= 0) m = INFINITY;
+    for (int j = 0; j < 16; ++j)
+      m[j] = fminf(j < nvalid ? s[j] : INFINITY, j + 16 < nvalid ? s[j + 16] : INFINITY);
   } else {
 #pragma unroll
-    for (int j = 1; j < 32; ++j) m = fminf(m, s[j]);
+    for (int j = 0; j < 16; ++j) m[j] = fminf(s[j], s[j + 16]);
   }
-  return __ballot_sync(0xffffffffu, m < tau);
+#pragma unroll
+  for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+    for (int j = 0; j < w; ++j) m[j] = fminf(m[j], m[j + w]);
+  return __ballot_sync(0xffffffffu, m[0] < tau);
 }
 
 // Step 2: append the candidates of the selected rows.  tile holds the same
 // 32 x 32 scores in shared memory, row r at tile + r * ld (lane = column).
-// tau / cnt / row_buf belong to this lane's row.
-__device__ __forceinline__ void stream_append(unsigned rows, const float* tile, int ld, int q0, int nvalid,
+// te = effective threshold of this lane's row; tau / cnt / row_buf are its
+// own state; pub_sh / pub_gl point at the published bounds of the warp's
+// row 0 (row r at + r).
+__device__ __forceinline__ void stream_append(unsigned rows, const float* tile, int ld, int q0, int nvalid, float te,
                                               float& tau, int& cnt, uint2* row_buf, const StreamCfg& cfg,
-                                              unsigned* hist) {
+                                              unsigned* hist, uint32_t* pub_sh, uint32_t* pub_gl, uint2& stats) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = lanemask_lt();
   while (rows) {
     const int r = __ffs(rows) - 1;
     rows &= rows - 1;
-    const float t_r = __shfl_sync(0xffffffffu, tau, r);
+    const float t_r = __shfl_sync(0xffffffffu, te, r);
     int c_r = __shfl_sync(0xffffffffu, cnt, r);
     uint2* b_r = reinterpret_cast<uint2*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(row_buf), r));
     const float v = tile[r * ld + lane];
@@ -203,15 +247,22 @@ __device__ __forceinline__ void stream_append(unsigned rows, const float* tile, 
     const unsigned bal = __ballot_sync(0xffffffffu, c);
     if (c) b_r[c_r + __popc(bal & lt_mask)] = make_uint2(float_order_key(v), (unsigned)(q0 + lane));
     c_r += __popc(bal);
-    float nt = t_r;
+    stats.x += __popc(bal);
     if (c_r > cfg.cap) {
       __syncwarp();
-      c_r = compact_pivot(b_r, c_r, cfg.kp, cfg.cap, hist, &nt);
+      float own = __shfl_sync(0xffffffffu, tau, r);
+      stats.y += 1;
+      uint32_t pub;
+      c_r = compact_mid(b_r, c_r, cfg.kp, cfg.cap, float_order_key(t_r), hist, &own, &pub);
+      if (lane == r) {
+        tau = own;
+        if (pub != 0xffffffffu) {
+          atomicMin(pub_sh + r, pub);
+          atomicMin(pub_gl + r, pub);
+        }
+      }
     }
-    if (lane == r) {
-      cnt = c_r;
-      tau = nt;
-    }
+    if (lane == r) cnt = c_r;
   }
   __syncwarp();
 }

@@ -50,10 +50,10 @@ def images_of(x: torch.Tensor, P: int) -> L.GlrImages:
     return images(n, C, H, W, P)
 
 
-def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0) -> L.GlrMatchOpts:
+def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0, cap: int = 0) -> L.GlrMatchOpts:
     m = {"fp32": L.GLR_MATCH_FP32, "bf16": L.GLR_MATCH_BF16}.get(mode, mode)
     o = L.GlrMatchOpts()
-    o.mode, o.k_over, o.splits = int(m), int(k_over), int(splits)
+    o.mode, o.k_over, o.splits, o.cap = int(m), int(k_over), int(splits), int(cap)
     return o
 
 
@@ -95,13 +95,13 @@ def select_keys(x, P, N, edge_th=0.1, *, keys=None, n_found=None, n_corner=None,
     return keys, n_found, n_corner
 
 
-def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, idx=None, dist=None, ws=None,
+def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, cap=0, idx=None, dist=None, ws=None,
                stream=None):
     """Global matching with a fused running top-K (Eq. 1 over the whole image, Eq. 4 as a contraction)."""
     lib = L.load()
     im = images_of(x, P)
     N = keys.shape[1]
-    o = match_opts(mode, k_over, splits)
+    o = match_opts(mode, k_over, splits, cap)
     dev = x.device
     if idx is None:
         idx = torch.empty((x.shape[0], N, K), dtype=torch.int32, device=dev)
@@ -184,11 +184,11 @@ def gap_step(y, masks, v=None, *, accelerate=False, y_acc=None, out=None, stream
 
 
 def poll_status(ws, reset=False, stream=None):
-    """(bits, [cand_overflow, svd_noconv, sweeps, groups]) of the last call that used ws."""
+    """(bits, [cand_overflow, svd_noconv, sweeps, groups, cand_appends, compactions]) of the last call that used ws."""
     lib = L.load()
     wp, _ = _ws(ws)
     bits = ctypes.c_uint32(0)
-    cnt = (ctypes.c_uint32 * 4)()
+    cnt = (ctypes.c_uint32 * 6)()
     code = lib.glr_poll_status(wp, ctypes.byref(bits), cnt, 1 if reset else 0, _stream(stream))
     if code not in (L.GLR_OK, L.GLR_EDEVICE):
         raise GlrError("glr_poll_status", code)
