@@ -50,7 +50,8 @@ enum {
   GLR_ENOMEM = 3,    /* the workspace is smaller than glr_workspace_size() */
   GLR_ETIMEDOUT = 4, /* a bounded device-side wait expired (status bit set) */
   GLR_ENOTSUP = 5,   /* the shape / mode is valid but not supported by this build */
-  GLR_EDEVICE = 6    /* a device-side error bit is set in the status block */
+  GLR_EDEVICE = 6,   /* a device-side error bit is set in the status block */
+  GLR_ETOOBIG = 7    /* the problem needs more scratch than glr_aggregate_noalloc reserves */
 };
 
 /* Status-block bits (glr_poll_status, `bits`). */
@@ -177,6 +178,28 @@ glr_status glr_lowrank_groups(const float* x, const glr_images* im, const int32_
 glr_status glr_aggregate(const float* groups, const int32_t* idx, const int32_t* n_found,
                          const glr_images* im, int32_t N, int32_t K, const float* x_in,
                          float* v_out, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * glr_aggregate without a workspace argument: the same computation and
+ * arguments as glr_aggregate, for callers that cannot allocate device memory
+ * (a plug-in inside a framework or server that owns all device allocations
+ * and forbids cudaMalloc on its request path, or a real-time loop with a fixed
+ * memory budget and no workspace to hand in).  The paper has no counterpart;
+ * this is a deployment convenience.
+ *
+ * Scratch comes from a 16 MiB array in device memory that the library
+ * reserves on every GPU that loads it, until the process exits.  Problems whose
+ * scratch (256 + n_img*C*H*W*4 + n_img*Hq*Wq*4 bytes, each part rounded up to
+ * 256) exceeds it return GLR_ETOOBIG without launching.  All calls share the
+ * array and leave their contents in it (each call clears what must start at
+ * zero); calls that overlap on the GPU race on it, so serialise them.  The
+ * first call on a device looks the array's address up with that device
+ * current and caches it: make that call before any stream capture.  Nothing
+ * is allocated or freed.
+ */
+glr_status glr_aggregate_noalloc(const float* groups, const int32_t* idx, const int32_t* n_found,
+                                 const glr_images* im, int32_t N, int32_t K, const float* x_in,
+                                 float* v_out, void* stream);
 
 /*
  * GAP projection for y = sum_t A_t x_t (Eq. 6 for video SCI; Eq. 8 for an

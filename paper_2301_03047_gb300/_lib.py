@@ -14,7 +14,7 @@ c_float = ctypes.c_float
 c_void_p = ctypes.c_void_p
 c_uint32_p = ctypes.POINTER(ctypes.c_uint32)
 
-GLR_OK, GLR_EINVAL, GLR_ECUDA, GLR_ENOMEM, GLR_ETIMEDOUT, GLR_ENOTSUP, GLR_EDEVICE = range(7)
+GLR_OK, GLR_EINVAL, GLR_ECUDA, GLR_ENOMEM, GLR_ETIMEDOUT, GLR_ENOTSUP, GLR_EDEVICE, GLR_ETOOBIG = range(8)
 GLR_DEV_TIMEOUT, GLR_DEV_NONFINITE, GLR_DEV_SVD_NOCONV, GLR_DEV_CAND_OVERFLOW, GLR_DEV_BAD_INDEX = 1, 2, 4, 8, 16
 GLR_MATCH_FP32, GLR_MATCH_BF16 = 0, 1
 GLR_OP_SELECT, GLR_OP_MATCH, GLR_OP_LOWRANK, GLR_OP_AGGREGATE = 1, 2, 3, 4
@@ -36,6 +36,7 @@ PROTOTYPES = {
     "glr_debug_match_scores": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_lowrank_groups": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_aggregate": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(GlrImages), c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "glr_aggregate_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(GlrImages), c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "glr_gap_step": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "glr_poll_status": (c_int32, [c_void_p, c_uint32_p, c_uint32_p, c_int32, c_void_p]),
     "glr_status_string": (ctypes.c_char_p, [c_int32]),

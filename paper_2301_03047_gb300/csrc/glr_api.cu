@@ -75,6 +75,7 @@ const char* glr_status_string(glr_status s) {
     case GLR_ETIMEDOUT: return "GLR_ETIMEDOUT: bounded device wait expired";
     case GLR_ENOTSUP: return "GLR_ENOTSUP: shape or mode not supported by this build";
     case GLR_EDEVICE: return "GLR_EDEVICE: device-side error flag set";
+    case GLR_ETOOBIG: return "GLR_ETOOBIG: problem exceeds the 16 MiB scratch of the no-allocation entry point";
     default: return "GLR_?: unknown status";
   }
 }
