@@ -312,9 +312,16 @@ def run_glr(args) -> None:
     sweeps = 0.0
     stream_stats = None
     launches = 0
+    tuned = {}
     for form in forms:
+        # autotune the matching schedule on the start image (set-up, untimed)
+        x0 = glr.gap_step(y[None], masks, None).view(cfg.T, 1, cfg.H, cfg.W).contiguous()
+        k0, n0, _ = glr.select_keys(x0, cfg.P, cfg.N, cfg.edge_th)
+        tuned[form] = glr.autotune_match(x0, cfg.P, k0, n0, cfg.K, form) if not args.no_tune else (0, 0, 0)
+        del x0, k0, n0
+        kover, splits, cap = tuned[form]
         rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=form, edge_th=cfg.edge_th,
-                                   device=dev)
+                                   device=dev, k_over=kover, splits=splits, cap=cap)
         rec.start(y, masks)
         k = 0
         for _ in range(args.warmup):
@@ -359,6 +366,25 @@ def run_glr(args) -> None:
         x = rec.x.cpu().numpy()[0]
         results[form] = {"total_s": total_s, "ms_per_step": total_s / args.steps * 1e3, "step_ms": step_ms,
                          "psnr": O.psnr_framewise(x, prob.truth), "iters": k}
+        if headline and not args.no_graph:
+            # the same iterations replayed from CUDA graphs (one per noise level)
+            rec.capture(sched, cfg.c_wnnm)
+            for i in range(args.warmup):
+                rec.step_graph(sched[(k + i) % len(sched)])
+            k += args.warmup
+            gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            for i in range(args.steps):
+                flush.zero_()
+                gev[i][0].record()
+                rec.step_graph(sched[k % len(sched)])
+                gev[i][1].record()
+                k += 1
+            torch.cuda.synchronize()
+            g_s = reduce_max(sum(a.elapsed_time(b) for a, b in gev) / 1e3, dist, dev)
+            results["graph"] = {"ms_per_step": g_s / args.steps * 1e3, "value": ws * args.steps / g_s}
         del rec
         torch.cuda.empty_cache()
 
@@ -438,6 +464,10 @@ def run_glr(args) -> None:
         "e2e": e2e,
         "clocks": clocks_summary,
     }
+    line["autotuned_match"] = {f: {"k_over": t[0], "splits": t[1], "cap": t[2]} for f, t in tuned.items()}
+    if "graph" in results:
+        line["cuda_graph"] = {"value": round(results["graph"]["value"], 4), "unit": UNIT,
+                              "ms_per_step": round(results["graph"]["ms_per_step"], 3)}
     if len(forms) > 1:
         pl = results["fp32"]
         line["plain"] = {"value": round(ws * args.steps / pl["total_s"], 4), "unit": UNIT,
@@ -505,6 +535,8 @@ def main() -> None:
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "glr":
         args.warmup = 3

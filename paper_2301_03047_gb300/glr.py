@@ -238,11 +238,11 @@ class GlrDenoiser:
     """Select -> match -> low-rank -> aggregate on fixed-size images, with preallocated buffers."""
 
     def __init__(self, shape: GlrShape, mode: str = "bf16", edge_th: float = 0.1, k_over: int = 0, splits: int = 0,
-                 device="cuda"):
+                 device="cuda", cap: int = 0):
         s = shape
         self.shape, self.mode, self.edge_th = s, mode, edge_th
-        self.opts = match_opts(mode, k_over, splits)
-        self.k_over, self.splits = k_over, splits
+        self.opts = match_opts(mode, k_over, splits, cap)
+        self.k_over, self.splits, self.cap = k_over, splits, cap
         im = images(s.n_img, s.C, s.H, s.W, s.P)
         dev = torch.device(device)
         d = s.C * s.P * s.P
@@ -264,7 +264,7 @@ class GlrDenoiser:
         select_keys(x, s.P, s.N, self.edge_th, keys=self.keys, n_found=self.n_found, n_corner=self.n_corner,
                     ws=self.ws_select, stream=stream)
         match_topk(x, s.P, self.keys, self.n_found, s.K, self.mode, k_over=self.k_over, splits=self.splits,
-                   idx=self.idx, dist=self.dist, ws=self.ws_match, stream=stream)
+                   cap=self.cap, idx=self.idx, dist=self.dist, ws=self.ws_match, stream=stream)
         lowrank_groups(x, s.P, self.idx, self.n_found, sigma_w, c_wnnm, groups=self.groups, rank=self.rank,
                        ws=self.ws_lowrank, stream=stream)
         return aggregate(self.groups, self.idx, self.n_found, x, s.P, out=out, ws=self.ws_agg, stream=stream)
@@ -274,9 +274,9 @@ class SciReconstructor:
     """GAP + GLR for one video snapshot y = sum_t M_t x_t (Eq. 6); frames are the images."""
 
     def __init__(self, T, H, W, P, N, K, mode="bf16", edge_th=0.1, accelerate=False, k_over=0, splits=0,
-                 device="cuda"):
+                 device="cuda", cap=0):
         self.T, self.H, self.W = T, H, W
-        self.den = GlrDenoiser(GlrShape(T, 1, H, W, P, N, K), mode, edge_th, k_over, splits, device)
+        self.den = GlrDenoiser(GlrShape(T, 1, H, W, P, N, K), mode, edge_th, k_over, splits, device, cap)
         self.accelerate = accelerate
         self.x = torch.empty((1, T, H, W), dtype=torch.float32, device=device)
         self.v = torch.empty_like(self.x)
@@ -297,3 +297,81 @@ class SciReconstructor:
         gap_step(self.y, self.masks, self.v, accelerate=self.accelerate, y_acc=self.y_acc if self.accelerate else None,
                  out=self.x, stream=stream)
         return self.x
+
+    def capture(self, sigmas, c_wnnm: float) -> None:
+        """Record one CUDA graph per distinct noise level of the schedule.
+
+        A captured step reads and writes the reconstructor's own buffers, so
+        replaying graph k advances the reconstruction exactly like step(); the
+        current state of x is not modified by the capture itself.
+        """
+        saved = self.x.clone()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):  # library set-up happens outside the capture
+            self.step(float(sigmas[0]), c_wnnm)
+        torch.cuda.current_stream().wait_stream(side)
+        self._graphs = {}
+        for sw in sigmas:
+            key = float(sw)
+            if key in self._graphs:
+                continue
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self.step(key, c_wnnm)
+            self._graphs[key] = g
+        torch.cuda.synchronize()
+        self.x.copy_(saved)
+
+    def step_graph(self, sigma_w: float) -> torch.Tensor:
+        """One GAP iteration by replaying the graph captured for this noise level."""
+        self._graphs[float(sigma_w)].replay()
+        return self.x
+
+
+# ---------------------------------------------------------------------------
+# Autotuner for the matching schedule (position splits, compaction trigger,
+# candidates kept per stream).  Tile shapes are fixed at compile time; these
+# are the run-time knobs.  Each candidate is timed with the library's per-kernel
+# events on the caller's data; results are cached per problem shape.
+# ---------------------------------------------------------------------------
+_TUNE_CACHE: dict = {}
+
+
+def autotune_match(x, P, keys, n_found, K, mode="bf16", candidates=None, repeats=2, cache_path=None):
+    """Return the fastest (k_over, splits, cap) for this shape; K' stays >= K + 16."""
+    import json
+    import os
+
+    shape_key = f"{mode}:{tuple(x.shape)}:P{P}:N{keys.shape[1]}:K{K}"
+    if cache_path and os.path.exists(cache_path) and not _TUNE_CACHE:
+        _TUNE_CACHE.update(json.load(open(cache_path)))
+    if shape_key in _TUNE_CACHE:
+        return tuple(_TUNE_CACHE[shape_key])
+    if candidates is None:
+        candidates = [(K + 16, sp, cap) for sp in (1, 2, 3) for cap in (0, 192, 320)]
+    im = images_of(x, P)
+    best, best_t = None, float("inf")
+    kname = "k_match_tc" if mode == "bf16" else "k_match_fp32"
+    for kover, sp, cap in candidates:
+        o = match_opts(mode, kover, sp, cap)
+        try:
+            ws = workspace(L.GLR_OP_MATCH, im, keys.shape[1], K, o, x.device)
+            match_topk(x, P, keys, n_found, K, mode, k_over=kover, splits=sp, cap=cap, ws=ws)
+        except GlrError:
+            continue
+        torch.cuda.synchronize()
+        profile_enable(True)
+        profile_collect()
+        for _ in range(repeats):
+            match_topk(x, P, keys, n_found, K, mode, k_over=kover, splits=sp, cap=cap, ws=ws)
+        prof = profile_collect()
+        profile_enable(False)
+        t = sum(v[0] for k, v in prof.items() if k in (kname, "k_rerank"))
+        if t < best_t:
+            best, best_t = (kover, sp, cap), t
+        del ws
+    _TUNE_CACHE[shape_key] = list(best)
+    if cache_path:
+        json.dump(_TUNE_CACHE, open(cache_path, "w"), indent=1)
+    return best

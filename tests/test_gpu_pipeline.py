@@ -1,0 +1,68 @@
+"""End-to-end GLR iterations on the GPU: CUDA-graph replay, the autotuner, and the
+whole reconstruction against the oracle step by step (teacher forcing)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import glr_oracle as O  # noqa: E402
+from paper_2301_03047_gb300 import glr, synth  # noqa: E402
+
+
+def _problem(T=4, H=96, W=100, N=80, K=24):
+    cfg = synth.scaled(synth.SCI_SMALL, T=T, H=H, W=W, N=N, K=K, iters=3)
+    prob = synth.sci_problem(cfg)
+    return cfg, prob, torch.from_numpy(prob.y).cuda(), torch.from_numpy(prob.masks).cuda()
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+def test_graph_replay_matches_eager(mode):
+    cfg, prob, y, m = _problem()
+    sig = cfg.sigma_schedule()
+    a = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=mode)
+    b = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=mode)
+    a.start(y, m)
+    b.start(y, m)
+    b.capture(sig, cfg.c_wnnm)
+    for s in sig:
+        a.step(s, cfg.c_wnnm)
+        b.step_graph(s)
+    torch.cuda.synchronize()
+    # the only non-associative step is the FP32 atomic accumulation of the aggregation
+    np.testing.assert_allclose(b.x.cpu().numpy(), a.x.cpu().numpy(), rtol=1e-4, atol=1e-4)
+
+
+def test_autotune_picks_a_working_schedule():
+    cfg, prob, y, m = _problem(T=2, H=128, W=128, N=200, K=32)
+    x = glr.gap_step(y[None], m, None).view(cfg.T, 1, cfg.H, cfg.W).contiguous()
+    keys, nf, _ = glr.select_keys(x, cfg.P, cfg.N)
+    best = glr.autotune_match(x, cfg.P, keys, nf, cfg.K, "bf16", candidates=[(48, 1, 0), (48, 2, 192), (64, 1, 320)])
+    assert best in [(48, 1, 0), (48, 2, 192), (64, 1, 320)]
+    ref, _ = glr.match_topk(x, cfg.P, keys, nf, cfg.K, "fp32")
+    got, _ = glr.match_topk(x, cfg.P, keys, nf, cfg.K, "bf16", k_over=best[0], splits=best[1], cap=best[2])
+    a, b = ref.cpu().numpy(), got.cpu().numpy()
+    same = np.mean([len(set(a[f, k]) & set(b[f, k])) / cfg.K for f in range(cfg.T) for k in range(cfg.N)])
+    assert same >= 0.99
+
+
+def test_reconstruction_tracks_oracle_teacher_forced():
+    """Three GAP iterations: each GPU step is fed the GPU state, and the oracle's step on the
+    same state must agree (keys bit-exact for 8-bit-quantised states, denoised frames close)."""
+    cfg, prob, y, m = _problem(T=2, H=64, W=72, N=60, K=16)
+    rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode="fp32")
+    rec.start(y, m)
+    for s in cfg.sigma_schedule():
+        # quantise the state so that both sides take the same edge decisions
+        q = torch.round(rec.x * 256.0) / 256.0
+        rec.x.copy_(q)
+        xs = rec.x.cpu().numpy()[0][:, None].astype(np.float64)
+        rec.step(s, cfg.c_wnnm)
+        v_gpu = rec.v.cpu().numpy()[0]
+        v_or, _ = O.glr_denoise(xs, cfg.P, cfg.N, cfg.K, s, cfg.c_wnnm, cfg.edge_th, eps=1e-8)
+        err = np.abs(v_gpu - v_or[:, 0])
+        assert np.sqrt(np.mean(err ** 2)) < 2e-4 and err.max() < 2e-3
+        x_or, _ = O.gap_project(prob.y, prob.masks, v_gpu)
+        np.testing.assert_allclose(rec.x.cpu().numpy()[0], x_or, rtol=1e-4, atol=1e-5)
