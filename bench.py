@@ -310,6 +310,7 @@ def run_glr(args) -> None:
     prof = None
     clocks_summary = None
     sweeps = 0.0
+    svd_noconv = None
     stream_stats = None
     launches = 0
     tuned = {}
@@ -360,6 +361,7 @@ def run_glr(args) -> None:
             glr.profile_enable(False)
             bits, cnt = glr.poll_status(rec.den.ws_lowrank)
             sweeps = cnt[2] / max(cnt[3], 1)
+            svd_noconv = cnt[1]
             _, mcnt = glr.poll_status(rec.den.ws_match)
             stream_stats = {"appends_per_key": round(mcnt[4] / (cfg.T * cfg.N), 1),
                             "compactions_per_key": round(mcnt[5] / (cfg.T * cfg.N), 2)}
@@ -458,6 +460,7 @@ def run_glr(args) -> None:
         "gpu_launches": launches,
         "kernels": kernels,
         "svd_sweeps_per_group": round(sweeps, 2),
+        "svd_groups_at_sweep_cap": svd_noconv,
         "topk_streams": stream_stats,
         "roofline": rl,
         "cpu_baseline": cpu,

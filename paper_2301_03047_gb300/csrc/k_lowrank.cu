@@ -60,12 +60,13 @@ __global__ void __launch_bounds__(256) k_gather(const float* __restrict__ x, int
 // changes them: alpha - t gamma, beta + t gamma); only gamma = a.b is summed.
 template <int DMAX>
 __device__ __forceinline__ void jacobi_pair(float (&a)[DMAX], float (&b)[DMAX], float& alpha, float& beta, float tol,
-                                            bool active, bool& rotated) {
+                                            float lam_skip, bool active, bool& rotated) {
   float ga[4] = {0.f, 0.f, 0.f, 0.f};  // four partial sums shorten the dependency chain
 #pragma unroll
   for (int r = 0; r < DMAX; ++r) ga[r & 3] = fmaf(a[r], b[r], ga[r & 3]);
   const float gamma = (ga[0] + ga[1]) + (ga[2] + ga[3]);
-  if (active && fabsf(gamma) > tol * sqrtf(alpha * beta) && gamma != 0.f) {
+  // pairs of columns that are both below lam_skip are left alone (see the sweep loop)
+  if (active && fabsf(gamma) > tol * sqrtf(alpha * beta) && gamma != 0.f && (alpha >= lam_skip || beta >= lam_skip)) {
     const float zeta = __fdividef(beta - alpha, 2.f * gamma);
     const float az = fabsf(zeta);
     float t = (az < 1e18f) ? __frcp_rn(az + sqrtf(fmaf(zeta, zeta, 1.f))) : __fdividef(0.5f, az);
@@ -127,6 +128,11 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_jacobi_wnnm(int n_img, int d,
     }
     int sweep = 0;
     bool converged = (m < 1);
+    // Components with s^2 < K sw^2 are always removed by the shrinkage.  When the
+    // columns below that level carry less than K sw^2 in total, no combination of
+    // them can reach it, so rotations among them cannot change X^ and are skipped
+    // (decided per sweep; a sweep without rotations ends the iteration).
+    const float lam = (float)K * sigma_w * sigma_w;
     // Parallel ordering by recursive halving (32 lanes, 64 column slots): at a
     // level with lane groups of size g, the B columns shift cyclically inside
     // each group for g rounds, so every A meets every B of its group; then each
@@ -137,6 +143,10 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_jacobi_wnnm(int n_img, int d,
       bool rotated = false;
       // exact norms once per sweep; tracked through the rotations within it
       float alpha = sq_norm<DMAX>(a), beta = sq_norm<DMAX>(b);
+      float small = (alpha < lam ? alpha : 0.f) + (beta < lam ? beta : 0.f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) small += __shfl_xor_sync(0xffffffffu, small, o);
+      const float lam_skip = (lam > 0.f && small < lam) ? lam : 0.f;
 #pragma unroll 1
       for (int g = 32; g >= 1; g >>= 1) {
         if (g < 32) {
@@ -158,7 +168,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_jacobi_wnnm(int n_img, int d,
         const int src = (lane & ~(g - 1)) | ((lane + 1) & (g - 1));
 #pragma unroll 1
         for (int rd = 0; rd < g; ++rd) {
-          jacobi_pair<DMAX>(a, b, alpha, beta, tol, live, rotated);
+          jacobi_pair<DMAX>(a, b, alpha, beta, tol, lam_skip, live, rotated);
           if (rd + 1 < g) {
 #pragma unroll
             for (int r = 0; r < DMAX; ++r) b[r] = __shfl_sync(0xffffffffu, b[r], src);

@@ -497,6 +497,12 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
     return GLR_ECUDA;
   if (cudaFuncSetAttribute(k_match_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) != cudaSuccess)
     return GLR_ECUDA;
+  {
+    int blocks_per_sm = 0;  // the kernel needs exactly one resident CTA per SM (all of TMEM)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_match_tc, TC_THREADS, TC_SMEM) != cudaSuccess ||
+        blocks_per_sm < 1)
+      return GLR_ENOTSUP;
+  }
   const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
   const StreamCfg cfg{pl.cap, pl.Kp};
   dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);

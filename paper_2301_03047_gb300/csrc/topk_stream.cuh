@@ -149,8 +149,15 @@ static __device__ __noinline__ int compact_mid(uint2* b, int n, int kp, int cap,
   uint32_t cut = te_key;
   *pub = 0xffffffffu;
   if (below_te > (cap + kp) / 2) {
-    // 32 samples spread over the buffer, sorted across the warp (bitonic, ascending)
-    uint32_t smp = b[(int)(((long long)lane * n) >> 5)].x;
+    // 32 samples (a block of 32 consecutive entries from the middle of the buffer,
+    // already in registers), sorted across the warp (bitonic, ascending)
+    uint32_t smp = e[0].x;
+    {
+      const int mid = min(kStreamSlots - 1, max(0, (n / 32) / 2));
+#pragma unroll
+      for (int i = 0; i < kStreamSlots; ++i)
+        if (i == mid) smp = e[i].x;
+    }
 #pragma unroll
     for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
