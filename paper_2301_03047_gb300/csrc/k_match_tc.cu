@@ -254,6 +254,130 @@ __global__ void __launch_bounds__(256) k_pack_keys(const float* __restrict__ key
   }
 }
 
+// Seed bounds: for each key, the K'-th smallest tensor-core score over 16 x 16
+// positions sampled at stride 2 around it.  That sample is a subset of the
+// positions, so at least K' positions score below this value: it is a valid
+// initial published bound.  The scores are recomputed here from the same
+// packed BF16 operands in FP32; a margin covers the different summation order.
+// One warp per key; 8 positions per lane; exact warp radix select.
+constexpr int SEED_WIN = 16;    // samples per side
+constexpr int SEED_STRIDE = 2;  // spacing of the samples
+__global__ void __launch_bounds__(256) k_seed_bounds(const __nv_bfloat16* __restrict__ qmain,
+                                                     const __nv_bfloat16* __restrict__ qaux,
+                                                     const __nv_bfloat16* __restrict__ kmain,
+                                                     const __nv_bfloat16* __restrict__ kaux,
+                                                     const int32_t* __restrict__ keys,
+                                                     const int32_t* __restrict__ n_found, int n_img, int N, int Npad,
+                                                     int Hq, int Wq, long long npos_pad, int kp,
+                                                     uint32_t* __restrict__ tau_gl) {
+  __shared__ unsigned hist_s[8][256];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned* hist = hist_s[wid];
+  const long long nkeys = (long long)n_img * N;
+  for (long long gk = blockIdx.x * 8LL + wid; gk < nkeys; gk += gridDim.x * 8LL) {
+    const int f = (int)(gk / N), k = (int)(gk - (long long)f * N);
+    if (k >= min(n_found[f], N)) continue;
+    const int kq = keys[gk];
+    if ((unsigned)kq >= (unsigned)(Hq * Wq)) continue;
+    constexpr int SPAN = SEED_WIN * SEED_STRIDE;
+    if (Hq < SPAN || Wq < SPAN) continue;  // small images: no seed
+    const int kr = kq / Wq, kc = kq - (kq / Wq) * Wq;
+    const int r0 = min(max(kr - SPAN / 2, 0), Hq - SPAN);
+    const int c0 = min(max(kc - SPAN / 2, 0), Wq - SPAN);
+    const int rows = SEED_WIN, cols = SEED_WIN;
+    // key operand: -2 p~ (64) and the three pn terms
+    const __nv_bfloat16* ka = kmain + ((long long)f * Npad + k) * DK_MAIN;
+    const __nv_bfloat16* kx = kaux + ((long long)f * Npad + k) * DK_AUX;
+    const float pn = __bfloat162float(kx[3]) + __bfloat162float(kx[4]) + __bfloat162float(kx[5]);
+    float kv[DK_MAIN];
+#pragma unroll
+    for (int e = 0; e < DK_MAIN; ++e) kv[e] = __bfloat162float(ka[e]);
+    constexpr int PER_LANE = SEED_WIN * SEED_WIN / 32;
+    uint32_t key_s[PER_LANE];
+    float qmax = 0.f;
+#pragma unroll
+    for (int i = 0; i < PER_LANE; ++i) {
+      // sample j = 32 i + lane: row j / 16, column j % 16 of the strided grid
+      uint32_t kk = 0xffffffffu;
+      {
+        const int j = 32 * i + lane;
+        const long long q = (long long)(r0 + SEED_STRIDE * (j / SEED_WIN)) * Wq + c0 + SEED_STRIDE * (j % SEED_WIN);
+        const uint4* qa = reinterpret_cast<const uint4*>(qmain + ((long long)f * npos_pad + q) * DK_MAIN);
+        float acc = 0.f;
+#pragma unroll
+        for (int v = 0; v < DK_MAIN / 8; ++v) {
+          const uint4 w = __ldg(qa + v);
+          const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&w);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) acc = fmaf(kv[v * 8 + t], __bfloat162float(hb[t]), acc);
+        }
+        const __nv_bfloat16* qx = qaux + ((long long)f * npos_pad + q) * DK_AUX;
+        const float qn = __bfloat162float(qx[0]) + __bfloat162float(qx[1]) + __bfloat162float(qx[2]);
+        qmax = fmaxf(qmax, qn);
+        kk = float_order_key((acc + qn) + pn);
+      }
+      key_s[i] = kk;
+    }
+    const int n = rows * cols;
+    if (n < kp) continue;
+    // exact kp-th smallest of the 32 x 32 keys (4-pass radix select over the registers)
+    uint32_t prefix = 0, pmask = 0;
+    int rank = kp;
+#pragma unroll 1
+    for (int pass = 0; pass < 4; ++pass) {
+      const int shift = 24 - 8 * pass;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) hist[lane * 8 + t] = 0;
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < PER_LANE; ++i)
+        if (key_s[i] != 0xffffffffu && (key_s[i] & pmask) == prefix) atomicAdd(&hist[(key_s[i] >> shift) & 255u], 1u);
+      __syncwarp();
+      int loc[8], sum = 0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        loc[t] = (int)hist[lane * 8 + t];
+        sum += loc[t];
+      }
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int yv = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += yv;
+      }
+      const int excl = incl - sum;
+      const int owner = __ffs(__ballot_sync(0xffffffffu, excl < rank && rank <= incl)) - 1;
+      int sel = 0, before = 0;
+      if (lane == owner) {
+        int c = excl;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          if (c + loc[t] >= rank) {
+            sel = lane * 8 + t;
+            before = c;
+            break;
+          }
+          c += loc[t];
+        }
+      }
+      sel = __shfl_sync(0xffffffffu, sel, owner);
+      before = __shfl_sync(0xffffffffu, before, owner);
+      rank -= before;
+      prefix |= (uint32_t)sel << shift;
+      pmask |= 255u << shift;
+      __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qmax = fmaxf(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+    if (lane == 0) {
+      // margin: FP32 summation-order difference of ~80 products (far above its actual size)
+      const float s_k = float_from_order_key(prefix);
+      const float margin = 1e-5f * (pn + qmax + 2.f * sqrtf(pn * qmax)) + 1e-7f;
+      tau_gl[(long long)f * Npad + k] = float_order_key(s_k + margin) + 1u;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_match_tc(const __grid_constant__ CUtensorMap tm_qmain, const __grid_constant__ CUtensorMap tm_qaux,
                const __grid_constant__ CUtensorMap tm_kmain, const __grid_constant__ CUtensorMap tm_kaux,
@@ -370,12 +494,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint2* mybuf = bufs + stream * (cfg.cap + 32);
     float tau = (key < nf) ? INFINITY : -INFINITY;
     int cnt = 0;
-    uint32_t gl_next = 0xffffffffu;  // published bound of other CTAs, loaded one tile ahead
+    uint32_t gl_next;  // seeded / published bound of the row, loaded one tile ahead
     uint2 stats = make_uint2(0u, 0u);
     unsigned* whist = hist + e * 256;
     float* wtile = tiles + e * 32 * TILE_LD;
     uint32_t* pub_sh = tau_sh + 32 * quad;
     uint32_t* pub_gl = tau_gl + (long long)f * Npad + (long long)kt * TC_M + 32 * quad;
+    gl_next = *reinterpret_cast<volatile uint32_t*>(pub_gl + lane);
     for (int i = 0; i < nt; ++i) {
       const int b = i & 1;
       const uint32_t bph = (uint32_t)(i >> 1) & 1u;
@@ -463,7 +588,7 @@ bool make_map(CUtensorMap* m, void* base, uint64_t rows, uint32_t cols, uint32_t
 extern float* g_tc_dump;
 
 glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int32_t* n_found, const MatchPlan& pl,
-                                char* ws, float* dump, cudaStream_t s) {
+                                char* ws, float* dump, const int32_t* seed_keys, int seed_N, cudaStream_t s) {
   const int d = im.C * im.P * im.P;
   if (d > DK_MAIN) return GLR_ENOTSUP;
   const float* mean = reinterpret_cast<const float*>(ws + pl.mean_off);
@@ -487,6 +612,14 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
     const int nk = im.n_img * pl.Npad;
     const int blocks = (int)std::max<long long>(1, ceil_div(nk, 256));
     GLR_LAUNCH("k_pack_keys", s, k_pack_keys<<<blocks, 256, 0, s>>>(keyv, nk, d, kmain, kaux));
+  }
+  if (seed_keys != nullptr) {
+    const long long nkeys = (long long)im.n_img * seed_N;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, 8), 152LL * 16));
+    GLR_LAUNCH("k_seed_bounds", s,
+               k_seed_bounds<<<blocks, 256, 0, s>>>(qmain, qaux, kmain, kaux, seed_keys, n_found, im.n_img, seed_N,
+                                                    pl.Npad, im.H - im.P + 1, im.W - im.P + 1, pl.npos_pad, pl.Kp,
+                                                    taugl));
   }
   CUtensorMap tq, tqa, tk, tka;
   const uint64_t qrows = (uint64_t)im.n_img * pl.npos_pad, krows = (uint64_t)im.n_img * pl.Npad;
@@ -515,9 +648,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
 
 glr_status launch_match_tc(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found, int N,
                            const MatchPlan& pl, char* ws, cudaStream_t s) {
-  (void)keys;
-  (void)N;
-  return launch_match_tc_impl(x, im, n_found, pl, ws, g_tc_dump, s);
+  return launch_match_tc_impl(x, im, n_found, pl, ws, g_tc_dump, g_tc_dump ? nullptr : keys, N, s);
 }
 
 float* g_tc_dump = nullptr;
