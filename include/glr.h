@@ -73,9 +73,14 @@ typedef struct glr_images {
 
 /* Contraction used by glr_match_topk. */
 enum {
-  GLR_MATCH_FP32 = 0, /* plain form: FP32 FMA on the CUDA cores */
-  GLR_MATCH_BF16 = 1  /* chosen form: BF16 tcgen05.mma into TMEM, FP32 accumulate, FP32 re-rank */
+  GLR_MATCH_FP32 = 0,   /* plain form: FP32 FMA on the CUDA cores */
+  GLR_MATCH_BF16 = 1,   /* chosen form: BF16 tcgen05.mma into TMEM, FP32 accumulate, FP32 re-rank */
+  GLR_MATCH_LEARNED = 2 /* learned proposal: k_over candidates by the 16-dim encoder embedding
+                           (BF16 tcgen05 contraction), then the exact FP32 re-rank on patches */
 };
+
+/* Number of floats of an encoder parameter buffer: W1[64][64], b1[64], W2[16][64], b2[16]. */
+#define GLR_ENCODER_PARAMS 5200
 
 typedef struct glr_match_opts {
   int32_t mode;   /* GLR_MATCH_* */
@@ -84,11 +89,13 @@ typedef struct glr_match_opts {
   int32_t splits; /* position splits per key tile; 0 = automatic */
   int32_t cap;    /* candidates a top-K stream may hold before it compacts
                      (> k_over, <= 512); 0 = automatic */
-  int32_t reserved[4];
+  const float* encoder; /* GLR_MATCH_LEARNED: device encoder parameters (GLR_ENCODER_PARAMS
+                           floats); k_over = candidates per key (0 = 256) */
+  int32_t reserved[2];
 } glr_match_opts;
 
 /* Operation codes for glr_workspace_size. */
-enum { GLR_OP_SELECT = 1, GLR_OP_MATCH = 2, GLR_OP_LOWRANK = 3, GLR_OP_AGGREGATE = 4 };
+enum { GLR_OP_SELECT = 1, GLR_OP_MATCH = 2, GLR_OP_LOWRANK = 3, GLR_OP_AGGREGATE = 4, GLR_OP_ENCODER = 5 };
 
 /*
  * Workspace bytes needed by one operation.  `opts` is used by GLR_OP_MATCH
@@ -138,6 +145,31 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
                           const int32_t* n_found, int32_t N, int32_t K,
                           const glr_match_opts* opts, int32_t* idx, float* dist, void* ws,
                           size_t ws_bytes, void* stream);
+
+/*
+ * Learned matching proposal (the project's learned-proposal pattern; the
+ * paper's Outlook only mentions low-rank networks).  The encoder
+ * f(p) = W2 relu(W1 p + b1) + b2 maps a mean-shifted patch (d <= 64, zero
+ * padded) to 16 values; GLR_MATCH_LEARNED retrieves candidates by
+ * ||f(p) - f(q)||^2 and re-ranks them with the exact patch distance.
+ * Inference rounds the weights to FP16 and computes in FP32.
+ *
+ * glr_encoder_embed: emb float32 [n_img][Hq*Wq][16] for every position.
+ *
+ * glr_encoder_train_step: one AdamW step (lr, weight decay on W1 and W2;
+ * betas 0.9 / 0.999, eps 1e-8; `step` >= 1 is the step number for the bias
+ * correction) on the loss mean_i w_i (||f(p_i) - f(q_i)||^2 - d_i)^2 with
+ * d_i the exact squared distance of the two patches and
+ * w_i = 1 / (d_i + 0.05)^2.  pairs int32 [n_pairs][3] = (image, position of
+ * p, position of q).  params, adam_m, adam_v: GLR_ENCODER_PARAMS floats each,
+ * updated in place (FP32 master).  loss: device float, receives the batch
+ * loss before the update.  Workspace: glr_workspace_size(GLR_OP_ENCODER, ...).
+ */
+glr_status glr_encoder_embed(const float* x, const glr_images* im, const float* params, float* emb, void* ws,
+                             size_t ws_bytes, void* stream);
+glr_status glr_encoder_train_step(const float* x, const glr_images* im, const int32_t* pairs, int32_t n_pairs,
+                                  float* params, float* adam_m, float* adam_v, int32_t step, float lr,
+                                  float weight_decay, float* loss, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * Testing aid for the BF16 tensor-core scorer: runs glr_match_topk in

@@ -16,8 +16,9 @@ c_uint32_p = ctypes.POINTER(ctypes.c_uint32)
 
 GLR_OK, GLR_EINVAL, GLR_ECUDA, GLR_ENOMEM, GLR_ETIMEDOUT, GLR_ENOTSUP, GLR_EDEVICE, GLR_ETOOBIG = range(8)
 GLR_DEV_TIMEOUT, GLR_DEV_NONFINITE, GLR_DEV_SVD_NOCONV, GLR_DEV_CAND_OVERFLOW, GLR_DEV_BAD_INDEX = 1, 2, 4, 8, 16
-GLR_MATCH_FP32, GLR_MATCH_BF16 = 0, 1
-GLR_OP_SELECT, GLR_OP_MATCH, GLR_OP_LOWRANK, GLR_OP_AGGREGATE = 1, 2, 3, 4
+GLR_MATCH_FP32, GLR_MATCH_BF16, GLR_MATCH_LEARNED = 0, 1, 2
+GLR_OP_SELECT, GLR_OP_MATCH, GLR_OP_LOWRANK, GLR_OP_AGGREGATE, GLR_OP_ENCODER = 1, 2, 3, 4, 5
+GLR_ENCODER_PARAMS = 5200
 
 
 class GlrImages(ctypes.Structure):
@@ -25,7 +26,8 @@ class GlrImages(ctypes.Structure):
 
 
 class GlrMatchOpts(ctypes.Structure):
-    _fields_ = [("mode", c_int32), ("k_over", c_int32), ("splits", c_int32), ("cap", c_int32), ("reserved", c_int32 * 4)]
+    _fields_ = [("mode", c_int32), ("k_over", c_int32), ("splits", c_int32), ("cap", c_int32), ("encoder", c_void_p),
+                ("reserved", c_int32 * 2)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/glr.h
@@ -34,6 +36,8 @@ PROTOTYPES = {
     "glr_select_keys": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_float, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_match_topk": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, ctypes.POINTER(GlrMatchOpts), c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_debug_match_scores": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "glr_encoder_embed": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "glr_encoder_train_step": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_float, c_float, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_lowrank_groups": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_aggregate": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(GlrImages), c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_aggregate_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(GlrImages), c_int32, c_int32, c_void_p, c_void_p, c_void_p]),

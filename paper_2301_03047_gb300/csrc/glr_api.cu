@@ -145,6 +145,12 @@ size_t glr_workspace_size(int32_t op, const glr_images* im, int32_t N, int32_t K
       return sizeof(StatusBlock);
     case GLR_OP_AGGREGATE:
       return agg_ws_layout(*im).total;
+    case GLR_OP_ENCODER: {
+      WsLayout L;
+      L.take((size_t)im->n_img * 4);             // image means
+      L.take((size_t)GLR_ENCODER_PARAMS * 4);    // gradient
+      return L.off;
+    }
     default:
       return 0;
   }
@@ -171,7 +177,9 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
   const long long npos = npos_of(im);
   if (N < 1 || K < 1 || K > npos) return GLR_EINVAL;
   if (K > 128) return GLR_ENOTSUP;
-  if (opts && opts->mode != GLR_MATCH_FP32 && opts->mode != GLR_MATCH_BF16) return GLR_EINVAL;
+  if (opts && opts->mode != GLR_MATCH_FP32 && opts->mode != GLR_MATCH_BF16 && opts->mode != GLR_MATCH_LEARNED)
+    return GLR_EINVAL;
+  if (opts && opts->mode == GLR_MATCH_LEARNED && (!opts->encoder || im->C * im->P * im->P > 64)) return GLR_EINVAL;
   if (opts && (opts->k_over < 0 || opts->splits < 0 || opts->cap < 0 || (opts->k_over > 0 && opts->k_over < K)))
     return GLR_EINVAL;
   if (opts && opts->cap > 512) return GLR_ENOTSUP;
@@ -180,7 +188,7 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
   cudaStream_t s = (cudaStream_t)stream;
   glr_status st = begin_ws(ws, ws_bytes, pl.total, s);
   if (st != GLR_OK) return st;
-  return launch_match(x, *im, keys, n_found, N, pl, idx, dist, (char*)ws, s);
+  return launch_match(x, *im, keys, n_found, N, pl, opts ? opts->encoder : nullptr, idx, dist, (char*)ws, s);
 }
 
 glr_status glr_debug_match_scores(const float* x, const glr_images* im, const int32_t* keys,
@@ -193,6 +201,39 @@ glr_status glr_debug_match_scores(const float* x, const glr_images* im, const in
   glr_status st = glr_match_topk(x, im, keys, n_found, N, K, &o, nullptr, nullptr, ws, ws_bytes, stream);
   g_tc_dump = nullptr;
   return st;
+}
+
+glr_status glr_encoder_embed(const float* x, const glr_images* im, const float* params, float* emb, void* ws,
+                             size_t ws_bytes, void* stream) {
+  if (!images_ok(im) || !x || !params || !emb) return GLR_EINVAL;
+  if (im->C * im->P * im->P > 64) return GLR_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t need = glr_workspace_size(GLR_OP_ENCODER, im, 1, 1, nullptr);
+  glr_status st = begin_ws(ws, ws_bytes, need, s);
+  if (st != GLR_OK) return st;
+  float* mean = reinterpret_cast<float*>((char*)ws + align_up(sizeof(StatusBlock)));
+  st = launch_image_mean(x, *im, mean, s);
+  if (st != GLR_OK) return st;
+  return launch_encode_positions(x, *im, mean, params, emb, s);
+}
+
+glr_status glr_encoder_train_step(const float* x, const glr_images* im, const int32_t* pairs, int32_t n_pairs,
+                                  float* params, float* adam_m, float* adam_v, int32_t step, float lr,
+                                  float weight_decay, float* loss, void* ws, size_t ws_bytes, void* stream) {
+  if (!images_ok(im) || !x || !pairs || !params || !adam_m || !adam_v || !loss) return GLR_EINVAL;
+  if (n_pairs < 1 || step < 1 || !(lr > 0.f) || !(weight_decay >= 0.f)) return GLR_EINVAL;
+  if (im->C * im->P * im->P > 64) return GLR_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t need = glr_workspace_size(GLR_OP_ENCODER, im, 1, 1, nullptr);
+  glr_status st = begin_ws(ws, ws_bytes, need, s);
+  if (st != GLR_OK) return st;
+  WsLayout L;
+  float* mean = reinterpret_cast<float*>((char*)ws + L.take((size_t)im->n_img * 4));
+  float* grad = reinterpret_cast<float*>((char*)ws + L.take((size_t)GLR_ENCODER_PARAMS * 4));
+  st = launch_image_mean(x, *im, mean, s);
+  if (st != GLR_OK) return st;
+  return launch_encoder_train(x, *im, mean, pairs, n_pairs, params, adam_m, adam_v, step, lr, weight_decay, grad,
+                              loss, s);
 }
 
 glr_status glr_lowrank_groups(const float* x, const glr_images* im, const int32_t* idx, const int32_t* n_found,

@@ -35,14 +35,29 @@ struct MatchPlan {
   int tiles_per_split;
   int dk;               // BF16 operand row length (elements)
   long long npos_pad;   // BF16 position rows per image (pos_tiles * pos_tile)
-  size_t mean_off, qn_off, keyv_off, buf_off, bufcnt_off, taugl_off, qpack_off, kpack_off, total;
+  size_t mean_off, qn_off, keyv_off, buf_off, bufcnt_off, taugl_off, qpack_off, kpack_off, embp_off, embk_off, total;
 };
 MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o);
 glr_status launch_match(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found, int N,
-                        const MatchPlan& plan, int32_t* idx, float* dist, char* ws, cudaStream_t s);
+                        const MatchPlan& plan, const float* encoder, int32_t* idx, float* dist, char* ws,
+                        cudaStream_t s);
 // tensor-core scorer (k_match_tc.cu); returns GLR_ENOTSUP when the shape is not covered
 glr_status launch_match_tc(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found,
                            int N, const MatchPlan& plan, char* ws, cudaStream_t s);
+glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int32_t* n_found, const MatchPlan& pl,
+                                char* ws, float* dump, const int32_t* seed_keys, int seed_N, const float* emb_pos,
+                                const float* emb_keys, cudaStream_t s);
+
+// ---- learned proposal (k_encoder.cu)
+glr_status launch_encode_positions(const float* x, const glr_images& im, const float* mean, const float* params,
+                                   float* emb, cudaStream_t s);
+glr_status launch_encode_vectors(const float* vecs, long long n, int d, const float* params, float* emb,
+                                 cudaStream_t s);
+glr_status launch_image_mean(const float* x, const glr_images& im, float* mean, cudaStream_t s);
+glr_status launch_encoder_train(const float* x, const glr_images& im, const float* mean, const int32_t* pairs,
+                                int n_pairs, float* params, float* m, float* v, int step, float lr, float wd,
+                                float* grad, float* loss, cudaStream_t s);
+
 // testing aid: when set, the tensor-core scorer also writes the raw scores of the
 // first position tile, [n_img][Npad][256] float32, to this device buffer
 extern float* g_tc_dump;

@@ -397,7 +397,8 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   MatchPlan pl{};
   pl.mode = o ? o->mode : GLR_MATCH_FP32;
   pl.K = K;
-  pl.Kp = (o && o->k_over > 0) ? o->k_over : K + 16;
+  const bool tc = pl.mode == GLR_MATCH_BF16 || pl.mode == GLR_MATCH_LEARNED;
+  pl.Kp = (o && o->k_over > 0) ? o->k_over : (pl.mode == GLR_MATCH_LEARNED ? std::max(256, K + 16) : K + 16);
   pl.Kp = std::max(pl.Kp, K);
   // a small compaction trigger publishes a first threshold early; each compaction keeps ~Kp + (cap - Kp) / 4
   pl.cap = (o && o->cap > 0) ? o->cap : std::min(std::max(2 * pl.Kp + 64, 256), kStreamMaxEntries - 32);
@@ -407,7 +408,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   pl.Npad = (int)(ceil_div(N, FT) * FT);
   const int Hq = im.H - im.P + 1, Wq = im.W - im.P + 1;
   const int ktiles = pl.Npad / FT;
-  if (pl.mode == GLR_MATCH_BF16) {
+  if (tc) {
     pl.pos_tile = 256;
     pl.pos_tiles = (int)ceil_div((long long)Hq * Wq, pl.pos_tile);
   } else {
@@ -433,7 +434,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   pl.buf_off = L.take((size_t)nstreams * (pl.cap + 32) * 8);
   pl.bufcnt_off = L.take((size_t)nstreams * 4);
   pl.taugl_off = L.take((size_t)im.n_img * pl.Npad * 4);
-  if (pl.mode == GLR_MATCH_BF16) {
+  if (tc) {
     // BF16 operands: positions [img][npos_pad][dk] and keys [img][Npad][dk], dk = d + 16 (norm columns)
     const int dk = 64 + 16;  // patch columns padded to 64, plus the norm columns
     pl.dk = dk;
@@ -441,12 +442,17 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
     pl.qpack_off = L.take((size_t)im.n_img * pl.npos_pad * dk * 2);
     pl.kpack_off = L.take((size_t)im.n_img * pl.Npad * dk * 2);
   }
+  if (pl.mode == GLR_MATCH_LEARNED) {
+    pl.embp_off = L.take((size_t)im.n_img * npos * 16 * 4);
+    pl.embk_off = L.take((size_t)im.n_img * pl.Npad * 16 * 4);
+  }
   pl.total = L.off;
   return pl;
 }
 
 glr_status launch_match(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found, int N,
-                        const MatchPlan& pl, int32_t* idx, float* dist, char* ws, cudaStream_t s) {
+                        const MatchPlan& pl, const float* encoder, int32_t* idx, float* dist, char* ws,
+                        cudaStream_t s) {
   const int Hq = im.H - im.P + 1, Wq = im.W - im.P + 1;
   const long long npos = (long long)Hq * Wq;
   const int d = im.C * im.P * im.P;
@@ -471,7 +477,15 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
                                         keyv, reinterpret_cast<StatusBlock*>(ws)));
   }
   StreamCfg cfg{pl.cap, pl.Kp};
-  if (pl.mode == GLR_MATCH_BF16) {
+  if (pl.mode == GLR_MATCH_LEARNED) {
+    float* emb_p = reinterpret_cast<float*>(ws + pl.embp_off);
+    float* emb_k = reinterpret_cast<float*>(ws + pl.embk_off);
+    glr_status st = launch_encode_positions(x, im, mean, encoder, emb_p, s);
+    if (st != GLR_OK) return st;
+    st = launch_encode_vectors(keyv, (long long)im.n_img * pl.Npad, d, encoder, emb_k, s);
+    if (st != GLR_OK) return st;
+  }
+  if (pl.mode == GLR_MATCH_BF16 || pl.mode == GLR_MATCH_LEARNED) {
     const glr_status st = launch_match_tc(x, im, keys, n_found, N, pl, ws, s);
     if (st != GLR_OK) return st;
   } else {

@@ -173,8 +173,10 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16&
 }
 
 // Positions: thread per position; writes 64 + 16 bf16.
+// emb != nullptr: pack the 16-value embeddings emb[img][q][16] instead of the patches.
 __global__ void __launch_bounds__(256) k_pack_positions(const float* __restrict__ x, const float* __restrict__ mean,
                                                         int n_img, int C, int H, int W, int P, long long npos_pad,
+                                                        const float* __restrict__ emb,
                                                         __nv_bfloat16* __restrict__ qmain,
                                                         __nv_bfloat16* __restrict__ qaux) {
   const int Hq = H - P + 1, Wq = W - P + 1;
@@ -197,7 +199,9 @@ __global__ void __launch_bounds__(256) k_pack_positions(const float* __restrict_
 #pragma unroll 8
       for (int e = 0; e < DK_MAIN; ++e) {
         float v = 0.f;
-        if (e < d) {
+        if (emb != nullptr) {
+          if (e < 16) v = __ldg(emb + (f * npos + q) * 16 + e);
+        } else if (e < d) {
           const int ch = e / (P * P), dr = (e / P) % P, dc = e % P;
           v = __ldg(x + (((long long)f * C + ch) * H + r + dr) * W + c + dc) - mu;
         }
@@ -588,11 +592,12 @@ bool make_map(CUtensorMap* m, void* base, uint64_t rows, uint32_t cols, uint32_t
 extern float* g_tc_dump;
 
 glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int32_t* n_found, const MatchPlan& pl,
-                                char* ws, float* dump, const int32_t* seed_keys, int seed_N, cudaStream_t s) {
-  const int d = im.C * im.P * im.P;
+                                char* ws, float* dump, const int32_t* seed_keys, int seed_N, const float* emb_pos,
+                                const float* emb_keys, cudaStream_t s) {
+  const int d = emb_keys ? 16 : im.C * im.P * im.P;
   if (d > DK_MAIN) return GLR_ENOTSUP;
   const float* mean = reinterpret_cast<const float*>(ws + pl.mean_off);
-  const float* keyv = reinterpret_cast<const float*>(ws + pl.keyv_off);
+  const float* keyv = emb_keys ? emb_keys : reinterpret_cast<const float*>(ws + pl.keyv_off);
   uint2* bufs = reinterpret_cast<uint2*>(ws + pl.buf_off);
   int* bufcnt = reinterpret_cast<int*>(ws + pl.bufcnt_off);
   uint32_t* taugl = reinterpret_cast<uint32_t*>(ws + pl.taugl_off);
@@ -605,8 +610,8 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
     const long long total = (long long)im.n_img * pl.npos_pad;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
     GLR_LAUNCH("k_pack_positions", s,
-               k_pack_positions<<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, pl.npos_pad, qmain,
-                                                       qaux));
+               k_pack_positions<<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, pl.npos_pad, emb_pos,
+                                                       qmain, qaux));
   }
   {
     const int nk = im.n_img * pl.Npad;
@@ -648,7 +653,9 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
 
 glr_status launch_match_tc(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found, int N,
                            const MatchPlan& pl, char* ws, cudaStream_t s) {
-  return launch_match_tc_impl(x, im, n_found, pl, ws, g_tc_dump, g_tc_dump ? nullptr : keys, N, s);
+  const float* ep = pl.mode == GLR_MATCH_LEARNED ? reinterpret_cast<const float*>(ws + pl.embp_off) : nullptr;
+  const float* ek = pl.mode == GLR_MATCH_LEARNED ? reinterpret_cast<const float*>(ws + pl.embk_off) : nullptr;
+  return launch_match_tc_impl(x, im, n_found, pl, ws, g_tc_dump, g_tc_dump ? nullptr : keys, N, ep, ek, s);
 }
 
 float* g_tc_dump = nullptr;

@@ -7,6 +7,7 @@ There is no CPU fallback; a missing library raises.
 from __future__ import annotations
 
 import ctypes
+import math
 from dataclasses import dataclass
 
 import torch
@@ -50,10 +51,12 @@ def images_of(x: torch.Tensor, P: int) -> L.GlrImages:
     return images(n, C, H, W, P)
 
 
-def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0, cap: int = 0) -> L.GlrMatchOpts:
-    m = {"fp32": L.GLR_MATCH_FP32, "bf16": L.GLR_MATCH_BF16}.get(mode, mode)
+def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0, cap: int = 0,
+               encoder: torch.Tensor | None = None) -> L.GlrMatchOpts:
+    m = {"fp32": L.GLR_MATCH_FP32, "bf16": L.GLR_MATCH_BF16, "learned": L.GLR_MATCH_LEARNED}.get(mode, mode)
     o = L.GlrMatchOpts()
     o.mode, o.k_over, o.splits, o.cap = int(m), int(k_over), int(splits), int(cap)
+    o.encoder = _ptr(encoder) if encoder is not None else None
     return o
 
 
@@ -95,13 +98,13 @@ def select_keys(x, P, N, edge_th=0.1, *, keys=None, n_found=None, n_corner=None,
     return keys, n_found, n_corner
 
 
-def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, cap=0, idx=None, dist=None, ws=None,
-               stream=None):
+def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, cap=0, encoder=None, idx=None, dist=None,
+               ws=None, stream=None):
     """Global matching with a fused running top-K (Eq. 1 over the whole image, Eq. 4 as a contraction)."""
     lib = L.load()
     im = images_of(x, P)
     N = keys.shape[1]
-    o = match_opts(mode, k_over, splits, cap)
+    o = match_opts(mode, k_over, splits, cap, encoder)
     dev = x.device
     if idx is None:
         idx = torch.empty((x.shape[0], N, K), dtype=torch.int32, device=dev)
@@ -375,3 +378,84 @@ def autotune_match(x, P, keys, n_found, K, mode="bf16", candidates=None, repeats
     if cache_path:
         json.dump(_TUNE_CACHE, open(cache_path, "w"), indent=1)
     return best
+
+
+# ---------------------------------------------------------------------------
+# Learned proposal: patch encoder (64 -> 64 -> 16) trained on exact distances
+# of pairs the matcher produced.  All arithmetic runs in libglr.so.
+# ---------------------------------------------------------------------------
+class Encoder:
+    """FP32 master parameters and AdamW state of the patch encoder (device tensors)."""
+
+    def __init__(self, seed: int = 0, device="cuda"):
+        import numpy as np
+
+        rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([20230107, 77, seed])))
+        w1 = rng.standard_normal((64, 64)) * np.sqrt(2.0 / 64)
+        w2 = rng.standard_normal((16, 64)) * np.sqrt(1.0 / 64)
+        flat = np.concatenate([w1.ravel(), np.zeros(64), w2.ravel(), np.zeros(16)]).astype(np.float32)
+        self.params = torch.from_numpy(flat).to(device)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step_no = 0
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self._ws = {}
+
+    def _workspace(self, im):
+        key = (im.n_img, im.C, im.H, im.W, im.P)
+        if key not in self._ws:
+            self._ws[key] = workspace(L.GLR_OP_ENCODER, im, 1, 1, None, self.params.device)
+        return self._ws[key]
+
+    def embed(self, x, P, out=None, stream=None):
+        """Embeddings [n_img][Hq*Wq][16] of every patch position of x."""
+        im = images_of(x, P)
+        npos = (x.shape[2] - P + 1) * (x.shape[3] - P + 1)
+        if out is None:
+            out = torch.empty((x.shape[0], npos, 16), dtype=torch.float32, device=x.device)
+        wp, wn = _ws(self._workspace(im))
+        _check("glr_encoder_embed", L.load().glr_encoder_embed(_ptr(x), ctypes.byref(im), _ptr(self.params), _ptr(out),
+                                                                wp, wn, _stream(stream)))
+        return out
+
+    def train_step(self, x, P, pairs, lr=1e-3, weight_decay=1e-4, stream=None):
+        """One AdamW step on the pairs int32 [n][3] = (image, position p, position q); returns the loss tensor."""
+        im = images_of(x, P)
+        self.step_no += 1
+        wp, wn = _ws(self._workspace(im))
+        _check("glr_encoder_train_step", L.load().glr_encoder_train_step(
+            _ptr(x), ctypes.byref(im), _ptr(pairs), int(pairs.shape[0]), _ptr(self.params), _ptr(self.m), _ptr(self.v),
+            self.step_no, float(lr), float(weight_decay), _ptr(self.loss), wp, wn, _stream(stream)))
+        return self.loss
+
+
+def harvest_pairs(keys, n_found, idx, n_pairs, Hq, Wq, near_frac=0.75, generator=None):
+    """Training pairs from the matcher's own output: (image, key, one of its matches) for
+    near pairs and (image, key, random position) for the rest.  int32 [n_pairs][3] on the device."""
+    dev = keys.device
+    g = generator
+    n_img, N = keys.shape
+    K = idx.shape[2]
+    f = torch.randint(0, n_img, (n_pairs,), device=dev, generator=g)
+    k = torch.randint(0, N, (n_pairs,), device=dev, generator=g) % n_found.long()[f].clamp(min=1)
+    kq = keys.long()[f, k]
+    near = torch.rand(n_pairs, device=dev, generator=g) < near_frac
+    j = torch.randint(0, K, (n_pairs,), device=dev, generator=g)
+    q_near = idx.long()[f, k, j]
+    q_rand = torch.randint(0, Hq * Wq, (n_pairs,), device=dev, generator=g)
+    q = torch.where(near, q_near, q_rand)
+    return torch.stack([f, kq, q], 1).to(torch.int32).contiguous()
+
+
+def train_encoder(enc: Encoder, batches, steps=200, batch_pairs=32768, lr=2e-3, weight_decay=1e-4, seed=0):
+    """Train on pairs harvested from (x, P, keys, n_found, idx) batches; returns the loss history."""
+    gen = torch.Generator(device=batches[0][0].device)
+    gen.manual_seed(20230107 + seed)
+    hist = []
+    for s in range(steps):
+        x, P, keys, nf, idx = batches[s % len(batches)]
+        Hq, Wq = x.shape[2] - P + 1, x.shape[3] - P + 1
+        pairs = harvest_pairs(keys, nf, idx, batch_pairs, Hq, Wq, generator=gen)
+        lr_s = lr * 0.5 * (1.0 + math.cos(math.pi * s / steps))
+        hist.append(enc.train_step(x, P, pairs, lr=lr_s, weight_decay=weight_decay).item())
+    return hist

@@ -1,0 +1,94 @@
+"""Learned matching proposal on the GPU: encoder forward and training step against the
+FP64 oracle, and what training gains over the untrained encoder at the same candidate budget."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import encoder_oracle as E  # noqa: E402
+from oracle import glr_oracle as O  # noqa: E402
+from paper_2301_03047_gb300 import glr, synth  # noqa: E402
+
+
+def _params_dict(flat):
+    f = flat.astype(np.float64)
+    return {"W1": f[:4096].reshape(64, 64), "b1": f[4096:4160], "W2": f[4160:5184].reshape(16, 64), "b2": f[5184:5200]}
+
+
+def test_embed_matches_oracle_forward():
+    rng = synth.rng_for("enc-embed")
+    x = synth.textured_frames(rng, 2, 40, 44)[:, None]
+    enc = glr.Encoder(seed=3)
+    enc.params.add_(torch.randn_like(enc.params) * 0.05)  # non-zero biases too
+    emb = enc.embed(torch.from_numpy(x).cuda(), 8).cpu().numpy()
+    p16 = enc.params.cpu().numpy().astype(np.float16).astype(np.float64)  # inference rounds weights to FP16
+    for f in range(2):
+        mu = np.float32(np.float64(x[f]).mean())
+        Q = O.patch_matrix((x[f] - mu).astype(np.float32), 8)
+        want, _ = E.forward(_params_dict(p16), Q)
+        np.testing.assert_allclose(emb[f], want, rtol=1e-4, atol=1e-4)
+
+
+def test_train_step_loss_and_gradient_match_oracle():
+    rng = synth.rng_for("enc-train")
+    H, W, P = 36, 40, 8
+    x = synth.textured_frames(rng, 2, H, W)[:, None]
+    npos = (H - P + 1) * (W - P + 1)
+    n = 300
+    pairs = np.stack([rng.integers(0, 2, n), rng.integers(0, npos, n), rng.integers(0, npos, n)], 1).astype(np.int32)
+    enc = glr.Encoder(seed=5)
+    p0 = enc.params.cpu().numpy().copy()
+    loss = enc.train_step(torch.from_numpy(x).cuda(), P, torch.from_numpy(pairs).cuda(), lr=1e-3, weight_decay=0.0)
+    loss = float(loss.item())
+    Pm, Qm = [], []
+    for f, a, b in pairs:
+        mu = np.float32(np.float64(x[f]).mean())
+        Q = O.patch_matrix((x[f] - mu).astype(np.float32), P)
+        Pm.append(Q[a])
+        Qm.append(Q[b])
+    Pm, Qm = np.array(Pm), np.array(Qm)
+    d = ((Pm - Qm) ** 2).sum(1)
+    params = _params_dict(p0)
+    assert abs(loss - E.pair_loss(params, Pm, Qm, d)) <= 1e-4 * abs(E.pair_loss(params, Pm, Qm, d))
+    g = E.pair_loss_grad(params, Pm, Qm, d)
+    g_gpu = enc.m.cpu().numpy().astype(np.float64) / 0.1  # first Adam moment = (1 - beta1) g
+    g_or = np.concatenate([g["W1"].ravel(), g["b1"], g["W2"].ravel(), g["b2"]])
+    assert np.abs(g_gpu - g_or).max() <= 1e-3 * np.abs(g_or).max()
+    # the update itself: one AdamW step of the oracle from the same state
+    zeros = {k: np.zeros_like(v) for k, v in params.items()}
+    p1, _, _ = E.adamw_step(params, g, zeros, zeros, 1, lr=1e-3, wd=0.0)
+    want = np.concatenate([p1["W1"].ravel(), p1["b1"], p1["W2"].ravel(), p1["b2"]])
+    moved = np.abs(g_or) > 1e-3 * np.abs(g_or).max()  # sign of tiny gradients is rounding noise
+    np.testing.assert_allclose(enc.params.cpu().numpy()[moved], want[moved], atol=1e-6)
+
+
+def test_learned_proposal_recall_and_training_gain():
+    """Train on pairs harvested from exhaustive matches of some frames, evaluate on other frames:
+    recall of the exhaustive top-K within the learned candidates, trained vs untrained."""
+    cfg = synth.scaled(synth.SCI_SMALL, T=6, H=128, W=128, N=200, K=32)
+    prob = synth.sci_problem(cfg)
+    y = torch.from_numpy(prob.y).cuda()
+    m = torch.from_numpy(prob.masks).cuda()
+    rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode="bf16")
+    rec.start(y, m)
+    rec.step(cfg.sigma_schedule()[0], cfg.c_wnnm)
+    x = rec.x.view(cfg.T, 1, cfg.H, cfg.W).contiguous()
+    keys, nf, _ = glr.select_keys(x, cfg.P, cfg.N)
+    ref, _ = glr.match_topk(x, cfg.P, keys, nf, cfg.K, "bf16")
+    tr = slice(0, 4)
+    batches = [(x[tr].contiguous(), cfg.P, keys[tr].contiguous(), nf[tr].contiguous(), ref[tr].contiguous())]
+    enc0 = glr.Encoder(seed=1)
+    enc = glr.Encoder(seed=1)
+    hist = glr.train_encoder(enc, batches, steps=150, batch_pairs=8192)
+    assert hist[-1] < 0.5 * hist[0]
+    xe, ke, ne, re = x[4:].contiguous(), keys[4:].contiguous(), nf[4:].contiguous(), ref[4:].cpu().numpy()
+
+    def recall(e, n_cand):
+        idx, dist = glr.match_topk(xe, cfg.P, ke, ne, cfg.K, "learned", k_over=n_cand, encoder=e.params)
+        a = idx.cpu().numpy()
+        return np.mean([len(set(a[f, k]) & set(re[f, k])) / cfg.K for f in range(a.shape[0]) for k in range(a.shape[1])])
+
+    r_trained, r_untrained = recall(enc, 128), recall(enc0, 128)
+    assert r_trained > r_untrained + 0.05, (r_trained, r_untrained)
+    assert r_trained > 0.6, r_trained
