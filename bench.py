@@ -318,11 +318,11 @@ def run_glr(args) -> None:
         # autotune the matching schedule on the start image (set-up, untimed)
         x0 = glr.gap_step(y[None], masks, None).view(cfg.T, 1, cfg.H, cfg.W).contiguous()
         k0, n0, _ = glr.select_keys(x0, cfg.P, cfg.N, cfg.edge_th)
-        tuned[form] = glr.autotune_match(x0, cfg.P, k0, n0, cfg.K, form) if not args.no_tune else (0, 0, 0)
+        tuned[form] = glr.autotune_match(x0, cfg.P, k0, n0, cfg.K, form) if not args.no_tune else (0, 0, 0, 0)
         del x0, k0, n0
-        kover, splits, cap = tuned[form]
+        kover, splits, cap, eb = tuned[form]
         rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=form, edge_th=cfg.edge_th,
-                                   device=dev, k_over=kover, splits=splits, cap=cap)
+                                   device=dev, k_over=kover, splits=splits, cap=cap, epi_batch=eb)
         rec.start(y, masks)
         k = 0
         for _ in range(args.warmup):
@@ -467,7 +467,8 @@ def run_glr(args) -> None:
         "e2e": e2e,
         "clocks": clocks_summary,
     }
-    line["autotuned_match"] = {f: {"k_over": t[0], "splits": t[1], "cap": t[2]} for f, t in tuned.items()}
+    line["autotuned_match"] = {f: {"k_over": t[0], "splits": t[1], "cap": t[2], "epi_batch": t[3]}
+                               for f, t in tuned.items()}
     if "graph" in results:
         line["cuda_graph"] = {"value": round(results["graph"]["value"], 4), "unit": UNIT,
                               "ms_per_step": round(results["graph"]["ms_per_step"], 3)}

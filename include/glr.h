@@ -91,7 +91,9 @@ typedef struct glr_match_opts {
                      (> k_over, <= 512); 0 = automatic */
   const float* encoder; /* GLR_MATCH_LEARNED: device encoder parameters (GLR_ENCODER_PARAMS
                            floats); k_over = candidates per key (0 = 256) */
-  int32_t reserved[2];
+  int32_t epi_batch;    /* tensor-core epilogue: 32-column chunks read from tensor memory per
+                           visit, 2 or 4 (0 = 4) */
+  int32_t reserved;
 } glr_match_opts;
 
 /* Operation codes for glr_workspace_size. */

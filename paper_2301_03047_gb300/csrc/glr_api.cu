@@ -183,6 +183,7 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
   if (opts && (opts->k_over < 0 || opts->splits < 0 || opts->cap < 0 || (opts->k_over > 0 && opts->k_over < K)))
     return GLR_EINVAL;
   if (opts && opts->cap > 512) return GLR_ENOTSUP;
+  if (opts && opts->epi_batch != 0 && opts->epi_batch != 2 && opts->epi_batch != 4) return GLR_EINVAL;
   const MatchPlan pl = match_plan(*im, N, K, opts);
   if (pl.Kp > 256 || pl.Kp >= pl.cap) return GLR_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;

@@ -34,6 +34,7 @@ struct MatchPlan {
   int pos_tiles;        // position tiles per image
   int tiles_per_split;
   int dk;               // BF16 operand row length (elements)
+  int epi_batch;        // tensor-core epilogue: 32-column chunks read from TMEM per visit (2 or 4)
   long long npos_pad;   // BF16 position rows per image (pos_tiles * pos_tile)
   size_t mean_off, qn_off, keyv_off, buf_off, bufcnt_off, taugl_off, qpack_off, kpack_off, embp_off, embk_off, total;
 };

@@ -382,6 +382,7 @@ __global__ void __launch_bounds__(256) k_seed_bounds(const __nv_bfloat16* __rest
   }
 }
 
+template <int EB>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_match_tc(const __grid_constant__ CUtensorMap tm_qmain, const __grid_constant__ CUtensorMap tm_qaux,
                const __grid_constant__ CUtensorMap tm_kmain, const __grid_constant__ CUtensorMap tm_kaux,
@@ -514,35 +515,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const long long tile_q0 = (long long)(t_begin + i) * TC_N;
       const uint32_t gl = gl_next;
       gl_next = *reinterpret_cast<volatile uint32_t*>(pub_gl + lane);
-      float v[4][32];
-      {
-        const uint32_t taddr = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128);
-        tmem_ld_32x32_nowait(taddr, v[0]);
-        tmem_ld_32x32_nowait(taddr + 32, v[1]);
-        tmem_ld_32x32_nowait(taddr + 64, v[2]);
-        tmem_ld_32x32_nowait(taddr + 96, v[3]);
-        tmem_ld_wait();
-      }
-      // the accumulator is in registers: hand the TMEM buffer back to the MMA warp
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty + b);
+      // EB chunks of 32 columns are read from TMEM per visit; the buffer goes back to
+      // the MMA warp after the last visit (EB = 4: one visit, earliest release)
+#pragma unroll 1
+      for (int c0 = 0; c0 < 4; c0 += EB) {
+        float v[EB][32];
+        {
+          const uint32_t taddr =
+              tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128 + 32 * c0);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int col = h * 128 + c * 32;
-        const long long q0 = tile_q0 + col;
-        const int nvalid = (int)max(0LL, min(32LL, npos - q0));
-        if (dump != nullptr && i == 0 && t_begin == 0) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) dump[((long long)f * Npad + key) * TC_N + col + j] = v[c][j];
+          for (int c = 0; c < EB; ++c) tmem_ld_32x32_nowait(taddr + 32 * c, v[c]);
+          tmem_ld_wait();
         }
-        const float te = stream_tau_eff(tau, *reinterpret_cast<volatile uint32_t*>(pub_sh + lane), gl);
-        const unsigned rows = stream_filter(v[c], nvalid, te);
-        if (rows) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) wtile[lane * TILE_LD + j] = v[c][j];
+        if (c0 + EB >= 4) {
+          tc_fence_before();
           __syncwarp();
-          stream_append(rows, wtile, TILE_LD, (int)q0, nvalid, te, tau, cnt, mybuf, cfg, whist, pub_sh, pub_gl, stats);
+          if (lane == 0) mbar_arrive(tempty + b);
+        }
+#pragma unroll
+        for (int c = 0; c < EB; ++c) {
+          const int col = h * 128 + (c0 + c) * 32;
+          const long long q0 = tile_q0 + col;
+          const int nvalid = (int)max(0LL, min(32LL, npos - q0));
+          if (dump != nullptr && i == 0 && t_begin == 0) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) dump[((long long)f * Npad + key) * TC_N + col + j] = v[c][j];
+          }
+          const float te = stream_tau_eff(tau, *reinterpret_cast<volatile uint32_t*>(pub_sh + lane), gl);
+          const unsigned rows = stream_filter(v[c], nvalid, te);
+          if (rows) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) wtile[lane * TILE_LD + j] = v[c][j];
+            __syncwarp();
+            stream_append(rows, wtile, TILE_LD, (int)q0, nvalid, te, tau, cnt, mybuf, cfg, whist, pub_sh, pub_gl,
+                          stats);
+          }
         }
       }
     }
@@ -633,11 +640,12 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
       !make_map(&tk, kmain, krows, DK_MAIN, TC_M, CU_TENSOR_MAP_SWIZZLE_128B) ||
       !make_map(&tka, kaux, krows, DK_AUX, TC_M, CU_TENSOR_MAP_SWIZZLE_32B))
     return GLR_ECUDA;
-  if (cudaFuncSetAttribute(k_match_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) != cudaSuccess)
+  auto kern = pl.epi_batch == 2 ? k_match_tc<2> : k_match_tc<4>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) != cudaSuccess)
     return GLR_ECUDA;
   {
     int blocks_per_sm = 0;  // the kernel needs exactly one resident CTA per SM (all of TMEM)
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_match_tc, TC_THREADS, TC_SMEM) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, TC_THREADS, TC_SMEM) != cudaSuccess ||
         blocks_per_sm < 1)
       return GLR_ENOTSUP;
   }
@@ -645,7 +653,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   const StreamCfg cfg{pl.cap, pl.Kp};
   dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
   GLR_LAUNCH("k_match_tc", s,
-             k_match_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
+             kern<<<grid, TC_THREADS, TC_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
                                                           pl.splits, pl.tiles_per_split, pl.pos_tiles, cfg, bufs,
                                                           bufcnt, taugl, st, dump));
   return GLR_OK;

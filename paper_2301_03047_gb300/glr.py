@@ -52,11 +52,12 @@ def images_of(x: torch.Tensor, P: int) -> L.GlrImages:
 
 
 def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0, cap: int = 0,
-               encoder: torch.Tensor | None = None) -> L.GlrMatchOpts:
+               encoder: torch.Tensor | None = None, epi_batch: int = 0) -> L.GlrMatchOpts:
     m = {"fp32": L.GLR_MATCH_FP32, "bf16": L.GLR_MATCH_BF16, "learned": L.GLR_MATCH_LEARNED}.get(mode, mode)
     o = L.GlrMatchOpts()
     o.mode, o.k_over, o.splits, o.cap = int(m), int(k_over), int(splits), int(cap)
     o.encoder = _ptr(encoder) if encoder is not None else None
+    o.epi_batch = int(epi_batch)
     return o
 
 
@@ -98,13 +99,13 @@ def select_keys(x, P, N, edge_th=0.1, *, keys=None, n_found=None, n_corner=None,
     return keys, n_found, n_corner
 
 
-def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, cap=0, encoder=None, idx=None, dist=None,
-               ws=None, stream=None):
+def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, cap=0, encoder=None, epi_batch=0,
+               idx=None, dist=None, ws=None, stream=None):
     """Global matching with a fused running top-K (Eq. 1 over the whole image, Eq. 4 as a contraction)."""
     lib = L.load()
     im = images_of(x, P)
     N = keys.shape[1]
-    o = match_opts(mode, k_over, splits, cap, encoder)
+    o = match_opts(mode, k_over, splits, cap, encoder, epi_batch)
     dev = x.device
     if idx is None:
         idx = torch.empty((x.shape[0], N, K), dtype=torch.int32, device=dev)
@@ -241,11 +242,11 @@ class GlrDenoiser:
     """Select -> match -> low-rank -> aggregate on fixed-size images, with preallocated buffers."""
 
     def __init__(self, shape: GlrShape, mode: str = "bf16", edge_th: float = 0.1, k_over: int = 0, splits: int = 0,
-                 device="cuda", cap: int = 0):
+                 device="cuda", cap: int = 0, epi_batch: int = 0):
         s = shape
         self.shape, self.mode, self.edge_th = s, mode, edge_th
-        self.opts = match_opts(mode, k_over, splits, cap)
-        self.k_over, self.splits, self.cap = k_over, splits, cap
+        self.opts = match_opts(mode, k_over, splits, cap, None, epi_batch)
+        self.k_over, self.splits, self.cap, self.epi_batch = k_over, splits, cap, epi_batch
         im = images(s.n_img, s.C, s.H, s.W, s.P)
         dev = torch.device(device)
         d = s.C * s.P * s.P
@@ -267,7 +268,8 @@ class GlrDenoiser:
         select_keys(x, s.P, s.N, self.edge_th, keys=self.keys, n_found=self.n_found, n_corner=self.n_corner,
                     ws=self.ws_select, stream=stream)
         match_topk(x, s.P, self.keys, self.n_found, s.K, self.mode, k_over=self.k_over, splits=self.splits,
-                   cap=self.cap, idx=self.idx, dist=self.dist, ws=self.ws_match, stream=stream)
+                   cap=self.cap, epi_batch=self.epi_batch, idx=self.idx, dist=self.dist, ws=self.ws_match,
+                   stream=stream)
         lowrank_groups(x, s.P, self.idx, self.n_found, sigma_w, c_wnnm, groups=self.groups, rank=self.rank,
                        ws=self.ws_lowrank, stream=stream)
         return aggregate(self.groups, self.idx, self.n_found, x, s.P, out=out, ws=self.ws_agg, stream=stream)
@@ -277,9 +279,9 @@ class SciReconstructor:
     """GAP + GLR for one video snapshot y = sum_t M_t x_t (Eq. 6); frames are the images."""
 
     def __init__(self, T, H, W, P, N, K, mode="bf16", edge_th=0.1, accelerate=False, k_over=0, splits=0,
-                 device="cuda", cap=0):
+                 device="cuda", cap=0, epi_batch=0):
         self.T, self.H, self.W = T, H, W
-        self.den = GlrDenoiser(GlrShape(T, 1, H, W, P, N, K), mode, edge_th, k_over, splits, device, cap)
+        self.den = GlrDenoiser(GlrShape(T, 1, H, W, P, N, K), mode, edge_th, k_over, splits, device, cap, epi_batch)
         self.accelerate = accelerate
         self.x = torch.empty((1, T, H, W), dtype=torch.float32, device=device)
         self.v = torch.empty_like(self.x)
@@ -342,7 +344,7 @@ _TUNE_CACHE: dict = {}
 
 
 def autotune_match(x, P, keys, n_found, K, mode="bf16", candidates=None, repeats=2, cache_path=None):
-    """Return the fastest (k_over, splits, cap) for this shape; K' stays >= K + 16."""
+    """Return the fastest (k_over, splits, cap, epi_batch) for this shape; K' stays >= K + 16."""
     import json
     import os
 
@@ -352,27 +354,29 @@ def autotune_match(x, P, keys, n_found, K, mode="bf16", candidates=None, repeats
     if shape_key in _TUNE_CACHE:
         return tuple(_TUNE_CACHE[shape_key])
     if candidates is None:
-        candidates = [(K + 16, sp, cap) for sp in (1, 2, 3) for cap in (0, 192, 320)]
+        eb = (2, 4) if mode != "fp32" else (0,)
+        candidates = [(K + 16, sp, cap, e) for sp in (1, 2, 3) for cap in (0, 192, 320) for e in eb]
+    candidates = [tuple(c) + (0,) * (4 - len(c)) for c in candidates]
     im = images_of(x, P)
     best, best_t = None, float("inf")
     kname = "k_match_tc" if mode == "bf16" else "k_match_fp32"
-    for kover, sp, cap in candidates:
-        o = match_opts(mode, kover, sp, cap)
+    for kover, sp, cap, eb in candidates:
+        o = match_opts(mode, kover, sp, cap, None, eb)
         try:
             ws = workspace(L.GLR_OP_MATCH, im, keys.shape[1], K, o, x.device)
-            match_topk(x, P, keys, n_found, K, mode, k_over=kover, splits=sp, cap=cap, ws=ws)
+            match_topk(x, P, keys, n_found, K, mode, k_over=kover, splits=sp, cap=cap, epi_batch=eb, ws=ws)
         except GlrError:
             continue
         torch.cuda.synchronize()
         profile_enable(True)
         profile_collect()
         for _ in range(repeats):
-            match_topk(x, P, keys, n_found, K, mode, k_over=kover, splits=sp, cap=cap, ws=ws)
+            match_topk(x, P, keys, n_found, K, mode, k_over=kover, splits=sp, cap=cap, epi_batch=eb, ws=ws)
         prof = profile_collect()
         profile_enable(False)
-        t = sum(v[0] for k, v in prof.items() if k in (kname, "k_rerank"))
+        t = sum(v[0] for k, v in prof.items() if k in (kname, "k_rerank", "k_seed_bounds"))
         if t < best_t:
-            best, best_t = (kover, sp, cap), t
+            best, best_t = (kover, sp, cap, eb), t
         del ws
     _TUNE_CACHE[shape_key] = list(best)
     if cache_path:

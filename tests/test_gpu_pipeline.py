@@ -39,10 +39,12 @@ def test_autotune_picks_a_working_schedule():
     cfg, prob, y, m = _problem(T=2, H=128, W=128, N=200, K=32)
     x = glr.gap_step(y[None], m, None).view(cfg.T, 1, cfg.H, cfg.W).contiguous()
     keys, nf, _ = glr.select_keys(x, cfg.P, cfg.N)
-    best = glr.autotune_match(x, cfg.P, keys, nf, cfg.K, "bf16", candidates=[(48, 1, 0), (48, 2, 192), (64, 1, 320)])
-    assert best in [(48, 1, 0), (48, 2, 192), (64, 1, 320)]
+    cands = [(48, 1, 0, 4), (48, 2, 192, 2), (64, 1, 320, 4)]
+    best = glr.autotune_match(x, cfg.P, keys, nf, cfg.K, "bf16", candidates=cands)
+    assert best in cands
     ref, _ = glr.match_topk(x, cfg.P, keys, nf, cfg.K, "fp32")
-    got, _ = glr.match_topk(x, cfg.P, keys, nf, cfg.K, "bf16", k_over=best[0], splits=best[1], cap=best[2])
+    got, _ = glr.match_topk(x, cfg.P, keys, nf, cfg.K, "bf16", k_over=best[0], splits=best[1], cap=best[2],
+                            epi_batch=best[3])
     a, b = ref.cpu().numpy(), got.cpu().numpy()
     same = np.mean([len(set(a[f, k]) & set(b[f, k])) / cfg.K for f in range(cfg.T) for k in range(cfg.N)])
     assert same >= 0.99
