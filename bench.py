@@ -529,7 +529,7 @@ def run_reference(args) -> None:
 def main() -> None:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="glr", choices=["glr", "reference"])
     ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32"])

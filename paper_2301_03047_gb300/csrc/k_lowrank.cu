@@ -60,11 +60,15 @@ __global__ void __launch_bounds__(256) k_gather(const float* __restrict__ x, int
 // changes them: alpha - t gamma, beta + t gamma); only gamma = a.b is summed.
 template <int DMAX>
 __device__ __forceinline__ void jacobi_pair(float (&a)[DMAX], float (&b)[DMAX], float& alpha, float& beta, float tol,
-                                            float lam_skip, bool active, bool& rotated) {
+                                            float lam_skip, float lam, float& acc_a, float& acc_b, bool active,
+                                            bool& rotated) {
   float ga[4] = {0.f, 0.f, 0.f, 0.f};  // four partial sums shorten the dependency chain
 #pragma unroll
   for (int r = 0; r < DMAX; ++r) ga[r & 3] = fmaf(a[r], b[r], ga[r & 3]);
   const float gamma = (ga[0] + ga[1]) + (ga[2] + ga[3]);
+  // Gershgorin sums of the block of columns below lam (see the sweep loop)
+  if (beta < lam) acc_a += fabsf(gamma);
+  if (alpha < lam) acc_b += fabsf(gamma);
   // pairs of columns that are both below lam_skip are left alone (see the sweep loop)
   if (active && fabsf(gamma) > tol * sqrtf(alpha * beta) && gamma != 0.f && (alpha >= lam_skip || beta >= lam_skip)) {
     const float zeta = __fdividef(beta - alpha, 2.f * gamma);
@@ -95,7 +99,7 @@ __device__ __forceinline__ float sq_norm(const float (&a)[DMAX]) {
 
 // DMAX rows per column, KMAX <= 64 columns, one warp per group, WARPS groups per CTA.
 template <int DMAX, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 2) k_jacobi_wnnm(int n_img, int d, int N, int K,
+__global__ void __launch_bounds__(WARPS * 32, 3) k_jacobi_wnnm(int n_img, int d, int N, int K,
                                                             const int32_t* __restrict__ n_found, float sigma_w,
                                                             float c_wnnm, float tol, int max_sweeps,
                                                             float* __restrict__ groups, int32_t* __restrict__ rank,
@@ -133,6 +137,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_jacobi_wnnm(int n_img, int d,
     // them can reach it, so rotations among them cannot change X^ and are skipped
     // (decided per sweep; a sweep without rotations ends the iteration).
     const float lam = (float)K * sigma_w * sigma_w;
+    bool gersh_ok = false;
     // Parallel ordering by recursive halving (32 lanes, 64 column slots): at a
     // level with lane groups of size g, the B columns shift cyclically inside
     // each group for g rounds, so every A meets every B of its group; then each
@@ -146,7 +151,12 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_jacobi_wnnm(int n_img, int d,
       float small = (alpha < lam ? alpha : 0.f) + (beta < lam ? beta : 0.f);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) small += __shfl_xor_sync(0xffffffffu, small, o);
-      const float lam_skip = (lam > 0.f && small < lam) ? lam : 0.f;
+      // skip pairs inside the below-lam block when no combination of its columns can
+      // reach lam: its total is below lam, or the previous sweep's Gershgorin bound
+      // (norm^2 + sum of |a.b| over block partners, largest over the block) was
+      // below lam / 2
+      const float lam_skip = (lam > 0.f && (small < lam || gersh_ok)) ? lam : 0.f;
+      float acc_a = 0.f, acc_b = 0.f;
 #pragma unroll 1
       for (int g = 32; g >= 1; g >>= 1) {
         if (g < 32) {
@@ -160,24 +170,33 @@ __global__ void __launch_bounds__(WARPS * 32, 2) k_jacobi_wnnm(int n_img, int d,
               a[r] = recv;
           }
           const float rn = __shfl_xor_sync(0xffffffffu, first ? beta : alpha, g);
-          if (first)
+          const float ra = __shfl_xor_sync(0xffffffffu, first ? acc_b : acc_a, g);
+          if (first) {
             beta = rn;
-          else
+            acc_b = ra;
+          } else {
             alpha = rn;
+            acc_a = ra;
+          }
         }
         const int src = (lane & ~(g - 1)) | ((lane + 1) & (g - 1));
 #pragma unroll 1
         for (int rd = 0; rd < g; ++rd) {
-          jacobi_pair<DMAX>(a, b, alpha, beta, tol, lam_skip, live, rotated);
+          jacobi_pair<DMAX>(a, b, alpha, beta, tol, lam_skip, lam, acc_a, acc_b, live, rotated);
           if (rd + 1 < g) {
 #pragma unroll
             for (int r = 0; r < DMAX; ++r) b[r] = __shfl_sync(0xffffffffu, b[r], src);
             beta = __shfl_sync(0xffffffffu, beta, src);
+            acc_b = __shfl_sync(0xffffffffu, acc_b, src);
           }
         }
       }
       ++sweep;
       converged = !__any_sync(0xffffffffu, rotated);
+      float gb = fmaxf(alpha < lam ? alpha + acc_a : 0.f, beta < lam ? beta + acc_b : 0.f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) gb = fmaxf(gb, __shfl_xor_sync(0xffffffffu, gb, o));
+      gersh_ok = gb < 0.5f * lam;
     }
     if (!converged && lane == 0) {
       atomicAdd(&st->svd_noconv, 1u);
