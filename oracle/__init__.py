@@ -5,3 +5,4 @@ benchmark's CPU-baseline leg are its only users.  The library never imports
 it and shares no code with it.
 """
 from . import glr_oracle  # noqa: F401
+from . import mri_oracle  # noqa: F401

@@ -235,3 +235,114 @@ def textured_frames(rng: np.random.Generator, F: int, H: int, W: int) -> np.ndar
     for f in range(F):
         out[f] = render_scene(rng, 1, H, W)[0]
     return out
+
+
+# ----------------------------------------------------------------------------
+# MRI: complex images, Cartesian variable-density k-space sampling (Section 3, MRI)
+# ----------------------------------------------------------------------------
+@dataclass(frozen=True)
+class MriConfig:
+    """A Fourier-domain compressive-imaging workload y = M F(x) (the paper's MRI model)."""
+
+    name: str
+    config_no: int
+    H: int
+    W: int
+    P: int  # patch side (complex patches: d = 2 P^2 real values)
+    N: int  # key patches
+    K: int  # matches per key
+    iters: int  # ADMM iterations
+    line_frac: float = 0.2  # fraction of k-space rows sampled
+    centre_lines: int = 32  # fully sampled low-frequency rows
+    noise_sigma: float = 0.005  # std of the real and of the imaginary part of the k-space noise
+    rho: float = 0.5  # ADMM penalty
+    sigma_first: float = 0.5
+    sigma_last: float = 0.02
+    edge_th: float = 0.1
+
+    @property
+    def c_wnnm(self) -> float:
+        return 2.0 * math.sqrt(self.K)
+
+    def sigma_schedule(self) -> list[float]:
+        if self.iters == 1:
+            return [self.sigma_last]
+        r = (self.sigma_last / self.sigma_first) ** (1.0 / (self.iters - 1))
+        return [float(self.sigma_first * r**k) for k in range(self.iters)]
+
+
+MRI_SMALL = MriConfig("mri_96x96_P6_N128_K24", 3, H=96, W=96, P=6, N=128, K=24, iters=3, centre_lines=8)
+MRI_LARGE = MriConfig("mri_1024x1024_P6_N8192_K48", 3, H=1024, W=1024, P=6, N=8192, K=48, iters=30)
+
+
+def mri_scaled(cfg: MriConfig, *, H=None, W=None, N=None, K=None, iters=None, centre_lines=None, name=None) -> MriConfig:
+    return MriConfig(
+        name or cfg.name + "_scaled", cfg.config_no, H=H or cfg.H, W=W or cfg.W, P=cfg.P, N=N or cfg.N,
+        K=K or cfg.K, iters=iters or cfg.iters, line_frac=cfg.line_frac,
+        centre_lines=centre_lines or cfg.centre_lines, noise_sigma=cfg.noise_sigma, rho=cfg.rho,
+        sigma_first=cfg.sigma_first, sigma_last=cfg.sigma_last, edge_th=cfg.edge_th)
+
+
+def complex_phantom(rng: np.random.Generator, H: int, W: int) -> np.ndarray:
+    """Complex image [2][H][W] (real plane, imaginary plane), float32.
+
+    Magnitude: 12-20 random ellipses whose intensities add (each in [0.1, 0.5])
+    over band-limited texture of amplitude 0.03, clipped to [0, 1]; phase: a
+    random quadratic polynomial of the normalised coordinates (|coefficients|
+    <= pi/4)."""
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    u = 2.0 * xx / max(W - 1, 1) - 1.0
+    v = 2.0 * yy / max(H - 1, 1) - 1.0
+    mag = np.zeros((H, W))
+    for _ in range(int(rng.integers(12, 21))):
+        cx, cy = rng.uniform(-0.7, 0.7, 2)
+        ax, ay = rng.uniform(0.08, 0.5, 2)
+        th = rng.uniform(0, math.pi)
+        ct, st = math.cos(th), math.sin(th)
+        xr = (u - cx) * ct + (v - cy) * st
+        yr = -(u - cx) * st + (v - cy) * ct
+        mag[(xr / ax) ** 2 + (yr / ay) ** 2 <= 1.0] += rng.uniform(0.1, 0.5)
+    tex = _lowpass_noise(rng, H, W, 2.0)
+    tex = tex / max(np.abs(tex).max(), 1e-12) * 0.03
+    mag = np.clip(mag + tex, 0.0, 1.0)
+    c = rng.uniform(-math.pi / 4, math.pi / 4, 6)
+    phase = c[0] + c[1] * u + c[2] * v + c[3] * u * u + c[4] * u * v + c[5] * v * v
+    return np.stack([mag * np.cos(phase), mag * np.sin(phase)]).astype(np.float32)
+
+
+def cartesian_mask(rng: np.random.Generator, H: int, W: int, frac: float, centre: int) -> np.ndarray:
+    """0/1 k-space mask [H][W] (float32) of whole rows, in the unshifted FFT layout
+    (row k holds frequency k for k < H/2 and k - H otherwise).  The `centre`
+    lowest frequencies are always taken; the other rows are drawn without
+    replacement with probability proportional to (1 - |k| / (H/2))^2 until
+    round(frac * H) rows are chosen."""
+    freq = np.where(np.arange(H) < H // 2, np.arange(H), np.arange(H) - H)
+    chosen = np.abs(freq + 0.5) < centre / 2.0
+    n_more = max(int(round(frac * H)) - int(chosen.sum()), 0)
+    pdf = (1.0 - np.abs(freq) / (H / 2.0)) ** 2
+    pdf[chosen] = 0.0
+    pdf /= pdf.sum()
+    pick = rng.choice(H, size=n_more, replace=False, p=pdf)
+    chosen[pick] = True
+    return np.repeat(chosen[:, None], W, axis=1).astype(np.float32)
+
+
+@dataclass
+class MriProblem:
+    cfg: MriConfig
+    truth: np.ndarray  # [2][H][W] float32 (real, imaginary planes)
+    mask: np.ndarray  # [H][W] float32 (0/1)
+    y: np.ndarray  # [2][H][W] float32 k-space measurement (zero off the mask)
+
+
+def mri_problem(cfg: MriConfig, extra: int = 0) -> MriProblem:
+    """Synthetic scan: y = M (F x + n), F the orthonormal 2-D DFT (unshifted),
+    n complex Gaussian with std noise_sigma per real component (the MRI model
+    of Section 3)."""
+    rs, rm, rn = streams(cfg.config_no, extra)
+    truth = complex_phantom(rs, cfg.H, cfg.W)
+    mask = cartesian_mask(rm, cfg.H, cfg.W, cfg.line_frac, cfg.centre_lines)
+    k = np.fft.fft2(truth[0].astype(np.float64) + 1j * truth[1].astype(np.float64), norm="ortho")
+    k = k + cfg.noise_sigma * (rn.standard_normal(k.shape) + 1j * rn.standard_normal(k.shape))
+    k = k * mask
+    return MriProblem(cfg, truth, mask, np.stack([k.real, k.imag]).astype(np.float32))
