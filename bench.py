@@ -87,11 +87,11 @@ def oracle_sample(n_keys: int = 24) -> dict:
     }
 
 
-def run_oracle_child(n_keys: int) -> dict:
+def run_oracle_child(n_keys: int, fn: str = "oracle_sample") -> dict:
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
-    code = f"import json,sys; sys.path.insert(0,{ROOT!r}); import bench; print(json.dumps(bench.oracle_sample({n_keys})))"
+    code = f"import json,sys; sys.path.insert(0,{ROOT!r}); import bench; print(json.dumps(bench.{fn}({n_keys})))"
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError("oracle child failed: " + r.stderr[-2000:])
@@ -208,6 +208,8 @@ def kernel_hash(fname: str) -> str:
 
 
 KERNEL_FILE = {"k_match_tc": "k_match_tc.cu", "k_match_fp32": "k_match.cu", "k_jacobi_wnnm": "k_lowrank.cu",
+               "k_jacobi_smem": "k_lowrank_wide.cu", "k_jacobi_wnnm_c": "k_lowrank.cu", "k_fft_rows": "k_fft.cu",
+               "k_fft_cols": "k_fft.cu",
                "k_gather": "k_lowrank.cu", "k_scatter": "k_aggregate.cu", "k_gap_step": "k_gap.cu",
                "k_rerank": "k_match.cu"}
 
@@ -223,12 +225,14 @@ def traffic_for(kernel: str, units_per_launch: float):
     return d["dram_bytes_per_unit"] * units_per_launch
 
 
-def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict) -> dict:
+def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict, n_img: int | None = None,
+             d: int | None = None) -> dict:
     """Roofline entry of the kernel with the largest share of the timed region."""
     name, (ms, n) = max(prof.items(), key=lambda kv: kv[1][0])
     avg_s = ms / n / 1e3
-    T, H, W, P, N, K = cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K
-    d = P * P
+    T = n_img if n_img is not None else cfg.T
+    H, W, P, N, K = cfg.H, cfg.W, cfg.P, cfg.N, cfg.K
+    d = d if d is not None else P * P
     npos = (H - P + 1) * (W - P + 1)
     sm = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     if name in ("k_match_tc", "k_match_fp32"):
@@ -242,9 +246,10 @@ def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict) -
                    "peak_note": f"derived FP32 FMA peak 152x128x2 at {sm:.0f} MHz"}
         achieved = work / avg_s / 1e12
         unit_name = "pairs"
-    elif name == "k_jacobi_wnnm":
+    elif name in ("k_jacobi_wnnm", "k_jacobi_smem", "k_jacobi_wnnm_c"):
         units = T * N
-        work = units * sweeps_per_group * 6.0 * d * K * K
+        # complex columns: a complex multiply-add is 4 real ones on 2 real values, twice the real count per value
+        work = units * sweeps_per_group * 6.0 * d * K * K * (2.0 if name == "k_jacobi_wnnm_c" else 1.0)
         achieved = work / avg_s / 1e12
         out = {"bound": "alu", "peak": round(fp32_alu_peak_tflops(sm), 1), "unit": "TFLOP/s",
                "peak_note": f"derived FP32 FMA peak 152x128x2 at {sm:.0f} MHz; work = 6 d K^2 per sweep x measured sweeps"}
@@ -281,6 +286,10 @@ def workload(name: str):
         return synth.scaled(synth.SCI_LARGE, T=4, name="sci_4x512x512_P8_N4096_K64")
     if name == "sci8":
         return synth.SCI_SMALL
+    if name == "mri1024":
+        return synth.MRI_LARGE
+    if name == "mri256":  # profiling case of the MRI path
+        return synth.mri_scaled(synth.MRI_LARGE, H=256, W=256, N=2048, name="mri_256x256_P6_N2048_K48")
     raise ValueError(name)
 
 
@@ -299,6 +308,8 @@ def run_glr(args) -> None:
     from paper_2301_03047_gb300 import glr, synth
 
     cfg = workload(args.workload)
+    if isinstance(cfg, synth.MriConfig):
+        return run_mri(args, cfg, dev, dist)
     prob = synth.sci_problem(cfg)
     y = torch.from_numpy(prob.y).to(dev)
     masks = torch.from_numpy(prob.masks).to(dev)
@@ -369,11 +380,10 @@ def run_glr(args) -> None:
         results[form] = {"total_s": total_s, "ms_per_step": total_s / args.steps * 1e3, "step_ms": step_ms,
                          "psnr": O.psnr_framewise(x, prob.truth), "iters": k}
         if headline and not args.no_graph:
-            # the same iterations replayed from CUDA graphs (one per noise level)
+            # the same noise levels as the eager timing, replayed from CUDA graphs (one per level)
             rec.capture(sched, cfg.c_wnnm)
             for i in range(args.warmup):
-                rec.step_graph(sched[(k + i) % len(sched)])
-            k += args.warmup
+                rec.step_graph(sched[i % len(sched)])
             gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
             if dist is not None:
                 dist.barrier()
@@ -381,9 +391,8 @@ def run_glr(args) -> None:
             for i in range(args.steps):
                 flush.zero_()
                 gev[i][0].record()
-                rec.step_graph(sched[k % len(sched)])
+                rec.step_graph(sched[(args.warmup + i) % len(sched)])
                 gev[i][1].record()
-                k += 1
             torch.cuda.synchronize()
             g_s = reduce_max(sum(a.elapsed_time(b) for a, b in gev) / 1e3, dist, dev)
             results["graph"] = {"ms_per_step": g_s / args.steps * 1e3, "value": ws * args.steps / g_s}
@@ -482,6 +491,212 @@ def run_glr(args) -> None:
     print(json.dumps(line))
 
 
+MRI_METRIC = "GLR ADMM iterations/s on Fourier-domain (MRI) reconstruction (chosen BF16 form; plain FP32 alongside)"
+
+
+def oracle_sample_mri(n_keys: int = 8) -> dict:
+    import numpy as np
+
+    from oracle import glr_oracle as O
+    from oracle import mri_oracle as MO
+    from paper_2301_03047_gb300 import synth
+
+    cfg = synth.MRI_LARGE
+    prob = synth.mri_problem(cfg)
+    sw = cfg.sigma_schedule()[0]
+    y = MO.planes_to_complex(prob.y)
+    x = MO.complex_to_planes(MO.ifft2c(y))
+    t0 = time.perf_counter()
+    keys, _ = O.select_keys(x, cfg.P, cfg.N, cfg.edge_th)
+    t_select = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Q = O.patch_matrix(x, cfg.P)
+    t_q = time.perf_counter() - t0
+    sample = keys[:n_keys]
+    t0 = time.perf_counter()
+    idx, _ = O.match_topk(x, cfg.P, sample, cfg.K, Q)
+    t_match = (time.perf_counter() - t0) / n_keys
+    t0 = time.perf_counter()
+    g = O.gather_groups(x, cfg.P, idx, Q)
+    xh, _ = MO.lowrank_groups_complex(g, sw, cfg.c_wnnm)
+    t_low = (time.perf_counter() - t0) / n_keys
+    t0 = time.perf_counter()
+    O.aggregate(xh, idx, x, cfg.P)
+    t_agg = (time.perf_counter() - t0) / n_keys
+    t0 = time.perf_counter()
+    MO.admm_dc(y, prob.mask, MO.planes_to_complex(x), cfg.rho)
+    t_dc = time.perf_counter() - t0
+    t_iter = t_select + t_q + cfg.N * (t_match + t_low + t_agg) + t_dc
+    npos = (cfg.H - cfg.P + 1) * (cfg.W - cfg.P + 1)
+    return {
+        "t_iter_s": t_iter,
+        "iters_per_s": 1.0 / t_iter,
+        "pair_dists_per_s": npos / t_match,
+        "sample": f"full key selection + {n_keys} of {cfg.N} keys matched over all {npos} positions, grouped, "
+        f"complex WNNM, aggregated; one data-consistency step; extrapolated linearly to {cfg.N} keys",
+    }
+
+
+def run_mri(args, cfg, dev, dist) -> None:
+    import numpy as np
+    import torch
+
+    from paper_2301_03047_gb300 import glr, synth
+
+    ws, rank, local = dist_info()
+    prob = synth.mri_problem(cfg)
+    y = torch.from_numpy(prob.y).to(dev)
+    mask = torch.from_numpy(prob.mask).to(dev)
+    gt = prob.truth[0].astype(np.float64) + 1j * prob.truth[1]
+    sched = cfg.sigma_schedule()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    pk = peaks()
+    forms = [args.mode] + (["fp32"] if args.mode != "fp32" and not args.no_plain else [])
+    results, tuned = {}, {}
+    prof = clocks_summary = stream_stats = None
+    sweeps, launches = 0.0, 0
+
+    def psnr(rec):
+        x = rec.x.cpu().numpy()[0]
+        return 10.0 * math.log10(1.0 / float(np.mean(np.abs(x[0] + 1j * x[1] - gt) ** 2)))
+
+    for form in forms:
+        x0 = glr.fft2(y[None], inverse=True)
+        k0, n0, _ = glr.select_keys(x0, cfg.P, cfg.N, cfg.edge_th)
+        tuned[form] = glr.autotune_match(x0, cfg.P, k0, n0, cfg.K, form) if not args.no_tune else (0, 0, 0, 0)
+        del x0, k0, n0
+        kover, splits, cap, eb = tuned[form]
+        rec = glr.MriReconstructor(cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=form, edge_th=cfg.edge_th, rho=cfg.rho,
+                                   device=dev, k_over=kover, splits=splits, cap=cap, epi_batch=eb)
+        rec.start(y, mask)
+        k = 0
+        for _ in range(args.warmup):
+            rec.step(sched[k % len(sched)], cfg.c_wnnm)
+            k += 1
+        torch.cuda.synchronize()
+        headline = form == forms[0]
+        if headline:
+            glr.profile_enable(True)
+            glr.profile_collect()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = glr.launch_count()
+        clk = Clocks(local) if headline else None
+        if clk:
+            clk.__enter__()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record()
+            rec.step(sched[k % len(sched)], cfg.c_wnnm)
+            ev[i][1].record()
+            k += 1
+        torch.cuda.synchronize()
+        if clk:
+            clk.__exit__()
+            clocks_summary = clk.summary()
+        if dist is not None:
+            dist.barrier()
+        total_s = reduce_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, dist, dev)
+        if headline:
+            launches = glr.launch_count() - l0
+            prof = glr.profile_collect()
+            glr.profile_enable(False)
+            _, cnt = glr.poll_status(rec.den.ws_lowrank)
+            sweeps = cnt[2] / max(cnt[3], 1)
+            _, mcnt = glr.poll_status(rec.den.ws_match)
+            stream_stats = {"appends_per_key": round(mcnt[4] / cfg.N, 1),
+                            "compactions_per_key": round(mcnt[5] / cfg.N, 2)}
+        results[form] = {"total_s": total_s, "ms_per_step": total_s / args.steps * 1e3, "psnr": psnr(rec),
+                         "residual": float(rec.residual[0])}
+        if headline and not args.no_graph:
+            # the same noise levels as the eager timing, replayed from CUDA graphs (one per level)
+            rec.capture(sched, cfg.c_wnnm)
+            for i in range(args.warmup):
+                rec.step_graph(sched[i % len(sched)])
+            gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            for i in range(args.steps):
+                flush.zero_()
+                gev[i][0].record()
+                rec.step_graph(sched[(args.warmup + i) % len(sched)])
+                gev[i][1].record()
+            torch.cuda.synchronize()
+            g_s = reduce_max(sum(a.elapsed_time(b) for a, b in gev) / 1e3, dist, dev)
+            results["graph"] = {"ms_per_step": g_s / args.steps * 1e3, "value": ws * args.steps / g_s}
+        del rec
+        torch.cuda.empty_cache()
+
+    head = results[forms[0]]
+    e2e = None
+    if not args.no_e2e:
+        y_h = torch.from_numpy(prob.y).pin_memory()
+        m_h = torch.from_numpy(prob.mask).pin_memory()
+        x_h = torch.empty((1, 2, cfg.H, cfg.W), dtype=torch.float32).pin_memory()
+        rec = glr.MriReconstructor(cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=forms[0], edge_th=cfg.edge_th,
+                                   rho=cfg.rho, device=dev)
+        y_d, m_d = torch.empty_like(y), torch.empty_like(mask)
+        y_d.copy_(y_h, non_blocking=True)
+        m_d.copy_(m_h, non_blocking=True)
+        rec.start(y_d, m_d)
+        for i in range(args.warmup):
+            rec.step(sched[i % len(sched)], cfg.c_wnnm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            y_d.copy_(y_h, non_blocking=True)
+            m_d.copy_(m_h, non_blocking=True)
+            rec.step(sched[i % len(sched)], cfg.c_wnnm)
+            x_h.copy_(rec.x, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
+        e2e = {"value": round(ws * args.steps / e2e_s, 4), "unit": UNIT,
+               "h2d_bytes_per_step": int(y_h.numel() * 4 + m_h.numel() * 4), "d2h_bytes_per_step": int(x_h.numel() * 4)}
+        del rec
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu:
+        try:
+            o = run_oracle_child(args.oracle_keys, "oracle_sample_mri")
+            cpu = {"value": round(o["iters_per_s"], 8), "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": o["sample"], "t_iter_s": round(o["t_iter_s"], 1)}
+        except Exception as e:
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+    npos = (cfg.H - cfg.P + 1) * (cfg.W - cfg.P + 1)
+    rl = roofline(prof, cfg, sweeps, clocks_summary or {}, pk, n_img=1, d=2 * cfg.P * cfg.P) if prof else None
+    line = {
+        "metric": MRI_METRIC, "value": round(ws * args.steps / head["total_s"], 4), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms_per_step"], 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if forms[0] == "bf16" else "f32",
+        "data": "synthetic (seeded complex ellipse phantom, Cartesian variable-density k-space rows)",
+        "config": {"workload": cfg.name, "H": cfg.H, "W": cfg.W, "P": cfg.P, "d": 2 * cfg.P * cfg.P, "N": cfg.N,
+                   "K": cfg.K, "rho": cfg.rho, "positions": npos, "match_form": forms[0],
+                   "parallelism": f"replicas x{ws}", "l2": "flushed (256 MB write) between timed steps"},
+        "pair_dists_per_s": round(ws * cfg.N * npos * args.steps / head["total_s"], 1),
+        "psnr_db": round(head["psnr"], 3), "dc_residual": head["residual"], "gpu_launches": launches,
+        "kernels": {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches": v[1]}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])} if prof else {},
+        "svd_sweeps_per_group": round(sweeps, 2), "topk_streams": stream_stats, "roofline": rl,
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks_summary,
+        "autotuned_match": {f: {"k_over": t[0], "splits": t[1], "cap": t[2], "epi_batch": t[3]} for f, t in tuned.items()},
+    }
+    if "graph" in results:
+        line["cuda_graph"] = {"value": round(results["graph"]["value"], 4), "unit": UNIT,
+                              "ms_per_step": round(results["graph"]["ms_per_step"], 3)}
+    if len(forms) > 1:
+        pl = results["fp32"]
+        line["plain"] = {"value": round(ws * args.steps / pl["total_s"], 4), "unit": UNIT,
+                         "ms_per_step": round(pl["ms_per_step"], 3), "psnr_db": round(pl["psnr"], 3)}
+        line["speedup_vs_plain"] = round(pl["total_s"] / head["total_s"], 3)
+        line["delta_psnr_db"] = round(head["psnr"] - pl["psnr"], 4)
+    print(json.dumps(line))
+
+
 def run_reference(args) -> None:
     ws, rank, _ = dist_info()
     if rank != 0:
@@ -534,8 +749,9 @@ def main() -> None:
     ap.add_argument("--impl", default="glr", choices=["glr", "reference"])
     ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--oracle-keys", type=int, default=96)
-    ap.add_argument("--workload", default="sci16", choices=["sci16", "sci4", "sci8"],
-                    help="sci16 = the headline workload; sci4 / sci8 are smaller cases for profiling")
+    ap.add_argument("--workload", default="sci16", choices=["sci16", "sci4", "sci8", "mri1024", "mri256"],
+                    help="sci16 = the headline workload; mri1024 = the MRI (ADMM) path on 1024^2 complex; "
+                    "sci4 / sci8 / mri256 are smaller cases for profiling")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -97,7 +97,8 @@ typedef struct glr_match_opts {
 } glr_match_opts;
 
 /* Operation codes for glr_workspace_size. */
-enum { GLR_OP_SELECT = 1, GLR_OP_MATCH = 2, GLR_OP_LOWRANK = 3, GLR_OP_AGGREGATE = 4, GLR_OP_ENCODER = 5 };
+enum { GLR_OP_SELECT = 1, GLR_OP_MATCH = 2, GLR_OP_LOWRANK = 3, GLR_OP_AGGREGATE = 4, GLR_OP_ENCODER = 5,
+       GLR_OP_ADMM = 6 };
 
 /*
  * Workspace bytes needed by one operation.  `opts` is used by GLR_OP_MATCH
@@ -137,6 +138,8 @@ glr_status glr_select_keys(const float* x, const glr_images* im, float edge_th, 
  *   keys     int32 [n_img][N] position ids (from glr_select_keys or the caller).
  *   n_found  int32 [n_img] valid keys per image (<= N); rows beyond are not written.
  *   K        matches per key, 1 <= K <= 128, K <= Hq*Wq.
+ *   modes    GLR_MATCH_FP32: d = C*P*P <= 256 and P <= 8; GLR_MATCH_BF16: d <= 74;
+ *            GLR_MATCH_LEARNED: d <= 64 (GLR_ENOTSUP / GLR_EINVAL otherwise).
  *   idx      out, int32 [n_img][N][K]: the K positions with the smallest
  *            squared L2 distance, ordered by (distance, position id); the key
  *            itself is included (distance 0).
@@ -190,17 +193,32 @@ glr_status glr_debug_match_scores(const float* x, const glr_images* im, const in
  * For every key the K matched patches form Y (d x K, d = C*P*P); with
  * Y = U S V^T, sigma_hat_i = sqrt(max(s_i^2 - K sigma_w^2, 0)),
  * tau_i = c_wnnm sigma_w^2 / (sigma_hat_i + 1e-8), s'_i = max(s_i - tau_i, 0),
- * the output is X^ = U diag(s') V^T.  The SVD is a one-sided Jacobi in FP32.
+ * the output is X^ = U diag(s') V^T.  The SVD is a one-sided Jacobi in FP32
+ * (columns in registers for d <= 64 and K <= 64, in shared memory otherwise).
  *
  *   idx      int32 [n_img][N][K] matches (from glr_match_topk).
  *   groups   out, float32 [n_img][N][K][d]: row j = column j of X^.
  *   rank     out (may be NULL), int32 [n_img][N]: number of s'_i > 0.
- * Limits of this build: d <= 64 and K <= 64 (GLR_ENOTSUP otherwise).
+ * Limits of this build: d <= 640, K <= 128, d % 4 == 0 (GLR_ENOTSUP otherwise).
  */
 glr_status glr_lowrank_groups(const float* x, const glr_images* im, const int32_t* idx,
                               const int32_t* n_found, int32_t N, int32_t K, float sigma_w,
                               float c_wnnm, float* groups, int32_t* rank, void* ws,
                               size_t ws_bytes, void* stream);
+
+/*
+ * The same step for a complex image (Section 3, MRI): x holds C == 2 planes
+ * per image (real, imaginary), so a gathered column is the real half followed
+ * by the imaginary half of a complex patch (m = P*P entries).  Y is the complex
+ * m x K matrix of the K patches; its SVD Y = U S V^H (one-sided Jacobi with
+ * Hermitian rotations, FP32) is shrunk with the same formula, sigma_w being
+ * the noise standard deviation per complex entry, and X^ = U diag(s') V^H is
+ * written back in the same two-half layout.  Limits: 2 P^2 <= 640, K <= 128.
+ */
+glr_status glr_lowrank_groups_complex(const float* x, const glr_images* im, const int32_t* idx,
+                                      const int32_t* n_found, int32_t N, int32_t K, float sigma_w,
+                                      float c_wnnm, float* groups, int32_t* rank, void* ws,
+                                      size_t ws_bytes, void* stream);
 
 /*
  * Aggregation: every group column is added back at its patch position with
@@ -252,6 +270,36 @@ glr_status glr_aggregate_noalloc(const float* groups, const int32_t* idx, const 
 glr_status glr_gap_step(const float* y, const float* masks, int64_t mask_group_stride,
                         const float* v, int32_t G, int32_t T, int32_t H, int32_t W,
                         int32_t accelerate, float* y_acc, float* x_out, void* stream);
+
+/*
+ * Orthonormal 2-D DFT of complex images (the F of the MRI model y = M F(x),
+ * Section 3): X[k][l] = sum_{r,c} x[r][c] exp(-+2 pi i (k r / H + l c / W)) / sqrt(H W)
+ * (minus sign forward, plus sign when inverse != 0), unshifted (index 0 is
+ * frequency 0).  in, out: float32 [n_img][2][H][W] (real plane, imaginary
+ * plane); out may alias in.  H and W are powers of two in [2, 4096].  FP32
+ * radix-2 transforms of the rows and then of the columns; no workspace.
+ */
+glr_status glr_fft2(const float* in, float* out, int32_t n_img, int32_t H, int32_t W, int32_t inverse,
+                    void* stream);
+
+/*
+ * One ADMM step after the denoiser for y = M F(x) (Section 3, MRI; ADMM
+ * ref. [26]), scaled form, given x (previous data-consistent image), z (the
+ * denoiser output D(x + u)) and u:
+ *   u   <- u + x - z                                  (in place)
+ *   x'   = F^-1((M y + rho F(z - u)) / (M + rho))      -> x_out
+ *   w    = x' + u                                      -> w_out (next denoiser input)
+ *   residual[i] = ||M F(x') - y||_2 of image i, accumulated in FP64 (F(x') is
+ *   the k-space array the step inverts, so no extra transform is needed).
+ * y (k-space, zero where M = 0), z, x, u, x_out, w_out: float32
+ * [n_img][2][H][W]; mask float32 [n_img][H][W] (>= 0, normally 0/1); rho > 0;
+ * residual: device double [n_img] (may be NULL).  x_out may alias x, w_out may
+ * alias z; no other aliasing.  H, W powers of two in [2, 4096].
+ * Workspace: glr_workspace_size(GLR_OP_ADMM, im with n_img, H, W, ...).
+ */
+glr_status glr_admm_step(const float* y, const float* mask, const float* z, const float* x, float* u,
+                         int32_t n_img, int32_t H, int32_t W, float rho, float* x_out, float* w_out,
+                         double* residual, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * Reads the status block of a workspace used by an earlier call (blocks on

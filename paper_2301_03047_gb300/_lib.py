@@ -17,7 +17,7 @@ c_uint32_p = ctypes.POINTER(ctypes.c_uint32)
 GLR_OK, GLR_EINVAL, GLR_ECUDA, GLR_ENOMEM, GLR_ETIMEDOUT, GLR_ENOTSUP, GLR_EDEVICE, GLR_ETOOBIG = range(8)
 GLR_DEV_TIMEOUT, GLR_DEV_NONFINITE, GLR_DEV_SVD_NOCONV, GLR_DEV_CAND_OVERFLOW, GLR_DEV_BAD_INDEX = 1, 2, 4, 8, 16
 GLR_MATCH_FP32, GLR_MATCH_BF16, GLR_MATCH_LEARNED = 0, 1, 2
-GLR_OP_SELECT, GLR_OP_MATCH, GLR_OP_LOWRANK, GLR_OP_AGGREGATE, GLR_OP_ENCODER = 1, 2, 3, 4, 5
+GLR_OP_SELECT, GLR_OP_MATCH, GLR_OP_LOWRANK, GLR_OP_AGGREGATE, GLR_OP_ENCODER, GLR_OP_ADMM = 1, 2, 3, 4, 5, 6
 GLR_ENCODER_PARAMS = 5200
 
 
@@ -39,6 +39,9 @@ PROTOTYPES = {
     "glr_encoder_embed": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_encoder_train_step": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_float, c_float, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_lowrank_groups": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "glr_lowrank_groups_complex": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "glr_fft2": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_void_p]),
+    "glr_admm_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_aggregate": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(GlrImages), c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_aggregate_noalloc": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(GlrImages), c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "glr_gap_step": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),

@@ -2,6 +2,7 @@
 // sequencing.  Every entry point validates on the host before launching
 // anything and never allocates device memory.
 #include <atomic>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <string>
@@ -143,6 +144,11 @@ size_t glr_workspace_size(int32_t op, const glr_images* im, int32_t N, int32_t K
       return match_plan(*im, N, K, opts).total;
     case GLR_OP_LOWRANK:
       return sizeof(StatusBlock);
+    case GLR_OP_ADMM: {
+      WsLayout L;
+      L.take((size_t)im->n_img * sizeof(double));  // residual accumulators
+      return L.off;
+    }
     case GLR_OP_AGGREGATE:
       return agg_ws_layout(*im).total;
     case GLR_OP_ENCODER: {
@@ -245,13 +251,67 @@ glr_status glr_lowrank_groups(const float* x, const glr_images* im, const int32_
   if (!(sigma_w >= 0.f) || !(c_wnnm >= 0.f)) return GLR_EINVAL;
   if (!aligned(groups, 16)) return GLR_EINVAL;
   const int d = im->C * im->P * im->P;
-  if (d > 64 || K > 64 || d % 4 != 0) return GLR_ENOTSUP;
+  if (d > 640 || K > 128 || d % 4 != 0) return GLR_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
   glr_status st = begin_ws(ws, ws_bytes, sizeof(StatusBlock), s);
   if (st != GLR_OK) return st;
   st = launch_gather(x, *im, idx, n_found, N, K, groups, (StatusBlock*)ws, s);
   if (st != GLR_OK) return st;
-  return launch_wnnm(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
+  if (d <= 64 && K <= 64) return launch_wnnm(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
+  return launch_wnnm_smem(*im, false, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
+}
+
+glr_status glr_lowrank_groups_complex(const float* x, const glr_images* im, const int32_t* idx,
+                                      const int32_t* n_found, int32_t N, int32_t K, float sigma_w, float c_wnnm,
+                                      float* groups, int32_t* rank, void* ws, size_t ws_bytes, void* stream) {
+  if (!images_ok(im) || !x || !idx || !n_found || !groups) return GLR_EINVAL;
+  if (im->C != 2) return GLR_EINVAL;
+  if (N < 1 || K < 1 || K > npos_of(im)) return GLR_EINVAL;
+  if (!(sigma_w >= 0.f) || !(c_wnnm >= 0.f)) return GLR_EINVAL;
+  if (!aligned(groups, 16)) return GLR_EINVAL;
+  const int d = im->C * im->P * im->P;
+  if (d > 640 || K > 128 || d % 4 != 0) return GLR_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  glr_status st = begin_ws(ws, ws_bytes, sizeof(StatusBlock), s);
+  if (st != GLR_OK) return st;
+  st = launch_gather(x, *im, idx, n_found, N, K, groups, (StatusBlock*)ws, s);
+  if (st != GLR_OK) return st;
+  if (d <= 72 && K <= 64)
+    return launch_wnnm_complex_regs(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
+  return launch_wnnm_smem(*im, true, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
+}
+
+static bool pow2_side(int32_t n) { return n >= 2 && n <= 4096 && (n & (n - 1)) == 0; }
+
+glr_status glr_fft2(const float* in, float* out, int32_t n_img, int32_t H, int32_t W, int32_t inverse,
+                    void* stream) {
+  if (!in || !out || n_img < 1) return GLR_EINVAL;
+  if (!pow2_side(H) || !pow2_side(W)) return GLR_ENOTSUP;
+  if ((long long)n_img * 2 * H * W > (1LL << 34)) return GLR_EINVAL;
+  return launch_fft2(in, out, n_img, H, W, inverse != 0, (cudaStream_t)stream);
+}
+
+glr_status glr_admm_step(const float* y, const float* mask, const float* z, const float* x, float* u,
+                         int32_t n_img, int32_t H, int32_t W, float rho, float* x_out, float* w_out,
+                         double* residual, void* ws, size_t ws_bytes, void* stream) {
+  if (!y || !mask || !z || !x || !u || !x_out || !w_out || n_img < 1) return GLR_EINVAL;
+  if (!(rho > 0.f) || !std::isfinite(rho)) return GLR_EINVAL;
+  if (!pow2_side(H) || !pow2_side(W)) return GLR_ENOTSUP;
+  if ((long long)n_img * 2 * H * W > (1LL << 34)) return GLR_EINVAL;
+  const void* outs[2] = {x_out, w_out};
+  for (const void* o : outs)
+    if (o == (const void*)y || o == (const void*)mask || o == (const void*)u) return GLR_EINVAL;
+  if ((const void*)x_out == (const void*)z || (const void*)w_out == (const void*)x || x_out == w_out)
+    return GLR_EINVAL;
+  glr_images im{n_img, 2, H, W, 1};
+  const size_t need = glr_workspace_size(GLR_OP_ADMM, &im, 1, 1, nullptr);
+  cudaStream_t s = (cudaStream_t)stream;
+  glr_status st = begin_ws(ws, ws_bytes, need, s);
+  if (st != GLR_OK) return st;
+  WsLayout L;
+  double* acc = reinterpret_cast<double*>((char*)ws + L.take((size_t)n_img * sizeof(double)));
+  if (cudaMemsetAsync(acc, 0, (size_t)n_img * sizeof(double), s) != cudaSuccess) return GLR_ECUDA;
+  return launch_admm_step(y, mask, z, x, u, n_img, H, W, rho, x_out, w_out, residual, acc, s);
 }
 
 glr_status glr_aggregate(const float* groups, const int32_t* idx, const int32_t* n_found, const glr_images* im,

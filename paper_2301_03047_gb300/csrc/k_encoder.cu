@@ -266,20 +266,6 @@ __global__ void k_adamw(float* __restrict__ params, const float* __restrict__ gr
   params[i] = p - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
 }
 
-__global__ void k_image_mean_enc(const float* __restrict__ x, long long n_per_img, float* __restrict__ mean) {
-  __shared__ double red[256];
-  const float* xf = x + blockIdx.x * n_per_img;
-  double s = 0.0;
-  for (long long i = threadIdx.x; i < n_per_img; i += 256) s += (double)xf[i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) mean[blockIdx.x] = (float)(red[0] / (double)n_per_img);
-}
-
 }  // namespace
 
 glr_status launch_encode_positions(const float* x, const glr_images& im, const float* mean, const float* params,
@@ -296,12 +282,6 @@ glr_status launch_encode_vectors(const float* vecs, long long n, int d, const fl
                                  cudaStream_t s) {
   const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(n, 128), 152LL * 16));
   GLR_LAUNCH("k_encode_vectors", s, k_encode_vectors<<<blocks, 128, NPARAM * 4, s>>>(vecs, n, d, params, emb));
-  return GLR_OK;
-}
-
-glr_status launch_image_mean(const float* x, const glr_images& im, float* mean, cudaStream_t s) {
-  GLR_LAUNCH("k_image_mean_enc", s,
-             k_image_mean_enc<<<im.n_img, 256, 0, s>>>(x, (long long)im.C * im.H * im.W, mean));
   return GLR_OK;
 }
 

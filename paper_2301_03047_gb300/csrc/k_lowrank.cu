@@ -89,6 +89,86 @@ __device__ __forceinline__ void jacobi_pair(float (&a)[DMAX], float (&b)[DMAX], 
   }
 }
 
+// Complex columns (real halves in [0, DMAX/2), imaginary halves in [DMAX/2, DMAX)):
+// with g = a^H b = |g| e, rotate (a, conj(e) b) as a real pair:
+// a' = c a - s conj(e) b, b' = s e a + c b, which zeroes a'^H b'.
+template <int DMAX>
+__device__ __forceinline__ void jacobi_pair_c(float (&a)[DMAX], float (&b)[DMAX], float& alpha, float& beta,
+                                              float tol, float lam_skip, float lam, float& acc_a, float& acc_b,
+                                              bool& rotated) {
+  constexpr int H2 = DMAX / 2;
+  float pr[2] = {0.f, 0.f}, pi[2] = {0.f, 0.f};
+#pragma unroll
+  for (int r = 0; r < H2; ++r) {
+    pr[r & 1] = fmaf(a[r], b[r], pr[r & 1]);
+    pr[r & 1] = fmaf(a[H2 + r], b[H2 + r], pr[r & 1]);
+    pi[r & 1] = fmaf(a[r], b[H2 + r], pi[r & 1]);
+    pi[r & 1] = fmaf(-a[H2 + r], b[r], pi[r & 1]);
+  }
+  const float gr = pr[0] + pr[1], gi = pi[0] + pi[1];
+  const float gm = sqrtf(fmaf(gr, gr, gi * gi));
+  if (beta < lam) acc_a += gm;
+  if (alpha < lam) acc_b += gm;
+  if (gm > tol * sqrtf(alpha * beta) && gm != 0.f && (alpha >= lam_skip || beta >= lam_skip)) {
+    const float zeta = __fdividef(beta - alpha, 2.f * gm);
+    const float az = fabsf(zeta);
+    float t = (az < 1e18f) ? __frcp_rn(az + sqrtf(fmaf(zeta, zeta, 1.f))) : __fdividef(0.5f, az);
+    t = copysignf(t, zeta);
+    const float cs = rsqrtf(fmaf(t, t, 1.f));
+    const float sn = cs * t;
+    const float inv = __frcp_rn(gm);
+    const float er = gr * inv, ei = gi * inv;
+#pragma unroll
+    for (int r = 0; r < H2; ++r) {
+      const float ar = a[r], ai = a[H2 + r], br = b[r], bi = b[H2 + r];
+      const float cbr = fmaf(er, br, ei * bi), cbi = fmaf(er, bi, -ei * br);  // conj(e) b
+      const float ear = fmaf(er, ar, -ei * ai), eai = fmaf(er, ai, ei * ar);  // e a
+      a[r] = fmaf(cs, ar, -sn * cbr);
+      a[H2 + r] = fmaf(cs, ai, -sn * cbi);
+      b[r] = fmaf(sn, ear, cs * br);
+      b[H2 + r] = fmaf(sn, eai, cs * bi);
+    }
+    alpha = fmaf(-t, gm, alpha);
+    beta = fmaf(t, gm, beta);
+    rotated = true;
+  }
+}
+
+// Column j of a group in global memory <-> registers.  Real: d values.  Complex:
+// m = d / 2 real parts then m imaginary parts, placed at [0, m) and [DMAX/2, DMAX/2 + m).
+template <int DMAX, bool CPLX>
+__device__ __forceinline__ void load_col(float (&a)[DMAX], const float* __restrict__ y, int d, bool own) {
+  if (CPLX) {
+    constexpr int H2 = DMAX / 2;
+    const int m = d / 2;
+#pragma unroll
+    for (int r = 0; r < H2; ++r) {
+      a[r] = (own && r < m) ? y[r] : 0.f;
+      a[H2 + r] = (own && r < m) ? y[m + r] : 0.f;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < DMAX; ++r) a[r] = (own && r < d) ? y[r] : 0.f;
+  }
+}
+template <int DMAX, bool CPLX>
+__device__ __forceinline__ void store_col(const float (&a)[DMAX], float* __restrict__ y, int d) {
+  if (CPLX) {
+    constexpr int H2 = DMAX / 2;
+    const int m = d / 2;
+#pragma unroll
+    for (int r = 0; r < H2; ++r)
+      if (r < m) {
+        y[r] = a[r];
+        y[m + r] = a[H2 + r];
+      }
+  } else {
+#pragma unroll
+    for (int r = 0; r < DMAX; ++r)
+      if (r < d) y[r] = a[r];
+  }
+}
+
 template <int DMAX>
 __device__ __forceinline__ float sq_norm(const float (&a)[DMAX]) {
   float p[4] = {0.f, 0.f, 0.f, 0.f};
@@ -98,8 +178,8 @@ __device__ __forceinline__ float sq_norm(const float (&a)[DMAX]) {
 }
 
 // DMAX rows per column, KMAX <= 64 columns, one warp per group, WARPS groups per CTA.
-template <int DMAX, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 3) k_jacobi_wnnm(int n_img, int d, int N, int K,
+template <int DMAX, int WARPS, bool CPLX>
+__global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_img, int d, int N, int K,
                                                             const int32_t* __restrict__ n_found, float sigma_w,
                                                             float c_wnnm, float tol, int max_sweeps,
                                                             float* __restrict__ groups, int32_t* __restrict__ rank,
@@ -116,11 +196,8 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_jacobi_wnnm(int n_img, int d,
     float* Y = groups + g * (long long)K * d;
     float a[DMAX], b[DMAX];
     const int ja = 2 * lane, jb = 2 * lane + 1;
-#pragma unroll
-    for (int r = 0; r < DMAX; ++r) {
-      a[r] = (ja < K && r < d) ? Y[(long long)ja * d + r] : 0.f;
-      b[r] = (live && jb < K && r < d) ? Y[(long long)jb * d + r] : 0.f;
-    }
+    load_col<DMAX, CPLX>(a, Y + (long long)ja * d, d, ja < K);
+    load_col<DMAX, CPLX>(b, Y + (long long)jb * d, d, live && jb < K);
     // non-finite input: leave the group unchanged and flag it
     float s0 = 0.f;
 #pragma unroll
@@ -182,7 +259,10 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_jacobi_wnnm(int n_img, int d,
         const int src = (lane & ~(g - 1)) | ((lane + 1) & (g - 1));
 #pragma unroll 1
         for (int rd = 0; rd < g; ++rd) {
-          jacobi_pair<DMAX>(a, b, alpha, beta, tol, lam_skip, lam, acc_a, acc_b, live, rotated);
+          if (CPLX)
+            jacobi_pair_c<DMAX>(a, b, alpha, beta, tol, lam_skip, lam, acc_a, acc_b, rotated);
+          else
+            jacobi_pair<DMAX>(a, b, alpha, beta, tol, lam_skip, lam, acc_a, acc_b, live, rotated);
           if (rd + 1 < g) {
 #pragma unroll
             for (int r = 0; r < DMAX; ++r) b[r] = __shfl_sync(0xffffffffu, b[r], src);
@@ -215,13 +295,20 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_jacobi_wnnm(int n_img, int d,
     }
     const float sw2 = sigma_w * sigma_w;
     float coef_a = 0.f, coef_b = 0.f;
+    // numerical rank: singular values at or below max(d, K) 2^-24 s_max are FP32
+    // rounding residue (the null space of a group with K > d), not components
+    float smax = fmaxf(na2, nb2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    const float rtol = (float)max(CPLX ? d / 2 : d, K) * 5.9604645e-8f;
+    const float floor2 = rtol * rtol * smax;
     {
       const float sa = sqrtf(na2), sb = sqrtf(nb2);
       const float ha = sqrtf(fmaxf(na2 - (float)K * sw2, 0.f)), hb = sqrtf(fmaxf(nb2 - (float)K * sw2, 0.f));
       const float pa = fmaxf(sa - c_wnnm * sw2 / (ha + 1e-8f), 0.f);
       const float pb = fmaxf(sb - c_wnnm * sw2 / (hb + 1e-8f), 0.f);
-      if (live && pa > 0.f && sa > 0.f) coef_a = pa / (sa * na2);
-      if (live && pb > 0.f && sb > 0.f) coef_b = pb / (sb * nb2);
+      if (live && pa > 0.f && na2 > floor2) coef_a = pa / (sa * na2);
+      if (live && pb > 0.f && nb2 > floor2) coef_b = pb / (sb * nb2);
     }
     const unsigned act_a = __ballot_sync(0xffffffffu, coef_a != 0.f);
     const unsigned act_b = __ballot_sync(0xffffffffu, coef_b != 0.f);
@@ -251,26 +338,40 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_jacobi_wnnm(int n_img, int d,
       const int j = 2 * lane + h;
       const bool own = live && j < K;
       // a / b are free once W is staged: reuse them as y_j and x^_j
+      load_col<DMAX, CPLX>(a, Y + (long long)j * d, d, own);
 #pragma unroll
-      for (int r = 0; r < DMAX; ++r) {
-        a[r] = (own && r < d) ? Y[(long long)j * d + r] : 0.f;
-        b[r] = 0.f;
-      }
+      for (int r = 0; r < DMAX; ++r) b[r] = 0.f;
       for (int i = 0; i < rnk; ++i) {
         const float* w = Ws + i * DMAX;
-        float zp[4] = {0.f, 0.f, 0.f, 0.f};
+        if (CPLX) {
+          // z = coef w^H y (complex); x^ += w z
+          constexpr int H2 = DMAX / 2;
+          float zr = 0.f, zi = 0.f;
 #pragma unroll
-        for (int r = 0; r < DMAX; ++r) zp[r & 3] = fmaf(w[r], a[r], zp[r & 3]);
-        const float z = ((zp[0] + zp[1]) + (zp[2] + zp[3])) * coef_s[wid][i];
+          for (int r = 0; r < H2; ++r) {
+            zr = fmaf(w[r], a[r], zr);
+            zr = fmaf(w[H2 + r], a[H2 + r], zr);
+            zi = fmaf(w[r], a[H2 + r], zi);
+            zi = fmaf(-w[H2 + r], a[r], zi);
+          }
+          zr *= coef_s[wid][i];
+          zi *= coef_s[wid][i];
 #pragma unroll
-        for (int r = 0; r < DMAX; ++r) b[r] = fmaf(z, w[r], b[r]);
+          for (int r = 0; r < H2; ++r) {
+            b[r] = fmaf(w[r], zr, fmaf(-w[H2 + r], zi, b[r]));
+            b[H2 + r] = fmaf(w[r], zi, fmaf(w[H2 + r], zr, b[H2 + r]));
+          }
+        } else {
+          float zp[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int r = 0; r < DMAX; ++r) zp[r & 3] = fmaf(w[r], a[r], zp[r & 3]);
+          const float z = ((zp[0] + zp[1]) + (zp[2] + zp[3])) * coef_s[wid][i];
+#pragma unroll
+          for (int r = 0; r < DMAX; ++r) b[r] = fmaf(z, w[r], b[r]);
+        }
       }
       __syncwarp();
-      if (own) {
-#pragma unroll
-        for (int r = 0; r < DMAX; ++r)
-          if (r < d) Y[(long long)j * d + r] = b[r];
-      }
+      if (own) store_col<DMAX, CPLX>(b, Y + (long long)j * d, d);
     }
     __syncwarp();
   }
@@ -288,22 +389,34 @@ glr_status launch_gather(const float* x, const glr_images& im, const int32_t* id
   return GLR_OK;
 }
 
-glr_status launch_wnnm(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
-                       float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s) {
-  const int d = im.C * im.P * im.P;
-  if (d > 64 || K > 64 || K < 1) return GLR_ENOTSUP;
+template <int DMAX, bool CPLX>
+glr_status launch_wnnm_regs(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
+                            float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s, const char* name) {
   constexpr int WARPS = 4;
-  constexpr int DMAX = 64;
+  const int d = im.C * im.P * im.P;
   const size_t smem = (size_t)WARPS * 64 * DMAX * sizeof(float);
-  if (cudaFuncSetAttribute(k_jacobi_wnnm<DMAX, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
+  if (cudaFuncSetAttribute(k_jacobi_wnnm<DMAX, WARPS, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
     return GLR_ECUDA;
   const long long ngroups = (long long)im.n_img * N;
   const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(ngroups, WARPS), 152LL * 64));
   const float tol = 1e-5f;
-  GLR_LAUNCH("k_jacobi_wnnm", s, k_jacobi_wnnm<DMAX, WARPS><<<blocks, WARPS * 32, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, 30,
-                                                             groups, rank, st));
+  GLR_LAUNCH(name, s, (k_jacobi_wnnm<DMAX, WARPS, CPLX><<<blocks, WARPS * 32, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, 30, groups, rank, st)));
   return GLR_OK;
+}
+
+glr_status launch_wnnm(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
+                       float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s) {
+  const int d = im.C * im.P * im.P;
+  if (d > 64 || K > 64 || K < 1) return GLR_ENOTSUP;
+  return launch_wnnm_regs<64, false>(im, n_found, N, K, sigma_w, c_wnnm, groups, rank, st, s, "k_jacobi_wnnm");
+}
+
+glr_status launch_wnnm_complex_regs(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w,
+                                   float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s) {
+  const int d = im.C * im.P * im.P;
+  if (d > 72 || (d % 2) != 0 || K > 64 || K < 1) return GLR_ENOTSUP;
+  return launch_wnnm_regs<72, true>(im, n_found, N, K, sigma_w, c_wnnm, groups, rank, st, s, "k_jacobi_wnnm_c");
 }
 
 }  // namespace glr

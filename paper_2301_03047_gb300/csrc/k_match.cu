@@ -13,6 +13,8 @@
 //                  through the running top-K' streams (topk_stream.cuh)
 //   k_rerank       per key: exact FP32 sum((p-q)^2) of every kept candidate,
 //                  sort by (distance, id), emit the K best.
+#include <cooperative_groups.h>
+
 #include "glr_kernels.cuh"
 #include "topk_stream.cuh"
 
@@ -20,19 +22,53 @@ namespace glr {
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_image_mean(const float* __restrict__ x, long long n_per_img,
-                                                    float* __restrict__ mean) {
-  __shared__ double red[256];
-  const float* xf = x + blockIdx.x * n_per_img;
+// Image mean: a cluster of MEAN_CTAS CTAs per image, each summing a contiguous
+// slice in FP64 (float4 loads when aligned); CTA 0 of the cluster adds the
+// slices' sums in rank order through distributed shared memory, so the result
+// does not depend on scheduling.
+constexpr int MEAN_CTAS = 8;
+__global__ void __cluster_dims__(MEAN_CTAS, 1, 1) __launch_bounds__(512)
+    k_image_mean(const float* __restrict__ x, long long n_per_img, float* __restrict__ mean) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double red[16];
+  __shared__ double part;
+  const int rankc = (int)cl.block_rank();
+  const long long f = blockIdx.x / MEAN_CTAS;
+  const float* xf = x + f * n_per_img;
+  const long long per = (n_per_img + MEAN_CTAS - 1) / MEAN_CTAS;
+  const long long lo = min(n_per_img, per * rankc), hi = min(n_per_img, lo + per);
   double s = 0.0;
-  for (long long i = threadIdx.x; i < n_per_img; i += 256) s += (double)xf[i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  long long i = lo + threadIdx.x;
+  // aligned float4 body (slice boundaries rounded to 4 elements)
+  const long long a0 = min(hi, (lo + 3) & ~3LL), a1 = max(a0, hi & ~3LL);
+  if ((reinterpret_cast<uintptr_t>(xf) & 15u) == 0) {
+    for (i = lo + threadIdx.x; i < a0; i += 512) s += (double)xf[i];
+    const float4* v4 = reinterpret_cast<const float4*>(xf);
+    for (long long j = a0 / 4 + threadIdx.x; j < a1 / 4; j += 512) {
+      const float4 v = __ldg(v4 + j);
+      s += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
+    }
+    for (i = a1 + threadIdx.x; i < hi; i += 512) s += (double)xf[i];
+  } else {
+    for (; i < hi; i += 512) s += (double)xf[i];
   }
-  if (threadIdx.x == 0) mean[blockIdx.x] = (float)(red[0] / (double)n_per_img);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 16; ++w) t += red[w];
+    part = t;
+  }
+  cl.sync();
+  if (rankc == 0 && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int r = 0; r < MEAN_CTAS; ++r) t += *cl.map_shared_rank(&part, r);
+    mean[f] = (float)(t / (double)n_per_img);
+  }
+  cl.sync();  // keep every CTA's shared memory alive until CTA 0 has read it
 }
 
 __global__ void __launch_bounds__(256) k_patch_norms(const float* __restrict__ x, const float* __restrict__ mean,
@@ -393,6 +429,12 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
 
 }  // namespace
 
+glr_status launch_image_mean(const float* x, const glr_images& im, float* mean, cudaStream_t s) {
+  GLR_LAUNCH("k_image_mean", s,
+             k_image_mean<<<im.n_img * MEAN_CTAS, 512, 0, s>>>(x, (long long)im.C * im.H * im.W, mean));
+  return GLR_OK;
+}
+
 MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o) {
   MatchPlan pl{};
   pl.mode = o ? o->mode : GLR_MATCH_FP32;
@@ -465,7 +507,11 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
   const long long HW = (long long)im.H * im.W;
   uint32_t* taugl = reinterpret_cast<uint32_t*>(ws + pl.taugl_off);
   if (cudaMemsetAsync(taugl, 0xff, (size_t)im.n_img * pl.Npad * 4, s) != cudaSuccess) return GLR_ECUDA;
-  GLR_LAUNCH("k_image_mean", s, k_image_mean<<<im.n_img, 256, 0, s>>>(x, (long long)im.C * HW, mean));
+  (void)HW;
+  {
+    const glr_status st = launch_image_mean(x, im, mean, s);
+    if (st != GLR_OK) return st;
+  }
   {
     const long long total = (long long)im.n_img * npos;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));

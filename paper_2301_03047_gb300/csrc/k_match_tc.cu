@@ -3,9 +3,12 @@
 // accumulators in tensor memory), operands staged by TMA, fused with the
 // running per-key top-K' of topk_stream.cuh so no score reaches HBM.
 //
-// Operands (packed once per call by k_pack_keys / k_pack_positions):
-//   A (keys)      row = [-2 p~ (d bf16, zero-padded to 64) | 1 1 1 pn_hi pn_mid pn_lo 0..]
-//   B (positions) row = [   q~ (d bf16, zero-padded to 64) | qn_hi qn_mid qn_lo 1 1 1 0..]
+// Operands (packed once per call by k_pack_keys / k_pack_positions), 80 BF16
+// columns per row, the first 64 in a 128-byte swizzled tile, the last 16 in a
+// 32-byte swizzled tile:
+//   A (keys)      row = [-2 p~ (d values) | 1 1 1 pn_hi pn_mid pn_lo | 0..]
+//   B (positions) row = [   q~ (d values) | qn_hi qn_mid qn_lo 1 1 1 | 0..]
+// with the six norm columns starting at column max(d, 64), so d <= 74.
 // where p~, q~ are the mean-shifted patches rounded to BF16 and pn, qn their
 // squared norms computed in FP32 from the rounded values, split into three
 // BF16 terms.  One 128 x 256 x 80 product therefore gives, per key/position,
@@ -172,6 +175,9 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16&
   l = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
+// First norm column of the 80-column operand rows for d patch values.
+__host__ __device__ constexpr int norm_col(int d) { return d > DK_MAIN ? d : DK_MAIN; }
+
 // Positions: thread per position; writes 64 + 16 bf16.
 // emb != nullptr: pack the 16-value embeddings emb[img][q][16] instead of the patches.
 __global__ void __launch_bounds__(256) k_pack_positions(const float* __restrict__ x, const float* __restrict__ mean,
@@ -181,48 +187,54 @@ __global__ void __launch_bounds__(256) k_pack_positions(const float* __restrict_
                                                         __nv_bfloat16* __restrict__ qaux) {
   const int Hq = H - P + 1, Wq = W - P + 1;
   const long long npos = (long long)Hq * Wq;
-  const int d = C * P * P;
+  const int d = emb != nullptr ? 16 : C * P * P;
+  const int nb = norm_col(d) - DK_MAIN;  // first norm column inside the aux tile
   const long long total = (long long)n_img * npos_pad;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long f = i / npos_pad;
     const long long q = i - f * npos_pad;
-    __align__(16) __nv_bfloat16 row[DK_MAIN];
-    __align__(16) __nv_bfloat16 aux[DK_AUX];
+    __align__(16) __nv_bfloat16 row[DK_MAIN + DK_AUX];
     const __nv_bfloat16 z = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
 #pragma unroll
-    for (int e = 0; e < DK_AUX; ++e) aux[e] = z;
+    for (int e = 0; e < DK_MAIN + DK_AUX; ++e) row[e] = z;
     if (q < npos) {
       const int r = (int)(q / Wq), c = (int)(q - (q / Wq) * Wq);
       const float mu = mean[f];
       float nrm = 0.f;
-#pragma unroll 8
-      for (int e = 0; e < DK_MAIN; ++e) {
-        float v = 0.f;
-        if (emb != nullptr) {
-          if (e < 16) v = __ldg(emb + (f * npos + q) * 16 + e);
-        } else if (e < d) {
-          const int ch = e / (P * P), dr = (e / P) % P, dc = e % P;
-          v = __ldg(x + (((long long)f * C + ch) * H + r + dr) * W + c + dc) - mu;
-        }
-        row[e] = __float2bfloat16_rn(v);
-        const float rv = __bfloat162float(row[e]);
-        nrm = fmaf(rv, rv, nrm);
-      }
-      split3(nrm, aux[0], aux[1], aux[2]);
-      aux[3] = aux[4] = aux[5] = one;
-    } else {
 #pragma unroll
-      for (int e = 0; e < DK_MAIN; ++e) row[e] = z;
+      for (int e = 0; e < DK_MAIN + DK_AUX; ++e) {
+        if (e < d) {
+          float v;
+          if (emb != nullptr) {
+            v = __ldg(emb + (f * npos + q) * 16 + e);
+          } else {
+            const int ch = e / (P * P), dr = (e / P) % P, dc = e % P;
+            v = __ldg(x + (((long long)f * C + ch) * H + r + dr) * W + c + dc) - mu;
+          }
+          row[e] = __float2bfloat16_rn(v);
+          const float rv = __bfloat162float(row[e]);
+          nrm = fmaf(rv, rv, nrm);
+        }
+      }
+      __nv_bfloat16 h, m, l;
+      split3(nrm, h, m, l);
+#pragma unroll
+      for (int e = 0; e < DK_AUX; ++e) {  // static register indices: select by offset
+        const int t = e - nb;
+        if (t == 0) row[DK_MAIN + e] = h;
+        else if (t == 1) row[DK_MAIN + e] = m;
+        else if (t == 2) row[DK_MAIN + e] = l;
+        else if (t >= 3 && t < 6) row[DK_MAIN + e] = one;
+      }
     }
     uint4* dst = reinterpret_cast<uint4*>(qmain + i * DK_MAIN);
     const uint4* src = reinterpret_cast<const uint4*>(row);
 #pragma unroll
     for (int k = 0; k < DK_MAIN / 8; ++k) dst[k] = src[k];
     uint4* dsta = reinterpret_cast<uint4*>(qaux + i * DK_AUX);
-    const uint4* srca = reinterpret_cast<const uint4*>(aux);
-    dsta[0] = srca[0];
-    dsta[1] = srca[1];
+    dsta[0] = src[DK_MAIN / 8];
+    dsta[1] = src[DK_MAIN / 8 + 1];
   }
 }
 
@@ -230,31 +242,38 @@ __global__ void __launch_bounds__(256) k_pack_positions(const float* __restrict_
 __global__ void __launch_bounds__(256) k_pack_keys(const float* __restrict__ keyv, int n_keys_total, int d,
                                                    __nv_bfloat16* __restrict__ kmain,
                                                    __nv_bfloat16* __restrict__ kaux) {
+  const int nb = norm_col(d) - DK_MAIN;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_keys_total; i += gridDim.x * blockDim.x) {
-    __align__(16) __nv_bfloat16 row[DK_MAIN];
-    __align__(16) __nv_bfloat16 aux[DK_AUX];
+    __align__(16) __nv_bfloat16 row[DK_MAIN + DK_AUX];
     const __nv_bfloat16 z = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
     float nrm = 0.f;
-#pragma unroll 8
-    for (int e = 0; e < DK_MAIN; ++e) {
-      const float v = e < d ? keyv[(long long)i * d + e] : 0.f;
-      const __nv_bfloat16 b = __float2bfloat16_rn(v);
-      const float rv = __bfloat162float(b);
-      nrm = fmaf(rv, rv, nrm);
-      row[e] = __float2bfloat16_rn(-2.f * rv);  // exact: scaling by -2
-    }
 #pragma unroll
-    for (int e = 0; e < DK_AUX; ++e) aux[e] = z;
-    aux[0] = aux[1] = aux[2] = one;
-    split3(nrm, aux[3], aux[4], aux[5]);
+    for (int e = 0; e < DK_MAIN + DK_AUX; ++e) {
+      row[e] = z;
+      if (e < d) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(keyv[(long long)i * d + e]);
+        const float rv = __bfloat162float(b);
+        nrm = fmaf(rv, rv, nrm);
+        row[e] = __float2bfloat16_rn(-2.f * rv);  // exact: scaling by -2
+      }
+    }
+    __nv_bfloat16 h, m, l;
+    split3(nrm, h, m, l);
+#pragma unroll
+    for (int e = 0; e < DK_AUX; ++e) {
+      const int t = e - nb;
+      if (t >= 0 && t < 3) row[DK_MAIN + e] = one;
+      else if (t == 3) row[DK_MAIN + e] = h;
+      else if (t == 4) row[DK_MAIN + e] = m;
+      else if (t == 5) row[DK_MAIN + e] = l;
+    }
     uint4* dst = reinterpret_cast<uint4*>(kmain + (long long)i * DK_MAIN);
     const uint4* src = reinterpret_cast<const uint4*>(row);
 #pragma unroll
     for (int k = 0; k < DK_MAIN / 8; ++k) dst[k] = src[k];
     uint4* dsta = reinterpret_cast<uint4*>(kaux + (long long)i * DK_AUX);
-    const uint4* srca = reinterpret_cast<const uint4*>(aux);
-    dsta[0] = srca[0];
-    dsta[1] = srca[1];
+    dsta[0] = src[DK_MAIN / 8];
+    dsta[1] = src[DK_MAIN / 8 + 1];
   }
 }
 
@@ -272,8 +291,9 @@ __global__ void __launch_bounds__(256) k_seed_bounds(const __nv_bfloat16* __rest
                                                      const __nv_bfloat16* __restrict__ kaux,
                                                      const int32_t* __restrict__ keys,
                                                      const int32_t* __restrict__ n_found, int n_img, int N, int Npad,
-                                                     int Hq, int Wq, long long npos_pad, int kp,
+                                                     int Hq, int Wq, long long npos_pad, int kp, int d,
                                                      uint32_t* __restrict__ tau_gl) {
+  const int nb = norm_col(d) - DK_MAIN;  // patch values in the aux tile: columns 0 .. nb-1
   __shared__ unsigned hist_s[8][256];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned* hist = hist_s[wid];
@@ -292,10 +312,12 @@ __global__ void __launch_bounds__(256) k_seed_bounds(const __nv_bfloat16* __rest
     // key operand: -2 p~ (64) and the three pn terms
     const __nv_bfloat16* ka = kmain + ((long long)f * Npad + k) * DK_MAIN;
     const __nv_bfloat16* kx = kaux + ((long long)f * Npad + k) * DK_AUX;
-    const float pn = __bfloat162float(kx[3]) + __bfloat162float(kx[4]) + __bfloat162float(kx[5]);
-    float kv[DK_MAIN];
+    const float pn = __bfloat162float(kx[nb + 3]) + __bfloat162float(kx[nb + 4]) + __bfloat162float(kx[nb + 5]);
+    float kv[DK_MAIN], kxv[DK_AUX];
 #pragma unroll
     for (int e = 0; e < DK_MAIN; ++e) kv[e] = __bfloat162float(ka[e]);
+#pragma unroll
+    for (int e = 0; e < DK_AUX; ++e) kxv[e] = e < nb ? __bfloat162float(kx[e]) : 0.f;
     constexpr int PER_LANE = SEED_WIN * SEED_WIN / 32;
     uint32_t key_s[PER_LANE];
     float qmax = 0.f;
@@ -316,7 +338,12 @@ __global__ void __launch_bounds__(256) k_seed_bounds(const __nv_bfloat16* __rest
           for (int t = 0; t < 8; ++t) acc = fmaf(kv[v * 8 + t], __bfloat162float(hb[t]), acc);
         }
         const __nv_bfloat16* qx = qaux + ((long long)f * npos_pad + q) * DK_AUX;
-        const float qn = __bfloat162float(qx[0]) + __bfloat162float(qx[1]) + __bfloat162float(qx[2]);
+        if (nb > 0) {
+#pragma unroll
+          for (int e = 0; e < DK_AUX; ++e)
+            if (e < nb) acc = fmaf(kxv[e], __bfloat162float(qx[e]), acc);
+        }
+        const float qn = __bfloat162float(qx[nb]) + __bfloat162float(qx[nb + 1]) + __bfloat162float(qx[nb + 2]);
         qmax = fmaxf(qmax, qn);
         kk = float_order_key((acc + qn) + pn);
       }
@@ -602,7 +629,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
                                 char* ws, float* dump, const int32_t* seed_keys, int seed_N, const float* emb_pos,
                                 const float* emb_keys, cudaStream_t s) {
   const int d = emb_keys ? 16 : im.C * im.P * im.P;
-  if (d > DK_MAIN) return GLR_ENOTSUP;
+  if (norm_col(d) + 6 > DK_MAIN + DK_AUX) return GLR_ENOTSUP;
   const float* mean = reinterpret_cast<const float*>(ws + pl.mean_off);
   const float* keyv = emb_keys ? emb_keys : reinterpret_cast<const float*>(ws + pl.keyv_off);
   uint2* bufs = reinterpret_cast<uint2*>(ws + pl.buf_off);
@@ -631,7 +658,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
     GLR_LAUNCH("k_seed_bounds", s,
                k_seed_bounds<<<blocks, 256, 0, s>>>(qmain, qaux, kmain, kaux, seed_keys, n_found, im.n_img, seed_N,
                                                     pl.Npad, im.H - im.P + 1, im.W - im.P + 1, pl.npos_pad, pl.Kp,
-                                                    taugl));
+                                                    d, taugl));
   }
   CUtensorMap tq, tqa, tk, tka;
   const uint64_t qrows = (uint64_t)im.n_img * pl.npos_pad, krows = (uint64_t)im.n_img * pl.Npad;

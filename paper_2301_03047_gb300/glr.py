@@ -134,8 +134,12 @@ def debug_match_scores(x, P, keys, n_found, K, *, ws=None, stream=None):
     return scores
 
 
-def lowrank_groups(x, P, idx, n_found, sigma_w, c_wnnm, *, groups=None, rank=None, ws=None, stream=None):
-    """R~_i x and the WNNM step of Eq. 5; returns (groups [n][N][K][d] = X^, rank [n][N])."""
+def lowrank_groups(x, P, idx, n_found, sigma_w, c_wnnm, *, groups=None, rank=None, ws=None, stream=None,
+                   complex_=False):
+    """R~_i x and the WNNM step of Eq. 5; returns (groups [n][N][K][d] = X^, rank [n][N]).
+
+    complex_=True: x holds (real, imaginary) planes (C == 2) and the group is the
+    complex P^2 x K matrix (glr_lowrank_groups_complex)."""
     lib = L.load()
     im = images_of(x, P)
     n, N, K = idx.shape
@@ -148,10 +152,41 @@ def lowrank_groups(x, P, idx, n_found, sigma_w, c_wnnm, *, groups=None, rank=Non
     if ws is None:
         ws = workspace(L.GLR_OP_LOWRANK, im, N, K, None, dev)
     wp, wn = _ws(ws)
-    _check("glr_lowrank_groups", lib.glr_lowrank_groups(_ptr(x), ctypes.byref(im), _ptr(idx), _ptr(n_found), int(N),
-                                                        int(K), float(sigma_w), float(c_wnnm), _ptr(groups),
-                                                        _ptr(rank), wp, wn, _stream(stream)))
+    name = "glr_lowrank_groups_complex" if complex_ else "glr_lowrank_groups"
+    _check(name, getattr(lib, name)(_ptr(x), ctypes.byref(im), _ptr(idx), _ptr(n_found), int(N), int(K),
+                                    float(sigma_w), float(c_wnnm), _ptr(groups), _ptr(rank), wp, wn,
+                                    _stream(stream)))
     return groups, rank
+
+
+def fft2(x, inverse=False, *, out=None, stream=None):
+    """Orthonormal unshifted 2-D DFT of complex images x [n][2][H][W] (real, imaginary planes)."""
+    lib = L.load()
+    n, two, H, W = x.shape
+    assert two == 2
+    if out is None:
+        out = torch.empty_like(x)
+    _check("glr_fft2", lib.glr_fft2(_ptr(x), _ptr(out), n, H, W, 1 if inverse else 0, _stream(stream)))
+    return out
+
+
+def admm_step(y, mask, z, x, u, rho, *, x_out=None, w_out=None, residual=None, ws=None, stream=None):
+    """One ADMM data-consistency step (y = M F(x)): u += x - z; x' = F^-1((M y + rho F(z - u)) / (M + rho));
+    w = x' + u.  Returns (x', w, residual [n] float64 = ||M F(x') - y||)."""
+    lib = L.load()
+    n, _, H, W = y.shape
+    if x_out is None:
+        x_out = torch.empty_like(y)
+    if w_out is None:
+        w_out = torch.empty_like(y)
+    if residual is None:
+        residual = torch.empty(n, dtype=torch.float64, device=y.device)
+    if ws is None:
+        ws = workspace(L.GLR_OP_ADMM, images(n, 2, H, W, 1), 1, 1, None, y.device)
+    wp, wn = _ws(ws)
+    _check("glr_admm_step", lib.glr_admm_step(_ptr(y), _ptr(mask), _ptr(z), _ptr(x), _ptr(u), n, H, W, float(rho),
+                                              _ptr(x_out), _ptr(w_out), _ptr(residual), wp, wn, _stream(stream)))
+    return x_out, w_out, residual
 
 
 def aggregate(groups, idx, n_found, x, P, *, out=None, ws=None, stream=None):
@@ -242,9 +277,9 @@ class GlrDenoiser:
     """Select -> match -> low-rank -> aggregate on fixed-size images, with preallocated buffers."""
 
     def __init__(self, shape: GlrShape, mode: str = "bf16", edge_th: float = 0.1, k_over: int = 0, splits: int = 0,
-                 device="cuda", cap: int = 0, epi_batch: int = 0):
+                 device="cuda", cap: int = 0, epi_batch: int = 0, complex_: bool = False):
         s = shape
-        self.shape, self.mode, self.edge_th = s, mode, edge_th
+        self.shape, self.mode, self.edge_th, self.complex_ = s, mode, edge_th, complex_
         self.opts = match_opts(mode, k_over, splits, cap, None, epi_batch)
         self.k_over, self.splits, self.cap, self.epi_batch = k_over, splits, cap, epi_batch
         im = images(s.n_img, s.C, s.H, s.W, s.P)
@@ -271,7 +306,7 @@ class GlrDenoiser:
                    cap=self.cap, epi_batch=self.epi_batch, idx=self.idx, dist=self.dist, ws=self.ws_match,
                    stream=stream)
         lowrank_groups(x, s.P, self.idx, self.n_found, sigma_w, c_wnnm, groups=self.groups, rank=self.rank,
-                       ws=self.ws_lowrank, stream=stream)
+                       ws=self.ws_lowrank, stream=stream, complex_=self.complex_)
         return aggregate(self.groups, self.idx, self.n_found, x, s.P, out=out, ws=self.ws_agg, stream=stream)
 
 
@@ -303,6 +338,10 @@ class SciReconstructor:
                  out=self.x, stream=stream)
         return self.x
 
+    def _state(self):
+        """Tensors a step reads and writes (saved around the capture's warm-up step)."""
+        return [self.x, self.y_acc] if self.accelerate else [self.x]
+
     def capture(self, sigmas, c_wnnm: float) -> None:
         """Record one CUDA graph per distinct noise level of the schedule.
 
@@ -310,7 +349,8 @@ class SciReconstructor:
         replaying graph k advances the reconstruction exactly like step(); the
         current state of x is not modified by the capture itself.
         """
-        saved = self.x.clone()
+        state = self._state()
+        saved = [t.clone() for t in state]
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):  # library set-up happens outside the capture
@@ -326,10 +366,53 @@ class SciReconstructor:
                 self.step(key, c_wnnm)
             self._graphs[key] = g
         torch.cuda.synchronize()
-        self.x.copy_(saved)
+        for t, v in zip(state, saved):
+            t.copy_(v)
 
     def step_graph(self, sigma_w: float) -> torch.Tensor:
         """One GAP iteration by replaying the graph captured for this noise level."""
+        self._graphs[float(sigma_w)].replay()
+        return self.x
+
+
+class MriReconstructor:
+    """ADMM + GLR for Fourier-domain imaging y = M F(x) (Section 3, MRI) on one complex image.
+
+    State: x (data-consistent image), u (scaled dual), w = x + u (denoiser input),
+    z (denoiser output); all [1][2][H][W] (real, imaginary planes)."""
+
+    def __init__(self, H, W, P, N, K, mode="bf16", edge_th=0.1, rho=0.5, k_over=0, splits=0, device="cuda",
+                 cap=0, epi_batch=0):
+        self.H, self.W, self.rho = H, W, rho
+        self.den = GlrDenoiser(GlrShape(1, 2, H, W, P, N, K), mode, edge_th, k_over, splits, device, cap, epi_batch,
+                               complex_=True)
+        z = lambda: torch.zeros((1, 2, H, W), dtype=torch.float32, device=device)
+        self.x, self.u, self.w, self.z = z(), z(), z(), z()
+        self.residual = torch.zeros(1, dtype=torch.float64, device=device)
+        self.ws_admm = workspace(L.GLR_OP_ADMM, images(1, 2, H, W, 1), 1, 1, None, device)
+
+    def start(self, y: torch.Tensor, mask: torch.Tensor) -> torch.Tensor:
+        """x0 = F^-1(y) (zero-filled), u = 0."""
+        self.y = y.view(1, 2, self.H, self.W)
+        self.mask = mask.view(1, self.H, self.W)
+        fft2(self.y, inverse=True, out=self.x)
+        self.u.zero_()
+        self.w.copy_(self.x)
+        return self.x
+
+    def step(self, sigma_w: float, c_wnnm: float, stream=None) -> torch.Tensor:
+        """z = D(x + u); u += x - z; x = data-consistency(z - u)."""
+        self.den(self.w, sigma_w, c_wnnm, out=self.z, stream=stream)
+        admm_step(self.y, self.mask, self.z, self.x, self.u, self.rho, x_out=self.x, w_out=self.w,
+                  residual=self.residual, ws=self.ws_admm, stream=stream)
+        return self.x
+
+    def _state(self):
+        return [self.x, self.u, self.w, self.residual]
+
+    capture = SciReconstructor.capture
+
+    def step_graph(self, sigma_w: float) -> torch.Tensor:
         self._graphs[float(sigma_w)].replay()
         return self.x
 
