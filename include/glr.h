@@ -272,6 +272,22 @@ glr_status glr_gap_step(const float* y, const float* masks, int64_t mask_group_s
                         int32_t accelerate, float* y_acc, float* x_out, void* stream);
 
 /*
+ * Start of multispectral-filter-array demosaicing (Section 3, MSFA; the GAP
+ * iterations then refine it): per band t, the normalised convolution of the
+ * sampled values with a separable tent of half-width s,
+ *   x_t(p) = sum_q w(q - p) A_t(q) y(q) / sum_q w(q - p) A_t(q),
+ *   w(dr, dc) = (1 - |dr|/s)(1 - |dc|/s) for |dr|, |dc| < s, q inside the image,
+ * which is bilinear interpolation for a periodic mosaic of period s; 0 where
+ * no sample of band t is in the window.  The paper gives no initialisation; a
+ * zero-filled start leaves the mosaic pattern in every patch and the low-rank
+ * step cannot remove it.
+ *   y [G][H][W], masks [T][H][W] per group at element stride mask_group_stride
+ *   (0 = shared), x_out [G][T][H][W]; 1 <= s <= 16.
+ */
+glr_status glr_mosaic_init(const float* y, const float* masks, int64_t mask_group_stride, int32_t G, int32_t T,
+                           int32_t H, int32_t W, int32_t s, float* x_out, void* stream);
+
+/*
  * Orthonormal 2-D DFT of complex images (the F of the MRI model y = M F(x),
  * Section 3): X[k][l] = sum_{r,c} x[r][c] exp(-+2 pi i (k r / H + l c / W)) / sqrt(H W)
  * (minus sign forward, plus sign when inverse != 0), unshifted (index 0 is

@@ -6,3 +6,4 @@ it and shares no code with it.
 """
 from . import glr_oracle  # noqa: F401
 from . import mri_oracle  # noqa: F401
+from . import msfa_oracle  # noqa: F401

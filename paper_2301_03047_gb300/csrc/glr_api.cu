@@ -281,6 +281,14 @@ glr_status glr_lowrank_groups_complex(const float* x, const glr_images* im, cons
   return launch_wnnm_smem(*im, true, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
 }
 
+glr_status glr_mosaic_init(const float* y, const float* masks, int64_t mask_group_stride, int32_t G, int32_t T,
+                           int32_t H, int32_t W, int32_t s, float* x_out, void* stream) {
+  if (!y || !masks || !x_out || G < 1 || T < 1 || H < 1 || W < 1 || s < 1 || s > 16) return GLR_EINVAL;
+  if (mask_group_stride < 0 || (long long)G * T * H * W > (1LL << 36)) return GLR_EINVAL;
+  if ((const void*)x_out == (const void*)y || (const void*)x_out == (const void*)masks) return GLR_EINVAL;
+  return launch_mosaic_init(y, masks, mask_group_stride, G, T, H, W, s, x_out, (cudaStream_t)stream);
+}
+
 static bool pow2_side(int32_t n) { return n >= 2 && n <= 4096 && (n & (n - 1)) == 0; }
 
 glr_status glr_fft2(const float* in, float* out, int32_t n_img, int32_t H, int32_t W, int32_t inverse,

@@ -68,6 +68,8 @@ glr_status launch_gather(const float* x, const glr_images& im, const int32_t* id
                          int K, float* groups, StatusBlock* st, cudaStream_t s);
 glr_status launch_wnnm_smem(const glr_images& im, bool cplx, const int32_t* n_found, int N, int K, float sigma_w,
                             float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
+glr_status launch_mosaic_init(const float* y, const float* masks, long long mstride, int G, int T, int H, int W, int s,
+                              float* x_out, cudaStream_t st);
 glr_status launch_fft2(const float* in, float* out, int n_img, int H, int W, int inverse, cudaStream_t s);
 glr_status launch_admm_step(const float* y, const float* mask, const float* z, const float* x, float* u, int n_img,
                             int H, int W, float rho, float* x_out, float* w_out, double* residual, double* res_acc,

@@ -83,3 +83,51 @@ glr_status launch_gap_step(const float* y, const float* masks, long long mstride
 }
 
 }  // namespace glr
+
+// Start of MSFA demosaicing: per band, normalised convolution of the sampled
+// values with a separable tent of half-width s (bilinear interpolation when
+// the mosaic period is s):
+//   x_t(p) = sum_q w(q - p) A_t(q) y(q) / sum_q w(q - p) A_t(q),
+//   w(dr, dc) = (1 - |dr| / s)(1 - |dc| / s), |dr|, |dc| < s, q inside the image;
+// 0 where no sample of band t lies in the window.  One thread per output value.
+namespace glr {
+
+__global__ void __launch_bounds__(256) k_mosaic_init(const float* __restrict__ y, const float* __restrict__ masks,
+                                                     long long mstride, int G, int T, int H, int W, int s,
+                                                     float* __restrict__ x_out) {
+  const long long HW = (long long)H * W;
+  const long long total = (long long)G * T * HW;
+  const float inv_s = 1.f / (float)s;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long gt = i / HW, p = i - gt * HW;
+    const int g = (int)(gt / T), t = (int)(gt - (long long)g * T);
+    const int r = (int)(p / W), c = (int)(p - (p / W) * W);
+    const float* yg = y + g * HW;
+    const float* a = masks + g * mstride + (long long)t * HW;
+    float num = 0.f, den = 0.f;
+    for (int dr = -(s - 1); dr <= s - 1; ++dr) {
+      const int rr = r + dr;
+      if (rr < 0 || rr >= H) continue;
+      const float wr = 1.f - fabsf((float)dr) * inv_s;
+      for (int dc = -(s - 1); dc <= s - 1; ++dc) {
+        const int cc = c + dc;
+        if (cc < 0 || cc >= W) continue;
+        const float w = wr * (1.f - fabsf((float)dc) * inv_s) * __ldg(a + (long long)rr * W + cc);
+        num = fmaf(w, __ldg(yg + (long long)rr * W + cc), num);
+        den += w;
+      }
+    }
+    x_out[i] = den > 0.f ? num / den : 0.f;
+  }
+}
+
+glr_status launch_mosaic_init(const float* y, const float* masks, long long mstride, int G, int T, int H, int W, int s,
+                              float* x_out, cudaStream_t st) {
+  const long long total = (long long)G * T * H * W;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+  GLR_LAUNCH("k_mosaic_init", st, k_mosaic_init<<<blocks, 256, 0, st>>>(y, masks, mstride, G, T, H, W, s, x_out));
+  return GLR_OK;
+}
+
+}  // namespace glr

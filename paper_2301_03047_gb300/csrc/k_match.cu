@@ -136,13 +136,16 @@ template <int P>
 __global__ void __launch_bounds__(256, 2)
     k_match_fp32(const float* __restrict__ x, const float* __restrict__ mean, const float* __restrict__ qn,
                  const float* __restrict__ keyv, const int32_t* __restrict__ n_found, int C, int H, int W, int Npad,
-                 int splits, int tiles_per_split, StreamCfg cfg, uint2* __restrict__ bufs,
+                 int splits, int tiles_per_split, int cc, StreamCfg cfg, uint2* __restrict__ bufs,
                  int* __restrict__ buf_cnt, uint32_t* __restrict__ tau_gl, StatusBlock* st) {
   extern __shared__ __align__(16) float smem[];
+  // channels are processed in chunks of cc (all of them at once when the key tile fits)
   const int d = C * P * P;
-  float* As = smem;                         // [d][FT]
-  float* strip = As + d * FT;               // [C][P][FT + 8]
-  float* Sc = strip + C * P * (FT + 8);     // [FT][SC_LD]
+  const int dc_ = cc * P * P;                // key values per chunk
+  const bool one_chunk = cc >= C;
+  float* As = smem;                          // [cc P^2][FT]
+  float* strip = As + dc_ * FT;              // [cc][P][FT + 8]
+  float* Sc = strip + cc * P * (FT + 8);     // [FT][SC_LD]
   float* pn = Sc + FT * SC_LD;              // [FT]
   unsigned* hist = reinterpret_cast<unsigned*>(pn + FT);  // [8][256]
   uint32_t* tau_sh = hist + 8 * 256;                        // [FT] published thresholds of the tile's rows
@@ -154,19 +157,26 @@ __global__ void __launch_bounds__(256, 2)
   const int nf = min(n_found[f], Npad);
   const float mu = mean[f];
 
-  // key tile, transposed: As[e][i]
+  // key tile, transposed: As[e][i] (channels ch0 .. ch0 + n of every key)
   const float* kv = keyv + ((long long)f * Npad + (long long)kt * FT) * d;
-  for (int i = tid; i < d * FT; i += 256) {
-    const int key = i / d, e = i - (i / d) * d;
-    As[e * FT + key] = kv[(long long)key * d + e];
-  }
-  __syncthreads();
+  auto load_keys = [&](int ch0, int n) {
+    const int dn = n * P * P;
+    for (int i = tid; i < dn * FT; i += 256) {
+      const int key = i / dn, e = i - (i / dn) * dn;
+      As[e * FT + key] = kv[(long long)key * d + ch0 * P * P + e];
+    }
+  };
+  if (one_chunk) load_keys(0, C);
   if (tid < FT) {
     float s = 0.f;
-    for (int e = 0; e < d; ++e) s = fmaf(As[e * FT + tid], As[e * FT + tid], s);
+    for (int e = 0; e < d; ++e) {
+      const float v = kv[(long long)tid * d + e];
+      s = fmaf(v, v, s);
+    }
     pn[tid] = s;
     tau_sh[tid] = 0xffffffffu;
   }
+  __syncthreads();
   // stream owned by this thread: row = 32 (wid % 4) + lane, column half h = wid / 4
   const int row = 32 * (wid & 3) + lane;
   const int h = wid >> 2;
@@ -185,20 +195,24 @@ __global__ void __launch_bounds__(256, 2)
   const int t_end = min(ntiles, t_begin + tiles_per_split);
   for (int t = t_begin; t < t_end; ++t) {
     const int r = t / tpr, c0 = (t - (t / tpr) * tpr) * FT;
-    __syncthreads();  // previous tile fully consumed
-    for (int i = tid; i < C * P * (FT + 8); i += 256) {
-      const int cr = i / (FT + 8), j = i - (i / (FT + 8)) * (FT + 8);
-      const int ch = cr / P, dr = cr - (cr / P) * P;
-      const int cc = c0 + j;
-      strip[i] = (cc < W) ? __ldg(x + (((long long)f * C + ch) * H + r + dr) * W + cc) - mu : 0.f;
-    }
-    __syncthreads();
     float acc[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    for (int ch = 0; ch < C; ++ch) {
+#pragma unroll 1
+    for (int ch0 = 0; ch0 < C; ch0 += cc) {
+    const int nch = min(cc, C - ch0);
+    __syncthreads();  // previous chunk / tile fully consumed
+    if (!one_chunk) load_keys(ch0, nch);
+    for (int i = tid; i < nch * P * (FT + 8); i += 256) {
+      const int cr = i / (FT + 8), j = i - (i / (FT + 8)) * (FT + 8);
+      const int ch = ch0 + cr / P, dr = cr - (cr / P) * P;
+      const int col = c0 + j;
+      strip[i] = (col < W) ? __ldg(x + (((long long)f * C + ch) * H + r + dr) * W + col) - mu : 0.f;
+    }
+    __syncthreads();
+    for (int ch = 0; ch < nch; ++ch) {
 #pragma unroll
       for (int dr = 0; dr < P; ++dr) {
         float w[16];
@@ -223,6 +237,7 @@ __global__ void __launch_bounds__(256, 2)
         }
       }
     }
+    }  // channel chunks
     // scores s = ||p||^2 + ||q||^2 - 2 <p,q>; missing positions -> +inf
     {
       float qv[8];
@@ -291,7 +306,8 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
   const int d = C * P * P;
   const int Wq = W - P + 1;
   unsigned long long* list = rr_smem + (size_t)wid * pow2;
-  float* pv = reinterpret_cast<float*>(rr_smem + (size_t)RR_WARPS * pow2) + wid * 512;  // key patch (d <= 256) + 256 counters
+  const int dpad = (d + 31) & ~31;
+  float* pv = reinterpret_cast<float*>(rr_smem + (size_t)RR_WARPS * pow2) + wid * (dpad + 256);  // key patch + 256 counters
   const long long nkeys = (long long)n_img * N;
   for (long long gk = blockIdx.x * (long long)RR_WARPS + wid; gk < nkeys; gk += (long long)gridDim.x * RR_WARPS) {
     const int f = (int)(gk / N), k = (int)(gk - (long long)f * N);
@@ -334,7 +350,7 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
     // 64-bit keys, then sort those K (bitonic); ties in distance go to smaller ids
     unsigned long long T = ~0ull;
     if (total > K) {
-      unsigned* hist = reinterpret_cast<unsigned*>(pv + 256);  // 256 counters after the key patch
+      unsigned* hist = reinterpret_cast<unsigned*>(pv + dpad);  // 256 counters after the key patch
       unsigned long long prefix = 0, pmask = 0;
       int rank = K;  // 1-based rank of the wanted key among those matching the prefix
       for (int pass = 0; pass < 8; ++pass) {
@@ -536,7 +552,13 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     const glr_status st = launch_match_tc(x, im, keys, n_found, N, pl, ws, s);
     if (st != GLR_OK) return st;
   } else {
-    const size_t smem = (size_t)(d * FT + im.C * im.P * (FT + 8) + FT * SC_LD + FT) * 4 + 8 * 256 * 4 + FT * 4;
+    // channels per chunk: all of them if the transposed key tile fits, else as many as fit
+    auto fp32_smem = [&](int cc) {
+      return (size_t)(cc * im.P * im.P * FT + cc * im.P * (FT + 8) + FT * SC_LD + FT) * 4 + 8 * 256 * 4 + FT * 4;
+    };
+    int cc = im.C;
+    while (cc > 1 && fp32_smem(cc) > 227 * 1024) --cc;
+    const size_t smem = fp32_smem(cc);
     if (smem > 227 * 1024) return GLR_ENOTSUP;
     dim3 grid((unsigned)(pl.Npad / FT), (unsigned)im.n_img, (unsigned)pl.splits);
 #define GLR_FP32_CASE(PP)                                                                                    \
@@ -546,7 +568,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
       return GLR_ECUDA;                                                                                      \
     GLR_LAUNCH("k_match_fp32", s,                                                                           \
                k_match_fp32<PP><<<grid, 256, smem, s>>>(x, mean, qn, keyv, n_found, im.C, im.H, im.W, pl.Npad,  \
-                                                        pl.splits, pl.tiles_per_split, cfg, bufs, bufcnt, taugl,   \
+                                                        pl.splits, pl.tiles_per_split, cc, cfg, bufs, bufcnt, taugl, \
                                                         reinterpret_cast<StatusBlock*>(ws)));                      \
   } break;
     switch (im.P) {
@@ -565,8 +587,9 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
   {
     int pow2 = 32;
     while (pow2 < pl.streams_per_key * pl.Kp) pow2 <<= 1;
-    const size_t smem = (size_t)RR_WARPS * pow2 * 8 + (size_t)RR_WARPS * 512 * 4;
-    if (smem > 227 * 1024 || d > 256) return GLR_ENOTSUP;
+    const int dpad = (d + 31) & ~31;
+    const size_t smem = (size_t)RR_WARPS * pow2 * 8 + (size_t)RR_WARPS * (dpad + 256) * 4;
+    if (smem > 227 * 1024 || d > 640) return GLR_ENOTSUP;
     if (cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return GLR_ECUDA;
     const long long nkeys = (long long)im.n_img * N;

@@ -346,3 +346,96 @@ def mri_problem(cfg: MriConfig, extra: int = 0) -> MriProblem:
     k = k + cfg.noise_sigma * (rn.standard_normal(k.shape) + 1j * rn.standard_normal(k.shape))
     k = k * mask
     return MriProblem(cfg, truth, mask, np.stack([k.real, k.imag]).astype(np.float32))
+
+
+# ----------------------------------------------------------------------------
+# MSFA: multispectral filter-array demosaicing, uneven image sizes (Section 3, MSFA)
+# ----------------------------------------------------------------------------
+@dataclass(frozen=True)
+class MsfaConfig:
+    """A batch of MSFA snapshots y = sum_b A_b x_b (Eq. 4 of the MSFA section) of uneven sizes."""
+
+    name: str
+    config_no: int
+    sides: tuple  # image side of every image of the batch (square images)
+    bands: int
+    P: int
+    K: int
+    iters: int
+    N_fixed: int = 0  # 0: N = min(8192, 1024 (side / 256)^2) per image
+    sigma_first: float = 0.1
+    sigma_last: float = 0.02
+    edge_th: float = 0.1
+
+    @property
+    def c_wnnm(self) -> float:
+        return 2.0 * math.sqrt(self.K)
+
+    def N_of(self, side: int) -> int:
+        if self.N_fixed:
+            return self.N_fixed
+        return int(min(8192, 1024 * (side / 256.0) ** 2))
+
+    def sigma_schedule(self) -> list[float]:
+        if self.iters == 1:
+            return [self.sigma_last]
+        r = (self.sigma_last / self.sigma_first) ** (1.0 / (self.iters - 1))
+        return [float(self.sigma_first * r**k) for k in range(self.iters)]
+
+
+def msfa_sides(n: int, seed_no: int = 4, choices=(256, 384, 512, 768, 1024)) -> tuple:
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([SEED_BASE + seed_no, 77])))
+    return tuple(int(v) for v in rng.choice(np.asarray(choices), size=n))
+
+
+MSFA_SMALL = MsfaConfig("msfa_3img_40-64_16band_P6_N48_K16", 4, sides=(40, 56, 64), bands=16, P=6, K=16, iters=2,
+                        N_fixed=48)
+MSFA_LARGE = MsfaConfig("msfa_32img_256-1024_16band_P6_K32", 4, sides=msfa_sides(32), bands=16, P=6, K=32, iters=10)
+
+
+def mosaic_masks(H: int, W: int, bands: int = 16) -> np.ndarray:
+    """Periodic square mosaic [bands][H][W] (0/1): pixel (r, c) sees band s*(r mod s) + (c mod s), s = sqrt(bands)."""
+    s = int(round(math.sqrt(bands)))
+    assert s * s == bands
+    r = np.arange(H)[:, None] % s
+    c = np.arange(W)[None, :] % s
+    band = s * r + c
+    return (band[None] == np.arange(bands)[:, None, None]).astype(np.float32)
+
+
+def spectral_cube(rng: np.random.Generator, bands: int, H: int, W: int, materials: int = 6) -> np.ndarray:
+    """Multispectral image [bands][H][W] in [0, 1]: `materials` spectra (each a sum of 4
+    Gaussians over the band index, peak-normalised) mixed by abundance maps drawn from
+    the scene model (independent textured frames, normalised to sum 1 per pixel),
+    times a shading map from the scene model."""
+    b = np.arange(bands, dtype=np.float64)
+    spectra = np.zeros((materials, bands))
+    for m in range(materials):
+        for _ in range(4):
+            spectra[m] += rng.uniform(0.2, 1.0) * np.exp(-0.5 * ((b - rng.uniform(0, bands - 1)) / rng.uniform(1.0, 4.0)) ** 2)
+        spectra[m] /= spectra[m].max()
+    ab = textured_frames(rng, materials, H, W).astype(np.float64) ** 3 + 1e-3
+    ab /= ab.sum(0, keepdims=True)
+    shade = 0.4 + 0.6 * textured_frames(rng, 1, H, W)[0].astype(np.float64)
+    cube = np.einsum("mhw,mb->bhw", ab, spectra) * shade[None]
+    return np.clip(cube, 0.0, 1.0).astype(np.float32)
+
+
+@dataclass
+class MsfaImage:
+    truth: np.ndarray  # [bands][H][W]
+    masks: np.ndarray  # [bands][H][W]
+    y: np.ndarray  # [H][W]
+    N: int
+
+
+def msfa_problem(cfg: MsfaConfig, extra: int = 0) -> list:
+    """Noiseless mosaic snapshots y = sum_b A_b x_b, one per image of the batch."""
+    rs, _, _ = streams(cfg.config_no, extra)
+    out = []
+    for side in cfg.sides:
+        truth = spectral_cube(rs, cfg.bands, side, side)
+        masks = mosaic_masks(side, side, cfg.bands)
+        y = (masks.astype(np.float64) * truth).sum(0).astype(np.float32)
+        out.append(MsfaImage(truth, masks, y, cfg.N_of(side)))
+    return out
