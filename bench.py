@@ -286,6 +286,11 @@ def workload(name: str):
         return synth.scaled(synth.SCI_LARGE, T=4, name="sci_4x512x512_P8_N4096_K64")
     if name == "sci8":
         return synth.SCI_SMALL
+    if name == "msfa32":
+        return synth.MSFA_LARGE
+    if name == "msfa4":  # profiling case: four images of the batch
+        return synth.MsfaConfig("msfa_4img_512-1024_16band_P6_K32", 4, sides=(1024, 768, 512, 384), bands=16, P=6,
+                                K=32, iters=10)
     if name == "mri1024":
         return synth.MRI_LARGE
     if name == "mri256":  # profiling case of the MRI path
@@ -310,6 +315,8 @@ def run_glr(args) -> None:
     cfg = workload(args.workload)
     if isinstance(cfg, synth.MriConfig):
         return run_mri(args, cfg, dev, dist)
+    if isinstance(cfg, synth.MsfaConfig):
+        return run_msfa(args, cfg, dev, dist)
     prob = synth.sci_problem(cfg)
     y = torch.from_numpy(prob.y).to(dev)
     masks = torch.from_numpy(prob.masks).to(dev)
@@ -697,6 +704,204 @@ def run_mri(args, cfg, dev, dist) -> None:
     print(json.dumps(line))
 
 
+MSFA_METRIC = "GLR GAP iterations/s on MSFA demosaicing of an uneven batch (chosen BF16 form; plain FP32 alongside)"
+
+
+def oracle_sample_msfa(n_keys: int = 4) -> dict:
+    from oracle import glr_oracle as O
+    from oracle import msfa_oracle as FO
+    from paper_2301_03047_gb300 import synth
+
+    cfg = synth.MSFA_LARGE
+    side = 256  # one of the batch's smallest images; the rest scale by their key and position counts
+    im = synth.msfa_problem(synth.MsfaConfig("s", cfg.config_no, sides=(side,), bands=cfg.bands, P=cfg.P, K=cfg.K,
+                                             iters=1))[0]
+    x = FO.mosaic_init(im.y, im.masks, 4)
+    t0 = time.perf_counter()
+    keys, _ = O.select_keys(x, cfg.P, im.N, cfg.edge_th)
+    Q = O.patch_matrix(x, cfg.P)
+    t_fixed = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    idx, _ = O.match_topk(x, cfg.P, keys[:n_keys], cfg.K, Q)
+    g = O.gather_groups(x, cfg.P, idx, Q)
+    xh, _ = O.lowrank_groups(g, cfg.sigma_schedule()[0], cfg.c_wnnm)
+    O.aggregate(xh, idx, x, cfg.P)
+    t_key = (time.perf_counter() - t0) / n_keys
+    npos0 = (side - cfg.P + 1) ** 2
+    # per-key work scales with the positions searched; fixed work with the pixels
+    t_iter = sum(t_fixed * (s / side) ** 2 + cfg.N_of(s) * t_key * ((s - cfg.P + 1) ** 2 / npos0) for s in cfg.sides)
+    return {"t_iter_s": t_iter, "iters_per_s": 1.0 / t_iter,
+            "sample": f"one {side}x{side} image: key selection + {n_keys} of {im.N} keys matched over all {npos0} "
+            f"positions, grouped, WNNM, aggregated; extrapolated by pixels and positions to the {len(cfg.sides)} images"}
+
+
+def run_msfa(args, cfg, dev, dist) -> None:
+    import numpy as np
+    import torch
+
+    from paper_2301_03047_gb300 import glr, synth
+
+    ws, rank, local = dist_info()
+    imgs = synth.msfa_problem(cfg)
+    sides = [im.y.shape[0] for im in imgs]
+    Ns = [im.N for im in imgs]
+    ys = [torch.from_numpy(im.y).to(dev) for im in imgs]
+    masks = {s: torch.from_numpy(synth.mosaic_masks(s, s, cfg.bands)).to(dev) for s in set(sides)}
+    sched = cfg.sigma_schedule()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    forms = [args.mode] + (["fp32"] if args.mode != "fp32" and not args.no_plain else [])
+    results = {}
+    prof = clocks_summary = None
+    launches = 0
+    sweeps = 0.0
+    pairs = sum(n * (s - cfg.P + 1) ** 2 for s, n in zip(sides, Ns))
+
+    def psnr(rec):
+        return float(np.mean([10 * math.log10(1.0 / float(np.mean((x.cpu().numpy() - im.truth) ** 2)))
+                              for x, im in zip(rec.images(), imgs)]))
+
+    for form in forms:
+        rec = glr.MsfaBatchReconstructor(sides, Ns, cfg.bands, cfg.P, cfg.K, mode=form, edge_th=cfg.edge_th,
+                                         device=dev)
+        rec.start(ys, masks)
+        steps = args.steps
+        k = 0
+        for _ in range(args.warmup):
+            rec.step(sched[k % len(sched)], cfg.c_wnnm)
+            k += 1
+        torch.cuda.synchronize()
+        headline = form == forms[0]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = glr.launch_count()
+        clk = Clocks(local) if headline else None
+        if clk:
+            clk.__enter__()
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record()
+            rec.step(sched[k % len(sched)], cfg.c_wnnm)
+            ev[i][1].record()
+            k += 1
+        torch.cuda.synchronize()
+        if clk:
+            clk.__exit__()
+            clocks_summary = clk.summary()
+        total_s = reduce_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, dist, dev)
+        if headline:
+            launches = glr.launch_count() - l0
+        results[form] = {"total_s": total_s, "steps": steps, "ms_per_step": total_s / steps * 1e3, "psnr": psnr(rec)}
+        if headline:
+            # per-kernel times with the classes run one after the other (concurrent classes would
+            # stretch each other's event intervals)
+            rec.concurrent = False
+            glr.profile_enable(True)
+            glr.profile_collect()
+            rec.step(sched[k % len(sched)], cfg.c_wnnm)
+            torch.cuda.synchronize()
+            prof = glr.profile_collect()
+            glr.profile_enable(False)
+            rec.concurrent = True
+            sw_groups = [glr.poll_status(c["den"].ws_lowrank)[1] for c in rec.classes]
+            sweeps = sum(c[2] for c in sw_groups) / max(1, sum(c[3] for c in sw_groups))
+            if not args.no_graph:
+                rec.capture(sched, cfg.c_wnnm)
+                for i in range(args.warmup):
+                    rec.step_graph(sched[i % len(sched)])
+                gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+                torch.cuda.synchronize()
+                for i in range(steps):
+                    flush.zero_()
+                    gev[i][0].record()
+                    rec.step_graph(sched[(args.warmup + i) % len(sched)])
+                    gev[i][1].record()
+                torch.cuda.synchronize()
+                g_s = reduce_max(sum(a.elapsed_time(b) for a, b in gev) / 1e3, dist, dev)
+                results["graph"] = {"ms_per_step": g_s / steps * 1e3, "value": ws * steps / g_s}
+        del rec
+        torch.cuda.empty_cache()
+    head = results[forms[0]]
+    e2e = None
+    if not args.no_e2e:
+        y_h = [torch.from_numpy(im.y).pin_memory() for im in imgs]
+        rec = glr.MsfaBatchReconstructor(sides, Ns, cfg.bands, cfg.P, cfg.K, mode=forms[0], edge_th=cfg.edge_th,
+                                         device=dev)
+        y_d = [torch.empty_like(y) for y in ys]
+        for a, b in zip(y_d, y_h):
+            a.copy_(b, non_blocking=True)
+        rec.start(y_d, masks)
+        out_h = [torch.empty((cfg.bands, s, s), dtype=torch.float32).pin_memory() for s in sides]
+        for i in range(args.warmup):
+            rec.step(sched[i % len(sched)], cfg.c_wnnm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(head["steps"]):
+            for c in rec.classes:  # the snapshots of each class come from pinned host memory
+                for j, idx in enumerate(c["ids"]):
+                    c["y"][j].copy_(y_h[idx], non_blocking=True)
+            rec.step(sched[i % len(sched)], cfg.c_wnnm)
+            for o, x in zip(out_h, rec.images()):
+                o.copy_(x, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
+        e2e = {"value": round(ws * head["steps"] / e2e_s, 4), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(y.numel() for y in y_h) * 4),
+               "d2h_bytes_per_step": int(sum(o.numel() for o in out_h) * 4)}
+        del rec
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu:
+        try:
+            o = run_oracle_child(min(args.oracle_keys, 16), "oracle_sample_msfa")
+            cpu = {"value": round(o["iters_per_s"], 8), "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": o["sample"], "t_iter_s": round(o["t_iter_s"], 1)}
+        except Exception as e:
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+    pk = peaks()
+    rl = None
+    if prof:
+        name, (ms, n) = max(prof.items(), key=lambda kv: kv[1][0])
+        rl = {"kernel": name, "ms_per_step_serial": round(ms, 3), "launches": n,
+              "note": "per-kernel times from one iteration with the size classes serialised"}
+        if name == "k_match_tc":
+            work = 2.0 * cfg.bands * cfg.P * cfg.P * pairs
+            rl.update({"bound": "tensor", "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                       "achieved": round(work / (ms / 1e3) / 1e12, 2)})
+            rl["frac"] = round(rl["achieved"] / rl["peak"], 4)
+    line = {
+        "metric": MSFA_METRIC, "value": round(ws * head["steps"] / head["total_s"], 4), "unit": UNIT, "n_gpus": ws,
+        "steps": head["steps"], "warmup": args.warmup, "ms_per_step": round(head["ms_per_step"], 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if forms[0] == "bf16" else "f32",
+        "data": "synthetic (seeded spectral cubes: 6 materials x 4-Gaussian spectra, textured abundances; 4x4 mosaic)",
+        "config": {"workload": cfg.name, "images": len(sides), "sides": sorted(set(sides)), "bands": cfg.bands,
+                   "P": cfg.P, "d": cfg.bands * cfg.P * cfg.P, "K": cfg.K, "keys_total": int(sum(Ns)),
+                   "pairs_per_iter": int(pairs), "match_form": forms[0], "parallelism": f"replicas x{ws}",
+                   "batching": "size classes on concurrent streams",
+                   "l2": "flushed (256 MB write) between timed steps"},
+        "pair_dists_per_s": round(ws * pairs * head["steps"] / head["total_s"], 1), "psnr_db": round(head["psnr"], 3),
+        "gpu_launches": launches,
+        "kernels_serial": {k: {"ms": round(v[0], 3), "launches": v[1]}
+                           for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])} if prof else {},
+        "svd_sweeps_per_group": round(sweeps, 2),
+        "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks_summary,
+    }
+    if "graph" in results:
+        line["cuda_graph"] = {"value": round(results["graph"]["value"], 4), "unit": UNIT,
+                              "ms_per_step": round(results["graph"]["ms_per_step"], 3)}
+    if len(forms) > 1:
+        pl = results["fp32"]
+        line["plain"] = {"value": round(ws * pl["steps"] / pl["total_s"], 4), "unit": UNIT,
+                         "ms_per_step": round(pl["ms_per_step"], 3), "psnr_db": round(pl["psnr"], 3),
+                         "steps": pl["steps"]}
+        line["speedup_vs_plain"] = round(pl["ms_per_step"] / head["ms_per_step"], 3)
+        line["delta_psnr_db"] = round(head["psnr"] - pl["psnr"], 4)
+    print(json.dumps(line))
+
+
 def run_reference(args) -> None:
     ws, rank, _ = dist_info()
     if rank != 0:
@@ -749,9 +954,11 @@ def main() -> None:
     ap.add_argument("--impl", default="glr", choices=["glr", "reference"])
     ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--oracle-keys", type=int, default=96)
-    ap.add_argument("--workload", default="sci16", choices=["sci16", "sci4", "sci8", "mri1024", "mri256"],
+    ap.add_argument("--workload", default="sci16",
+                    choices=["sci16", "sci4", "sci8", "mri1024", "mri256", "msfa32", "msfa4"],
                     help="sci16 = the headline workload; mri1024 = the MRI (ADMM) path on 1024^2 complex; "
-                    "sci4 / sci8 / mri256 are smaller cases for profiling")
+                    "msfa32 = MSFA demosaicing of 32 images of uneven sizes; sci4 / sci8 / mri256 / msfa4 are "
+                    "smaller cases for profiling")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

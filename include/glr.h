@@ -223,7 +223,10 @@ glr_status glr_lowrank_groups_complex(const float* x, const glr_images* im, cons
 /*
  * Aggregation: every group column is added back at its patch position with
  * weight 1 and overlapping estimates are averaged; pixels no patch covers
- * keep x_in.  v_out must not alias groups; it may alias x_in.
+ * keep x_in.  The sums are accumulated in 64-bit fixed point (2^-32 units), so
+ * the result does not depend on the order of the additions (run to run and
+ * eager vs graph replay give identical bits).  v_out must not alias groups; it
+ * may alias x_in.
  *   groups float32 [n_img][N][K][d], idx int32 [n_img][N][K],
  *   x_in, v_out float32 [n_img][C][H][W].
  */
@@ -241,7 +244,7 @@ glr_status glr_aggregate(const float* groups, const int32_t* idx, const int32_t*
  *
  * Scratch comes from a 16 MiB array in device memory that the library
  * reserves on every GPU that loads it, until the process exits.  Problems whose
- * scratch (256 + n_img*C*H*W*4 + n_img*Hq*Wq*4 bytes, each part rounded up to
+ * scratch (256 + n_img*C*H*W*8 + n_img*Hq*Wq*4 bytes, each part rounded up to
  * 256) exceeds it return GLR_ETOOBIG without launching.  All calls share the
  * array and leave their contents in it (each call clears what must start at
  * zero); calls that overlap on the GPU race on it, so serialise them.  The

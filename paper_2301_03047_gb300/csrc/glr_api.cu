@@ -258,6 +258,9 @@ glr_status glr_lowrank_groups(const float* x, const glr_images* im, const int32_
   st = launch_gather(x, *im, idx, n_found, N, K, groups, (StatusBlock*)ws, s);
   if (st != GLR_OK) return st;
   if (d <= 64 && K <= 64) return launch_wnnm(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
+  // tall groups: Gram matrix + two-sided Jacobi (work O(d K^2) once instead of per sweep)
+  if (K <= 32 && d >= 2 * K)
+    return launch_gram_wnnm(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
   return launch_wnnm_smem(*im, false, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
 }
 

@@ -34,6 +34,7 @@ struct MatchPlan {
   int pos_tiles;        // position tiles per image
   int tiles_per_split;
   int dk;               // BF16 operand row length (elements)
+  int nkc;              // 64-column chunks of patch values in a BF16 operand row (1 unless d > 74)
   int epi_batch;        // tensor-core epilogue: 32-column chunks read from TMEM per visit (2 or 4)
   long long npos_pad;   // BF16 position rows per image (pos_tiles * pos_tile)
   size_t mean_off, qn_off, keyv_off, buf_off, bufcnt_off, taugl_off, qpack_off, kpack_off, embp_off, embk_off, total;
@@ -66,6 +67,8 @@ extern float* g_tc_dump;
 // ---- low-rank step (k_lowrank.cu)
 glr_status launch_gather(const float* x, const glr_images& im, const int32_t* idx, const int32_t* n_found, int N,
                          int K, float* groups, StatusBlock* st, cudaStream_t s);
+glr_status launch_gram_wnnm(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
+                            float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
 glr_status launch_wnnm_smem(const glr_images& im, bool cplx, const int32_t* n_found, int N, int K, float sigma_w,
                             float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
 glr_status launch_mosaic_init(const float* y, const float* masks, long long mstride, int G, int T, int H, int W, int s,

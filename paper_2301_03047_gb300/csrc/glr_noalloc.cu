@@ -12,7 +12,7 @@
 //   * The array holds kNoAllocScratchBytes (16 MiB) and is reserved on every
 //     GPU that loads the library, until the process exits.
 //   * Problems whose scratch does not fit are rejected with GLR_ETOOBIG before
-//     anything is launched (scratch = 256 + n_img*C*H*W*4 + n_img*Hq*Wq*4 bytes,
+//     anything is launched (scratch = 256 + n_img*C*H*W*8 + n_img*Hq*Wq*4 bytes,
 //     each part rounded up to 256 bytes).
 //   * Every call shares the same array and leaves its contents behind; each call
 //     clears what must start at zero.  Calls whose work overlaps on the GPU

@@ -2,10 +2,13 @@
 // overlapping estimates are averaged (weight 1); uncovered pixels keep x_in.
 //
 //  k_scatter    one warp per matched patch (group row); lanes add its d values
-//               into the numerator planes with FP32 atomics (L2-resident), and
-//               lane 0 adds 1 to the integer count of that patch position.
+//               into the numerator planes as 64-bit fixed point (value x 2^32,
+//               rounded to an integer: exact for |value| >= 2^-9, else within
+//               2^-33) with integer atomics, so the sums do not depend on the
+//               order in which the atomics land; lane 0 adds 1 to the integer
+//               count of that patch position.
 //  k_normalise  32x32 pixel tiles: den = P x P box sum of the position counts
-//               (separable, in shared memory), v = num / den or x_in.
+//               (separable, in shared memory), v = num 2^-32 / den (FP64) or x_in.
 #include "glr_kernels.cuh"
 
 namespace glr {
@@ -14,7 +17,7 @@ namespace {
 
 __global__ void __launch_bounds__(256) k_scatter(const float* __restrict__ groups, const int32_t* __restrict__ idx,
                                                  const int32_t* __restrict__ n_found, int n_img, int C, int H, int W,
-                                                 int P, int N, int K, float* __restrict__ num,
+                                                 int P, int N, int K, unsigned long long* __restrict__ num,
                                                  int* __restrict__ cnt, StatusBlock* st) {
   const int d = C * P * P;
   const int Wq = W - P + 1, Hq = H - P + 1;
@@ -34,7 +37,10 @@ __global__ void __launch_bounds__(256) k_scatter(const float* __restrict__ group
     const float* src = groups + row * d;
     for (int e = lane; e < d; e += 32) {
       const int ch = e / (P * P), rr = (e / P) % P, cc = e % P;
-      atomicAdd(num + ((f * C + ch) * H + r + rr) * (long long)W + c + cc, __ldg(src + e));
+      // |value| < 2^30 keeps every partial sum of up to 2^32 terms inside int64
+      const float v = fminf(fmaxf(__ldg(src + e), -1073741824.f), 1073741824.f);
+      const long long fx = __float2ll_rn(v * 4294967296.f);  // exact scaling by 2^32
+      atomicAdd(num + ((f * C + ch) * H + r + rr) * (long long)W + c + cc, (unsigned long long)fx);
     }
     if (lane == 0) atomicAdd(cnt + f * (long long)Hq * Wq + q, 1);
   }
@@ -42,7 +48,7 @@ __global__ void __launch_bounds__(256) k_scatter(const float* __restrict__ group
 
 constexpr int AT = 32;
 
-__global__ void __launch_bounds__(256) k_normalise(const float* __restrict__ num, const int* __restrict__ cnt,
+__global__ void __launch_bounds__(256) k_normalise(const long long* __restrict__ num, const int* __restrict__ cnt,
                                                    const float* x_in, float* v_out, int C, int H, int W, int P) {
   // counts of positions that cover the tile: rows r0-P+1 .. r0+AT-1
   __shared__ int cs[AT + 16][AT + 16];
@@ -74,7 +80,7 @@ __global__ void __launch_bounds__(256) k_normalise(const float* __restrict__ num
     for (int t = 0; t < P; ++t) den += hs[a + t][b];
     for (int ch = 0; ch < C; ++ch) {
       const long long o = (((long long)f * C + ch) * H + rr) * W + cc;
-      v_out[o] = den > 0 ? num[o] / (float)den : x_in[o];
+      v_out[o] = den > 0 ? (float)((double)num[o] * 2.3283064365386963e-10 / (double)den) : x_in[o];
     }
   }
 }
@@ -84,7 +90,7 @@ __global__ void __launch_bounds__(256) k_normalise(const float* __restrict__ num
 AggWs agg_ws_layout(const glr_images& im) {
   WsLayout L;
   AggWs w;
-  w.num_off = L.take((size_t)im.n_img * im.C * im.H * im.W * 4);
+  w.num_off = L.take((size_t)im.n_img * im.C * im.H * im.W * 8);
   w.cnt_off = L.take((size_t)im.n_img * (im.H - im.P + 1) * (im.W - im.P + 1) * 4);
   w.total = L.off;
   return w;
@@ -93,9 +99,9 @@ AggWs agg_ws_layout(const glr_images& im) {
 glr_status launch_aggregate(const float* groups, const int32_t* idx, const int32_t* n_found, const glr_images& im,
                             int N, int K, const float* x_in, float* v_out, char* ws, const AggWs& L,
                             cudaStream_t s) {
-  float* num = reinterpret_cast<float*>(ws + L.num_off);
+  unsigned long long* num = reinterpret_cast<unsigned long long*>(ws + L.num_off);
   int* cnt = reinterpret_cast<int*>(ws + L.cnt_off);
-  const size_t num_b = (size_t)im.n_img * im.C * im.H * im.W * 4;
+  const size_t num_b = (size_t)im.n_img * im.C * im.H * im.W * 8;
   const size_t cnt_b = (size_t)im.n_img * (im.H - im.P + 1) * (im.W - im.P + 1) * 4;
   if (cudaMemsetAsync(num, 0, num_b, s) != cudaSuccess) return GLR_ECUDA;
   if (cudaMemsetAsync(cnt, 0, cnt_b, s) != cudaSuccess) return GLR_ECUDA;
@@ -103,7 +109,7 @@ glr_status launch_aggregate(const float* groups, const int32_t* idx, const int32
   const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(rows * 32, 256), 152LL * 32));
   GLR_LAUNCH("k_scatter", s, k_scatter<<<blocks, 256, 0, s>>>(groups, idx, n_found, im.n_img, im.C, im.H, im.W, im.P, N, K, num, cnt, reinterpret_cast<StatusBlock*>(ws)));
   dim3 g((unsigned)ceil_div(im.W, AT), (unsigned)ceil_div(im.H, AT), (unsigned)im.n_img);
-  GLR_LAUNCH("k_normalise", s, k_normalise<<<g, 256, 0, s>>>(num, cnt, x_in, v_out, im.C, im.H, im.W, im.P));
+  GLR_LAUNCH("k_normalise", s, k_normalise<<<g, 256, 0, s>>>(reinterpret_cast<const long long*>(num), cnt, x_in, v_out, im.C, im.H, im.W, im.P));
   return GLR_OK;
 }
 

@@ -277,7 +277,239 @@ __global__ void __launch_bounds__(WJ_THREADS) k_jacobi_smem(int n_img, int dr, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// k_gram_wnnm: tall real groups (d >= 2K, K <= 32), one warp per group.
+// The K x K Gram matrix G = Y^T Y is formed in FP32 (Y streamed through a
+// 32 x 32 shared-memory tile), diagonalised by the cyclic two-sided Jacobi
+// method (G <- J^T G J, V <- V J, 16 disjoint pairs per round, circle
+// ordering), and X^ = Y V diag(c) V^T with c_i = s'_i / s_i, s_i = sqrt(l_i):
+// since Y v_i = s_i u_i, this is U diag(s') V^T.  Work per group is
+// O(d K^2) once instead of per sweep, and the weights c_i <= 1 never amplify
+// rounding.  Eigenvalues carry an absolute error of order 2^-24 l_max, which
+// moves components near the WNNM threshold only (the shrinkage removes them).
+// The WNNM skip rule of the one-sided kernels applies to the diagonal, and
+// off-diagonal entries below the Gram matrix's rounding level (4 ulps of its
+// largest diagonal entry) are not rotated: they carry no information, and the
+// relative test alone would never be met among components at that level.
+// ---------------------------------------------------------------------------
+constexpr int GW_WARPS = 4;
+constexpr int GW_LD = 33;
+
+__device__ __forceinline__ void circle_pair(int k, int r, int& p, int& q) {  // n = 32 slots
+  if (k == 0) {
+    p = r;
+    q = 31;
+  } else {
+    p = (r + k) % 31;
+    q = (r - k + 31) % 31;
+  }
+}
+
+__global__ void __launch_bounds__(GW_WARPS * 32) k_gram_wnnm(int n_img, int d, int N, int K,
+                                                             const int32_t* __restrict__ n_found, float sigma_w,
+                                                             float c_wnnm, float tol, int max_sweeps,
+                                                             float* __restrict__ groups, int32_t* __restrict__ rank,
+                                                             StatusBlock* st) {
+  __shared__ float Gs[GW_WARPS][32][GW_LD];
+  __shared__ float Vs[GW_WARPS][32][GW_LD];
+  __shared__ float Ts[GW_WARPS][32][GW_LD];
+  __shared__ float2 cs_s[GW_WARPS][16];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float(*G)[GW_LD] = Gs[wid];
+  float(*V)[GW_LD] = Vs[wid];
+  float(*T)[GW_LD] = Ts[wid];
+  float2* cs = cs_s[wid];
+  const long long ngroups = (long long)n_img * N;
+  const float lam = (float)K * sigma_w * sigma_w;
+  for (long long g = blockIdx.x * (long long)GW_WARPS + wid; g < ngroups; g += (long long)gridDim.x * GW_WARPS) {
+    const int f = (int)(g / N), k = (int)(g - (long long)f * N);
+    if (k >= min(n_found[f], N)) continue;
+    float* Y = groups + g * (long long)K * d;
+    // ---- Gram matrix: lane j accumulates row j
+    float gacc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) gacc[i] = 0.f;
+    bool bad = false;
+    for (int r0 = 0; r0 < d; r0 += 32) {
+      const int rr = r0 + lane;
+      for (int j = 0; j < 32; ++j) {
+        const float v = (j < K && rr < d) ? Y[(long long)j * d + rr] : 0.f;
+        bad |= !isfinite(v);
+        T[lane][j] = v;
+      }
+      __syncwarp();
+#pragma unroll 4
+      for (int t = 0; t < 32; ++t) {
+        const float yj = T[t][lane];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) gacc[i] = fmaf(T[t][i], yj, gacc[i]);
+      }
+      __syncwarp();
+    }
+    if (__any_sync(0xffffffffu, bad)) {
+      if (lane == 0) {
+        status_set(st, GLR_DEV_NONFINITE);
+        if (rank) rank[g] = -1;
+      }
+      continue;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      G[lane][i] = gacc[i];
+      V[lane][i] = (i == lane) ? 1.f : 0.f;
+    }
+    __syncwarp();
+    // ---- cyclic two-sided Jacobi on G
+    int sweep = 0;
+    bool converged = K < 2;
+    bool gersh_ok = false;
+    while (!converged && sweep < max_sweeps) {
+      // WNNM skip rule (see the one-sided kernels): diagonal entries below lam form the block
+      const float dii = G[lane][lane];
+      float small = (lane < K && dii < lam) ? dii : 0.f;
+      float dmax = dii;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        small += __shfl_xor_sync(0xffffffffu, small, o);
+        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      }
+      // entries of G below its FP32 rounding level (a few ulps of the largest
+      // diagonal entry) carry no information: they are not rotated away
+      const float gfloor = 2.384e-7f * dmax;
+      const float lam_skip = (lam > 0.f && (small < lam || gersh_ok)) ? lam : 0.f;
+      bool rotated = false;
+      for (int r = 0; r < 31; ++r) {
+        if (lane < 16) {
+          int p, q;
+          circle_pair(lane, r, p, q);
+          const float app = G[p][p], aqq = G[q][q], apq = G[p][q];
+          float c = 1.f, s = 0.f;
+          if (fabsf(apq) > tol * sqrtf(fabsf(app * aqq)) && fabsf(apq) > gfloor &&
+              (app >= lam_skip || aqq >= lam_skip)) {
+            const float tau = (aqq - app) / (2.f * apq);
+            const float at = fabsf(tau);
+            float t = (at < 1e18f) ? 1.f / (at + sqrtf(fmaf(tau, tau, 1.f))) : 0.5f / at;
+            t = copysignf(t, tau);
+            c = rsqrtf(fmaf(t, t, 1.f));
+            s = t * c;
+            rotated = true;
+          }
+          cs[lane] = make_float2(c, s);
+        }
+        __syncwarp();
+        // columns of G and V: lane = row
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+          const float2 w = cs[kk];
+          if (w.y == 0.f) continue;
+          int p, q;
+          circle_pair(kk, r, p, q);
+          const float gp = G[lane][p], gq = G[lane][q];
+          G[lane][p] = fmaf(w.x, gp, -w.y * gq);
+          G[lane][q] = fmaf(w.y, gp, w.x * gq);
+          const float vp = V[lane][p], vq = V[lane][q];
+          V[lane][p] = fmaf(w.x, vp, -w.y * vq);
+          V[lane][q] = fmaf(w.y, vp, w.x * vq);
+        }
+        __syncwarp();
+        // rows of G: lane = column
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+          const float2 w = cs[kk];
+          if (w.y == 0.f) continue;
+          int p, q;
+          circle_pair(kk, r, p, q);
+          const float gp = G[p][lane], gq = G[q][lane];
+          G[p][lane] = fmaf(w.x, gp, -w.y * gq);
+          G[q][lane] = fmaf(w.y, gp, w.x * gq);
+        }
+        __syncwarp();
+      }
+      ++sweep;
+      converged = !__any_sync(0xffffffffu, rotated);
+      // Gershgorin bound of the block below lam on the current matrix, for the next sweep
+      float gb = 0.f;
+      if (lane < K && G[lane][lane] < lam) {
+        float rs = G[lane][lane];
+        for (int j = 0; j < K; ++j)
+          if (j != lane && G[j][j] < lam) rs += fabsf(G[lane][j]);
+        gb = rs;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) gb = fmaxf(gb, __shfl_xor_sync(0xffffffffu, gb, o));
+      gersh_ok = gb < 0.5f * lam;
+    }
+    if (lane == 0) {
+      if (!converged) {
+        atomicAdd(&st->svd_noconv, 1u);
+        status_set(st, GLR_DEV_SVD_NOCONV);
+      }
+      atomicAdd(&st->sweeps, (unsigned)sweep);
+      atomicAdd(&st->groups, 1u);
+    }
+    // ---- WNNM weights c_i = s'_i / s_i
+    const float li = G[lane][lane];
+    float ci = 0.f;
+    if (lane < K && li > 0.f) {
+      const float sg = sqrtf(li);
+      const float sh = sqrtf(fmaxf(li - lam, 0.f));
+      const float sp = fmaxf(sg - c_wnnm * sigma_w * sigma_w / (sh + 1e-8f), 0.f);
+      ci = sp / sg;
+    }
+    const unsigned act = __ballot_sync(0xffffffffu, ci > 0.f);
+    if (rank && lane == 0) rank[g] = __popc(act);
+    __syncwarp();
+    // M = V diag(c) V^T, lane j keeps column j
+    float mcol[32];
+    {
+      float vj[32];
+#pragma unroll
+      for (int kk = 0; kk < 32; ++kk) vj[kk] = V[lane][kk] * __shfl_sync(0xffffffffu, ci, kk);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        float m = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) m = fmaf(V[i][kk], vj[kk], m);
+        mcol[i] = m;
+      }
+    }
+    // ---- X^ = Y M, 32 rows at a time, in place
+    for (int r0 = 0; r0 < d; r0 += 32) {
+      const int rr = r0 + lane;
+      for (int j = 0; j < K; ++j) T[lane][j] = (rr < d) ? Y[(long long)j * d + rr] : 0.f;
+      __syncwarp();
+      float out[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) out[t] = 0.f;
+      // columns i >= K of T and rows i >= K of M are zero
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float m = mcol[i];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) out[t] = fmaf(T[t][i], m, out[t]);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < 32; ++t) T[t][lane] = out[t];
+      __syncwarp();
+      if (rr < d)
+        for (int j = 0; j < K; ++j) Y[(long long)j * d + rr] = T[lane][j];
+      __syncwarp();
+    }
+  }
+}
+
 }  // namespace
+
+glr_status launch_gram_wnnm(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
+                            float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s) {
+  const int d = im.C * im.P * im.P;
+  if (K < 1 || K > 32 || d < 2 * K) return GLR_ENOTSUP;
+  const long long ngroups = (long long)im.n_img * N;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(ngroups, GW_WARPS), 152LL * 64));
+  GLR_LAUNCH("k_gram_wnnm", s, k_gram_wnnm<<<blocks, GW_WARPS * 32, 0, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, 1e-5f, 30, groups, rank, st));
+  return GLR_OK;
+}
 
 size_t wnnm_smem_bytes(int d, int K) {
   const int Kp = K + (K & 1);

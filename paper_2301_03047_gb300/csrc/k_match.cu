@@ -494,8 +494,12 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   pl.bufcnt_off = L.take((size_t)nstreams * 4);
   pl.taugl_off = L.take((size_t)im.n_img * pl.Npad * 4);
   if (tc) {
-    // BF16 operands: positions [img][npos_pad][dk] and keys [img][Npad][dk], dk = d + 16 (norm columns)
-    const int dk = 64 + 16;  // patch columns padded to 64, plus the norm columns
+    // BF16 operands: positions [img][npos_pad][dk] and keys [img][Npad][dk]: 80 columns
+    // (patch values and norm terms) for d <= 74; for wider patches nkc chunks of 64
+    // patch columns, then 16 norm columns
+    const int dmat = pl.mode == GLR_MATCH_LEARNED ? 16 : d;
+    pl.nkc = dmat > 74 ? (int)ceil_div(dmat, 64) : 1;
+    const int dk = 64 * pl.nkc + 16;
     pl.dk = dk;
     pl.npos_pad = (long long)pl.pos_tiles * pl.pos_tile;
     pl.qpack_off = L.take((size_t)im.n_img * pl.npos_pad * dk * 2);

@@ -62,6 +62,18 @@ constexpr uint32_t OFF_TILE = OFF_HIST + TC_EPI_WARPS * 256 * 4;
 constexpr uint32_t OFF_TAU = OFF_TILE + TC_EPI_WARPS * 32 * TILE_LD * 4;  // published thresholds of the 128 rows
 constexpr uint32_t TC_SMEM = OFF_TAU + TC_M * 4 + 1024;                   // + alignment slack
 static_assert(TC_SMEM <= 232448, "shared memory budget");
+// Wide operands (d > 74): the key tile no longer fits next to a position ring, so
+// every 64-column chunk of keys and positions streams through a 3-stage ring of
+// (A chunk, B chunk) pairs; the 16 norm columns come last as a 16-column chunk.
+constexpr int W_STAGES = 3;
+constexpr uint32_t W_STAGE_BYTES = A_MAIN_BYTES + B_MAIN_BYTES;  // 48 KB
+constexpr uint32_t W_OFF_BAR = W_STAGES * W_STAGE_BYTES;
+constexpr uint32_t W_OFF_MISC = W_OFF_BAR + NBAR * 8;
+constexpr uint32_t W_OFF_HIST = (W_OFF_MISC + 64 + 15) / 16 * 16;
+constexpr uint32_t W_OFF_TILE = W_OFF_HIST + TC_EPI_WARPS * 256 * 4;
+constexpr uint32_t W_OFF_TAU = W_OFF_TILE + TC_EPI_WARPS * 32 * TILE_LD * 4;
+constexpr uint32_t W_SMEM = W_OFF_TAU + TC_M * 4 + 1024;
+static_assert(W_SMEM <= 232448, "shared memory budget (wide)");
 constexpr unsigned long long kWaitNs = 1000000000ull;                   // 1 s
 
 // ---------------------------------------------------------------- PTX helpers
@@ -277,6 +289,91 @@ __global__ void __launch_bounds__(256) k_pack_keys(const float* __restrict__ key
   }
 }
 
+// Wide operands (d > 74): rows of nkc 64-column chunks of patch values, then a
+// separate 16-column row of norm terms ([qn_hi qn_mid qn_lo 1 1 1] for positions,
+// [1 1 1 pn_hi pn_mid pn_lo] for keys).
+__global__ void __launch_bounds__(256) k_pack_positions_w(const float* __restrict__ x, const float* __restrict__ mean,
+                                                          int n_img, int C, int H, int W, int P, long long npos_pad,
+                                                          int nkc, __nv_bfloat16* __restrict__ qmain,
+                                                          __nv_bfloat16* __restrict__ qaux) {
+  const int Hq = H - P + 1, Wq = W - P + 1;
+  const long long npos = (long long)Hq * Wq;
+  const int d = C * P * P, PP = P * P;
+  const long long total = (long long)n_img * npos_pad;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / npos_pad;
+    const long long q = i - f * npos_pad;
+    const bool valid = q < npos;
+    const int r = valid ? (int)(q / Wq) : 0, c = valid ? (int)(q - (q / Wq) * Wq) : 0;
+    const float mu = mean[f];
+    const float* xf = x + (long long)f * C * H * W;
+    float nrm = 0.f;
+    uint4* dst = reinterpret_cast<uint4*>(qmain + i * (long long)nkc * DK_MAIN);
+    for (int kc = 0; kc < nkc; ++kc) {
+      __align__(16) __nv_bfloat16 row[DK_MAIN];
+#pragma unroll
+      for (int j = 0; j < DK_MAIN; ++j) {
+        const int e = kc * DK_MAIN + j;
+        float v = 0.f;
+        if (valid && e < d) {
+          const int ch = e / PP, rem = e - ch * PP, dr = rem / P, dc = rem - dr * P;
+          v = __ldg(xf + ((long long)ch * H + r + dr) * W + c + dc) - mu;
+        }
+        row[j] = __float2bfloat16_rn(v);
+        const float rv = __bfloat162float(row[j]);
+        nrm = fmaf(rv, rv, nrm);
+      }
+      const uint4* src = reinterpret_cast<const uint4*>(row);
+#pragma unroll
+      for (int k = 0; k < DK_MAIN / 8; ++k) dst[kc * (DK_MAIN / 8) + k] = src[k];
+    }
+    __align__(16) __nv_bfloat16 aux[DK_AUX];
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
+#pragma unroll
+    for (int e = 0; e < DK_AUX; ++e) aux[e] = z;
+    if (valid) {
+      split3(nrm, aux[0], aux[1], aux[2]);
+      aux[3] = aux[4] = aux[5] = one;
+    }
+    uint4* dsta = reinterpret_cast<uint4*>(qaux + i * DK_AUX);
+    dsta[0] = reinterpret_cast<const uint4*>(aux)[0];
+    dsta[1] = reinterpret_cast<const uint4*>(aux)[1];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_pack_keys_w(const float* __restrict__ keyv, int n_keys_total, int d, int nkc,
+                                                     __nv_bfloat16* __restrict__ kmain,
+                                                     __nv_bfloat16* __restrict__ kaux) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_keys_total; i += gridDim.x * blockDim.x) {
+    float nrm = 0.f;
+    uint4* dst = reinterpret_cast<uint4*>(kmain + (long long)i * nkc * DK_MAIN);
+    for (int kc = 0; kc < nkc; ++kc) {
+      __align__(16) __nv_bfloat16 row[DK_MAIN];
+#pragma unroll
+      for (int j = 0; j < DK_MAIN; ++j) {
+        const int e = kc * DK_MAIN + j;
+        const __nv_bfloat16 b = __float2bfloat16_rn(e < d ? keyv[(long long)i * d + e] : 0.f);
+        const float rv = __bfloat162float(b);
+        nrm = fmaf(rv, rv, nrm);
+        row[j] = __float2bfloat16_rn(-2.f * rv);  // exact: scaling by -2
+      }
+      const uint4* src = reinterpret_cast<const uint4*>(row);
+#pragma unroll
+      for (int k = 0; k < DK_MAIN / 8; ++k) dst[kc * (DK_MAIN / 8) + k] = src[k];
+    }
+    __align__(16) __nv_bfloat16 aux[DK_AUX];
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
+#pragma unroll
+    for (int e = 0; e < DK_AUX; ++e) aux[e] = z;
+    aux[0] = aux[1] = aux[2] = one;
+    split3(nrm, aux[3], aux[4], aux[5]);
+    uint4* dsta = reinterpret_cast<uint4*>(kaux + (long long)i * DK_AUX);
+    dsta[0] = reinterpret_cast<const uint4*>(aux)[0];
+    dsta[1] = reinterpret_cast<const uint4*>(aux)[1];
+  }
+}
+
 // Seed bounds: for each key, the K'-th smallest tensor-core score over 16 x 16
 // positions sampled at stride 2 around it.  That sample is a subset of the
 // positions, so at least K' positions score below this value: it is a valid
@@ -409,27 +506,31 @@ __global__ void __launch_bounds__(256) k_seed_bounds(const __nv_bfloat16* __rest
   }
 }
 
-template <int EB>
+template <int EB, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_match_tc(const __grid_constant__ CUtensorMap tm_qmain, const __grid_constant__ CUtensorMap tm_qaux,
                const __grid_constant__ CUtensorMap tm_kmain, const __grid_constant__ CUtensorMap tm_kaux,
                const int32_t* __restrict__ n_found, int Npad, long long npos, long long npos_pad, int splits,
-               int tiles_per_split, int ntiles, StreamCfg cfg, uint2* __restrict__ bufs, int* __restrict__ buf_cnt,
-               uint32_t* __restrict__ tau_gl, StatusBlock* st, float* __restrict__ dump) {
+               int tiles_per_split, int ntiles, int nkc, StreamCfg cfg, uint2* __restrict__ bufs,
+               int* __restrict__ buf_cnt, uint32_t* __restrict__ tau_gl, StatusBlock* st, float* __restrict__ dump) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
+  constexpr uint32_t kBar = WIDE ? W_OFF_BAR : OFF_BAR, kMisc = WIDE ? W_OFF_MISC : OFF_MISC;
+  constexpr uint32_t kHist = WIDE ? W_OFF_HIST : OFF_HIST, kTile = WIDE ? W_OFF_TILE : OFF_TILE;
+  constexpr uint32_t kTau = WIDE ? W_OFF_TAU : OFF_TAU;
+  constexpr int NST = WIDE ? W_STAGES : TC_STAGES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBar);
   uint64_t* full = bars;
   uint64_t* empty = bars + TC_STAGES;
   uint64_t* tfull = bars + 2 * TC_STAGES;
   uint64_t* tempty = tfull + 2;
   uint64_t* a_full = tempty + 2;
   uint64_t* mma_done = a_full + 1;
-  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(smem + OFF_MISC);
-  volatile int* abort_s = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
-  unsigned* hist = reinterpret_cast<unsigned*>(smem + OFF_HIST);
-  float* tiles = reinterpret_cast<float*>(smem + OFF_TILE);
-  uint32_t* tau_sh = reinterpret_cast<uint32_t*>(smem + OFF_TAU);
+  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(smem + kMisc);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(smem + kMisc + 4);
+  unsigned* hist = reinterpret_cast<unsigned*>(smem + kHist);
+  float* tiles = reinterpret_cast<float*>(smem + kTile);
+  uint32_t* tau_sh = reinterpret_cast<uint32_t*>(smem + kTau);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kt = blockIdx.x, f = blockIdx.y, split = blockIdx.z;
@@ -461,7 +562,78 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_base_s;
 
-  if (warp == 0) {
+  if (WIDE && warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------ producer (wide operands)
+      const int arow = f * Npad + kt * TC_M;
+      int it = 0;
+      bool ok = true;
+      for (int i = 0; ok && i < nt; ++i) {
+        const int brow = (int)(f * npos_pad + (long long)(t_begin + i) * TC_N);
+        for (int kc = 0; kc <= nkc; ++kc) {
+          const int s = it % NST;
+          const uint32_t ph = (uint32_t)(it / NST) & 1u;
+          if (!mbar_wait(empty + s, ph ^ 1u, abort_s, st)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + s * W_STAGE_BYTES;
+          uint8_t* sb = sa + A_MAIN_BYTES;
+          if (kc < nkc) {
+            mbar_arrive_expect_tx(full + s, A_MAIN_BYTES + B_MAIN_BYTES);
+            tma_load_2d(&tm_kmain, full + s, sa, DK_MAIN * kc, arow);
+            tma_load_2d(&tm_qmain, full + s, sb, DK_MAIN * kc, brow);
+          } else {
+            mbar_arrive_expect_tx(full + s, A_AUX_BYTES + B_AUX_BYTES);
+            tma_load_2d(&tm_kaux, full + s, sa, 0, arow);
+            tma_load_2d(&tm_qaux, full + s, sb, 0, brow);
+          }
+          ++it;
+        }
+      }
+      // teardown: every issued copy has landed before the CTA may exit
+      for (int j = max(0, it - NST); j < it; ++j)
+        mbar_wait(full + (j % NST), (uint32_t)(j / NST) & 1u, abort_s, st, false);
+    }
+  } else if (WIDE && warp == 1) {
+    if (lane == 0) {
+      // ---------------------------------------------- MMA issuer (wide operands)
+      constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+      int it = 0;
+      bool ok = true;
+      for (int i = 0; ok && i < nt; ++i) {
+        const int b = i & 1;
+        const uint32_t bph = (uint32_t)(i >> 1) & 1u;
+        if (!mbar_wait(tempty + b, bph ^ 1u, abort_s, st)) break;
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * TC_N);
+        for (int kc = 0; kc <= nkc; ++kc) {
+          const int s = it % NST;
+          const uint32_t ph = (uint32_t)(it / NST) & 1u;
+          if (!mbar_wait(full + s, ph, abort_s, st)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * W_STAGE_BYTES);
+          const uint32_t sb = sa + A_MAIN_BYTES;
+          if (kc < nkc) {
+#pragma unroll
+            for (int k = 0; k < DK_MAIN / 16; ++k)
+              mma_bf16(d_tmem, smem_desc(sa + 32 * k, 1024, LAYOUT_SW128), smem_desc(sb + 32 * k, 1024, LAYOUT_SW128),
+                       idesc, (kc > 0 || k > 0) ? 1u : 0u);
+          } else {
+            mma_bf16(d_tmem, smem_desc(sa, 256, LAYOUT_SW32), smem_desc(sb, 256, LAYOUT_SW32), idesc, 1u);
+          }
+          mma_commit(empty + s);
+          ++it;
+        }
+        if (ok) mma_commit(tfull + b);
+      }
+      // teardown: all issued MMAs have completed
+      mma_commit(mma_done);
+      mbar_wait(mma_done, 0, abort_s, st, false);
+    }
+  } else if (warp == 0) {
     if (lane == 0) {
       // ---------------------------------------------------------- producer
       mbar_arrive_expect_tx(a_full, A_MAIN_BYTES + A_AUX_BYTES);
@@ -610,12 +782,13 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, void* base, uint64_t rows, uint32_t cols, uint32_t box_rows, CUtensorMapSwizzle sw) {
+bool make_map(CUtensorMap* m, void* base, uint64_t rows, uint32_t cols, uint32_t box_rows, CUtensorMapSwizzle sw,
+              uint32_t box_cols = 0) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {cols, rows};
   const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  const cuuint32_t box[2] = {cols, box_rows};
+  const cuuint32_t box[2] = {box_cols ? box_cols : cols, box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -629,7 +802,9 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
                                 char* ws, float* dump, const int32_t* seed_keys, int seed_N, const float* emb_pos,
                                 const float* emb_keys, cudaStream_t s) {
   const int d = emb_keys ? 16 : im.C * im.P * im.P;
-  if (norm_col(d) + 6 > DK_MAIN + DK_AUX) return GLR_ENOTSUP;
+  const bool wide = pl.nkc > 1;
+  if (!wide && norm_col(d) + 6 > DK_MAIN + DK_AUX) return GLR_ENOTSUP;
+  if (wide && (emb_keys != nullptr || dump != nullptr || pl.nkc * DK_MAIN < d)) return GLR_ENOTSUP;
   const float* mean = reinterpret_cast<const float*>(ws + pl.mean_off);
   const float* keyv = emb_keys ? emb_keys : reinterpret_cast<const float*>(ws + pl.keyv_off);
   uint2* bufs = reinterpret_cast<uint2*>(ws + pl.buf_off);
@@ -637,9 +812,46 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   uint32_t* taugl = reinterpret_cast<uint32_t*>(ws + pl.taugl_off);
   StatusBlock* st = reinterpret_cast<StatusBlock*>(ws);
   __nv_bfloat16* qmain = reinterpret_cast<__nv_bfloat16*>(ws + pl.qpack_off);
-  __nv_bfloat16* qaux = qmain + (size_t)im.n_img * pl.npos_pad * DK_MAIN;
+  __nv_bfloat16* qaux = qmain + (size_t)im.n_img * pl.npos_pad * DK_MAIN * pl.nkc;
   __nv_bfloat16* kmain = reinterpret_cast<__nv_bfloat16*>(ws + pl.kpack_off);
-  __nv_bfloat16* kaux = kmain + (size_t)im.n_img * pl.Npad * DK_MAIN;
+  __nv_bfloat16* kaux = kmain + (size_t)im.n_img * pl.Npad * DK_MAIN * pl.nkc;
+  if (wide) {
+    {
+      const long long total = (long long)im.n_img * pl.npos_pad;
+      const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+      GLR_LAUNCH("k_pack_positions", s,
+                 k_pack_positions_w<<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, pl.npos_pad,
+                                                           pl.nkc, qmain, qaux));
+    }
+    {
+      const int nk = im.n_img * pl.Npad;
+      const int blocks = (int)std::max<long long>(1, ceil_div(nk, 256));
+      GLR_LAUNCH("k_pack_keys", s, k_pack_keys_w<<<blocks, 256, 0, s>>>(keyv, nk, d, pl.nkc, kmain, kaux));
+    }
+    CUtensorMap tq, tqa, tk, tka;
+    const uint64_t qrows = (uint64_t)im.n_img * pl.npos_pad, krows = (uint64_t)im.n_img * pl.Npad;
+    const uint32_t wcols = (uint32_t)(pl.nkc * DK_MAIN);
+    if (!make_map(&tq, qmain, qrows, wcols, TC_N, CU_TENSOR_MAP_SWIZZLE_128B, DK_MAIN) ||
+        !make_map(&tqa, qaux, qrows, DK_AUX, TC_N, CU_TENSOR_MAP_SWIZZLE_32B) ||
+        !make_map(&tk, kmain, krows, wcols, TC_M, CU_TENSOR_MAP_SWIZZLE_128B, DK_MAIN) ||
+        !make_map(&tka, kaux, krows, DK_AUX, TC_M, CU_TENSOR_MAP_SWIZZLE_32B))
+      return GLR_ECUDA;
+    auto kern = pl.epi_batch == 2 ? k_match_tc<2, true> : k_match_tc<4, true>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W_SMEM) != cudaSuccess)
+      return GLR_ECUDA;
+    int blocks_per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, TC_THREADS, W_SMEM) != cudaSuccess ||
+        blocks_per_sm != 1)  // all of TMEM: exactly one resident CTA per SM
+      return GLR_ENOTSUP;
+    const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
+    const StreamCfg cfg{pl.cap, pl.Kp};
+    dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
+    GLR_LAUNCH("k_match_tc", s,
+               kern<<<grid, TC_THREADS, W_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad, pl.splits,
+                                                     pl.tiles_per_split, pl.pos_tiles, pl.nkc, cfg, bufs, bufcnt,
+                                                     taugl, st, nullptr));
+    return GLR_OK;
+  }
   {
     const long long total = (long long)im.n_img * pl.npos_pad;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
@@ -667,7 +879,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
       !make_map(&tk, kmain, krows, DK_MAIN, TC_M, CU_TENSOR_MAP_SWIZZLE_128B) ||
       !make_map(&tka, kaux, krows, DK_AUX, TC_M, CU_TENSOR_MAP_SWIZZLE_32B))
     return GLR_ECUDA;
-  auto kern = pl.epi_batch == 2 ? k_match_tc<2> : k_match_tc<4>;
+  auto kern = pl.epi_batch == 2 ? k_match_tc<2, false> : k_match_tc<4, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) != cudaSuccess)
     return GLR_ECUDA;
   {
@@ -681,7 +893,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
   GLR_LAUNCH("k_match_tc", s,
              kern<<<grid, TC_THREADS, TC_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
-                                                          pl.splits, pl.tiles_per_split, pl.pos_tiles, cfg, bufs,
+                                                          pl.splits, pl.tiles_per_split, pl.pos_tiles, 1, cfg, bufs,
                                                           bufcnt, taugl, st, dump));
   return GLR_OK;
 }
@@ -690,7 +902,9 @@ glr_status launch_match_tc(const float* x, const glr_images& im, const int32_t* 
                            const MatchPlan& pl, char* ws, cudaStream_t s) {
   const float* ep = pl.mode == GLR_MATCH_LEARNED ? reinterpret_cast<const float*>(ws + pl.embp_off) : nullptr;
   const float* ek = pl.mode == GLR_MATCH_LEARNED ? reinterpret_cast<const float*>(ws + pl.embk_off) : nullptr;
-  return launch_match_tc_impl(x, im, n_found, pl, ws, g_tc_dump, g_tc_dump ? nullptr : keys, N, ep, ek, s);
+  // seed bounds read the narrow operand layout only
+  const int32_t* seed = (g_tc_dump || pl.nkc > 1) ? nullptr : keys;
+  return launch_match_tc_impl(x, im, n_found, pl, ws, g_tc_dump, seed, N, ep, ek, s);
 }
 
 float* g_tc_dump = nullptr;

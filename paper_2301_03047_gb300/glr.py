@@ -417,6 +417,87 @@ class MriReconstructor:
         return self.x
 
 
+def mosaic_init(y, masks, s, *, out=None, stream=None):
+    """Bilinear start of MSFA demosaicing.  y: [G][H][W]; masks: [T][H][W] (shared) or [G][T][H][W]."""
+    lib = L.load()
+    G, H, W = y.shape
+    T = masks.shape[-3]
+    mstride = 0 if masks.dim() == 3 else T * H * W
+    if out is None:
+        out = torch.empty((G, T, H, W), dtype=torch.float32, device=y.device)
+    _check("glr_mosaic_init", lib.glr_mosaic_init(_ptr(y), _ptr(masks), int(mstride), G, T, H, W, int(s), _ptr(out),
+                                                  _stream(stream)))
+    return out
+
+
+class MsfaBatchReconstructor:
+    """GAP + GLR demosaicing of a batch of MSFA snapshots of uneven sizes (Section 3, MSFA).
+
+    Images are grouped by size into classes; each class is a uniform batch with
+    its own buffers, workspaces and CUDA stream, so one iteration launches every
+    kernel once per class and the classes run concurrently.  capture() records
+    the whole iteration (all classes, fork / join across the class streams) in
+    one CUDA graph per noise level.
+    """
+
+    def __init__(self, sides, Ns, bands, P, K, mode="bf16", edge_th=0.1, device="cuda", tuned=None,
+                 concurrent=True):
+        self.bands, self.P, self.K, self.concurrent = bands, P, K, concurrent
+        self.s = int(round(math.sqrt(bands)))
+        self.classes = []  # (side, image indices, N, denoiser, stream, x, v, y, masks)
+        order = {}
+        for i, (sd, n) in enumerate(zip(sides, Ns)):
+            order.setdefault((int(sd), int(n)), []).append(i)
+        for (sd, n), ids in sorted(order.items()):
+            kw = (tuned or {}).get((sd, n), (0, 0, 0, 0))
+            den = GlrDenoiser(GlrShape(len(ids), bands, sd, sd, P, n, K), mode, edge_th, kw[0], kw[1], device, kw[2],
+                              kw[3])
+            x = torch.empty((len(ids), bands, sd, sd), dtype=torch.float32, device=device)
+            self.classes.append({"side": sd, "ids": ids, "N": n, "den": den, "stream": torch.cuda.Stream(device=device),
+                                 "x": x, "v": torch.empty_like(x)})
+
+    def start(self, ys, masks_by_side):
+        """ys: list of [H][W] device tensors (batch order); masks_by_side: {side: [bands][side][side]}."""
+        for c in self.classes:
+            c["y"] = torch.stack([ys[i] for i in c["ids"]]).contiguous()
+            c["masks"] = masks_by_side[c["side"]]
+            mosaic_init(c["y"], c["masks"], self.s, out=c["x"])
+        return self
+
+    def step(self, sigma_w: float, c_wnnm: float) -> None:
+        main = torch.cuda.current_stream()
+        if not self.concurrent:  # one class after the other on the current stream (for per-kernel timing)
+            for c in self.classes:
+                c["den"](c["x"], sigma_w, c_wnnm, out=c["v"], stream=main)
+                gap_step(c["y"], c["masks"], c["v"], out=c["x"], stream=main)
+            return
+        for c in self.classes:
+            c["stream"].wait_stream(main)
+        for c in self.classes:
+            with torch.cuda.stream(c["stream"]):
+                st = c["stream"]
+                c["den"](c["x"], sigma_w, c_wnnm, out=c["v"], stream=st)
+                gap_step(c["y"], c["masks"], c["v"], out=c["x"], stream=st)
+        for c in self.classes:
+            main.wait_stream(c["stream"])
+
+    def _state(self):
+        return [c["x"] for c in self.classes]
+
+    capture = SciReconstructor.capture
+
+    def step_graph(self, sigma_w: float) -> None:
+        self._graphs[float(sigma_w)].replay()
+
+    def images(self):
+        """The current estimates in batch order ([bands][side][side] views)."""
+        out = [None] * sum(len(c["ids"]) for c in self.classes)
+        for c in self.classes:
+            for j, i in enumerate(c["ids"]):
+                out[i] = c["x"][j]
+        return out
+
+
 # ---------------------------------------------------------------------------
 # Autotuner for the matching schedule (position splits, compaction trigger,
 # candidates kept per stream).  Tile shapes are fixed at compile time; these
