@@ -292,53 +292,76 @@ __global__ void __launch_bounds__(256) k_pack_keys(const float* __restrict__ key
 // Wide operands (d > 74): rows of nkc 64-column chunks of patch values, then a
 // separate 16-column row of norm terms ([qn_hi qn_mid qn_lo 1 1 1] for positions,
 // [1 1 1 pn_hi pn_mid pn_lo] for keys).
+// 32 consecutive positions per CTA: each warp packs whole channels (lane = position,
+// coalesced image reads) into rows staged in shared memory; the channel partial
+// norms are added in channel order (deterministic) and the rows leave as one
+// contiguous block of 16-byte stores.
+constexpr int PW_POS = 32;
 __global__ void __launch_bounds__(256) k_pack_positions_w(const float* __restrict__ x, const float* __restrict__ mean,
                                                           int n_img, int C, int H, int W, int P, long long npos_pad,
                                                           int nkc, __nv_bfloat16* __restrict__ qmain,
                                                           __nv_bfloat16* __restrict__ qaux) {
+  extern __shared__ __align__(16) uint8_t pw_smem[];
+  const int rowlen = nkc * DK_MAIN;  // bf16 per row
+  const int ld = rowlen + 2;         // shared-memory row stride: an odd number of words (no bank conflicts)
+  __nv_bfloat16* rows = reinterpret_cast<__nv_bfloat16*>(pw_smem);        // [PW_POS][ld]
+  float* pnorm = reinterpret_cast<float*>(pw_smem + (size_t)PW_POS * ld * 2);  // [C][PW_POS]
   const int Hq = H - P + 1, Wq = W - P + 1;
   const long long npos = (long long)Hq * Wq;
-  const int d = C * P * P, PP = P * P;
-  const long long total = (long long)n_img * npos_pad;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long f = i / npos_pad;
-    const long long q = i - f * npos_pad;
+  const int PP = P * P, d = C * PP;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long blocks_per_img = npos_pad / PW_POS;
+  for (long long blk = blockIdx.x; blk < (long long)n_img * blocks_per_img; blk += gridDim.x) {
+    const long long f = blk / blocks_per_img;
+    const long long q0 = (blk - f * blocks_per_img) * PW_POS;
+    const float mu = mean[f];
+    // padding columns (e >= d) of every row
+    for (int i = threadIdx.x; i < PW_POS * (rowlen - d); i += blockDim.x) {
+      const int j = i / (rowlen - d), e = d + i - (i / (rowlen - d)) * (rowlen - d);
+      rows[j * ld + e] = __float2bfloat16_rn(0.f);
+    }
+    const long long q = q0 + lane;
     const bool valid = q < npos;
     const int r = valid ? (int)(q / Wq) : 0, c = valid ? (int)(q - (q / Wq) * Wq) : 0;
-    const float mu = mean[f];
-    const float* xf = x + (long long)f * C * H * W;
-    float nrm = 0.f;
-    uint4* dst = reinterpret_cast<uint4*>(qmain + i * (long long)nkc * DK_MAIN);
-    for (int kc = 0; kc < nkc; ++kc) {
-      __align__(16) __nv_bfloat16 row[DK_MAIN];
-#pragma unroll
-      for (int j = 0; j < DK_MAIN; ++j) {
-        const int e = kc * DK_MAIN + j;
-        float v = 0.f;
-        if (valid && e < d) {
-          const int ch = e / PP, rem = e - ch * PP, dr = rem / P, dc = rem - dr * P;
-          v = __ldg(xf + ((long long)ch * H + r + dr) * W + c + dc) - mu;
+    for (int ch = wid; ch < C; ch += nw) {
+      const float* xc = x + ((long long)f * C + ch) * H * W;
+      float nrm = 0.f;
+      for (int dr = 0; dr < P; ++dr)
+        for (int dc = 0; dc < P; ++dc) {
+          const float v = valid ? __ldg(xc + (long long)(r + dr) * W + c + dc) - mu : 0.f;
+          const __nv_bfloat16 b = __float2bfloat16_rn(v);
+          const float rv = __bfloat162float(b);
+          nrm = fmaf(rv, rv, nrm);
+          rows[lane * ld + ch * PP + dr * P + dc] = b;
         }
-        row[j] = __float2bfloat16_rn(v);
-        const float rv = __bfloat162float(row[j]);
-        nrm = fmaf(rv, rv, nrm);
+      pnorm[ch * PW_POS + lane] = nrm;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      float nrm = 0.f;
+      for (int ch = 0; ch < C; ++ch) nrm += pnorm[ch * PW_POS + lane];
+      __align__(16) __nv_bfloat16 aux[DK_AUX];
+      const __nv_bfloat16 z = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
+#pragma unroll
+      for (int e = 0; e < DK_AUX; ++e) aux[e] = z;
+      if (valid) {
+        split3(nrm, aux[0], aux[1], aux[2]);
+        aux[3] = aux[4] = aux[5] = one;
       }
-      const uint4* src = reinterpret_cast<const uint4*>(row);
-#pragma unroll
-      for (int k = 0; k < DK_MAIN / 8; ++k) dst[kc * (DK_MAIN / 8) + k] = src[k];
+      uint4* dsta = reinterpret_cast<uint4*>(qaux + (f * npos_pad + q) * DK_AUX);
+      dsta[0] = reinterpret_cast<const uint4*>(aux)[0];
+      dsta[1] = reinterpret_cast<const uint4*>(aux)[1];
     }
-    __align__(16) __nv_bfloat16 aux[DK_AUX];
-    const __nv_bfloat16 z = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
-#pragma unroll
-    for (int e = 0; e < DK_AUX; ++e) aux[e] = z;
-    if (valid) {
-      split3(nrm, aux[0], aux[1], aux[2]);
-      aux[3] = aux[4] = aux[5] = one;
+    // the 32 rows are contiguous in the packed array (4-byte words: the staged rows are
+    // padded by one word)
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(rows);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(qmain + (f * npos_pad + q0) * (long long)rowlen);
+    const int wpr = rowlen / 2;
+    for (int i = threadIdx.x; i < PW_POS * wpr; i += blockDim.x) {
+      const int j = i / wpr;
+      dst[i] = src[j * (wpr + 1) + (i - j * wpr)];
     }
-    uint4* dsta = reinterpret_cast<uint4*>(qaux + i * DK_AUX);
-    dsta[0] = reinterpret_cast<const uint4*>(aux)[0];
-    dsta[1] = reinterpret_cast<const uint4*>(aux)[1];
+    __syncthreads();
   }
 }
 
@@ -817,11 +840,16 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   __nv_bfloat16* kaux = kmain + (size_t)im.n_img * pl.Npad * DK_MAIN * pl.nkc;
   if (wide) {
     {
-      const long long total = (long long)im.n_img * pl.npos_pad;
-      const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+      const size_t psmem = (size_t)PW_POS * (pl.nkc * DK_MAIN + 2) * 2 + (size_t)im.C * PW_POS * 4;
+      if (psmem > 227 * 1024) return GLR_ENOTSUP;
+      if (cudaFuncSetAttribute(k_pack_positions_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem) !=
+          cudaSuccess)
+        return GLR_ECUDA;
+      const long long nblk = (long long)im.n_img * (pl.npos_pad / PW_POS);
+      const int pblocks = (int)std::max<long long>(1, std::min<long long>(nblk, 152LL * 16));
       GLR_LAUNCH("k_pack_positions", s,
-                 k_pack_positions_w<<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, pl.npos_pad,
-                                                           pl.nkc, qmain, qaux));
+                 k_pack_positions_w<<<pblocks, 256, psmem, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P,
+                                                                 pl.npos_pad, pl.nkc, qmain, qaux));
     }
     {
       const int nk = im.n_img * pl.Npad;
