@@ -12,6 +12,8 @@ notation, written for clarity, not speed:
   Sobel horizontal / vertical gradients and the four signed binary edge maps.
 * ``corner_response`` / ``nms3`` / ``select_keys`` -- Section 2: exemplar (key)
   patches are centred on corner points of the averaged edge map.
+* ``edge_match_topk``              -- the paper's global-matching heat map (Eq. 8):
+  correlation of binary edge patches over the four maps of Eq. 6.
 * ``match_topk``                   -- Eq. 1 made global (Section 2): the K
   positions with the smallest squared L2 distance to each key over the whole
   image; the grouping operator R~_i of Eq. 5.
@@ -52,6 +54,10 @@ A9  WNNM single pass: sigma_hat_i = sqrt(max(s_i^2 - K sw^2, 0)),
 A10 Aggregation weight 1; pixels no patch covers keep the input value.
 A12 Plain GAP (accelerated is a flag); R = sum_t A_t^2 with R = 0 -> 1;
     x0 = Phi^T (y / R).
+A18 The paper's own matching score (the heat map of Eq. 8, ``edge_match_topk``):
+    Conv2d is a correlation summed over the four maps and the C channels (the
+    per-channel maps, not the OR-ed ones of key selection); a larger value is a
+    better match; the K largest are kept, ties by smaller position id.
 
 Layouts: images x[F][C][H][W]; a patch vector is ordered channel, then row,
 then column (index ch*P*P + dr*P + dc); a position id is q = r*Wq + c of the
@@ -249,6 +255,43 @@ def match_topk(x: np.ndarray, P: int, keys: np.ndarray, K: int, Q: np.ndarray | 
         idx[i] = order
         dist[i] = d[order]
     return idx, dist
+
+
+def edge_planes(x: np.ndarray, th: float) -> np.ndarray:
+    """The four binary edge maps of Eq. 6 (reading A1) for every channel of x[C][H][W]:
+    planes[m * C + c] for m in (h+, h-, v+, v-), values 0/1 (float64)."""
+    C = x.shape[0]
+    out = np.zeros((4 * C,) + x.shape[1:])
+    for c in range(C):
+        e = edge_maps(x[c], th)
+        for m, name in enumerate(("h+", "h-", "v+", "v-")):
+            out[m * C + c] = e[name]
+    return out
+
+
+def edge_heatmap(x: np.ndarray, P: int, key: int, th: float, E: np.ndarray | None = None) -> np.ndarray:
+    """Eq. 8: H(q) = sum over the four maps and the C channels of the Conv2d (a
+    correlation) of the key's edge patch with the edge maps, at every valid
+    position q (an integer: the number of edge pixels the two patches share)."""
+    if E is None:
+        E = edge_planes(x, th)
+    Qe = patch_matrix(E, P)  # rows: every position's 4 C P^2 edge values
+    return Qe @ Qe[key]
+
+
+def edge_match_topk(x: np.ndarray, P: int, keys: np.ndarray, K: int, th: float):
+    """Global matching by the heat map of Eq. 8: for each key the K positions of
+    largest H, ties by smaller position id (reading A18); returns (idx, H values)."""
+    E = edge_planes(x, th)
+    Qe = patch_matrix(E, P)
+    idx = np.empty((len(keys), K), dtype=np.int32)
+    val = np.empty((len(keys), K))
+    for i, k in enumerate(keys):
+        h = Qe @ Qe[int(k)]
+        order = np.lexsort((np.arange(len(h)), -h))[:K]
+        idx[i] = order
+        val[i] = h[order]
+    return idx, val
 
 
 def all_distances(x: np.ndarray, P: int, key: int, Q: np.ndarray | None = None) -> np.ndarray:

@@ -390,3 +390,46 @@ def test_sigma_schedule_reading():
         x = O.glr_reconstruct(prob.y, prob.masks, cfg.P, cfg.N, cfg.K, sched, cfg.c_wnnm, cfg.edge_th)
         res[name] = O.psnr_framewise(x, prob.truth)
     assert res["used"] > res["survey"] + 8.0, res
+
+
+# ---------------------------------------------------------------------------
+# The paper's heat-map score (Eq. 8), reading A18
+# ---------------------------------------------------------------------------
+def test_edge_heatmap_counts_shared_edge_pixels():
+    """H(q) is the number of (map, channel, pixel) edge entries the two patches share:
+    brute force over the maps on a tiny two-channel image."""
+    rng = synth.rng_for("hm")
+    x = synth.quantize8(rng.random((2, 9, 11)))
+    P, th = 3, 0.3
+    E = O.edge_planes(x, th)
+    assert set(np.unique(E)) <= {0.0, 1.0}
+    Hq, Wq = 7, 9
+    key = 2 * Wq + 5
+    h = O.edge_heatmap(x, P, key, th)
+    kr, kc = divmod(key, Wq)
+    for q in range(Hq * Wq):
+        r, c = divmod(q, Wq)
+        want = 0
+        for m in range(8):
+            want += int(np.sum(E[m, r:r + P, c:c + P] * E[m, kr:kr + P, kc:kc + P]))
+        assert h[q] == want
+
+
+def test_edge_heatmap_self_is_maximal_and_copies_tie():
+    """H(q) <= H(key) for every q (shared entries cannot exceed the key's own count),
+    and a planted copy of the key region ties with the key (then smaller id first)."""
+    rng = synth.rng_for("hm2")
+    x = synth.quantize8(rng.random((1, 20, 24)))
+    x[0, 12:20, 14:22] = x[0, 2:10, 3:11]  # copy including a 1-pixel margin for the Sobel support
+    P, th = 6, 0.25
+    key = 3 * 19 + 4  # top-left (3, 4); its copy sits at (13, 15)
+    h = O.edge_heatmap(x, P, key, th)
+    assert h.max() == h[key]
+    assert h[13 * 19 + 15] == h[key]
+    idx, val = O.edge_match_topk(x, P, np.array([key]), 3, th)
+    assert val[0, 0] == h[key] and idx[0, 0] == min(key, 13 * 19 + 15)
+
+
+def test_edge_heatmap_flat_image_is_zero():
+    x = np.full((1, 12, 12), 0.4)
+    assert np.all(O.edge_heatmap(x, 4, 10, 0.1) == 0)
