@@ -472,7 +472,7 @@ def run_glr(args) -> None:
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16" if forms[0] == "bf16" else "f32",
+        "dtype": "f32" if forms[0] == "fp32" else "bf16",
         "data": "synthetic (seeded moving-shapes scenes, Bernoulli masks; stand-in for the paper's CACTI videos)",
         "config": {"workload": cfg.name, "frames": cfg.T, "H": cfg.H, "W": cfg.W, "P": cfg.P, "N": cfg.N, "K": cfg.K,
                    "positions_per_frame": npos, "match_form": forms[0], "parallelism": f"replicas x{ws}",
@@ -688,7 +688,7 @@ def run_mri(args, cfg, dev, dist) -> None:
         "metric": MRI_METRIC, "value": round(ws * args.steps / head["total_s"], 4), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms_per_step"], 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if forms[0] == "bf16" else "f32",
+        "dtype": "f32" if forms[0] == "fp32" else "bf16",
         "data": "synthetic (seeded complex ellipse phantom, Cartesian variable-density k-space rows)",
         "config": {"workload": cfg.name, "H": cfg.H, "W": cfg.W, "P": cfg.P, "d": 2 * cfg.P * cfg.P, "N": cfg.N,
                    "K": cfg.K, "rho": cfg.rho, "positions": npos, "match_form": forms[0],
@@ -886,7 +886,7 @@ def run_msfa(args, cfg, dev, dist) -> None:
         "metric": MSFA_METRIC, "value": round(ws * head["steps"] / head["total_s"], 4), "unit": UNIT, "n_gpus": ws,
         "steps": head["steps"], "warmup": args.warmup, "ms_per_step": round(head["ms_per_step"], 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if forms[0] == "bf16" else "f32",
+        "dtype": "f32" if forms[0] == "fp32" else "bf16",
         "data": "synthetic (seeded spectral cubes: 6 materials x 4-Gaussian spectra, textured abundances; 4x4 mosaic)",
         "config": {"workload": cfg.name, "images": len(sides), "sides": sorted(set(sides)), "bands": cfg.bands,
                    "P": cfg.P, "d": cfg.bands * cfg.P * cfg.P, "K": cfg.K, "keys_total": int(sum(Ns)),
@@ -963,7 +963,8 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="glr", choices=["glr", "reference"])
-    ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32", "edge"],
+                    help="matching form: bf16 (chosen), fp32 (plain), edge (the paper's heat map of Eq. 8)")
     ap.add_argument("--oracle-keys", type=int, default=96)
     ap.add_argument("--workload", default="sci16",
                     choices=["sci16", "sci4", "sci8", "mri1024", "mri256", "msfa32", "msfa4", "msfa2"],

@@ -75,8 +75,11 @@ typedef struct glr_images {
 enum {
   GLR_MATCH_FP32 = 0,   /* plain form: FP32 FMA on the CUDA cores */
   GLR_MATCH_BF16 = 1,   /* chosen form: BF16 tcgen05.mma into TMEM, FP32 accumulate, FP32 re-rank */
-  GLR_MATCH_LEARNED = 2 /* learned proposal: k_over candidates by the 16-dim encoder embedding
+  GLR_MATCH_LEARNED = 2, /* learned proposal: k_over candidates by the 16-dim encoder embedding
                            (BF16 tcgen05 contraction), then the exact FP32 re-rank on patches */
+  GLR_MATCH_EDGE = 3     /* the paper's heat map (Eq. 8): binary edge patches (Eq. 6, threshold
+                           edge_th) correlated over the four maps and all channels on the tensor
+                           cores (0/1 operands: exact); the K largest values, ties by smaller id */
 };
 
 /* Number of floats of an encoder parameter buffer: W1[64][64], b1[64], W2[16][64], b2[16]. */
@@ -93,7 +96,7 @@ typedef struct glr_match_opts {
                            floats); k_over = candidates per key (0 = 256) */
   int32_t epi_batch;    /* tensor-core epilogue: 32-column chunks read from tensor memory per
                            visit, 2 or 4 (0 = 4) */
-  int32_t reserved;
+  float edge_th;        /* GLR_MATCH_EDGE: the threshold th of Eq. 7 on Sobel output (>= 0) */
 } glr_match_opts;
 
 /* Operation codes for glr_workspace_size. */
@@ -139,7 +142,10 @@ glr_status glr_select_keys(const float* x, const glr_images* im, float edge_th, 
  *   n_found  int32 [n_img] valid keys per image (<= N); rows beyond are not written.
  *   K        matches per key, 1 <= K <= 128, K <= Hq*Wq.
  *   modes    GLR_MATCH_FP32: d = C*P*P <= 256 and P <= 8; GLR_MATCH_BF16: d <= 74;
- *            GLR_MATCH_LEARNED: d <= 64 (GLR_ENOTSUP / GLR_EINVAL otherwise).
+ *            GLR_MATCH_LEARNED: d <= 64; GLR_MATCH_EDGE: 4 C P^2 <= 640
+ *            (GLR_ENOTSUP / GLR_EINVAL otherwise).
+ *            With GLR_MATCH_EDGE, idx is ordered by descending heat-map value H
+ *            (ties by smaller id) and dist receives H (an integer count).
  *   idx      out, int32 [n_img][N][K]: the K positions with the smallest
  *            squared L2 distance, ordered by (distance, position id); the key
  *            itself is included (distance 0).

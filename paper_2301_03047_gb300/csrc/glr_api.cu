@@ -183,8 +183,13 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
   const long long npos = npos_of(im);
   if (N < 1 || K < 1 || K > npos) return GLR_EINVAL;
   if (K > 128) return GLR_ENOTSUP;
-  if (opts && opts->mode != GLR_MATCH_FP32 && opts->mode != GLR_MATCH_BF16 && opts->mode != GLR_MATCH_LEARNED)
+  if (opts && opts->mode != GLR_MATCH_FP32 && opts->mode != GLR_MATCH_BF16 && opts->mode != GLR_MATCH_LEARNED &&
+      opts->mode != GLR_MATCH_EDGE)
     return GLR_EINVAL;
+  if (opts && opts->mode == GLR_MATCH_EDGE) {
+    if (!(opts->edge_th >= 0.f)) return GLR_EINVAL;
+    if (4 * im->C * im->P * im->P > 640) return GLR_ENOTSUP;
+  }
   if (opts && opts->mode == GLR_MATCH_LEARNED && (!opts->encoder || im->C * im->P * im->P > 64)) return GLR_EINVAL;
   if (opts && (opts->k_over < 0 || opts->splits < 0 || opts->cap < 0 || (opts->k_over > 0 && opts->k_over < K)))
     return GLR_EINVAL;

@@ -35,6 +35,8 @@ struct MatchPlan {
   int tiles_per_split;
   int dk;               // BF16 operand row length (elements)
   int nkc;              // 64-column chunks of patch values in a BF16 operand row (1 unless d > 74)
+  float edge_th;        // GLR_MATCH_EDGE: threshold of the edge maps
+  size_t edge_off;      // GLR_MATCH_EDGE: edge planes [n_img][4 C][H][W]
   int epi_batch;        // tensor-core epilogue: 32-column chunks read from TMEM per visit (2 or 4)
   long long npos_pad;   // BF16 position rows per image (pos_tiles * pos_tile)
   size_t mean_off, qn_off, keyv_off, buf_off, bufcnt_off, taugl_off, qpack_off, kpack_off, embp_off, embk_off, total;
@@ -71,6 +73,7 @@ glr_status launch_gram_wnnm(const glr_images& im, const int32_t* n_found, int N,
                             float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
 glr_status launch_wnnm_smem(const glr_images& im, bool cplx, const int32_t* n_found, int N, int K, float sigma_w,
                             float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
+glr_status launch_edge_planes(const float* x, const glr_images& im, float th, float* planes, cudaStream_t s);
 glr_status launch_mosaic_init(const float* y, const float* masks, long long mstride, int G, int T, int H, int W, int s,
                               float* x_out, cudaStream_t st);
 glr_status launch_fft2(const float* in, float* out, int n_img, int H, int W, int inverse, cudaStream_t s);

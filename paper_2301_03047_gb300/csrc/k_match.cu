@@ -300,7 +300,9 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
     k_rerank(const float* __restrict__ x, const int32_t* __restrict__ keys, const int32_t* __restrict__ n_found,
              int n_img, int C, int H, int W, int P, int N, int Npad, int K, int streams_per_key, int cap_slots,
              int kp, int pow2, const uint2* __restrict__ bufs, const int* __restrict__ buf_cnt,
-             int32_t* __restrict__ idx, float* __restrict__ dist) {
+             int exact_scores, float dist_scale, int32_t* __restrict__ idx, float* __restrict__ dist) {
+  // exact_scores != 0: the stream scores are already exact (the heat map of Eq. 8 on
+  // 0/1 operands); they are sorted as they are and dist = dist_scale * score
   extern __shared__ unsigned long long rr_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int d = C * P * P;
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
     const int kq = keys[gk];
     if ((unsigned)kq >= (unsigned)(Wq * (H - P + 1))) continue;  // flagged by k_key_vectors
     const int kr = kq / Wq, kc = kq - (kq / Wq) * Wq;
-    for (int e = lane; e < d; e += 32) {
+    for (int e = lane; !exact_scores && e < d; e += 32) {
       const int ch = e / (P * P), dr = (e / P) % P, dc = e % P;
       pv[e] = __ldg(x + (((long long)f * C + ch) * H + kr + dr) * W + kc + dc);
     }
@@ -325,12 +327,15 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
     for (int sidx = 0; sidx < streams_per_key; ++sidx) {
       const int n = min(buf_cnt[s0 + sidx], kp);
       const uint2* b = bufs + (s0 + sidx) * cap_slots;
-      for (int i = lane; i < n; i += 32) list[total + i] = b[i].y;
+      for (int i = lane; i < n; i += 32) {
+        const uint2 e = b[i];
+        list[total + i] = exact_scores ? (((unsigned long long)e.x << 32) | e.y) : e.y;
+      }
       total += n;
     }
     __syncwarp();
     // exact FP32 distances, summed in a fixed order over the vector index
-    for (int i = lane; i < total; i += 32) {
+    for (int i = lane; !exact_scores && i < total; i += 32) {
       const int q = (int)list[i];
       const int r = q / Wq, c = q - (q / Wq) * Wq;
       float acc = 0.f;
@@ -437,7 +442,7 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
     for (int i = lane; i < K; i += 32) {
       const unsigned long long e = list[i];
       if (idx) idx[gk * K + i] = (int32_t)(e & 0xffffffffu);
-      if (dist) dist[gk * K + i] = float_from_order_key((uint32_t)(e >> 32));
+      if (dist) dist[gk * K + i] = dist_scale * float_from_order_key((uint32_t)(e >> 32));
     }
     __syncwarp();
   }
@@ -455,7 +460,9 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   MatchPlan pl{};
   pl.mode = o ? o->mode : GLR_MATCH_FP32;
   pl.K = K;
-  const bool tc = pl.mode == GLR_MATCH_BF16 || pl.mode == GLR_MATCH_LEARNED;
+  const bool edge = pl.mode == GLR_MATCH_EDGE;
+  const bool tc = pl.mode == GLR_MATCH_BF16 || pl.mode == GLR_MATCH_LEARNED || edge;
+  pl.edge_th = (o && edge) ? o->edge_th : 0.f;
   pl.Kp = (o && o->k_over > 0) ? o->k_over : (pl.mode == GLR_MATCH_LEARNED ? std::max(256, K + 16) : K + 16);
   pl.Kp = std::max(pl.Kp, K);
   // a small compaction trigger publishes a first threshold early; each compaction keeps ~Kp + (cap - Kp) / 4
@@ -483,7 +490,8 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   pl.tiles_per_split = (int)ceil_div(pl.pos_tiles, splits);
   pl.splits = (int)ceil_div(pl.pos_tiles, pl.tiles_per_split);
   pl.streams_per_key = pl.splits * pl.subs;
-  const int d = im.C * im.P * im.P;
+  // the heat map of Eq. 8 contracts the 4 C binary edge planes instead of the image
+  const int d = (edge ? 4 : 1) * im.C * im.P * im.P;
   const long long npos = (long long)Hq * Wq;
   WsLayout L;
   pl.mean_off = L.take((size_t)im.n_img * 4);
@@ -505,6 +513,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
     pl.qpack_off = L.take((size_t)im.n_img * pl.npos_pad * dk * 2);
     pl.kpack_off = L.take((size_t)im.n_img * pl.Npad * dk * 2);
   }
+  if (edge) pl.edge_off = L.take((size_t)im.n_img * 4 * im.C * im.H * im.W * 4);
   if (pl.mode == GLR_MATCH_LEARNED) {
     pl.embp_off = L.take((size_t)im.n_img * npos * 16 * 4);
     pl.embk_off = L.take((size_t)im.n_img * pl.Npad * 16 * 4);
@@ -518,7 +527,12 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
                         cudaStream_t s) {
   const int Hq = im.H - im.P + 1, Wq = im.W - im.P + 1;
   const long long npos = (long long)Hq * Wq;
-  const int d = im.C * im.P * im.P;
+  const bool edge = pl.mode == GLR_MATCH_EDGE;
+  const bool tc = pl.mode == GLR_MATCH_BF16 || pl.mode == GLR_MATCH_LEARNED || edge;
+  // GLR_MATCH_EDGE: every later step sees the 4 C binary edge planes as the image
+  glr_images ime = im;
+  if (edge) ime.C = 4 * im.C;
+  const int d = ime.C * im.P * im.P;
   float* mean = reinterpret_cast<float*>(ws + pl.mean_off);
   float* qn = reinterpret_cast<float*>(ws + pl.qn_off);
   float* keyv = reinterpret_cast<float*>(ws + pl.keyv_off);
@@ -528,11 +542,19 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
   uint32_t* taugl = reinterpret_cast<uint32_t*>(ws + pl.taugl_off);
   if (cudaMemsetAsync(taugl, 0xff, (size_t)im.n_img * pl.Npad * 4, s) != cudaSuccess) return GLR_ECUDA;
   (void)HW;
-  {
+  const float* xs = x;
+  if (edge) {
+    // binary edge planes, no mean shift (the correlation is not shift-invariant)
+    float* planes = reinterpret_cast<float*>(ws + pl.edge_off);
+    glr_status st = launch_edge_planes(x, im, pl.edge_th, planes, s);
+    if (st != GLR_OK) return st;
+    xs = planes;
+    if (cudaMemsetAsync(mean, 0, (size_t)im.n_img * 4, s) != cudaSuccess) return GLR_ECUDA;
+  } else {
     const glr_status st = launch_image_mean(x, im, mean, s);
     if (st != GLR_OK) return st;
   }
-  {
+  if (!tc) {  // the FP32 scorer adds ||q||^2 itself; the tensor-core operands carry their norms
     const long long total = (long long)im.n_img * npos;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
     GLR_LAUNCH("k_patch_norms", s, k_patch_norms<<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, qn));
@@ -540,7 +562,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
   {
     const long long total = (long long)im.n_img * pl.Npad * d;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
-    GLR_LAUNCH("k_key_vectors", s, k_key_vectors<<<blocks, 256, 0, s>>>(x, mean, keys, n_found, im.n_img, im.C, im.H, im.W, im.P, N, pl.Npad,
+    GLR_LAUNCH("k_key_vectors", s, k_key_vectors<<<blocks, 256, 0, s>>>(xs, mean, keys, n_found, im.n_img, ime.C, im.H, im.W, im.P, N, pl.Npad,
                                         keyv, reinterpret_cast<StatusBlock*>(ws)));
   }
   StreamCfg cfg{pl.cap, pl.Kp};
@@ -552,8 +574,8 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     st = launch_encode_vectors(keyv, (long long)im.n_img * pl.Npad, d, encoder, emb_k, s);
     if (st != GLR_OK) return st;
   }
-  if (pl.mode == GLR_MATCH_BF16 || pl.mode == GLR_MATCH_LEARNED) {
-    const glr_status st = launch_match_tc(x, im, keys, n_found, N, pl, ws, s);
+  if (tc) {
+    const glr_status st = launch_match_tc(xs, ime, keys, n_found, N, pl, ws, s);
     if (st != GLR_OK) return st;
   } else {
     // channels per chunk: all of them if the transposed key tile fits, else as many as fit
@@ -600,7 +622,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, RR_WARPS), 152LL * 16));
     GLR_LAUNCH("k_rerank", s, k_rerank<<<blocks, RR_WARPS * 32, smem, s>>>(x, keys, n_found, im.n_img, im.C, im.H, im.W, im.P, N, pl.Npad,
                                                  pl.K, pl.streams_per_key, pl.cap + 32, pl.Kp, pow2, bufs, bufcnt,
-                                                 idx, dist));
+                                                 edge ? 1 : 0, edge ? -0.5f : 1.f, idx, dist));
   }
   return GLR_OK;
 }

@@ -194,7 +194,7 @@ __host__ __device__ constexpr int norm_col(int d) { return d > DK_MAIN ? d : DK_
 // emb != nullptr: pack the 16-value embeddings emb[img][q][16] instead of the patches.
 __global__ void __launch_bounds__(256) k_pack_positions(const float* __restrict__ x, const float* __restrict__ mean,
                                                         int n_img, int C, int H, int W, int P, long long npos_pad,
-                                                        const float* __restrict__ emb,
+                                                        const float* __restrict__ emb, int raw,
                                                         __nv_bfloat16* __restrict__ qmain,
                                                         __nv_bfloat16* __restrict__ qaux) {
   const int Hq = H - P + 1, Wq = W - P + 1;
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) k_pack_positions(const float* __restrict_
       split3(nrm, h, m, l);
 #pragma unroll
       for (int e = 0; e < DK_AUX; ++e) {  // static register indices: select by offset
-        const int t = e - nb;
+        const int t = raw ? -1 : e - nb;  // raw operands (heat map): no norm columns
         if (t == 0) row[DK_MAIN + e] = h;
         else if (t == 1) row[DK_MAIN + e] = m;
         else if (t == 2) row[DK_MAIN + e] = l;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(256) k_pack_positions(const float* __restrict_
 }
 
 // Keys: thread per key slot of the padded key array.
-__global__ void __launch_bounds__(256) k_pack_keys(const float* __restrict__ keyv, int n_keys_total, int d,
+__global__ void __launch_bounds__(256) k_pack_keys(const float* __restrict__ keyv, int n_keys_total, int d, int raw,
                                                    __nv_bfloat16* __restrict__ kmain,
                                                    __nv_bfloat16* __restrict__ kaux) {
   const int nb = norm_col(d) - DK_MAIN;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256) k_pack_keys(const float* __restrict__ key
     split3(nrm, h, m, l);
 #pragma unroll
     for (int e = 0; e < DK_AUX; ++e) {
-      const int t = e - nb;
+      const int t = raw ? -1 : e - nb;
       if (t >= 0 && t < 3) row[DK_MAIN + e] = one;
       else if (t == 3) row[DK_MAIN + e] = h;
       else if (t == 4) row[DK_MAIN + e] = m;
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(256) k_pack_keys(const float* __restrict__ key
 constexpr int PW_POS = 32;
 __global__ void __launch_bounds__(256) k_pack_positions_w(const float* __restrict__ x, const float* __restrict__ mean,
                                                           int n_img, int C, int H, int W, int P, long long npos_pad,
-                                                          int nkc, __nv_bfloat16* __restrict__ qmain,
+                                                          int nkc, int raw, __nv_bfloat16* __restrict__ qmain,
                                                           __nv_bfloat16* __restrict__ qaux) {
   extern __shared__ __align__(16) uint8_t pw_smem[];
   const int rowlen = nkc * DK_MAIN;  // bf16 per row
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(256) k_pack_positions_w(const float* __restric
       const __nv_bfloat16 z = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
 #pragma unroll
       for (int e = 0; e < DK_AUX; ++e) aux[e] = z;
-      if (valid) {
+      if (valid && !raw) {
         split3(nrm, aux[0], aux[1], aux[2]);
         aux[3] = aux[4] = aux[5] = one;
       }
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(256) k_pack_positions_w(const float* __restric
 }
 
 __global__ void __launch_bounds__(256) k_pack_keys_w(const float* __restrict__ keyv, int n_keys_total, int d, int nkc,
-                                                     __nv_bfloat16* __restrict__ kmain,
+                                                     int raw, __nv_bfloat16* __restrict__ kmain,
                                                      __nv_bfloat16* __restrict__ kaux) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_keys_total; i += gridDim.x * blockDim.x) {
     float nrm = 0.f;
@@ -389,8 +389,10 @@ __global__ void __launch_bounds__(256) k_pack_keys_w(const float* __restrict__ k
     const __nv_bfloat16 z = __float2bfloat16_rn(0.f), one = __float2bfloat16_rn(1.f);
 #pragma unroll
     for (int e = 0; e < DK_AUX; ++e) aux[e] = z;
-    aux[0] = aux[1] = aux[2] = one;
-    split3(nrm, aux[3], aux[4], aux[5]);
+    if (!raw) {
+      aux[0] = aux[1] = aux[2] = one;
+      split3(nrm, aux[3], aux[4], aux[5]);
+    }
     uint4* dsta = reinterpret_cast<uint4*>(kaux + (long long)i * DK_AUX);
     dsta[0] = reinterpret_cast<const uint4*>(aux)[0];
     dsta[1] = reinterpret_cast<const uint4*>(aux)[1];
@@ -826,6 +828,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
                                 const float* emb_keys, cudaStream_t s) {
   const int d = emb_keys ? 16 : im.C * im.P * im.P;
   const bool wide = pl.nkc > 1;
+  const int raw = pl.mode == GLR_MATCH_EDGE ? 1 : 0;  // heat-map operands: no norm columns
   if (!wide && norm_col(d) + 6 > DK_MAIN + DK_AUX) return GLR_ENOTSUP;
   if (wide && (emb_keys != nullptr || dump != nullptr || pl.nkc * DK_MAIN < d)) return GLR_ENOTSUP;
   const float* mean = reinterpret_cast<const float*>(ws + pl.mean_off);
@@ -849,12 +852,12 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
       const int pblocks = (int)std::max<long long>(1, std::min<long long>(nblk, 152LL * 16));
       GLR_LAUNCH("k_pack_positions", s,
                  k_pack_positions_w<<<pblocks, 256, psmem, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P,
-                                                                 pl.npos_pad, pl.nkc, qmain, qaux));
+                                                                 pl.npos_pad, pl.nkc, raw, qmain, qaux));
     }
     {
       const int nk = im.n_img * pl.Npad;
       const int blocks = (int)std::max<long long>(1, ceil_div(nk, 256));
-      GLR_LAUNCH("k_pack_keys", s, k_pack_keys_w<<<blocks, 256, 0, s>>>(keyv, nk, d, pl.nkc, kmain, kaux));
+      GLR_LAUNCH("k_pack_keys", s, k_pack_keys_w<<<blocks, 256, 0, s>>>(keyv, nk, d, pl.nkc, raw, kmain, kaux));
     }
     CUtensorMap tq, tqa, tk, tka;
     const uint64_t qrows = (uint64_t)im.n_img * pl.npos_pad, krows = (uint64_t)im.n_img * pl.Npad;
@@ -885,12 +888,12 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
     GLR_LAUNCH("k_pack_positions", s,
                k_pack_positions<<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, pl.npos_pad, emb_pos,
-                                                       qmain, qaux));
+                                                       raw, qmain, qaux));
   }
   {
     const int nk = im.n_img * pl.Npad;
     const int blocks = (int)std::max<long long>(1, ceil_div(nk, 256));
-    GLR_LAUNCH("k_pack_keys", s, k_pack_keys<<<blocks, 256, 0, s>>>(keyv, nk, d, kmain, kaux));
+    GLR_LAUNCH("k_pack_keys", s, k_pack_keys<<<blocks, 256, 0, s>>>(keyv, nk, d, raw, kmain, kaux));
   }
   if (seed_keys != nullptr) {
     const long long nkeys = (long long)im.n_img * seed_N;

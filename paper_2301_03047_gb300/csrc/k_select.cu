@@ -24,6 +24,41 @@ namespace {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// Sobel gradients (replicated border) at (r, c) of one channel, in a fixed FP32
+// order (exact for 8-bit-quantised images): gh = right - left columns, gv =
+// bottom - top rows, weights 1 2 1.
+__device__ __forceinline__ void sobel_at(const float* __restrict__ im, int H, int W, int r, int c, float& gh,
+                                         float& gv) {
+  const int rm = max(r - 1, 0), rp = min(r + 1, H - 1), cm = max(c - 1, 0), cp = min(c + 1, W - 1);
+  const float a00 = __ldg(im + rm * W + cm), a01 = __ldg(im + rm * W + c), a02 = __ldg(im + rm * W + cp);
+  const float a10 = __ldg(im + r * W + cm), a12 = __ldg(im + r * W + cp);
+  const float a20 = __ldg(im + rp * W + cm), a21 = __ldg(im + rp * W + c), a22 = __ldg(im + rp * W + cp);
+  gh = ((a02 - a00) + 2.f * (a12 - a10)) + (a22 - a20);
+  gv = ((a20 - a00) + 2.f * (a21 - a01)) + (a22 - a02);
+}
+
+// The four binary edge maps of Eq. 6 for every channel (the operands of the
+// heat map of Eq. 8): planes[f][m * C + ch][r][c] = 0 / 1 for m = h+, h-, v+, v-.
+__global__ void __launch_bounds__(256) k_edge_planes(const float* __restrict__ x, int n_img, int C, int H, int W,
+                                                     float th, float* __restrict__ planes) {
+  const long long HW = (long long)H * W;
+  const long long total = (long long)n_img * C * HW;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long fc = i / HW;
+    const int p = (int)(i - fc * HW);
+    const int f = (int)(fc / C), ch = (int)(fc - (long long)f * C);
+    const int r = p / W, c = p - (p / W) * W;
+    float gh, gv;
+    sobel_at(x + fc * HW, H, W, r, c, gh, gv);
+    float* o = planes + ((long long)f * 4 * C + ch) * HW + p;
+    o[0] = gh > th ? 1.f : 0.f;
+    o[(long long)C * HW] = -gh > th ? 1.f : 0.f;
+    o[2LL * C * HW] = gv > th ? 1.f : 0.f;
+    o[3LL * C * HW] = -gv > th ? 1.f : 0.f;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_edge_sum(const float* __restrict__ x, int n_img, int C, int H, int W,
                                                   float th, uint8_t* __restrict__ S) {
   const long long HW = (long long)H * W;
@@ -33,15 +68,10 @@ __global__ void __launch_bounds__(256) k_edge_sum(const float* __restrict__ x, i
     const long long f = i / HW;
     const int p = (int)(i - f * HW);
     const int r = p / W, c = p - (p / W) * W;
-    const int rm = max(r - 1, 0), rp = min(r + 1, H - 1), cm = max(c - 1, 0), cp = min(c + 1, W - 1);
     unsigned bits = 0;
     for (int ch = 0; ch < C; ++ch) {
-      const float* im = x + (f * C + ch) * HW;
-      const float a00 = __ldg(im + rm * W + cm), a01 = __ldg(im + rm * W + c), a02 = __ldg(im + rm * W + cp);
-      const float a10 = __ldg(im + r * W + cm), a12 = __ldg(im + r * W + cp);
-      const float a20 = __ldg(im + rp * W + cm), a21 = __ldg(im + rp * W + c), a22 = __ldg(im + rp * W + cp);
-      const float gh = ((a02 - a00) + 2.f * (a12 - a10)) + (a22 - a20);
-      const float gv = ((a20 - a00) + 2.f * (a21 - a01)) + (a22 - a02);
+      float gh, gv;
+      sobel_at(x + (f * C + ch) * HW, H, W, r, c, gh, gv);
       bits |= (gh > th ? 1u : 0u) | (-gh > th ? 2u : 0u) | (gv > th ? 4u : 0u) | (-gv > th ? 8u : 0u);
     }
     S[i] = (uint8_t)__popc(bits);
@@ -375,6 +405,13 @@ glr_status launch_select(const float* x, const glr_images& im, float th, int N, 
     attr_done = true;
   }
   GLR_LAUNCH("k_topn", s, k_topn<<<im.n_img, 1024, smem, s>>>(cand, cnt, cap, im.H, im.W, im.P, N, pow2, bm, keys, n_found, n_corner));
+  return GLR_OK;
+}
+
+glr_status launch_edge_planes(const float* x, const glr_images& im, float th, float* planes, cudaStream_t s) {
+  const long long total = (long long)im.n_img * im.C * im.H * im.W;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+  GLR_LAUNCH("k_edge_planes", s, k_edge_planes<<<blocks, 256, 0, s>>>(x, im.n_img, im.C, im.H, im.W, th, planes));
   return GLR_OK;
 }
 
