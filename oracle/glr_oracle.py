@@ -54,6 +54,11 @@ A9  WNNM single pass: sigma_hat_i = sqrt(max(s_i^2 - K sw^2, 0)),
 A10 Aggregation weight 1; pixels no patch covers keep the input value.
 A12 Plain GAP (accelerated is a flag); R = sum_t A_t^2 with R = 0 -> 1;
     x0 = Phi^T (y / R).
+A19 Corner + uniform keys (Section 3, CACTI and the matching-strategy
+    comparison): at most N - n_uniform corners, then a uniform grid of stride
+    isqrt(Hq*Wq // n_uniform) in row-major order, skipping chosen positions.
+A20 ADMM for y = Phi x (the paper uses GAP or ADMM): scaled form z = D(x + u),
+    u = u + x - z, x = w + Phi^T((y - Phi w)/(R + rho)) with w = z - u.
 A18 The paper's own matching score (the heat map of Eq. 8, ``edge_match_topk``):
     Conv2d is a correlation summed over the four maps and the C channels (the
     per-channel maps, not the OR-ed ones of key selection); a larger value is a
@@ -176,15 +181,21 @@ def nms3(R: np.ndarray) -> np.ndarray:
     return keep
 
 
-def select_keys(x: np.ndarray, P: int, N: int, th: float) -> tuple[np.ndarray, int]:
+def select_keys(x: np.ndarray, P: int, N: int, th: float, n_uniform: int = 0) -> tuple[np.ndarray, int]:
     """Key (exemplar) positions of one image x[C][H][W]: corners first, then a uniform grid.
 
+    n_uniform > 0 mixes in uniformly placed keys (reading A19, the corner +
+    uniform selections of Section 3): at most N - n_uniform corners, then the
+    row-major grid of stride max(1, isqrt(Hq*Wq // n_uniform)) up to N keys,
+    skipping chosen positions (then the reading-A5 grid if still short).
     Returns (keys int32[N] position ids in rank order, number of corner keys kept).
     """
     C, H, W = x.shape
     Hq, Wq = H - P + 1, W - P + 1
     if N > Hq * Wq or N <= 0:
         raise ValueError("N must be in 1..Hq*Wq")
+    if not 0 <= n_uniform <= N:
+        raise ValueError("n_uniform must be in 0..N")
     S = edge_sum(x, th)
     R = corner_response(S)
     keep = nms3(R)
@@ -192,7 +203,7 @@ def select_keys(x: np.ndarray, P: int, N: int, th: float) -> tuple[np.ndarray, i
     pix = rr * W + cc
     resp = R[rr, cc]
     order = np.lexsort((pix, -resp))  # R descending, pixel id ascending
-    top = order[:N]
+    top = order[:N - n_uniform]
     chosen: list[int] = []
     seen: set[int] = set()
     for i in top:
@@ -203,6 +214,16 @@ def select_keys(x: np.ndarray, P: int, N: int, th: float) -> tuple[np.ndarray, i
             seen.add(q)
             chosen.append(q)
     n_corner = len(chosen)
+    if n_uniform > 0:
+        su = max(1, math.isqrt((Hq * Wq) // n_uniform))
+        for gr in range(0, Hq, su):
+            for gc in range(0, Wq, su):
+                if len(chosen) == N:
+                    break
+                q = gr * Wq + gc
+                if q not in seen:
+                    seen.add(q)
+                    chosen.append(q)
     s = max(1, math.isqrt((Hq * Wq) // N))
     if len(chosen) < N:
         for gr in range(0, Hq, s):
@@ -410,6 +431,30 @@ def gap_project(y: np.ndarray, masks: np.ndarray, v: np.ndarray, y_acc: np.ndarr
         yd = y_acc
     x = vd + A * ((yd - phi_v) / R)[None]
     return x, y_acc
+
+
+def admm_sci_step(y, masks, z, x, u, rho):
+    """One ADMM step for y = Phi x after the denoiser (reading A20, scaled form):
+    u <- u + x - z;  x' = argmin ||y - Phi x||^2 + rho ||x - (z - u)||^2
+    = w + Phi^T ((y - Phi w) / (R + rho)) with w = z - u (Phi Phi^T = diag(R));
+    returns (x', u, the next denoiser input x' + u)."""
+    A = np.asarray(masks, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64) + np.asarray(x, dtype=np.float64) - np.asarray(z, dtype=np.float64)
+    w = np.asarray(z, dtype=np.float64) - u
+    R = (A * A).sum(0)
+    xn = w + A * ((np.asarray(y, dtype=np.float64) - (A * w).sum(0)) / (R + rho))[None]
+    return xn, u, xn + u
+
+
+def glr_reconstruct_admm(y, masks, P, N, K, sigmas, c, th, rho, eps=1e-16, n_uniform=0):
+    """ADMM iterations with the GLR denoiser (reading A20): start x = Phi^T(y/R), u = 0;
+    z = D(x + u), then admm_sci_step."""
+    x = gap_init(y, masks)
+    u = np.zeros_like(x)
+    for sw in sigmas:
+        z, _ = glr_denoise((x + u)[:, None], P, N, K, sw, c, th, eps)
+        x, u, _ = admm_sci_step(y, masks, z[:, 0], x, u, rho)
+    return x
 
 
 def glr_reconstruct(y, masks, P, N, K, sigmas, c, th, accelerate=False, eps=1e-16, callback=None):

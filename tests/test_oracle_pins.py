@@ -433,3 +433,44 @@ def test_edge_heatmap_self_is_maximal_and_copies_tie():
 def test_edge_heatmap_flat_image_is_zero():
     x = np.full((1, 12, 12), 0.4)
     assert np.all(O.edge_heatmap(x, 4, 10, 0.1) == 0)
+
+
+# ---------------------------------------------------------------------------
+# Corner + uniform keys (A19) and ADMM for SCI (A20)
+# ---------------------------------------------------------------------------
+def test_select_keys_uniform_mix_closed_form():
+    """On a flat image there are no corners: n_uniform keys come from the stride
+    isqrt(Hq*Wq // n_uniform) grid, the rest from the reading-A5 grid."""
+    x = np.full((1, 30, 30), 0.5)
+    P, N, nu = 5, 20, 9
+    keys, nc = O.select_keys(x, P, N, 0.1, n_uniform=nu)
+    Hq = Wq = 26
+    su = int(np.sqrt(Hq * Wq // nu))  # 8
+    want = [r * Wq + c for r in range(0, Hq, su) for c in range(0, Wq, su)][:nu]
+    assert nc == 0 and list(keys[:nu]) == want and len(set(keys.tolist())) == N
+
+
+def test_select_keys_uniform_mix_caps_corners():
+    x = synth.quantize8(synth.textured_frames(synth.rng_for("mix"), 1, 64, 64))[None][0]
+    k0, n0 = O.select_keys(x, 8, 40, 0.1)
+    k1, n1 = O.select_keys(x, 8, 40, 0.1, n_uniform=15)
+    assert n1 <= 25 and list(k1[:n1]) == list(k0[:n1])  # the same corners, in rank order, capped
+
+
+def test_admm_sci_step_is_the_minimiser():
+    rng = synth.rng_for("admm-sci")
+    T, H, W = 4, 9, 11
+    A = (rng.random((T, H, W)) < 0.5).astype(float)
+    y = rng.random((H, W))
+    z, x, u = rng.random((T, H, W)), rng.random((T, H, W)), rng.random((T, H, W))
+    for rho in (0.05, 1.0, 5.0):
+        xn, un, wn = O.admm_sci_step(y, A, z, x, u, rho)
+        assert np.allclose(un, u + x - z) and np.allclose(wn, xn + un)
+        w = z - un
+        # gradient of ||y - Phi x||^2 / 2 + rho ||x - w||^2 / 2 vanishes
+        g = A * ((A * xn).sum(0) - y)[None] + rho * (xn - w)
+        assert np.abs(g).max() < 1e-12
+    # rho -> 0 gives the GAP projection of w (Phi x = y where R > 0)
+    xn, _, _ = O.admm_sci_step(y, A, z, x, u, 1e-12)
+    R = (A * A).sum(0)
+    assert np.allclose(((A * xn).sum(0) - y)[R > 0], 0, atol=1e-9)
