@@ -133,6 +133,19 @@ glr_status glr_select_keys(const float* x, const glr_images* im, float edge_th, 
                            size_t ws_bytes, void* stream);
 
 /*
+ * Corner + uniform exemplar mixes (Section 3: the CACTI experiments add uniformly
+ * selected exemplars to the corner-based ones; the matching-strategy comparison
+ * uses as many uniform as corner exemplars).  At most N - n_uniform corners (in
+ * the rank order above), then the row-major grid of stride
+ * max(1, isqrt(Hq*Wq / n_uniform)) up to N keys, skipping chosen positions, then
+ * the stride-isqrt(Hq*Wq/N) grid if keys are still missing.  0 <= n_uniform <= N;
+ * n_uniform = 0 is glr_select_keys.  Same workspace as glr_select_keys.
+ */
+glr_status glr_select_keys_mixed(const float* x, const glr_images* im, float edge_th, int32_t N,
+                                 int32_t n_uniform, int32_t* keys, int32_t* n_found, int32_t* n_corner,
+                                 void* ws, size_t ws_bytes, void* stream);
+
+/*
  * Global matching -- Section 2 (Eq. 1 over the entire image; the heat map of
  * Eq. 4 computed as ||p||^2 - 2<p,q> + ||q||^2 for every key p and every
  * position q of the same image, fused with a running per-key top-K so the
@@ -279,6 +292,21 @@ glr_status glr_aggregate_noalloc(const float* groups, const int32_t* idx, const 
 glr_status glr_gap_step(const float* y, const float* masks, int64_t mask_group_stride,
                         const float* v, int32_t G, int32_t T, int32_t H, int32_t W,
                         int32_t accelerate, float* y_acc, float* x_out, void* stream);
+
+/*
+ * ADMM for y = sum_t A_t x_t (the paper's SCI reconstruction uses GAP or ADMM,
+ * Section 2 after Eq. 5), scaled form, after the denoiser z = D(x + u):
+ *   u  <- u + x - z                                  (in place)
+ *   x'  = w + Phi^T ((y - Phi w) / (R + rho)),  w = z - u,  R = sum_t A_t^2
+ *         (the minimiser of ||y - Phi x||^2 + rho ||x - w||^2)      -> x_out
+ *   x' + u                                           -> w_out (next denoiser input)
+ * y [G][H][W]; masks [T][H][W] per group at element stride mask_group_stride
+ * (0 = shared); z, x, u, x_out, w_out [G][T][H][W]; rho > 0.  x_out may alias x,
+ * w_out may alias z; no other aliasing.
+ */
+glr_status glr_admm_sci_step(const float* y, const float* masks, int64_t mask_group_stride, const float* z,
+                             const float* x, float* u, int32_t G, int32_t T, int32_t H, int32_t W, float rho,
+                             float* x_out, float* w_out, void* stream);
 
 /*
  * Start of multispectral-filter-array demosaicing (Section 3, MSFA; the GAP

@@ -34,6 +34,8 @@ class GlrMatchOpts(ctypes.Structure):
 PROTOTYPES = {
     "glr_workspace_size": (c_size_t, [c_int32, ctypes.POINTER(GlrImages), c_int32, c_int32, ctypes.POINTER(GlrMatchOpts)]),
     "glr_select_keys": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_float, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "glr_select_keys_mixed": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_float, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "glr_admm_sci_step": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_float, c_void_p, c_void_p, c_void_p]),
     "glr_match_topk": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, ctypes.POINTER(GlrMatchOpts), c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_debug_match_scores": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_encoder_embed": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

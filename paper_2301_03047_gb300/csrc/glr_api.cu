@@ -164,6 +164,13 @@ size_t glr_workspace_size(int32_t op, const glr_images* im, int32_t N, int32_t K
 
 glr_status glr_select_keys(const float* x, const glr_images* im, float edge_th, int32_t N, int32_t* keys,
                            int32_t* n_found, int32_t* n_corner, void* ws, size_t ws_bytes, void* stream) {
+  return glr_select_keys_mixed(x, im, edge_th, N, 0, keys, n_found, n_corner, ws, ws_bytes, stream);
+}
+
+glr_status glr_select_keys_mixed(const float* x, const glr_images* im, float edge_th, int32_t N, int32_t n_uniform,
+                                 int32_t* keys, int32_t* n_found, int32_t* n_corner, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  if (n_uniform < 0 || n_uniform > N) return GLR_EINVAL;
   if (!images_ok(im) || !x || !keys || !n_found) return GLR_EINVAL;
   if (!(edge_th >= 0.f) || !aligned(x, 4) || !aligned(keys, 4)) return GLR_EINVAL;
   const long long npos = npos_of(im);
@@ -173,7 +180,7 @@ glr_status glr_select_keys(const float* x, const glr_images* im, float edge_th, 
   const SelectWs L = select_ws_layout(*im, N);
   glr_status st = begin_ws(ws, ws_bytes, L.total, s);
   if (st != GLR_OK) return st;
-  return launch_select(x, *im, edge_th, N, keys, n_found, n_corner, (char*)ws, L, s);
+  return launch_select(x, *im, edge_th, N, n_uniform, keys, n_found, n_corner, (char*)ws, L, s);
 }
 
 glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* keys, const int32_t* n_found,
@@ -287,6 +294,20 @@ glr_status glr_lowrank_groups_complex(const float* x, const glr_images* im, cons
   if (d <= 72 && K <= 64)
     return launch_wnnm_complex_regs(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
   return launch_wnnm_smem(*im, true, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
+}
+
+glr_status glr_admm_sci_step(const float* y, const float* masks, int64_t mask_group_stride, const float* z,
+                             const float* x, float* u, int32_t G, int32_t T, int32_t H, int32_t W, float rho,
+                             float* x_out, float* w_out, void* stream) {
+  if (!y || !masks || !z || !x || !u || !x_out || !w_out || G < 1 || T < 1 || H < 1 || W < 1) return GLR_EINVAL;
+  if (!(rho > 0.f) || !std::isfinite(rho) || mask_group_stride < 0) return GLR_EINVAL;
+  if ((long long)G * T * H * W > (1LL << 36)) return GLR_EINVAL;
+  if ((const void*)x_out == (const void*)w_out || (const void*)x_out == (const void*)u ||
+      (const void*)w_out == (const void*)u || (const void*)x_out == (const void*)z ||
+      (const void*)w_out == (const void*)x)
+    return GLR_EINVAL;
+  return launch_admm_sci(y, masks, mask_group_stride, z, x, u, G, T, (long long)H * W, rho, x_out, w_out,
+                         (cudaStream_t)stream);
 }
 
 glr_status glr_mosaic_init(const float* y, const float* masks, int64_t mask_group_stride, int32_t G, int32_t T,

@@ -17,7 +17,7 @@ struct SelectWs {
   size_t S_off, R_off, cand_off, cnt_off, bitmap_off, total;
 };
 SelectWs select_ws_layout(const glr_images& im, int N);
-glr_status launch_select(const float* x, const glr_images& im, float th, int N, int32_t* keys, int32_t* n_found,
+glr_status launch_select(const float* x, const glr_images& im, float th, int N, int n_uniform, int32_t* keys, int32_t* n_found,
                          int32_t* n_corner, char* ws, const SelectWs& L, cudaStream_t s);
 
 // ---- matching (k_match.cu, k_match_tc.cu)
@@ -74,6 +74,8 @@ glr_status launch_gram_wnnm(const glr_images& im, const int32_t* n_found, int N,
 glr_status launch_wnnm_smem(const glr_images& im, bool cplx, const int32_t* n_found, int N, int K, float sigma_w,
                             float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
 glr_status launch_edge_planes(const float* x, const glr_images& im, float th, float* planes, cudaStream_t s);
+glr_status launch_admm_sci(const float* y, const float* masks, long long mstride, const float* z, const float* x,
+                           float* u, int G, int T, long long HW, float rho, float* x_out, float* w_out, cudaStream_t s);
 glr_status launch_mosaic_init(const float* y, const float* masks, long long mstride, int G, int T, int H, int W, int s,
                               float* x_out, cudaStream_t st);
 glr_status launch_fft2(const float* in, float* out, int n_img, int H, int W, int inverse, cudaStream_t s);

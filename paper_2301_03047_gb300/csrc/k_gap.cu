@@ -131,3 +131,49 @@ glr_status launch_mosaic_init(const float* y, const float* masks, long long mstr
 }
 
 }  // namespace glr
+
+// ADMM step for y = sum_t A_t x_t after the denoiser (scaled form): u += x - z,
+// w = z - u, x' = w + A (y - Phi w) / (R + rho), next denoiser input x' + u.
+// One thread per pixel over all T frames (x_out may alias x, w_out may alias z:
+// each element is read before it is written by the same thread).
+namespace glr {
+
+__global__ void __launch_bounds__(256) k_admm_sci(const float* __restrict__ y, const float* __restrict__ masks,
+                                                  long long mstride, const float* z, const float* x, float* u, int G,
+                                                  int T, long long HW, float rho, float* x_out, float* w_out) {
+  const long long total = (long long)G * HW;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long g = i / HW, p = i - g * HW;
+    const float* mg = masks + g * mstride;
+    float R = 0.f, phi = 0.f;
+    for (int t = 0; t < T; ++t) {
+      const long long o = (g * T + t) * HW + p;
+      const float a = __ldg(mg + (long long)t * HW + p);
+      const float un = u[o] + x[o] - z[o];
+      u[o] = un;
+      const float w = z[o] - un;
+      R = fmaf(a, a, R);
+      phi = fmaf(a, w, phi);
+    }
+    const float coef = (__ldg(y + g * HW + p) - phi) / (R + rho);
+    for (int t = 0; t < T; ++t) {
+      const long long o = (g * T + t) * HW + p;
+      const float a = __ldg(mg + (long long)t * HW + p);
+      const float un = u[o];
+      const float xn = fmaf(a, coef, z[o] - un);
+      x_out[o] = xn;
+      w_out[o] = xn + un;
+    }
+  }
+}
+
+glr_status launch_admm_sci(const float* y, const float* masks, long long mstride, const float* z, const float* x,
+                           float* u, int G, int T, long long HW, float rho, float* x_out, float* w_out, cudaStream_t s) {
+  const long long total = (long long)G * HW;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 16));
+  GLR_LAUNCH("k_admm_sci", s, k_admm_sci<<<blocks, 256, 0, s>>>(y, masks, mstride, z, x, u, G, T, HW, rho, x_out, w_out));
+  return GLR_OK;
+}
+
+}  // namespace glr

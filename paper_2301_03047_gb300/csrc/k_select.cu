@@ -203,7 +203,7 @@ __device__ int block_exclusive_scan(int v, int* warp_sums, int* total) {
 
 __global__ void __launch_bounds__(1024) k_topn(const unsigned long long* __restrict__ cand,
                                                const unsigned int* __restrict__ cnt, long long cap, int H, int W,
-                                               int P, int N, int pow2, uint32_t* __restrict__ bitmap,
+                                               int P, int N, int n_uniform, int pow2, uint32_t* __restrict__ bitmap,
                                                int32_t* __restrict__ keys, int32_t* __restrict__ n_found,
                                                int32_t* __restrict__ n_corner) {
   extern __shared__ unsigned long long sb[];  // [pow2]
@@ -217,14 +217,16 @@ __global__ void __launch_bounds__(1024) k_topn(const unsigned long long* __restr
   const int Hq = H - P + 1, Wq = W - P + 1;
   const long long M = min((long long)cnt[f], cap);
   const unsigned long long* cf = cand + (long long)f * cap;
+  const int Nc = N - n_uniform;  // corners allowed (the rest are uniform keys)
 
-  // 1. radix-select the N-th smallest rank key when there are more than N corners
+  // 1. radix-select the Nc-th smallest rank key when there are more than Nc corners
   unsigned long long T = ~0ull;
-  if (M > N) {
+  if (Nc == 0) T = 0;  // no corner is taken (rank keys of corners are never 0: R > 0)
+  if (Nc > 0 && M > Nc) {
     if (tid == 0) {
       s_prefix = 0;
       s_mask = 0;
-      s_k = N;
+      s_k = Nc;
     }
     __syncthreads();
     for (int pass = 0; pass < 8; ++pass) {
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(1024) k_topn(const unsigned long long* __restr
   if (tid == 0) s_nsel = 0;
   for (int i = tid; i < pow2; i += 1024) sb[i] = ~0ull;
   __syncthreads();
-  for (long long i = tid; i < M; i += 1024) {
+  for (long long i = tid; Nc > 0 && i < M; i += 1024) {
     const unsigned long long k = cf[i];
     if (k <= T) {
       const int slot = atomicAdd(&s_nsel, 1);
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(1024) k_topn(const unsigned long long* __restr
     }
   }
   __syncthreads();
-  const int nsel = min(s_nsel, N);
+  const int nsel = min(s_nsel, Nc);
   for (int k = 2; k <= pow2; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = tid; i < pow2; i += 1024) {
@@ -320,7 +322,9 @@ __global__ void __launch_bounds__(1024) k_topn(const unsigned long long* __restr
     for (int t = 0; t < per; ++t)
       if (keepbits & (1 << t)) kf[o++] = (int32_t)sb[tid * per + t];
   }
-  // 5. uniform grid fill in row-major order, skipping positions already chosen
+  // 5. uniform grid fill in row-major order, skipping positions already chosen:
+  //    first the grid of stride isqrt(npos / n_uniform) (mixed selections), then the
+  //    grid of stride isqrt(npos / N) while keys are still missing
   if (n_kept < N) {
     const long long npos = (long long)Hq * Wq;
     const long long words = (npos + 31) / 32;
@@ -333,26 +337,32 @@ __global__ void __launch_bounds__(1024) k_topn(const unsigned long long* __restr
         atomicOr(bm + (q >> 5), 1u << (q & 31));
       }
     __syncthreads();
-    long long ratio = npos / N;
-    long long s = (long long)sqrt((double)ratio);
-    while (s * s > ratio) --s;
-    while ((s + 1) * (s + 1) <= ratio) ++s;
-    if (s < 1) s = 1;
-    const long long ncol = (Wq + s - 1) / s, nrow = (Hq + s - 1) / s;
-    const long long G = ncol * nrow;
     int filled = n_kept;
-    for (long long g0 = 0; g0 < G && filled < N; g0 += 1024) {
-      const long long g = g0 + tid;
-      int freeq = 0;
-      long long q = 0;
-      if (g < G) {
-        q = (g / ncol) * s * Wq + (g % ncol) * s;
-        freeq = ((bm[q >> 5] >> (q & 31)) & 1u) ? 0 : 1;
+    for (int pass = (n_uniform > 0 ? 0 : 1); pass < 2 && filled < N; ++pass) {
+      const long long ratio = npos / (pass == 0 ? n_uniform : N);
+      long long s = (long long)sqrt((double)ratio);
+      while (s * s > ratio) --s;
+      while ((s + 1) * (s + 1) <= ratio) ++s;
+      if (s < 1) s = 1;
+      const long long ncol = (Wq + s - 1) / s, nrow = (Hq + s - 1) / s;
+      const long long G = ncol * nrow;
+      for (long long g0 = 0; g0 < G && filled < N; g0 += 1024) {
+        const long long g = g0 + tid;
+        int freeq = 0;
+        long long q = 0;
+        if (g < G) {
+          q = (g / ncol) * s * Wq + (g % ncol) * s;
+          freeq = ((bm[q >> 5] >> (q & 31)) & 1u) ? 0 : 1;
+        }
+        const int off = block_exclusive_scan(freeq, warp_sums, &s_total);
+        if (freeq && filled + off < N) {
+          kf[filled + off] = (int32_t)q;
+          atomicOr(bm + (q >> 5), 1u << (q & 31));  // the second grid skips it
+        }
+        filled += s_total;  // every thread sees the same s_total
+        __syncthreads();
       }
-      const int off = block_exclusive_scan(freeq, warp_sums, &s_total);
-      if (freeq && filled + off < N) kf[filled + off] = (int32_t)q;
-      filled += s_total;  // every thread sees the same s_total
-      __syncthreads();
+      filled = min(filled, N);
     }
   }
   if (tid == 0) {
@@ -379,8 +389,8 @@ SelectWs select_ws_layout(const glr_images& im, int N) {
   return w;
 }
 
-glr_status launch_select(const float* x, const glr_images& im, float th, int N, int32_t* keys, int32_t* n_found,
-                         int32_t* n_corner, char* ws, const SelectWs& L, cudaStream_t s) {
+glr_status launch_select(const float* x, const glr_images& im, float th, int N, int n_uniform, int32_t* keys,
+                         int32_t* n_found, int32_t* n_corner, char* ws, const SelectWs& L, cudaStream_t s) {
   const long long HW = (long long)im.H * im.W;
   const long long cap = (long long)((im.H + 1) / 2) * ((im.W + 1) / 2);
   uint8_t* S = reinterpret_cast<uint8_t*>(ws + L.S_off);
@@ -404,7 +414,7 @@ glr_status launch_select(const float* x, const glr_images& im, float th, int N, 
       return GLR_ECUDA;
     attr_done = true;
   }
-  GLR_LAUNCH("k_topn", s, k_topn<<<im.n_img, 1024, smem, s>>>(cand, cnt, cap, im.H, im.W, im.P, N, pow2, bm, keys, n_found, n_corner));
+  GLR_LAUNCH("k_topn", s, k_topn<<<im.n_img, 1024, smem, s>>>(cand, cnt, cap, im.H, im.W, im.P, N, n_uniform, pow2, bm, keys, n_found, n_corner));
   return GLR_OK;
 }
 

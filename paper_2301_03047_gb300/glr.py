@@ -83,8 +83,10 @@ def _ws(ws: torch.Tensor) -> tuple[int, int]:
     return p + off, ws.numel() - off
 
 
-def select_keys(x, P, N, edge_th=0.1, *, keys=None, n_found=None, n_corner=None, ws=None, stream=None):
-    """Corner-based key selection (Section 2, Eq. 2-3).  x: [n_img][C][H][W] float32."""
+def select_keys(x, P, N, edge_th=0.1, *, n_uniform=0, keys=None, n_found=None, n_corner=None, ws=None,
+                stream=None):
+    """Corner-based key selection (Section 2, Eq. 2-3).  x: [n_img][C][H][W] float32.
+    n_uniform > 0: corner + uniform mix (at most N - n_uniform corners, then a uniform grid)."""
     lib = L.load()
     im = images_of(x, P)
     dev = x.device
@@ -97,8 +99,9 @@ def select_keys(x, P, N, edge_th=0.1, *, keys=None, n_found=None, n_corner=None,
     if ws is None:
         ws = workspace(L.GLR_OP_SELECT, im, N, 1, None, dev)
     wp, wn = _ws(ws)
-    _check("glr_select_keys", lib.glr_select_keys(_ptr(x), ctypes.byref(im), float(edge_th), int(N), _ptr(keys),
-                                                  _ptr(n_found), _ptr(n_corner), wp, wn, _stream(stream)))
+    _check("glr_select_keys_mixed", lib.glr_select_keys_mixed(_ptr(x), ctypes.byref(im), float(edge_th), int(N),
+                                                              int(n_uniform), _ptr(keys), _ptr(n_found),
+                                                              _ptr(n_corner), wp, wn, _stream(stream)))
     return keys, n_found, n_corner
 
 
@@ -226,6 +229,23 @@ def gap_step(y, masks, v=None, *, accelerate=False, y_acc=None, out=None, stream
     return out
 
 
+def admm_sci_step(y, masks, z, x, u, rho, *, x_out=None, w_out=None, stream=None):
+    """ADMM step for y = sum_t A_t x_t after the denoiser: u += x - z; x' = w + Phi^T((y - Phi w)/(R + rho)),
+    w = z - u; returns (x', x' + u).  y: [G][H][W]; masks: [T][H][W] or [G][T][H][W]; z, x, u: [G][T][H][W]."""
+    lib = L.load()
+    G, H, W = y.shape
+    T = z.shape[1]
+    mstride = 0 if masks.dim() == 3 else T * H * W
+    if x_out is None:
+        x_out = torch.empty_like(z)
+    if w_out is None:
+        w_out = torch.empty_like(z)
+    _check("glr_admm_sci_step", lib.glr_admm_sci_step(_ptr(y), _ptr(masks), int(mstride), _ptr(z), _ptr(x), _ptr(u),
+                                                      G, T, H, W, float(rho), _ptr(x_out), _ptr(w_out),
+                                                      _stream(stream)))
+    return x_out, w_out
+
+
 def poll_status(ws, reset=False, stream=None):
     """(bits, [cand_overflow, svd_noconv, sweeps, groups, cand_appends, compactions]) of the last call that used ws."""
     lib = L.load()
@@ -281,9 +301,10 @@ class GlrDenoiser:
     """Select -> match -> low-rank -> aggregate on fixed-size images, with preallocated buffers."""
 
     def __init__(self, shape: GlrShape, mode: str = "bf16", edge_th: float = 0.1, k_over: int = 0, splits: int = 0,
-                 device="cuda", cap: int = 0, epi_batch: int = 0, complex_: bool = False):
+                 device="cuda", cap: int = 0, epi_batch: int = 0, complex_: bool = False, n_uniform: int = 0):
         s = shape
         self.shape, self.mode, self.edge_th, self.complex_ = s, mode, edge_th, complex_
+        self.n_uniform = n_uniform
         self.opts = match_opts(mode, k_over, splits, cap, None, epi_batch, edge_th)
         self.k_over, self.splits, self.cap, self.epi_batch = k_over, splits, cap, epi_batch
         im = images(s.n_img, s.C, s.H, s.W, s.P)
@@ -304,8 +325,8 @@ class GlrDenoiser:
     def __call__(self, x: torch.Tensor, sigma_w: float, c_wnnm: float, out: torch.Tensor | None = None,
                  stream=None) -> torch.Tensor:
         s = self.shape
-        select_keys(x, s.P, s.N, self.edge_th, keys=self.keys, n_found=self.n_found, n_corner=self.n_corner,
-                    ws=self.ws_select, stream=stream)
+        select_keys(x, s.P, s.N, self.edge_th, n_uniform=self.n_uniform, keys=self.keys, n_found=self.n_found,
+                    n_corner=self.n_corner, ws=self.ws_select, stream=stream)
         match_topk(x, s.P, self.keys, self.n_found, s.K, self.mode, k_over=self.k_over, splits=self.splits,
                    cap=self.cap, epi_batch=self.epi_batch, edge_th=self.edge_th, idx=self.idx, dist=self.dist,
                    ws=self.ws_match, stream=stream)
@@ -318,13 +339,20 @@ class SciReconstructor:
     """GAP + GLR for one video snapshot y = sum_t M_t x_t (Eq. 6); frames are the images."""
 
     def __init__(self, T, H, W, P, N, K, mode="bf16", edge_th=0.1, accelerate=False, k_over=0, splits=0,
-                 device="cuda", cap=0, epi_batch=0):
+                 device="cuda", cap=0, epi_batch=0, admm_rho=0.0, n_uniform=0):
+        """admm_rho > 0: ADMM (z = D(x + u), u += x - z, x = the data step) instead of GAP;
+        n_uniform > 0: corner + uniform key mix."""
         self.T, self.H, self.W = T, H, W
-        self.den = GlrDenoiser(GlrShape(T, 1, H, W, P, N, K), mode, edge_th, k_over, splits, device, cap, epi_batch)
+        self.den = GlrDenoiser(GlrShape(T, 1, H, W, P, N, K), mode, edge_th, k_over, splits, device, cap, epi_batch,
+                               n_uniform=n_uniform)
         self.accelerate = accelerate
+        self.rho = admm_rho
         self.x = torch.empty((1, T, H, W), dtype=torch.float32, device=device)
         self.v = torch.empty_like(self.x)
         self.y_acc = torch.empty((1, H, W), dtype=torch.float32, device=device)
+        if admm_rho > 0:
+            self.u = torch.zeros_like(self.x)
+            self.w = torch.empty_like(self.x)
 
     def start(self, y: torch.Tensor, masks: torch.Tensor) -> torch.Tensor:
         """x0 = Phi^T(y/R)."""
@@ -332,10 +360,19 @@ class SciReconstructor:
         if self.accelerate:
             self.y_acc.copy_(self.y)
         gap_step(self.y, masks, None, out=self.x)
+        if self.rho > 0:
+            self.u.zero_()
+            self.w.copy_(self.x)
         return self.x
 
     def step(self, sigma_w: float, c_wnnm: float, stream=None) -> torch.Tensor:
-        """One GAP iteration: v = D(x); x = project(v)."""
+        """One GAP iteration: v = D(x); x = project(v).  ADMM: z = D(x + u); u += x - z; x = data step."""
+        if self.rho > 0:
+            wi = self.w.view(self.T, 1, self.H, self.W)
+            self.den(wi, sigma_w, c_wnnm, out=self.v.view(self.T, 1, self.H, self.W), stream=stream)
+            admm_sci_step(self.y, self.masks, self.v, self.x, self.u, self.rho, x_out=self.x, w_out=self.w,
+                          stream=stream)
+            return self.x
         xi = self.x.view(self.T, 1, self.H, self.W)
         self.den(xi, sigma_w, c_wnnm, out=self.v.view(self.T, 1, self.H, self.W), stream=stream)
         gap_step(self.y, self.masks, self.v, accelerate=self.accelerate, y_acc=self.y_acc if self.accelerate else None,
@@ -344,6 +381,8 @@ class SciReconstructor:
 
     def _state(self):
         """Tensors a step reads and writes (saved around the capture's warm-up step)."""
+        if self.rho > 0:
+            return [self.x, self.u, self.w]
         return [self.x, self.y_acc] if self.accelerate else [self.x]
 
     def capture(self, sigmas, c_wnnm: float) -> None:
