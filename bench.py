@@ -913,6 +913,59 @@ def run_msfa(args, cfg, dev, dist) -> None:
     print(json.dumps(line))
 
 
+def run_ablation(args) -> None:
+    """Matching strategies of the paper's comparison of global and block matching:
+    GM (global, corner keys; BF16 and FP32 forms) against block matching in a
+    +-20 window with uniform (BM-U), corner (BM-C) and half-and-half (BM-C-U) keys.
+    Reports, per strategy, GAP iterations/s, the PSNR after the full schedule and the
+    recall of the exact global top-K on the start image."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from oracle import glr_oracle as O  # PSNR bookkeeping only
+    from paper_2301_03047_gb300 import glr, synth
+
+    cfg = workload(args.workload)
+    prob = synth.sci_problem(cfg)
+    dev = torch.device("cuda", 0)
+    y = torch.from_numpy(prob.y).to(dev)
+    masks = torch.from_numpy(prob.masks).to(dev)
+    sched = cfg.sigma_schedule()
+    strategies = [("GM-bf16", "bf16", 0), ("GM-fp32", "fp32", 0), ("BM-U", "window", cfg.N),
+                  ("BM-C", "window", 0), ("BM-C-U", "window", cfg.N // 2)]
+    x0 = glr.gap_step(y[None], masks, None).view(cfg.T, 1, cfg.H, cfg.W).contiguous()
+    out = {}
+    for name, mode, nu in strategies:
+        k0, n0, _ = glr.select_keys(x0, cfg.P, cfg.N, cfg.edge_th, n_uniform=nu)
+        exact, _ = glr.match_topk(x0, cfg.P, k0, n0, cfg.K, "fp32")
+        got, _ = glr.match_topk(x0, cfg.P, k0, n0, cfg.K, mode, window=20)
+        e, g = exact.cpu().numpy(), got.cpu().numpy()
+        hits = sum(len(set(e[f, i].tolist()) & set(g[f, i].tolist())) for f in range(cfg.T) for i in range(cfg.N))
+        rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=mode, edge_th=cfg.edge_th,
+                                   device=dev, n_uniform=nu, window=20)
+        rec.start(y, masks)
+        rec.step(sched[0], cfg.c_wnnm)  # warm-up (library set-up)
+        rec.start(y, masks)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for s in sched:
+            rec.step(s, cfg.c_wnnm)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / len(sched)
+        out[name] = {"iter_per_s": round(1e3 / ms, 3), "ms_per_iter": round(ms, 3),
+                     "psnr_db": round(O.psnr_framewise(rec.x.cpu().numpy()[0], prob.truth), 3),
+                     "recall_of_global_topk": round(hits / (cfg.T * cfg.N * cfg.K), 4), "n_uniform": nu}
+        del rec
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "matching-strategy comparison (GM vs block matching)", "workload": cfg.name,
+                      "iterations": len(sched), "window": 20, "strategies": out}))
+
+
 def run_reference(args) -> None:
     ws, rank, _ = dist_info()
     if rank != 0:
@@ -976,6 +1029,8 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--ablation", action="store_true",
+                    help="print the matching-strategy comparison (GM vs block matching) instead of the bench line")
     ap.add_argument("--match-schedule", default="",
                     help="k_over,splits,cap,epi_batch: a fixed matching schedule instead of the autotuner's")
     args = ap.parse_args()
@@ -983,6 +1038,8 @@ def main() -> None:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.ablation:
+        run_ablation(args)
     else:
         run_glr(args)
 

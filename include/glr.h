@@ -77,9 +77,12 @@ enum {
   GLR_MATCH_BF16 = 1,   /* chosen form: BF16 tcgen05.mma into TMEM, FP32 accumulate, FP32 re-rank */
   GLR_MATCH_LEARNED = 2, /* learned proposal: k_over candidates by the 16-dim encoder embedding
                            (BF16 tcgen05 contraction), then the exact FP32 re-rank on patches */
-  GLR_MATCH_EDGE = 3     /* the paper's heat map (Eq. 8): binary edge patches (Eq. 6, threshold
+  GLR_MATCH_EDGE = 3,    /* the paper's heat map (Eq. 8): binary edge patches (Eq. 6, threshold
                            edge_th) correlated over the four maps and all channels on the tensor
                            cores (0/1 operands: exact); the K largest values, ties by smaller id */
+  GLR_MATCH_WINDOW = 4   /* block matching in a local window (Eq. 1 restricted to positions within
+                           `window` rows and columns of the key, the baseline the paper's global
+                           matching replaces): exact FP32 distances, the K smallest */
 };
 
 /* Number of floats of an encoder parameter buffer: W1[64][64], b1[64], W2[16][64], b2[16]. */
@@ -97,6 +100,10 @@ typedef struct glr_match_opts {
   int32_t epi_batch;    /* tensor-core epilogue: 32-column chunks read from tensor memory per
                            visit, 2 or 4 (0 = 4) */
   float edge_th;        /* GLR_MATCH_EDGE: the threshold th of Eq. 7 on Sobel output (>= 0) */
+  int32_t window;       /* GLR_MATCH_WINDOW: half-width w of the search window, 1 <= w <= 22:
+                           the (2w+1)^2 positions centred on the key, shifted inside the
+                           position grid at its borders; K <= (2w+1)^2 */
+  int32_t reserved;
 } glr_match_opts;
 
 /* Operation codes for glr_workspace_size. */
@@ -136,9 +143,9 @@ glr_status glr_select_keys(const float* x, const glr_images* im, float edge_th, 
  * Corner + uniform exemplar mixes (Section 3: the CACTI experiments add uniformly
  * selected exemplars to the corner-based ones; the matching-strategy comparison
  * uses as many uniform as corner exemplars).  At most N - n_uniform corners (in
- * the rank order above), then the row-major grid of stride
- * max(1, isqrt(Hq*Wq / n_uniform)) up to N keys, skipping chosen positions, then
- * the stride-isqrt(Hq*Wq/N) grid if keys are still missing.  0 <= n_uniform <= N;
+ * the rank order above), then the row-major grid of the smallest stride s with
+ * ceil(Hq/s) ceil(Wq/s) <= n_uniform (a grid over the whole image), skipping
+ * chosen positions, then the stride-isqrt(Hq*Wq/N) grid up to N keys.  0 <= n_uniform <= N;
  * n_uniform = 0 is glr_select_keys.  Same workspace as glr_select_keys.
  */
 glr_status glr_select_keys_mixed(const float* x, const glr_images* im, float edge_th, int32_t N,

@@ -55,10 +55,14 @@ A10 Aggregation weight 1; pixels no patch covers keep the input value.
 A12 Plain GAP (accelerated is a flag); R = sum_t A_t^2 with R = 0 -> 1;
     x0 = Phi^T (y / R).
 A19 Corner + uniform keys (Section 3, CACTI and the matching-strategy
-    comparison): at most N - n_uniform corners, then a uniform grid of stride
-    isqrt(Hq*Wq // n_uniform) in row-major order, skipping chosen positions.
+    comparison): at most N - n_uniform corners, then the uniform grid of the
+    smallest stride s with ceil(Hq/s) ceil(Wq/s) <= n_uniform (so the grid covers
+    the image) in row-major order, skipping chosen positions.
 A20 ADMM for y = Phi x (the paper uses GAP or ADMM): scaled form z = D(x + u),
     u = u + x - z, x = w + Phi^T((y - Phi w)/(R + rho)) with w = z - u.
+A21 Block matching baseline: a (2w+1) x (2w+1) window of positions centred on
+    the key, shifted inside the position grid at its borders (so every key sees
+    (2w+1)^2 candidates); K smallest distances, ties by smaller id.
 A18 The paper's own matching score (the heat map of Eq. 8, ``edge_match_topk``):
     Conv2d is a correlation summed over the four maps and the C channels (the
     per-channel maps, not the OR-ed ones of key selection); a larger value is a
@@ -186,8 +190,9 @@ def select_keys(x: np.ndarray, P: int, N: int, th: float, n_uniform: int = 0) ->
 
     n_uniform > 0 mixes in uniformly placed keys (reading A19, the corner +
     uniform selections of Section 3): at most N - n_uniform corners, then the
-    row-major grid of stride max(1, isqrt(Hq*Wq // n_uniform)) up to N keys,
-    skipping chosen positions (then the reading-A5 grid if still short).
+    row-major grid of the smallest stride s with ceil(Hq/s) ceil(Wq/s) <= n_uniform
+    (it covers the whole image), skipping chosen positions, then the reading-A5
+    grid up to N keys.
     Returns (keys int32[N] position ids in rank order, number of corner keys kept).
     """
     C, H, W = x.shape
@@ -215,7 +220,9 @@ def select_keys(x: np.ndarray, P: int, N: int, th: float, n_uniform: int = 0) ->
             chosen.append(q)
     n_corner = len(chosen)
     if n_uniform > 0:
-        su = max(1, math.isqrt((Hq * Wq) // n_uniform))
+        su = 1
+        while -(-Hq // su) * -(-Wq // su) > n_uniform:
+            su += 1
         for gr in range(0, Hq, su):
             for gc in range(0, Wq, su):
                 if len(chosen) == N:
@@ -313,6 +320,30 @@ def edge_match_topk(x: np.ndarray, P: int, keys: np.ndarray, K: int, th: float):
         idx[i] = order
         val[i] = h[order]
     return idx, val
+
+
+def window_match_topk(x: np.ndarray, P: int, keys: np.ndarray, K: int, w: int, Q: np.ndarray | None = None):
+    """Block matching (Eq. 1 in a local window, the baseline global matching replaces;
+    reading A21): the (2w+1)^2 positions centred on the key, the window shifted inside
+    the position grid at its borders; the K smallest distances, ties by smaller id."""
+    C, H, W = x.shape
+    Hq, Wq = H - P + 1, W - P + 1
+    if Q is None:
+        Q = patch_matrix(x, P)
+    wl = 2 * w + 1
+    idx = np.empty((len(keys), K), dtype=np.int32)
+    dist = np.empty((len(keys), K))
+    for i, k in enumerate(keys):
+        kr, kc = divmod(int(k), Wq)
+        r0 = min(max(kr - w, 0), Hq - wl)
+        c0 = min(max(kc - w, 0), Wq - wl)
+        cand = np.array([(r0 + a) * Wq + c0 + b for a in range(wl) for b in range(wl)])
+        diff = Q[cand] - Q[int(k)]
+        dd = np.einsum("ij,ij->i", diff, diff)
+        order = np.lexsort((cand, dd))[:K]
+        idx[i] = cand[order]
+        dist[i] = dd[order]
+    return idx, dist
 
 
 def all_distances(x: np.ndarray, P: int, key: int, Q: np.ndarray | None = None) -> np.ndarray:

@@ -16,7 +16,7 @@ c_uint32_p = ctypes.POINTER(ctypes.c_uint32)
 
 GLR_OK, GLR_EINVAL, GLR_ECUDA, GLR_ENOMEM, GLR_ETIMEDOUT, GLR_ENOTSUP, GLR_EDEVICE, GLR_ETOOBIG = range(8)
 GLR_DEV_TIMEOUT, GLR_DEV_NONFINITE, GLR_DEV_SVD_NOCONV, GLR_DEV_CAND_OVERFLOW, GLR_DEV_BAD_INDEX = 1, 2, 4, 8, 16
-GLR_MATCH_FP32, GLR_MATCH_BF16, GLR_MATCH_LEARNED, GLR_MATCH_EDGE = 0, 1, 2, 3
+GLR_MATCH_FP32, GLR_MATCH_BF16, GLR_MATCH_LEARNED, GLR_MATCH_EDGE, GLR_MATCH_WINDOW = 0, 1, 2, 3, 4
 GLR_OP_SELECT, GLR_OP_MATCH, GLR_OP_LOWRANK, GLR_OP_AGGREGATE, GLR_OP_ENCODER, GLR_OP_ADMM = 1, 2, 3, 4, 5, 6
 GLR_ENCODER_PARAMS = 5200
 
@@ -27,7 +27,7 @@ class GlrImages(ctypes.Structure):
 
 class GlrMatchOpts(ctypes.Structure):
     _fields_ = [("mode", c_int32), ("k_over", c_int32), ("splits", c_int32), ("cap", c_int32), ("encoder", c_void_p),
-                ("epi_batch", c_int32), ("edge_th", c_float)]
+                ("epi_batch", c_int32), ("edge_th", c_float), ("window", c_int32), ("reserved", c_int32)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/glr.h

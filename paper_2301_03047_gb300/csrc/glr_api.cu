@@ -191,8 +191,14 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
   if (N < 1 || K < 1 || K > npos) return GLR_EINVAL;
   if (K > 128) return GLR_ENOTSUP;
   if (opts && opts->mode != GLR_MATCH_FP32 && opts->mode != GLR_MATCH_BF16 && opts->mode != GLR_MATCH_LEARNED &&
-      opts->mode != GLR_MATCH_EDGE)
+      opts->mode != GLR_MATCH_EDGE && opts->mode != GLR_MATCH_WINDOW)
     return GLR_EINVAL;
+  if (opts && opts->mode == GLR_MATCH_WINDOW) {
+    if (opts->window < 1 || opts->window > 22) return GLR_EINVAL;
+    const int wl = 2 * opts->window + 1;
+    if (K > wl * wl || im->H - im->P + 1 < wl || im->W - im->P + 1 < wl) return GLR_EINVAL;
+    if (im->C * im->P * im->P > 640) return GLR_ENOTSUP;
+  }
   if (opts && opts->mode == GLR_MATCH_EDGE) {
     if (!(opts->edge_th >= 0.f)) return GLR_EINVAL;
     if (4 * im->C * im->P * im->P > 640) return GLR_ENOTSUP;

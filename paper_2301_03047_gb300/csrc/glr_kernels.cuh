@@ -36,6 +36,7 @@ struct MatchPlan {
   int dk;               // BF16 operand row length (elements)
   int nkc;              // 64-column chunks of patch values in a BF16 operand row (1 unless d > 74)
   float edge_th;        // GLR_MATCH_EDGE: threshold of the edge maps
+  int window;           // GLR_MATCH_WINDOW: half-width of the search window
   size_t edge_off;      // GLR_MATCH_EDGE: edge planes [n_img][4 C][H][W]
   int epi_batch;        // tensor-core epilogue: 32-column chunks read from TMEM per visit (2 or 4)
   long long npos_pad;   // BF16 position rows per image (pos_tiles * pos_tile)

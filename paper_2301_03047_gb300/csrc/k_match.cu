@@ -300,7 +300,9 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
     k_rerank(const float* __restrict__ x, const int32_t* __restrict__ keys, const int32_t* __restrict__ n_found,
              int n_img, int C, int H, int W, int P, int N, int Npad, int K, int streams_per_key, int cap_slots,
              int kp, int pow2, const uint2* __restrict__ bufs, const int* __restrict__ buf_cnt,
-             int exact_scores, float dist_scale, int32_t* __restrict__ idx, float* __restrict__ dist) {
+             int exact_scores, float dist_scale, int window, int32_t* __restrict__ idx, float* __restrict__ dist) {
+  // window > 0: the candidates are every position within `window` rows and columns
+  // of the key (block matching in a local window) instead of the stream buffers
   // exact_scores != 0: the stream scores are already exact (the heat map of Eq. 8 on
   // 0/1 operands); they are sorted as they are and dist = dist_scale * score
   extern __shared__ unsigned long long rr_smem[];
@@ -323,8 +325,15 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
     }
     // gather candidate ids
     int total = 0;
+    if (window > 0) {
+      // a (2w+1)^2 window centred on the key, shifted inside the position grid at its borders
+      const int Hq = H - P + 1, wl = 2 * window + 1;
+      const int r0 = min(max(kr - window, 0), Hq - wl), c0 = min(max(kc - window, 0), Wq - wl);
+      total = wl * wl;
+      for (int i = lane; i < total; i += 32) list[i] = (unsigned)((r0 + i / wl) * Wq + c0 + i % wl);
+    }
     const long long s0 = ((long long)f * Npad + k) * streams_per_key;
-    for (int sidx = 0; sidx < streams_per_key; ++sidx) {
+    for (int sidx = 0; window == 0 && sidx < streams_per_key; ++sidx) {
       const int n = min(buf_cnt[s0 + sidx], kp);
       const uint2* b = bufs + (s0 + sidx) * cap_slots;
       for (int i = lane; i < n; i += 32) {
@@ -463,6 +472,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   const bool edge = pl.mode == GLR_MATCH_EDGE;
   const bool tc = pl.mode == GLR_MATCH_BF16 || pl.mode == GLR_MATCH_LEARNED || edge;
   pl.edge_th = (o && edge) ? o->edge_th : 0.f;
+  pl.window = (o && pl.mode == GLR_MATCH_WINDOW) ? o->window : 0;
   pl.Kp = (o && o->k_over > 0) ? o->k_over : (pl.mode == GLR_MATCH_LEARNED ? std::max(256, K + 16) : K + 16);
   pl.Kp = std::max(pl.Kp, K);
   // a small compaction trigger publishes a first threshold early; each compaction keeps ~Kp + (cap - Kp) / 4
@@ -529,6 +539,23 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
   const long long npos = (long long)Hq * Wq;
   const bool edge = pl.mode == GLR_MATCH_EDGE;
   const bool tc = pl.mode == GLR_MATCH_BF16 || pl.mode == GLR_MATCH_LEARNED || edge;
+  if (pl.window > 0) {
+    // block matching in a local window: every candidate is scored exactly by the re-rank kernel
+    const int d0 = im.C * im.P * im.P;
+    const int dpad = (d0 + 31) & ~31;
+    int pow2 = 32;
+    const int nwin = (2 * pl.window + 1) * (2 * pl.window + 1);
+    while (pow2 < nwin) pow2 <<= 1;
+    const size_t smem = (size_t)RR_WARPS * pow2 * 8 + (size_t)RR_WARPS * (dpad + 256) * 4;
+    if (smem > 227 * 1024 || pow2 > kRerankMaxList) return GLR_ENOTSUP;
+    if (cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return GLR_ECUDA;
+    const long long nkeys = (long long)im.n_img * N;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, RR_WARPS), 152LL * 16));
+    GLR_LAUNCH("k_rerank", s, k_rerank<<<blocks, RR_WARPS * 32, smem, s>>>(x, keys, n_found, im.n_img, im.C, im.H, im.W, im.P, N, pl.Npad,
+                                                 pl.K, 0, 0, 0, pow2, nullptr, nullptr, 0, 1.f, pl.window, idx, dist));
+    return GLR_OK;
+  }
   // GLR_MATCH_EDGE: every later step sees the 4 C binary edge planes as the image
   glr_images ime = im;
   if (edge) ime.C = 4 * im.C;
@@ -622,7 +649,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, RR_WARPS), 152LL * 16));
     GLR_LAUNCH("k_rerank", s, k_rerank<<<blocks, RR_WARPS * 32, smem, s>>>(x, keys, n_found, im.n_img, im.C, im.H, im.W, im.P, N, pl.Npad,
                                                  pl.K, pl.streams_per_key, pl.cap + 32, pl.Kp, pow2, bufs, bufcnt,
-                                                 edge ? 1 : 0, edge ? -0.5f : 1.f, idx, dist));
+                                                 edge ? 1 : 0, edge ? -0.5f : 1.f, 0, idx, dist));
   }
   return GLR_OK;
 }

@@ -339,11 +339,17 @@ __global__ void __launch_bounds__(1024) k_topn(const unsigned long long* __restr
     __syncthreads();
     int filled = n_kept;
     for (int pass = (n_uniform > 0 ? 0 : 1); pass < 2 && filled < N; ++pass) {
-      const long long ratio = npos / (pass == 0 ? n_uniform : N);
-      long long s = (long long)sqrt((double)ratio);
-      while (s * s > ratio) --s;
-      while ((s + 1) * (s + 1) <= ratio) ++s;
-      if (s < 1) s = 1;
+      long long s;
+      if (pass == 0) {  // the smallest stride whose grid has at most n_uniform points
+        s = 1;
+        while (((Hq + s - 1) / s) * ((Wq + s - 1) / s) > n_uniform) ++s;
+      } else {
+        const long long ratio = npos / N;
+        s = (long long)sqrt((double)ratio);
+        while (s * s > ratio) --s;
+        while ((s + 1) * (s + 1) <= ratio) ++s;
+        if (s < 1) s = 1;
+      }
       const long long ncol = (Wq + s - 1) / s, nrow = (Hq + s - 1) / s;
       const long long G = ncol * nrow;
       for (long long g0 = 0; g0 < G && filled < N; g0 += 1024) {

@@ -52,15 +52,18 @@ def images_of(x: torch.Tensor, P: int) -> L.GlrImages:
 
 
 def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0, cap: int = 0,
-               encoder: torch.Tensor | None = None, epi_batch: int = 0, edge_th: float = 0.1) -> L.GlrMatchOpts:
-    """mode: "fp32" (plain), "bf16" (chosen), "learned", or "edge" (the paper's heat map of Eq. 8)."""
+               encoder: torch.Tensor | None = None, epi_batch: int = 0, edge_th: float = 0.1,
+               window: int = 20) -> L.GlrMatchOpts:
+    """mode: "fp32" (plain), "bf16" (chosen), "learned", "edge" (the paper's heat map of Eq. 8),
+    or "window" (block matching within +-window of the key)."""
     m = {"fp32": L.GLR_MATCH_FP32, "bf16": L.GLR_MATCH_BF16, "learned": L.GLR_MATCH_LEARNED,
-         "edge": L.GLR_MATCH_EDGE}.get(mode, mode)
+         "edge": L.GLR_MATCH_EDGE, "window": L.GLR_MATCH_WINDOW}.get(mode, mode)
     o = L.GlrMatchOpts()
     o.mode, o.k_over, o.splits, o.cap = int(m), int(k_over), int(splits), int(cap)
     o.encoder = _ptr(encoder) if encoder is not None else None
     o.epi_batch = int(epi_batch)
     o.edge_th = float(edge_th)
+    o.window = int(window)
     return o
 
 
@@ -106,13 +109,13 @@ def select_keys(x, P, N, edge_th=0.1, *, n_uniform=0, keys=None, n_found=None, n
 
 
 def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, cap=0, encoder=None, epi_batch=0,
-               edge_th=0.1, idx=None, dist=None, ws=None, stream=None):
+               edge_th=0.1, window=20, idx=None, dist=None, ws=None, stream=None):
     """Global matching with a fused running top-K (Eq. 1 over the whole image as a contraction).
     mode "edge": the paper's heat map (Eq. 8); dist then holds the heat-map values (descending)."""
     lib = L.load()
     im = images_of(x, P)
     N = keys.shape[1]
-    o = match_opts(mode, k_over, splits, cap, encoder, epi_batch, edge_th)
+    o = match_opts(mode, k_over, splits, cap, encoder, epi_batch, edge_th, window)
     dev = x.device
     if idx is None:
         idx = torch.empty((x.shape[0], N, K), dtype=torch.int32, device=dev)
@@ -301,11 +304,12 @@ class GlrDenoiser:
     """Select -> match -> low-rank -> aggregate on fixed-size images, with preallocated buffers."""
 
     def __init__(self, shape: GlrShape, mode: str = "bf16", edge_th: float = 0.1, k_over: int = 0, splits: int = 0,
-                 device="cuda", cap: int = 0, epi_batch: int = 0, complex_: bool = False, n_uniform: int = 0):
+                 device="cuda", cap: int = 0, epi_batch: int = 0, complex_: bool = False, n_uniform: int = 0,
+                 window: int = 20):
         s = shape
         self.shape, self.mode, self.edge_th, self.complex_ = s, mode, edge_th, complex_
-        self.n_uniform = n_uniform
-        self.opts = match_opts(mode, k_over, splits, cap, None, epi_batch, edge_th)
+        self.n_uniform, self.window = n_uniform, window
+        self.opts = match_opts(mode, k_over, splits, cap, None, epi_batch, edge_th, window)
         self.k_over, self.splits, self.cap, self.epi_batch = k_over, splits, cap, epi_batch
         im = images(s.n_img, s.C, s.H, s.W, s.P)
         dev = torch.device(device)
@@ -328,8 +332,8 @@ class GlrDenoiser:
         select_keys(x, s.P, s.N, self.edge_th, n_uniform=self.n_uniform, keys=self.keys, n_found=self.n_found,
                     n_corner=self.n_corner, ws=self.ws_select, stream=stream)
         match_topk(x, s.P, self.keys, self.n_found, s.K, self.mode, k_over=self.k_over, splits=self.splits,
-                   cap=self.cap, epi_batch=self.epi_batch, edge_th=self.edge_th, idx=self.idx, dist=self.dist,
-                   ws=self.ws_match, stream=stream)
+                   cap=self.cap, epi_batch=self.epi_batch, edge_th=self.edge_th, window=self.window, idx=self.idx,
+                   dist=self.dist, ws=self.ws_match, stream=stream)
         lowrank_groups(x, s.P, self.idx, self.n_found, sigma_w, c_wnnm, groups=self.groups, rank=self.rank,
                        ws=self.ws_lowrank, stream=stream, complex_=self.complex_)
         return aggregate(self.groups, self.idx, self.n_found, x, s.P, out=out, ws=self.ws_agg, stream=stream)
@@ -339,12 +343,12 @@ class SciReconstructor:
     """GAP + GLR for one video snapshot y = sum_t M_t x_t (Eq. 6); frames are the images."""
 
     def __init__(self, T, H, W, P, N, K, mode="bf16", edge_th=0.1, accelerate=False, k_over=0, splits=0,
-                 device="cuda", cap=0, epi_batch=0, admm_rho=0.0, n_uniform=0):
+                 device="cuda", cap=0, epi_batch=0, admm_rho=0.0, n_uniform=0, window=20):
         """admm_rho > 0: ADMM (z = D(x + u), u += x - z, x = the data step) instead of GAP;
         n_uniform > 0: corner + uniform key mix."""
         self.T, self.H, self.W = T, H, W
         self.den = GlrDenoiser(GlrShape(T, 1, H, W, P, N, K), mode, edge_th, k_over, splits, device, cap, epi_batch,
-                               n_uniform=n_uniform)
+                               n_uniform=n_uniform, window=window)
         self.accelerate = accelerate
         self.rho = admm_rho
         self.x = torch.empty((1, T, H, W), dtype=torch.float32, device=device)

@@ -75,3 +75,26 @@ def test_admm_reconstruction_step_tracks_oracle():
         xn, un, wn = O.admm_sci_step(prob.y, prob.masks, z_gpu, x_prev, u_prev, 0.5)
         np.testing.assert_allclose(rec.x.cpu().numpy()[0], xn, rtol=1e-4, atol=1e-5)
         np.testing.assert_allclose(rec.w.cpu().numpy()[0], wn, rtol=1e-4, atol=1e-5)
+
+
+@pytest.mark.parametrize("case", [("w1", 2, 1, 50, 60, 8, 30, 16, 20), ("w2", 1, 3, 40, 44, 5, 25, 12, 6),
+                                  ("w3", 1, 1, 30, 30, 6, 20, 9, 1)])
+def test_window_matching_parity(case):
+    tag, F, C, H, W, P, N, K, w = case
+    rng = synth.rng_for(tag)
+    x = synth.textured_frames(rng, F * C, H, W).reshape(F, C, H, W)
+    npos = (H - P + 1) * (W - P + 1)
+    keys = np.stack([rng.choice(npos, size=N, replace=False) for _ in range(F)]).astype(np.int32)
+    keys[:, 0] = 0  # a corner key: its window is shifted inside the grid
+    idx, dist = glr.match_topk(cuda(x), P, cuda(keys, torch.int32), cuda(np.full(F, N, np.int32), torch.int32), K,
+                               "window", window=w)
+    torch.cuda.synchronize()
+    idx, dist = idx.cpu().numpy(), dist.cpu().numpy()
+    for f in range(F):
+        oi, od = O.window_match_topk(x[f], P, keys[f], K, w)
+        np.testing.assert_allclose(dist[f], od, rtol=2e-5, atol=2e-6)
+        for i in range(N):
+            for j in range(K):
+                sep = min(od[i, j + 1] - od[i, j] if j + 1 < K else np.inf, od[i, j] - od[i, j - 1] if j > 0 else np.inf)
+                if sep > 1e-4:
+                    assert idx[f, i, j] == oi[i, j], (f, i, j)

@@ -439,14 +439,14 @@ def test_edge_heatmap_flat_image_is_zero():
 # Corner + uniform keys (A19) and ADMM for SCI (A20)
 # ---------------------------------------------------------------------------
 def test_select_keys_uniform_mix_closed_form():
-    """On a flat image there are no corners: n_uniform keys come from the stride
-    isqrt(Hq*Wq // n_uniform) grid, the rest from the reading-A5 grid."""
+    """On a flat image there are no corners: the uniform keys are the grid of stride 9
+    (the smallest stride whose grid has at most 9 points on 26 x 26 positions:
+    stride 8 gives 4 x 4), which spans the whole image; the rest come from the A5 grid."""
     x = np.full((1, 30, 30), 0.5)
     P, N, nu = 5, 20, 9
     keys, nc = O.select_keys(x, P, N, 0.1, n_uniform=nu)
-    Hq = Wq = 26
-    su = int(np.sqrt(Hq * Wq // nu))  # 8
-    want = [r * Wq + c for r in range(0, Hq, su) for c in range(0, Wq, su)][:nu]
+    Wq = 26
+    want = [r * Wq + c for r in (0, 9, 18) for c in (0, 9, 18)]
     assert nc == 0 and list(keys[:nu]) == want and len(set(keys.tolist())) == N
 
 
@@ -474,3 +474,26 @@ def test_admm_sci_step_is_the_minimiser():
     xn, _, _ = O.admm_sci_step(y, A, z, x, u, 1e-12)
     R = (A * A).sum(0)
     assert np.allclose(((A * xn).sum(0) - y)[R > 0], 0, atol=1e-9)
+
+
+def test_window_matching_is_global_matching_restricted():
+    """Reading A21: the window result equals global matching on the window's positions
+    (brute force), and a window covering the whole grid gives the global result."""
+    rng = synth.rng_for("win")
+    x = rng.random((1, 14, 15))
+    P, K = 3, 6
+    Hq, Wq = 12, 13
+    keys = np.array([0, 40, 155], np.int32)
+    Q = O.patch_matrix(x, P)
+    idx, dist = O.window_match_topk(x, P, keys, K, 2, Q)
+    for i, k in enumerate(keys):
+        kr, kc = divmod(int(k), Wq)
+        r0, c0 = min(max(kr - 2, 0), Hq - 5), min(max(kc - 2, 0), Wq - 5)
+        cand = [(r, c) for r in range(r0, r0 + 5) for c in range(c0, c0 + 5)]
+        d = sorted((float(((Q[r * Wq + c] - Q[k]) ** 2).sum()), r * Wq + c) for r, c in cand)[:K]
+        assert [q for _, q in d] == list(idx[i]) and np.allclose([v for v, _ in d], dist[i])
+    xs = rng.random((1, 13, 13))  # an 11 x 11 position grid: w = 5 covers all of it
+    Qs = O.patch_matrix(xs, P)
+    gi, gd = O.match_topk(xs, P, np.array([37]), K, Qs)
+    wi, wd = O.window_match_topk(xs, P, np.array([37]), K, 5, Qs)
+    assert np.array_equal(gi, wi) and np.allclose(gd, wd)
