@@ -210,6 +210,7 @@ def kernel_hash(fname: str) -> str:
 KERNEL_FILE = {"k_match_tc": "k_match_tc.cu", "k_match_fp32": "k_match.cu", "k_jacobi_wnnm": "k_lowrank.cu",
                "k_jacobi_smem": "k_lowrank_wide.cu", "k_jacobi_wnnm_c": "k_lowrank.cu", "k_fft_rows": "k_fft.cu",
                "k_match_tc_w": "k_match_tc.cu", "k_gram_wnnm": "k_lowrank_wide.cu",
+               "k_jacobi_wnnm_fused": "k_lowrank.cu",
                "k_fft_cols": "k_fft.cu",
                "k_gather": "k_lowrank.cu", "k_scatter": "k_aggregate.cu", "k_gap_step": "k_gap.cu",
                "k_rerank": "k_match.cu"}
@@ -247,7 +248,7 @@ def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict, n
                    "peak_note": f"derived FP32 FMA peak 152x128x2 at {sm:.0f} MHz"}
         achieved = work / avg_s / 1e12
         unit_name = "pairs"
-    elif name in ("k_jacobi_wnnm", "k_jacobi_smem", "k_jacobi_wnnm_c"):
+    elif name in ("k_jacobi_wnnm", "k_jacobi_smem", "k_jacobi_wnnm_c", "k_jacobi_wnnm_fused"):
         units = T * N
         # complex columns: a complex multiply-add is 4 real ones on 2 real values, twice the real count per value
         work = units * sweeps_per_group * 6.0 * d * K * K * (2.0 if name == "k_jacobi_wnnm_c" else 1.0)
@@ -383,7 +384,7 @@ def run_glr(args) -> None:
             launches = glr.launch_count() - l0
             prof = glr.profile_collect()
             glr.profile_enable(False)
-            bits, cnt = glr.poll_status(rec.den.ws_lowrank)
+            bits, cnt = glr.poll_status(rec.den.ws_lowrank_status)
             sweeps = cnt[2] / max(cnt[3], 1)
             svd_noconv = cnt[1]
             _, mcnt = glr.poll_status(rec.den.ws_match)
@@ -619,7 +620,7 @@ def run_mri(args, cfg, dev, dist) -> None:
             launches = glr.launch_count() - l0
             prof = glr.profile_collect()
             glr.profile_enable(False)
-            _, cnt = glr.poll_status(rec.den.ws_lowrank)
+            _, cnt = glr.poll_status(rec.den.ws_lowrank_status)
             sweeps = cnt[2] / max(cnt[3], 1)
             _, mcnt = glr.poll_status(rec.den.ws_match)
             stream_stats = {"appends_per_key": round(mcnt[4] / cfg.N, 1),
@@ -813,7 +814,7 @@ def run_msfa(args, cfg, dev, dist) -> None:
             prof = glr.profile_collect()
             glr.profile_enable(False)
             rec.concurrent = True
-            sw_groups = [glr.poll_status(c["den"].ws_lowrank)[1] for c in rec.classes]
+            sw_groups = [glr.poll_status(c["den"].ws_lowrank_status)[1] for c in rec.classes]
             sweeps = sum(c[2] for c in sw_groups) / max(1, sum(c[3] for c in sw_groups))
             if not args.no_graph:
                 rec.capture(sched, cfg.c_wnnm)

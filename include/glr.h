@@ -233,6 +233,21 @@ glr_status glr_lowrank_groups(const float* x, const glr_images* im, const int32_
                               size_t ws_bytes, void* stream);
 
 /*
+ * Grouping, low-rank step and aggregation in one pass (the fused form of
+ * glr_lowrank_groups followed by glr_aggregate with x_in = x): each group's K
+ * patches are read from x, shrunk exactly as glr_lowrank_groups does, and the
+ * estimates are added straight into the aggregation sums, so no group buffer is
+ * written.  v_out [n_img][C][H][W] receives what glr_aggregate would, bit for bit
+ * (the sums are fixed point; the per-group arithmetic is the same code).
+ * rank (may be NULL) as in glr_lowrank_groups.  v_out must not alias x.
+ * Limits: d = C P^2 <= 64 and K <= 64 (GLR_ENOTSUP otherwise).
+ * Workspace: glr_workspace_size(GLR_OP_AGGREGATE, ...).
+ */
+glr_status glr_lowrank_aggregate(const float* x, const glr_images* im, const int32_t* idx,
+                                 const int32_t* n_found, int32_t N, int32_t K, float sigma_w, float c_wnnm,
+                                 float* v_out, int32_t* rank, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * The same step for a complex image (Section 3, MRI): x holds C == 2 planes
  * per image (real, imaginary), so a gathered column is the real half followed
  * by the imaginary half of a complex patch (m = P*P entries).  Y is the complex

@@ -282,6 +282,21 @@ glr_status glr_lowrank_groups(const float* x, const glr_images* im, const int32_
   return launch_wnnm_smem(*im, false, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
 }
 
+glr_status glr_lowrank_aggregate(const float* x, const glr_images* im, const int32_t* idx, const int32_t* n_found,
+                                 int32_t N, int32_t K, float sigma_w, float c_wnnm, float* v_out, int32_t* rank,
+                                 void* ws, size_t ws_bytes, void* stream) {
+  if (!images_ok(im) || !x || !idx || !n_found || !v_out) return GLR_EINVAL;
+  if (N < 1 || K < 1 || K > npos_of(im)) return GLR_EINVAL;
+  if (!(sigma_w >= 0.f) || !(c_wnnm >= 0.f)) return GLR_EINVAL;
+  if ((const void*)v_out == (const void*)x) return GLR_EINVAL;
+  if (im->C * im->P * im->P > 64 || K > 64) return GLR_ENOTSUP;
+  const AggWs L = agg_ws_layout(*im);
+  cudaStream_t s = (cudaStream_t)stream;
+  glr_status st = begin_ws(ws, ws_bytes, L.total, s);
+  if (st != GLR_OK) return st;
+  return launch_fused_lowrank_aggregate(x, *im, idx, n_found, N, K, sigma_w, c_wnnm, v_out, rank, (char*)ws, L, s);
+}
+
 glr_status glr_lowrank_groups_complex(const float* x, const glr_images* im, const int32_t* idx,
                                       const int32_t* n_found, int32_t N, int32_t K, float sigma_w, float c_wnnm,
                                       float* groups, int32_t* rank, void* ws, size_t ws_bytes, void* stream) {

@@ -83,6 +83,9 @@ glr_status launch_fft2(const float* in, float* out, int n_img, int H, int W, int
 glr_status launch_admm_step(const float* y, const float* mask, const float* z, const float* x, float* u, int n_img,
                             int H, int W, float rho, float* x_out, float* w_out, double* residual, double* res_acc,
                             cudaStream_t s);
+glr_status launch_wnnm_fused(const float* x, const glr_images& im, const int32_t* idx, const int32_t* n_found, int N,
+                             int K, float sigma_w, float c_wnnm, unsigned long long* num, int* cnt, int32_t* rank,
+                             StatusBlock* st, cudaStream_t s);
 glr_status launch_wnnm_complex_regs(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w,
                                    float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
 glr_status launch_wnnm(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
@@ -93,6 +96,9 @@ struct AggWs {
   size_t num_off, cnt_off, total;
 };
 AggWs agg_ws_layout(const glr_images& im);
+glr_status launch_fused_lowrank_aggregate(const float* x, const glr_images& im, const int32_t* idx,
+                                         const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
+                                         float* v_out, int32_t* rank, char* ws, const AggWs& L, cudaStream_t s);
 glr_status launch_aggregate(const float* groups, const int32_t* idx, const int32_t* n_found, const glr_images& im,
                             int N, int K, const float* x_in, float* v_out, char* ws, const AggWs& L,
                             cudaStream_t s);

@@ -96,6 +96,23 @@ AggWs agg_ws_layout(const glr_images& im) {
   return w;
 }
 
+glr_status launch_fused_lowrank_aggregate(const float* x, const glr_images& im, const int32_t* idx,
+                                         const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
+                                         float* v_out, int32_t* rank, char* ws, const AggWs& L, cudaStream_t s) {
+  unsigned long long* num = reinterpret_cast<unsigned long long*>(ws + L.num_off);
+  int* cnt = reinterpret_cast<int*>(ws + L.cnt_off);
+  const size_t num_b = (size_t)im.n_img * im.C * im.H * im.W * 8;
+  const size_t cnt_b = (size_t)im.n_img * (im.H - im.P + 1) * (im.W - im.P + 1) * 4;
+  if (cudaMemsetAsync(num, 0, num_b, s) != cudaSuccess) return GLR_ECUDA;
+  if (cudaMemsetAsync(cnt, 0, cnt_b, s) != cudaSuccess) return GLR_ECUDA;
+  const glr_status st = launch_wnnm_fused(x, im, idx, n_found, N, K, sigma_w, c_wnnm, num, cnt, rank,
+                                          reinterpret_cast<StatusBlock*>(ws), s);
+  if (st != GLR_OK) return st;
+  dim3 g((unsigned)ceil_div(im.W, AT), (unsigned)ceil_div(im.H, AT), (unsigned)im.n_img);
+  GLR_LAUNCH("k_normalise", s, k_normalise<<<g, 256, 0, s>>>(reinterpret_cast<const long long*>(num), cnt, x, v_out, im.C, im.H, im.W, im.P));
+  return GLR_OK;
+}
+
 glr_status launch_aggregate(const float* groups, const int32_t* idx, const int32_t* n_found, const glr_images& im,
                             int N, int K, const float* x_in, float* v_out, char* ws, const AggWs& L,
                             cudaStream_t s) {

@@ -169,6 +169,49 @@ __device__ __forceinline__ void store_col(const float (&a)[DMAX], float* __restr
   }
 }
 
+// Fused path: the group's columns are gathered from the image (R~_i x of Eq. 5)
+// and the estimates are added straight into the aggregation planes (64-bit fixed
+// point, as k_scatter does), so the group never goes to memory.
+struct FusedIO {
+  const float* x;
+  int C, H, W, P;
+  const int32_t* idx;        // [n_img][N][K]
+  unsigned long long* num;   // [n_img][C][H][W] fixed-point numerators
+  int* cnt;                  // [n_img][Hq][Wq] patch counts
+};
+
+template <int DMAX>
+__device__ __forceinline__ void gather_col(float (&a)[DMAX], const FusedIO& io, int f, int q, int d, bool own) {
+  const int Wq = io.W - io.P + 1, PP = io.P * io.P;
+  const int r0 = own ? q / Wq : 0, c0 = own ? q - (q / Wq) * Wq : 0;
+  const float* xf = io.x + (long long)f * io.C * io.H * io.W;
+#pragma unroll
+  for (int r = 0; r < DMAX; ++r) {
+    float v = 0.f;
+    if (own && r < d) {
+      const int ch = r / PP, rem = r - ch * PP, dr = rem / io.P, dc = rem - dr * io.P;
+      v = __ldg(xf + ((long long)ch * io.H + r0 + dr) * io.W + c0 + dc);
+    }
+    a[r] = v;
+  }
+}
+
+template <int DMAX>
+__device__ __forceinline__ void scatter_col(const float (&a)[DMAX], const FusedIO& io, int f, int q, int d) {
+  const int Wq = io.W - io.P + 1, Hq = io.H - io.P + 1, PP = io.P * io.P;
+  const int r0 = q / Wq, c0 = q - (q / Wq) * Wq;
+  unsigned long long* nf = io.num + (long long)f * io.C * io.H * io.W;
+#pragma unroll
+  for (int r = 0; r < DMAX; ++r)
+    if (r < d) {
+      const int ch = r / PP, rem = r - ch * PP, dr = rem / io.P, dc = rem - dr * io.P;
+      const float v = fminf(fmaxf(a[r], -1073741824.f), 1073741824.f);
+      atomicAdd(nf + ((long long)ch * io.H + r0 + dr) * io.W + c0 + dc,
+                (unsigned long long)__float2ll_rn(v * 4294967296.f));
+    }
+  atomicAdd(io.cnt + (long long)f * Hq * Wq + q, 1);
+}
+
 template <int DMAX>
 __device__ __forceinline__ float sq_norm(const float (&a)[DMAX]) {
   float p[4] = {0.f, 0.f, 0.f, 0.f};
@@ -178,12 +221,12 @@ __device__ __forceinline__ float sq_norm(const float (&a)[DMAX]) {
 }
 
 // DMAX rows per column, KMAX <= 64 columns, one warp per group, WARPS groups per CTA.
-template <int DMAX, int WARPS, bool CPLX>
+template <int DMAX, int WARPS, bool CPLX, bool FUSED>
 __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_img, int d, int N, int K,
                                                             const int32_t* __restrict__ n_found, float sigma_w,
                                                             float c_wnnm, float tol, int max_sweeps,
                                                             float* __restrict__ groups, int32_t* __restrict__ rank,
-                                                            StatusBlock* st) {
+                                                            StatusBlock* st, FusedIO io) {
   extern __shared__ float wsm[];  // [WARPS][64][DMAX]: active columns of W
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float* Ws = wsm + (size_t)wid * 64 * DMAX;
@@ -193,11 +236,24 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
   for (long long g = blockIdx.x * (long long)WARPS + wid; g < ngroups; g += (long long)gridDim.x * WARPS) {
     const int f = (int)(g / N), k = (int)(g - (long long)f * N);
     if (k >= min(n_found[f], N)) continue;
-    float* Y = groups + g * (long long)K * d;
+    float* Y = FUSED ? nullptr : groups + g * (long long)K * d;
     float a[DMAX], b[DMAX];
     const int ja = 2 * lane, jb = 2 * lane + 1;
-    load_col<DMAX, CPLX>(a, Y + (long long)ja * d, d, ja < K);
-    load_col<DMAX, CPLX>(b, Y + (long long)jb * d, d, live && jb < K);
+    int qa = -1, qb = -1;  // FUSED: patch positions of the two columns (-1: none / invalid)
+    if (FUSED) {
+      const int npos = (io.H - io.P + 1) * (io.W - io.P + 1);
+      if (ja < K) qa = io.idx[g * K + ja];
+      if (jb < K) qb = io.idx[g * K + jb];
+      if ((ja < K && (unsigned)qa >= (unsigned)npos) || (jb < K && (unsigned)qb >= (unsigned)npos))
+        status_set(st, GLR_DEV_BAD_INDEX);
+      if ((unsigned)qa >= (unsigned)npos) qa = -1;
+      if ((unsigned)qb >= (unsigned)npos) qb = -1;
+      gather_col<DMAX>(a, io, f, qa, d, qa >= 0);
+      gather_col<DMAX>(b, io, f, qb, d, qb >= 0);
+    } else {
+      load_col<DMAX, CPLX>(a, Y + (long long)ja * d, d, ja < K);
+      load_col<DMAX, CPLX>(b, Y + (long long)jb * d, d, live && jb < K);
+    }
     // non-finite input: leave the group unchanged and flag it
     float s0 = 0.f;
 #pragma unroll
@@ -338,7 +394,11 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
       const int j = 2 * lane + h;
       const bool own = live && j < K;
       // a / b are free once W is staged: reuse them as y_j and x^_j
-      load_col<DMAX, CPLX>(a, Y + (long long)j * d, d, own);
+      const int qj = h == 0 ? qa : qb;
+      if (FUSED)
+        gather_col<DMAX>(a, io, f, qj, d, own && qj >= 0);
+      else
+        load_col<DMAX, CPLX>(a, Y + (long long)j * d, d, own);
 #pragma unroll
       for (int r = 0; r < DMAX; ++r) b[r] = 0.f;
       for (int i = 0; i < rnk; ++i) {
@@ -371,7 +431,11 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
         }
       }
       __syncwarp();
-      if (own) store_col<DMAX, CPLX>(b, Y + (long long)j * d, d);
+      if (FUSED) {
+        if (own && qj >= 0) scatter_col<DMAX>(b, io, f, qj, d);
+      } else if (own) {
+        store_col<DMAX, CPLX>(b, Y + (long long)j * d, d);
+      }
     }
     __syncwarp();
   }
@@ -389,19 +453,20 @@ glr_status launch_gather(const float* x, const glr_images& im, const int32_t* id
   return GLR_OK;
 }
 
-template <int DMAX, bool CPLX>
+template <int DMAX, bool CPLX, bool FUSED = false>
 glr_status launch_wnnm_regs(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
-                            float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s, const char* name) {
+                            float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s, const char* name,
+                            FusedIO io = FusedIO{}) {
   constexpr int WARPS = 4;
   const int d = im.C * im.P * im.P;
   const size_t smem = (size_t)WARPS * 64 * DMAX * sizeof(float);
-  if (cudaFuncSetAttribute(k_jacobi_wnnm<DMAX, WARPS, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_jacobi_wnnm<DMAX, WARPS, CPLX, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return GLR_ECUDA;
   const long long ngroups = (long long)im.n_img * N;
   const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(ngroups, WARPS), 152LL * 64));
   const float tol = 1e-5f;
-  GLR_LAUNCH(name, s, (k_jacobi_wnnm<DMAX, WARPS, CPLX><<<blocks, WARPS * 32, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, 30, groups, rank, st)));
+  GLR_LAUNCH(name, s, (k_jacobi_wnnm<DMAX, WARPS, CPLX, FUSED><<<blocks, WARPS * 32, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, 30, groups, rank, st, io)));
   return GLR_OK;
 }
 
@@ -410,6 +475,16 @@ glr_status launch_wnnm(const glr_images& im, const int32_t* n_found, int N, int 
   const int d = im.C * im.P * im.P;
   if (d > 64 || K > 64 || K < 1) return GLR_ENOTSUP;
   return launch_wnnm_regs<64, false>(im, n_found, N, K, sigma_w, c_wnnm, groups, rank, st, s, "k_jacobi_wnnm");
+}
+
+glr_status launch_wnnm_fused(const float* x, const glr_images& im, const int32_t* idx, const int32_t* n_found, int N,
+                             int K, float sigma_w, float c_wnnm, unsigned long long* num, int* cnt, int32_t* rank,
+                             StatusBlock* st, cudaStream_t s) {
+  const int d = im.C * im.P * im.P;
+  if (d > 64 || K > 64 || K < 1) return GLR_ENOTSUP;
+  FusedIO io{x, im.C, im.H, im.W, im.P, idx, num, cnt};
+  return launch_wnnm_regs<64, false, true>(im, n_found, N, K, sigma_w, c_wnnm, nullptr, rank, st, s,
+                                           "k_jacobi_wnnm_fused", io);
 }
 
 glr_status launch_wnnm_complex_regs(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w,

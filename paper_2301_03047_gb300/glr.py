@@ -199,6 +199,22 @@ def admm_step(y, mask, z, x, u, rho, *, x_out=None, w_out=None, residual=None, w
     return x_out, w_out, residual
 
 
+def lowrank_aggregate(x, P, idx, n_found, sigma_w, c_wnnm, *, out=None, rank=None, ws=None, stream=None):
+    """Fused grouping + WNNM + aggregation (no group buffer); equals lowrank_groups then aggregate, bit for bit."""
+    lib = L.load()
+    im = images_of(x, P)
+    n, N, K = idx.shape
+    if out is None:
+        out = torch.empty_like(x)
+    if ws is None:
+        ws = workspace(L.GLR_OP_AGGREGATE, im, N, K, None, x.device)
+    wp, wn = _ws(ws)
+    _check("glr_lowrank_aggregate", lib.glr_lowrank_aggregate(_ptr(x), ctypes.byref(im), _ptr(idx), _ptr(n_found),
+                                                              int(N), int(K), float(sigma_w), float(c_wnnm),
+                                                              _ptr(out), _ptr(rank), wp, wn, _stream(stream)))
+    return out
+
+
 def aggregate(groups, idx, n_found, x, P, *, out=None, ws=None, stream=None):
     """Average the group estimates back into the image (weight 1; uncovered pixels keep x)."""
     lib = L.load()
@@ -305,10 +321,16 @@ class GlrDenoiser:
 
     def __init__(self, shape: GlrShape, mode: str = "bf16", edge_th: float = 0.1, k_over: int = 0, splits: int = 0,
                  device="cuda", cap: int = 0, epi_batch: int = 0, complex_: bool = False, n_uniform: int = 0,
-                 window: int = 20):
+                 window: int = 20, fused: bool = False):
+        """fused (real images, d <= 64, K <= 64): grouping, WNNM and aggregation in one kernel pass
+        (glr_lowrank_aggregate): no group buffer (1 GB less on the 16 x 512^2 workload) but slower
+        there (23 ms against 12 ms for the three separate kernels: the per-lane gathers and atomics
+        of the fused kernel do not coalesce), so it is off by default."""
         s = shape
         self.shape, self.mode, self.edge_th, self.complex_ = s, mode, edge_th, complex_
         self.n_uniform, self.window = n_uniform, window
+        can_fuse = not complex_ and s.C * s.P * s.P <= 64 and s.K <= 64
+        self.fused = fused and can_fuse
         self.opts = match_opts(mode, k_over, splits, cap, None, epi_batch, edge_th, window)
         self.k_over, self.splits, self.cap, self.epi_batch = k_over, splits, cap, epi_batch
         im = images(s.n_img, s.C, s.H, s.W, s.P)
@@ -319,12 +341,14 @@ class GlrDenoiser:
         self.n_corner = torch.empty(s.n_img, dtype=torch.int32, device=dev)
         self.idx = torch.empty((s.n_img, s.N, s.K), dtype=torch.int32, device=dev)
         self.dist = torch.empty((s.n_img, s.N, s.K), dtype=torch.float32, device=dev)
-        self.groups = torch.empty((s.n_img, s.N, s.K, d), dtype=torch.float32, device=dev)
+        self.groups = None if self.fused else torch.empty((s.n_img, s.N, s.K, d), dtype=torch.float32, device=dev)
         self.rank = torch.empty((s.n_img, s.N), dtype=torch.int32, device=dev)
         self.ws_select = workspace(L.GLR_OP_SELECT, im, s.N, s.K, None, dev)
         self.ws_match = workspace(L.GLR_OP_MATCH, im, s.N, s.K, self.opts, dev)
         self.ws_lowrank = workspace(L.GLR_OP_LOWRANK, im, s.N, s.K, None, dev)
         self.ws_agg = workspace(L.GLR_OP_AGGREGATE, im, s.N, s.K, None, dev)
+        # the workspace whose status block counts the low-rank step's sweeps and groups
+        self.ws_lowrank_status = self.ws_agg if self.fused else self.ws_lowrank
 
     def __call__(self, x: torch.Tensor, sigma_w: float, c_wnnm: float, out: torch.Tensor | None = None,
                  stream=None) -> torch.Tensor:
@@ -334,6 +358,9 @@ class GlrDenoiser:
         match_topk(x, s.P, self.keys, self.n_found, s.K, self.mode, k_over=self.k_over, splits=self.splits,
                    cap=self.cap, epi_batch=self.epi_batch, edge_th=self.edge_th, window=self.window, idx=self.idx,
                    dist=self.dist, ws=self.ws_match, stream=stream)
+        if self.fused:
+            return lowrank_aggregate(x, s.P, self.idx, self.n_found, sigma_w, c_wnnm, out=out, rank=self.rank,
+                                     ws=self.ws_agg, stream=stream)
         lowrank_groups(x, s.P, self.idx, self.n_found, sigma_w, c_wnnm, groups=self.groups, rank=self.rank,
                        ws=self.ws_lowrank, stream=stream, complex_=self.complex_)
         return aggregate(self.groups, self.idx, self.n_found, x, s.P, out=out, ws=self.ws_agg, stream=stream)

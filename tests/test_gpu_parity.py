@@ -292,3 +292,27 @@ def test_workspace_too_small():
     with pytest.raises(glr.GlrError) as e:
         glr.select_keys(x, 8, 10, ws=ws)
     assert e.value.code == glr.L.GLR_ENOMEM
+
+
+# ---------------------------------------------------------------------------
+# Fused grouping + WNNM + aggregation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", [("fz1", 2, 1, 60, 70, 8, 50, 40, 0.2), ("fz2", 1, 3, 33, 40, 4, 30, 24, 0.05),
+                                  ("fz3", 1, 1, 40, 40, 8, 20, 64, 0.0)])
+def test_fused_lowrank_aggregate_equals_separate_steps_bitwise(case):
+    tag, F, C, H, W, P, N, K, sw = case
+    x = scene(tag, F, H, W, quant=False, C=C)
+    rng = synth.rng_for(tag + "idx")
+    npos = (H - P + 1) * (W - P + 1)
+    idx = rng.integers(0, npos, size=(F, N, K)).astype(np.int32)
+    nf = np.full(F, N, np.int32)
+    nf[0] = N - 3  # rows beyond n_found take no part
+    cw = 2 * math.sqrt(K)
+    xt, it, nt = cuda(x), cuda(idx, torch.int32), cuda(nf, torch.int32)
+    groups, rank = glr.lowrank_groups(xt, P, it, nt, sw, cw)
+    want = glr.aggregate(groups, it, nt, xt, P)
+    rk = torch.empty_like(rank)
+    got = glr.lowrank_aggregate(xt, P, it, nt, sw, cw, rank=rk)
+    torch.cuda.synchronize()
+    assert torch.equal(got, want)
+    assert torch.equal(rk[0, :N - 3], rank[0, :N - 3])
