@@ -431,7 +431,32 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
         }
       }
       __syncwarp();
-      if (FUSED) {
+      if (FUSED && rnk <= 32 && DMAX == 64) {
+        // coalesced scatter: the 32 columns of this half go through the free half of
+        // the staging area (active columns use rows < rnk <= 32), XOR-swizzled so
+        // that both the column writes and the element reads avoid bank conflicts;
+        // then the warp adds one column at a time, lane = element
+        float* T = Ws + 32 * DMAX;
+#pragma unroll
+        for (int r = 0; r < DMAX; ++r) T[r * 32 + (lane ^ (r & 31))] = b[r];
+        __syncwarp();
+        const int Wq = io.W - io.P + 1, Hq = io.H - io.P + 1, PP = io.P * io.P;
+        unsigned long long* nf = io.num + (long long)f * io.C * io.H * io.W;
+        const int ok = own && qj >= 0;
+        for (int c = 0; c < 32; ++c) {
+          const int qc = __shfl_sync(0xffffffffu, ok ? qj : -1, c);
+          if (qc < 0) continue;  // uniform over the warp
+          const int r0 = qc / Wq, c0 = qc - (qc / Wq) * Wq;
+          for (int e = lane; e < d; e += 32) {
+            const float v = fminf(fmaxf(T[e * 32 + (c ^ (e & 31))], -1073741824.f), 1073741824.f);
+            const int ch = e / PP, rem = e - ch * PP, dr = rem / io.P, dc = rem - dr * io.P;
+            atomicAdd(nf + ((long long)ch * io.H + r0 + dr) * io.W + c0 + dc,
+                      (unsigned long long)__float2ll_rn(v * 4294967296.f));
+          }
+          if (lane == 0) atomicAdd(io.cnt + (long long)f * Hq * Wq + qc, 1);
+        }
+        __syncwarp();
+      } else if (FUSED) {
         if (own && qj >= 0) scatter_col<DMAX>(b, io, f, qj, d);
       } else if (own) {
         store_col<DMAX, CPLX>(b, Y + (long long)j * d, d);
