@@ -192,11 +192,14 @@ __host__ __device__ constexpr int norm_col(int d) { return d > DK_MAIN ? d : DK_
 
 // Positions: thread per position; writes 64 + 16 bf16.
 // emb != nullptr: pack the 16-value embeddings emb[img][q][16] instead of the patches.
+// PT: the patch side when it is known at compile time (cheap index arithmetic), 0 = P
+template <int PT>
 __global__ void __launch_bounds__(256) k_pack_positions(const float* __restrict__ x, const float* __restrict__ mean,
-                                                        int n_img, int C, int H, int W, int P, long long npos_pad,
+                                                        int n_img, int C, int H, int W, int P_, long long npos_pad,
                                                         const float* __restrict__ emb, int raw,
                                                         __nv_bfloat16* __restrict__ qmain,
                                                         __nv_bfloat16* __restrict__ qaux) {
+  const int P = PT ? PT : P_;
   const int Hq = H - P + 1, Wq = W - P + 1;
   const long long npos = (long long)Hq * Wq;
   const int d = emb != nullptr ? 16 : C * P * P;
@@ -886,9 +889,18 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   {
     const long long total = (long long)im.n_img * pl.npos_pad;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
-    GLR_LAUNCH("k_pack_positions", s,
-               k_pack_positions<<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, pl.npos_pad, emb_pos,
-                                                       raw, qmain, qaux));
+#define GLR_PACK_CASE(PP)                                                                                  \
+  GLR_LAUNCH("k_pack_positions", s,                                                                          \
+             k_pack_positions<PP><<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, pl.npos_pad, \
+                                                         emb_pos, raw, qmain, qaux))
+    switch (im.P) {
+      case 4: GLR_PACK_CASE(4); break;
+      case 5: GLR_PACK_CASE(5); break;
+      case 6: GLR_PACK_CASE(6); break;
+      case 8: GLR_PACK_CASE(8); break;
+      default: GLR_PACK_CASE(0); break;
+    }
+#undef GLR_PACK_CASE
   }
   {
     const int nk = im.n_img * pl.Npad;
