@@ -98,7 +98,7 @@ typedef struct glr_match_opts {
   const float* encoder; /* GLR_MATCH_LEARNED: device encoder parameters (GLR_ENCODER_PARAMS
                            floats); k_over = candidates per key (0 = 256) */
   int32_t epi_batch;    /* tensor-core epilogue: 32-column chunks read from tensor memory per
-                           visit, 2 or 4 (0 = 4) */
+                           visit, 2 or 4 (0 = 2) */
   float edge_th;        /* GLR_MATCH_EDGE: the threshold th of Eq. 7 on Sobel output (>= 0) */
   int32_t window;       /* GLR_MATCH_WINDOW: half-width w of the search window, 1 <= w <= 22:
                            the (2w+1)^2 positions centred on the key, shifted inside the

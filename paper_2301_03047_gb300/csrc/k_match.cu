@@ -479,7 +479,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   pl.cap = (o && o->cap > 0) ? o->cap : std::min(std::max(2 * pl.Kp + 64, 256), kStreamMaxEntries - 32);
   pl.cap = (int)(pl.cap / 32) * 32;
   pl.subs = 2;
-  pl.epi_batch = (o && o->epi_batch == 2) ? 2 : 4;
+  pl.epi_batch = (o && o->epi_batch == 4) ? 4 : 2;  // 2 chunks per visit: no register spills
   pl.key_tile = FT;
   pl.Npad = (int)(ceil_div(N, FT) * FT);
   const int Hq = im.H - im.P + 1, Wq = im.W - im.P + 1;
