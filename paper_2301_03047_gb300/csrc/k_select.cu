@@ -234,9 +234,17 @@ __global__ void __launch_bounds__(1024) k_topn(const unsigned long long* __restr
       for (int i = tid; i < 256; i += 1024) hist[i] = 0;
       __syncthreads();
       const unsigned long long pre = s_prefix, msk = s_mask;
-      for (long long i = tid; i < M; i += 1024) {
-        const unsigned long long k = cf[i];
-        if ((k & msk) == pre) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+      // warp-aggregated counts: the leading bytes of the rank keys are nearly constant,
+      // so lanes of a warp mostly share one bin; one atomic per distinct bin per warp
+      for (long long i0 = 0; i0 < M; i0 += 1024) {
+        const long long i = i0 + tid;
+        unsigned bin = 256u;
+        if (i < M) {
+          const unsigned long long k = cf[i];
+          if ((k & msk) == pre) bin = (unsigned)((k >> shift) & 255u);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        if (bin < 256u && (tid & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
       }
       __syncthreads();
       if (tid == 0) {
