@@ -1018,7 +1018,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="glr", choices=["glr", "reference"])
     ap.add_argument("--mode", default="bf16", choices=["bf16", "fp32", "edge"],
-                    help="matching form: bf16 (chosen), fp32 (plain), edge (the paper's heat map of Eq. 8)")
+                    help="matching form: bf16 (chosen), fp32 (plain), edge (the paper's heat map of Eq. 4)")
     ap.add_argument("--oracle-keys", type=int, default=96)
     ap.add_argument("--workload", default="sci16",
                     choices=["sci16", "sci4", "sci8", "mri1024", "mri256", "msfa32", "msfa4", "msfa2"],

@@ -77,7 +77,7 @@ enum {
   GLR_MATCH_BF16 = 1,   /* chosen form: BF16 tcgen05.mma into TMEM, FP32 accumulate, FP32 re-rank */
   GLR_MATCH_LEARNED = 2, /* learned proposal: k_over candidates by the 16-dim encoder embedding
                            (BF16 tcgen05 contraction), then the exact FP32 re-rank on patches */
-  GLR_MATCH_EDGE = 3,    /* the paper's heat map (Eq. 8): binary edge patches (Eq. 6, threshold
+  GLR_MATCH_EDGE = 3,    /* the paper's heat map (Eq. 4): binary edge patches (Eq. 2, threshold
                            edge_th) correlated over the four maps and all channels on the tensor
                            cores (0/1 operands: exact); the K largest values, ties by smaller id */
   GLR_MATCH_WINDOW = 4   /* block matching in a local window (Eq. 1 restricted to positions within
@@ -99,7 +99,7 @@ typedef struct glr_match_opts {
                            floats); k_over = candidates per key (0 = 256) */
   int32_t epi_batch;    /* tensor-core epilogue: 32-column chunks read from tensor memory per
                            visit, 2 or 4 (0 = 2) */
-  float edge_th;        /* GLR_MATCH_EDGE: the threshold th of Eq. 7 on Sobel output (>= 0) */
+  float edge_th;        /* GLR_MATCH_EDGE: the threshold th of Eq. 3 on Sobel output (>= 0) */
   int32_t window;       /* GLR_MATCH_WINDOW: half-width w of the search window, 1 <= w <= 22:
                            the (2w+1)^2 positions centred on the key, shifted inside the
                            position grid at its borders; K <= (2w+1)^2 */
@@ -118,9 +118,9 @@ size_t glr_workspace_size(int32_t op, const glr_images* im, int32_t N, int32_t K
                           const glr_match_opts* opts);
 
 /*
- * Key (exemplar) patch selection -- Section 2: "exemplar patches centred on
- * corner points of the averaged edge map", edge maps of Eq. 2 with the
- * threshold function of Eq. 3.
+ * Key (exemplar) patch selection -- Section 2: the exemplars sit at corners of
+ * the averaged binary edge map (edge maps of Eq. 2, threshold function of
+ * Eq. 3).
  *
  *   x        [n_img][C][H][W] float32, the current estimate.
  *   edge_th  the threshold th of Eq. 3 (applied to Sobel output).

@@ -12,8 +12,8 @@ notation, written for clarity, not speed:
   Sobel horizontal / vertical gradients and the four signed binary edge maps.
 * ``corner_response`` / ``nms3`` / ``select_keys`` -- Section 2: exemplar (key)
   patches are centred on corner points of the averaged edge map.
-* ``edge_match_topk``              -- the paper's global-matching heat map (Eq. 8):
-  correlation of binary edge patches over the four maps of Eq. 6.
+* ``edge_match_topk``              -- the paper's global-matching heat map (Eq. 4):
+  correlation of binary edge patches over the four maps of Eq. 2.
 * ``match_topk``                   -- Eq. 1 made global (Section 2): the K
   positions with the smallest squared L2 distance to each key over the whole
   image; the grouping operator R~_i of Eq. 5.
@@ -63,7 +63,7 @@ A20 ADMM for y = Phi x (the paper uses GAP or ADMM): scaled form z = D(x + u),
 A21 Block matching baseline: a (2w+1) x (2w+1) window of positions centred on
     the key, shifted inside the position grid at its borders (so every key sees
     (2w+1)^2 candidates); K smallest distances, ties by smaller id.
-A18 The paper's own matching score (the heat map of Eq. 8, ``edge_match_topk``):
+A18 The paper's own matching score (the heat map of Eq. 4, ``edge_match_topk``):
     Conv2d is a correlation summed over the four maps and the C channels (the
     per-channel maps, not the OR-ed ones of key selection); a larger value is a
     better match; the K largest are kept, ties by smaller position id.
@@ -286,7 +286,7 @@ def match_topk(x: np.ndarray, P: int, keys: np.ndarray, K: int, Q: np.ndarray | 
 
 
 def edge_planes(x: np.ndarray, th: float) -> np.ndarray:
-    """The four binary edge maps of Eq. 6 (reading A1) for every channel of x[C][H][W]:
+    """The four binary edge maps of Eq. 2 (reading A1) for every channel of x[C][H][W]:
     planes[m * C + c] for m in (h+, h-, v+, v-), values 0/1 (float64)."""
     C = x.shape[0]
     out = np.zeros((4 * C,) + x.shape[1:])
@@ -298,7 +298,7 @@ def edge_planes(x: np.ndarray, th: float) -> np.ndarray:
 
 
 def edge_heatmap(x: np.ndarray, P: int, key: int, th: float, E: np.ndarray | None = None) -> np.ndarray:
-    """Eq. 8: H(q) = sum over the four maps and the C channels of the Conv2d (a
+    """Eq. 4: H(q) = sum over the four maps and the C channels of the Conv2d (a
     correlation) of the key's edge patch with the edge maps, at every valid
     position q (an integer: the number of edge pixels the two patches share)."""
     if E is None:
@@ -308,7 +308,7 @@ def edge_heatmap(x: np.ndarray, P: int, key: int, th: float, E: np.ndarray | Non
 
 
 def edge_match_topk(x: np.ndarray, P: int, keys: np.ndarray, K: int, th: float):
-    """Global matching by the heat map of Eq. 8: for each key the K positions of
+    """Global matching by the heat map of Eq. 4: for each key the K positions of
     largest H, ties by smaller position id (reading A18); returns (idx, H values)."""
     E = edge_planes(x, th)
     Qe = patch_matrix(E, P)

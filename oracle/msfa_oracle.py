@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py): the library never imports it.
 
-The MSFA model of Section 3 is y = sum_b A_b x_b (the MSFA section's Eq. 4)
-with masks that do not overlap (its Eq. 5: A_b * A_c = 0 for b != c), so the
+The MSFA model of Section 3 is y = sum_b A_b x_b (Eq. 8) with masks that do
+not overlap (Eq. 9: A_b * A_c = 0 for b != c), so the
 GAP normaliser R = sum_b A_b^2 is 1 wherever a band is sampled.  One
 iteration denoises the whole multispectral image with GLR, patches spanning
 all bands (C = bands, d = bands P^2; multi-channel matching as in the paper's

@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
              int exact_scores, float dist_scale, int window, int32_t* __restrict__ idx, float* __restrict__ dist) {
   // window > 0: the candidates are every position within `window` rows and columns
   // of the key (block matching in a local window) instead of the stream buffers
-  // exact_scores != 0: the stream scores are already exact (the heat map of Eq. 8 on
+  // exact_scores != 0: the stream scores are already exact (the heat map of Eq. 4 on
   // 0/1 operands); they are sorted as they are and dist = dist_scale * score
   extern __shared__ unsigned long long rr_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -500,7 +500,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   pl.tiles_per_split = (int)ceil_div(pl.pos_tiles, splits);
   pl.splits = (int)ceil_div(pl.pos_tiles, pl.tiles_per_split);
   pl.streams_per_key = pl.splits * pl.subs;
-  // the heat map of Eq. 8 contracts the 4 C binary edge planes instead of the image
+  // the heat map of Eq. 4 contracts the 4 C binary edge planes instead of the image
   const int d = (edge ? 4 : 1) * im.C * im.P * im.P;
   const long long npos = (long long)Hq * Wq;
   WsLayout L;

@@ -37,8 +37,8 @@ __device__ __forceinline__ void sobel_at(const float* __restrict__ im, int H, in
   gv = ((a20 - a00) + 2.f * (a21 - a01)) + (a22 - a02);
 }
 
-// The four binary edge maps of Eq. 6 for every channel (the operands of the
-// heat map of Eq. 8): planes[f][m * C + ch][r][c] = 0 / 1 for m = h+, h-, v+, v-.
+// The four binary edge maps of Eq. 2 for every channel (the operands of the
+// heat map of Eq. 4): planes[f][m * C + ch][r][c] = 0 / 1 for m = h+, h-, v+, v-.
 __global__ void __launch_bounds__(256) k_edge_planes(const float* __restrict__ x, int n_img, int C, int H, int W,
                                                      float th, float* __restrict__ planes) {
   const long long HW = (long long)H * W;

@@ -54,7 +54,7 @@ def images_of(x: torch.Tensor, P: int) -> L.GlrImages:
 def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0, cap: int = 0,
                encoder: torch.Tensor | None = None, epi_batch: int = 0, edge_th: float = 0.1,
                window: int = 20) -> L.GlrMatchOpts:
-    """mode: "fp32" (plain), "bf16" (chosen), "learned", "edge" (the paper's heat map of Eq. 8),
+    """mode: "fp32" (plain), "bf16" (chosen), "learned", "edge" (the paper's heat map of Eq. 4),
     or "window" (block matching within +-window of the key)."""
     m = {"fp32": L.GLR_MATCH_FP32, "bf16": L.GLR_MATCH_BF16, "learned": L.GLR_MATCH_LEARNED,
          "edge": L.GLR_MATCH_EDGE, "window": L.GLR_MATCH_WINDOW}.get(mode, mode)
@@ -111,7 +111,7 @@ def select_keys(x, P, N, edge_th=0.1, *, n_uniform=0, keys=None, n_found=None, n
 def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, cap=0, encoder=None, epi_batch=0,
                edge_th=0.1, window=20, idx=None, dist=None, ws=None, stream=None):
     """Global matching with a fused running top-K (Eq. 1 over the whole image as a contraction).
-    mode "edge": the paper's heat map (Eq. 8); dist then holds the heat-map values (descending)."""
+    mode "edge": the paper's heat map (Eq. 4); dist then holds the heat-map values (descending)."""
     lib = L.load()
     im = images_of(x, P)
     N = keys.shape[1]

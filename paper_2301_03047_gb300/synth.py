@@ -353,7 +353,7 @@ def mri_problem(cfg: MriConfig, extra: int = 0) -> MriProblem:
 # ----------------------------------------------------------------------------
 @dataclass(frozen=True)
 class MsfaConfig:
-    """A batch of MSFA snapshots y = sum_b A_b x_b (Eq. 4 of the MSFA section) of uneven sizes."""
+    """A batch of MSFA snapshots y = sum_b A_b x_b (Eq. 8) of uneven sizes."""
 
     name: str
     config_no: int

@@ -1,4 +1,4 @@
-"""The paper's heat-map matching (Eq. 8, GLR_MATCH_EDGE) against the FP64 oracle.
+"""The paper's heat-map matching (Eq. 4, GLR_MATCH_EDGE) against the FP64 oracle.
 
 The operands are binary edge patches, exact in BF16, and the heat-map values
 are integers, so the values are compared exactly.  Ids: the top-K by value is

@@ -9,7 +9,7 @@ from paper_2301_03047_gb300 import synth
 
 def test_mosaic_masks_are_orthogonal_and_cover():
     m = synth.mosaic_masks(10, 13, 16)
-    assert np.all(m.sum(0) == 1)  # every pixel sees exactly one band (Eq. 5: A_b A_c = 0)
+    assert np.all(m.sum(0) == 1)  # every pixel sees exactly one band (Eq. 9: A_b A_c = 0)
     for b in range(16):
         rr, cc = np.nonzero(m[b])
         assert np.all(4 * (rr % 4) + (cc % 4) == b)

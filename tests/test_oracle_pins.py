@@ -393,7 +393,7 @@ def test_sigma_schedule_reading():
 
 
 # ---------------------------------------------------------------------------
-# The paper's heat-map score (Eq. 8), reading A18
+# The paper's heat-map score (Eq. 4), reading A18
 # ---------------------------------------------------------------------------
 def test_edge_heatmap_counts_shared_edge_pixels():
     """H(q) is the number of (map, channel, pixel) edge entries the two patches share:
