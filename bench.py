@@ -424,29 +424,35 @@ def run_glr(args) -> None:
         y_h = torch.from_numpy(prob.y).pin_memory()
         m_h = torch.from_numpy(prob.masks).pin_memory()
         x_h = torch.empty((1, cfg.T, cfg.H, cfg.W), dtype=torch.float32).pin_memory()
+        kover, splits, cap, eb = tuned[forms[0]]
         rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=forms[0], edge_th=cfg.edge_th,
-                                   device=dev)
+                                   device=dev, k_over=kover, splits=splits, cap=cap, epi_batch=eb)
         y_d = torch.empty_like(y)
         m_d = torch.empty_like(masks)
         y_d.copy_(y_h, non_blocking=True)
         m_d.copy_(m_h, non_blocking=True)
         rec.start(y_d, m_d)
+        use_graph = not args.no_graph  # the public API's graph replay (SciReconstructor.capture / step_graph)
+        if use_graph:
+            rec.capture(sched, cfg.c_wnnm)
+        run = (lambda s: rec.step_graph(s)) if use_graph else (lambda s: rec.step(s, cfg.c_wnnm))
         for i in range(args.warmup):
-            rec.step(sched[i % len(sched)], cfg.c_wnnm)
+            run(sched[i % len(sched)])
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
         t0 = time.perf_counter()
         for i in range(args.steps):
+            # this step's snapshot and masks come from pinned host memory, the estimate goes back
             y_d.copy_(y_h, non_blocking=True)
             m_d.copy_(m_h, non_blocking=True)
-            rec.step(sched[i % len(sched)], cfg.c_wnnm)
+            run(sched[(args.warmup + i) % len(sched)])
             x_h.copy_(rec.x, non_blocking=True)
             torch.cuda.current_stream().synchronize()
         e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
         e2e = {"value": round(ws * args.steps / e2e_s, 4), "unit": UNIT,
                "h2d_bytes_per_step": int(y_h.numel() * 4 + m_h.numel() * 4),
-               "d2h_bytes_per_step": int(x_h.numel() * 4)}
+               "d2h_bytes_per_step": int(x_h.numel() * 4), "via": "graph replay" if use_graph else "eager"}
         del rec
 
     if rank != 0:
@@ -653,25 +659,31 @@ def run_mri(args, cfg, dev, dist) -> None:
         y_h = torch.from_numpy(prob.y).pin_memory()
         m_h = torch.from_numpy(prob.mask).pin_memory()
         x_h = torch.empty((1, 2, cfg.H, cfg.W), dtype=torch.float32).pin_memory()
+        kover, splits, cap, eb = tuned[forms[0]]
         rec = glr.MriReconstructor(cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=forms[0], edge_th=cfg.edge_th,
-                                   rho=cfg.rho, device=dev)
+                                   rho=cfg.rho, device=dev, k_over=kover, splits=splits, cap=cap, epi_batch=eb)
         y_d, m_d = torch.empty_like(y), torch.empty_like(mask)
         y_d.copy_(y_h, non_blocking=True)
         m_d.copy_(m_h, non_blocking=True)
         rec.start(y_d, m_d)
+        use_graph = not args.no_graph
+        if use_graph:
+            rec.capture(sched, cfg.c_wnnm)
+        run = (lambda s: rec.step_graph(s)) if use_graph else (lambda s: rec.step(s, cfg.c_wnnm))
         for i in range(args.warmup):
-            rec.step(sched[i % len(sched)], cfg.c_wnnm)
+            run(sched[i % len(sched)])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(args.steps):
             y_d.copy_(y_h, non_blocking=True)
             m_d.copy_(m_h, non_blocking=True)
-            rec.step(sched[i % len(sched)], cfg.c_wnnm)
+            run(sched[(args.warmup + i) % len(sched)])
             x_h.copy_(rec.x, non_blocking=True)
             torch.cuda.current_stream().synchronize()
         e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
         e2e = {"value": round(ws * args.steps / e2e_s, 4), "unit": UNIT,
-               "h2d_bytes_per_step": int(y_h.numel() * 4 + m_h.numel() * 4), "d2h_bytes_per_step": int(x_h.numel() * 4)}
+               "h2d_bytes_per_step": int(y_h.numel() * 4 + m_h.numel() * 4), "d2h_bytes_per_step": int(x_h.numel() * 4),
+               "via": "graph replay" if use_graph else "eager"}
         del rec
     if rank != 0:
         return
@@ -843,22 +855,27 @@ def run_msfa(args, cfg, dev, dist) -> None:
             a.copy_(b, non_blocking=True)
         rec.start(y_d, masks)
         out_h = [torch.empty((cfg.bands, s, s), dtype=torch.float32).pin_memory() for s in sides]
+        use_graph = not args.no_graph
+        if use_graph:
+            rec.capture(sched, cfg.c_wnnm)
+        run = (lambda s: rec.step_graph(s)) if use_graph else (lambda s: rec.step(s, cfg.c_wnnm))
         for i in range(args.warmup):
-            rec.step(sched[i % len(sched)], cfg.c_wnnm)
+            run(sched[i % len(sched)])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(head["steps"]):
             for c in rec.classes:  # the snapshots of each class come from pinned host memory
                 for j, idx in enumerate(c["ids"]):
                     c["y"][j].copy_(y_h[idx], non_blocking=True)
-            rec.step(sched[i % len(sched)], cfg.c_wnnm)
+            run(sched[(args.warmup + i) % len(sched)])
             for o, x in zip(out_h, rec.images()):
                 o.copy_(x, non_blocking=True)
             torch.cuda.current_stream().synchronize()
         e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
         e2e = {"value": round(ws * head["steps"] / e2e_s, 4), "unit": UNIT,
                "h2d_bytes_per_step": int(sum(y.numel() for y in y_h) * 4),
-               "d2h_bytes_per_step": int(sum(o.numel() for o in out_h) * 4)}
+               "d2h_bytes_per_step": int(sum(o.numel() for o in out_h) * 4),
+               "via": "graph replay" if use_graph else "eager"}
         del rec
     if rank != 0:
         return
