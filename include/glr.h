@@ -103,7 +103,9 @@ typedef struct glr_match_opts {
   int32_t window;       /* GLR_MATCH_WINDOW: half-width w of the search window, 1 <= w <= 22:
                            the (2w+1)^2 positions centred on the key, shifted inside the
                            position grid at its borders; K <= (2w+1)^2 */
-  int32_t reserved;
+  int32_t bound_pass;   /* tensor-core scorer: run a first scan that only records score
+                           minima, and start the candidate scan from the bound they give;
+                           1 = on, -1 = off, 0 = automatic */
 } glr_match_opts;
 
 /* Operation codes for glr_workspace_size. */

@@ -27,7 +27,7 @@ class GlrImages(ctypes.Structure):
 
 class GlrMatchOpts(ctypes.Structure):
     _fields_ = [("mode", c_int32), ("k_over", c_int32), ("splits", c_int32), ("cap", c_int32), ("encoder", c_void_p),
-                ("epi_batch", c_int32), ("edge_th", c_float), ("window", c_int32), ("reserved", c_int32)]
+                ("epi_batch", c_int32), ("edge_th", c_float), ("window", c_int32), ("bound_pass", c_int32)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/glr.h

@@ -40,6 +40,8 @@ struct MatchPlan {
   size_t edge_off;      // GLR_MATCH_EDGE: edge planes [n_img][4 C][H][W]
   int epi_batch;        // tensor-core epilogue: 32-column chunks read from TMEM per visit (2 or 4)
   long long npos_pad;   // BF16 position rows per image (pos_tiles * pos_tile)
+  int bound_pass;       // tensor-core scorer: minima scan first (bound from half-tile minima)
+  size_t mins_off;      // bound_pass: half-tile minima [n_img][Npad][2 pos_tiles] float32
   size_t mean_off, qn_off, keyv_off, buf_off, bufcnt_off, taugl_off, qpack_off, kpack_off, embp_off, embk_off, total;
 };
 MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o);

@@ -522,6 +522,10 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
     pl.npos_pad = (long long)pl.pos_tiles * pl.pos_tile;
     pl.qpack_off = L.take((size_t)im.n_img * pl.npos_pad * dk * 2);
     pl.kpack_off = L.take((size_t)im.n_img * pl.Npad * dk * 2);
+    // the bound of the minima scan needs Kp half tiles; automatic: on
+    const int bp = o ? o->bound_pass : 0;
+    pl.bound_pass = (bp >= 0 && 2LL * pl.pos_tiles >= pl.Kp) ? 1 : 0;
+    if (pl.bound_pass) pl.mins_off = L.take((size_t)im.n_img * pl.Npad * 2 * pl.pos_tiles * 4);
   }
   if (edge) pl.edge_off = L.take((size_t)im.n_img * 4 * im.C * im.H * im.W * 4);
   if (pl.mode == GLR_MATCH_LEARNED) {

@@ -402,6 +402,74 @@ __global__ void __launch_bounds__(256) k_pack_keys_w(const float* __restrict__ k
   }
 }
 
+// Bound from the half-tile minima: the kp-th smallest of the 2 ntiles minima of a
+// key's row.  kp half tiles each hold a score no larger than it, so at least kp
+// scores of the key are <= it: published (+1 in the order key, the filter is
+// strict) it is a valid bound for the scan that keeps candidates.  One warp per
+// key, exact 4-pass radix select over the order-preserving keys.
+__global__ void __launch_bounds__(256) k_tau_bound(const float* __restrict__ mins, const int32_t* __restrict__ n_found,
+                                                   int n_img, int N, int Npad, int L, int kp,
+                                                   uint32_t* __restrict__ tau_gl) {
+  __shared__ unsigned hist_s[8][256];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned* hist = hist_s[wid];
+  const long long nkeys = (long long)n_img * N;
+  for (long long gk = blockIdx.x * 8LL + wid; gk < nkeys; gk += gridDim.x * 8LL) {
+    const int f = (int)(gk / N), k = (int)(gk - (long long)f * N);
+    if (k >= min(n_found[f], N)) continue;
+    const float* m = mins + ((long long)f * Npad + k) * L;
+    uint32_t prefix = 0, pmask = 0;
+    int rank = kp;
+#pragma unroll 1
+    for (int pass = 0; pass < 4; ++pass) {
+      const int shift = 24 - 8 * pass;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) hist[lane * 8 + t] = 0;
+      __syncwarp();
+      for (int i = lane; i < L; i += 32) {
+        const uint32_t kk = float_order_key(m[i]);
+        if ((kk & pmask) == prefix) atomicAdd(&hist[(kk >> shift) & 255u], 1u);
+      }
+      __syncwarp();
+      int loc[8], sum = 0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        loc[t] = (int)hist[lane * 8 + t];
+        sum += loc[t];
+      }
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int yv = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += yv;
+      }
+      const int excl = incl - sum;
+      const int owner = __ffs(__ballot_sync(0xffffffffu, excl < rank && rank <= incl)) - 1;
+      int sel = 0, before = 0;
+      if (lane == owner) {
+        int c = excl;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          if (c + loc[t] >= rank) {
+            sel = lane * 8 + t;
+            before = c;
+            break;
+          }
+          c += loc[t];
+        }
+      }
+      sel = __shfl_sync(0xffffffffu, sel, owner);
+      before = __shfl_sync(0xffffffffu, before, owner);
+      rank -= before;
+      prefix |= (uint32_t)sel << shift;
+      pmask |= 255u << shift;
+      __syncwarp();
+    }
+    // a finite kp-th minimum bounds the scan (an infinite one says nothing)
+    if (lane == 0 && prefix < float_order_key(INFINITY)) atomicMin(tau_gl + (long long)f * Npad + k, prefix + 1u);
+  }
+}
+
 // Seed bounds: for each key, the K'-th smallest tensor-core score over 16 x 16
 // positions sampled at stride 2 around it.  That sample is a subset of the
 // positions, so at least K' positions score below this value: it is a valid
@@ -540,7 +608,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                const __grid_constant__ CUtensorMap tm_kmain, const __grid_constant__ CUtensorMap tm_kaux,
                const int32_t* __restrict__ n_found, int Npad, long long npos, long long npos_pad, int splits,
                int tiles_per_split, int ntiles, int nkc, StreamCfg cfg, uint2* __restrict__ bufs,
-               int* __restrict__ buf_cnt, uint32_t* __restrict__ tau_gl, StatusBlock* st, float* __restrict__ dump) {
+               int* __restrict__ buf_cnt, uint32_t* __restrict__ tau_gl, StatusBlock* st, float* __restrict__ dump,
+               float* __restrict__ mins) {
+  // mins != nullptr: bound pass.  No candidate is kept; each epilogue lane writes the
+  // minimum score of its row over every half tile (128 positions) to
+  // mins[key][2 tile + half] instead.
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t kBar = WIDE ? W_OFF_BAR : OFF_BAR, kMisc = WIDE ? W_OFF_MISC : OFF_MISC;
@@ -742,6 +814,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const long long tile_q0 = (long long)(t_begin + i) * TC_N;
       const uint32_t gl = gl_next;
       gl_next = *reinterpret_cast<volatile uint32_t*>(pub_gl + lane);
+      float mrun = INFINITY;  // bound pass: minimum of this lane's row over the half tile
       // EB chunks of 32 columns are read from TMEM per visit; the buffer goes back to
       // the MMA warp after the last visit (EB = 4: one visit, earliest release)
 #pragma unroll 1
@@ -768,6 +841,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j) dump[((long long)f * Npad + key) * TC_N + col + j] = v[c][j];
           }
+          if (mins != nullptr) {
+            mrun = fminf(mrun, stream_min(v[c], nvalid));
+            continue;
+          }
           const float te = stream_tau_eff(tau, *reinterpret_cast<volatile uint32_t*>(pub_sh + lane), gl);
           const unsigned rows = stream_filter(v[c], nvalid, te);
           if (rows) {
@@ -779,10 +856,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
+      if (mins != nullptr) mins[(((long long)f * Npad + key) * ntiles + t_begin + i) * 2 + h] = mrun;
     }
-    stream_finish(tau, cnt, mybuf, cfg, whist);
-    stream_stats_flush(stats, st);
-    buf_cnt[stream] = (key < nf) ? cnt : 0;
+    if (mins == nullptr) {
+      stream_finish(tau, cnt, mybuf, cfg, whist);
+      stream_stats_flush(stats, st);
+      buf_cnt[stream] = (key < nf) ? cnt : 0;
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -826,6 +906,15 @@ bool make_map(CUtensorMap* m, void* base, uint64_t rows, uint32_t cols, uint32_t
 
 extern float* g_tc_dump;
 
+glr_status launch_tau_bound(const float* mins, const int32_t* n_found, int n_img, int N, const MatchPlan& pl,
+                            uint32_t* taugl, cudaStream_t s) {
+  const long long nkeys = (long long)n_img * N;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, 8), 152LL * 16));
+  GLR_LAUNCH("k_tau_bound", s,
+             k_tau_bound<<<blocks, 256, 0, s>>>(mins, n_found, n_img, N, pl.Npad, 2 * pl.pos_tiles, pl.Kp, taugl));
+  return GLR_OK;
+}
+
 glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int32_t* n_found, const MatchPlan& pl,
                                 char* ws, float* dump, const int32_t* seed_keys, int seed_N, const float* emb_pos,
                                 const float* emb_keys, cudaStream_t s) {
@@ -839,6 +928,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   uint2* bufs = reinterpret_cast<uint2*>(ws + pl.buf_off);
   int* bufcnt = reinterpret_cast<int*>(ws + pl.bufcnt_off);
   uint32_t* taugl = reinterpret_cast<uint32_t*>(ws + pl.taugl_off);
+  float* mins = pl.bound_pass ? reinterpret_cast<float*>(ws + pl.mins_off) : nullptr;
   StatusBlock* st = reinterpret_cast<StatusBlock*>(ws);
   __nv_bfloat16* qmain = reinterpret_cast<__nv_bfloat16*>(ws + pl.qpack_off);
   __nv_bfloat16* qaux = qmain + (size_t)im.n_img * pl.npos_pad * DK_MAIN * pl.nkc;
@@ -880,10 +970,18 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
     const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
     const StreamCfg cfg{pl.cap, pl.Kp};
     dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
+    if (pl.bound_pass) {
+      GLR_LAUNCH("k_match_tc_min", s,
+                 kern<<<grid, TC_THREADS, W_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
+                                                       pl.splits, pl.tiles_per_split, pl.pos_tiles, pl.nkc, cfg, bufs,
+                                                       bufcnt, taugl, st, nullptr, mins));
+      const glr_status bs = launch_tau_bound(mins, n_found, im.n_img, seed_N, pl, taugl, s);
+      if (bs != GLR_OK) return bs;
+    }
     GLR_LAUNCH("k_match_tc", s,
                kern<<<grid, TC_THREADS, W_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad, pl.splits,
                                                      pl.tiles_per_split, pl.pos_tiles, pl.nkc, cfg, bufs, bufcnt,
-                                                     taugl, st, nullptr));
+                                                     taugl, st, nullptr, nullptr));
     return GLR_OK;
   }
   {
@@ -934,10 +1032,18 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
   const StreamCfg cfg{pl.cap, pl.Kp};
   dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
+  if (pl.bound_pass && dump == nullptr) {
+    GLR_LAUNCH("k_match_tc_min", s,
+               kern<<<grid, TC_THREADS, TC_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
+                                                      pl.splits, pl.tiles_per_split, pl.pos_tiles, 1, cfg, bufs,
+                                                      bufcnt, taugl, st, nullptr, mins));
+    const glr_status bs = launch_tau_bound(mins, n_found, im.n_img, seed_N, pl, taugl, s);
+    if (bs != GLR_OK) return bs;
+  }
   GLR_LAUNCH("k_match_tc", s,
              kern<<<grid, TC_THREADS, TC_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
                                                           pl.splits, pl.tiles_per_split, pl.pos_tiles, 1, cfg, bufs,
-                                                          bufcnt, taugl, st, dump));
+                                                          bufcnt, taugl, st, dump, nullptr));
   return GLR_OK;
 }
 
@@ -945,8 +1051,8 @@ glr_status launch_match_tc(const float* x, const glr_images& im, const int32_t* 
                            const MatchPlan& pl, char* ws, cudaStream_t s) {
   const float* ep = pl.mode == GLR_MATCH_LEARNED ? reinterpret_cast<const float*>(ws + pl.embp_off) : nullptr;
   const float* ek = pl.mode == GLR_MATCH_LEARNED ? reinterpret_cast<const float*>(ws + pl.embk_off) : nullptr;
-  // seed bounds read the narrow operand layout only
-  const int32_t* seed = (g_tc_dump || pl.nkc > 1) ? nullptr : keys;
+  // seed bounds read the narrow operand layout only; the minima scan gives a tighter bound
+  const int32_t* seed = (g_tc_dump || pl.nkc > 1 || pl.bound_pass) ? nullptr : keys;
   return launch_match_tc_impl(x, im, n_found, pl, ws, g_tc_dump, seed, N, ep, ek, s);
 }
 

@@ -215,7 +215,7 @@ __device__ __forceinline__ float stream_tau_eff(float tau_own, uint32_t pub_shar
 // Step 1 of a chunk push: rows (bit r = lane r) whose 32 scores contain one
 // below their tau.  s = this lane's row scores, column j = position q0 + j;
 // columns j >= nvalid do not exist.
-__device__ __forceinline__ unsigned stream_filter(const float (&s)[32], int nvalid, float tau) {
+__device__ __forceinline__ float stream_min(const float (&s)[32], int nvalid) {
   // tree-shaped minimum: depth 5 instead of a 31-long dependency chain
   float m[16];
   if (nvalid < 32) {
@@ -230,7 +230,11 @@ __device__ __forceinline__ unsigned stream_filter(const float (&s)[32], int nval
   for (int w = 8; w > 0; w >>= 1)
 #pragma unroll
     for (int j = 0; j < w; ++j) m[j] = fminf(m[j], m[j + w]);
-  return __ballot_sync(0xffffffffu, m[0] < tau);
+  return m[0];
+}
+
+__device__ __forceinline__ unsigned stream_filter(const float (&s)[32], int nvalid, float tau) {
+  return __ballot_sync(0xffffffffu, stream_min(s, nvalid) < tau);
 }
 
 // Step 2: append the candidates of the selected rows.  tile holds the same

@@ -53,9 +53,10 @@ def images_of(x: torch.Tensor, P: int) -> L.GlrImages:
 
 def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0, cap: int = 0,
                encoder: torch.Tensor | None = None, epi_batch: int = 0, edge_th: float = 0.1,
-               window: int = 20) -> L.GlrMatchOpts:
+               window: int = 20, bound_pass: int = 0) -> L.GlrMatchOpts:
     """mode: "fp32" (plain), "bf16" (chosen), "learned", "edge" (the paper's heat map of Eq. 4),
-    or "window" (block matching within +-window of the key)."""
+    or "window" (block matching within +-window of the key).  bound_pass (tensor-core modes):
+    1 = a minima scan gives each key its starting bound, -1 = no minima scan, 0 = automatic."""
     m = {"fp32": L.GLR_MATCH_FP32, "bf16": L.GLR_MATCH_BF16, "learned": L.GLR_MATCH_LEARNED,
          "edge": L.GLR_MATCH_EDGE, "window": L.GLR_MATCH_WINDOW}.get(mode, mode)
     o = L.GlrMatchOpts()
@@ -64,6 +65,7 @@ def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0, cap: 
     o.epi_batch = int(epi_batch)
     o.edge_th = float(edge_th)
     o.window = int(window)
+    o.bound_pass = int(bound_pass)
     return o
 
 
@@ -109,13 +111,13 @@ def select_keys(x, P, N, edge_th=0.1, *, n_uniform=0, keys=None, n_found=None, n
 
 
 def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, cap=0, encoder=None, epi_batch=0,
-               edge_th=0.1, window=20, idx=None, dist=None, ws=None, stream=None):
+               edge_th=0.1, window=20, bound_pass=0, idx=None, dist=None, ws=None, stream=None):
     """Global matching with a fused running top-K (Eq. 1 over the whole image as a contraction).
     mode "edge": the paper's heat map (Eq. 4); dist then holds the heat-map values (descending)."""
     lib = L.load()
     im = images_of(x, P)
     N = keys.shape[1]
-    o = match_opts(mode, k_over, splits, cap, encoder, epi_batch, edge_th, window)
+    o = match_opts(mode, k_over, splits, cap, encoder, epi_batch, edge_th, window, bound_pass)
     dev = x.device
     if idx is None:
         idx = torch.empty((x.shape[0], N, K), dtype=torch.int32, device=dev)
