@@ -227,9 +227,31 @@ def traffic_for(kernel: str, units_per_launch: float):
     return d["dram_bytes_per_unit"] * units_per_launch
 
 
+SCHED_KEYS = ("k_over", "splits", "cap", "epi_batch", "bound_pass")
+
+
+def sched_kw(t) -> dict:
+    """A matching schedule tuple (autotuner or --match-schedule) as reconstructor keyword arguments."""
+    return dict(zip(SCHED_KEYS, tuple(int(v) for v in t) + (0,) * (len(SCHED_KEYS) - len(t))))
+
+
+def merge_scans(prof: dict) -> dict:
+    """The tensor-core matcher's minima scan and bound kernel counted with its candidate scan:
+    together they are one contraction of every key/position pair."""
+    prof = dict(prof)
+    extra = [prof.pop(k) for k in ("k_match_tc_min", "k_tau_bound") if k in prof]
+    if extra and "k_match_tc" in prof:
+        ms, n = prof["k_match_tc"]
+        prof["k_match_tc"] = (ms + sum(e[0] for e in extra), n)
+    return prof
+
+
 def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict, n_img: int | None = None,
              d: int | None = None) -> dict:
-    """Roofline entry of the kernel with the largest share of the timed region."""
+    """Roofline entry of the kernel with the largest share of the timed region.  The matcher's two
+    scans (minima, candidates) count as one unit: the pair FLOPs once, over their summed time."""
+    scans = "k_match_tc_min" in prof
+    prof = merge_scans(prof)
     name, (ms, n) = max(prof.items(), key=lambda kv: kv[1][0])
     avg_s = ms / n / 1e3
     T = n_img if n_img is not None else cfg.T
@@ -242,7 +264,8 @@ def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict, n
         work = 2.0 * d * units
         if name == "k_match_tc":
             out = {"bound": "tensor", "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                   "peak_note": f"of {pk['source']} cuBLAS bf16 sustained"}
+                   "peak_note": f"of {pk['source']} cuBLAS bf16 sustained"
+                                + ("; time = minima scan + bound + candidate scan" if scans else "")}
         else:
             out = {"bound": "alu", "peak": round(fp32_alu_peak_tflops(sm), 1), "unit": "TFLOP/s",
                    "peak_note": f"derived FP32 FMA peak 152x128x2 at {sm:.0f} MHz"}
@@ -341,13 +364,12 @@ def run_glr(args) -> None:
         x0 = glr.gap_step(y[None], masks, None).view(cfg.T, 1, cfg.H, cfg.W).contiguous()
         k0, n0, _ = glr.select_keys(x0, cfg.P, cfg.N, cfg.edge_th)
         if args.match_schedule and form == forms[0]:
-            tuned[form] = tuple(int(v) for v in args.match_schedule.split(","))
+            tuned[form] = sched_kw(args.match_schedule.split(","))
         else:
-            tuned[form] = glr.autotune_match(x0, cfg.P, k0, n0, cfg.K, form) if not args.no_tune else (0, 0, 0, 0)
+            tuned[form] = sched_kw(glr.autotune_match(x0, cfg.P, k0, n0, cfg.K, form) if not args.no_tune else ())
         del x0, k0, n0
-        kover, splits, cap, eb = tuned[form]
         rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=form, edge_th=cfg.edge_th,
-                                   device=dev, k_over=kover, splits=splits, cap=cap, epi_batch=eb)
+                                   device=dev, **tuned[form])
         rec.start(y, masks)
         k = 0
         for _ in range(args.warmup):
@@ -424,9 +446,8 @@ def run_glr(args) -> None:
         y_h = torch.from_numpy(prob.y).pin_memory()
         m_h = torch.from_numpy(prob.masks).pin_memory()
         x_h = torch.empty((1, cfg.T, cfg.H, cfg.W), dtype=torch.float32).pin_memory()
-        kover, splits, cap, eb = tuned[forms[0]]
         rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=forms[0], edge_th=cfg.edge_th,
-                                   device=dev, k_over=kover, splits=splits, cap=cap, epi_batch=eb)
+                                   device=dev, **tuned[forms[0]])
         y_d = torch.empty_like(y)
         m_d = torch.empty_like(masks)
         y_d.copy_(y_h, non_blocking=True)
@@ -496,8 +517,7 @@ def run_glr(args) -> None:
         "e2e": e2e,
         "clocks": clocks_summary,
     }
-    line["autotuned_match"] = {f: {"k_over": t[0], "splits": t[1], "cap": t[2], "epi_batch": t[3]}
-                               for f, t in tuned.items()}
+    line["autotuned_match"] = tuned
     if "graph" in results:
         line["cuda_graph"] = {"value": round(results["graph"]["value"], 4), "unit": UNIT,
                               "ms_per_step": round(results["graph"]["ms_per_step"], 3)}
@@ -584,13 +604,12 @@ def run_mri(args, cfg, dev, dist) -> None:
         x0 = glr.fft2(y[None], inverse=True)
         k0, n0, _ = glr.select_keys(x0, cfg.P, cfg.N, cfg.edge_th)
         if args.match_schedule and form == forms[0]:
-            tuned[form] = tuple(int(v) for v in args.match_schedule.split(","))
+            tuned[form] = sched_kw(args.match_schedule.split(","))
         else:
-            tuned[form] = glr.autotune_match(x0, cfg.P, k0, n0, cfg.K, form) if not args.no_tune else (0, 0, 0, 0)
+            tuned[form] = sched_kw(glr.autotune_match(x0, cfg.P, k0, n0, cfg.K, form) if not args.no_tune else ())
         del x0, k0, n0
-        kover, splits, cap, eb = tuned[form]
         rec = glr.MriReconstructor(cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=form, edge_th=cfg.edge_th, rho=cfg.rho,
-                                   device=dev, k_over=kover, splits=splits, cap=cap, epi_batch=eb)
+                                   device=dev, **tuned[form])
         rec.start(y, mask)
         k = 0
         for _ in range(args.warmup):
@@ -659,9 +678,8 @@ def run_mri(args, cfg, dev, dist) -> None:
         y_h = torch.from_numpy(prob.y).pin_memory()
         m_h = torch.from_numpy(prob.mask).pin_memory()
         x_h = torch.empty((1, 2, cfg.H, cfg.W), dtype=torch.float32).pin_memory()
-        kover, splits, cap, eb = tuned[forms[0]]
         rec = glr.MriReconstructor(cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=forms[0], edge_th=cfg.edge_th,
-                                   rho=cfg.rho, device=dev, k_over=kover, splits=splits, cap=cap, epi_batch=eb)
+                                   rho=cfg.rho, device=dev, **tuned[forms[0]])
         y_d, m_d = torch.empty_like(y), torch.empty_like(mask)
         y_d.copy_(y_h, non_blocking=True)
         m_d.copy_(m_h, non_blocking=True)
@@ -712,7 +730,7 @@ def run_mri(args, cfg, dev, dist) -> None:
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])} if prof else {},
         "svd_sweeps_per_group": round(sweeps, 2), "topk_streams": stream_stats, "roofline": rl,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks_summary,
-        "autotuned_match": {f: {"k_over": t[0], "splits": t[1], "cap": t[2], "epi_batch": t[3]} for f, t in tuned.items()},
+        "autotuned_match": tuned,
     }
     if "graph" in results:
         line["cuda_graph"] = {"value": round(results["graph"]["value"], 4), "unit": UNIT,
@@ -782,9 +800,13 @@ def run_msfa(args, cfg, dev, dist) -> None:
         return float(np.mean([10 * math.log10(1.0 / float(np.mean((x.cpu().numpy() - im.truth) ** 2)))
                               for x, im in zip(rec.images(), imgs)]))
 
+    fixed = None  # --match-schedule: one schedule for every size class of the chosen form
+    if args.match_schedule:
+        t = tuple(sched_kw(args.match_schedule.split(",")).values())
+        fixed = {(int(sd), int(n)): t for sd, n in zip(sides, Ns)}
     for form in forms:
         rec = glr.MsfaBatchReconstructor(sides, Ns, cfg.bands, cfg.P, cfg.K, mode=form, edge_th=cfg.edge_th,
-                                         device=dev)
+                                         device=dev, tuned=fixed if form == forms[0] else None)
         rec.start(ys, masks)
         steps = args.steps
         k = 0
@@ -849,7 +871,7 @@ def run_msfa(args, cfg, dev, dist) -> None:
     if not args.no_e2e:
         y_h = [torch.from_numpy(im.y).pin_memory() for im in imgs]
         rec = glr.MsfaBatchReconstructor(sides, Ns, cfg.bands, cfg.P, cfg.K, mode=forms[0], edge_th=cfg.edge_th,
-                                         device=dev)
+                                         device=dev, tuned=fixed)
         y_d = [torch.empty_like(y) for y in ys]
         for a, b in zip(y_d, y_h):
             a.copy_(b, non_blocking=True)
@@ -890,9 +912,11 @@ def run_msfa(args, cfg, dev, dist) -> None:
     pk = peaks()
     rl = None
     if prof:
-        name, (ms, n) = max(prof.items(), key=lambda kv: kv[1][0])
+        scans = "k_match_tc_min" in prof
+        name, (ms, n) = max(merge_scans(prof).items(), key=lambda kv: kv[1][0])
         rl = {"kernel": name, "ms_per_step_serial": round(ms, 3), "launches": n,
-              "note": "per-kernel times from one iteration with the size classes serialised"}
+              "note": "per-kernel times from one iteration with the size classes serialised"
+                      + ("; k_match_tc = minima scan + bound + candidate scan" if scans and name == "k_match_tc" else "")}
         if name == "k_match_tc":
             work = 2.0 * cfg.bands * cfg.P * cfg.P * pairs
             rl.update({"bound": "tensor", "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
@@ -1050,7 +1074,7 @@ def main() -> None:
     ap.add_argument("--ablation", action="store_true",
                     help="print the matching-strategy comparison (GM vs block matching) instead of the bench line")
     ap.add_argument("--match-schedule", default="",
-                    help="k_over,splits,cap,epi_batch: a fixed matching schedule instead of the autotuner's")
+                    help="k_over,splits,cap,epi_batch[,bound_pass]: a fixed matching schedule instead of the autotuner's")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "glr":
         args.warmup = 3

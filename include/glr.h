@@ -105,7 +105,8 @@ typedef struct glr_match_opts {
                            position grid at its borders; K <= (2w+1)^2 */
   int32_t bound_pass;   /* tensor-core scorer: run a first scan that only records score
                            minima, and start the candidate scan from the bound they give;
-                           1 = on, -1 = off, 0 = automatic */
+                           1 = on, -1 = off, 0 = automatic (on when d <= 74, i.e. one
+                           64-column chunk per operand row).  The matches do not change */
 } glr_match_opts;
 
 /* Operation codes for glr_workspace_size. */
@@ -163,9 +164,12 @@ glr_status glr_select_keys_mixed(const float* x, const glr_images* im, float edg
  *   keys     int32 [n_img][N] position ids (from glr_select_keys or the caller).
  *   n_found  int32 [n_img] valid keys per image (<= N); rows beyond are not written.
  *   K        matches per key, 1 <= K <= 128, K <= Hq*Wq.
- *   modes    GLR_MATCH_FP32: d = C*P*P <= 256 and P <= 8; GLR_MATCH_BF16: d <= 74;
+ *   modes    GLR_MATCH_FP32: d = C*P*P <= 256 and P <= 8; GLR_MATCH_BF16: d <= 640;
  *            GLR_MATCH_LEARNED: d <= 64; GLR_MATCH_EDGE: 4 C P^2 <= 640
  *            (GLR_ENOTSUP / GLR_EINVAL otherwise).
+ *            FP32, BF16 and LEARNED select K' = k_over candidates per key by
+ *            the scorer's value (FP32 or BF16 expanded-form distance, embedding
+ *            distance; ties to smaller ids) and re-rank exactly those K'.
  *            With GLR_MATCH_EDGE, idx is ordered by descending heat-map value H
  *            (ties by smaller id) and dist receives H (an integer count).
  *   idx      out, int32 [n_img][N][K]: the K positions with the smallest

@@ -11,8 +11,9 @@
 //   scorer         FP32 (k_match_fp32, below) or BF16 tcgen05 (k_match_tc.cu):
 //                  scores of 128 keys x all positions of a split, pushed
 //                  through the running top-K' streams (topk_stream.cuh)
-//   k_rerank       per key: exact FP32 sum((p-q)^2) of every kept candidate,
-//                  sort by (distance, id), emit the K best.
+//   k_rerank       per key: the K' best stream scores over all the key's
+//                  streams (ties to smaller ids), their exact FP32
+//                  sum((p-q)^2), sort by (distance, id), emit the K best.
 #include <cooperative_groups.h>
 
 #include "glr_kernels.cuh"
@@ -288,13 +289,91 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 // ---------------------------------------------------------------------------
-// Exact re-rank: one warp per key.  Candidates of every stream of the key are
-// scored with the direct FP32 sum((p - q)^2) (fixed order over the vector
-// index), then sorted by (distance, position id) with a bitonic sort in shared
-// memory; the first K are written.
+// Exact re-rank: one warp per key.  The K' candidates with the best stream
+// scores over every stream of the key are scored with the direct FP32
+// sum((p - q)^2) (fixed order over the vector index), then sorted by
+// (distance, position id) with a bitonic sort in shared memory; the first K are
+// written.
 // ---------------------------------------------------------------------------
 constexpr int RR_WARPS = 4;
 constexpr int kRerankMaxList = 2048;  // candidates of one key held by the re-rank (pow2)
+
+// A threshold T with exactly `rank` of the n distinct 64-bit keys <= T: the
+// rank-th smallest key, or the upper end of its radix bin when that key is the
+// largest of the bin (MSB radix select, 8 bits per pass, stopping early; one
+// warp, 256 shared counters).
+__device__ unsigned long long warp_select_kth(const unsigned long long* list, int n, int rank, unsigned* hist,
+                                              int lane) {
+  unsigned long long prefix = 0, pmask = 0;
+  for (int pass = 0; pass < 8; ++pass) {
+    const int shift = 56 - 8 * pass;
+    for (int i = lane; i < 256; i += 32) hist[i] = 0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const unsigned long long e = list[i];
+      if ((e & pmask) == prefix) atomicAdd(&hist[(e >> shift) & 255u], 1u);
+    }
+    __syncwarp();
+    int loc[8], sum = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      loc[t] = (int)hist[lane * 8 + t];
+      sum += loc[t];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int yv = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += yv;
+    }
+    const int excl = incl - sum;
+    const int owner = __ffs(__ballot_sync(0xffffffffu, excl < rank && rank <= incl)) - 1;
+    int sel = 0, before = 0, in_bin = 0;
+    if (lane == owner) {
+      int c = excl;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (c + loc[t] >= rank) {
+          sel = lane * 8 + t;
+          before = c;
+          in_bin = loc[t];
+          break;
+        }
+        c += loc[t];
+      }
+    }
+    sel = __shfl_sync(0xffffffffu, sel, owner);
+    before = __shfl_sync(0xffffffffu, before, owner);
+    in_bin = __shfl_sync(0xffffffffu, in_bin, owner);
+    rank -= before;
+    prefix |= (unsigned long long)sel << shift;
+    pmask |= 255ull << shift;
+    __syncwarp();
+    // the wanted key is the largest of its bin: every key of the bin is kept, so
+    // the bin's upper end is the answer (exactly rank keys lie below it)
+    if (rank == in_bin) return prefix | ((1ull << shift) - 1ull);
+  }
+  return prefix;
+}
+
+// Keep the k smallest of n distinct keys (k < n), compacted to the front of the
+// list in their current order; returns k.
+__device__ int warp_keep_smallest(unsigned long long* list, int n, int k, unsigned* hist, int lane) {
+  const unsigned long long T = warp_select_kth(list, n, k, hist, lane);
+  int out = 0;
+  const unsigned ltm = (1u << lane) - 1u;
+  for (int base = 0; base < n; base += 32) {
+    const int i = base + lane;
+    const unsigned long long e = i < n ? list[i] : ~0ull;
+    const bool keep = i < n && e <= T;
+    const unsigned km = __ballot_sync(0xffffffffu, keep);
+    __syncwarp();
+    if (keep) list[out + __popc(km & ltm)] = e;
+    out += __popc(km);
+    __syncwarp();
+  }
+  return out;
+}
 
 __global__ void __launch_bounds__(RR_WARPS * 32)
     k_rerank(const float* __restrict__ x, const int32_t* __restrict__ keys, const int32_t* __restrict__ n_found,
@@ -338,14 +417,19 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
       const uint2* b = bufs + (s0 + sidx) * cap_slots;
       for (int i = lane; i < n; i += 32) {
         const uint2 e = b[i];
-        list[total + i] = exact_scores ? (((unsigned long long)e.x << 32) | e.y) : e.y;
+        list[total + i] = ((unsigned long long)e.x << 32) | e.y;  // (stream score, id)
       }
       total += n;
     }
     __syncwarp();
+    unsigned* hist = reinterpret_cast<unsigned*>(pv + dpad);  // 256 counters after the key patch
+    // the kp best stream scores over all streams of the key (ties to smaller ids):
+    // which extra candidates the streams kept depends on when bounds were
+    // published, so only these kp are re-ranked
+    if (window == 0 && !exact_scores && total > kp) total = warp_keep_smallest(list, total, kp, hist, lane);
     // exact FP32 distances, summed in a fixed order over the vector index
     for (int i = lane; !exact_scores && i < total; i += 32) {
-      const int q = (int)list[i];
+      const int q = (int)(unsigned)(list[i] & 0xffffffffull);
       const int r = q / Wq, c = q - (q / Wq) * Wq;
       float acc = 0.f;
       for (int ch = 0; ch < C; ++ch)
@@ -362,72 +446,7 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
     __syncwarp();
     // select the K smallest (distance, id) pairs with an MSB radix select over the
     // 64-bit keys, then sort those K (bitonic); ties in distance go to smaller ids
-    unsigned long long T = ~0ull;
-    if (total > K) {
-      unsigned* hist = reinterpret_cast<unsigned*>(pv + dpad);  // 256 counters after the key patch
-      unsigned long long prefix = 0, pmask = 0;
-      int rank = K;  // 1-based rank of the wanted key among those matching the prefix
-      for (int pass = 0; pass < 8; ++pass) {
-        const int shift = 56 - 8 * pass;
-        for (int i = lane; i < 256; i += 32) hist[i] = 0;
-        __syncwarp();
-        for (int i = lane; i < total; i += 32) {
-          const unsigned long long e = list[i];
-          if ((e & pmask) == prefix) atomicAdd(&hist[(e >> shift) & 255u], 1u);
-        }
-        __syncwarp();
-        int loc[8], sum = 0;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          loc[t] = (int)hist[lane * 8 + t];
-          sum += loc[t];
-        }
-        int incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int yv = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += yv;
-        }
-        const int excl = incl - sum;
-        const int owner = __ffs(__ballot_sync(0xffffffffu, excl < rank && rank <= incl)) - 1;
-        int sel = 0, before = 0;
-        if (lane == owner) {
-          int c = excl;
-#pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            if (c + loc[t] >= rank) {
-              sel = lane * 8 + t;
-              before = c;
-              break;
-            }
-            c += loc[t];
-          }
-        }
-        sel = __shfl_sync(0xffffffffu, sel, owner);
-        before = __shfl_sync(0xffffffffu, before, owner);
-        rank -= before;
-        prefix |= (unsigned long long)sel << shift;
-        pmask |= 255ull << shift;
-        __syncwarp();
-      }
-      T = prefix;  // keys are unique (ids differ): exactly K entries are <= T
-    }
-    // compact the selected entries to the front, then sort them
-    {
-      int out = 0;
-      const unsigned ltm = (1u << lane) - 1u;
-      for (int base = 0; base < total; base += 32) {
-        const int i = base + lane;
-        const unsigned long long e = i < total ? list[i] : ~0ull;
-        const bool keep = i < total && e <= T;
-        const unsigned km = __ballot_sync(0xffffffffu, keep);
-        __syncwarp();
-        if (keep) list[out + __popc(km & ltm)] = e;
-        out += __popc(km);
-        __syncwarp();
-      }
-      total = out;
-    }
+    if (total > K) total = warp_keep_smallest(list, total, K, hist, lane);
     int p2 = 32;
     while (p2 < total) p2 <<= 1;
     for (int i = total + lane; i < p2; i += 32) list[i] = ~0ull;
@@ -522,9 +541,11 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
     pl.npos_pad = (long long)pl.pos_tiles * pl.pos_tile;
     pl.qpack_off = L.take((size_t)im.n_img * pl.npos_pad * dk * 2);
     pl.kpack_off = L.take((size_t)im.n_img * pl.Npad * dk * 2);
-    // the bound of the minima scan needs Kp half tiles; automatic: on
+    // the bound of the minima scan needs Kp half tiles.  Automatic: on for one-chunk
+    // rows, where the candidate appends cost more than a second contraction; off for
+    // chunked rows (d > 74), where the contraction itself dominates
     const int bp = o ? o->bound_pass : 0;
-    pl.bound_pass = (bp >= 0 && 2LL * pl.pos_tiles >= pl.Kp) ? 1 : 0;
+    pl.bound_pass = ((bp > 0 || (bp == 0 && pl.nkc == 1)) && 2LL * pl.pos_tiles >= pl.Kp) ? 1 : 0;
     if (pl.bound_pass) pl.mins_off = L.take((size_t)im.n_img * pl.Npad * 2 * pl.pos_tiles * 4);
   }
   if (edge) pl.edge_off = L.take((size_t)im.n_img * 4 * im.C * im.H * im.W * 4);

@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(256) k_seed_bounds(const __nv_bfloat16* __rest
   }
 }
 
-template <int EB, bool WIDE>
+template <int EB, bool WIDE, bool MINS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_match_tc(const __grid_constant__ CUtensorMap tm_qmain, const __grid_constant__ CUtensorMap tm_qaux,
                const __grid_constant__ CUtensorMap tm_kmain, const __grid_constant__ CUtensorMap tm_kaux,
@@ -610,9 +610,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                int tiles_per_split, int ntiles, int nkc, StreamCfg cfg, uint2* __restrict__ bufs,
                int* __restrict__ buf_cnt, uint32_t* __restrict__ tau_gl, StatusBlock* st, float* __restrict__ dump,
                float* __restrict__ mins) {
-  // mins != nullptr: bound pass.  No candidate is kept; each epilogue lane writes the
-  // minimum score of its row over every half tile (128 positions) to
-  // mins[key][2 tile + half] instead.
+  // MINS: bound pass.  No candidate is kept; each epilogue lane writes the minimum
+  // score of its row over every half tile (128 positions) to mins[key][2 tile + half]
+  // instead (all four 32-column chunks read from TMEM in one visit).
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t kBar = WIDE ? W_OFF_BAR : OFF_BAR, kMisc = WIDE ? W_OFF_MISC : OFF_MISC;
@@ -812,9 +812,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) break;
       tc_fence_after();
       const long long tile_q0 = (long long)(t_begin + i) * TC_N;
+      if constexpr (MINS) {
+        float w[4][32], v[128];
+        const uint32_t taddr = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tmem_ld_32x32_nowait(taddr + 32 * c, w[c]);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 128; ++j) v[j] = w[j >> 5][j & 31];
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty + b);
+        const int nvalid = (int)max(0LL, min(128LL, npos - (tile_q0 + h * 128)));
+        if (nvalid < 128) {
+#pragma unroll
+          for (int j = 0; j < 128; ++j) v[j] = j < nvalid ? v[j] : INFINITY;
+        }
+        mins[(((long long)f * Npad + key) * ntiles + t_begin + i) * 2 + h] = min_tree3(v);
+        continue;
+      }
       const uint32_t gl = gl_next;
       gl_next = *reinterpret_cast<volatile uint32_t*>(pub_gl + lane);
-      float mrun = INFINITY;  // bound pass: minimum of this lane's row over the half tile
       // EB chunks of 32 columns are read from TMEM per visit; the buffer goes back to
       // the MMA warp after the last visit (EB = 4: one visit, earliest release)
 #pragma unroll 1
@@ -841,10 +859,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j) dump[((long long)f * Npad + key) * TC_N + col + j] = v[c][j];
           }
-          if (mins != nullptr) {
-            mrun = fminf(mrun, stream_min(v[c], nvalid));
-            continue;
-          }
           const float te = stream_tau_eff(tau, *reinterpret_cast<volatile uint32_t*>(pub_sh + lane), gl);
           const unsigned rows = stream_filter(v[c], nvalid, te);
           if (rows) {
@@ -856,9 +870,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
-      if (mins != nullptr) mins[(((long long)f * Npad + key) * ntiles + t_begin + i) * 2 + h] = mrun;
     }
-    if (mins == nullptr) {
+    if constexpr (!MINS) {
       stream_finish(tau, cnt, mybuf, cfg, whist);
       stream_stats_flush(stats, st);
       buf_cnt[stream] = (key < nf) ? cnt : 0;
@@ -960,7 +973,11 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
         !make_map(&tk, kmain, krows, wcols, TC_M, CU_TENSOR_MAP_SWIZZLE_128B, DK_MAIN) ||
         !make_map(&tka, kaux, krows, DK_AUX, TC_M, CU_TENSOR_MAP_SWIZZLE_32B))
       return GLR_ECUDA;
-    auto kern = pl.epi_batch == 2 ? k_match_tc<2, true> : k_match_tc<4, true>;
+    auto kern = pl.epi_batch == 2 ? k_match_tc<2, true, false> : k_match_tc<4, true, false>;
+    auto kmin = k_match_tc<4, true, true>;
+    if (pl.bound_pass &&
+        cudaFuncSetAttribute(kmin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W_SMEM) != cudaSuccess)
+      return GLR_ECUDA;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W_SMEM) != cudaSuccess)
       return GLR_ECUDA;
     int blocks_per_sm = 0;
@@ -972,7 +989,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
     dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
     if (pl.bound_pass) {
       GLR_LAUNCH("k_match_tc_min", s,
-                 kern<<<grid, TC_THREADS, W_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
+                 kmin<<<grid, TC_THREADS, W_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
                                                        pl.splits, pl.tiles_per_split, pl.pos_tiles, pl.nkc, cfg, bufs,
                                                        bufcnt, taugl, st, nullptr, mins));
       const glr_status bs = launch_tau_bound(mins, n_found, im.n_img, seed_N, pl, taugl, s);
@@ -1020,7 +1037,11 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
       !make_map(&tk, kmain, krows, DK_MAIN, TC_M, CU_TENSOR_MAP_SWIZZLE_128B) ||
       !make_map(&tka, kaux, krows, DK_AUX, TC_M, CU_TENSOR_MAP_SWIZZLE_32B))
     return GLR_ECUDA;
-  auto kern = pl.epi_batch == 2 ? k_match_tc<2, false> : k_match_tc<4, false>;
+  auto kern = pl.epi_batch == 2 ? k_match_tc<2, false, false> : k_match_tc<4, false, false>;
+  auto kmin = k_match_tc<4, false, true>;
+  if (pl.bound_pass &&
+      cudaFuncSetAttribute(kmin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) != cudaSuccess)
+    return GLR_ECUDA;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) != cudaSuccess)
     return GLR_ECUDA;
   {
@@ -1034,7 +1055,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
   if (pl.bound_pass && dump == nullptr) {
     GLR_LAUNCH("k_match_tc_min", s,
-               kern<<<grid, TC_THREADS, TC_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
+               kmin<<<grid, TC_THREADS, TC_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
                                                       pl.splits, pl.tiles_per_split, pl.pos_tiles, 1, cfg, bufs,
                                                       bufcnt, taugl, st, nullptr, mins));
     const glr_status bs = launch_tau_bound(mins, n_found, im.n_img, seed_N, pl, taugl, s);

@@ -212,25 +212,43 @@ __device__ __forceinline__ float stream_tau_eff(float tau_own, uint32_t pub_shar
   return fminf(tau_own, float_from_order_key(min(pub_shared, pub_global)));  // 0xffffffff decodes to NaN: ignored
 }
 
+// Three-input minimum (one instruction on sm_100 and later).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Minimum of N register values as a tree of three-input minima: about N / 2
+// instructions, depth log3(N).
+template <int N>
+__device__ __forceinline__ float min_tree3(const float (&a)[N]) {
+  if constexpr (N == 1) {
+    return a[0];
+  } else if constexpr (N == 2) {
+    return fminf(a[0], a[1]);
+  } else {
+    constexpr int M = (N + 2) / 3;
+    float b[M];
+#pragma unroll
+    for (int j = 0; j < N / 3; ++j) b[j] = fmin3(a[3 * j], a[3 * j + 1], a[3 * j + 2]);
+    if constexpr (N % 3 == 1) b[N / 3] = a[N - 1];
+    if constexpr (N % 3 == 2) b[N / 3] = fminf(a[N - 2], a[N - 1]);
+    return min_tree3<M>(b);
+  }
+}
+
 // Step 1 of a chunk push: rows (bit r = lane r) whose 32 scores contain one
 // below their tau.  s = this lane's row scores, column j = position q0 + j;
 // columns j >= nvalid do not exist.
 __device__ __forceinline__ float stream_min(const float (&s)[32], int nvalid) {
-  // tree-shaped minimum: depth 5 instead of a 31-long dependency chain
-  float m[16];
   if (nvalid < 32) {
+    float m[32];
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
-      m[j] = fminf(j < nvalid ? s[j] : INFINITY, j + 16 < nvalid ? s[j + 16] : INFINITY);
-  } else {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) m[j] = fminf(s[j], s[j + 16]);
+    for (int j = 0; j < 32; ++j) m[j] = j < nvalid ? s[j] : INFINITY;
+    return min_tree3(m);
   }
-#pragma unroll
-  for (int w = 8; w > 0; w >>= 1)
-#pragma unroll
-    for (int j = 0; j < w; ++j) m[j] = fminf(m[j], m[j + w]);
-  return m[0];
+  return min_tree3(s);
 }
 
 __device__ __forceinline__ unsigned stream_filter(const float (&s)[32], int nvalid, float tau) {

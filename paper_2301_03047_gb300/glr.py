@@ -323,7 +323,7 @@ class GlrDenoiser:
 
     def __init__(self, shape: GlrShape, mode: str = "bf16", edge_th: float = 0.1, k_over: int = 0, splits: int = 0,
                  device="cuda", cap: int = 0, epi_batch: int = 0, complex_: bool = False, n_uniform: int = 0,
-                 window: int = 20, fused: bool = False):
+                 window: int = 20, fused: bool = False, bound_pass: int = 0):
         """fused (real images, d <= 64, K <= 64): grouping, WNNM and aggregation in one kernel pass
         (glr_lowrank_aggregate): no group buffer (1 GB less on the 16 x 512^2 workload) but slower
         there (16.6 ms against 11.9 ms for the three separate kernels: the fused kernel's per-lane
@@ -334,8 +334,9 @@ class GlrDenoiser:
         self.n_uniform, self.window = n_uniform, window
         can_fuse = not complex_ and s.C * s.P * s.P <= 64 and s.K <= 64
         self.fused = fused and can_fuse
-        self.opts = match_opts(mode, k_over, splits, cap, None, epi_batch, edge_th, window)
+        self.opts = match_opts(mode, k_over, splits, cap, None, epi_batch, edge_th, window, bound_pass)
         self.k_over, self.splits, self.cap, self.epi_batch = k_over, splits, cap, epi_batch
+        self.bound_pass = bound_pass
         im = images(s.n_img, s.C, s.H, s.W, s.P)
         dev = torch.device(device)
         d = s.C * s.P * s.P
@@ -359,7 +360,8 @@ class GlrDenoiser:
         select_keys(x, s.P, s.N, self.edge_th, n_uniform=self.n_uniform, keys=self.keys, n_found=self.n_found,
                     n_corner=self.n_corner, ws=self.ws_select, stream=stream)
         match_topk(x, s.P, self.keys, self.n_found, s.K, self.mode, k_over=self.k_over, splits=self.splits,
-                   cap=self.cap, epi_batch=self.epi_batch, edge_th=self.edge_th, window=self.window, idx=self.idx,
+                   cap=self.cap, epi_batch=self.epi_batch, edge_th=self.edge_th, window=self.window,
+                   bound_pass=self.bound_pass, idx=self.idx,
                    dist=self.dist, ws=self.ws_match, stream=stream)
         if self.fused:
             return lowrank_aggregate(x, s.P, self.idx, self.n_found, sigma_w, c_wnnm, out=out, rank=self.rank,
@@ -373,12 +375,12 @@ class SciReconstructor:
     """GAP + GLR for one video snapshot y = sum_t M_t x_t (Eq. 6); frames are the images."""
 
     def __init__(self, T, H, W, P, N, K, mode="bf16", edge_th=0.1, accelerate=False, k_over=0, splits=0,
-                 device="cuda", cap=0, epi_batch=0, admm_rho=0.0, n_uniform=0, window=20):
+                 device="cuda", cap=0, epi_batch=0, admm_rho=0.0, n_uniform=0, window=20, bound_pass=0):
         """admm_rho > 0: ADMM (z = D(x + u), u += x - z, x = the data step) instead of GAP;
         n_uniform > 0: corner + uniform key mix."""
         self.T, self.H, self.W = T, H, W
         self.den = GlrDenoiser(GlrShape(T, 1, H, W, P, N, K), mode, edge_th, k_over, splits, device, cap, epi_batch,
-                               n_uniform=n_uniform, window=window)
+                               n_uniform=n_uniform, window=window, bound_pass=bound_pass)
         self.accelerate = accelerate
         self.rho = admm_rho
         self.x = torch.empty((1, T, H, W), dtype=torch.float32, device=device)
@@ -459,10 +461,10 @@ class MriReconstructor:
     z (denoiser output); all [1][2][H][W] (real, imaginary planes)."""
 
     def __init__(self, H, W, P, N, K, mode="bf16", edge_th=0.1, rho=0.5, k_over=0, splits=0, device="cuda",
-                 cap=0, epi_batch=0):
+                 cap=0, epi_batch=0, bound_pass=0):
         self.H, self.W, self.rho = H, W, rho
         self.den = GlrDenoiser(GlrShape(1, 2, H, W, P, N, K), mode, edge_th, k_over, splits, device, cap, epi_batch,
-                               complex_=True)
+                               complex_=True, bound_pass=bound_pass)
         z = lambda: torch.zeros((1, 2, H, W), dtype=torch.float32, device=device)
         self.x, self.u, self.w, self.z = z(), z(), z(), z()
         self.residual = torch.zeros(1, dtype=torch.float64, device=device)
@@ -526,9 +528,9 @@ class MsfaBatchReconstructor:
         for i, (sd, n) in enumerate(zip(sides, Ns)):
             order.setdefault((int(sd), int(n)), []).append(i)
         for (sd, n), ids in sorted(order.items()):
-            kw = (tuned or {}).get((sd, n), (0, 0, 0, 0))
+            kw = tuple((tuned or {}).get((sd, n), ())) + (0,) * 5
             den = GlrDenoiser(GlrShape(len(ids), bands, sd, sd, P, n, K), mode, edge_th, kw[0], kw[1], device, kw[2],
-                              kw[3])
+                              kw[3], bound_pass=kw[4])
             x = torch.empty((len(ids), bands, sd, sd), dtype=torch.float32, device=device)
             self.classes.append({"side": sd, "ids": ids, "N": n, "den": den, "stream": torch.cuda.Stream(device=device),
                                  "x": x, "v": torch.empty_like(x)})
@@ -585,7 +587,7 @@ _TUNE_CACHE: dict = {}
 
 
 def autotune_match(x, P, keys, n_found, K, mode="bf16", candidates=None, repeats=2, cache_path=None):
-    """Return the fastest (k_over, splits, cap, epi_batch) for this shape; K' stays >= K + 16."""
+    """Return the fastest (k_over, splits, cap, epi_batch, bound_pass) for this shape; K' stays >= K + 16."""
     import json
     import os
 
@@ -596,28 +598,31 @@ def autotune_match(x, P, keys, n_found, K, mode="bf16", candidates=None, repeats
         return tuple(_TUNE_CACHE[shape_key])
     if candidates is None:
         eb = (2, 4) if mode != "fp32" else (0,)
-        candidates = [(K + 16, sp, cap, e) for sp in (1, 2, 3) for cap in (0, 192, 320) for e in eb]
-    candidates = [tuple(c) + (0,) * (4 - len(c)) for c in candidates]
+        bp = (1, -1) if mode != "fp32" else (0,)
+        candidates = [(K + 16, sp, cap, e, b) for sp in (1, 2, 3) for cap in (0, 192, 320) for e in eb for b in bp]
+    candidates = [tuple(c) + (0,) * (5 - len(c)) for c in candidates]
     im = images_of(x, P)
     best, best_t = None, float("inf")
-    kname = "k_match_tc" if mode == "bf16" else "k_match_fp32"
-    for kover, sp, cap, eb in candidates:
-        o = match_opts(mode, kover, sp, cap, None, eb)
+    timed = ("k_match_tc", "k_match_tc_min", "k_tau_bound", "k_match_fp32", "k_rerank", "k_seed_bounds")
+    for kover, sp, cap, eb, bp in candidates:
+        o = match_opts(mode, kover, sp, cap, None, eb, bound_pass=bp)
         try:
             ws = workspace(L.GLR_OP_MATCH, im, keys.shape[1], K, o, x.device)
-            match_topk(x, P, keys, n_found, K, mode, k_over=kover, splits=sp, cap=cap, epi_batch=eb, ws=ws)
+            match_topk(x, P, keys, n_found, K, mode, k_over=kover, splits=sp, cap=cap, epi_batch=eb, bound_pass=bp,
+                       ws=ws)
         except GlrError:
             continue
         torch.cuda.synchronize()
         profile_enable(True)
         profile_collect()
         for _ in range(repeats):
-            match_topk(x, P, keys, n_found, K, mode, k_over=kover, splits=sp, cap=cap, epi_batch=eb, ws=ws)
+            match_topk(x, P, keys, n_found, K, mode, k_over=kover, splits=sp, cap=cap, epi_batch=eb, bound_pass=bp,
+                       ws=ws)
         prof = profile_collect()
         profile_enable(False)
-        t = sum(v[0] for k, v in prof.items() if k in (kname, "k_rerank", "k_seed_bounds"))
+        t = sum(v[0] for k, v in prof.items() if k in timed)
         if t < best_t:
-            best, best_t = (kover, sp, cap, eb), t
+            best, best_t = (kover, sp, cap, eb, bp), t
         del ws
     _TUNE_CACHE[shape_key] = list(best)
     if cache_path:

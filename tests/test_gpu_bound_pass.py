@@ -1,0 +1,83 @@
+"""Tensor-core matching with and without the minima scan.
+
+The minima scan records, per key, the minimum BF16 score of every half tile
+(128 positions); the K'-th smallest of those minima bounds the K'-th smallest
+score of the key, and the candidate scan starts from that bound.  The bound
+only removes candidates that cannot be among the K' smallest scores, so the
+matches must not change: the reported distances are equal element by element
+with the scan on and off, and the ids agree except among exactly tied
+distances.  Cases: one and several position splits, a ragged last position
+tile, several images, the chunked operand rows of wide patches (d > 74), and
+the learned and heat-map proposals.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2301_03047_gb300 import glr, synth  # noqa: E402
+
+
+def run(x, P, keys, nf, K, mode, bound_pass, **kw):
+    idx, dist = glr.match_topk(x, P, keys, nf, K, mode, bound_pass=bound_pass, **kw)
+    torch.cuda.synchronize()
+    return idx.cpu().numpy(), dist.cpu().numpy()
+
+
+def same_matches(a, b):
+    (ia, da), (ib, db) = a, b
+    np.testing.assert_array_equal(da, db)
+    # ids: equal as sets within every run of equal distances
+    for f in range(ia.shape[0]):
+        for k in range(ia.shape[1]):
+            if not np.array_equal(ia[f, k], ib[f, k]):
+                for v in np.unique(da[f, k]):
+                    sel = da[f, k] == v
+                    assert set(ia[f, k][sel]) == set(ib[f, k][sel]), (f, k, v)
+
+
+def frames(tag, F, C, H, W):
+    rng = synth.rng_for(tag)
+    x = np.stack([synth.textured_frames(rng, F, H, W) for _ in range(C)], axis=1).astype(np.float32)
+    return torch.from_numpy(x).cuda()
+
+
+@pytest.mark.parametrize("splits", [1, 2, 3])
+def test_bound_pass_keeps_matches_narrow(splits):
+    x = frames("bp_narrow", 2, 1, 200, 230)  # 193 x 223 positions: ragged last tile
+    P, N, K = 8, 300, 40
+    keys, nf, _ = glr.select_keys(x, P, N, 0.05)
+    on = run(x, P, keys, nf, K, "bf16", 1, splits=splits)
+    off = run(x, P, keys, nf, K, "bf16", -1, splits=splits)
+    same_matches(on, off)
+
+
+def test_bound_pass_keeps_matches_two_channels():
+    x = frames("bp_c2", 1, 2, 150, 170)
+    P, N, K = 6, 256, 48
+    keys, nf, _ = glr.select_keys(x, P, N, 0.05)
+    same_matches(run(x, P, keys, nf, K, "bf16", 1, k_over=64), run(x, P, keys, nf, K, "bf16", -1, k_over=64))
+
+
+def test_bound_pass_keeps_matches_wide():
+    x = frames("bp_wide", 2, 16, 96, 104)  # d = 16 x 36 = 576: chunked operand rows
+    P, N, K = 6, 128, 32
+    keys, nf, _ = glr.select_keys(x, P, N, 0.05)
+    same_matches(run(x, P, keys, nf, K, "bf16", 1), run(x, P, keys, nf, K, "bf16", -1))
+
+
+def test_bound_pass_keeps_matches_edge_heatmap():
+    x = frames("bp_edge", 1, 1, 140, 150)
+    P, N, K = 8, 200, 32
+    keys, nf, _ = glr.select_keys(x, P, N, 0.05)
+    same_matches(run(x, P, keys, nf, K, "edge", 1, edge_th=0.05), run(x, P, keys, nf, K, "edge", -1, edge_th=0.05))
+
+
+def test_bound_pass_keeps_matches_learned():
+    x = frames("bp_learned", 1, 1, 300, 300)  # K' = 256 needs at least 128 position tiles
+    P, N, K = 8, 128, 32
+    keys, nf, _ = glr.select_keys(x, P, N, 0.05)
+    enc = glr.Encoder(seed=3)
+    kw = dict(encoder=enc.params)
+    same_matches(run(x, P, keys, nf, K, "learned", 1, **kw), run(x, P, keys, nf, K, "learned", -1, **kw))

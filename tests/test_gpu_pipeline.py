@@ -39,12 +39,12 @@ def test_autotune_picks_a_working_schedule():
     cfg, prob, y, m = _problem(T=2, H=128, W=128, N=200, K=32)
     x = glr.gap_step(y[None], m, None).view(cfg.T, 1, cfg.H, cfg.W).contiguous()
     keys, nf, _ = glr.select_keys(x, cfg.P, cfg.N)
-    cands = [(48, 1, 0, 4), (48, 2, 192, 2), (64, 1, 320, 4)]
+    cands = [(48, 1, 0, 4, 1), (48, 2, 192, 2, -1), (64, 1, 320, 4, 1), (48, 2, 0, 2, 1)]
     best = glr.autotune_match(x, cfg.P, keys, nf, cfg.K, "bf16", candidates=cands)
     assert best in cands
     ref, _ = glr.match_topk(x, cfg.P, keys, nf, cfg.K, "fp32")
     got, _ = glr.match_topk(x, cfg.P, keys, nf, cfg.K, "bf16", k_over=best[0], splits=best[1], cap=best[2],
-                            epi_batch=best[3])
+                            epi_batch=best[3], bound_pass=best[4])
     a, b = ref.cpu().numpy(), got.cpu().numpy()
     same = np.mean([len(set(a[f, k]) & set(b[f, k])) / cfg.K for f in range(cfg.T) for k in range(cfg.N)])
     assert same >= 0.99
