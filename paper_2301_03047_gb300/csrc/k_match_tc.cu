@@ -57,11 +57,15 @@ constexpr uint32_t OFF_BAR = OFF_B_AUX + TC_STAGES * B_AUX_BYTES;  // 8-byte bar
 constexpr int NBAR = 2 * TC_STAGES + 4 + 2;                        // full, empty, tmem_full x2, tmem_empty x2, a_full, mma_done
 constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;                  // tmem base, abort flag
 constexpr uint32_t OFF_HIST = (OFF_MISC + 64 + 15) / 16 * 16;
-constexpr int TILE_LD = 33;  // per-warp 32 x 32 score tile for the row-wise append
+// per-warp 32 x 32 score tile for the row-wise append: rows written as eight 16-byte
+// stores (a stride of 36 words keeps each quarter-warp phase on distinct banks), read
+// one row per instruction
+constexpr int TILE_LD = 36;
 constexpr uint32_t OFF_TILE = OFF_HIST + TC_EPI_WARPS * 256 * 4;
 constexpr uint32_t OFF_TAU = OFF_TILE + TC_EPI_WARPS * 32 * TILE_LD * 4;  // published thresholds of the 128 rows
 constexpr uint32_t TC_SMEM = OFF_TAU + TC_M * 4 + 1024;                   // + alignment slack
 static_assert(TC_SMEM <= 232448, "shared memory budget");
+static_assert(OFF_TILE % 16 == 0 && (TILE_LD * 4) % 16 == 0, "16-byte aligned tile rows");
 // Wide operands (d > 74): the key tile no longer fits next to a position ring, so
 // every 64-column chunk of keys and positions streams through a 3-stage ring of
 // (A chunk, B chunk) pairs; the 16 norm columns come last as a 16-column chunk.
@@ -863,7 +867,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const unsigned rows = stream_filter(v[c], nvalid, te);
           if (rows) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) wtile[lane * TILE_LD + j] = v[c][j];
+            for (int j = 0; j < 8; ++j)
+              reinterpret_cast<float4*>(wtile + lane * TILE_LD)[j] =
+                  make_float4(v[c][4 * j], v[c][4 * j + 1], v[c][4 * j + 2], v[c][4 * j + 3]);
             __syncwarp();
             stream_append(rows, wtile, TILE_LD, (int)q0, nvalid, te, tau, cnt, mybuf, cfg, whist, pub_sh, pub_gl,
                           stats);
