@@ -55,17 +55,21 @@ __global__ void __launch_bounds__(256) k_gather(const float* __restrict__ x, int
   }
 }
 
-// One Jacobi rotation of the column pair (a, b) held by this lane.  alpha / beta
-// are the tracked squared norms of a / b (updated exactly as the rotation
-// changes them: alpha - t gamma, beta + t gamma); only gamma = a.b is summed.
+// One Jacobi rotation of the column pair held by this lane.  The columns are kept
+// scaled: the true columns are da a and db b.  A rotation by (c, s) = c (1, t) of
+// the true columns is then a shear of the stored ones plus the factor c on both
+// scales (a' = a - t (db / da) b, b' = b + t (da / db) a, da' = c da, db' = c db):
+// two FMAs per row instead of four operations.  alpha / beta are the tracked
+// squared norms of the true columns (updated exactly as the rotation changes
+// them: alpha - t gamma, beta + t gamma); only gamma = da db (a.b) is summed.
 template <int DMAX>
-__device__ __forceinline__ void jacobi_pair(float (&a)[DMAX], float (&b)[DMAX], float& alpha, float& beta, float tol,
-                                            float lam_skip, float lam, float& acc_a, float& acc_b, bool active,
-                                            bool& rotated) {
+__device__ __forceinline__ void jacobi_pair(float (&a)[DMAX], float (&b)[DMAX], float& da, float& db, float& alpha,
+                                            float& beta, float tol, float lam_skip, float lam, float& acc_a,
+                                            float& acc_b, bool active, bool& rotated) {
   float ga[4] = {0.f, 0.f, 0.f, 0.f};  // four partial sums shorten the dependency chain
 #pragma unroll
   for (int r = 0; r < DMAX; ++r) ga[r & 3] = fmaf(a[r], b[r], ga[r & 3]);
-  const float gamma = (ga[0] + ga[1]) + (ga[2] + ga[3]);
+  const float gamma = ((ga[0] + ga[1]) + (ga[2] + ga[3])) * (da * db);
   // Gershgorin sums of the block of columns below lam (see the sweep loop)
   if (beta < lam) acc_a += fabsf(gamma);
   if (alpha < lam) acc_b += fabsf(gamma);
@@ -76,13 +80,15 @@ __device__ __forceinline__ void jacobi_pair(float (&a)[DMAX], float (&b)[DMAX], 
     float t = (az < 1e18f) ? __frcp_rn(az + sqrtf(fmaf(zeta, zeta, 1.f))) : __fdividef(0.5f, az);
     t = copysignf(t, zeta);
     const float cs = rsqrtf(fmaf(t, t, 1.f));
-    const float sn = cs * t;
+    const float ta = t * __fdividef(db, da), tb = t * __fdividef(da, db);
 #pragma unroll
     for (int r = 0; r < DMAX; ++r) {
       const float ar = a[r], br = b[r];
-      a[r] = fmaf(cs, ar, -sn * br);
-      b[r] = fmaf(sn, ar, cs * br);
+      a[r] = fmaf(-ta, br, ar);
+      b[r] = fmaf(tb, ar, br);
     }
+    da *= cs;
+    db *= cs;
     alpha = fmaf(-t, gamma, alpha);
     beta = fmaf(t, gamma, beta);
     rotated = true;
@@ -92,10 +98,12 @@ __device__ __forceinline__ void jacobi_pair(float (&a)[DMAX], float (&b)[DMAX], 
 // Complex columns (real halves in [0, DMAX/2), imaginary halves in [DMAX/2, DMAX)):
 // with g = a^H b = |g| e, rotate (a, conj(e) b) as a real pair:
 // a' = c a - s conj(e) b, b' = s e a + c b, which zeroes a'^H b'.
+// Scaled as the real pair: a' = a - t (db / da) conj(e) b, b' = b + t (da / db) e a,
+// both scales times c (four FMAs per complex row and column instead of eight).
 template <int DMAX>
-__device__ __forceinline__ void jacobi_pair_c(float (&a)[DMAX], float (&b)[DMAX], float& alpha, float& beta,
-                                              float tol, float lam_skip, float lam, float& acc_a, float& acc_b,
-                                              bool& rotated) {
+__device__ __forceinline__ void jacobi_pair_c(float (&a)[DMAX], float (&b)[DMAX], float& da, float& db, float& alpha,
+                                              float& beta, float tol, float lam_skip, float lam, float& acc_a,
+                                              float& acc_b, bool& rotated) {
   constexpr int H2 = DMAX / 2;
   float pr[2] = {0.f, 0.f}, pi[2] = {0.f, 0.f};
 #pragma unroll
@@ -105,7 +113,8 @@ __device__ __forceinline__ void jacobi_pair_c(float (&a)[DMAX], float (&b)[DMAX]
     pi[r & 1] = fmaf(a[r], b[H2 + r], pi[r & 1]);
     pi[r & 1] = fmaf(-a[H2 + r], b[r], pi[r & 1]);
   }
-  const float gr = pr[0] + pr[1], gi = pi[0] + pi[1];
+  const float sab = da * db;
+  const float gr = (pr[0] + pr[1]) * sab, gi = (pi[0] + pi[1]) * sab;
   const float gm = sqrtf(fmaf(gr, gr, gi * gi));
   if (beta < lam) acc_a += gm;
   if (alpha < lam) acc_b += gm;
@@ -115,19 +124,20 @@ __device__ __forceinline__ void jacobi_pair_c(float (&a)[DMAX], float (&b)[DMAX]
     float t = (az < 1e18f) ? __frcp_rn(az + sqrtf(fmaf(zeta, zeta, 1.f))) : __fdividef(0.5f, az);
     t = copysignf(t, zeta);
     const float cs = rsqrtf(fmaf(t, t, 1.f));
-    const float sn = cs * t;
     const float inv = __frcp_rn(gm);
     const float er = gr * inv, ei = gi * inv;
+    const float p = t * __fdividef(db, da), q = t * __fdividef(da, db);
+    const float per = p * er, pei = p * ei, qer = q * er, qei = q * ei;
 #pragma unroll
     for (int r = 0; r < H2; ++r) {
       const float ar = a[r], ai = a[H2 + r], br = b[r], bi = b[H2 + r];
-      const float cbr = fmaf(er, br, ei * bi), cbi = fmaf(er, bi, -ei * br);  // conj(e) b
-      const float ear = fmaf(er, ar, -ei * ai), eai = fmaf(er, ai, ei * ar);  // e a
-      a[r] = fmaf(cs, ar, -sn * cbr);
-      a[H2 + r] = fmaf(cs, ai, -sn * cbi);
-      b[r] = fmaf(sn, ear, cs * br);
-      b[H2 + r] = fmaf(sn, eai, cs * bi);
+      a[r] = fmaf(-per, br, fmaf(-pei, bi, ar));      // a - p conj(e) b
+      a[H2 + r] = fmaf(-per, bi, fmaf(pei, br, ai));
+      b[r] = fmaf(qer, ar, fmaf(-qei, ai, br));       // b + q e a
+      b[H2 + r] = fmaf(qer, ai, fmaf(qei, ar, bi));
     }
+    da *= cs;
+    db *= cs;
     alpha = fmaf(-t, gm, alpha);
     beta = fmaf(t, gm, beta);
     rotated = true;
@@ -277,9 +287,17 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
     // group of 2g lanes regroups into A-A pairs (first half) and B-B pairs
     // (second half) for the next level.  Levels g = 32, 16, ..., 1 give
     // 63 rounds covering all 2016 pairs; a shift costs one shuffle per element.
+    float da = 1.f, db = 1.f;  // column scales (see jacobi_pair)
     while (!converged && sweep < max_sweeps) {
       bool rotated = false;
-      // exact norms once per sweep; tracked through the rotations within it
+      // fold the scales into the columns, then exact norms once per sweep (tracked
+      // through the rotations within it; a sweep shrinks a scale by at most 2^-32)
+#pragma unroll
+      for (int r = 0; r < DMAX; ++r) {
+        a[r] *= da;
+        b[r] *= db;
+      }
+      da = db = 1.f;
       float alpha = sq_norm<DMAX>(a), beta = sq_norm<DMAX>(b);
       float small = (alpha < lam ? alpha : 0.f) + (beta < lam ? beta : 0.f);
 #pragma unroll
@@ -304,26 +322,30 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
           }
           const float rn = __shfl_xor_sync(0xffffffffu, first ? beta : alpha, g);
           const float ra = __shfl_xor_sync(0xffffffffu, first ? acc_b : acc_a, g);
+          const float rs = __shfl_xor_sync(0xffffffffu, first ? db : da, g);
           if (first) {
             beta = rn;
             acc_b = ra;
+            db = rs;
           } else {
             alpha = rn;
             acc_a = ra;
+            da = rs;
           }
         }
         const int src = (lane & ~(g - 1)) | ((lane + 1) & (g - 1));
 #pragma unroll 1
         for (int rd = 0; rd < g; ++rd) {
           if (CPLX)
-            jacobi_pair_c<DMAX>(a, b, alpha, beta, tol, lam_skip, lam, acc_a, acc_b, rotated);
+            jacobi_pair_c<DMAX>(a, b, da, db, alpha, beta, tol, lam_skip, lam, acc_a, acc_b, rotated);
           else
-            jacobi_pair<DMAX>(a, b, alpha, beta, tol, lam_skip, lam, acc_a, acc_b, live, rotated);
+            jacobi_pair<DMAX>(a, b, da, db, alpha, beta, tol, lam_skip, lam, acc_a, acc_b, live, rotated);
           if (rd + 1 < g) {
 #pragma unroll
             for (int r = 0; r < DMAX; ++r) b[r] = __shfl_sync(0xffffffffu, b[r], src);
             beta = __shfl_sync(0xffffffffu, beta, src);
             acc_b = __shfl_sync(0xffffffffu, acc_b, src);
+            db = __shfl_sync(0xffffffffu, db, src);
           }
         }
       }
@@ -333,6 +355,11 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) gb = fmaxf(gb, __shfl_xor_sync(0xffffffffu, gb, o));
       gersh_ok = gb < 0.5f * lam;
+    }
+#pragma unroll
+    for (int r = 0; r < DMAX; ++r) {
+      a[r] *= da;
+      b[r] *= db;
     }
     if (!converged && lane == 0) {
       atomicAdd(&st->svd_noconv, 1u);
