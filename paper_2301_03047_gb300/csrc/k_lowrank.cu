@@ -1,8 +1,9 @@
 // Grouping R~_i x and the WNNM low-rank step of Eq. 5.
 //
 //  k_gather      groups[f][k][j][:] = patch at idx[f][k][j] (vector order
-//                ch, dr, dc).  One thread per 4 output floats: coalesced 16-byte
-//                stores; loads hit the L2-resident image.  HBM-write bound.
+//                ch, dr, dc).  One CTA per group, one thread per 4 output
+//                floats: coalesced 16-byte stores; loads hit the L2-resident
+//                image.  HBM-write bound.
 //  k_jacobi_wnnm one warp per group Y (d x K).  One-sided Jacobi (Hestenes)
 //                SVD in FP32 with the columns held in registers: lane L owns two
 //                column slots (zero beyond K); the 32 lanes rotate their pairs in
@@ -21,37 +22,48 @@ namespace glr {
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_gather(const float* __restrict__ x, int n_img, int C, int H, int W, int P,
+// PT = P (compile-time patch side; 0: the runtime value).  One CTA per group:
+// thread t writes float4 number e4 = t mod q4 of members j = t / q4, t / q4 + 256 / q4,
+// ... (q4 = d / 4), so the index arithmetic per value is a few constant divisions.
+template <int PT>
+__global__ void __launch_bounds__(256) k_gather(const float* __restrict__ x, int n_img, int C, int H, int W, int Prt,
                                                 const int32_t* __restrict__ idx, const int32_t* __restrict__ n_found,
                                                 int N, int K, float* __restrict__ groups, StatusBlock* st) {
-  const int d = C * P * P;
-  const int Wq = W - P + 1;
+  const int P = PT ? PT : Prt;
+  const int PP = P * P;
+  const int d = C * PP;
   const int q4 = d / 4;  // d % 4 == 0 on this path
-  const long long per_img = (long long)N * K * q4;
-  const long long total = (long long)n_img * per_img;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long f = i / per_img;
-    const long long rem = i - f * per_img;
-    const long long gj = rem / q4;  // k*K + j
-    const int e0 = (int)(rem - gj * q4) * 4;
-    const int k = (int)(gj / K);
-    if (k >= min(n_found[f], N)) continue;
-    const int q = idx[f * (long long)N * K + gj];
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
-    if ((unsigned)q >= (unsigned)(Wq * (H - P + 1))) {
-      if (e0 == 0) status_set(st, GLR_DEV_BAD_INDEX);
-      reinterpret_cast<float4*>(groups)[(f * (long long)N * K + gj) * q4 + e0 / 4] = make_float4(0.f, 0.f, 0.f, 0.f);
-      continue;
-    }
-    const int r = q / Wq, c = q - (q / Wq) * Wq;
+  const int Wq = W - P + 1, npos = Wq * (H - P + 1);
+  const int jstep = 256 / q4;  // members per pass (q4 <= 160 for d <= 640)
+  const int t = threadIdx.x;
+  const int j0 = t / q4, e0 = (t - j0 * q4) * 4;
+  if (j0 >= jstep) return;
+  // vector index -> (channel, row, column) offsets of the four values, fixed per thread
+  int off[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int e = e0 + t;
-      const int ch = e / (P * P), rr = (e / P) % P, cc = e % P;
-      v[t] = __ldg(x + (((long long)f * C + ch) * H + r + rr) * W + c + cc);
+  for (int u = 0; u < 4; ++u) {
+    const int e = e0 + u;
+    const int ch = e / PP, rem = e - ch * PP, rr = rem / P, cc = rem - rr * P;
+    off[u] = (ch * H + rr) * W + cc;
+  }
+  const long long ngroups = (long long)n_img * N;
+  for (long long g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const int f = (int)(g / N), k = (int)(g - (long long)f * N);
+    if (k >= min(n_found[f], N)) continue;
+    const float* xf = x + (long long)f * C * H * W;
+    float4* out = reinterpret_cast<float4*>(groups + g * (long long)K * d);
+    for (int j = j0; j < K; j += jstep) {
+      const int q = idx[g * K + j];
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if ((unsigned)q >= (unsigned)npos) {
+        if (e0 == 0) status_set(st, GLR_DEV_BAD_INDEX);
+      } else {
+        const int r = q / Wq, c = q - (q / Wq) * Wq;
+        const float* base = xf + (long long)r * W + c;
+        v = make_float4(__ldg(base + off[0]), __ldg(base + off[1]), __ldg(base + off[2]), __ldg(base + off[3]));
+      }
+      out[(long long)j * q4 + e0 / 4] = v;
     }
-    reinterpret_cast<float4*>(groups)[(f * (long long)N * K + gj) * q4 + e0 / 4] = make_float4(v[0], v[1], v[2], v[3]);
   }
 }
 
@@ -499,9 +511,18 @@ glr_status launch_gather(const float* x, const glr_images& im, const int32_t* id
                          int K, float* groups, StatusBlock* st, cudaStream_t s) {
   const int d = im.C * im.P * im.P;
   if (d % 4 != 0) return GLR_ENOTSUP;
-  const long long total = (long long)im.n_img * N * K * (d / 4);
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
-  GLR_LAUNCH("k_gather", s, k_gather<<<blocks, 256, 0, s>>>(x, im.n_img, im.C, im.H, im.W, im.P, idx, n_found, N, K, groups, st));
+  if (d / 4 > 256) return GLR_ENOTSUP;
+  const long long ngroups = (long long)im.n_img * N;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ngroups, 152LL * 16));
+#define GLR_GATHER_CASE(PP) \
+  GLR_LAUNCH("k_gather", s, k_gather<PP><<<blocks, 256, 0, s>>>(x, im.n_img, im.C, im.H, im.W, im.P, idx, n_found, N, K, groups, st))
+  switch (im.P) {
+    case 4: GLR_GATHER_CASE(4); break;
+    case 6: GLR_GATHER_CASE(6); break;
+    case 8: GLR_GATHER_CASE(8); break;
+    default: GLR_GATHER_CASE(0); break;
+  }
+#undef GLR_GATHER_CASE
   return GLR_OK;
 }
 
