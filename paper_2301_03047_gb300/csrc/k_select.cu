@@ -303,23 +303,34 @@ __global__ void __launch_bounds__(1024) k_topn(const unsigned long long* __restr
   }
   __syncthreads();
   // 4. duplicates: only top-lefts on the border of the position grid can collide
-  //    (an unclamped coordinate is one-to-one); drop later ranks of a repeated id.
+  //    (an unclamped coordinate is one-to-one); drop later ranks of a repeated id:
+  //    each border position records its first rank (atomicMin over the ranks).
   const int per = (nsel + 1023) / 1024;
+  int* first = reinterpret_cast<int*>(sb + pow2);  // [2 (Hq + Wq)] border slots
+  for (int i = tid; i < 2 * (Hq + Wq); i += 1024) first[i] = 0x7fffffff;
+  __syncthreads();
+  // slot of a border position: top row, bottom row, left column, right column
+  auto border_slot = [&](int q) -> int {
+    const int tr = q / Wq, tc = q - (q / Wq) * Wq;
+    if (tr == 0) return tc;
+    if (tr == Hq - 1) return Wq + tc;
+    if (tc == 0) return 2 * Wq + tr;
+    if (tc == Wq - 1) return 2 * Wq + Hq + tr;
+    return -1;
+  };
+  for (int t = 0; t < per; ++t) {
+    const int i = tid * per + t;
+    if (i >= nsel) break;
+    const int b = border_slot((int)sb[i]);
+    if (b >= 0) atomicMin(first + b, i);
+  }
+  __syncthreads();
   int keepbits = 0;  // bit t: entry tid*per + t is kept
   for (int t = 0; t < per; ++t) {
     const int i = tid * per + t;
     if (i >= nsel) break;
-    const int q = (int)sb[i];
-    const int tr = q / Wq, tc = q % Wq;
-    bool keep = true;
-    if (tr == 0 || tr == Hq - 1 || tc == 0 || tc == Wq - 1) {
-      for (int j = 0; j < i; ++j)
-        if ((int)sb[j] == q) {
-          keep = false;
-          break;
-        }
-    }
-    if (keep) keepbits |= 1 << t;
+    const int b = border_slot((int)sb[i]);
+    if (b < 0 || first[b] == i) keepbits |= 1 << t;
   }
   const int nk_local = __popc(keepbits);
   const int base = block_exclusive_scan(nk_local, warp_sums, &s_total);
@@ -421,7 +432,9 @@ glr_status launch_select(const float* x, const glr_images& im, float th, int N, 
   GLR_LAUNCH("k_nms_collect", s, k_nms_collect<<<blocks, 256, 0, s>>>(R, im.n_img, im.H, im.W, cand, cap, cnt));
   int pow2 = 1;
   while (pow2 < N) pow2 <<= 1;
-  const size_t smem = (size_t)pow2 * 8;
+  const int Hq = im.H - im.P + 1, Wq = im.W - im.P + 1;
+  const size_t smem = (size_t)pow2 * 8 + (size_t)2 * (Hq + Wq) * 4;  // sort buffer + border slots
+  if (smem > 200 * 1024) return GLR_ENOTSUP;
   static bool attr_done = false;
   if (!attr_done) {
     if (cudaFuncSetAttribute(k_topn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
