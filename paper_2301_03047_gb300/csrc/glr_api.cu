@@ -155,6 +155,7 @@ size_t glr_workspace_size(int32_t op, const glr_images* im, int32_t N, int32_t K
       WsLayout L;
       L.take((size_t)im->n_img * 4);             // image means
       L.take((size_t)GLR_ENCODER_PARAMS * 4);    // gradient
+      L.take((size_t)im->n_img * kMeanMaxSlices * 8);  // partial sums of the means
       return L.off;
     }
     default:
@@ -236,8 +237,11 @@ glr_status glr_encoder_embed(const float* x, const glr_images* im, const float* 
   const size_t need = glr_workspace_size(GLR_OP_ENCODER, im, 1, 1, nullptr);
   glr_status st = begin_ws(ws, ws_bytes, need, s);
   if (st != GLR_OK) return st;
-  float* mean = reinterpret_cast<float*>((char*)ws + align_up(sizeof(StatusBlock)));
-  st = launch_image_mean(x, *im, mean, s);
+  WsLayout L;
+  float* mean = reinterpret_cast<float*>((char*)ws + L.take((size_t)im->n_img * 4));
+  L.take((size_t)GLR_ENCODER_PARAMS * 4);
+  double* part = reinterpret_cast<double*>((char*)ws + L.take((size_t)im->n_img * kMeanMaxSlices * 8));
+  st = launch_image_mean(x, *im, mean, part, s);
   if (st != GLR_OK) return st;
   return launch_encode_positions(x, *im, mean, params, emb, s);
 }
@@ -255,7 +259,8 @@ glr_status glr_encoder_train_step(const float* x, const glr_images* im, const in
   WsLayout L;
   float* mean = reinterpret_cast<float*>((char*)ws + L.take((size_t)im->n_img * 4));
   float* grad = reinterpret_cast<float*>((char*)ws + L.take((size_t)GLR_ENCODER_PARAMS * 4));
-  st = launch_image_mean(x, *im, mean, s);
+  double* part = reinterpret_cast<double*>((char*)ws + L.take((size_t)im->n_img * kMeanMaxSlices * 8));
+  st = launch_image_mean(x, *im, mean, part, s);
   if (st != GLR_OK) return st;
   return launch_encoder_train(x, *im, mean, pairs, n_pairs, params, adam_m, adam_v, step, lr, weight_decay, grad,
                               loss, s);

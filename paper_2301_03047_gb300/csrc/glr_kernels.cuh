@@ -42,7 +42,7 @@ struct MatchPlan {
   long long npos_pad;   // BF16 position rows per image (pos_tiles * pos_tile)
   int bound_pass;       // tensor-core scorer: minima scan first (bound from half-tile minima)
   size_t mins_off;      // bound_pass: half-tile minima [n_img][Npad][2 pos_tiles] float32
-  size_t mean_off, qn_off, keyv_off, buf_off, bufcnt_off, taugl_off, qpack_off, kpack_off, embp_off, embk_off, total;
+  size_t mean_off, meanp_off, qn_off, keyv_off, buf_off, bufcnt_off, taugl_off, qpack_off, kpack_off, embp_off, embk_off, total;
 };
 MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o);
 glr_status launch_match(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found, int N,
@@ -60,7 +60,9 @@ glr_status launch_encode_positions(const float* x, const glr_images& im, const f
                                    float* emb, cudaStream_t s);
 glr_status launch_encode_vectors(const float* vecs, long long n, int d, const float* params, float* emb,
                                  cudaStream_t s);
-glr_status launch_image_mean(const float* x, const glr_images& im, float* mean, cudaStream_t s);
+// image means: part = scratch of n_img x kMeanMaxSlices doubles
+constexpr int kMeanMaxSlices = 256;
+glr_status launch_image_mean(const float* x, const glr_images& im, float* mean, double* part, cudaStream_t s);
 glr_status launch_encoder_train(const float* x, const glr_images& im, const float* mean, const int32_t* pairs,
                                 int n_pairs, float* params, float* m, float* v, int step, float lr, float wd,
                                 float* grad, float* loss, cudaStream_t s);

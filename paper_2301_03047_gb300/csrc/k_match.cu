@@ -14,8 +14,6 @@
 //   k_rerank       per key: the K' best stream scores over all the key's
 //                  streams (ties to smaller ids), their exact FP32
 //                  sum((p-q)^2), sort by (distance, id), emit the K best.
-#include <cooperative_groups.h>
-
 #include "glr_kernels.cuh"
 #include "topk_stream.cuh"
 
@@ -23,22 +21,18 @@ namespace glr {
 
 namespace {
 
-// Image mean: a cluster of MEAN_CTAS CTAs per image, each summing a contiguous
-// slice in FP64 (float4 loads when aligned); CTA 0 of the cluster adds the
-// slices' sums in rank order through distributed shared memory, so the result
-// does not depend on scheduling.
-constexpr int MEAN_CTAS = 8;
-__global__ void __cluster_dims__(MEAN_CTAS, 1, 1) __launch_bounds__(512)
-    k_image_mean(const float* __restrict__ x, long long n_per_img, float* __restrict__ mean) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
+// Image mean in two passes: S CTAs per image each sum a contiguous slice in FP64
+// (float4 loads when aligned) into part[f][slice]; then one thread per image adds
+// the S partial sums in slice order, so the result does not depend on scheduling.
+// S depends only on the shape (about two CTAs per SM over the batch).
+__global__ void __launch_bounds__(512)
+    k_image_mean_part(const float* __restrict__ x, long long n_per_img, int S, double* __restrict__ part) {
   __shared__ double red[16];
-  __shared__ double part;
-  const int rankc = (int)cl.block_rank();
-  const long long f = blockIdx.x / MEAN_CTAS;
+  const long long f = blockIdx.x / S;
+  const int sl = (int)(blockIdx.x - f * S);
   const float* xf = x + f * n_per_img;
-  const long long per = (n_per_img + MEAN_CTAS - 1) / MEAN_CTAS;
-  const long long lo = min(n_per_img, per * rankc), hi = min(n_per_img, lo + per);
+  const long long per = (n_per_img + S - 1) / S;
+  const long long lo = min(n_per_img, per * sl), hi = min(n_per_img, lo + per);
   double s = 0.0;
   long long i = lo + threadIdx.x;
   // aligned float4 body (slice boundaries rounded to 4 elements)
@@ -61,15 +55,17 @@ __global__ void __cluster_dims__(MEAN_CTAS, 1, 1) __launch_bounds__(512)
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < 16; ++w) t += red[w];
-    part = t;
+    part[f * S + sl] = t;
   }
-  cl.sync();
-  if (rankc == 0 && threadIdx.x == 0) {
-    double t = 0.0;
-    for (int r = 0; r < MEAN_CTAS; ++r) t += *cl.map_shared_rank(&part, r);
-    mean[f] = (float)(t / (double)n_per_img);
-  }
-  cl.sync();  // keep every CTA's shared memory alive until CTA 0 has read it
+}
+
+__global__ void k_image_mean_final(const double* __restrict__ part, int n_img, int S, long long n_per_img,
+                                   float* __restrict__ mean) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_img) return;
+  double t = 0.0;
+  for (int sl = 0; sl < S; ++sl) t += part[(long long)f * S + sl];
+  mean[f] = (float)(t / (double)n_per_img);
 }
 
 __global__ void __launch_bounds__(256) k_patch_norms(const float* __restrict__ x, const float* __restrict__ mean,
@@ -478,9 +474,19 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
 
 }  // namespace
 
-glr_status launch_image_mean(const float* x, const glr_images& im, float* mean, cudaStream_t s) {
-  GLR_LAUNCH("k_image_mean", s,
-             k_image_mean<<<im.n_img * MEAN_CTAS, 512, 0, s>>>(x, (long long)im.C * im.H * im.W, mean));
+int image_mean_slices(const glr_images& im) {
+  const long long n = (long long)im.C * im.H * im.W;
+  long long S = ceil_div(2 * 152, (long long)im.n_img);
+  S = std::min<long long>(S, ceil_div(n, 4096));
+  return (int)std::max<long long>(1, std::min<long long>(S, kMeanMaxSlices));
+}
+
+glr_status launch_image_mean(const float* x, const glr_images& im, float* mean, double* part, cudaStream_t s) {
+  const long long n = (long long)im.C * im.H * im.W;
+  const int S = image_mean_slices(im);
+  GLR_LAUNCH("k_image_mean", s, k_image_mean_part<<<(unsigned)(im.n_img * S), 512, 0, s>>>(x, n, S, part));
+  GLR_LAUNCH("k_image_mean_final", s,
+             k_image_mean_final<<<(unsigned)ceil_div(im.n_img, 128), 128, 0, s>>>(part, im.n_img, S, n, mean));
   return GLR_OK;
 }
 
@@ -524,6 +530,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   const long long npos = (long long)Hq * Wq;
   WsLayout L;
   pl.mean_off = L.take((size_t)im.n_img * 4);
+  pl.meanp_off = L.take((size_t)im.n_img * kMeanMaxSlices * 8);
   pl.qn_off = L.take((size_t)im.n_img * npos * 4);
   pl.keyv_off = L.take((size_t)im.n_img * pl.Npad * d * 4);
   const long long nstreams = (long long)im.n_img * pl.Npad * pl.streams_per_key;
@@ -603,7 +610,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     xs = planes;
     if (cudaMemsetAsync(mean, 0, (size_t)im.n_img * 4, s) != cudaSuccess) return GLR_ECUDA;
   } else {
-    const glr_status st = launch_image_mean(x, im, mean, s);
+    const glr_status st = launch_image_mean(x, im, mean, reinterpret_cast<double*>(ws + pl.meanp_off), s);
     if (st != GLR_OK) return st;
   }
   if (!tc) {  // the FP32 scorer adds ||q||^2 itself; the tensor-core operands carry their norms
