@@ -28,6 +28,7 @@ struct MatchPlan {
   int splits;           // position splits per key tile
   int subs;             // streams per key and split (column halves inside a tile)
   int streams_per_key;  // splits * subs
+  int finish;           // streams end with their exact K' selection (else the re-rank makes it)
   int key_tile;         // keys per CTA
   int Npad;             // N rounded up to key_tile
   int pos_tile;         // positions per scorer tile

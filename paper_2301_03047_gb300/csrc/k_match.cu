@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256, 2)
                       cfg, whist, pub_sh, pub_gl, stats);
     }
   }
-  stream_finish(tau, cnt, mybuf, cfg, whist);
+  if (cfg.finish) stream_finish(tau, cnt, mybuf, cfg, whist);
   stream_stats_flush(stats, st);
   buf_cnt[stream] = (key < nf) ? cnt : 0;
 }
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
     }
     const long long s0 = ((long long)f * Npad + k) * streams_per_key;
     for (int sidx = 0; window == 0 && sidx < streams_per_key; ++sidx) {
-      const int n = min(buf_cnt[s0 + sidx], kp);
+      const int n = min(buf_cnt[s0 + sidx], cap_slots);
       const uint2* b = bufs + (s0 + sidx) * cap_slots;
       for (int i = lane; i < n; i += 32) {
         const uint2 e = b[i];
@@ -525,6 +525,9 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   pl.tiles_per_split = (int)ceil_div(pl.pos_tiles, splits);
   pl.splits = (int)ceil_div(pl.pos_tiles, pl.tiles_per_split);
   pl.streams_per_key = pl.splits * pl.subs;
+  // the re-rank keeps the K' best stream entries of a key itself; when every buffer
+  // fits its list unreduced, the streams skip their own final exact selection
+  pl.finish = (long long)pl.streams_per_key * (pl.cap + 32) <= kRerankMaxList ? 0 : 1;
   // the heat map of Eq. 4 contracts the 4 C binary edge planes instead of the image
   const int d = (edge ? 4 : 1) * im.C * im.P * im.P;
   const long long npos = (long long)Hq * Wq;
@@ -624,7 +627,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     GLR_LAUNCH("k_key_vectors", s, k_key_vectors<<<blocks, 256, 0, s>>>(xs, mean, keys, n_found, im.n_img, ime.C, im.H, im.W, im.P, N, pl.Npad,
                                         keyv, reinterpret_cast<StatusBlock*>(ws)));
   }
-  StreamCfg cfg{pl.cap, pl.Kp};
+  StreamCfg cfg{pl.cap, pl.Kp, pl.finish};
   if (pl.mode == GLR_MATCH_LEARNED) {
     float* emb_p = reinterpret_cast<float*>(ws + pl.embp_off);
     float* emb_k = reinterpret_cast<float*>(ws + pl.embk_off);
@@ -671,7 +674,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
   }
   {
     int pow2 = 32;
-    while (pow2 < pl.streams_per_key * pl.Kp) pow2 <<= 1;
+    while (pow2 < pl.streams_per_key * (pl.finish ? pl.Kp : pl.cap + 32)) pow2 <<= 1;
     const int dpad = (d + 31) & ~31;
     const size_t smem = (size_t)RR_WARPS * pow2 * 8 + (size_t)RR_WARPS * (dpad + 256) * 4;
     if (smem > 227 * 1024 || d > 640) return GLR_ENOTSUP;

@@ -878,7 +878,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
     if constexpr (!MINS) {
-      stream_finish(tau, cnt, mybuf, cfg, whist);
+      if (cfg.finish) stream_finish(tau, cnt, mybuf, cfg, whist);
       stream_stats_flush(stats, st);
       buf_cnt[stream] = (key < nf) ? cnt : 0;
     }
@@ -991,7 +991,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
         blocks_per_sm != 1)  // all of TMEM: exactly one resident CTA per SM
       return GLR_ENOTSUP;
     const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
-    const StreamCfg cfg{pl.cap, pl.Kp};
+    const StreamCfg cfg{pl.cap, pl.Kp, pl.finish};
     dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
     if (pl.bound_pass) {
       GLR_LAUNCH("k_match_tc_min", s,
@@ -1057,7 +1057,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
       return GLR_ENOTSUP;
   }
   const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
-  const StreamCfg cfg{pl.cap, pl.Kp};
+  const StreamCfg cfg{pl.cap, pl.Kp, pl.finish};
   dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
   if (pl.bound_pass && dump == nullptr) {
     GLR_LAUNCH("k_match_tc_min", s,

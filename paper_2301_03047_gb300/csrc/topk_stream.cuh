@@ -33,8 +33,9 @@
 namespace glr {
 
 struct StreamCfg {
-  int cap;  // compaction trigger (entries)
-  int kp;   // entries kept per stream
+  int cap;     // compaction trigger (entries)
+  int kp;      // entries kept per stream
+  int finish;  // 0: leave the buffers as they are (the re-rank selects the K' best itself)
 };
 
 constexpr int kStreamSlots = 17;                      // buffer entries per lane of the compacting warp
