@@ -1,7 +1,8 @@
 // Aggregation: the low-rank patch estimates go back to their positions and
 // overlapping estimates are averaged (weight 1); uncovered pixels keep x_in.
 //
-//  k_scatter    one warp per group, its rows one after the other; lanes add a row's d values
+//  k_scatter    one warp per group (its rows one after the other) for short rows, one warp
+//               per row for d > 128; lanes add a row's d values
 //               into the numerator planes as 64-bit fixed point (value x 2^32,
 //               rounded to an integer: exact for |value| >= 2^-9, else within
 //               2^-33) with integer atomics, so the sums do not depend on the
@@ -15,42 +16,52 @@ namespace glr {
 
 namespace {
 
-// PT = P (compile-time patch side; 0: the runtime value).  One warp per group: the
-// image and key are decoded once, then the K rows one after the other.
+// Adds one group row (a patch estimate at position q) into the fixed-point sums.
 template <int PT>
+__device__ __forceinline__ void scatter_row(const float* __restrict__ src, int q, unsigned long long* __restrict__ nf,
+                                            int* __restrict__ cnt_f, int C, int H, int W, int P, int lane) {
+  const int PP = P * P, d = C * PP, Wq = W - P + 1;
+  const int r = q / Wq, c = q - (q / Wq) * Wq;
+  unsigned long long* dst = nf + (long long)r * W + c;
+  for (int e = lane; e < d; e += 32) {
+    const int ch = e / PP, rem = e - ch * PP, rr = rem / P, cc = rem - rr * P;
+    // |value| < 2^30 keeps every partial sum of up to 2^32 terms inside int64
+    const float v = fminf(fmaxf(__ldg(src + e), -1073741824.f), 1073741824.f);
+    const long long fx = __float2ll_rn(v * 4294967296.f);  // exact scaling by 2^32
+    atomicAdd(dst + ((long long)ch * H + rr) * W + cc, (unsigned long long)fx);
+  }
+  if (lane == 0) atomicAdd(cnt_f + q, 1);
+}
+
+// PT = P (compile-time patch side; 0: the runtime value).  PER_ROW = false: one
+// warp per group (the image and key decoded once, the K rows one after the
+// other; short rows); true: one warp per row (long rows, d > 128).
+template <int PT, bool PER_ROW>
 __global__ void __launch_bounds__(256) k_scatter(const float* __restrict__ groups, const int32_t* __restrict__ idx,
                                                  const int32_t* __restrict__ n_found, int n_img, int C, int H, int W,
                                                  int Prt, int N, int K, unsigned long long* __restrict__ num,
                                                  int* __restrict__ cnt, StatusBlock* st) {
   const int P = PT ? PT : Prt;
-  const int PP = P * P;
-  const int d = C * PP;
+  const int d = C * P * P;
   const int Wq = W - P + 1, Hq = H - P + 1;
-  const long long ngroups = (long long)n_img * N;
   const int lane = threadIdx.x & 31;
-  for (long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; g < ngroups;
-       g += ((long long)gridDim.x * blockDim.x) >> 5) {
+  const long long units = (long long)n_img * N * (PER_ROW ? K : 1);
+  for (long long u = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; u < units;
+       u += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const long long g = PER_ROW ? u / K : u;
     const int f = (int)(g / N), k = (int)(g - (long long)f * N);
     if (k >= min(n_found[f], N)) continue;
     unsigned long long* nf = num + (long long)f * C * H * W;
-    for (int j = 0; j < K; ++j) {
+    int* cnt_f = cnt + (long long)f * Hq * Wq;
+    const int j0 = PER_ROW ? (int)(u - g * K) : 0, j1 = PER_ROW ? j0 + 1 : K;
+    for (int j = j0; j < j1; ++j) {
       const long long row = g * K + j;
       const int q = idx[row];
       if ((unsigned)q >= (unsigned)(Wq * Hq)) {
         if (lane == 0) status_set(st, GLR_DEV_BAD_INDEX);
         continue;
       }
-      const int r = q / Wq, c = q - (q / Wq) * Wq;
-      const float* src = groups + row * d;
-      unsigned long long* dst = nf + (long long)r * W + c;
-      for (int e = lane; e < d; e += 32) {
-        const int ch = e / PP, rem = e - ch * PP, rr = rem / P, cc = rem - rr * P;
-        // |value| < 2^30 keeps every partial sum of up to 2^32 terms inside int64
-        const float v = fminf(fmaxf(__ldg(src + e), -1073741824.f), 1073741824.f);
-        const long long fx = __float2ll_rn(v * 4294967296.f);  // exact scaling by 2^32
-        atomicAdd(dst + ((long long)ch * H + rr) * W + cc, (unsigned long long)fx);
-      }
-      if (lane == 0) atomicAdd(cnt + (long long)f * Hq * Wq + q, 1);
+      scatter_row<PT>(groups + row * d, q, nf, cnt_f, C, H, W, P, lane);
     }
   }
 }
@@ -131,17 +142,23 @@ glr_status launch_aggregate(const float* groups, const int32_t* idx, const int32
   const size_t cnt_b = (size_t)im.n_img * (im.H - im.P + 1) * (im.W - im.P + 1) * 4;
   if (cudaMemsetAsync(num, 0, num_b, s) != cudaSuccess) return GLR_ECUDA;
   if (cudaMemsetAsync(cnt, 0, cnt_b, s) != cudaSuccess) return GLR_ECUDA;
-  const long long ngroups = (long long)im.n_img * N;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(ngroups * 32, 256), 152LL * 32));
-#define GLR_SCATTER_CASE(PP)                                                                                  \
-  GLR_LAUNCH("k_scatter", s, k_scatter<PP><<<blocks, 256, 0, s>>>(groups, idx, n_found, im.n_img, im.C, im.H, im.W, \
-                                                                  im.P, N, K, num, cnt,                       \
-                                                                  reinterpret_cast<StatusBlock*>(ws)))
-  switch (im.P) {
-    case 4: GLR_SCATTER_CASE(4); break;
-    case 6: GLR_SCATTER_CASE(6); break;
-    case 8: GLR_SCATTER_CASE(8); break;
-    default: GLR_SCATTER_CASE(0); break;
+  const bool per_row = im.C * im.P * im.P > 128;
+  const long long units = (long long)im.n_img * N * (per_row ? K : 1);
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(units * 32, 256), 152LL * 32));
+#define GLR_SCATTER_CASE(PP, ROW)                                                                            \
+  GLR_LAUNCH("k_scatter", s,                                                                                 \
+             (k_scatter<PP, ROW><<<blocks, 256, 0, s>>>(groups, idx, n_found, im.n_img, im.C, im.H, im.W, im.P, N, \
+                                                        K, num, cnt, reinterpret_cast<StatusBlock*>(ws))))
+  switch (im.P * 2 + (per_row ? 1 : 0)) {
+    case 8: GLR_SCATTER_CASE(4, false); break;
+    case 12: GLR_SCATTER_CASE(6, false); break;
+    case 13: GLR_SCATTER_CASE(6, true); break;
+    case 16: GLR_SCATTER_CASE(8, false); break;
+    case 17: GLR_SCATTER_CASE(8, true); break;
+    default:
+      if (per_row) GLR_SCATTER_CASE(0, true);
+      else GLR_SCATTER_CASE(0, false);
+      break;
   }
 #undef GLR_SCATTER_CASE
   dim3 g((unsigned)ceil_div(im.W, AT), (unsigned)ceil_div(im.H, AT), (unsigned)im.n_img);

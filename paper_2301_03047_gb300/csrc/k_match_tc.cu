@@ -67,15 +67,17 @@ constexpr uint32_t TC_SMEM = OFF_TAU + TC_M * 4 + 1024;                   // + a
 static_assert(TC_SMEM <= 232448, "shared memory budget");
 static_assert(OFF_TILE % 16 == 0 && (TILE_LD * 4) % 16 == 0, "16-byte aligned tile rows");
 // Wide operands (d > 74): the key tile no longer fits next to a position ring, so
-// every 64-column chunk of keys and positions streams through a 3-stage ring of
+// every 64-column chunk of keys and positions streams through a 4-stage ring of
 // (A chunk, B chunk) pairs; the 16 norm columns come last as a 16-column chunk.
-constexpr int W_STAGES = 3;
+// The fourth stage takes the room of the append tile (appends go through
+// shuffles here: the contraction of a tile is long enough to hide them).
+constexpr int W_STAGES = 4;
+static_assert(W_STAGES <= TC_STAGES, "barrier slots");
 constexpr uint32_t W_STAGE_BYTES = A_MAIN_BYTES + B_MAIN_BYTES;  // 48 KB
 constexpr uint32_t W_OFF_BAR = W_STAGES * W_STAGE_BYTES;
 constexpr uint32_t W_OFF_MISC = W_OFF_BAR + NBAR * 8;
 constexpr uint32_t W_OFF_HIST = (W_OFF_MISC + 64 + 15) / 16 * 16;
-constexpr uint32_t W_OFF_TILE = W_OFF_HIST + TC_EPI_WARPS * 256 * 4;
-constexpr uint32_t W_OFF_TAU = W_OFF_TILE + TC_EPI_WARPS * 32 * TILE_LD * 4;
+constexpr uint32_t W_OFF_TAU = W_OFF_HIST + TC_EPI_WARPS * 256 * 4;  // no append tile: rows go through shuffles
 constexpr uint32_t W_SMEM = W_OFF_TAU + TC_M * 4 + 1024;
 static_assert(W_SMEM <= 232448, "shared memory budget (wide)");
 constexpr unsigned long long kWaitNs = 1000000000ull;                   // 1 s
@@ -620,7 +622,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t kBar = WIDE ? W_OFF_BAR : OFF_BAR, kMisc = WIDE ? W_OFF_MISC : OFF_MISC;
-  constexpr uint32_t kHist = WIDE ? W_OFF_HIST : OFF_HIST, kTile = WIDE ? W_OFF_TILE : OFF_TILE;
+  constexpr uint32_t kHist = WIDE ? W_OFF_HIST : OFF_HIST, kTile = WIDE ? W_OFF_TAU : OFF_TILE;
   constexpr uint32_t kTau = WIDE ? W_OFF_TAU : OFF_TAU;
   constexpr int NST = WIDE ? W_STAGES : TC_STAGES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBar);
@@ -866,13 +868,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const float te = stream_tau_eff(tau, *reinterpret_cast<volatile uint32_t*>(pub_sh + lane), gl);
           const unsigned rows = stream_filter(v[c], nvalid, te);
           if (rows) {
+            if constexpr (WIDE) {
+              stream_append_regs(rows, v[c], (int)q0, nvalid, te, tau, cnt, mybuf, cfg, whist, pub_sh, pub_gl, stats);
+            } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-              reinterpret_cast<float4*>(wtile + lane * TILE_LD)[j] =
-                  make_float4(v[c][4 * j], v[c][4 * j + 1], v[c][4 * j + 2], v[c][4 * j + 3]);
-            __syncwarp();
-            stream_append(rows, wtile, TILE_LD, (int)q0, nvalid, te, tau, cnt, mybuf, cfg, whist, pub_sh, pub_gl,
-                          stats);
+              for (int j = 0; j < 8; ++j)
+                reinterpret_cast<float4*>(wtile + lane * TILE_LD)[j] =
+                    make_float4(v[c][4 * j], v[c][4 * j + 1], v[c][4 * j + 2], v[c][4 * j + 3]);
+              __syncwarp();
+              stream_append(rows, wtile, TILE_LD, (int)q0, nvalid, te, tau, cnt, mybuf, cfg, whist, pub_sh, pub_gl,
+                            stats);
+            }
           }
         }
       }

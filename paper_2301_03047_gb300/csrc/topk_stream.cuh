@@ -261,9 +261,11 @@ __device__ __forceinline__ unsigned stream_filter(const float (&s)[32], int nval
 // te = effective threshold of this lane's row; tau / cnt / row_buf are its
 // own state; pub_sh / pub_gl point at the published bounds of the warp's
 // row 0 (row r at + r).
-__device__ __forceinline__ void stream_append(unsigned rows, const float* tile, int ld, int q0, int nvalid, float te,
-                                              float& tau, int& cnt, uint2* row_buf, const StreamCfg& cfg,
-                                              unsigned* hist, uint32_t* pub_sh, uint32_t* pub_gl, uint2& stats) {
+// row_value(r): this lane's column of row r (lane = column).
+template <class RowValue>
+__device__ __forceinline__ void stream_append_rows(unsigned rows, RowValue row_value, int q0, int nvalid, float te,
+                                                   float& tau, int& cnt, uint2* row_buf, const StreamCfg& cfg,
+                                                   unsigned* hist, uint32_t* pub_sh, uint32_t* pub_gl, uint2& stats) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = lanemask_lt();
   while (rows) {
@@ -272,7 +274,7 @@ __device__ __forceinline__ void stream_append(unsigned rows, const float* tile, 
     const float t_r = __shfl_sync(0xffffffffu, te, r);
     int c_r = __shfl_sync(0xffffffffu, cnt, r);
     uint2* b_r = reinterpret_cast<uint2*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(row_buf), r));
-    const float v = tile[r * ld + lane];
+    const float v = row_value(r);
     const bool c = (lane < nvalid) && v < t_r;
     const unsigned bal = __ballot_sync(0xffffffffu, c);
     if (c) b_r[c_r + __popc(bal & lt_mask)] = make_uint2(float_order_key(v), (unsigned)(q0 + lane));
@@ -295,6 +297,34 @@ __device__ __forceinline__ void stream_append(unsigned rows, const float* tile, 
     if (lane == r) cnt = c_r;
   }
   __syncwarp();
+}
+
+// The rows from a 32 x 32 shared-memory tile (row r at tile + r * ld).
+__device__ __forceinline__ void stream_append(unsigned rows, const float* tile, int ld, int q0, int nvalid, float te,
+                                              float& tau, int& cnt, uint2* row_buf, const StreamCfg& cfg,
+                                              unsigned* hist, uint32_t* pub_sh, uint32_t* pub_gl, uint2& stats) {
+  const int lane = threadIdx.x & 31;
+  stream_append_rows(rows, [&](int r) { return tile[r * ld + lane]; }, q0, nvalid, te, tau, cnt, row_buf, cfg, hist,
+                     pub_sh, pub_gl, stats);
+}
+
+// The rows straight from registers (lane r holds row r's 32 values): a row reaches
+// the warp through 32 shuffles.  For kernels without room for the tile.
+__device__ __forceinline__ void stream_append_regs(unsigned rows, const float (&s)[32], int q0, int nvalid, float te,
+                                                   float& tau, int& cnt, uint2* row_buf, const StreamCfg& cfg,
+                                                   unsigned* hist, uint32_t* pub_sh, uint32_t* pub_gl,
+                                                   uint2& stats) {
+  const int lane = threadIdx.x & 31;
+  auto row_value = [&](int r) {
+    float mine = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float t = __shfl_sync(0xffffffffu, s[j], r);
+      mine = lane == j ? t : mine;
+    }
+    return mine;
+  };
+  stream_append_rows(rows, row_value, q0, nvalid, te, tau, cnt, row_buf, cfg, hist, pub_sh, pub_gl, stats);
 }
 
 // End of a stream: every buffer keeps exactly its min(cnt, kp) smallest entries.
