@@ -25,6 +25,12 @@
 //   warps 2-9   epilogue: tcgen05.ld 32 lanes x 32 columns, push into the
 //               per-row top-K' stream; warps w and w+4 share a TMEM lane
 //               quadrant and take one column half each
+// Two scans of the same contraction (bound_pass): k_match_tc<4, W, true> keeps no
+// candidate and writes the minimum score of every (key, 128-position half tile);
+// k_tau_bound turns the K'-th smallest of a key's minima into its starting bound;
+// k_match_tc<EB, W, false> then pushes only scores below that bound into the
+// streams.  Chunked rows (d > 74, W = true) stream key and position chunks
+// through a 4-stage ring and append from registers (no shared tile).
 // Every mbarrier wait is bounded (1 s of %globaltimer): on expiry the CTA sets
 // GLR_DEV_TIMEOUT and an abort flag, every role leaves its loop, in-flight TMA
 // loads and MMAs are waited for (bounded) and TMEM is freed before exit.

@@ -5,11 +5,13 @@
 //
 // One 32-column chunk is pushed in two steps:
 //   1. filter   each lane takes the minimum of its row's 32 scores (in
-//               registers) and compares it with its tau: one instruction per
-//               score, and a warp vote gives the rows that have a candidate.
+//               registers, a tree of three-input minima: about half an
+//               instruction per score) and compares it with its tau; a warp
+//               vote gives the rows that have a candidate.
 //   2. append   for each such row the warp reads the row from a shared-memory
-//               tile (lane = column), votes on s < tau and appends the
-//               candidates in position order with one coalesced store.
+//               tile (or, without one, through 32 shuffles; lane = column),
+//               votes on s < tau and appends the candidates in position order
+//               with one coalesced store.
 // When a buffer holds more than cap entries the warp compacts it: the new
 // threshold is a pivot drawn from 32 sorted samples such that at least K'
 // entries lie below it (entries >= pivot are dropped), or, if the sample
@@ -17,7 +19,8 @@
 // buffer therefore always holds every entry that can still be among the K'
 // smallest (score, id) pairs of the stream.  At the end of the stream an
 // exact compaction leaves exactly the K' smallest, ties by smaller id
-// (entries are appended in increasing id order).
+// (entries are appended in increasing id order), unless the re-rank takes the
+// unreduced buffers and selects the K' best itself (StreamCfg::finish = 0).
 //
 // Several streams serve one key (column halves of a tile, position splits).
 // A compaction that leaves at least K' entries strictly below a value v
