@@ -312,10 +312,12 @@ __global__ void __launch_bounds__(256) k_pack_keys(const float* __restrict__ key
 // norms are added in channel order (deterministic) and the rows leave as one
 // contiguous block of 16-byte stores.
 constexpr int PW_POS = 32;
+template <int PT>  // P at compile time (0: runtime): unrolled patch loops
 __global__ void __launch_bounds__(256) k_pack_positions_w(const float* __restrict__ x, const float* __restrict__ mean,
-                                                          int n_img, int C, int H, int W, int P, long long npos_pad,
+                                                          int n_img, int C, int H, int W, int P_, long long npos_pad,
                                                           int nkc, int raw, __nv_bfloat16* __restrict__ qmain,
                                                           __nv_bfloat16* __restrict__ qaux) {
+  const int P = PT ? PT : P_;
   extern __shared__ __align__(16) uint8_t pw_smem[];
   const int rowlen = nkc * DK_MAIN;  // bf16 per row
   const int ld = rowlen + 2;         // shared-memory row stride: an odd number of words (no bank conflicts)
@@ -341,9 +343,12 @@ __global__ void __launch_bounds__(256) k_pack_positions_w(const float* __restric
     for (int ch = wid; ch < C; ch += nw) {
       const float* xc = x + ((long long)f * C + ch) * H * W;
       float nrm = 0.f;
-      for (int dr = 0; dr < P; ++dr)
+      const float* xp = xc + (long long)r * W + c;
+#pragma unroll
+      for (int dr = 0; dr < (PT ? PT : 1) * 0 + P; ++dr)
+#pragma unroll
         for (int dc = 0; dc < P; ++dc) {
-          const float v = valid ? __ldg(xc + (long long)(r + dr) * W + c + dc) - mu : 0.f;
+          const float v = valid ? __ldg(xp + (long long)dr * W + dc) - mu : 0.f;
           const __nv_bfloat16 b = __float2bfloat16_rn(v);
           const float rv = __bfloat162float(b);
           nrm = fmaf(rv, rv, nrm);
@@ -969,14 +974,23 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
     {
       const size_t psmem = (size_t)PW_POS * (pl.nkc * DK_MAIN + 2) * 2 + (size_t)im.C * PW_POS * 4;
       if (psmem > 227 * 1024) return GLR_ENOTSUP;
-      if (cudaFuncSetAttribute(k_pack_positions_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem) !=
-          cudaSuccess)
-        return GLR_ECUDA;
       const long long nblk = (long long)im.n_img * (pl.npos_pad / PW_POS);
       const int pblocks = (int)std::max<long long>(1, std::min<long long>(nblk, 152LL * 16));
-      GLR_LAUNCH("k_pack_positions", s,
-                 k_pack_positions_w<<<pblocks, 256, psmem, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P,
-                                                                 pl.npos_pad, pl.nkc, raw, qmain, qaux));
+#define GLR_PACKW_CASE(PP)                                                                                     \
+  {                                                                                                            \
+    if (cudaFuncSetAttribute(k_pack_positions_w<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem) != \
+        cudaSuccess)                                                                                           \
+      return GLR_ECUDA;                                                                                        \
+    GLR_LAUNCH("k_pack_positions", s,                                                                          \
+               k_pack_positions_w<PP><<<pblocks, 256, psmem, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P,     \
+                                                                  pl.npos_pad, pl.nkc, raw, qmain, qaux));     \
+  }
+      switch (im.P) {
+        case 6: GLR_PACKW_CASE(6); break;
+        case 8: GLR_PACKW_CASE(8); break;
+        default: GLR_PACKW_CASE(0); break;
+      }
+#undef GLR_PACKW_CASE
     }
     {
       const int nk = im.n_img * pl.Npad;
