@@ -326,9 +326,9 @@ class GlrDenoiser:
                  window: int = 20, fused: bool = False, bound_pass: int = 0):
         """fused (real images, d <= 64, K <= 64): grouping, WNNM and aggregation in one kernel pass
         (glr_lowrank_aggregate): no group buffer (1 GB less on the 16 x 512^2 workload) but slower
-        there (16.6 ms against 11.9 ms for the three separate kernels: the fused kernel's per-lane
-        patch gathers do not coalesce and its 12 warps per SM hide the atomics poorly), so it is
-        off by default."""
+        there (27.7 ms against 23.5 ms for the separate kernels on the GAP start image: the fused
+        kernel's per-lane patch gathers do not coalesce and its 12 warps per SM hide the atomics
+        poorly), so it is off by default."""
         s = shape
         self.shape, self.mode, self.edge_th, self.complex_ = s, mode, edge_th, complex_
         self.n_uniform, self.window = n_uniform, window
