@@ -81,3 +81,15 @@ def test_bound_pass_keeps_matches_learned():
     enc = glr.Encoder(seed=3)
     kw = dict(encoder=enc.params)
     same_matches(run(x, P, keys, nf, K, "learned", 1, **kw), run(x, P, keys, nf, K, "learned", -1, **kw))
+
+
+def test_stream_final_selection_and_rerank_selection_agree():
+    """With few streams the re-rank takes the unreduced buffers and selects the K' best itself;
+    with many (8 splits, capacity 512) every stream ends with its own exact K' selection.  The
+    key's K' best (score, id) pairs are the same either way, so are the matches."""
+    x = frames("bp_finish", 1, 1, 220, 240)
+    P, N, K = 8, 256, 48
+    keys, nf, _ = glr.select_keys(x, P, N, 0.05)
+    few = run(x, P, keys, nf, K, "bf16", 1, splits=1)
+    many = run(x, P, keys, nf, K, "bf16", 1, splits=8, cap=512)
+    same_matches(few, many)

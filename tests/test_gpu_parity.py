@@ -257,7 +257,11 @@ def test_lowrank_noiseless_low_rank_recovery():
 # ---------------------------------------------------------------------------
 # Aggregation
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("case", [("a1", 2, 1, 33, 47, 8, 25, 10), ("a2", 1, 3, 20, 21, 4, 12, 6)])
+@pytest.mark.parametrize("case", [("a1", 2, 1, 33, 47, 8, 25, 10), ("a2", 1, 3, 20, 21, 4, 12, 6),
+                                  # K > 128 (rows past the preloaded ones), one warp per row (d > 128),
+                                  # a patch side without a compiled specialisation
+                                  ("a3", 1, 1, 40, 44, 6, 9, 160), ("a4", 1, 4, 30, 30, 6, 7, 20),
+                                  ("a5", 1, 2, 25, 27, 5, 8, 10)])
 def test_aggregate_parity(case):
     tag, F, C, H, W, P, N, K = case
     rng = synth.rng_for(tag)
