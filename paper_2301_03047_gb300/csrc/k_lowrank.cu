@@ -242,6 +242,10 @@ __device__ __forceinline__ float sq_norm(const float (&a)[DMAX]) {
   return (p[0] + p[1]) + (p[2] + p[3]);
 }
 
+// Columns at or above the skip level up to which a sweep is replaced by a direct test of
+// their pairs (each costs one broadcast column: DMAX shuffles and 2 DMAX FMAs per lane).
+constexpr int kDirectCheckCols = 4;
+
 // DMAX rows per column, KMAX <= 64 columns, one warp per group, WARPS groups per CTA.
 template <int DMAX, int WARPS, bool CPLX, bool FUSED>
 __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_img, int d, int N, int K,
@@ -319,6 +323,39 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
       // (norm^2 + sum of |a.b| over block partners, largest over the block) was
       // below lam / 2
       const float lam_skip = (lam > 0.f && (small < lam || gersh_ok)) ? lam : 0.f;
+      // With the skip rule on, only pairs with a column at or above lam_skip can rotate.
+      // When there are few such columns, test those pairs directly (each such column
+      // broadcast once, the same inner products and test as the sweep's): if none
+      // passes, the sweep would rotate nothing, so it is not run.
+      if (!CPLX && lam_skip > 0.f) {
+        unsigned ma = __ballot_sync(0xffffffffu, alpha >= lam_skip);
+        unsigned mb = __ballot_sync(0xffffffffu, beta >= lam_skip);
+        if (__popc(ma) + __popc(mb) <= kDirectCheckCols) {
+          bool need = false;
+          while (ma | mb) {
+            const bool from_a = ma != 0;
+            const int src = __ffs(from_a ? ma : mb) - 1;
+            if (from_a) ma &= ma - 1;
+            else mb &= mb - 1;
+            const float nb = __shfl_sync(0xffffffffu, from_a ? alpha : beta, src);
+            float ga[4] = {0.f, 0.f, 0.f, 0.f}, gb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int r = 0; r < DMAX; ++r) {
+              const float bv = __shfl_sync(0xffffffffu, from_a ? a[r] : b[r], src);
+              ga[r & 3] = fmaf(a[r], bv, ga[r & 3]);
+              gb[r & 3] = fmaf(b[r], bv, gb[r & 3]);
+            }
+            const float g_a = (ga[0] + ga[1]) + (ga[2] + ga[3]), g_b = (gb[0] + gb[1]) + (gb[2] + gb[3]);
+            const bool self_a = from_a && lane == src, self_b = !from_a && lane == src;
+            need |= !self_a && fabsf(g_a) > tol * sqrtf(alpha * nb) && g_a != 0.f;
+            need |= !self_b && fabsf(g_b) > tol * sqrtf(beta * nb) && g_b != 0.f;
+          }
+          if (!__any_sync(0xffffffffu, need)) {
+            converged = true;
+            break;
+          }
+        }
+      }
       float acc_a = 0.f, acc_b = 0.f;
 #pragma unroll 1
       for (int g = 32; g >= 1; g >>= 1) {
