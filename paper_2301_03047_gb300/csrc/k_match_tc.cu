@@ -202,7 +202,8 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16&
 // First norm column of the 80-column operand rows for d patch values.
 __host__ __device__ constexpr int norm_col(int d) { return d > DK_MAIN ? d : DK_MAIN; }
 
-// Positions: thread per position; writes 64 + 16 bf16.
+// Positions: thread per position builds its 64 + 16 bf16; a warp stores its 32 rows as
+// contiguous blocks through shared memory.
 // emb != nullptr: pack the 16-value embeddings emb[img][q][16] instead of the patches.
 // PT: the patch side when it is known at compile time (cheap index arithmetic), 0 = P
 template <int PT>
@@ -216,7 +217,8 @@ __global__ void __launch_bounds__(256) k_pack_positions(const float* __restrict_
   const long long npos = (long long)Hq * Wq;
   const int d = emb != nullptr ? 16 : C * P * P;
   const int nb = norm_col(d) - DK_MAIN;  // first norm column inside the aux tile
-  const long long total = (long long)n_img * npos_pad;
+  const long long total = (long long)n_img * npos_pad;  // a multiple of 32: whole warps per pass
+  __shared__ __align__(16) __nv_bfloat16 stage[8][32][DK_MAIN + DK_AUX];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long f = i / npos_pad;
@@ -255,13 +257,24 @@ __global__ void __launch_bounds__(256) k_pack_positions(const float* __restrict_
         else if (t >= 3 && t < 6) row[DK_MAIN + e] = one;
       }
     }
-    uint4* dst = reinterpret_cast<uint4*>(qmain + i * DK_MAIN);
+    // the warp's 32 rows (consecutive positions) go through shared memory and leave as
+    // two contiguous blocks (4 KB of patch columns, 1 KB of norm columns)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint4* srow = reinterpret_cast<uint4*>(stage[wid][lane]);
     const uint4* src = reinterpret_cast<const uint4*>(row);
 #pragma unroll
-    for (int k = 0; k < DK_MAIN / 8; ++k) dst[k] = src[k];
-    uint4* dsta = reinterpret_cast<uint4*>(qaux + i * DK_AUX);
-    dsta[0] = src[DK_MAIN / 8];
-    dsta[1] = src[DK_MAIN / 8 + 1];
+    for (int k = 0; k < (DK_MAIN + DK_AUX) / 8; ++k) srow[k] = src[k];
+    __syncwarp();
+    const long long i0 = i - lane;
+    uint4* dmain = reinterpret_cast<uint4*>(qmain + i0 * DK_MAIN);
+#pragma unroll
+    for (int t = lane; t < 32 * DK_MAIN / 8; t += 32)
+      dmain[t] = reinterpret_cast<const uint4*>(stage[wid][t / (DK_MAIN / 8)])[t % (DK_MAIN / 8)];
+    uint4* daux = reinterpret_cast<uint4*>(qaux + i0 * DK_AUX);
+#pragma unroll
+    for (int t = lane; t < 32 * DK_AUX / 8; t += 32)
+      daux[t] = reinterpret_cast<const uint4*>(stage[wid][t / (DK_AUX / 8)])[DK_MAIN / 8 + t % (DK_AUX / 8)];
+    __syncwarp();
   }
 }
 
@@ -423,7 +436,9 @@ __global__ void __launch_bounds__(256) k_pack_keys_w(const float* __restrict__ k
 // key's row.  kp half tiles each hold a score no larger than it, so at least kp
 // scores of the key are <= it: published (+1 in the order key, the filter is
 // strict) it is a valid bound for the scan that keeps candidates.  One warp per
-// key, exact 4-pass radix select over the order-preserving keys.
+// key, 4-pass radix select over the order-preserving keys, stopping after the third
+// pass when the kp-th minimum closes its bin (the bin's upper end is then as valid a
+// bound, at most 256 ulps looser).
 __global__ void __launch_bounds__(256) k_tau_bound(const float* __restrict__ mins, const int32_t* __restrict__ n_found,
                                                    int n_img, int N, int Npad, int L, int kp,
                                                    uint32_t* __restrict__ tau_gl) {
@@ -462,7 +477,7 @@ __global__ void __launch_bounds__(256) k_tau_bound(const float* __restrict__ min
       }
       const int excl = incl - sum;
       const int owner = __ffs(__ballot_sync(0xffffffffu, excl < rank && rank <= incl)) - 1;
-      int sel = 0, before = 0;
+      int sel = 0, before = 0, in_bin = 0;
       if (lane == owner) {
         int c = excl;
 #pragma unroll
@@ -470,6 +485,7 @@ __global__ void __launch_bounds__(256) k_tau_bound(const float* __restrict__ min
           if (c + loc[t] >= rank) {
             sel = lane * 8 + t;
             before = c;
+            in_bin = loc[t];
             break;
           }
           c += loc[t];
@@ -477,10 +493,18 @@ __global__ void __launch_bounds__(256) k_tau_bound(const float* __restrict__ min
       }
       sel = __shfl_sync(0xffffffffu, sel, owner);
       before = __shfl_sync(0xffffffffu, before, owner);
+      in_bin = __shfl_sync(0xffffffffu, in_bin, owner);
       rank -= before;
       prefix |= (uint32_t)sel << shift;
       pmask |= 255u << shift;
       __syncwarp();
+      // the kp-th minimum is the largest of its bin: at least kp minima lie at or below
+      // the bin's upper end, which bounds the scan as well; stop refining once a bin
+      // spans at most 2^8 order keys (the bound stays within 256 ulps)
+      if (rank == in_bin && shift <= 8) {
+        prefix |= (1u << shift) - 1u;
+        break;
+      }
     }
     // a finite kp-th minimum bounds the scan (an infinite one says nothing)
     if (lane == 0 && prefix < float_order_key(INFINITY)) atomicMin(tau_gl + (long long)f * Npad + k, prefix + 1u);
