@@ -599,7 +599,8 @@ def autotune_match(x, P, keys, n_found, K, mode="bf16", candidates=None, repeats
     if candidates is None:
         eb = (2, 4) if mode != "fp32" else (0,)
         bp = (1, -1) if mode != "fp32" else (0,)
-        candidates = [(K + 16, sp, cap, e, b) for sp in (1, 2, 3) for cap in (0, 128, 192, 320) for e in eb
+        # position splits up to 8: with few key tiles (one large image) more splits fill the SMs
+        candidates = [(K + 16, sp, cap, e, b) for sp in (1, 2, 3, 4, 6, 8) for cap in (0, 128, 320) for e in eb
                       for b in bp]
     candidates = [tuple(c) + (0,) * (5 - len(c)) for c in candidates]
     im = images_of(x, P)
