@@ -221,16 +221,31 @@ glr_status glr_debug_match_scores(const float* x, const glr_images* im, const in
                                   size_t ws_bytes, void* stream);
 
 /*
+ * Testing aid for the FP64 fallback of the low-rank step: sets the sweep cap of
+ * the FP32 register Jacobi used by glr_lowrank_groups (cap <= 0: the default 30)
+ * for later calls of this process and returns the previous setting (0 =
+ * default).  Groups that reach the cap are recomputed in FP64 (Gram matrix and a
+ * two-sided Jacobi); a small cap sends most groups there.  Not thread-safe.
+ */
+int32_t glr_debug_wnnm_sweep_cap(int32_t cap);
+
+/*
  * Grouping and low-rank step -- Eq. 5 (R~_i x) solved by WNNM (Section 2).
  * For every key the K matched patches form Y (d x K, d = C*P*P); with
  * Y = U S V^T, sigma_hat_i = sqrt(max(s_i^2 - K sigma_w^2, 0)),
  * tau_i = c_wnnm sigma_w^2 / (sigma_hat_i + 1e-8), s'_i = max(s_i - tau_i, 0),
  * the output is X^ = U diag(s') V^T.  The SVD is a one-sided Jacobi in FP32
- * (columns in registers for d <= 64 and K <= 64, in shared memory otherwise).
+ * (columns in registers for d <= 64 and K <= 64, in shared memory otherwise;
+ * tall groups with K <= 32 through the Gram matrix).  Register-path groups that
+ * reach the 30-sweep cap are recomputed in FP64 (Gram matrix, two-sided Jacobi)
+ * by a second kernel in the same call; the status block counts them
+ * (svd_noconv).
  *
  *   idx      int32 [n_img][N][K] matches (from glr_match_topk).
  *   groups   out, float32 [n_img][N][K][d]: row j = column j of X^.
  *   rank     out (may be NULL), int32 [n_img][N]: number of s'_i > 0.
+ *   ws       glr_workspace_size(GLR_OP_LOWRANK, im, N, K, NULL) bytes (status block
+ *            and the FP64 fallback's queue).
  * Limits of this build: d <= 640, K <= 128, d % 4 == 0 (GLR_ENOTSUP otherwise).
  */
 glr_status glr_lowrank_groups(const float* x, const glr_images* im, const int32_t* idx,

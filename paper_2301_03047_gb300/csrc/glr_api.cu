@@ -142,8 +142,12 @@ size_t glr_workspace_size(int32_t op, const glr_images* im, int32_t N, int32_t K
     case GLR_OP_MATCH:
       if (N < 1 || K < 1 || K > 128 || K > npos) return 0;
       return match_plan(*im, N, K, opts).total;
-    case GLR_OP_LOWRANK:
-      return sizeof(StatusBlock);
+    case GLR_OP_LOWRANK: {
+      if (N < 1) return 0;
+      WsLayout L;
+      L.take((size_t)im->n_img * N * 4);  // queue of the FP64 fallback
+      return L.off;
+    }
     case GLR_OP_ADMM: {
       WsLayout L;
       L.take((size_t)im->n_img * sizeof(double));  // residual accumulators
@@ -217,6 +221,12 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
   return launch_match(x, *im, keys, n_found, N, pl, opts ? opts->encoder : nullptr, idx, dist, (char*)ws, s);
 }
 
+int32_t glr_debug_wnnm_sweep_cap(int32_t cap) {
+  const int32_t old = g_wnnm_sweep_cap;
+  g_wnnm_sweep_cap = cap > 0 ? cap : 0;
+  return old;
+}
+
 glr_status glr_debug_match_scores(const float* x, const glr_images* im, const int32_t* keys,
                                   const int32_t* n_found, int32_t N, int32_t K, float* scores, void* ws,
                                   size_t ws_bytes, void* stream) {
@@ -276,11 +286,14 @@ glr_status glr_lowrank_groups(const float* x, const glr_images* im, const int32_
   const int d = im->C * im->P * im->P;
   if (d > 640 || K > 128 || d % 4 != 0) return GLR_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
-  glr_status st = begin_ws(ws, ws_bytes, sizeof(StatusBlock), s);
+  glr_status st = begin_ws(ws, ws_bytes, glr_workspace_size(GLR_OP_LOWRANK, im, N, K, nullptr), s);
   if (st != GLR_OK) return st;
   st = launch_gather(x, *im, idx, n_found, N, K, groups, (StatusBlock*)ws, s);
   if (st != GLR_OK) return st;
-  if (d <= 64 && K <= 64) return launch_wnnm(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
+  WsLayout L;
+  int32_t* fb_queue = reinterpret_cast<int32_t*>((char*)ws + L.take((size_t)im->n_img * N * 4));
+  if (d <= 64 && K <= 64)
+    return launch_wnnm(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, fb_queue, s);
   // tall groups: Gram matrix + two-sided Jacobi (work O(d K^2) once instead of per sweep)
   if (K <= 32 && d >= 2 * K)
     return launch_gram_wnnm(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);

@@ -17,7 +17,7 @@ struct StatusBlock {
   uint32_t svd_noconv;     // groups that reached the sweep cap
   uint32_t sweeps;         // total Jacobi sweeps
   uint32_t groups;         // groups processed
-  uint32_t pad0;
+  uint32_t fb_count;       // groups queued for the FP64 low-rank fallback
   unsigned long long cand_appends;  // candidates appended by the top-K streams
   unsigned long long compactions;   // stream compactions
   uint32_t pad[54];

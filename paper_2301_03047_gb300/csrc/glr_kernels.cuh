@@ -93,8 +93,14 @@ glr_status launch_wnnm_fused(const float* x, const glr_images& im, const int32_t
                              StatusBlock* st, cudaStream_t s);
 glr_status launch_wnnm_complex_regs(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w,
                                    float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
+// fb_queue: n_img * N int32 of scratch for the FP64 fallback (nullptr: no fallback)
 glr_status launch_wnnm(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
-                       float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
+                       float* groups, int32_t* rank, StatusBlock* st, int32_t* fb_queue, cudaStream_t s);
+// FP64 Gram + two-sided Jacobi for the groups queued by the register kernel (k_lowrank_fp64.cu)
+glr_status launch_wnnm_fp64(int d, int K, float sigma_w, float c_wnnm, float* groups, int32_t* rank,
+                            const int32_t* queue, StatusBlock* st, cudaStream_t s);
+// testing aid: sweep cap of the register Jacobi (0: 30)
+extern int g_wnnm_sweep_cap;
 
 // ---- aggregation (k_aggregate.cu)
 struct AggWs {

@@ -252,7 +252,8 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
                                                             const int32_t* __restrict__ n_found, float sigma_w,
                                                             float c_wnnm, float tol, int max_sweeps,
                                                             float* __restrict__ groups, int32_t* __restrict__ rank,
-                                                            StatusBlock* st, FusedIO io) {
+                                                            StatusBlock* st, FusedIO io,
+                                                            int32_t* __restrict__ fb_queue) {
   extern __shared__ float wsm[];  // [WARPS][64][DMAX]: active columns of W
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float* Ws = wsm + (size_t)wid * 64 * DMAX;
@@ -414,6 +415,16 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
       atomicAdd(&st->svd_noconv, 1u);
       status_set(st, GLR_DEV_SVD_NOCONV);
     }
+    if (!FUSED && !converged && fb_queue != nullptr) {
+      // the sweep cap was reached: leave the group as gathered and queue it for the
+      // FP64 fallback, which writes X^ and the rank
+      if (lane == 0) {
+        fb_queue[atomicAdd(&st->fb_count, 1u)] = (int32_t)g;
+        atomicAdd(&st->sweeps, (unsigned)sweep);
+        atomicAdd(&st->groups, 1u);
+      }
+      continue;
+    }
     if (lane == 0) {
       atomicAdd(&st->sweeps, (unsigned)sweep);
       atomicAdd(&st->groups, 1u);
@@ -563,10 +574,13 @@ glr_status launch_gather(const float* x, const glr_images& im, const int32_t* id
   return GLR_OK;
 }
 
+// testing aid: sweep cap of the register Jacobi (0: 30)
+int g_wnnm_sweep_cap = 0;
+
 template <int DMAX, bool CPLX, bool FUSED = false>
 glr_status launch_wnnm_regs(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
                             float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s, const char* name,
-                            FusedIO io = FusedIO{}) {
+                            FusedIO io = FusedIO{}, int32_t* fb_queue = nullptr) {
   constexpr int WARPS = 4;
   const int d = im.C * im.P * im.P;
   const size_t smem = (size_t)WARPS * 64 * DMAX * sizeof(float);
@@ -576,15 +590,19 @@ glr_status launch_wnnm_regs(const glr_images& im, const int32_t* n_found, int N,
   const long long ngroups = (long long)im.n_img * N;
   const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(ngroups, WARPS), 152LL * 64));
   const float tol = 1e-5f;
-  GLR_LAUNCH(name, s, (k_jacobi_wnnm<DMAX, WARPS, CPLX, FUSED><<<blocks, WARPS * 32, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, 30, groups, rank, st, io)));
+  const int cap = g_wnnm_sweep_cap > 0 ? g_wnnm_sweep_cap : 30;
+  GLR_LAUNCH(name, s, (k_jacobi_wnnm<DMAX, WARPS, CPLX, FUSED><<<blocks, WARPS * 32, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, cap, groups, rank, st, io, fb_queue)));
   return GLR_OK;
 }
 
 glr_status launch_wnnm(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
-                       float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s) {
+                       float* groups, int32_t* rank, StatusBlock* st, int32_t* fb_queue, cudaStream_t s) {
   const int d = im.C * im.P * im.P;
   if (d > 64 || K > 64 || K < 1) return GLR_ENOTSUP;
-  return launch_wnnm_regs<64, false>(im, n_found, N, K, sigma_w, c_wnnm, groups, rank, st, s, "k_jacobi_wnnm");
+  glr_status r = launch_wnnm_regs<64, false>(im, n_found, N, K, sigma_w, c_wnnm, groups, rank, st, s,
+                                             "k_jacobi_wnnm", FusedIO{}, fb_queue);
+  if (r != GLR_OK || fb_queue == nullptr) return r;
+  return launch_wnnm_fp64(d, K, sigma_w, c_wnnm, groups, rank, fb_queue, st, s);
 }
 
 glr_status launch_wnnm_fused(const float* x, const glr_images& im, const int32_t* idx, const int32_t* n_found, int N,

@@ -131,6 +131,12 @@ def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, cap=0
     return idx, dist
 
 
+def debug_wnnm_sweep_cap(cap: int) -> int:
+    """Testing aid: sweep cap of the FP32 register Jacobi (<= 0: the default 30); returns the old one.
+    Groups that reach the cap are recomputed by the FP64 fallback."""
+    return int(L.load().glr_debug_wnnm_sweep_cap(int(cap)))
+
+
 def debug_match_scores(x, P, keys, n_found, K, *, ws=None, stream=None):
     """Raw BF16 tensor-core scores of every key against the first 256 positions (testing aid)."""
     lib = L.load()

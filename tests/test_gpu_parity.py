@@ -240,6 +240,47 @@ def test_lowrank_parity(case):
             assert abs(int(rk[f, i]) - int(ro[i])) <= 1
 
 
+@pytest.mark.parametrize("case", [("f1", 2, 1, 40, 44, 8, 30, 40, 0.3), ("f2", 1, 1, 30, 30, 8, 20, 64, 0.1),
+                                  ("f3", 1, 1, 25, 27, 4, 15, 7, 0.05), ("f4", 1, 1, 30, 30, 8, 10, 64, 0.0)])
+def test_lowrank_fp64_fallback(case):
+    """A sweep cap of 1 sends the groups the FP32 Jacobi cannot finish in one sweep to the FP64
+    fallback (Gram matrix + two-sided Jacobi); its X^ is the oracle's to FP32 output rounding and
+    its rank the oracle's over the components an FP64 Gram matrix resolves."""
+    tag, F, C, H, W, P, N, K, sw = case
+    x = scene(tag, F, H, W, quant=False, C=C)
+    rng = synth.rng_for(tag + "idx")
+    npos = (H - P + 1) * (W - P + 1)
+    idx = rng.integers(0, npos, size=(F, N, K)).astype(np.int32)
+    nf = np.full(F, N, np.int32)
+    cw = 2 * math.sqrt(K)
+    im = glr.images(F, C, H, W, P)
+    ws = glr.workspace(glr.L.GLR_OP_LOWRANK, im, N, K)
+    old = glr.debug_wnnm_sweep_cap(1)
+    try:
+        groups, rank = glr.lowrank_groups(cuda(x), P, cuda(idx, torch.int32), cuda(nf, torch.int32), sw, cw, ws=ws)
+        torch.cuda.synchronize()
+        _, cnt = glr.poll_status(ws)
+    finally:
+        glr.debug_wnnm_sweep_cap(old)
+    assert cnt[1] > 0  # groups sent to the fallback
+    g = groups.cpu().numpy()
+    rk = rank.cpu().numpy()
+    d = C * P * P
+    for f in range(F):
+        Y = O.gather_groups(x[f], P, idx[f])
+        Xo, _ = O.lowrank_groups(Y, sw, cw, eps=1e-8)
+        for i in range(N):
+            # FP64 arithmetic, FP32 output: 50x tighter than the FP32 Jacobi's bar
+            scale = np.linalg.norm(Y[i]) / math.sqrt(d * K)
+            err = g[f, i] - Xo[i]
+            assert np.sqrt(np.mean(err**2)) <= 4e-6 * max(scale, 1e-3), (f, i)
+            assert np.abs(err).max() <= 2e-5 * max(np.abs(Y[i]).max(), 1e-3)
+            _, _, sv, s_new = O.wnnm(Y[i].T, sw, cw, eps=1e-8)
+            tol = math.sqrt(2 * max(d, K) * 2.0 ** -52) * sv[0]
+            ro = int(np.count_nonzero((s_new > 0) & (sv > tol)))
+            assert abs(int(rk[f, i]) - ro) <= 1, (f, i, int(rk[f, i]), ro)
+
+
 def test_lowrank_noiseless_low_rank_recovery():
     """Groups of exactly rank 2 are returned unchanged (up to FP32) for a tiny sigma_w."""
     H, W, P, K = 20, 20, 8, 32
