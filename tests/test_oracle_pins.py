@@ -386,10 +386,10 @@ def test_sigma_schedule_reading():
     cfg = synth.scaled(synth.SCI_SMALL, T=8, H=64, W=64, N=100)
     prob = synth.sci_problem(cfg)
     res = {}
-    for name, sched in (("survey", [0.08, 0.04, 0.02]), ("used", [0.5, 0.3, 0.15])):
+    for name, sched in (("low", [0.08, 0.04, 0.02]), ("used", [0.5, 0.3, 0.15])):
         x = O.glr_reconstruct(prob.y, prob.masks, cfg.P, cfg.N, cfg.K, sched, cfg.c_wnnm, cfg.edge_th)
         res[name] = O.psnr_framewise(x, prob.truth)
-    assert res["used"] > res["survey"] + 8.0, res
+    assert res["used"] > res["low"] + 8.0, res
 
 
 # ---------------------------------------------------------------------------
