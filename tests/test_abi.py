@@ -49,6 +49,11 @@ def test_workspace_size_validation(lib):
     assert lib.glr_workspace_size(L.GLR_OP_SELECT, ctypes.byref(bad), 10, 1, None) == 0
     assert lib.glr_workspace_size(L.GLR_OP_SELECT, ctypes.byref(im), 57 * 57 + 1, 1, None) == 0
     assert lib.glr_workspace_size(99, ctypes.byref(im), 10, 1, None) == 0
+    # low-rank step: status block + the FP64 fallback's queue (one int32 per group)
+    small = lib.glr_workspace_size(L.GLR_OP_LOWRANK, ctypes.byref(im), 100, 10, None)
+    large = lib.glr_workspace_size(L.GLR_OP_LOWRANK, ctypes.byref(im), 4000, 10, None)
+    assert 256 + 2 * 100 * 4 <= small < large and large >= 256 + 2 * 4000 * 4
+    assert lib.glr_workspace_size(L.GLR_OP_LOWRANK, ctypes.byref(im), 0, 10, None) == 0
 
 
 def test_entry_points_reject_bad_arguments_on_host(lib):
