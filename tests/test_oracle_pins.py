@@ -497,3 +497,118 @@ def test_window_matching_is_global_matching_restricted():
     gi, gd = O.match_topk(xs, P, np.array([37]), K, Qs)
     wi, wd = O.window_match_topk(xs, P, np.array([37]), K, 5, Qs)
     assert np.array_equal(gi, wi) and np.allclose(gd, wd)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 5 glue: lowrank_groups, glr_denoise; Eq. 6 loops: glr_reconstruct(_admm)
+# ---------------------------------------------------------------------------
+def test_lowrank_groups_shrinks_with_member_count_k():
+    """lowrank_groups reads a group [K][d] as the d x K matrix of Eq. 5: the noise term of
+    sigma_hat is K sigma_w^2 with K the number of members.  A rank-1 group with K = 3 members
+    of d = 5 values, s^2 = 2.4 and sigma_w^2 = 0.6 lies between K sigma_w^2 = 1.8 (kept) and
+    d sigma_w^2 = 3.0 (which would remove it), so reading d for K, or a transposed group,
+    changes the result.  By hand: sigma_hat = sqrt(0.6), tau = 0.5 * 0.6 / sqrt(0.6) = sqrt(0.6) / 2,
+    s = sqrt(2.4) = 2 sqrt(0.6), s' = s - tau = 1.5 sqrt(0.6), X^ = (s'/s) Y = 0.75 Y."""
+    a = np.array([1.0, 1.0, 1.0])  # member weights (K = 3)
+    b = np.full(5, 0.4)  # patch (d = 5)
+    g = np.outer(a, b)[None]  # [N=1][K=3][d=5]
+    out, rank = O.lowrank_groups(g, math.sqrt(0.6), 0.5)
+    assert out.shape == (1, 3, 5)
+    assert rank.tolist() == [1]
+    np.testing.assert_allclose(out[0], 0.75 * g[0], rtol=1e-12, atol=1e-14)
+    # the same group with 5 members of 3 values: now K sigma_w^2 = 3.0 > s^2 = 2.4, removed
+    out2, rank2 = O.lowrank_groups(np.outer(b, a)[None], math.sqrt(0.6), 0.5)
+    assert rank2.tolist() == [0] and np.all(out2 == 0)
+
+
+def test_glr_denoise_without_noise_returns_the_image():
+    """sigma_w = 0: WNNM keeps every singular value (tau = 0), so each group comes back
+    unchanged and averaging the exact patches returns x wherever a patch covers it and x
+    itself elsewhere: the whole pass is the identity (two channels, P = 3)."""
+    rng = synth.rng_for("denoise-identity")
+    x = rng.random((2, 2, 12, 13))
+    v, info = O.glr_denoise(x, 3, 20, 5, 0.0, 4.0, 0.1)
+    np.testing.assert_allclose(v, x, rtol=0, atol=1e-12)
+    assert all(len(i["keys"]) == 20 for i in info)
+
+
+def test_glr_denoise_constant_image_closed_form():
+    """A constant image c: no corners, so the keys are the reading-A5 grid; every distance is
+    0, so every key's K matches are positions 0..K-1 (ties by id); each group is c times a
+    d x K matrix of ones with s = c sqrt(dK), and WNNM scales it by s'/s.  Covered pixels
+    (rows 0..P-1, columns 0..K+P-2) become c s'/s, the rest keep c."""
+    c, P, N, K, sw = 0.5, 3, 10, 4, 0.4
+    H = W = 10
+    x = np.full((1, 1, H, W), c)
+    C_w = 2.0 * math.sqrt(K)
+    v, info = O.glr_denoise(x, P, N, K, sw, C_w, 0.1)
+    d = P * P
+    s = c * math.sqrt(d * K)
+    s_hat = math.sqrt(s * s - K * sw * sw)
+    s_new = s - C_w * sw * sw / s_hat
+    want = np.full((H, W), c)
+    want[:P, : K + P - 1] = c * s_new / s
+    np.testing.assert_allclose(v[0, 0], want, rtol=1e-12)
+    assert info[0]["n_corner"] == 0
+    assert np.all(info[0]["idx"] == np.arange(K))
+
+
+def test_glr_reconstruct_full_mask_is_the_projection():
+    """One frame behind a mask of 2 everywhere: R = 4, x0 = 2 y / 4 = y / 2, and the GAP update
+    x = v + 2 (y - 2 v) / 4 = y / 2 whatever the denoiser returned.  So the reconstruction is
+    y / 2 exactly; a dropped R, R = sum A instead of sum A^2, or a flipped residual sign fails."""
+    rng = synth.rng_for("gap-full-mask")
+    y = rng.random((9, 11))
+    masks = np.full((1, 9, 11), 2.0)
+    x = O.glr_reconstruct(y, masks, 3, 12, 4, [0.3, 0.1], 4.0, 0.1)
+    np.testing.assert_allclose(x, (y / 2.0)[None], rtol=0, atol=1e-12)
+
+
+def test_glr_reconstruct_identity_denoiser_keeps_x0():
+    """sigma_w = 0 makes the denoiser the identity (previous pin), and x0 = Phi^T(y/R) already
+    satisfies Phi x0 = y where R > 0, so every GAP iteration returns x0 = A_t y / R (0 where
+    no mask is set), computed here by hand."""
+    rng = synth.rng_for("gap-identity")
+    T, H, W = 3, 10, 12
+    masks = (rng.random((T, H, W)) < 0.5).astype(np.float64)
+    y = rng.random((H, W))
+    R = masks.sum(0)
+    x0 = masks * np.where(R > 0, y / np.where(R > 0, R, 1.0), 0.0)[None]
+    x = O.glr_reconstruct(y, masks, 3, 15, 4, [0.0, 0.0], 4.0, 0.1)
+    np.testing.assert_allclose(x, x0, rtol=0, atol=1e-12)
+
+
+def _zero_denoiser_case(tag, T):
+    """Random frames small enough that every position can be a key (N = Hq Wq): every pixel
+    is then covered by its own key's patch (the unique distance-0 match of a random image),
+    and with a huge sigma_w (sigma_hat = 0, tau = C sw^2 / eps) WNNM removes every group,
+    so the denoiser returns exactly 0."""
+    rng = synth.rng_for(tag)
+    H, W, P = 7, 8, 2
+    masks = (rng.random((T, H, W)) < 0.6).astype(np.float64) if T > 1 else np.full((1, H, W), 2.0)
+    y = 0.2 + rng.random((H, W))
+    N = (H - P + 1) * (W - P + 1)
+    return y, masks, P, N
+
+
+def test_glr_reconstruct_accelerated_with_zero_denoiser():
+    """Accelerated GAP with v = 0: y_acc = y + (y - 0) = 2y after the first iteration and 3y after
+    the second, so x_k = (k + 1) Phi^T(y / R) (by hand): pins the residual accumulation."""
+    y, masks, P, N = _zero_denoiser_case("gap-acc-zero", 3)
+    v, _ = O.glr_denoise(O.gap_init(y, masks)[:, None], P, N, 2, 1e3, 4.0, 0.1)
+    assert np.all(v == 0)
+    R = masks.sum(0)
+    x0 = masks * np.where(R > 0, y / np.where(R > 0, R, 1.0), 0.0)[None]
+    x = O.glr_reconstruct(y, masks, P, N, 2, [1e3, 1e3], 4.0, 0.1, accelerate=True)
+    np.testing.assert_allclose(x, 3.0 * x0, rtol=1e-12, atol=1e-14)
+
+
+def test_glr_reconstruct_admm_with_zero_denoiser_closed_form():
+    """Scaled ADMM (reading A20), one frame behind a mask of 2 (R = 4), rho = 1, z = D(.) = 0:
+    x0 = y/2; iteration 1: u = x0 = y/2, w = -y/2, x1 = w + 2 (y - 2 w) / 5 = 0.3 y;
+    iteration 2: u = 0.5 y + 0.3 y = 0.8 y, w = -0.8 y, x2 = -0.8 y + 2 (y + 1.6 y) / 5 = 0.24 y."""
+    y, masks, P, N = _zero_denoiser_case("admm-zero", 1)
+    x1 = O.glr_reconstruct_admm(y, masks, P, N, 2, [1e3], 4.0, 0.1, 1.0)
+    np.testing.assert_allclose(x1, (0.3 * y)[None], rtol=1e-12)
+    x2 = O.glr_reconstruct_admm(y, masks, P, N, 2, [1e3, 1e3], 4.0, 0.1, 1.0)
+    np.testing.assert_allclose(x2, (0.24 * y)[None], rtol=1e-12)
