@@ -87,15 +87,57 @@ def oracle_sample(n_keys: int = 24) -> dict:
     }
 
 
-def run_oracle_child(n_keys: int, fn: str = "oracle_sample") -> dict:
+def _oracle_cmd(n_keys: int, fn: str):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
     code = f"import json,sys; sys.path.insert(0,{ROOT!r}); import bench; print(json.dumps(bench.{fn}({n_keys})))"
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    return [sys.executable, "-c", code], env
+
+
+def run_oracle_child(n_keys: int, fn: str = "oracle_sample") -> dict:
+    cmd, env = _oracle_cmd(n_keys, fn)
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError("oracle child failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_all_cores(n_keys: int, fn: str = "oracle_sample", procs: int | None = None) -> dict:
+    """The same sample on every host core at once: `procs` single-threaded children run side by
+    side (their per-key and per-frame times include the contention for memory bandwidth), and the
+    full iteration's work is divided over them (frames and keys are independent units)."""
+    procs = procs or os.cpu_count() or 1
+    cmd, env = _oracle_cmd(n_keys, fn)
+    children = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT)
+                for _ in range(procs)]
+    outs = []
+    for c in children:
+        out, err = c.communicate()
+        if c.returncode != 0:
+            raise RuntimeError("oracle child failed: " + err[-2000:])
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    t_iter_1 = statistics.mean(o["t_iter_s"] for o in outs)  # one core's share of the iteration, under load
+    res = dict(outs[0])
+    res["t_iter_s"] = t_iter_1 / procs
+    res["iters_per_s"] = procs / t_iter_1
+    res["pair_dists_per_s"] = sum(o["pair_dists_per_s"] for o in outs)
+    res["procs"] = procs
+    res["sample"] = f"{procs} single-threaded processes at once, each: " + outs[0]["sample"] + \
+        f"; the iteration divided over the {procs} cores"
+    return res
+
+
+def cpu_baseline_entry(n_keys: int, fn: str, unit: str = "iter/s") -> dict:
+    """cpu_baseline: the oracle on all host cores (value) and on one core (single_core), nproc recorded."""
+    one = run_oracle_child(n_keys, fn)
+    allc = run_oracle_all_cores(max(4, n_keys // 4), fn)
+    return {"value": round(allc["iters_per_s"], 8), "unit": unit, "cores": allc["procs"], "nproc": os.cpu_count(),
+            "kind": "oracle", "sample": allc["sample"], "t_iter_s": round(allc["t_iter_s"], 1),
+            "pair_dists_per_s": round(allc["pair_dists_per_s"], 1),
+            "single_core": {"value": round(one["iters_per_s"], 8), "unit": unit, "cores": 1, "sample": one["sample"],
+                            "t_iter_s": round(one["t_iter_s"], 1),
+                            "pair_dists_per_s": round(one["pair_dists_per_s"], 1)}}
 
 
 # ---------------------------------------------------------------------------
@@ -481,12 +523,9 @@ def run_glr(args) -> None:
     cpu = None
     if not args.no_cpu:
         try:
-            o = run_oracle_child(args.oracle_keys)
-            cpu = {"value": round(o["iters_per_s"], 8), "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": o["sample"], "pair_dists_per_s": round(o["pair_dists_per_s"], 1),
-                   "t_iter_s": round(o["t_iter_s"], 1)}
+            cpu = cpu_baseline_entry(args.oracle_keys, "oracle_sample")
         except Exception as e:  # the CPU baseline must not hide the GPU result
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
     rl = roofline(prof, cfg, sweeps, clocks_summary or {}, pk) if prof else None
     kernels = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])} if prof else {}
     line = {
@@ -708,11 +747,9 @@ def run_mri(args, cfg, dev, dist) -> None:
     cpu = None
     if not args.no_cpu:
         try:
-            o = run_oracle_child(args.oracle_keys, "oracle_sample_mri")
-            cpu = {"value": round(o["iters_per_s"], 8), "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": o["sample"], "t_iter_s": round(o["t_iter_s"], 1)}
+            cpu = cpu_baseline_entry(args.oracle_keys, "oracle_sample_mri")
         except Exception as e:
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
     npos = (cfg.H - cfg.P + 1) * (cfg.W - cfg.P + 1)
     rl = roofline(prof, cfg, sweeps, clocks_summary or {}, pk, n_img=1, d=2 * cfg.P * cfg.P) if prof else None
     line = {
@@ -904,11 +941,9 @@ def run_msfa(args, cfg, dev, dist) -> None:
     cpu = None
     if not args.no_cpu:
         try:
-            o = run_oracle_child(min(args.oracle_keys, 16), "oracle_sample_msfa")
-            cpu = {"value": round(o["iters_per_s"], 8), "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": o["sample"], "t_iter_s": round(o["t_iter_s"], 1)}
+            cpu = cpu_baseline_entry(min(args.oracle_keys, 16), "oracle_sample_msfa")
         except Exception as e:
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
     pk = peaks()
     rl = None
     if prof:
@@ -1017,14 +1052,16 @@ def run_reference(args) -> None:
     cfg = synth.SCI_LARGE
     vals = []
     o = None
-    # each step is one bounded oracle sample; one short warm-up sample is discarded
+    # each step is one bounded oracle sample on all host cores; one short warm-up sample is
+    # discarded; one single-core sample is recorded beside the result
     if args.warmup > 0:
         run_oracle_child(2)
     t0 = time.perf_counter()
     for i in range(args.steps):
-        o = run_oracle_child(args.oracle_keys)
+        o = run_oracle_all_cores(max(4, args.oracle_keys // 4))
         vals.append(o["t_iter_s"])
     wall = time.perf_counter() - t0
+    one = run_oracle_child(args.oracle_keys)
     t_iter = statistics.mean(vals)
     value = 1.0 / t_iter
     npos = (cfg.H - cfg.P + 1) * (cfg.W - cfg.P + 1)
@@ -1044,7 +1081,10 @@ def run_reference(args) -> None:
         "data": "synthetic (seeded moving-shapes scenes, Bernoulli masks)",
         "config": {"workload": cfg.name, "frames": cfg.T, "H": cfg.H, "W": cfg.W, "P": cfg.P, "N": cfg.N, "K": cfg.K,
                    "positions_per_frame": npos, "match_form": "oracle FP64 direct distances"},
-        "cpu_baseline": {"value": round(value, 8), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": o["sample"]},
+        "cpu_baseline": {"value": round(value, 8), "unit": UNIT, "cores": o["procs"], "nproc": os.cpu_count(),
+                         "kind": "oracle", "sample": o["sample"],
+                         "single_core": {"value": round(one["iters_per_s"], 8), "unit": UNIT, "cores": 1,
+                                         "sample": one["sample"]}},
         "e2e": {"value": round(value, 8), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": round(wall, 1),
         "pair_dists_per_s": round(o["pair_dists_per_s"], 1),

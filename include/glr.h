@@ -221,6 +221,19 @@ glr_status glr_debug_match_scores(const float* x, const glr_images* im, const in
                                   size_t ws_bytes, void* stream);
 
 /*
+ * Testing aid for the bounded waits of the tensor-core scorer (BF16, LEARNED and
+ * EDGE modes): sets the limit, in nanoseconds of %globaltimer, of the waits
+ * between its producer, MMA and epilogue warps for later calls of this process
+ * (0: the default of 1 s) and returns the previous setting.  A wait that runs
+ * out sets GLR_DEV_TIMEOUT (glr_poll_status then returns GLR_ETIMEDOUT) and the
+ * CTA stops its work; the copies and MMAs it already issued are still waited
+ * for with the full second, so nothing is in flight when it exits.  The
+ * matches of such a call are incomplete.  The paper has no counterpart.  Not
+ * thread-safe.
+ */
+uint64_t glr_debug_match_wait_ns(uint64_t ns);
+
+/*
  * Testing aid for the FP64 fallback of the low-rank step: sets the sweep cap of
  * the FP32 register Jacobi used by glr_lowrank_groups (cap <= 0: the default 30)
  * for later calls of this process and returns the previous setting (0 =
@@ -311,8 +324,10 @@ glr_status glr_aggregate(const float* groups, const int32_t* idx, const int32_t*
  * array and leave their contents in it (each call clears what must start at
  * zero); calls that overlap on the GPU race on it, so serialise them.  The
  * first call on a device looks the array's address up with that device
- * current and caches it: make that call before any stream capture.  Nothing
- * is allocated or freed.
+ * current and caches it: make that call before any stream capture.  Device-side
+ * conditions (a match id outside the position grid: that entry is skipped) go
+ * to a status block in the array; read it with glr_poll_status(NULL, ...) on
+ * the same device once the stream is done.  Nothing is allocated or freed.
  */
 glr_status glr_aggregate_noalloc(const float* groups, const int32_t* idx, const int32_t* n_found,
                                  const glr_images* im, int32_t N, int32_t K, const float* x_in,
@@ -399,12 +414,15 @@ glr_status glr_admm_step(const float* y, const float* mask, const float* z, cons
 
 /*
  * Reads the status block of a workspace used by an earlier call (blocks on
- * `stream`).  bits = OR of GLR_DEV_*; counters (may be NULL) receives 6
- * uint32 values: [0] keys whose candidate buffer overflowed, [1] groups whose
- * SVD hit the sweep cap, [2] total Jacobi sweeps, [3] groups processed,
- * [4] candidates appended by the matching top-K streams (saturating),
- * [5] top-K stream compactions (saturating).
- * Returns GLR_EDEVICE if any error bit (timeout, non-finite, bad index) is set.
+ * `stream`).  ws == NULL reads the status block of glr_aggregate_noalloc's
+ * scratch array on the current device instead.  bits = OR of GLR_DEV_*;
+ * counters (may be NULL) receives 7 uint32 values: [0] keys whose candidate
+ * buffer overflowed, [1] groups whose SVD hit the FP32 sweep cap, [2] total
+ * Jacobi sweeps, [3] groups processed, [4] candidates appended by the matching
+ * top-K streams (saturating), [5] top-K stream compactions (saturating),
+ * [6] groups whose FP64 fallback also reached its sweep cap.
+ * Returns GLR_ETIMEDOUT if a bounded device wait expired (GLR_DEV_TIMEOUT),
+ * else GLR_EDEVICE if another error bit (non-finite, bad index) is set.
  * Pass reset != 0 to clear the block afterwards.
  */
 glr_status glr_poll_status(const void* ws, uint32_t* bits, uint32_t* counters, int32_t reset,

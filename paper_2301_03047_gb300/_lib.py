@@ -39,6 +39,7 @@ PROTOTYPES = {
     "glr_match_topk": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, ctypes.POINTER(GlrMatchOpts), c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_debug_match_scores": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_debug_wnnm_sweep_cap": (c_int32, [c_int32]),
+    "glr_debug_match_wait_ns": (ctypes.c_uint64, [ctypes.c_uint64]),
     "glr_encoder_embed": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_encoder_train_step": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_float, c_float, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_lowrank_groups": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

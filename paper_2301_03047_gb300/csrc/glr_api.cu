@@ -15,6 +15,18 @@ namespace glr {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
+// Streaming multiprocessors of the current device, read once per device (grid sizing).
+static std::atomic<int> g_sm_count[64];
+int num_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  int n = g_sm_count[dev].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 152;
+  g_sm_count[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
 // ---- optional per-kernel event timing (host side, single-threaded use)
 namespace {
 struct ProfRec {
@@ -221,6 +233,12 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
   return launch_match(x, *im, keys, n_found, N, pl, opts ? opts->encoder : nullptr, idx, dist, (char*)ws, s);
 }
 
+uint64_t glr_debug_match_wait_ns(uint64_t ns) {
+  const uint64_t old = g_match_wait_ns;
+  g_match_wait_ns = ns;
+  return old;
+}
+
 int32_t glr_debug_wnnm_sweep_cap(int32_t cap) {
   const int32_t old = g_wnnm_sweep_cap;
   g_wnnm_sweep_cap = cap > 0 ? cap : 0;
@@ -415,7 +433,14 @@ glr_status glr_gap_step(const float* y, const float* masks, int64_t mask_group_s
 }
 
 glr_status glr_poll_status(const void* ws, uint32_t* bits, uint32_t* counters, int32_t reset, void* stream) {
-  if (!ws || !bits) return GLR_EINVAL;
+  if (!bits) return GLR_EINVAL;
+  if (!ws) {
+    // the status block of glr_aggregate_noalloc's scratch array on the current device
+    void* p = nullptr;
+    const glr_status r = noalloc_scratch_address(&p);
+    if (r != GLR_OK) return r;
+    ws = p;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   StatusBlock h;
   if (cudaMemcpyAsync(&h, ws, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GLR_ECUDA;
@@ -428,11 +453,13 @@ glr_status glr_poll_status(const void* ws, uint32_t* bits, uint32_t* counters, i
     counters[3] = h.groups;
     counters[4] = (uint32_t)std::min<unsigned long long>(h.cand_appends, 0xffffffffull);
     counters[5] = (uint32_t)std::min<unsigned long long>(h.compactions, 0xffffffffull);
+    counters[6] = h.fb_noconv;
   }
   if (reset) {
     if (cudaMemsetAsync(const_cast<void*>(ws), 0, sizeof(StatusBlock), s) != cudaSuccess) return GLR_ECUDA;
   }
-  return (h.bits & (GLR_DEV_TIMEOUT | GLR_DEV_NONFINITE | GLR_DEV_BAD_INDEX)) ? GLR_EDEVICE : GLR_OK;
+  if (h.bits & GLR_DEV_TIMEOUT) return GLR_ETIMEDOUT;
+  return (h.bits & (GLR_DEV_NONFINITE | GLR_DEV_BAD_INDEX)) ? GLR_EDEVICE : GLR_OK;
 }
 
 }  // extern "C"

@@ -20,7 +20,8 @@ struct StatusBlock {
   uint32_t fb_count;       // groups queued for the FP64 low-rank fallback
   unsigned long long cand_appends;  // candidates appended by the top-K streams
   unsigned long long compactions;   // stream compactions
-  uint32_t pad[54];
+  uint32_t fb_noconv;      // groups the FP64 fallback did not converge within its sweep cap
+  uint32_t pad[53];
 };
 static_assert(sizeof(StatusBlock) == 256, "status block is 256 bytes");
 
@@ -65,6 +66,11 @@ __device__ inline void status_set(StatusBlock* st, uint32_t bit) { atomicOr(&st-
 
 // host: launch counting and optional per-kernel event timing (glr_api.cu)
 void note_launch(int n = 1);
+// host: streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, cached)
+int num_sms();
+// host: device address of glr_aggregate_noalloc's scratch array on the current device
+// (its first 256 bytes are that entry point's status block; glr_noalloc.cu)
+glr_status noalloc_scratch_address(void** out);
 void prof_begin(cudaStream_t s);
 void prof_end(const char* name, cudaStream_t s);
 

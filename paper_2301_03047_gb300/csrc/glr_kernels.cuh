@@ -71,6 +71,8 @@ glr_status launch_encoder_train(const float* x, const glr_images& im, const floa
 // testing aid: when set, the tensor-core scorer also writes the raw scores of the
 // first position tile, [n_img][Npad][256] float32, to this device buffer
 extern float* g_tc_dump;
+// testing aid: limit of the tensor-core scorer's pipeline waits in ns (0: 1 s)
+extern unsigned long long g_match_wait_ns;
 
 // ---- low-rank step (k_lowrank.cu)
 glr_status launch_gather(const float* x, const glr_images& im, const int32_t* idx, const int32_t* n_found, int N,

@@ -21,6 +21,9 @@
 //   * The first call on a device looks up the array's device address (with that
 //     device current) and caches it; make that first call before any stream
 //     capture on the device.
+//   * Device-side conditions (a match id outside the position grid, whose entry is
+//     skipped) are recorded in a status block at the start of the array; read it
+//     with glr_poll_status(NULL, ...) on the same device after the stream is done.
 //   * No cudaMalloc, cudaFree or other allocating routine is called.
 #include <mutex>
 
@@ -37,8 +40,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};
 
+}  // namespace
+
 // Device address of the scratch array on the current device (looked up once per device).
-glr_status noalloc_scratch(void** out) {
+glr_status noalloc_scratch_address(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GLR_ECUDA;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -50,8 +55,6 @@ glr_status noalloc_scratch(void** out) {
   *out = g_noalloc_ptr[dev];
   return GLR_OK;
 }
-
-}  // namespace
 
 }  // namespace glr
 
@@ -70,7 +73,7 @@ extern "C" glr_status glr_aggregate_noalloc(const float* groups, const int32_t* 
   const AggWs L = agg_ws_layout(*im);
   if (L.total > kNoAllocScratchBytes) return GLR_ETOOBIG;
   void* ws = nullptr;
-  const glr_status st = noalloc_scratch(&ws);
+  const glr_status st = noalloc_scratch_address(&ws);
   if (st != GLR_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(ws, 0, sizeof(StatusBlock), s) != cudaSuccess) return GLR_ECUDA;

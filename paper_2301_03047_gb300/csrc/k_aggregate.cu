@@ -144,7 +144,7 @@ glr_status launch_aggregate(const float* groups, const int32_t* idx, const int32
   if (cudaMemsetAsync(cnt, 0, cnt_b, s) != cudaSuccess) return GLR_ECUDA;
   const bool per_row = im.C * im.P * im.P > 128;
   const long long units = (long long)im.n_img * N * (per_row ? K : 1);
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(units * 32, 256), 152LL * 32));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(units * 32, 256), (long long)num_sms() * 32));
 #define GLR_SCATTER_CASE(PP, ROW)                                                                            \
   GLR_LAUNCH("k_scatter", s,                                                                                 \
              (k_scatter<PP, ROW><<<blocks, 256, 0, s>>>(groups, idx, n_found, im.n_img, im.C, im.H, im.W, im.P, N, \

@@ -271,7 +271,7 @@ __global__ void k_adamw(float* __restrict__ params, const float* __restrict__ gr
 glr_status launch_encode_positions(const float* x, const glr_images& im, const float* mean, const float* params,
                                    float* emb, cudaStream_t s) {
   const long long total = (long long)im.n_img * (im.H - im.P + 1) * (im.W - im.P + 1);
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 128), 152LL * 16));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 128), (long long)num_sms() * 16));
   const size_t smem = NPARAM * 4;
   GLR_LAUNCH("k_encode_positions", s,
              k_encode_positions<<<blocks, 128, smem, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, params, emb));
@@ -280,7 +280,7 @@ glr_status launch_encode_positions(const float* x, const glr_images& im, const f
 
 glr_status launch_encode_vectors(const float* vecs, long long n, int d, const float* params, float* emb,
                                  cudaStream_t s) {
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(n, 128), 152LL * 16));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(n, 128), (long long)num_sms() * 16));
   GLR_LAUNCH("k_encode_vectors", s, k_encode_vectors<<<blocks, 128, NPARAM * 4, s>>>(vecs, n, d, params, emb));
   return GLR_OK;
 }

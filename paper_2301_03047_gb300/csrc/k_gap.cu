@@ -73,7 +73,7 @@ glr_status launch_gap_step(const float* y, const float* masks, long long mstride
                    (mstride % 4 == 0) && (!v || (uintptr_t)v % 16 == 0) && ((uintptr_t)x_out % 16 == 0) &&
                    (!y_acc || (uintptr_t)y_acc % 16 == 0);
   const long long work = (long long)G * (vec ? HW / 4 : HW);
-  int blocks = (int)std::min<long long>(ceil_div(work, 256), 152LL * 16);
+  int blocks = (int)std::min<long long>(ceil_div(work, 256), (long long)num_sms() * 16);
   if (blocks < 1) blocks = 1;
   if (vec)
     GLR_LAUNCH("k_gap_step", s, k_gap_step<true><<<blocks, 256, 0, s>>>(y, masks, mstride, v, G, T, HW, accelerate, y_acc, x_out));
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) k_mosaic_init(const float* __restrict__ y
 glr_status launch_mosaic_init(const float* y, const float* masks, long long mstride, int G, int T, int H, int W, int s,
                               float* x_out, cudaStream_t st) {
   const long long total = (long long)G * T * H * W;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)num_sms() * 32));
   GLR_LAUNCH("k_mosaic_init", st, k_mosaic_init<<<blocks, 256, 0, st>>>(y, masks, mstride, G, T, H, W, s, x_out));
   return GLR_OK;
 }
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) k_admm_sci(const float* __restrict__ y, c
 glr_status launch_admm_sci(const float* y, const float* masks, long long mstride, const float* z, const float* x,
                            float* u, int G, int T, long long HW, float rho, float* x_out, float* w_out, cudaStream_t s) {
   const long long total = (long long)G * HW;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 16));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)num_sms() * 16));
   GLR_LAUNCH("k_admm_sci", s, k_admm_sci<<<blocks, 256, 0, s>>>(y, masks, mstride, z, x, u, G, T, HW, rho, x_out, w_out));
   return GLR_OK;
 }

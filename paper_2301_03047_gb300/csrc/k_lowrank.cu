@@ -561,7 +561,7 @@ glr_status launch_gather(const float* x, const glr_images& im, const int32_t* id
   if (d % 4 != 0) return GLR_ENOTSUP;
   if (d / 4 > 256) return GLR_ENOTSUP;
   const long long ngroups = (long long)im.n_img * N;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ngroups, 152LL * 16));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ngroups, (long long)num_sms() * 16));
 #define GLR_GATHER_CASE(PP) \
   GLR_LAUNCH("k_gather", s, k_gather<PP><<<blocks, 256, 0, s>>>(x, im.n_img, im.C, im.H, im.W, im.P, idx, n_found, N, K, groups, st))
   switch (im.P) {
@@ -588,7 +588,7 @@ glr_status launch_wnnm_regs(const glr_images& im, const int32_t* n_found, int N,
                            (int)smem) != cudaSuccess)
     return GLR_ECUDA;
   const long long ngroups = (long long)im.n_img * N;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(ngroups, WARPS), 152LL * 64));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(ngroups, WARPS), (long long)num_sms() * 64));
   const float tol = 1e-5f;
   const int cap = g_wnnm_sweep_cap > 0 ? g_wnnm_sweep_cap : 30;
   GLR_LAUNCH(name, s, (k_jacobi_wnnm<DMAX, WARPS, CPLX, FUSED><<<blocks, WARPS * 32, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, cap, groups, rank, st, io, fb_queue)));

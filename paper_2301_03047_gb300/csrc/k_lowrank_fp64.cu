@@ -11,8 +11,9 @@
 // resolved, below the FP32 path's 2^-24 max(d, K) s_1.
 //
 // One warp per queued group, one group per CTA at a time (G and V in shared memory,
-// 64 x 64 doubles each); the queue length is read on the device, so the launch
-// needs no host synchronisation.
+// 64 x 64 doubles each, and a 32-row slab of the group for the Gram products); the
+// queue length is read on the device, so the launch needs no host synchronisation.
+// A group whose FP64 sweeps also reach their cap is counted (fb_noconv) and flagged.
 #include "glr_kernels.cuh"
 
 namespace glr {
@@ -39,6 +40,7 @@ __global__ void __launch_bounds__(32) k_wnnm_fp64(int d, int K, float sigma_w, f
   extern __shared__ double f64_smem[];
   double* G = f64_smem;                      // [64][F64_LD]
   double* V = f64_smem + F64_N * F64_LD;     // [64][F64_LD]
+  double* slab = f64_smem + 2 * F64_N * F64_LD;  // [64][33]: 32 rows of every column
   __shared__ double2 cs[F64_N / 2];
   const int lane = threadIdx.x;
   const unsigned count = *reinterpret_cast<volatile unsigned*>(&st->fb_count);
@@ -47,16 +49,28 @@ __global__ void __launch_bounds__(32) k_wnnm_fp64(int d, int K, float sigma_w, f
   for (unsigned qi = blockIdx.x; qi < count; qi += gridDim.x) {
     const long long g = queue[qi];
     float* Y = groups + g * (long long)K * d;  // column j at Y + j d
-    // ---- G = Y^T Y (lane = row i of G, two rows per lane), padded with zeros
+    // ---- G = Y^T Y, padded with zeros.  The group is read in slabs of 32 rows, each staged
+    //      in shared memory by coalesced loads (lane = row inside the slab); then lane = row i
+    //      of G (two rows per lane) accumulates the slab's contribution to its 64 entries.
     for (int i = lane; i < F64_N; i += 32)
       for (int j = 0; j < F64_N; ++j) {
-        double acc = 0.0;
-        if (i < K && j < K)
-          for (int r = 0; r < d; ++r) acc = fma((double)Y[(long long)i * d + r], (double)Y[(long long)j * d + r], acc);
-        G[i * F64_LD + j] = acc;
+        G[i * F64_LD + j] = 0.0;
         V[i * F64_LD + j] = (i == j) ? 1.0 : 0.0;
       }
     __syncwarp();
+    for (int r0 = 0; r0 < d; r0 += 32) {
+      const int r = r0 + lane;
+      for (int j = 0; j < K; ++j) slab[j * 33 + lane] = r < d ? (double)Y[(long long)j * d + r] : 0.0;
+      __syncwarp();
+      for (int i = lane; i < K; i += 32)
+        for (int j = 0; j < K; ++j) {
+          double acc = G[i * F64_LD + j];
+#pragma unroll 8
+          for (int t = 0; t < 32; ++t) acc = fma(slab[i * 33 + t], slab[j * 33 + t], acc);
+          G[i * F64_LD + j] = acc;
+        }
+      __syncwarp();
+    }
     // ---- cyclic two-sided Jacobi: G <- J^T G J, V <- V J per round
     double dmax = 0.0;
     for (int i = 0; i < K; ++i) dmax = fmax(dmax, G[i * F64_LD + i]);
@@ -113,6 +127,11 @@ __global__ void __launch_bounds__(32) k_wnnm_fp64(int d, int K, float sigma_w, f
       }
       converged = !__any_sync(0xffffffffu, rotated);
     }
+    if (!converged && lane == 0) {
+      // the FP64 sweeps ran out too: X^ below is computed from the last rotation state
+      atomicAdd(&st->fb_noconv, 1u);
+      status_set(st, GLR_DEV_SVD_NOCONV);
+    }
     // ---- shrinkage coefficients c_i = s'_i / s_i (components at the FP64 rounding level of
     //      the Gram matrix carry no information: treated as zero)
     __shared__ double coef[F64_N];
@@ -157,7 +176,7 @@ __global__ void __launch_bounds__(32) k_wnnm_fp64(int d, int K, float sigma_w, f
 
 }  // namespace
 
-size_t wnnm_fp64_smem_bytes() { return (size_t)2 * F64_N * F64_LD * sizeof(double); }
+size_t wnnm_fp64_smem_bytes() { return ((size_t)2 * F64_N * F64_LD + (size_t)F64_N * 33) * sizeof(double); }
 
 glr_status launch_wnnm_fp64(int d, int K, float sigma_w, float c_wnnm, float* groups, int32_t* rank,
                             const int32_t* queue, StatusBlock* st, cudaStream_t s) {
@@ -166,7 +185,7 @@ glr_status launch_wnnm_fp64(int d, int K, float sigma_w, float c_wnnm, float* gr
   if (cudaFuncSetAttribute(k_wnnm_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return GLR_ECUDA;
   GLR_LAUNCH("k_wnnm_fp64", s,
-             k_wnnm_fp64<<<152, 32, smem, s>>>(d, K, sigma_w, c_wnnm, 30, groups, rank, queue, st));
+             k_wnnm_fp64<<<num_sms(), 32, smem, s>>>(d, K, sigma_w, c_wnnm, 30, groups, rank, queue, st));
   return GLR_OK;
 }
 

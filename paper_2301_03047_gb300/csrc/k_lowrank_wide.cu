@@ -506,7 +506,7 @@ glr_status launch_gram_wnnm(const glr_images& im, const int32_t* n_found, int N,
   const int d = im.C * im.P * im.P;
   if (K < 1 || K > 32 || d < 2 * K) return GLR_ENOTSUP;
   const long long ngroups = (long long)im.n_img * N;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(ngroups, GW_WARPS), 152LL * 64));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(ngroups, GW_WARPS), (long long)num_sms() * 64));
   GLR_LAUNCH("k_gram_wnnm", s, k_gram_wnnm<<<blocks, GW_WARPS * 32, 0, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, 1e-5f, 30, groups, rank, st));
   return GLR_OK;
 }
@@ -539,7 +539,7 @@ glr_status launch_wnnm_smem(const glr_images& im, bool cplx, const int32_t* n_fo
       return GLR_ECUDA;
   }
   if (per_sm < 1) return GLR_ENOTSUP;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ngroups, 152LL * per_sm * 4));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ngroups, (long long)num_sms() * per_sm * 4));
   const float tol = 1e-5f;
   if (cplx)
     GLR_LAUNCH("k_jacobi_smem", s, k_jacobi_smem<true><<<blocks, WJ_THREADS, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, 30, groups, rank, st));

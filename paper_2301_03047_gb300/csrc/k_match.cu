@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
 
 int image_mean_slices(const glr_images& im) {
   const long long n = (long long)im.C * im.H * im.W;
-  long long S = ceil_div(2 * 152, (long long)im.n_img);
+  long long S = ceil_div(2LL * num_sms(), (long long)im.n_img);
   S = std::min<long long>(S, ceil_div(n, 4096));
   return (int)std::max<long long>(1, std::min<long long>(S, kMeanMaxSlices));
 }
@@ -518,7 +518,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   }
   // fewer splits mean fewer streams per key (less re-rank work and threshold learning):
   // split the positions only when key tiles alone would leave SMs idle
-  int splits = (o && o->splits > 0) ? o->splits : (int)ceil_div(152, (long long)ktiles * im.n_img);
+  int splits = (o && o->splits > 0) ? o->splits : (int)ceil_div((long long)num_sms(), (long long)ktiles * im.n_img);
   // the exact re-rank holds every stream's candidates of one key in shared memory
   const int max_splits = std::max(1, kRerankMaxList / (pl.subs * pl.Kp));
   splits = std::max(1, std::min({splits, pl.pos_tiles, max_splits}));
@@ -586,7 +586,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     if (cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return GLR_ECUDA;
     const long long nkeys = (long long)im.n_img * N;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, RR_WARPS), 152LL * 16));
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, RR_WARPS), (long long)num_sms() * 16));
     GLR_LAUNCH("k_rerank", s, k_rerank<<<blocks, RR_WARPS * 32, smem, s>>>(x, keys, n_found, im.n_img, im.C, im.H, im.W, im.P, N, pl.Npad,
                                                  pl.K, 0, 0, 0, pow2, nullptr, nullptr, 0, 1.f, pl.window, idx, dist));
     return GLR_OK;
@@ -618,12 +618,12 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
   }
   if (!tc) {  // the FP32 scorer adds ||q||^2 itself; the tensor-core operands carry their norms
     const long long total = (long long)im.n_img * npos;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)num_sms() * 32));
     GLR_LAUNCH("k_patch_norms", s, k_patch_norms<<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, qn));
   }
   {
     const long long total = (long long)im.n_img * pl.Npad * d;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)num_sms() * 32));
     GLR_LAUNCH("k_key_vectors", s, k_key_vectors<<<blocks, 256, 0, s>>>(xs, mean, keys, n_found, im.n_img, ime.C, im.H, im.W, im.P, N, pl.Npad,
                                         keyv, reinterpret_cast<StatusBlock*>(ws)));
   }
@@ -681,7 +681,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     if (cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return GLR_ECUDA;
     const long long nkeys = (long long)im.n_img * N;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, RR_WARPS), 152LL * 16));
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, RR_WARPS), (long long)num_sms() * 16));
     GLR_LAUNCH("k_rerank", s, k_rerank<<<blocks, RR_WARPS * 32, smem, s>>>(x, keys, n_found, im.n_img, im.C, im.H, im.W, im.P, N, pl.Npad,
                                                  pl.K, pl.streams_per_key, pl.cap + 32, pl.Kp, pow2, bufs, bufcnt,
                                                  edge ? 1 : 0, edge ? -0.5f : 1.f, 0, idx, dist));

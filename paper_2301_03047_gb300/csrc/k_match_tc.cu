@@ -114,16 +114,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait.  Returns false if the CTA aborted or this wait timed out (then
-// it raises the abort flag and the device status bit).
+// it raises the abort flag and the device status bit).  The pipeline's waits take
+// the launch's limit (1 s unless a test shortens it); the teardown waits
+// (honour_abort = false), which only wait for copies and MMAs already issued,
+// always keep the full second.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, StatusBlock* st,
-                                          bool honour_abort = true) {
+                                          bool honour_abort = true, unsigned long long limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 0) {
       if (honour_abort && *abort) return false;
-      if (globaltimer() - t0 > kWaitNs) {
+      if (globaltimer() - t0 > (honour_abort ? limit_ns : kWaitNs)) {
         *abort = 1;
         status_set(st, GLR_DEV_TIMEOUT);
         return false;
@@ -714,7 +717,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int kc = 0; kc <= nkc; ++kc) {
           const int s = it % NST;
           const uint32_t ph = (uint32_t)(it / NST) & 1u;
-          if (!mbar_wait(empty + s, ph ^ 1u, abort_s, st)) {
+          if (!mbar_wait(empty + s, ph ^ 1u, abort_s, st, true, cfg.wait_ns)) {
             ok = false;
             break;
           }
@@ -745,12 +748,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int i = 0; ok && i < nt; ++i) {
         const int b = i & 1;
         const uint32_t bph = (uint32_t)(i >> 1) & 1u;
-        if (!mbar_wait(tempty + b, bph ^ 1u, abort_s, st)) break;
+        if (!mbar_wait(tempty + b, bph ^ 1u, abort_s, st, true, cfg.wait_ns)) break;
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * TC_N);
         for (int kc = 0; kc <= nkc; ++kc) {
           const int s = it % NST;
           const uint32_t ph = (uint32_t)(it / NST) & 1u;
-          if (!mbar_wait(full + s, ph, abort_s, st)) {
+          if (!mbar_wait(full + s, ph, abort_s, st, true, cfg.wait_ns)) {
             ok = false;
             break;
           }
@@ -785,7 +788,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int i = 0; i < nt; ++i) {
         const int s = i % TC_STAGES;
         const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
-        if (!mbar_wait(empty + s, ph ^ 1u, abort_s, st)) break;
+        if (!mbar_wait(empty + s, ph ^ 1u, abort_s, st, true, cfg.wait_ns)) break;
         mbar_arrive_expect_tx(full + s, B_MAIN_BYTES + B_AUX_BYTES);
         const int brow = (int)(f * npos_pad + (long long)(t_begin + i) * TC_N);
         tma_load_2d(&tm_qmain, full + s, smem + OFF_B_MAIN + s * B_MAIN_BYTES, 0, brow);
@@ -802,15 +805,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // --------------------------------------------------------- MMA issuer
       constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
       const uint32_t a_main = smem_u32(smem + OFF_A_MAIN), a_aux = smem_u32(smem + OFF_A_AUX);
-      bool ok = mbar_wait(a_full, 0, abort_s, st);
+      bool ok = mbar_wait(a_full, 0, abort_s, st, true, cfg.wait_ns);
       tc_fence_after();
       for (int i = 0; ok && i < nt; ++i) {
         const int s = i % TC_STAGES;
         const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
         const int b = i & 1;
         const uint32_t bph = (uint32_t)(i >> 1) & 1u;
-        if (!mbar_wait(full + s, ph, abort_s, st)) break;
-        if (!mbar_wait(tempty + b, bph ^ 1u, abort_s, st)) break;
+        if (!mbar_wait(full + s, ph, abort_s, st, true, cfg.wait_ns)) break;
+        if (!mbar_wait(tempty + b, bph ^ 1u, abort_s, st, true, cfg.wait_ns)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * TC_N);
         const uint32_t b_main = smem_u32(smem + OFF_B_MAIN + s * B_MAIN_BYTES);
@@ -849,7 +852,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int i = 0; i < nt; ++i) {
       const int b = i & 1;
       const uint32_t bph = (uint32_t)(i >> 1) & 1u;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull + b, bph, abort_s, st));
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull + b, bph, abort_s, st, true, cfg.wait_ns));
       if (!ok) break;
       tc_fence_after();
       const long long tile_q0 = (long long)(t_begin + i) * TC_N;
@@ -969,7 +972,7 @@ extern float* g_tc_dump;
 glr_status launch_tau_bound(const float* mins, const int32_t* n_found, int n_img, int N, const MatchPlan& pl,
                             uint32_t* taugl, cudaStream_t s) {
   const long long nkeys = (long long)n_img * N;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, 8), 152LL * 16));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, 8), (long long)num_sms() * 16));
   GLR_LAUNCH("k_tau_bound", s,
              k_tau_bound<<<blocks, 256, 0, s>>>(mins, n_found, n_img, N, pl.Npad, 2 * pl.pos_tiles, pl.Kp, taugl));
   return GLR_OK;
@@ -999,7 +1002,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
       const size_t psmem = (size_t)PW_POS * (pl.nkc * DK_MAIN + 2) * 2 + (size_t)im.C * PW_POS * 4;
       if (psmem > 227 * 1024) return GLR_ENOTSUP;
       const long long nblk = (long long)im.n_img * (pl.npos_pad / PW_POS);
-      const int pblocks = (int)std::max<long long>(1, std::min<long long>(nblk, 152LL * 16));
+      const int pblocks = (int)std::max<long long>(1, std::min<long long>(nblk, (long long)num_sms() * 16));
 #define GLR_PACKW_CASE(PP)                                                                                     \
   {                                                                                                            \
     if (cudaFuncSetAttribute(k_pack_positions_w<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem) != \
@@ -1041,7 +1044,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
         blocks_per_sm != 1)  // all of TMEM: exactly one resident CTA per SM
       return GLR_ENOTSUP;
     const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
-    const StreamCfg cfg{pl.cap, pl.Kp, pl.finish};
+    const StreamCfg cfg{pl.cap, pl.Kp, pl.finish, g_match_wait_ns > 0 ? g_match_wait_ns : kWaitNs};
     dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
     if (pl.bound_pass) {
       GLR_LAUNCH("k_match_tc_min", s,
@@ -1059,7 +1062,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   }
   {
     const long long total = (long long)im.n_img * pl.npos_pad;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)num_sms() * 32));
 #define GLR_PACK_CASE(PP)                                                                                  \
   GLR_LAUNCH("k_pack_positions", s,                                                                          \
              k_pack_positions<PP><<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, pl.npos_pad, \
@@ -1080,7 +1083,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   }
   if (seed_keys != nullptr) {
     const long long nkeys = (long long)im.n_img * seed_N;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, 8), 152LL * 16));
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, 8), (long long)num_sms() * 16));
     GLR_LAUNCH("k_seed_bounds", s,
                k_seed_bounds<<<blocks, 256, 0, s>>>(qmain, qaux, kmain, kaux, seed_keys, n_found, im.n_img, seed_N,
                                                     pl.Npad, im.H - im.P + 1, im.W - im.P + 1, pl.npos_pad, pl.Kp,
@@ -1107,7 +1110,7 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
       return GLR_ENOTSUP;
   }
   const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
-  const StreamCfg cfg{pl.cap, pl.Kp, pl.finish};
+  const StreamCfg cfg{pl.cap, pl.Kp, pl.finish, g_match_wait_ns > 0 ? g_match_wait_ns : kWaitNs};
   dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
   if (pl.bound_pass && dump == nullptr) {
     GLR_LAUNCH("k_match_tc_min", s,
@@ -1134,5 +1137,6 @@ glr_status launch_match_tc(const float* x, const glr_images& im, const int32_t* 
 }
 
 float* g_tc_dump = nullptr;
+unsigned long long g_match_wait_ns = 0;
 
 }  // namespace glr

@@ -425,7 +425,7 @@ glr_status launch_select(const float* x, const glr_images& im, float th, int N, 
   auto* bm = reinterpret_cast<uint32_t*>(ws + L.bitmap_off);
   if (cudaMemsetAsync(cnt, 0, (size_t)im.n_img * 4, s) != cudaSuccess) return GLR_ECUDA;
   const long long total = (long long)im.n_img * HW;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)num_sms() * 32));
   GLR_LAUNCH("k_edge_sum", s, k_edge_sum<<<blocks, 256, 0, s>>>(x, im.n_img, im.C, im.H, im.W, th, S));
   dim3 hg((unsigned)ceil_div(im.W, HT), (unsigned)ceil_div(im.H, HT), (unsigned)im.n_img);
   GLR_LAUNCH("k_harris", s, k_harris<<<hg, 256, 0, s>>>(S, im.H, im.W, R));
@@ -447,7 +447,7 @@ glr_status launch_select(const float* x, const glr_images& im, float th, int N, 
 
 glr_status launch_edge_planes(const float* x, const glr_images& im, float th, float* planes, cudaStream_t s) {
   const long long total = (long long)im.n_img * im.C * im.H * im.W;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), 152LL * 32));
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)num_sms() * 32));
   GLR_LAUNCH("k_edge_planes", s, k_edge_planes<<<blocks, 256, 0, s>>>(x, im.n_img, im.C, im.H, im.W, th, planes));
   return GLR_OK;
 }

@@ -39,6 +39,7 @@ struct StreamCfg {
   int cap;     // compaction trigger (entries)
   int kp;      // entries kept per stream
   int finish;  // 0: leave the buffers as they are (the re-rank selects the K' best itself)
+  unsigned long long wait_ns;  // limit of the pipeline's mbarrier waits (teardown waits keep 1 s)
 };
 
 constexpr int kStreamSlots = 17;                      // buffer entries per lane of the compacting warp

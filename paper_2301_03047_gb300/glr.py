@@ -137,6 +137,11 @@ def debug_wnnm_sweep_cap(cap: int) -> int:
     return int(L.load().glr_debug_wnnm_sweep_cap(int(cap)))
 
 
+def debug_match_wait_ns(ns: int) -> int:
+    """Testing aid: limit (ns) of the tensor-core scorer's pipeline waits (0: 1 s); returns the old one."""
+    return int(L.load().glr_debug_match_wait_ns(int(ns)))
+
+
 def debug_match_scores(x, P, keys, n_found, K, *, ws=None, stream=None):
     """Raw BF16 tensor-core scores of every key against the first 256 positions (testing aid)."""
     lib = L.load()
@@ -274,13 +279,15 @@ def admm_sci_step(y, masks, z, x, u, rho, *, x_out=None, w_out=None, stream=None
 
 
 def poll_status(ws, reset=False, stream=None):
-    """(bits, [cand_overflow, svd_noconv, sweeps, groups, cand_appends, compactions]) of the last call that used ws."""
+    """(bits, [cand_overflow, svd_noconv, sweeps, groups, cand_appends, compactions, fb_noconv]) of the
+    last call that used ws.  ws=None reads the status block of glr_aggregate_noalloc's scratch array
+    on the current device."""
     lib = L.load()
-    wp, _ = _ws(ws)
+    wp = _ws(ws)[0] if ws is not None else None
     bits = ctypes.c_uint32(0)
-    cnt = (ctypes.c_uint32 * 6)()
+    cnt = (ctypes.c_uint32 * 7)()
     code = lib.glr_poll_status(wp, ctypes.byref(bits), cnt, 1 if reset else 0, _stream(stream))
-    if code not in (L.GLR_OK, L.GLR_EDEVICE):
+    if code not in (L.GLR_OK, L.GLR_EDEVICE, L.GLR_ETIMEDOUT):
         raise GlrError("glr_poll_status", code)
     return int(bits.value), [int(c) for c in cnt]
 

@@ -75,3 +75,25 @@ def test_entry_points_reject_bad_arguments_on_host(lib):
     assert lib.glr_gap_step(p, p, 0, None, 1, 0, 8, 8, 0, None, p, None) == L.GLR_EINVAL
     assert lib.glr_gap_step(p, p, 0, None, 1, 2, 8, 8, 1, None, p, None) == L.GLR_EINVAL  # accelerate needs y_acc
     assert lib.glr_launch_count() == 0
+
+
+def _noalloc_bytes(n, C, H, W, P):
+    """Scratch of glr_aggregate_noalloc as its header states it: 256 + n C H W 8 + n Hq Wq 4,
+    each part rounded up to 256 bytes."""
+    up = lambda v: (v + 255) // 256 * 256
+    return 256 + up(n * C * H * W * 8) + up(n * (H - P + 1) * (W - P + 1) * 4)
+
+
+def test_noalloc_scratch_limit_on_host(lib):
+    """One column past the 16 MiB scratch is rejected before anything touches the device.
+    320 x 4369 with P = 1 needs exactly 16 MiB (accepted: checked on the GPU by
+    tests/test_zz_no_alloc.py); 320 x 4370 needs 3840 bytes more."""
+    assert _noalloc_bytes(1, 1, 320, 4369, 1) == 16 << 20
+    assert _noalloc_bytes(1, 1, 320, 4370, 1) > 16 << 20
+    p = ctypes.c_void_p(256)  # never dereferenced: the size check fails first
+    over = L.GlrImages(1, 1, 320, 4370, 1)
+    assert lib.glr_aggregate_noalloc(p, p, p, ctypes.byref(over), 1, 1, p, ctypes.c_void_p(512), None) == L.GLR_ETOOBIG
+    # a second image doubles the planes: far over
+    two = L.GlrImages(2, 1, 320, 4369, 1)
+    assert lib.glr_aggregate_noalloc(p, p, p, ctypes.byref(two), 1, 1, p, ctypes.c_void_p(512), None) == L.GLR_ETOOBIG
+    assert lib.glr_launch_count() == 0

@@ -93,3 +93,79 @@ def test_stream_final_selection_and_rerank_selection_agree():
     few = run(x, P, keys, nf, K, "bf16", 1, splits=1)
     many = run(x, P, keys, nf, K, "bf16", 1, splits=8, cap=512)
     same_matches(few, many)
+
+
+@pytest.mark.parametrize("bound_pass", [-1, 1])
+def test_stream_compactions_against_the_oracle(bound_pass):
+    """A stream capacity just above K' with three position splits makes the streams compact
+    many times; keys on a flat half of the image tie exactly (every BF16 score and every exact
+    distance there is equal), so compaction has to fall back from its sampled pivot to the exact
+    radix select and keep the smaller ids.  Against the FP64 oracle: flat keys return exactly the
+    oracle's K smallest ids among the tied positions, textured keys pass the BF16 separation
+    check of the tensor-core tests."""
+    from oracle import glr_oracle as O
+    from test_gpu_tc import check_bf16_topk
+
+    rng = synth.rng_for("compact")
+    H, W, P, K, Kp = 100, 120, 8, 32, 48
+    x = synth.textured_frames(rng, 1, H, W)[:, None].astype(np.float32)
+    x[0, 0, : H // 2] = 0.5
+    Wq = W - P + 1
+    flat = [r * Wq + c for r in (3, 10, 20, 30) for c in (5, 50, 100)]
+    textured = [r * Wq + c for r in (60, 70, 80, 90) for c in (7, 44, 81, 110)]
+    keys = np.array([flat + textured], np.int32)
+    N = keys.shape[1]
+    kt = torch.from_numpy(keys).cuda()
+    nf = torch.tensor([N], dtype=torch.int32, device="cuda")
+    xt = torch.from_numpy(x).cuda()
+    im = glr.images_of(xt, P)
+    opts = glr.match_opts("bf16", k_over=Kp, splits=3, cap=Kp + 8, bound_pass=bound_pass)
+    ws = glr.workspace(glr.L.GLR_OP_MATCH, im, N, K, opts)
+    idx, dist = glr.match_topk(xt, P, kt, nf, K, "bf16", k_over=Kp, splits=3, cap=Kp + 8, bound_pass=bound_pass,
+                               ws=ws)
+    torch.cuda.synchronize()
+    _, cnt = glr.poll_status(ws)
+    assert cnt[5] > 0  # compactions happened
+    idx, dist = idx.cpu().numpy(), dist.cpu().numpy()
+    Q = O.patch_matrix(x[0], P)
+    for i in range(len(flat)):
+        d_all = O.all_distances(x[0], P, keys[0, i], Q)
+        order = np.lexsort((np.arange(len(d_all)), d_all))
+        assert d_all[order[K - 1]] == 0.0
+        assert idx[0, i].tolist() == order[:K].tolist(), i
+        assert np.all(dist[0, i] == 0.0)
+    nt = len(textured)
+    covered = check_bf16_topk(x, P, keys[:, len(flat):], K, Kp, idx[:, len(flat):], dist[:, len(flat):])
+    assert covered * nt >= nt - 2, covered
+
+
+def test_forced_wait_expiry_reports_timeout_and_recovers():
+    """The scorer's pipeline waits given a 1 ns limit: the first wait that is not already
+    satisfied expires, the call records GLR_DEV_TIMEOUT and glr_poll_status returns
+    GLR_ETIMEDOUT; the CTAs still drain the copies and MMAs they issued.  With the default
+    limit restored, the next call on the same workspace returns the same matches as a call on
+    a fresh workspace."""
+    import ctypes
+
+    x = frames("timeout", 1, 1, 90, 100)
+    P, N, K = 8, 128, 16
+    keys, nf, _ = glr.select_keys(x, P, N, 0.05)
+    im = glr.images_of(x, P)
+    opts = glr.match_opts("bf16")
+    ws = glr.workspace(glr.L.GLR_OP_MATCH, im, N, K, opts)
+    lib = glr.L.load()
+    old = glr.debug_match_wait_ns(1)
+    try:
+        glr.match_topk(x, P, keys, nf, K, "bf16", ws=ws)
+        torch.cuda.synchronize()
+    finally:
+        glr.debug_match_wait_ns(old)
+    bits = ctypes.c_uint32(0)
+    code = lib.glr_poll_status(glr._ws(ws)[0], ctypes.byref(bits), None, 1, torch.cuda.current_stream().cuda_stream)
+    assert code == glr.L.GLR_ETIMEDOUT and bits.value & glr.L.GLR_DEV_TIMEOUT
+    again = run(x, P, keys, nf, K, "bf16", 0, ws=ws)
+    code = lib.glr_poll_status(glr._ws(ws)[0], ctypes.byref(bits), None, 0, torch.cuda.current_stream().cuda_stream)
+    assert code == glr.L.GLR_OK and bits.value == 0
+    fresh = run(x, P, keys, nf, K, "bf16", 0)
+    np.testing.assert_array_equal(again[0], fresh[0])
+    np.testing.assert_array_equal(again[1], fresh[1])

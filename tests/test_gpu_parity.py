@@ -361,3 +361,28 @@ def test_fused_lowrank_aggregate_equals_separate_steps_bitwise(case):
     torch.cuda.synchronize()
     assert torch.equal(got, want)
     assert torch.equal(rk[0, :N - 3], rank[0, :N - 3])
+
+
+@pytest.mark.parametrize("case", [("fo1", 2, 1, 60, 70, 8, 50, 40, 0.2), ("fo2", 1, 3, 33, 40, 4, 30, 24, 0.05)])
+def test_fused_lowrank_aggregate_matches_oracle(case):
+    """The fused pass against the oracle's own steps (gather, WNNM, aggregate) on the same idx:
+    a fault shared by the fused and the separate kernels would not show in the bitwise test
+    above.  Each output pixel averages WNNM estimates, so it stays within the low-rank bar."""
+    tag, F, C, H, W, P, N, K, sw = case
+    x = scene(tag, F, H, W, quant=False, C=C)
+    rng = synth.rng_for(tag + "idx")
+    npos = (H - P + 1) * (W - P + 1)
+    idx = rng.integers(0, npos, size=(F, N, K)).astype(np.int32)
+    nf = np.full(F, N, np.int32)
+    nf[-1] = N - 5
+    cw = 2 * math.sqrt(K)
+    got = glr.lowrank_aggregate(cuda(x), P, cuda(idx, torch.int32), cuda(nf, torch.int32), sw, cw)
+    torch.cuda.synchronize()
+    got = got.cpu().numpy()
+    for f in range(F):
+        Y = O.gather_groups(x[f], P, idx[f, : nf[f]])
+        Xo, _ = O.lowrank_groups(Y, sw, cw, eps=1e-8)
+        vo = O.aggregate(Xo, idx[f, : nf[f]], x[f], P)
+        err = got[f] - vo
+        assert np.sqrt(np.mean(err**2)) <= 2e-4 * max(np.sqrt(np.mean(x[f] ** 2)), 1e-3)
+        assert np.abs(err).max() <= 1e-3 * max(np.abs(x[f]).max(), 1e-3)

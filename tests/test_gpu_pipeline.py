@@ -31,8 +31,9 @@ def test_graph_replay_matches_eager(mode):
         a.step(s, cfg.c_wnnm)
         b.step_graph(s)
     torch.cuda.synchronize()
-    # the only non-associative step is the FP32 atomic accumulation of the aggregation
-    np.testing.assert_allclose(b.x.cpu().numpy(), a.x.cpu().numpy(), rtol=1e-4, atol=1e-4)
+    # every step is order-independent (the aggregation sums in fixed point), so the replayed
+    # graph and the eager launches give the same bits
+    assert torch.equal(b.x, a.x)
 
 
 def test_autotune_picks_a_working_schedule():
@@ -68,3 +69,24 @@ def test_reconstruction_tracks_oracle_teacher_forced():
         assert np.sqrt(np.mean(err ** 2)) < 2e-4 and err.max() < 2e-3
         x_or, _ = O.gap_project(prob.y, prob.masks, v_gpu)
         np.testing.assert_allclose(rec.x.cpu().numpy()[0], x_or, rtol=1e-4, atol=1e-5)
+
+
+def test_config1_free_running_against_oracle():
+    """The whole plain FP32 reconstruction of the small video workload (8 frames of 128 x 128,
+    N = 200 keys, K = 40, 3 GAP iterations), free running on both sides from the same
+    snapshot: the GPU result must stay within 50 dB PSNR of the FP64 oracle's (a key picked
+    differently on a near-tied corner response changes a few patches, not the image)."""
+    cfg = synth.SCI_SMALL
+    prob = synth.sci_problem(cfg)
+    rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode="fp32")
+    rec.start(torch.from_numpy(prob.y).cuda(), torch.from_numpy(prob.masks).cuda())
+    for s in cfg.sigma_schedule():
+        rec.step(s, cfg.c_wnnm)
+    torch.cuda.synchronize()
+    x_gpu = rec.x.cpu().numpy()[0]
+    x_or = O.glr_reconstruct(prob.y, prob.masks, cfg.P, cfg.N, cfg.K, cfg.sigma_schedule(), cfg.c_wnnm,
+                             cfg.edge_th, eps=1e-8)
+    agree = O.psnr(x_gpu, x_or)
+    assert agree >= 50.0, agree
+    # and both reconstruct the scene equally well
+    assert abs(O.psnr_framewise(x_gpu, prob.truth) - O.psnr_framewise(x_or, prob.truth)) < 0.05

@@ -61,3 +61,32 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     out = torch.empty_like(x)
     assert _noalloc(lib, g, idx, nf, x, 8, out) == L.GLR_ETOOBIG
     assert b"16 MiB" in lib.glr_status_string(L.GLR_ETOOBIG)
+
+
+def test_noalloc_accepts_a_problem_of_exactly_its_scratch():
+    """320 x 4369 pixels with P = 1 need exactly the 16 MiB of scratch (the host-side test
+    computes this from the documented formula): accepted, and equal to glr_aggregate."""
+    lib = L.load()
+    x, idx, g, nf = _inputs("na_exact", 1, 1, 320, 4369, 1, 50, 3)
+    want = glr.aggregate(g, idx, nf, x, 1)
+    out = torch.full_like(x, float("nan"))
+    assert _noalloc(lib, g, idx, nf, x, 1, out) == L.GLR_OK
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out.cpu().numpy(), want.cpu().numpy(), rtol=1e-5, atol=1e-6)
+
+
+def test_noalloc_reports_a_bad_index_through_poll_status():
+    """A match id outside the position grid is skipped and recorded in the status block of the
+    scratch array, which glr_poll_status(NULL, ...) reads; the next clean call clears it."""
+    lib = L.load()
+    x, idx, g, nf = _inputs("na_bad", 1, 1, 30, 34, 6, 10, 4)
+    npos = (30 - 6 + 1) * (34 - 6 + 1)
+    bad = idx.clone()
+    bad[0, 3, 2] = npos  # one past the last position
+    out = torch.empty_like(x)
+    assert _noalloc(lib, g, bad, nf, x, 6, out) == L.GLR_OK
+    bits, _ = glr.poll_status(None)
+    assert bits & L.GLR_DEV_BAD_INDEX
+    assert _noalloc(lib, g, idx, nf, x, 6, out) == L.GLR_OK
+    bits, _ = glr.poll_status(None)
+    assert bits == 0
