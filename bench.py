@@ -235,9 +235,16 @@ def peaks() -> dict:
             "source": "fallback"}
 
 
+def num_sms() -> int:
+    """Streaming multiprocessors of the current device (152 on a GB300)."""
+    import torch
+
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
 def fp32_alu_peak_tflops(sm_mhz: float) -> float:
-    """FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flop x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    """FP32 FMA peak: SMs (read from the device) x 128 FP32 lanes x 2 flop x clock."""
+    return num_sms() * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def kernel_hash(fname: str) -> str:
@@ -310,7 +317,7 @@ def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict, n
                                 + ("; time = minima scan + bound + candidate scan" if scans else "")}
         else:
             out = {"bound": "alu", "peak": round(fp32_alu_peak_tflops(sm), 1), "unit": "TFLOP/s",
-                   "peak_note": f"derived FP32 FMA peak 152x128x2 at {sm:.0f} MHz"}
+                   "peak_note": f"derived FP32 FMA peak {num_sms()}x128x2 at {sm:.0f} MHz"}
         achieved = work / avg_s / 1e12
         unit_name = "pairs"
     elif name in ("k_jacobi_wnnm", "k_jacobi_smem", "k_jacobi_wnnm_c", "k_jacobi_wnnm_fused"):
@@ -319,7 +326,7 @@ def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict, n
         work = units * sweeps_per_group * 6.0 * d * K * K * (2.0 if name == "k_jacobi_wnnm_c" else 1.0)
         achieved = work / avg_s / 1e12
         out = {"bound": "alu", "peak": round(fp32_alu_peak_tflops(sm), 1), "unit": "TFLOP/s",
-               "peak_note": f"derived FP32 FMA peak 152x128x2 at {sm:.0f} MHz; work = 6 d K^2 per sweep x measured sweeps"}
+               "peak_note": f"derived FP32 FMA peak {num_sms()}x128x2 at {sm:.0f} MHz; work = 6 d K^2 per sweep x measured sweeps"}
         unit_name = "groups"
     else:
         units = T * N
