@@ -122,11 +122,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
                                           bool honour_abort = true, unsigned long long limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
+  const unsigned long long limit = honour_abort ? limit_ns : kWaitNs;
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0) {
+    // the clock is read every 256 polls, or at every poll under a shortened (test) limit
+    if ((it & 255u) == 0 || limit < kWaitNs) {
       if (honour_abort && *abort) return false;
-      if (globaltimer() - t0 > (honour_abort ? limit_ns : kWaitNs)) {
+      if (globaltimer() - t0 > limit) {
         *abort = 1;
         status_set(st, GLR_DEV_TIMEOUT);
         return false;
