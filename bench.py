@@ -288,6 +288,12 @@ def merge_scans(prof: dict) -> dict:
     """The tensor-core matcher's minima scan and bound kernel counted with its candidate scan:
     together they are one contraction of every key/position pair."""
     prof = dict(prof)
+    if "k_match_tc_chunk" in prof:
+        # chunk minima (the contraction) + the exact evaluation of the candidate chunks
+        ms, n = prof.pop("k_match_tc_chunk")
+        extra = [prof.pop(k) for k in ("k_chunk_topk", "k_patch_norms") if k in prof]
+        prof["k_match_tc"] = (ms + sum(e[0] for e in extra), n)
+        return prof
     extra = [prof.pop(k) for k in ("k_match_tc_min", "k_tau_bound") if k in prof]
     if extra and "k_match_tc" in prof:
         ms, n = prof["k_match_tc"]
@@ -300,6 +306,7 @@ def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict, n
     """Roofline entry of the kernel with the largest share of the timed region.  The matcher's two
     scans (minima, candidates) count as one unit: the pair FLOPs once, over their summed time."""
     scans = "k_match_tc_min" in prof
+    chunks = "k_match_tc_chunk" in prof
     prof = merge_scans(prof)
     name, (ms, n) = max(prof.items(), key=lambda kv: kv[1][0])
     avg_s = ms / n / 1e3
@@ -314,7 +321,8 @@ def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict, n
         if name == "k_match_tc":
             out = {"bound": "tensor", "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
                    "peak_note": f"of {pk['source']} cuBLAS bf16 sustained"
-                                + ("; time = minima scan + bound + candidate scan" if scans else "")}
+                                + ("; time = minima scan + bound + candidate scan" if scans else "")
+                                + ("; time = chunk-minima scan + exact evaluation of the candidate chunks" if chunks else "")}
         else:
             out = {"bound": "alu", "peak": round(fp32_alu_peak_tflops(sm), 1), "unit": "TFLOP/s",
                    "peak_note": f"derived FP32 FMA peak {num_sms()}x128x2 at {sm:.0f} MHz"}

@@ -103,10 +103,18 @@ typedef struct glr_match_opts {
   int32_t window;       /* GLR_MATCH_WINDOW: half-width w of the search window, 1 <= w <= 22:
                            the (2w+1)^2 positions centred on the key, shifted inside the
                            position grid at its borders; K <= (2w+1)^2 */
-  int32_t bound_pass;   /* tensor-core scorer: run a first scan that only records score
-                           minima, and start the candidate scan from the bound they give;
-                           1 = on, -1 = off, 0 = automatic (on when d <= 74, i.e. one
-                           64-column chunk per operand row).  The matches do not change */
+  int32_t bound_pass;   /* tensor-core scorer:
+                           2 = one scan that records the minimum BF16 score of every
+                             32-position chunk per key, then every chunk whose minimum is
+                             at or below the key's K'-th smallest chunk minimum is scored
+                             exactly in FP32 (a superset of the K' best BF16 scores), and
+                             the K' best of those are re-ranked (GLR_MATCH_BF16 with d <= 74
+                             and P in {4, 6, 8}, C P <= 16);
+                           1 = a first scan that only records the minimum of every
+                             128-position half tile, and a candidate scan started from the
+                             bound they give (same matches as -1);
+                           -1 = one candidate scan;
+                           0 = automatic (2 where it applies, else 1 when d <= 74, else -1) */
 } glr_match_opts;
 
 /* Operation codes for glr_workspace_size. */

@@ -251,6 +251,7 @@ glr_status glr_debug_match_scores(const float* x, const glr_images* im, const in
   if (!scores) return GLR_EINVAL;
   glr_match_opts o{};
   o.mode = GLR_MATCH_BF16;
+  o.bound_pass = -1;  // the raw scores come from the candidate scan
   g_tc_dump = scores;
   glr_status st = glr_match_topk(x, im, keys, n_found, N, K, &o, nullptr, nullptr, ws, ws_bytes, stream);
   g_tc_dump = nullptr;

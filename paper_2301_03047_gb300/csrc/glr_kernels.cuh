@@ -42,7 +42,9 @@ struct MatchPlan {
   int epi_batch;        // tensor-core epilogue: 32-column chunks read from TMEM per visit (2 or 4)
   long long npos_pad;   // BF16 position rows per image (pos_tiles * pos_tile)
   int bound_pass;       // tensor-core scorer: minima scan first (bound from half-tile minima)
-  size_t mins_off;      // bound_pass: half-tile minima [n_img][Npad][2 pos_tiles] float32
+  size_t mins_off;      // bound_pass 1: half-tile minima [n_img][Npad][2 pos_tiles] float32;
+                        // bound_pass 2: 16-bit chunk minima [n_img][Npad][8 pos_tiles]
+  size_t ccnt_off, clist_off;  // bound_pass 2: candidate chunks per key (count, the first 256 ids)
   size_t mean_off, meanp_off, qn_off, keyv_off, buf_off, bufcnt_off, taugl_off, qpack_off, kpack_off, embp_off, embk_off, total;
 };
 MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o);

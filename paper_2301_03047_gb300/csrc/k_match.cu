@@ -300,8 +300,26 @@ constexpr int kRerankMaxList = 2048;  // candidates of one key held by the re-ra
 // warp, 256 shared counters).
 __device__ unsigned long long warp_select_kth(const unsigned long long* list, int n, int rank, unsigned* hist,
                                               int lane) {
-  unsigned long long prefix = 0, pmask = 0;
-  for (int pass = 0; pass < 8; ++pass) {
+  // leading bytes that every entry shares need no pass (nearby scores share their exponent byte,
+  // and a pass over one bin would put every entry's atomic on the same counter)
+  unsigned long long all_and = ~0ull, all_or = 0ull;
+  for (int i = lane; i < n; i += 32) {
+    const unsigned long long e = list[i];
+    all_and &= e;
+    all_or |= e;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    all_and &= __shfl_xor_sync(0xffffffffu, all_and, o);
+    all_or |= __shfl_xor_sync(0xffffffffu, all_or, o);
+  }
+  const unsigned long long diff = all_and ^ all_or;  // bits that vary over the list
+  if (diff == 0) return all_and;                    // every entry equal (n == 1)
+  const int first = 63 - __clzll((long long)diff);  // highest varying bit
+  const int pass0 = (63 - first) / 8;                // first byte with a varying bit
+  unsigned long long pmask = pass0 > 0 ? ~0ull << (64 - 8 * pass0) : 0ull;
+  unsigned long long prefix = all_and & pmask;
+  for (int pass = pass0; pass < 8; ++pass) {
     const int shift = 56 - 8 * pass;
     for (int i = lane; i < 256; i += 32) hist[i] = 0;
     __syncwarp();
@@ -472,6 +490,418 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
   }
 }
 
+// Keep the k smallest of n distinct keys (k < n) like warp_keep_smallest and return the
+// largest kept key (the k-th smallest) in *kth.
+__device__ int warp_keep_smallest_kth(unsigned long long* list, int n, int k, unsigned* hist, int lane,
+                                      unsigned long long* kth) {
+  const int out = warp_keep_smallest(list, n, k, hist, lane);
+  unsigned long long m = 0;
+  for (int i = lane; i < out; i += 32) m = max(m, list[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  *kth = m;
+  return out;
+}
+
+// Bound and candidate chunks of every key for the exact evaluation (one warp per key, many
+// warps per SM to hide the memory latency).
+//  * Each lane keeps the 8 smallest of its share of the key's rounded-up 16-bit chunk minima
+//    (pairs of adjacent chunks, interleaved over the lanes) in registers; the K'-th smallest of
+//    those 256 values is tau16.  It bounds the K'-th smallest of all the minima from above (the
+//    K'-th smallest of a subset is never smaller), so every chunk that holds one of the key's K'
+//    smallest BF16 scores has its minimum at or below tau16; it equals the exact K'-th smallest
+//    unless a lane's share holds more than 8 of the K' smallest.
+//  * Then the ids of every chunk at or below tau16, ascending (the first CT_CL of them; ccount
+//    receives the full count).
+constexpr int CT_CL = 256;
+
+__global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ mins16, const int32_t* __restrict__ n_found,
+                                                   int n_img, int N, int Npad, int nchunks, int kp,
+                                                   uint32_t* __restrict__ tau16, int32_t* __restrict__ ccount,
+                                                   uint32_t* __restrict__ clist, StatusBlock* st) {
+  __shared__ unsigned hist_s[8][256];
+  __shared__ uint16_t vals_s[8][256];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned* hist = hist_s[wid];
+  uint16_t* vals = vals_s[wid];
+  const long long nkeys = (long long)n_img * N;
+  const int n2 = nchunks / 2, n8 = nchunks / 8;  // nchunks is a multiple of 8
+  for (long long gk = blockIdx.x * 8LL + wid; gk < nkeys; gk += gridDim.x * 8LL) {
+    const int f = (int)(gk / N), k = (int)(gk - (long long)f * N);
+    if (k >= min(n_found[f], N)) continue;
+    const long long row = (long long)f * Npad + k;
+    uint32_t prefix = 0xffffu;
+    if (nchunks > kp) {
+      // per-lane 8 smallest (sorted ascending)
+      const uint32_t* m2 = reinterpret_cast<const uint32_t*>(mins16 + row * nchunks);
+      uint32_t t[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) t[j] = 0xffffu;
+      for (int i = lane; i < n2; i += 32) {
+        const uint32_t w = __ldg(m2 + i);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t v = (w >> (16 * h)) & 0xffffu;
+          if (v < t[7]) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {  // insertion: t stays sorted, the largest drops out
+              const uint32_t lo = min(t[j], v);
+              v = max(t[j], v);
+              t[j] = lo;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) vals[lane * 8 + j] = (uint16_t)t[j];
+      __syncwarp();
+      // the kp-th smallest of the 256 kept values: two 8-bit radix passes
+      int rank = kp;
+      prefix = 0;
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {
+        const int shift = 8 - 8 * pass;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) hist[lane * 8 + j] = 0;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const uint32_t e = vals[j * 32 + lane];
+          if (pass == 0 || (e >> 8) == prefix) atomicAdd(&hist[(e >> shift) & 255u], 1u);
+        }
+        __syncwarp();
+        int loc[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          loc[j] = (int)hist[lane * 8 + j];
+          sum += loc[j];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int yv = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += yv;
+        }
+        const int excl = incl - sum;
+        const int owner = __ffs(__ballot_sync(0xffffffffu, excl < rank && rank <= incl)) - 1;
+        int sel = 0, before = 0;
+        if (lane == owner) {
+          int c = excl;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (c + loc[j] >= rank) {
+              sel = lane * 8 + j;
+              before = c;
+              break;
+            }
+            c += loc[j];
+          }
+        }
+        sel = __shfl_sync(0xffffffffu, sel, owner);
+        before = __shfl_sync(0xffffffffu, before, owner);
+        rank -= before;
+        prefix = (prefix << 8) | (uint32_t)sel;
+        __syncwarp();
+      }
+    }
+    // candidate chunks in ascending order
+    const uint4* m8 = reinterpret_cast<const uint4*>(mins16 + row * nchunks);
+    int total = 0;
+    for (int base = 0; base < n8; base += 32) {
+      const int i = base + lane;
+      uint32_t bits = 0;
+      if (i < n8) {
+        const uint4 v = __ldg(m8 + i);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (((w[j >> 1] >> (16 * (j & 1))) & 0xffffu) <= prefix) bits |= 1u << j;
+      }
+      const int c = __popc(bits);
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int yv = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += yv;
+      }
+      int pos = total + incl - c;
+      while (bits) {
+        const int j = __ffs(bits) - 1;
+        bits &= bits - 1;
+        if (pos < CT_CL) clist[row * CT_CL + pos] = (uint32_t)(8 * i + j);
+        ++pos;
+      }
+      total += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) {
+      tau16[row] = prefix;
+      ccount[row] = total;
+      atomicAdd(&st->cand_appends, (unsigned long long)total);  // candidate chunks (status counter 4)
+    }
+  }
+}
+
+// Candidate chunks of the chunk-minima scan, evaluated exactly.  One warp per key:
+//  1. tau = the K'-th smallest rounded-up chunk minimum of the key (every chunk holding one of
+//     the key's K' smallest BF16 scores has its minimum at or below tau);
+//  2. every chunk with minimum <= tau (in position order, 4 chunks at a time: the image strips
+//     of the 4 chunks staged in shared memory, each lane scoring 4 adjacent positions from
+//     registers) gets the FP32 score ||q - mu||^2 - 2 <p - mu, q> (the squared distance of the
+//     mean-shifted patches minus a constant of the key), and a running list keeps the K' best
+//     (score, id) pairs;
+//  3. those K' get their exact distance sum((p - q)^2) (the re-rank's arithmetic), and the K
+//     smallest (distance, id) pairs are written sorted.
+// Chunks whose 32 positions wrap to the next row of the position grid are scored position by
+// position from global memory.
+constexpr int CT_WARPS = 4;
+constexpr int CT_LCAP = 512;  // running top-K' list of a warp (entries)
+constexpr int CT_CCAP = 512;  // candidate chunk ids gathered before they are scored
+
+constexpr int CT_SROW = 48;   // strip row stride (floats; 16-byte aligned rows)
+
+template <int PT, int CMAX>
+__host__ __device__ constexpr size_t chunk_topk_warp_bytes() {
+  return (size_t)CT_LCAP * 8 + CT_CCAP * 4 + 256 * 4 + (size_t)4 * CMAX * PT * CT_SROW * 4 + 2 * 96 * 4;
+}
+
+template <int PT, int CMAX>
+__global__ void __launch_bounds__(CT_WARPS * 32, 4)
+    k_chunk_topk(const float* __restrict__ x, const float* __restrict__ mean, const float* __restrict__ qn,
+                 const float* __restrict__ keyv,
+                 const int32_t* __restrict__ keys, const int32_t* __restrict__ n_found,
+                 const uint16_t* __restrict__ mins16, const uint32_t* __restrict__ tau16s,
+                 const int32_t* __restrict__ ccount, const uint32_t* __restrict__ clist_g, int n_img, int C, int H,
+                 int W, int N, int Npad, int nchunks, int K, int Kp, int32_t* __restrict__ idx,
+                 float* __restrict__ dist) {
+  constexpr int P = PT, PP = P * P, CP = CMAX * P, DM = CMAX * PP, SW = 32 + P - 1;
+  extern __shared__ unsigned long long ct_smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint8_t* wbase = reinterpret_cast<uint8_t*>(ct_smem) + (size_t)wid * chunk_topk_warp_bytes<PT, CMAX>();
+  unsigned long long* list = reinterpret_cast<unsigned long long*>(wbase);
+  uint32_t* clist = reinterpret_cast<uint32_t*>(wbase + CT_LCAP * 8);
+  unsigned* hist = reinterpret_cast<unsigned*>(wbase + CT_LCAP * 8 + CT_CCAP * 4);
+  float* strip = reinterpret_cast<float*>(wbase + CT_LCAP * 8 + CT_CCAP * 4 + 256 * 4);  // [4][CP][CT_SROW]
+  float* pv = strip + 4 * CP * CT_SROW;  // raw key patch (exact distances)
+  float* pk = pv + 96;                   // mean-shifted key patch
+  const int d = C * PP;
+  const int Hq = H - P + 1, Wq = W - P + 1;
+  const long long npos = (long long)Hq * Wq;
+  const int g = lane >> 3, l8 = lane & 7;
+  const unsigned ltm = (1u << lane) - 1u;
+  const long long nkeys = (long long)n_img * N;
+  for (long long gk = blockIdx.x * (long long)CT_WARPS + wid; gk < nkeys; gk += (long long)gridDim.x * CT_WARPS) {
+    const int f = (int)(gk / N), k = (int)(gk - (long long)f * N);
+    if (k >= min(n_found[f], N)) continue;
+    const int kq = keys[gk];
+    if ((unsigned)kq >= (unsigned)npos) continue;  // flagged by k_key_vectors
+    const int kr = kq / Wq, kc = kq - (kq / Wq) * Wq;
+    const float* xf = x + (long long)f * C * H * W;
+    for (int e = lane; e < d; e += 32) {
+      const int ch = e / PP, dr = (e / P) % P, dc = e % P;
+      pv[e] = __ldg(xf + ((long long)ch * H + kr + dr) * W + kc + dc);
+      pk[e] = keyv[((long long)f * Npad + k) * d + e];
+    }
+    __syncwarp();
+    float kreg[DM];
+#pragma unroll
+    for (int e = 0; e < DM; ++e) kreg[e] = e < d ? pk[e] : 0.f;
+    // the FP32 score sc = ||q'||^2 - 2 <p', q> is the squared distance of the mean-shifted
+    // patches minus c_k = ||p'||^2 + 2 mu sum(p'); a position can only hold one of the key's K'
+    // smallest BF16 scores if its distance is at most tau plus the BF16 error of that score,
+    // |s~ - d| <= 2^-8 S^2 + ... with S = ||p'|| + ||q'|| (BF16 rounds within 2^-9 per value),
+    // so only positions within that bound enter the list
+    float pn2 = 0.f, psum = 0.f;
+#pragma unroll
+    for (int e = 0; e < DM; ++e) {
+      pn2 = fmaf(kreg[e], kreg[e], pn2);
+      psum += kreg[e];
+    }
+    const float pn = sqrtf(pn2);
+    const float c_k = pn2 + 2.f * mean[f] * psum;
+    // 1. the bound and the candidate chunks (k_tau_chunk); a key with more candidates than the
+    //    list holds scans its chunk minima here
+    const long long row = (long long)f * Npad + k;
+    const uint32_t tau16 = tau16s[row];
+    const int ctot = ccount[row];
+    const bool listed = ctot <= CT_CL;
+    const uint16_t* mk = mins16 + row * nchunks;
+    const float* qf = qn + (long long)f * npos;
+    const float tau_f = tau16 < 0xff80u ? float_from_order_key((tau16 << 16) | 0xffffu) : INFINITY;
+    const float inv_wq = 1.f / (float)Wq;
+    // 2. candidate chunks, scored in groups of four
+    int cnt = 0, scan = 0;
+    unsigned long long kth = ~0ull;
+    for (;;) {
+      const uint32_t* ids;
+      int ncl = 0;
+      if (listed) {
+        for (int i = lane; i < ctot; i += 32) clist[i] = clist_g[row * CT_CL + i];
+        __syncwarp();
+        ids = clist;
+        ncl = ctot;
+      } else {
+        while (scan < nchunks && ncl < CT_CCAP - 32) {
+          const int c = scan + lane;
+          const bool cand = c < nchunks && (uint32_t)__ldg(mk + c) <= tau16;
+          const unsigned m = __ballot_sync(0xffffffffu, cand);
+          if (cand) clist[ncl + __popc(m & ltm)] = (uint32_t)c;
+          ncl += __popc(m);
+          scan += 32;
+        }
+        __syncwarp();
+        ids = clist;
+      }
+      for (int i0 = 0; i0 < ncl; i0 += 4) {
+        // the four chunks of this group; slot g of the warp scores chunk i0 + g.  Positions fit
+        // in 24 bits, so the row of a position id comes from a float reciprocal plus one fix-up.
+        const int cid = i0 + g < ncl ? (int)ids[i0 + g] : -1;
+        const int q0c = 32 * max(cid, 0);
+        int ra = (int)((float)q0c * inv_wq);
+        int ca = q0c - ra * Wq;
+        if (ca < 0) { --ra; ca += Wq; } else if (ca >= Wq) { ++ra; ca -= Wq; }
+        const bool simple = cid >= 0 && q0c < npos && ca + 31 < Wq;
+        // stage the strips of the slots' chunks: row by row, lanes along the row (coalesced)
+#pragma unroll
+        for (int s4 = 0; s4 < 4; ++s4) {
+          const int rs = __shfl_sync(0xffffffffu, ra, 8 * s4), cs = __shfl_sync(0xffffffffu, ca, 8 * s4);
+          if (__shfl_sync(0xffffffffu, (int)simple, 8 * s4)) {
+            const float* src = xf + (long long)rs * W + cs;
+            float* dst = strip + s4 * CP * CT_SROW;
+#pragma unroll
+            for (int row = 0; row < CP; ++row) {
+              if (row < C * P) {
+                const int ch = row / P, dr = row - (row / P) * P;
+                const float* sr = src + ((long long)ch * H + dr) * W;
+                dst[row * CT_SROW + lane] = __ldg(sr + lane);
+                if (lane < SW - 32) dst[row * CT_SROW + 32 + lane] = __ldg(sr + 32 + lane);
+              }
+            }
+          }
+        }
+        __syncwarp();
+        const int q0 = q0c + 4 * l8;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (simple) {
+#pragma unroll
+          for (int ch = 0; ch < CMAX; ++ch) {
+            if (ch < C) {
+#pragma unroll
+              for (int dr = 0; dr < P; ++dr) {
+                const float4* srow = reinterpret_cast<const float4*>(strip + (g * CP + ch * P + dr) * CT_SROW + 4 * l8);
+                float v[12];
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                  const float4 t = srow[u];
+                  v[4 * u] = t.x;
+                  v[4 * u + 1] = t.y;
+                  v[4 * u + 2] = t.z;
+                  v[4 * u + 3] = t.w;
+                }
+#pragma unroll
+                for (int dc = 0; dc < P; ++dc)
+#pragma unroll
+                  for (int i = 0; i < 4; ++i) acc[i] = fmaf(kreg[(ch * P + dr) * P + dc], v[i + dc], acc[i]);
+              }
+            }
+          }
+        } else if (cid >= 0) {
+          // the chunk wraps to the next row of positions (or ends the grid): position by position,
+          // the key patch read back from shared memory (a short loop keeps the code small)
+#pragma unroll 1
+          for (int i = 0; i < 4; ++i) {
+            const int q = q0 + i;
+            float a = 0.f;
+            if (q < npos) {
+              int r = (int)((float)q * inv_wq);
+              int c = q - r * Wq;
+              if (c < 0) { --r; c += Wq; } else if (c >= Wq) { ++r; c -= Wq; }
+#pragma unroll 1
+              for (int ch = 0; ch < C; ++ch)
+#pragma unroll 1
+                for (int dr = 0; dr < P; ++dr) {
+                  const float* xr = xf + ((long long)ch * H + r + dr) * W + c;
+                  const float* kp = pk + (ch * P + dr) * P;
+#pragma unroll
+                  for (int dc = 0; dc < P; ++dc) a = fmaf(kp[dc], __ldg(xr + dc), a);
+                }
+            }
+            acc[i] = a;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int q = q0 + i;
+          const bool valid = cid >= 0 && q < npos;
+          unsigned long long e = ~0ull;
+          bool near = false;
+          if (valid) {
+            const float qq = __ldg(qf + q);
+            const float sc = fmaf(-2.f, acc[i], qq);
+            const float S = pn + sqrtf(qq);
+            const float thr = tau_f + 0.004f * S * S + 1e-4f * (1.f + fabsf(sc) + fabsf(c_k) + qq + pn2);
+            near = sc + c_k <= thr;
+            e = ((unsigned long long)float_order_key(sc) << 32) | (unsigned)q;
+          }
+          const bool keep = valid && near && e < kth;
+          const unsigned m = __ballot_sync(0xffffffffu, keep);
+          if (keep) list[cnt + __popc(m & ltm)] = e;
+          cnt += __popc(m);
+        }
+        __syncwarp();
+        if (cnt > CT_LCAP - 128 && cnt > Kp) cnt = warp_keep_smallest_kth(list, cnt, Kp, hist, lane, &kth);
+      }
+      __syncwarp();
+      if (listed || scan >= nchunks) break;
+    }
+    if (cnt > Kp) cnt = warp_keep_smallest_kth(list, cnt, Kp, hist, lane, &kth);
+    // 3. exact distances of the K' best, in the re-rank's order of summation
+    for (int i = lane; i < cnt; i += 32) {
+      const int q = (int)(unsigned)(list[i] & 0xffffffffull);
+      const int r = q / Wq, c = q - (q / Wq) * Wq;
+      float acc = 0.f;
+      for (int ch = 0; ch < C; ++ch)
+        for (int dr = 0; dr < P; ++dr) {
+          const float* rowp = xf + ((long long)ch * H + r + dr) * W + c;
+          const float* pp = pv + (ch * P + dr) * P;
+          for (int dc = 0; dc < P; ++dc) {
+            const float df = pp[dc] - __ldg(rowp + dc);
+            acc = fmaf(df, df, acc);
+          }
+        }
+      list[i] = ((unsigned long long)float_order_key(acc) << 32) | (unsigned)q;
+    }
+    __syncwarp();
+    int total = cnt;
+    if (total > K) total = warp_keep_smallest(list, total, K, hist, lane);
+    int p2 = 32;
+    while (p2 < total) p2 <<= 1;
+    for (int i = total + lane; i < p2; i += 32) list[i] = ~0ull;
+    __syncwarp();
+    for (int kk = 2; kk <= p2; kk <<= 1) {
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < p2; i += 32) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const bool up = (i & kk) == 0;
+            const unsigned long long a = list[i], b = list[ixj];
+            if ((a > b) == up) {
+              list[i] = b;
+              list[ixj] = a;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    for (int i = lane; i < K; i += 32) {
+      const unsigned long long e = list[i];
+      if (idx) idx[gk * K + i] = (int32_t)(e & 0xffffffffu);
+      if (dist) dist[gk * K + i] = float_from_order_key((uint32_t)(e >> 32));
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace
 
 int image_mean_slices(const glr_images& im) {
@@ -487,6 +917,42 @@ glr_status launch_image_mean(const float* x, const glr_images& im, float* mean, 
   GLR_LAUNCH("k_image_mean", s, k_image_mean_part<<<(unsigned)(im.n_img * S), 512, 0, s>>>(x, n, S, part));
   GLR_LAUNCH("k_image_mean_final", s,
              k_image_mean_final<<<(unsigned)ceil_div(im.n_img, 128), 128, 0, s>>>(part, im.n_img, S, n, mean));
+  return GLR_OK;
+}
+
+// Exact evaluation of the candidate chunks (bound_pass 2).
+glr_status launch_chunk_topk(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found,
+                             int N, const MatchPlan& pl, const float* mean, const float* qn, const float* keyv,
+                             const uint16_t* mins16, char* ws, int32_t* idx, float* dist, cudaStream_t s) {
+  const long long nkeys = (long long)im.n_img * N;
+  const int nchunks = 8 * pl.pos_tiles;
+  uint32_t* tau16s = reinterpret_cast<uint32_t*>(ws + pl.taugl_off);
+  int32_t* ccount = reinterpret_cast<int32_t*>(ws + pl.ccnt_off);
+  uint32_t* clist_g = reinterpret_cast<uint32_t*>(ws + pl.clist_off);
+  {
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, 8), (long long)num_sms() * 16));
+    GLR_LAUNCH("k_tau_chunk", s, k_tau_chunk<<<blocks, 256, 0, s>>>(mins16, n_found, im.n_img, N, pl.Npad, nchunks,
+                                                                     pl.Kp, tau16s, ccount, clist_g,
+                                                                     reinterpret_cast<StatusBlock*>(ws)));
+  }
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, CT_WARPS), (long long)num_sms() * 8));
+#define GLR_CHUNK_CASE(PP, CM)                                                                                  \
+  {                                                                                                             \
+    const size_t smem = (size_t)CT_WARPS * chunk_topk_warp_bytes<PP, CM>();                                     \
+    if (cudaFuncSetAttribute(k_chunk_topk<PP, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=    \
+        cudaSuccess)                                                                                            \
+      return GLR_ECUDA;                                                                                         \
+    GLR_LAUNCH("k_chunk_topk", s,                                                                               \
+               (k_chunk_topk<PP, CM><<<blocks, CT_WARPS * 32, smem, s>>>(x, mean, qn, keyv, keys, n_found, mins16, \
+                                                                        tau16s, ccount, clist_g, im.n_img, im.C, \
+                                                                        im.H, im.W, N, pl.Npad, nchunks, pl.K,   \
+                                                                        pl.Kp, idx, dist)));                     \
+  }
+  if (im.P == 8 && im.C == 1) GLR_CHUNK_CASE(8, 1)
+  else if (im.P == 6 && im.C <= 2) GLR_CHUNK_CASE(6, 2)
+  else if (im.P == 4 && im.C <= 4) GLR_CHUNK_CASE(4, 4)
+  else return GLR_ENOTSUP;
+#undef GLR_CHUNK_CASE
   return GLR_OK;
 }
 
@@ -536,7 +1002,13 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   pl.meanp_off = L.take((size_t)im.n_img * kMeanMaxSlices * 8);
   pl.qn_off = L.take((size_t)im.n_img * npos * 4);
   pl.keyv_off = L.take((size_t)im.n_img * pl.Npad * d * 4);
-  const long long nstreams = (long long)im.n_img * pl.Npad * pl.streams_per_key;
+  // chunk-minima scan + exact evaluation of the candidate chunks (bound_pass 2): BF16 mode,
+  // one 64-column chunk per operand row, a patch side the evaluation kernel is compiled for
+  const int bp = o ? o->bound_pass : 0;
+  const bool chunk_ok = pl.mode == GLR_MATCH_BF16 && d <= 74 && (im.P == 4 || im.P == 6 || im.P == 8) &&
+                        im.C * im.P <= 16 && npos < (1LL << 24) - 64;  // position ids exact in FP32
+  const bool chunk = chunk_ok && (bp == 2 || bp == 0);
+  const long long nstreams = chunk ? 0 : (long long)im.n_img * pl.Npad * pl.streams_per_key;
   pl.buf_off = L.take((size_t)nstreams * (pl.cap + 32) * 8);
   pl.bufcnt_off = L.take((size_t)nstreams * 4);
   pl.taugl_off = L.take((size_t)im.n_img * pl.Npad * 4);
@@ -554,9 +1026,15 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
     // the bound of the minima scan needs Kp half tiles.  Automatic: on for one-chunk
     // rows, where the candidate appends cost more than a second contraction; off for
     // chunked rows (d > 74), where the contraction itself dominates
-    const int bp = o ? o->bound_pass : 0;
-    pl.bound_pass = ((bp > 0 || (bp == 0 && pl.nkc == 1)) && 2LL * pl.pos_tiles >= pl.Kp) ? 1 : 0;
-    if (pl.bound_pass) pl.mins_off = L.take((size_t)im.n_img * pl.Npad * 2 * pl.pos_tiles * 4);
+    if (chunk) {
+      pl.bound_pass = 2;  // rounded-up 16-bit minima of every 32-position chunk
+      pl.mins_off = L.take((size_t)im.n_img * pl.Npad * 8 * pl.pos_tiles * 2);
+      pl.ccnt_off = L.take((size_t)im.n_img * pl.Npad * 4);
+      pl.clist_off = L.take((size_t)im.n_img * pl.Npad * CT_CL * 4);
+    } else {
+      pl.bound_pass = ((bp == 1 || ((bp == 0 || bp == 2) && pl.nkc == 1)) && 2LL * pl.pos_tiles >= pl.Kp) ? 1 : 0;
+      if (pl.bound_pass) pl.mins_off = L.take((size_t)im.n_img * pl.Npad * 2 * pl.pos_tiles * 4);
+    }
   }
   if (edge) pl.edge_off = L.take((size_t)im.n_img * 4 * im.C * im.H * im.W * 4);
   if (pl.mode == GLR_MATCH_LEARNED) {
@@ -616,7 +1094,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     const glr_status st = launch_image_mean(x, im, mean, reinterpret_cast<double*>(ws + pl.meanp_off), s);
     if (st != GLR_OK) return st;
   }
-  if (!tc) {  // the FP32 scorer adds ||q||^2 itself; the tensor-core operands carry their norms
+  if (!tc || pl.bound_pass == 2) {  // the FP32 scorers add ||q||^2 themselves; the tensor-core operands carry theirs
     const long long total = (long long)im.n_img * npos;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)num_sms() * 32));
     GLR_LAUNCH("k_patch_norms", s, k_patch_norms<<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, qn));
@@ -639,6 +1117,9 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
   if (tc) {
     const glr_status st = launch_match_tc(xs, ime, keys, n_found, N, pl, ws, s);
     if (st != GLR_OK) return st;
+    if (pl.bound_pass == 2)
+      return launch_chunk_topk(x, im, keys, n_found, N, pl, mean, qn, keyv,
+                               reinterpret_cast<const uint16_t*>(ws + pl.mins_off), ws, idx, dist, s);
   } else {
     // channels per chunk: all of them if the transposed key tile fits, else as many as fit
     auto fp32_smem = [&](int cc) {

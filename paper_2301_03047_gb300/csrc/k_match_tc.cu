@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(256) k_seed_bounds(const __nv_bfloat16* __rest
   }
 }
 
-template <int EB, bool WIDE, bool MINS>
+template <int EB, bool WIDE, int MINS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_match_tc(const __grid_constant__ CUtensorMap tm_qmain, const __grid_constant__ CUtensorMap tm_qaux,
                const __grid_constant__ CUtensorMap tm_kmain, const __grid_constant__ CUtensorMap tm_kaux,
@@ -656,9 +656,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                int tiles_per_split, int ntiles, int nkc, StreamCfg cfg, uint2* __restrict__ bufs,
                int* __restrict__ buf_cnt, uint32_t* __restrict__ tau_gl, StatusBlock* st, float* __restrict__ dump,
                float* __restrict__ mins) {
-  // MINS: bound pass.  No candidate is kept; each epilogue lane writes the minimum
+  // MINS = 1: bound pass.  No candidate is kept; each epilogue lane writes the minimum
   // score of its row over every half tile (128 positions) to mins[key][2 tile + half]
   // instead (all four 32-column chunks read from TMEM in one visit).
+  // MINS = 2: chunk-minima scan.  The minimum of every 32-position chunk, as the upper
+  // 16 bits of its order key rounded up (so it is never below the true minimum), four
+  // chunks of a half tile packed in 8 bytes: mins viewed as uint16 [key][8 tile + 4 half + c].
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t kBar = WIDE ? W_OFF_BAR : OFF_BAR, kMisc = WIDE ? W_OFF_MISC : OFF_MISC;
@@ -858,7 +861,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) break;
       tc_fence_after();
       const long long tile_q0 = (long long)(t_begin + i) * TC_N;
-      if constexpr (MINS) {
+      if constexpr (MINS == 2) {
+        float w[4][32];
+        const uint32_t taddr = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tmem_ld_32x32_nowait(taddr + 32 * c, w[c]);
+        tmem_ld_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty + b);
+        uint32_t k16[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int nvalid = (int)max(0LL, min(32LL, npos - (tile_q0 + h * 128 + 32 * c)));
+          const uint32_t k32 = float_order_key(stream_min(w[c], nvalid));
+          k16[c] = min((k32 >> 16) + ((k32 & 0xffffu) != 0u ? 1u : 0u), 0xffffu);
+        }
+        reinterpret_cast<uint2*>(mins)[(((long long)f * Npad + key) * ntiles + t_begin + i) * 2 + h] =
+            make_uint2(k16[0] | (k16[1] << 16), k16[2] | (k16[3] << 16));
+        continue;
+      } else if constexpr (MINS == 1) {
         float w[4][32], v[128];
         const uint32_t taddr = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128);
 #pragma unroll
@@ -923,7 +945,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
     }
-    if constexpr (!MINS) {
+    if constexpr (MINS == 0) {
       if (cfg.finish) stream_finish(tau, cnt, mybuf, cfg, whist);
       stream_stats_flush(stats, st);
       buf_cnt[stream] = (key < nf) ? cnt : 0;
@@ -1034,8 +1056,8 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
         !make_map(&tk, kmain, krows, wcols, TC_M, CU_TENSOR_MAP_SWIZZLE_128B, DK_MAIN) ||
         !make_map(&tka, kaux, krows, DK_AUX, TC_M, CU_TENSOR_MAP_SWIZZLE_32B))
       return GLR_ECUDA;
-    auto kern = pl.epi_batch == 2 ? k_match_tc<2, true, false> : k_match_tc<4, true, false>;
-    auto kmin = k_match_tc<4, true, true>;
+    auto kern = pl.epi_batch == 2 ? k_match_tc<2, true, 0> : k_match_tc<4, true, 0>;
+    auto kmin = k_match_tc<4, true, 1>;
     if (pl.bound_pass &&
         cudaFuncSetAttribute(kmin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W_SMEM) != cudaSuccess)
       return GLR_ECUDA;
@@ -1098,8 +1120,22 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
       !make_map(&tk, kmain, krows, DK_MAIN, TC_M, CU_TENSOR_MAP_SWIZZLE_128B) ||
       !make_map(&tka, kaux, krows, DK_AUX, TC_M, CU_TENSOR_MAP_SWIZZLE_32B))
     return GLR_ECUDA;
-  auto kern = pl.epi_batch == 2 ? k_match_tc<2, false, false> : k_match_tc<4, false, false>;
-  auto kmin = k_match_tc<4, false, true>;
+  auto kern = pl.epi_batch == 2 ? k_match_tc<2, false, 0> : k_match_tc<4, false, 0>;
+  auto kmin = k_match_tc<4, false, 1>;
+  if (pl.bound_pass == 2) {
+    // chunk-minima scan only; the exact evaluation of the candidate chunks follows (k_match.cu)
+    auto kch = k_match_tc<4, false, 2>;
+    if (cudaFuncSetAttribute(kch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) != cudaSuccess)
+      return GLR_ECUDA;
+    const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
+    const StreamCfg cfg{pl.cap, pl.Kp, pl.finish, g_match_wait_ns > 0 ? g_match_wait_ns : kWaitNs};
+    dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
+    GLR_LAUNCH("k_match_tc_chunk", s,
+               kch<<<grid, TC_THREADS, TC_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad, pl.splits,
+                                                     pl.tiles_per_split, pl.pos_tiles, 1, cfg, bufs, bufcnt, taugl, st,
+                                                     nullptr, mins));
+    return GLR_OK;
+  }
   if (pl.bound_pass &&
       cudaFuncSetAttribute(kmin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) != cudaSuccess)
     return GLR_ECUDA;

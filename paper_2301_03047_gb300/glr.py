@@ -56,7 +56,9 @@ def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0, cap: 
                window: int = 20, bound_pass: int = 0) -> L.GlrMatchOpts:
     """mode: "fp32" (plain), "bf16" (chosen), "learned", "edge" (the paper's heat map of Eq. 4),
     or "window" (block matching within +-window of the key).  bound_pass (tensor-core modes):
-    1 = a minima scan gives each key its starting bound, -1 = no minima scan, 0 = automatic."""
+    2 = chunk minima, then an exact FP32 evaluation of the candidate chunks; 1 = a minima scan
+    gives each key its starting bound for the candidate scan; -1 = one candidate scan;
+    0 = automatic."""
     m = {"fp32": L.GLR_MATCH_FP32, "bf16": L.GLR_MATCH_BF16, "learned": L.GLR_MATCH_LEARNED,
          "edge": L.GLR_MATCH_EDGE, "window": L.GLR_MATCH_WINDOW}.get(mode, mode)
     o = L.GlrMatchOpts()
@@ -149,8 +151,8 @@ def debug_match_scores(x, P, keys, n_found, K, *, ws=None, stream=None):
     N = keys.shape[1]
     npad = (N + 127) // 128 * 128
     scores = torch.full((x.shape[0], npad, 256), float("nan"), dtype=torch.float32, device=x.device)
-    if ws is None:
-        ws = workspace(L.GLR_OP_MATCH, im, N, K, match_opts("bf16"), x.device)
+    if ws is None:  # the raw scores come from the candidate scan (bound_pass -1)
+        ws = workspace(L.GLR_OP_MATCH, im, N, K, match_opts("bf16", bound_pass=-1), x.device)
     wp, wn = _ws(ws)
     _check("glr_debug_match_scores", lib.glr_debug_match_scores(_ptr(x), ctypes.byref(im), _ptr(keys), _ptr(n_found),
                                                                 int(N), int(K), _ptr(scores), wp, wn, _stream(stream)))
@@ -615,10 +617,14 @@ def autotune_match(x, P, keys, n_found, K, mode="bf16", candidates=None, repeats
         # position splits up to 8: with few key tiles (one large image) more splits fill the SMs
         candidates = [(K + 16, sp, cap, e, b) for sp in (1, 2, 3, 4, 6, 8) for cap in (0, 128, 320) for e in eb
                       for b in bp]
+        if mode == "bf16":
+            # chunk minima + exact evaluation: no streams, so capacity and epilogue batch do not apply
+            candidates = [(K + 16, sp, 0, 0, 2) for sp in (1, 2, 3, 4, 6, 8)] + candidates
     candidates = [tuple(c) + (0,) * (5 - len(c)) for c in candidates]
     im = images_of(x, P)
     best, best_t = None, float("inf")
-    timed = ("k_match_tc", "k_match_tc_min", "k_tau_bound", "k_match_fp32", "k_rerank", "k_seed_bounds")
+    timed = ("k_match_tc", "k_match_tc_min", "k_tau_bound", "k_match_fp32", "k_rerank", "k_seed_bounds",
+             "k_match_tc_chunk", "k_chunk_topk", "k_patch_norms")
     for kover, sp, cap, eb, bp in candidates:
         o = match_opts(mode, kover, sp, cap, None, eb, bound_pass=bp)
         try:
