@@ -257,10 +257,11 @@ int32_t glr_debug_wnnm_sweep_cap(int32_t cap);
  * tau_i = c_wnnm sigma_w^2 / (sigma_hat_i + 1e-8), s'_i = max(s_i - tau_i, 0),
  * the output is X^ = U diag(s') V^T.  The SVD is a one-sided Jacobi in FP32
  * (columns in registers for d <= 64 and K <= 64, in shared memory otherwise;
- * tall groups with K <= 32 through the Gram matrix).  Register-path groups that
- * reach the 30-sweep cap are recomputed in FP64 (Gram matrix, two-sided Jacobi)
- * by a second kernel in the same call; the status block counts them
- * (svd_noconv).
+ * tall groups with K <= 32 through the Gram matrix).  Groups that reach the
+ * 30-sweep cap of any of these paths are recomputed in FP64 (Gram matrix,
+ * two-sided Jacobi) by a second kernel in the same call (K <= 96; above that a
+ * capped group keeps its FP32 result); the status block counts them
+ * (svd_noconv, and fb_noconv for groups the FP64 sweeps cannot finish either).
  *
  *   idx      int32 [n_img][N][K] matches (from glr_match_topk).
  *   groups   out, float32 [n_img][N][K][d]: row j = column j of X^.
@@ -296,7 +297,10 @@ glr_status glr_lowrank_aggregate(const float* x, const glr_images* im, const int
  * m x K matrix of the K patches; its SVD Y = U S V^H (one-sided Jacobi with
  * Hermitian rotations, FP32) is shrunk with the same formula, sigma_w being
  * the noise standard deviation per complex entry, and X^ = U diag(s') V^H is
- * written back in the same two-half layout.  Limits: 2 P^2 <= 640, K <= 128.
+ * written back in the same two-half layout.  Groups at the sweep cap are
+ * recomputed in FP64 as the real 2 P^2 x 2K matrix [[Re, -Im], [Im, Re]] (same
+ * singular values, each twice) when K <= 48.  Limits: 2 P^2 <= 640, K <= 128.
+ * Workspace: glr_workspace_size(GLR_OP_LOWRANK, ...).
  */
 glr_status glr_lowrank_groups_complex(const float* x, const glr_images* im, const int32_t* idx,
                                       const int32_t* n_found, int32_t N, int32_t K, float sigma_w,

@@ -315,8 +315,8 @@ glr_status glr_lowrank_groups(const float* x, const glr_images* im, const int32_
     return launch_wnnm(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, fb_queue, s);
   // tall groups: Gram matrix + two-sided Jacobi (work O(d K^2) once instead of per sweep)
   if (K <= 32 && d >= 2 * K)
-    return launch_gram_wnnm(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
-  return launch_wnnm_smem(*im, false, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
+    return launch_gram_wnnm(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, fb_queue, s);
+  return launch_wnnm_smem(*im, false, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, fb_queue, s);
 }
 
 glr_status glr_lowrank_aggregate(const float* x, const glr_images* im, const int32_t* idx, const int32_t* n_found,
@@ -345,13 +345,15 @@ glr_status glr_lowrank_groups_complex(const float* x, const glr_images* im, cons
   const int d = im->C * im->P * im->P;
   if (d > 640 || K > 128 || d % 4 != 0) return GLR_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
-  glr_status st = begin_ws(ws, ws_bytes, sizeof(StatusBlock), s);
+  glr_status st = begin_ws(ws, ws_bytes, glr_workspace_size(GLR_OP_LOWRANK, im, N, K, nullptr), s);
   if (st != GLR_OK) return st;
   st = launch_gather(x, *im, idx, n_found, N, K, groups, (StatusBlock*)ws, s);
   if (st != GLR_OK) return st;
+  WsLayout L;
+  int32_t* fb_queue = reinterpret_cast<int32_t*>((char*)ws + L.take((size_t)im->n_img * N * 4));
   if (d <= 72 && K <= 64)
-    return launch_wnnm_complex_regs(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
-  return launch_wnnm_smem(*im, true, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, s);
+    return launch_wnnm_complex_regs(*im, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, fb_queue, s);
+  return launch_wnnm_smem(*im, true, n_found, N, K, sigma_w, c_wnnm, groups, rank, (StatusBlock*)ws, fb_queue, s);
 }
 
 glr_status glr_admm_sci_step(const float* y, const float* masks, int64_t mask_group_stride, const float* z,

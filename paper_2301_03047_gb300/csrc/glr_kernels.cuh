@@ -79,10 +79,13 @@ extern unsigned long long g_match_wait_ns;
 // ---- low-rank step (k_lowrank.cu)
 glr_status launch_gather(const float* x, const glr_images& im, const int32_t* idx, const int32_t* n_found, int N,
                          int K, float* groups, StatusBlock* st, cudaStream_t s);
+// fb_queue (may be nullptr): groups at the sweep cap are queued for the FP64 fallback instead of
+// keeping their FP32 result (the caller then runs launch_wnnm_fp64)
 glr_status launch_gram_wnnm(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
-                            float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
+                            float* groups, int32_t* rank, StatusBlock* st, int32_t* fb_queue, cudaStream_t s);
 glr_status launch_wnnm_smem(const glr_images& im, bool cplx, const int32_t* n_found, int N, int K, float sigma_w,
-                            float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
+                            float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, int32_t* fb_queue,
+                            cudaStream_t s);
 glr_status launch_edge_planes(const float* x, const glr_images& im, float th, float* planes, cudaStream_t s);
 glr_status launch_admm_sci(const float* y, const float* masks, long long mstride, const float* z, const float* x,
                            float* u, int G, int T, long long HW, float rho, float* x_out, float* w_out, cudaStream_t s);
@@ -96,13 +99,16 @@ glr_status launch_wnnm_fused(const float* x, const glr_images& im, const int32_t
                              int K, float sigma_w, float c_wnnm, unsigned long long* num, int* cnt, int32_t* rank,
                              StatusBlock* st, cudaStream_t s);
 glr_status launch_wnnm_complex_regs(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w,
-                                   float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s);
+                                   float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, int32_t* fb_queue,
+                                   cudaStream_t s);
 // fb_queue: n_img * N int32 of scratch for the FP64 fallback (nullptr: no fallback)
 glr_status launch_wnnm(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
                        float* groups, int32_t* rank, StatusBlock* st, int32_t* fb_queue, cudaStream_t s);
-// FP64 Gram + two-sided Jacobi for the groups queued by the register kernel (k_lowrank_fp64.cu)
+// FP64 Gram + two-sided Jacobi for the groups queued by the FP32 kernels (k_lowrank_fp64.cu);
+// complex groups (cplx) through their real 2m x 2K form; supported while K (2K complex) <= 96
+bool wnnm_fp64_supported(int K, bool cplx);
 glr_status launch_wnnm_fp64(int d, int K, float sigma_w, float c_wnnm, float* groups, int32_t* rank,
-                            const int32_t* queue, StatusBlock* st, cudaStream_t s);
+                            const int32_t* queue, StatusBlock* st, cudaStream_t s, bool cplx = false);
 // testing aid: sweep cap of the register Jacobi (0: 30)
 extern int g_wnnm_sweep_cap;
 

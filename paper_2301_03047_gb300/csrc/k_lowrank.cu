@@ -616,10 +616,15 @@ glr_status launch_wnnm_fused(const float* x, const glr_images& im, const int32_t
 }
 
 glr_status launch_wnnm_complex_regs(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w,
-                                   float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s) {
+                                   float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, int32_t* fb_queue,
+                                   cudaStream_t s) {
   const int d = im.C * im.P * im.P;
   if (d > 72 || (d % 2) != 0 || K > 64 || K < 1) return GLR_ENOTSUP;
-  return launch_wnnm_regs<72, true>(im, n_found, N, K, sigma_w, c_wnnm, groups, rank, st, s, "k_jacobi_wnnm_c");
+  if (!wnnm_fp64_supported(K, true)) fb_queue = nullptr;  // capped groups keep their FP32 result (flagged)
+  glr_status r = launch_wnnm_regs<72, true>(im, n_found, N, K, sigma_w, c_wnnm, groups, rank, st, s,
+                                            "k_jacobi_wnnm_c", FusedIO{}, fb_queue);
+  if (r != GLR_OK || fb_queue == nullptr) return r;
+  return launch_wnnm_fp64(d, K, sigma_w, c_wnnm, groups, rank, fb_queue, st, s, true);
 }
 
 }  // namespace glr

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(WJ_THREADS) k_jacobi_smem(int n_img, int dr, i
                                                             const int32_t* __restrict__ n_found, float sigma_w,
                                                             float c_wnnm, float tol, int max_sweeps,
                                                             float* __restrict__ groups, int32_t* __restrict__ rank,
-                                                            StatusBlock* st) {
+                                                            StatusBlock* st, int32_t* __restrict__ fb_queue) {
   extern __shared__ float sm[];
   const int Kp = K + (K & 1);  // an odd K gets one zero column (it never rotates)
   float* Wc = sm;              // [Kp][dr]
@@ -184,10 +184,13 @@ __global__ void __launch_bounds__(WJ_THREADS) k_jacobi_smem(int n_img, int dr, i
       if (!converged) {
         atomicAdd(&st->svd_noconv, 1u);
         status_set(st, GLR_DEV_SVD_NOCONV);
+        // the group stays as gathered and goes to the FP64 fallback, which writes X^ and the rank
+        if (fb_queue != nullptr) fb_queue[atomicAdd(&st->fb_count, 1u)] = (int32_t)g;
       }
       atomicAdd(&st->sweeps, (unsigned)sweep);
       atomicAdd(&st->groups, 1u);
     }
+    if (!converged && fb_queue != nullptr) continue;  // uniform over the CTA
     // singular values s_i = |w_i| and the WNNM coefficients s'_i / s_i^3
     for (int j = wid; j < Kp; j += WJ_WARPS) {
       const float* w = Wc + (size_t)j * dr;
@@ -309,7 +312,7 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_gram_wnnm(int n_img, int d, i
                                                              const int32_t* __restrict__ n_found, float sigma_w,
                                                              float c_wnnm, float tol, int max_sweeps,
                                                              float* __restrict__ groups, int32_t* __restrict__ rank,
-                                                             StatusBlock* st) {
+                                                             StatusBlock* st, int32_t* __restrict__ fb_queue) {
   __shared__ float Gs[GW_WARPS][32][GW_LD];
   __shared__ float Vs[GW_WARPS][32][GW_LD];
   __shared__ float Ts[GW_WARPS][32][GW_LD];
@@ -443,10 +446,13 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_gram_wnnm(int n_img, int d, i
       if (!converged) {
         atomicAdd(&st->svd_noconv, 1u);
         status_set(st, GLR_DEV_SVD_NOCONV);
+        // the group stays as gathered and goes to the FP64 fallback, which writes X^ and the rank
+        if (fb_queue != nullptr) fb_queue[atomicAdd(&st->fb_count, 1u)] = (int32_t)g;
       }
       atomicAdd(&st->sweeps, (unsigned)sweep);
       atomicAdd(&st->groups, 1u);
     }
+    if (!converged && fb_queue != nullptr) continue;  // uniform over the warp
     // ---- WNNM weights c_i = s'_i / s_i
     const float li = G[lane][lane];
     float ci = 0.f;
@@ -502,13 +508,15 @@ __global__ void __launch_bounds__(GW_WARPS * 32) k_gram_wnnm(int n_img, int d, i
 }  // namespace
 
 glr_status launch_gram_wnnm(const glr_images& im, const int32_t* n_found, int N, int K, float sigma_w, float c_wnnm,
-                            float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s) {
+                            float* groups, int32_t* rank, StatusBlock* st, int32_t* fb_queue, cudaStream_t s) {
   const int d = im.C * im.P * im.P;
   if (K < 1 || K > 32 || d < 2 * K) return GLR_ENOTSUP;
   const long long ngroups = (long long)im.n_img * N;
   const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(ngroups, GW_WARPS), (long long)num_sms() * 64));
-  GLR_LAUNCH("k_gram_wnnm", s, k_gram_wnnm<<<blocks, GW_WARPS * 32, 0, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, 1e-5f, 30, groups, rank, st));
-  return GLR_OK;
+  const int cap = g_wnnm_sweep_cap > 0 ? g_wnnm_sweep_cap : 30;
+  GLR_LAUNCH("k_gram_wnnm", s, k_gram_wnnm<<<blocks, GW_WARPS * 32, 0, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, 1e-5f, cap, groups, rank, st, fb_queue));
+  if (fb_queue == nullptr) return GLR_OK;
+  return launch_wnnm_fp64(d, K, sigma_w, c_wnnm, groups, rank, fb_queue, st, s, false);
 }
 
 size_t wnnm_smem_bytes(int d, int K) {
@@ -517,7 +525,8 @@ size_t wnnm_smem_bytes(int d, int K) {
 }
 
 glr_status launch_wnnm_smem(const glr_images& im, bool cplx, const int32_t* n_found, int N, int K, float sigma_w,
-                            float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, cudaStream_t s) {
+                            float c_wnnm, float* groups, int32_t* rank, StatusBlock* st, int32_t* fb_queue,
+                            cudaStream_t s) {
   const int d = im.C * im.P * im.P;
   if (K < 1 || K > 128 || d > 640 || (cplx && (d % 2) != 0)) return GLR_ENOTSUP;
   const size_t smem = wnnm_smem_bytes(d, K);
@@ -541,11 +550,14 @@ glr_status launch_wnnm_smem(const glr_images& im, bool cplx, const int32_t* n_fo
   if (per_sm < 1) return GLR_ENOTSUP;
   const int blocks = (int)std::max<long long>(1, std::min<long long>(ngroups, (long long)num_sms() * per_sm * 4));
   const float tol = 1e-5f;
+  const int cap = g_wnnm_sweep_cap > 0 ? g_wnnm_sweep_cap : 30;
+  if (!wnnm_fp64_supported(K, cplx)) fb_queue = nullptr;  // capped groups keep their FP32 result (flagged)
   if (cplx)
-    GLR_LAUNCH("k_jacobi_smem", s, k_jacobi_smem<true><<<blocks, WJ_THREADS, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, 30, groups, rank, st));
+    GLR_LAUNCH("k_jacobi_smem", s, k_jacobi_smem<true><<<blocks, WJ_THREADS, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, cap, groups, rank, st, fb_queue));
   else
-    GLR_LAUNCH("k_jacobi_smem", s, k_jacobi_smem<false><<<blocks, WJ_THREADS, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, 30, groups, rank, st));
-  return GLR_OK;
+    GLR_LAUNCH("k_jacobi_smem", s, k_jacobi_smem<false><<<blocks, WJ_THREADS, smem, s>>>(im.n_img, d, N, K, n_found, sigma_w, c_wnnm, tol, cap, groups, rank, st, fb_queue));
+  if (fb_queue == nullptr) return GLR_OK;
+  return launch_wnnm_fp64(d, K, sigma_w, c_wnnm, groups, rank, fb_queue, st, s, cplx);
 }
 
 }  // namespace glr

@@ -270,3 +270,69 @@ def test_mri_graph_replay_matches_eager():
         b.step_graph(s)
     torch.cuda.synchronize()
     np.testing.assert_allclose(b.x.cpu().numpy(), a.x.cpu().numpy(), rtol=1e-4, atol=1e-4)
+
+
+def _fallback_run(x, P, idx, nf, sw, cw, complex_):
+    im = glr.images(x.shape[0], x.shape[1], x.shape[2], x.shape[3], P)
+    N, K = idx.shape[1], idx.shape[2]
+    ws = glr.workspace(glr.L.GLR_OP_LOWRANK, im, N, K)
+    old = glr.debug_wnnm_sweep_cap(1)
+    try:
+        groups, rank = glr.lowrank_groups(cuda(x), P, cuda(idx, torch.int32), cuda(nf, torch.int32), sw, cw, ws=ws,
+                                          complex_=complex_)
+        torch.cuda.synchronize()
+        _, cnt = glr.poll_status(ws)
+    finally:
+        glr.debug_wnnm_sweep_cap(old)
+    return groups.cpu().numpy(), rank.cpu().numpy(), cnt
+
+
+@pytest.mark.parametrize("case", [("fbw1", 16, 24, 26, 6, 8, 32, 0.05),   # tall groups: the Gram path (d 576, K 32)
+                                  ("fbw2", 3, 24, 26, 6, 8, 40, 0.1),    # shared-memory path (d 108, K 40)
+                                  ("fbw3", 2, 24, 24, 8, 6, 90, 0.02)])  # shared-memory path, K 90 (FP64 size 96)
+def test_lowrank_fp64_fallback_wide_real(case):
+    """A sweep cap of 1 sends the groups the FP32 Gram / shared-memory Jacobi cannot finish in one
+    sweep to the FP64 fallback; its X^ is the oracle's to FP32 output rounding (the bar of the
+    register path's fallback test)."""
+    tag, C, H, W, P, N, K, sw = case
+    rng = synth.rng_for(tag)
+    x = synth.textured_frames(rng, C, H, W).reshape(1, C, H, W)
+    npos = (H - P + 1) * (W - P + 1)
+    idx = rng.integers(0, npos, size=(1, N, K)).astype(np.int32)
+    cw = 2 * math.sqrt(K)
+    g, rk, cnt = _fallback_run(x, P, idx, np.array([N], np.int32), sw, cw, False)
+    assert cnt[1] > 0
+    Y = O.gather_groups(x[0], P, idx[0])
+    Xo, ro = O.lowrank_groups(Y, sw, cw, eps=1e-8)
+    d = C * P * P
+    for i in range(N):
+        scale = np.linalg.norm(Y[i]) / math.sqrt(d * K)
+        err = g[0, i] - Xo[i]
+        assert np.sqrt(np.mean(err**2)) <= 4e-6 * max(scale, 1e-3), i
+        assert np.abs(err).max() <= 2e-5 * max(np.abs(Y[i]).max(), 1e-3), i
+        assert abs(int(rk[0, i]) - int(ro[i])) <= 1
+
+
+@pytest.mark.parametrize("case", [("fbc1", 30, 30, 6, 10, 24, 0.05),   # complex register path (FP64 size 48)
+                                  ("fbc2", 30, 32, 6, 8, 48, 0.02),    # complex register path, K 48 (FP64 size 96)
+                                  ("fbc3", 30, 30, 8, 6, 16, 0.05)])   # complex shared-memory path (d 128)
+def test_lowrank_fp64_fallback_complex(case):
+    """Complex groups at the sweep cap go to the FP64 fallback as the real 2m x 2K matrix
+    [[A, -B], [B, A]]; its result is the oracle's complex WNNM to FP32 output rounding."""
+    tag, H, W, P, N, K, sw = case
+    x = complex_image(tag, H, W)[None]
+    rng = synth.rng_for(tag + "idx")
+    npos = (H - P + 1) * (W - P + 1)
+    idx = rng.integers(0, npos, size=(1, N, K)).astype(np.int32)
+    cw = 2 * math.sqrt(K)
+    g, rk, cnt = _fallback_run(x, P, idx, np.array([N], np.int32), sw, cw, True)
+    assert cnt[1] > 0
+    Y = O.gather_groups(x[0], P, idx[0])
+    Xo, ro = MO.lowrank_groups_complex(Y, sw, cw, eps=1e-8)
+    d = 2 * P * P
+    for i in range(N):
+        scale = np.linalg.norm(Y[i]) / math.sqrt(d * K)
+        err = g[0, i] - Xo[i]
+        assert np.sqrt(np.mean(err**2)) <= 4e-6 * max(scale, 1e-3), i
+        assert np.abs(err).max() <= 2e-5 * max(np.abs(Y[i]).max(), 1e-3), i
+        assert abs(int(rk[0, i]) - int(ro[i])) <= 1
