@@ -87,6 +87,75 @@ def oracle_sample(n_keys: int = 24) -> dict:
     }
 
 
+def psnr_framewise(a, b, peak: float = 1.0) -> float:
+    """Mean over frames of the per-frame PSNR (result bookkeeping)."""
+    import numpy as np
+
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    vals = []
+    for i in range(a.shape[0]):
+        mse = float(np.mean((a[i] - b[i]) ** 2))
+        vals.append(float("inf") if mse == 0 else 10.0 * math.log10(peak * peak / mse))
+    return float(np.mean(vals))
+
+
+def oracle_check(path: str) -> dict:
+    """Per-result error of the GPU path against the FP64 oracle on one frame of the timed workload
+    (part of the CPU-baseline leg; runs in a child process).  The GPU's outputs of one GLR step on
+    the frame are compared step by step with the oracle fed the same inputs: key selection, the
+    matches of a sample of keys, the WNNM estimates of those keys' groups, and the aggregation."""
+    import numpy as np
+
+    from oracle import glr_oracle as O
+
+    z = np.load(path)
+    x = z["x"].astype(np.float64)  # [C][H][W]
+    P, K, N = int(z["P"]), int(z["K"]), int(z["N"])
+    sw, cw, th = float(z["sw"]), float(z["cw"]), float(z["th"])
+    keys_g, idx_g, dist_g, grp_g, v_g = z["keys"], z["idx"], z["dist"], z["groups"], z["v"]
+    out = {}
+    keys_o, _ = O.select_keys(x, P, N, th)
+    out["key_selection_equal_frac"] = round(float(np.mean(keys_o == keys_g)), 6)
+    Q = O.patch_matrix(x, P)
+    sample = np.linspace(0, N - 1, 32).astype(int)
+    exact = sep = 0
+    dist_err = 0.0
+    for i in sample:
+        d_all = O.all_distances(x, P, keys_g[i], Q)
+        order = np.lexsort((np.arange(len(d_all)), d_all))
+        ds = d_all[order]
+        dist_err = max(dist_err, float(np.max(np.abs(dist_g[i] - d_all[idx_g[i]]) / np.maximum(d_all[idx_g[i]], 1e-6))))
+        for j in range(K):
+            lo = ds[j] - ds[j - 1] if j > 0 else np.inf
+            hi = ds[j + 1] - ds[j] if j + 1 < len(ds) else np.inf
+            if lo > 1e-4 and hi > 1e-4:
+                sep += 1
+                exact += int(idx_g[i, j] == order[j])
+    out["match_ids_exact_where_separated"] = f"{exact}/{sep}"
+    out["match_dist_max_rel_err"] = float(f"{dist_err:.3g}")
+    Y = O.gather_groups(x, P, idx_g[sample], Q)
+    Xo, _ = O.lowrank_groups(Y, sw, cw, eps=1e-8)
+    err = grp_g[sample].astype(np.float64) - Xo
+    out["wnnm_max_abs_err_rel"] = float(f"{np.abs(err).max() / max(np.abs(Y).max(), 1e-12):.3g}")
+    out["wnnm_rms_err_rel"] = float(f"{np.sqrt(np.mean(err ** 2)) / max(np.sqrt(np.mean(Y ** 2)), 1e-12):.3g}")
+    vo = O.aggregate(grp_g.astype(np.float64), idx_g, x, P)
+    out["aggregate_max_abs_err"] = float(f"{np.abs(v_g - vo).max():.3g}")
+    out["sample"] = f"frame 0 after the timed iterations: all {N} keys selected, {len(sample)} keys matched and shrunk, all groups aggregated"
+    return out
+
+
+def run_oracle_check(path: str) -> dict:
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    code = f"import json,sys; sys.path.insert(0,{ROOT!r}); import bench; print(json.dumps(bench.oracle_check({path!r})))"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle check failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def _oracle_cmd(n_keys: int, fn: str):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
@@ -393,7 +462,6 @@ def run_glr(args) -> None:
     import __graft_entry__
 
     __graft_entry__.build()
-    from oracle import glr_oracle as O  # only for PSNR bookkeeping of the result (no compute on the path)
     from paper_2301_03047_gb300 import glr, synth
 
     cfg = workload(args.workload)
@@ -470,8 +538,10 @@ def run_glr(args) -> None:
             stream_stats = {"appends_per_key": round(mcnt[4] / (cfg.T * cfg.N), 1),
                             "compactions_per_key": round(mcnt[5] / (cfg.T * cfg.N), 2)}
         x = rec.x.cpu().numpy()[0]
+        if headline:
+            x_final = torch.from_numpy(x)
         results[form] = {"total_s": total_s, "ms_per_step": total_s / args.steps * 1e3, "step_ms": step_ms,
-                         "psnr": O.psnr_framewise(x, prob.truth), "iters": k}
+                         "psnr": psnr_framewise(x, prob.truth), "iters": k}
         if headline and not args.no_graph:
             # the same noise levels as the eager timing, replayed from CUDA graphs (one per level)
             rec.capture(sched, cfg.c_wnnm)
@@ -533,6 +603,24 @@ def run_glr(args) -> None:
                "d2h_bytes_per_step": int(x_h.numel() * 4), "via": "graph replay" if use_graph else "eager"}
         del rec
 
+    # one GLR step of the chosen form on frame 0 of the final state, saved for the oracle check
+    oracle_inputs = None
+    if rank == 0 and not args.no_cpu:
+        import numpy as np
+
+        x1 = x_final[0:1].reshape(1, 1, cfg.H, cfg.W).contiguous().to(dev)
+        sw_c = sched[len(sched) // 2]
+        k1, n1, _ = glr.select_keys(x1, cfg.P, cfg.N, cfg.edge_th)
+        i1, d1 = glr.match_topk(x1, cfg.P, k1, n1, cfg.K, forms[0], **tuned[forms[0]])
+        g1, _ = glr.lowrank_groups(x1, cfg.P, i1, n1, sw_c, cfg.c_wnnm)
+        v1 = glr.aggregate(g1, i1, n1, x1, cfg.P)
+        torch.cuda.synchronize()
+        fd, oracle_inputs = tempfile.mkstemp(suffix=".npz")
+        os.close(fd)
+        np.savez(oracle_inputs, x=x1.cpu().numpy()[0], keys=k1.cpu().numpy()[0], idx=i1.cpu().numpy()[0],
+                 dist=d1.cpu().numpy()[0], groups=g1.cpu().numpy()[0], v=v1.cpu().numpy()[0], P=cfg.P, K=cfg.K,
+                 N=cfg.N, sw=sw_c, cw=cfg.c_wnnm, th=cfg.edge_th)
+        del x1, k1, n1, i1, d1, g1, v1
     if rank != 0:
         return
     cpu = None
@@ -541,6 +629,12 @@ def run_glr(args) -> None:
             cpu = cpu_baseline_entry(args.oracle_keys, "oracle_sample")
         except Exception as e:  # the CPU baseline must not hide the GPU result
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
+        if oracle_inputs is not None:
+            try:
+                cpu["oracle_error"] = run_oracle_check(oracle_inputs)
+            except Exception as e:
+                cpu["oracle_error"] = {"failed": str(e)[-300:]}
+            os.unlink(oracle_inputs)
     rl = roofline(prof, cfg, sweeps, clocks_summary or {}, pk) if prof else None
     kernels = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])} if prof else {}
     line = {
@@ -1017,7 +1111,6 @@ def run_ablation(args) -> None:
     import __graft_entry__
 
     __graft_entry__.build()
-    from oracle import glr_oracle as O  # PSNR bookkeeping only
     from paper_2301_03047_gb300 import glr, synth
 
     cfg = workload(args.workload)
@@ -1050,7 +1143,7 @@ def run_ablation(args) -> None:
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / len(sched)
         out[name] = {"iter_per_s": round(1e3 / ms, 3), "ms_per_iter": round(ms, 3),
-                     "psnr_db": round(O.psnr_framewise(rec.x.cpu().numpy()[0], prob.truth), 3),
+                     "psnr_db": round(psnr_framewise(rec.x.cpu().numpy()[0], prob.truth), 3),
                      "recall_of_global_topk": round(hits / (cfg.T * cfg.N * cfg.K), 4), "n_uniform": nu}
         del rec
         torch.cuda.empty_cache()
