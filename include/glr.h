@@ -71,6 +71,28 @@ typedef struct glr_images {
   int32_t P;     /* patch side; 1 <= P <= min(H, W) */
 } glr_images;
 
+/*
+ * A batch of images of different sizes (an uneven batch, e.g. multispectral
+ * images of several sides, Section 3 MSFA), stored back to back: image i holds
+ * C * H[i] * W[i] values of x from d_pix_off[i], its N[i] keys (and the N[i]
+ * rows of idx / dist) from d_key_off[i].  C and P are common to all images;
+ * images of the same size must have the same N.  The host arrays plan the call;
+ * the device arrays (which must hold the same values) are what the kernels read,
+ * so a call can be captured into a CUDA graph.
+ */
+typedef struct glr_batch {
+  int32_t n_img;            /* number of images */
+  int32_t C;                /* channels per image */
+  int32_t P;                /* patch side */
+  const int32_t* H;         /* host [n_img]: image heights */
+  const int32_t* W;         /* host [n_img]: image widths */
+  const int32_t* N;         /* host [n_img]: keys per image */
+  const int32_t* d_H;       /* device mirror of H */
+  const int32_t* d_W;       /* device mirror of W */
+  const int64_t* d_pix_off; /* device [n_img]: first value of image i in x */
+  const int64_t* d_key_off; /* device [n_img]: first key of image i in keys (first row of idx / dist) */
+} glr_batch;
+
 /* Contraction used by glr_match_topk. */
 enum {
   GLR_MATCH_FP32 = 0,   /* plain form: FP32 FMA on the CUDA cores */
@@ -190,6 +212,30 @@ glr_status glr_match_topk(const float* x, const glr_images* im, const int32_t* k
                           const int32_t* n_found, int32_t N, int32_t K,
                           const glr_match_opts* opts, int32_t* idx, float* dist, void* ws,
                           size_t ws_bytes, void* stream);
+
+/*
+ * glr_match_topk for an uneven batch (the batching pattern of the project):
+ * the same matches per image as glr_match_topk in GLR_MATCH_BF16 mode (K'
+ * candidates by the BF16 tensor-core score, exact FP32 re-rank), computed by
+ * ONE launch of a persistent tensor-core kernel that claims work items --
+ * (image, key tile of 128 keys, position split) over every image of the
+ * batch, largest images first -- from a counter until the queue is empty, so
+ * the SMs stay busy across image sizes.  The preparation (image means, BF16
+ * operands) and the exact re-rank run per size class.
+ *   x       float32, the images back to back (see glr_batch).
+ *   keys    int32, image i's N[i] position ids from d_key_off[i].
+ *   n_found int32 [n_img]: valid keys per image (<= N[i]).
+ *   idx, dist: out, rows d_key_off[i] .. + N[i] - 1 of [sum N][K].
+ *   opts    NULL or mode GLR_MATCH_BF16 (GLR_ENOTSUP otherwise); k_over,
+ *           splits (the same for every image), cap and epi_batch as for
+ *           glr_match_topk.
+ * Limits: at most 8 different image sizes, d = C P^2 <= 640, K <= 128.
+ * Workspace: glr_workspace_size_batch(b, K, opts) bytes (0: invalid).
+ */
+size_t glr_workspace_size_batch(const glr_batch* b, int32_t K, const glr_match_opts* opts);
+glr_status glr_match_topk_batch(const float* x, const glr_batch* b, const int32_t* keys, const int32_t* n_found,
+                                int32_t K, const glr_match_opts* opts, int32_t* idx, float* dist, void* ws,
+                                size_t ws_bytes, void* stream);
 
 /*
  * Learned matching proposal (the project's learned-proposal pattern; the

@@ -30,8 +30,16 @@ class GlrMatchOpts(ctypes.Structure):
                 ("epi_batch", c_int32), ("edge_th", c_float), ("window", c_int32), ("bound_pass", c_int32)]
 
 
+class GlrBatch(ctypes.Structure):
+    _fields_ = [("n_img", c_int32), ("C", c_int32), ("P", c_int32), ("H", c_void_p), ("W", c_void_p), ("N", c_void_p),
+                ("d_H", c_void_p), ("d_W", c_void_p), ("d_pix_off", c_void_p), ("d_key_off", c_void_p)]
+
+
 # name -> (restype, argtypes); every symbol declared in include/glr.h
 PROTOTYPES = {
+    "glr_workspace_size_batch": (c_size_t, [ctypes.POINTER(GlrBatch), c_int32, ctypes.POINTER(GlrMatchOpts)]),
+    "glr_match_topk_batch": (c_int32, [c_void_p, ctypes.POINTER(GlrBatch), c_void_p, c_void_p, c_int32,
+                                       ctypes.POINTER(GlrMatchOpts), c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_workspace_size": (c_size_t, [c_int32, ctypes.POINTER(GlrImages), c_int32, c_int32, ctypes.POINTER(GlrMatchOpts)]),
     "glr_select_keys": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_float, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_select_keys_mixed": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_float, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

@@ -64,6 +64,25 @@ __host__ __device__ inline float float_from_order_key(uint32_t k) {
 __device__ inline void status_set(StatusBlock* st, uint32_t bit) { atomicOr(&st->bits, bit); }
 #endif
 
+// Images of an uneven batch seen by a kernel written for a uniform batch: the kernel's image f
+// is image map[f] of the caller's batch, whose pixels start pix_off[] floats into x and whose
+// keys (and rows of idx / dist) start key_off[] keys into keys.  map == nullptr: the uniform
+// layout (image f at f C H W, keys at f N).
+struct ImgMap {
+  const int32_t* map = nullptr;
+  const int64_t* pix_off = nullptr;
+  const int64_t* key_off = nullptr;
+#ifdef __CUDACC__
+  __device__ __forceinline__ int id(int f) const { return map ? map[f] : f; }
+  __device__ __forceinline__ long long pix(int f, long long per_img) const {
+    return map ? (long long)pix_off[map[f]] : (long long)f * per_img;
+  }
+  __device__ __forceinline__ long long key(int f, long long N) const {
+    return map ? (long long)key_off[map[f]] : (long long)f * N;
+  }
+#endif
+};
+
 // host: launch counting and optional per-kernel event timing (glr_api.cu)
 void note_launch(int n = 1);
 // host: streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, cached)

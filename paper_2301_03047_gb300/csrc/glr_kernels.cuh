@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cuda_bf16.h>
+
 #include "glr_common.cuh"
 
 namespace glr {
@@ -65,10 +67,37 @@ glr_status launch_encode_vectors(const float* vecs, long long n, int d, const fl
                                  cudaStream_t s);
 // image means: part = scratch of n_img x kMeanMaxSlices doubles
 constexpr int kMeanMaxSlices = 256;
-glr_status launch_image_mean(const float* x, const glr_images& im, float* mean, double* part, cudaStream_t s);
+glr_status launch_image_mean(const float* x, const glr_images& im, float* mean, double* part, cudaStream_t s,
+                             ImgMap imap = ImgMap{});
 glr_status launch_encoder_train(const float* x, const glr_images& im, const float* mean, const int32_t* pairs,
                                 int n_pairs, float* params, float* m, float* v, int step, float lr, float wd,
                                 float* grad, float* loss, cudaStream_t s);
+
+// ---- uneven batches (glr_batch.cu)
+struct QClassHost {  // one size class of the persistent scorer's work queue
+  int n_img, Npad, N, ntiles, tps, img0;
+  long long npos, npos_pad, krow0, qrow0, item0;
+};
+struct QBatchHost {
+  int n_classes, splits;
+  long long n_items;
+  QClassHost c[8];
+};
+glr_status launch_pack_class_w(const float* x, const float* mean, const glr_images& im, long long npos_pad, int nkc,
+                               const float* keyv, int Npad, __nv_bfloat16* qmain, __nv_bfloat16* qaux,
+                               __nv_bfloat16* kmain, __nv_bfloat16* kaux, ImgMap imap, cudaStream_t s);
+glr_status launch_match_tc_queue(const QBatchHost& hb, const int32_t* img_map, const int32_t* n_found, int nkc,
+                                 int cap, int Kp, int finish, int epi_batch, __nv_bfloat16* qmain,
+                                 __nv_bfloat16* qaux, __nv_bfloat16* kmain, __nv_bfloat16* kaux, long long qrows,
+                                 long long krows, uint2* bufs, int* bufcnt, uint32_t* taugl, unsigned* queue,
+                                 StatusBlock* st, cudaStream_t s);
+glr_status launch_key_vectors(const float* x, const float* mean, const int32_t* keys, const int32_t* n_found,
+                              const glr_images& im, int N, int Npad, float* keyv, StatusBlock* st, ImgMap imap,
+                              cudaStream_t s);
+glr_status launch_rerank_streams(const float* x, const int32_t* keys, const int32_t* n_found, const glr_images& im,
+                                 int N, int Npad, int K, int streams_per_key, int cap, int Kp, int finish,
+                                 const uint2* bufs, const int* bufcnt, int32_t* idx, float* dist, ImgMap imap,
+                                 cudaStream_t s);
 
 // testing aid: when set, the tensor-core scorer also writes the raw scores of the
 // first position tile, [n_img][Npad][256] float32, to this device buffer

@@ -26,11 +26,11 @@ namespace {
 // the S partial sums in slice order, so the result does not depend on scheduling.
 // S depends only on the shape (about two CTAs per SM over the batch).
 __global__ void __launch_bounds__(512)
-    k_image_mean_part(const float* __restrict__ x, long long n_per_img, int S, double* __restrict__ part) {
+    k_image_mean_part(const float* __restrict__ x, long long n_per_img, int S, double* __restrict__ part, ImgMap imap) {
   __shared__ double red[16];
   const long long f = blockIdx.x / S;
   const int sl = (int)(blockIdx.x - f * S);
-  const float* xf = x + f * n_per_img;
+  const float* xf = x + imap.pix((int)f, n_per_img);
   const long long per = (n_per_img + S - 1) / S;
   const long long lo = min(n_per_img, per * sl), hi = min(n_per_img, lo + per);
   double s = 0.0;
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) k_key_vectors(const float* __restrict__ x
                                                      const int32_t* __restrict__ keys,
                                                      const int32_t* __restrict__ n_found, int n_img, int C, int H,
                                                      int W, int P, int N, int Npad, float* __restrict__ keyv,
-                                                     StatusBlock* st) {
+                                                     StatusBlock* st, ImgMap imap) {
   const int d = C * P * P;
   const int Wq = W - P + 1;
   const long long total = (long long)n_img * Npad * d;
@@ -106,13 +106,13 @@ __global__ void __launch_bounds__(256) k_key_vectors(const float* __restrict__ x
     const int e = (int)(i - fk * d);
     const int f = (int)(fk / Npad), k = (int)(fk - (long long)f * Npad);
     float v = 0.f;
-    const int q = k < min(n_found[f], N) ? keys[(long long)f * N + k] : -1;
+    const int q = k < min(n_found[imap.id(f)], N) ? keys[imap.key(f, N) + k] : -1;
     if ((unsigned)q >= (unsigned)(Wq * (H - P + 1))) {
       if (q != -1 && e == 0) status_set(st, GLR_DEV_BAD_INDEX);
     } else {
       const int r = q / Wq, c = q - (q / Wq) * Wq;
       const int ch = e / (P * P), dr = (e / P) % P, dc = e % P;
-      v = __ldg(x + (((long long)f * C + ch) * H + r + dr) * W + c + dc) - mean[f];
+      v = __ldg(x + imap.pix(f, (long long)C * H * W) + ((long long)ch * H + r + dr) * W + c + dc) - mean[f];
     }
     keyv[i] = v;
   }
@@ -393,7 +393,8 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
     k_rerank(const float* __restrict__ x, const int32_t* __restrict__ keys, const int32_t* __restrict__ n_found,
              int n_img, int C, int H, int W, int P, int N, int Npad, int K, int streams_per_key, int cap_slots,
              int kp, int pow2, const uint2* __restrict__ bufs, const int* __restrict__ buf_cnt,
-             int exact_scores, float dist_scale, int window, int32_t* __restrict__ idx, float* __restrict__ dist) {
+             int exact_scores, float dist_scale, int window, int32_t* __restrict__ idx, float* __restrict__ dist,
+             ImgMap imap) {
   // window > 0: the candidates are every position within `window` rows and columns
   // of the key (block matching in a local window) instead of the stream buffers
   // exact_scores != 0: the stream scores are already exact (the heat map of Eq. 4 on
@@ -408,13 +409,15 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
   const long long nkeys = (long long)n_img * N;
   for (long long gk = blockIdx.x * (long long)RR_WARPS + wid; gk < nkeys; gk += (long long)gridDim.x * RR_WARPS) {
     const int f = (int)(gk / N), k = (int)(gk - (long long)f * N);
-    if (k >= min(n_found[f], N)) continue;
-    const int kq = keys[gk];
+    if (k >= min(n_found[imap.id(f)], N)) continue;
+    const long long krow = imap.key(f, N) + k;  // row of this key in keys, idx and dist
+    const float* xf = x + imap.pix(f, (long long)C * H * W);
+    const int kq = keys[krow];
     if ((unsigned)kq >= (unsigned)(Wq * (H - P + 1))) continue;  // flagged by k_key_vectors
     const int kr = kq / Wq, kc = kq - (kq / Wq) * Wq;
     for (int e = lane; !exact_scores && e < d; e += 32) {
       const int ch = e / (P * P), dr = (e / P) % P, dc = e % P;
-      pv[e] = __ldg(x + (((long long)f * C + ch) * H + kr + dr) * W + kc + dc);
+      pv[e] = __ldg(xf + ((long long)ch * H + kr + dr) * W + kc + dc);
     }
     // gather candidate ids
     int total = 0;
@@ -448,7 +451,7 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
       float acc = 0.f;
       for (int ch = 0; ch < C; ++ch)
         for (int dr = 0; dr < P; ++dr) {
-          const float* rowp = x + (((long long)f * C + ch) * H + r + dr) * W + c;
+          const float* rowp = xf + ((long long)ch * H + r + dr) * W + c;
           const float* pp = pv + (ch * P + dr) * P;
           for (int dc = 0; dc < P; ++dc) {
             const float df = pp[dc] - __ldg(rowp + dc);
@@ -483,8 +486,8 @@ __global__ void __launch_bounds__(RR_WARPS * 32)
     }
     for (int i = lane; i < K; i += 32) {
       const unsigned long long e = list[i];
-      if (idx) idx[gk * K + i] = (int32_t)(e & 0xffffffffu);
-      if (dist) dist[gk * K + i] = dist_scale * float_from_order_key((uint32_t)(e >> 32));
+      if (idx) idx[krow * K + i] = (int32_t)(e & 0xffffffffu);
+      if (dist) dist[krow * K + i] = dist_scale * float_from_order_key((uint32_t)(e >> 32));
     }
     __syncwarp();
   }
@@ -911,12 +914,45 @@ int image_mean_slices(const glr_images& im) {
   return (int)std::max<long long>(1, std::min<long long>(S, kMeanMaxSlices));
 }
 
-glr_status launch_image_mean(const float* x, const glr_images& im, float* mean, double* part, cudaStream_t s) {
+glr_status launch_image_mean(const float* x, const glr_images& im, float* mean, double* part, cudaStream_t s,
+                             ImgMap imap) {
   const long long n = (long long)im.C * im.H * im.W;
   const int S = image_mean_slices(im);
-  GLR_LAUNCH("k_image_mean", s, k_image_mean_part<<<(unsigned)(im.n_img * S), 512, 0, s>>>(x, n, S, part));
+  GLR_LAUNCH("k_image_mean", s, k_image_mean_part<<<(unsigned)(im.n_img * S), 512, 0, s>>>(x, n, S, part, imap));
   GLR_LAUNCH("k_image_mean_final", s,
              k_image_mean_final<<<(unsigned)ceil_div(im.n_img, 128), 128, 0, s>>>(part, im.n_img, S, n, mean));
+  return GLR_OK;
+}
+
+glr_status launch_key_vectors(const float* x, const float* mean, const int32_t* keys, const int32_t* n_found,
+                              const glr_images& im, int N, int Npad, float* keyv, StatusBlock* st, ImgMap imap,
+                              cudaStream_t s) {
+  const int d = im.C * im.P * im.P;
+  const long long total = (long long)im.n_img * Npad * d;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)num_sms() * 32));
+  GLR_LAUNCH("k_key_vectors", s, k_key_vectors<<<blocks, 256, 0, s>>>(x, mean, keys, n_found, im.n_img, im.C, im.H,
+                                                                       im.W, im.P, N, Npad, keyv, st, imap));
+  return GLR_OK;
+}
+
+glr_status launch_rerank_streams(const float* x, const int32_t* keys, const int32_t* n_found, const glr_images& im,
+                                 int N, int Npad, int K, int streams_per_key, int cap, int Kp, int finish,
+                                 const uint2* bufs, const int* bufcnt, int32_t* idx, float* dist, ImgMap imap,
+                                 cudaStream_t s) {
+  const int d = im.C * im.P * im.P;
+  int pow2 = 32;
+  while (pow2 < streams_per_key * (finish ? Kp : cap + 32)) pow2 <<= 1;
+  const int dpad = (d + 31) & ~31;
+  const size_t smem = (size_t)RR_WARPS * pow2 * 8 + (size_t)RR_WARPS * (dpad + 256) * 4;
+  if (smem > 227 * 1024 || d > 640) return GLR_ENOTSUP;
+  if (cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GLR_ECUDA;
+  const long long nkeys = (long long)im.n_img * N;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, RR_WARPS), (long long)num_sms() * 16));
+  GLR_LAUNCH("k_rerank", s, k_rerank<<<blocks, RR_WARPS * 32, smem, s>>>(x, keys, n_found, im.n_img, im.C, im.H, im.W,
+                                                                          im.P, N, Npad, K, streams_per_key, cap + 32,
+                                                                          Kp, pow2, bufs, bufcnt, 0, 1.f, 0, idx, dist,
+                                                                          imap));
   return GLR_OK;
 }
 
@@ -1066,7 +1102,8 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     const long long nkeys = (long long)im.n_img * N;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, RR_WARPS), (long long)num_sms() * 16));
     GLR_LAUNCH("k_rerank", s, k_rerank<<<blocks, RR_WARPS * 32, smem, s>>>(x, keys, n_found, im.n_img, im.C, im.H, im.W, im.P, N, pl.Npad,
-                                                 pl.K, 0, 0, 0, pow2, nullptr, nullptr, 0, 1.f, pl.window, idx, dist));
+                                                 pl.K, 0, 0, 0, pow2, nullptr, nullptr, 0, 1.f, pl.window, idx, dist,
+                                                 ImgMap{}));
     return GLR_OK;
   }
   // GLR_MATCH_EDGE: every later step sees the 4 C binary edge planes as the image
@@ -1103,7 +1140,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     const long long total = (long long)im.n_img * pl.Npad * d;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)num_sms() * 32));
     GLR_LAUNCH("k_key_vectors", s, k_key_vectors<<<blocks, 256, 0, s>>>(xs, mean, keys, n_found, im.n_img, ime.C, im.H, im.W, im.P, N, pl.Npad,
-                                        keyv, reinterpret_cast<StatusBlock*>(ws)));
+                                        keyv, reinterpret_cast<StatusBlock*>(ws), ImgMap{}));
   }
   StreamCfg cfg{pl.cap, pl.Kp, pl.finish};
   if (pl.mode == GLR_MATCH_LEARNED) {
@@ -1165,7 +1202,7 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, RR_WARPS), (long long)num_sms() * 16));
     GLR_LAUNCH("k_rerank", s, k_rerank<<<blocks, RR_WARPS * 32, smem, s>>>(x, keys, n_found, im.n_img, im.C, im.H, im.W, im.P, N, pl.Npad,
                                                  pl.K, pl.streams_per_key, pl.cap + 32, pl.Kp, pow2, bufs, bufcnt,
-                                                 edge ? 1 : 0, edge ? -0.5f : 1.f, 0, idx, dist));
+                                                 edge ? 1 : 0, edge ? -0.5f : 1.f, 0, idx, dist, ImgMap{}));
   }
   return GLR_OK;
 }

@@ -334,7 +334,7 @@ template <int PT>  // P at compile time (0: runtime): unrolled patch loops
 __global__ void __launch_bounds__(256) k_pack_positions_w(const float* __restrict__ x, const float* __restrict__ mean,
                                                           int n_img, int C, int H, int W, int P_, long long npos_pad,
                                                           int nkc, int raw, __nv_bfloat16* __restrict__ qmain,
-                                                          __nv_bfloat16* __restrict__ qaux) {
+                                                          __nv_bfloat16* __restrict__ qaux, ImgMap imap) {
   const int P = PT ? PT : P_;
   extern __shared__ __align__(16) uint8_t pw_smem[];
   const int rowlen = nkc * DK_MAIN;  // bf16 per row
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(256) k_pack_positions_w(const float* __restric
     const bool valid = q < npos;
     const int r = valid ? (int)(q / Wq) : 0, c = valid ? (int)(q - (q / Wq) * Wq) : 0;
     for (int ch = wid; ch < C; ch += nw) {
-      const float* xc = x + ((long long)f * C + ch) * H * W;
+      const float* xc = x + imap.pix((int)f, (long long)C * H * W) + (long long)ch * H * W;
       float nrm = 0.f;
       const float* xp = xc + (long long)r * W + c;
 #pragma unroll
@@ -959,6 +959,250 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
+// One size class of an uneven batch in the persistent scorer.  Its images are contiguous in
+// the flat packed operands (key rows from krow0, position rows from qrow0) and in the image map.
+constexpr int kMaxClasses = 8;
+struct QClass {
+  int n_img;       // images of the class
+  int Npad;        // key rows per image (keys padded to 128)
+  int N;           // keys per image
+  int ntiles;      // position tiles per image
+  int tps;         // position tiles per split
+  int img0;        // first entry of the class in the image map
+  long long npos;  // valid positions per image
+  long long npos_pad;
+  long long krow0, qrow0;
+  long long item0;  // first work item of the class
+};
+struct QBatch {
+  int n_classes;
+  int splits;
+  long long n_items;
+  QClass c[kMaxClasses];
+};
+
+// Persistent candidate scan over an uneven batch (chunked operand rows).  One CTA per SM claims
+// work items -- (class, image, key tile, position split) -- from a counter until the queue is
+// empty; an item is the scan of one CTA of the uniform kernel (k_match_tc<EB, true, 0>): the same
+// producer / MMA / epilogue roles, the operand ring and TMEM buffers continuing from item to item
+// (their phases run on), the streams of the item's keys initialised at its start and closed at
+// its end.  Between items the CTA synchronises: by then every copy and MMA of the item has been
+// consumed.  The waits are bounded as in the uniform kernel.
+template <int EB>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_match_tc_queue(const __grid_constant__ CUtensorMap tm_qmain, const __grid_constant__ CUtensorMap tm_qaux,
+                     const __grid_constant__ CUtensorMap tm_kmain, const __grid_constant__ CUtensorMap tm_kaux,
+                     const __grid_constant__ QBatch qb, const int32_t* __restrict__ img_map,
+                     const int32_t* __restrict__ n_found, int nkc, StreamCfg cfg, uint2* __restrict__ bufs,
+                     int* __restrict__ buf_cnt, uint32_t* __restrict__ tau_gl, unsigned* __restrict__ queue,
+                     StatusBlock* st) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr int NST = W_STAGES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + W_OFF_BAR);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + TC_STAGES;
+  uint64_t* tfull = bars + 2 * TC_STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* mma_done = tempty + 3;
+  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(smem + W_OFF_MISC);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(smem + W_OFF_MISC + 4);
+  volatile long long* item_s = reinterpret_cast<volatile long long*>(smem + W_OFF_MISC + 8);
+  unsigned* hist = reinterpret_cast<unsigned*>(smem + W_OFF_HIST);
+  uint32_t* tau_sh = reinterpret_cast<uint32_t*>(smem + W_OFF_TAU);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int splits = qb.splits;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);
+      mbar_init(tempty + b, TC_EPI_WARPS);
+    }
+    mbar_init(mma_done, 1);
+    *abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_base_s, 512);
+    tmem_relinquish();
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_base_s;
+  int it_ring = 0;  // operand ring slots used so far (producer and MMA count alike)
+  int it_tile = 0;  // position tiles scored so far (TMEM buffer and phase)
+  for (;;) {
+    if (threadIdx.x == 0) *item_s = (long long)atomicAdd(queue, 1u);
+    if (threadIdx.x < TC_M) tau_sh[threadIdx.x] = 0xffffffffu;
+    __syncthreads();
+    const long long item = *item_s;
+    const bool stop = item >= qb.n_items || *abort_s;
+    __syncthreads();  // every thread has read the item before thread 0 claims the next one
+    if (stop) break;
+    // decode: class, image, key tile, split
+    int c = 0;
+    while (c + 1 < qb.n_classes && item >= qb.c[c + 1].item0) ++c;
+    const QClass& qc = qb.c[c];
+    const long long local = item - qc.item0;
+    const int ktiles = qc.Npad / TC_M;
+    const int f = (int)(local / ((long long)ktiles * splits));
+    const int rem = (int)(local - (long long)f * ktiles * splits);
+    const int kt = rem / splits, split = rem - (rem / splits) * splits;
+    const int t_begin = split * qc.tps;
+    const int t_end = min(qc.ntiles, t_begin + qc.tps);
+    const int nt = max(0, t_end - t_begin);
+    const long long krow = qc.krow0 + (long long)f * qc.Npad;  // first key row of the image
+    const long long qrow = qc.qrow0 + (long long)f * qc.npos_pad;
+    if (warp == 0) {
+      if (lane == 0) {
+        // ---------------------------------------------------------- producer
+        const int arow = (int)(krow + (long long)kt * TC_M);
+        bool ok = true;
+        for (int i = 0; ok && i < nt; ++i) {
+          const int brow = (int)(qrow + (long long)(t_begin + i) * TC_N);
+          for (int kc = 0; kc <= nkc; ++kc) {
+            const int s = it_ring % NST;
+            const uint32_t ph = (uint32_t)(it_ring / NST) & 1u;
+            if (!mbar_wait(empty + s, ph ^ 1u, abort_s, st, true, cfg.wait_ns)) {
+              ok = false;
+              break;
+            }
+            uint8_t* sa = smem + s * W_STAGE_BYTES;
+            uint8_t* sb = sa + A_MAIN_BYTES;
+            if (kc < nkc) {
+              mbar_arrive_expect_tx(full + s, A_MAIN_BYTES + B_MAIN_BYTES);
+              tma_load_2d(&tm_kmain, full + s, sa, DK_MAIN * kc, arow);
+              tma_load_2d(&tm_qmain, full + s, sb, DK_MAIN * kc, brow);
+            } else {
+              mbar_arrive_expect_tx(full + s, A_AUX_BYTES + B_AUX_BYTES);
+              tma_load_2d(&tm_kaux, full + s, sa, 0, arow);
+              tma_load_2d(&tm_qaux, full + s, sb, 0, brow);
+            }
+            ++it_ring;
+          }
+        }
+        if (!ok) {
+          // teardown after an expired wait: every issued copy lands before the CTA may exit
+          for (int j = max(0, it_ring - NST); j < it_ring; ++j)
+            mbar_wait(full + (j % NST), (uint32_t)(j / NST) & 1u, abort_s, st, false);
+        }
+      }
+    } else if (warp == 1) {
+      if (lane == 0) {
+        // --------------------------------------------------------- MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(TC_M, TC_N);
+        bool ok = true;
+        for (int i = 0; ok && i < nt; ++i) {
+          const int b = it_tile & 1;
+          const uint32_t bph = (uint32_t)(it_tile >> 1) & 1u;
+          if (!mbar_wait(tempty + b, bph ^ 1u, abort_s, st, true, cfg.wait_ns)) break;
+          const uint32_t d_tmem = tmem_base + (uint32_t)(b * TC_N);
+          for (int kc = 0; kc <= nkc; ++kc) {
+            const int s = it_ring % NST;
+            const uint32_t ph = (uint32_t)(it_ring / NST) & 1u;
+            if (!mbar_wait(full + s, ph, abort_s, st, true, cfg.wait_ns)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * W_STAGE_BYTES);
+            const uint32_t sb = sa + A_MAIN_BYTES;
+            if (kc < nkc) {
+#pragma unroll
+              for (int k = 0; k < DK_MAIN / 16; ++k)
+                mma_bf16(d_tmem, smem_desc(sa + 32 * k, 1024, LAYOUT_SW128), smem_desc(sb + 32 * k, 1024, LAYOUT_SW128),
+                         idesc, (kc > 0 || k > 0) ? 1u : 0u);
+            } else {
+              mma_bf16(d_tmem, smem_desc(sa, 256, LAYOUT_SW32), smem_desc(sb, 256, LAYOUT_SW32), idesc, 1u);
+            }
+            mma_commit(empty + s);
+            ++it_ring;
+          }
+          if (ok) mma_commit(tfull + b);
+          ++it_tile;
+        }
+      }
+      // (it_tile is tracked by the epilogue warps and lane 0 of this warp alike)
+    } else {
+      // ------------------------------------------------------------- epilogue
+      const int e = warp - 2;
+      const int quad = warp & 3;
+      const int h = e >> 2;
+      const int row = 32 * quad + lane;
+      const int key = kt * TC_M + row;  // key of the image
+      const int nf = min(n_found[img_map[qc.img0 + f]], qc.Npad);
+      const long long stream = ((krow + key) * splits + split) * 2 + h;
+      uint2* mybuf = bufs + stream * (cfg.cap + 32);
+      float tau = (key < nf) ? INFINITY : -INFINITY;
+      int cnt = 0;
+      uint2 stats = make_uint2(0u, 0u);
+      unsigned* whist = hist + e * 256;
+      uint32_t* pub_sh = tau_sh + 32 * quad;
+      uint32_t* pub_gl = tau_gl + krow + (long long)kt * TC_M + 32 * quad;
+      uint32_t gl_next = *reinterpret_cast<volatile uint32_t*>(pub_gl + lane);
+      for (int i = 0; i < nt; ++i) {
+        const int b = it_tile & 1;
+        const uint32_t bph = (uint32_t)(it_tile >> 1) & 1u;
+        ++it_tile;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull + b, bph, abort_s, st, true, cfg.wait_ns));
+        if (!ok) break;
+        tc_fence_after();
+        const long long tile_q0 = (long long)(t_begin + i) * TC_N;
+        const uint32_t gl = gl_next;
+        gl_next = *reinterpret_cast<volatile uint32_t*>(pub_gl + lane);
+#pragma unroll 1
+        for (int c0 = 0; c0 < 4; c0 += EB) {
+          float v[EB][32];
+          {
+            const uint32_t taddr =
+                tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128 + 32 * c0);
+#pragma unroll
+            for (int cc = 0; cc < EB; ++cc) tmem_ld_32x32_nowait(taddr + 32 * cc, v[cc]);
+            tmem_ld_wait();
+          }
+          if (c0 + EB >= 4) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty + b);
+          }
+#pragma unroll
+          for (int cc = 0; cc < EB; ++cc) {
+            const int col = h * 128 + (c0 + cc) * 32;
+            const long long q0 = tile_q0 + col;
+            const int nvalid = (int)max(0LL, min(32LL, qc.npos - q0));
+            const float te = stream_tau_eff(tau, *reinterpret_cast<volatile uint32_t*>(pub_sh + lane), gl);
+            const unsigned rows = stream_filter(v[cc], nvalid, te);
+            if (rows)
+              stream_append_regs(rows, v[cc], (int)q0, nvalid, te, tau, cnt, mybuf, cfg, whist, pub_sh, pub_gl, stats);
+          }
+        }
+      }
+      if (cfg.finish) stream_finish(tau, cnt, mybuf, cfg, whist);
+      stream_stats_flush(stats, st);
+      buf_cnt[stream] = (key < nf) ? cnt : 0;
+    }
+    // the MMA warp's lanes other than 0 and the producer warp's keep the tile count in step
+    if ((warp == 0) || (warp == 1 && lane != 0)) it_tile += nt;
+    __syncthreads();
+  }
+  // teardown: all issued MMAs have completed before TMEM is freed
+  if (warp == 1 && lane == 0) {
+    mma_commit(mma_done);
+    mbar_wait(mma_done, 0, abort_s, st, false);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 512);
+  }
+}
+
 // ---------------------------------------------------------------- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -1034,7 +1278,8 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
       return GLR_ECUDA;                                                                                        \
     GLR_LAUNCH("k_pack_positions", s,                                                                          \
                k_pack_positions_w<PP><<<pblocks, 256, psmem, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P,     \
-                                                                  pl.npos_pad, pl.nkc, raw, qmain, qaux));     \
+                                                                  pl.npos_pad, pl.nkc, raw, qmain, qaux,       \
+                                                                  ImgMap{}));                                  \
   }
       switch (im.P) {
         case 6: GLR_PACKW_CASE(6); break;
@@ -1162,6 +1407,76 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
              kern<<<grid, TC_THREADS, TC_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad,
                                                           pl.splits, pl.tiles_per_split, pl.pos_tiles, 1, cfg, bufs,
                                                           bufcnt, taugl, st, dump, nullptr));
+  return GLR_OK;
+}
+
+// ---- uneven batches (glr_batch.cu): packing of one size class into the flat operands, and the
+//      persistent scan over all classes
+glr_status launch_pack_class_w(const float* x, const float* mean, const glr_images& im, long long npos_pad, int nkc,
+                               const float* keyv, int Npad, __nv_bfloat16* qmain, __nv_bfloat16* qaux,
+                               __nv_bfloat16* kmain, __nv_bfloat16* kaux, ImgMap imap, cudaStream_t s) {
+  const int d = im.C * im.P * im.P;
+  {
+    const size_t psmem = (size_t)PW_POS * (nkc * DK_MAIN + 2) * 2 + (size_t)im.C * PW_POS * 4;
+    if (psmem > 227 * 1024) return GLR_ENOTSUP;
+    const long long nblk = (long long)im.n_img * (npos_pad / PW_POS);
+    const int pblocks = (int)std::max<long long>(1, std::min<long long>(nblk, (long long)num_sms() * 16));
+#define GLR_PACKB_CASE(PP)                                                                                     \
+  {                                                                                                            \
+    if (cudaFuncSetAttribute(k_pack_positions_w<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem) != \
+        cudaSuccess)                                                                                           \
+      return GLR_ECUDA;                                                                                        \
+    GLR_LAUNCH("k_pack_positions", s,                                                                          \
+               k_pack_positions_w<PP><<<pblocks, 256, psmem, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P,     \
+                                                                  npos_pad, nkc, 0, qmain, qaux, imap));       \
+  }
+    switch (im.P) {
+      case 6: GLR_PACKB_CASE(6); break;
+      case 8: GLR_PACKB_CASE(8); break;
+      default: GLR_PACKB_CASE(0); break;
+    }
+#undef GLR_PACKB_CASE
+  }
+  const int nk = im.n_img * Npad;
+  const int blocks = (int)std::max<long long>(1, ceil_div(nk, 256));
+  GLR_LAUNCH("k_pack_keys", s, k_pack_keys_w<<<blocks, 256, 0, s>>>(keyv, nk, d, nkc, 0, kmain, kaux));
+  return GLR_OK;
+}
+
+glr_status launch_match_tc_queue(const QBatchHost& hb, const int32_t* img_map, const int32_t* n_found, int nkc,
+                                 int cap, int Kp, int finish, int epi_batch, __nv_bfloat16* qmain,
+                                 __nv_bfloat16* qaux, __nv_bfloat16* kmain, __nv_bfloat16* kaux, long long qrows,
+                                 long long krows, uint2* bufs, int* bufcnt, uint32_t* taugl, unsigned* queue,
+                                 StatusBlock* st, cudaStream_t s) {
+  if (hb.n_classes < 1 || hb.n_classes > kMaxClasses) return GLR_ENOTSUP;
+  QBatch qb{};
+  qb.n_classes = hb.n_classes;
+  qb.splits = hb.splits;
+  qb.n_items = hb.n_items;
+  for (int c = 0; c < hb.n_classes; ++c) {
+    const QClassHost& h = hb.c[c];
+    qb.c[c] = QClass{h.n_img, h.Npad, h.N, h.ntiles, h.tps, h.img0, h.npos, h.npos_pad, h.krow0, h.qrow0, h.item0};
+  }
+  CUtensorMap tq, tqa, tk, tka;
+  const uint32_t wcols = (uint32_t)(nkc * DK_MAIN);
+  if (!make_map(&tq, qmain, (uint64_t)qrows, wcols, TC_N, CU_TENSOR_MAP_SWIZZLE_128B, DK_MAIN) ||
+      !make_map(&tqa, qaux, (uint64_t)qrows, DK_AUX, TC_N, CU_TENSOR_MAP_SWIZZLE_32B) ||
+      !make_map(&tk, kmain, (uint64_t)krows, wcols, TC_M, CU_TENSOR_MAP_SWIZZLE_128B, DK_MAIN) ||
+      !make_map(&tka, kaux, (uint64_t)krows, DK_AUX, TC_M, CU_TENSOR_MAP_SWIZZLE_32B))
+    return GLR_ECUDA;
+  auto kern = epi_batch == 4 ? k_match_tc_queue<4> : k_match_tc_queue<2>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W_SMEM) != cudaSuccess)
+    return GLR_ECUDA;
+  int blocks_per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, TC_THREADS, W_SMEM) != cudaSuccess ||
+      blocks_per_sm != 1)  // all of TMEM: exactly one resident CTA per SM
+    return GLR_ENOTSUP;
+  if (cudaMemsetAsync(queue, 0, sizeof(unsigned), s) != cudaSuccess) return GLR_ECUDA;
+  const StreamCfg cfg{cap, Kp, finish, g_match_wait_ns > 0 ? g_match_wait_ns : kWaitNs};
+  const int grid = (int)std::max<long long>(1, std::min<long long>(hb.n_items, (long long)num_sms()));
+  GLR_LAUNCH("k_match_tc_queue", s,
+             kern<<<grid, TC_THREADS, W_SMEM, s>>>(tq, tqa, tk, tka, qb, img_map, n_found, nkc, cfg, bufs, bufcnt,
+                                                    taugl, queue, st));
   return GLR_OK;
 }
 

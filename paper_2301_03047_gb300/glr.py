@@ -133,6 +133,68 @@ def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, cap=0
     return idx, dist
 
 
+class Batch:
+    """An uneven batch (glr_batch): images of different sizes stored back to back in one flat
+    float32 tensor, keys per image back to back in one int32 tensor.  Holds the host arrays and
+    their device mirrors (keep the object alive while calls that use it run)."""
+
+    def __init__(self, sides, C, P, N, device="cuda"):
+        import numpy as np
+
+        self.sides = [(int(h), int(w)) for h, w in sides]
+        self.C, self.P = int(C), int(P)
+        self.N = [int(n) for n in (N if hasattr(N, "__len__") else [N] * len(self.sides))]
+        n = len(self.sides)
+        self._H = np.array([h for h, _ in self.sides], np.int32)
+        self._W = np.array([w for _, w in self.sides], np.int32)
+        self._N = np.array(self.N, np.int32)
+        pix = np.concatenate([[0], np.cumsum([self.C * h * w for h, w in self.sides])]).astype(np.int64)
+        key = np.concatenate([[0], np.cumsum(self.N)]).astype(np.int64)
+        self.pix_off, self.key_off = pix, key
+        self.d_H = torch.from_numpy(self._H).to(device)
+        self.d_W = torch.from_numpy(self._W).to(device)
+        self.d_pix_off = torch.from_numpy(pix[:n].copy()).to(device)
+        self.d_key_off = torch.from_numpy(key[:n].copy()).to(device)
+        self.c = L.GlrBatch(n, self.C, self.P, self._H.ctypes.data, self._W.ctypes.data, self._N.ctypes.data,
+                            _ptr(self.d_H), _ptr(self.d_W), _ptr(self.d_pix_off), _ptr(self.d_key_off))
+
+    @property
+    def total_pixels(self) -> int:
+        return int(self.pix_off[-1])
+
+    @property
+    def total_keys(self) -> int:
+        return int(self.key_off[-1])
+
+    def image(self, x_flat, i):
+        """View of image i of a flat batch tensor as [C][H][W]."""
+        h, w = self.sides[i]
+        return x_flat[int(self.pix_off[i]):int(self.pix_off[i + 1])].view(self.C, h, w)
+
+
+def match_topk_batch(x_flat, batch: Batch, keys_flat, n_found, K, *, k_over=0, splits=0, cap=0, epi_batch=0,
+                     idx=None, dist=None, ws=None, stream=None):
+    """glr_match_topk_batch: BF16 matching of every image of an uneven batch, one persistent
+    tensor-core launch over all images.  Returns (idx [sum N][K], dist [sum N][K])."""
+    lib = L.load()
+    o = match_opts("bf16", k_over, splits, cap, None, epi_batch)
+    dev = x_flat.device
+    if idx is None:
+        idx = torch.empty((batch.total_keys, K), dtype=torch.int32, device=dev)
+    if dist is None:
+        dist = torch.empty((batch.total_keys, K), dtype=torch.float32, device=dev)
+    if ws is None:
+        n = lib.glr_workspace_size_batch(ctypes.byref(batch.c), int(K), ctypes.byref(o))
+        if n == 0:
+            raise GlrError("glr_workspace_size_batch", L.GLR_EINVAL)
+        ws = torch.empty(int(n) + 256, dtype=torch.uint8, device=dev)
+    wp, wn = _ws(ws)
+    _check("glr_match_topk_batch", lib.glr_match_topk_batch(_ptr(x_flat), ctypes.byref(batch.c), _ptr(keys_flat),
+                                                            _ptr(n_found), int(K), ctypes.byref(o), _ptr(idx),
+                                                            _ptr(dist), wp, wn, _stream(stream)))
+    return idx, dist
+
+
 def debug_wnnm_sweep_cap(cap: int) -> int:
     """Testing aid: sweep cap of the FP32 register Jacobi (<= 0: the default 30); returns the old one.
     Groups that reach the cap are recomputed by the FP64 fallback."""
