@@ -951,8 +951,10 @@ def run_msfa(args, cfg, dev, dist) -> None:
         t = tuple(sched_kw(args.match_schedule.split(",")).values())
         fixed = {(int(sd), int(n)): t for sd, n in zip(sides, Ns)}
     for form in forms:
+        # the chosen BF16 form matches the whole batch in one persistent launch (glr_match_topk_batch)
         rec = glr.MsfaBatchReconstructor(sides, Ns, cfg.bands, cfg.P, cfg.K, mode=form, edge_th=cfg.edge_th,
-                                         device=dev, tuned=fixed if form == forms[0] else None)
+                                         device=dev, tuned=fixed if form == forms[0] else None,
+                                         persistent=form == "bf16" and not args.no_persistent)
         rec.start(ys, masks)
         steps = args.steps
         k = 0
@@ -1017,7 +1019,8 @@ def run_msfa(args, cfg, dev, dist) -> None:
     if not args.no_e2e:
         y_h = [torch.from_numpy(im.y).pin_memory() for im in imgs]
         rec = glr.MsfaBatchReconstructor(sides, Ns, cfg.bands, cfg.P, cfg.K, mode=forms[0], edge_th=cfg.edge_th,
-                                         device=dev, tuned=fixed)
+                                         device=dev, tuned=fixed,
+                                         persistent=forms[0] == "bf16" and not args.no_persistent)
         y_d = [torch.empty_like(y) for y in ys]
         for a, b in zip(y_d, y_h):
             a.copy_(b, non_blocking=True)
@@ -1219,6 +1222,8 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-persistent", action="store_true",
+                    help="msfa workloads: match each size class in its own launch instead of one persistent launch")
     ap.add_argument("--ablation", action="store_true",
                     help="print the matching-strategy comparison (GM vs block matching) instead of the bench line")
     ap.add_argument("--match-schedule", default="",

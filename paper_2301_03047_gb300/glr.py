@@ -597,18 +597,54 @@ class MsfaBatchReconstructor:
     """
 
     def __init__(self, sides, Ns, bands, P, K, mode="bf16", edge_th=0.1, device="cuda", tuned=None,
-                 concurrent=True):
+                 concurrent=True, persistent=False):
+        """persistent (BF16 mode): the matching of the whole batch is ONE launch of the persistent
+        tensor-core scorer over every image (glr_match_topk_batch); the other steps stay per class.
+        The class images, keys and matches then live in flat buffers (class order) that the uneven-batch
+        descriptor covers."""
         self.bands, self.P, self.K, self.concurrent = bands, P, K, concurrent
+        self.persistent = persistent and mode == "bf16"
+        self.edge_th = edge_th
         self.s = int(round(math.sqrt(bands)))
         self.classes = []  # (side, image indices, N, denoiser, stream, x, v, y, masks)
         order = {}
         for i, (sd, n) in enumerate(zip(sides, Ns)):
             order.setdefault((int(sd), int(n)), []).append(i)
-        for (sd, n), ids in sorted(order.items()):
+        groups = sorted(order.items())
+        if self.persistent:
+            npix = sum(len(ids) * bands * sd * sd for (sd, n), ids in groups)
+            nkeys = sum(len(ids) * n for (sd, n), ids in groups)
+            self.x_flat = torch.empty(npix, dtype=torch.float32, device=device)
+            self.keys_flat = torch.empty(nkeys, dtype=torch.int32, device=device)
+            self.nf_flat = torch.empty(sum(len(ids) for _, ids in groups), dtype=torch.int32, device=device)
+            self.idx_flat = torch.empty((nkeys, K), dtype=torch.int32, device=device)
+            self.dist_flat = torch.empty((nkeys, K), dtype=torch.float32, device=device)
+            bsides, bN = [], []
+            for (sd, n), ids in groups:
+                bsides += [(sd, sd)] * len(ids)
+                bN += [n] * len(ids)
+            self.batch = Batch(bsides, bands, P, bN, device=device)
+            self.batch_opts = match_opts("bf16")
+            lib = L.load()
+            nws = lib.glr_workspace_size_batch(ctypes.byref(self.batch.c), int(K), ctypes.byref(self.batch_opts))
+            if nws == 0:
+                raise GlrError("glr_workspace_size_batch", L.GLR_EINVAL)
+            self.ws_batch = torch.empty(int(nws) + 256, dtype=torch.uint8, device=device)
+        p0 = k0 = i0 = 0
+        for (sd, n), ids in groups:
             kw = tuple((tuned or {}).get((sd, n), ())) + (0,) * 5
             den = GlrDenoiser(GlrShape(len(ids), bands, sd, sd, P, n, K), mode, edge_th, kw[0], kw[1], device, kw[2],
                               kw[3], bound_pass=kw[4])
-            x = torch.empty((len(ids), bands, sd, sd), dtype=torch.float32, device=device)
+            if self.persistent:
+                m = len(ids)
+                x = self.x_flat[p0:p0 + m * bands * sd * sd].view(m, bands, sd, sd)
+                den.keys = self.keys_flat[k0:k0 + m * n].view(m, n)
+                den.n_found = self.nf_flat[i0:i0 + m]
+                den.idx = self.idx_flat[k0:k0 + m * n].view(m, n, K)
+                den.dist = self.dist_flat[k0:k0 + m * n].view(m, n, K)
+                p0, k0, i0 = p0 + m * bands * sd * sd, k0 + m * n, i0 + m
+            else:
+                x = torch.empty((len(ids), bands, sd, sd), dtype=torch.float32, device=device)
             self.classes.append({"side": sd, "ids": ids, "N": n, "den": den, "stream": torch.cuda.Stream(device=device),
                                  "x": x, "v": torch.empty_like(x)})
 
@@ -620,7 +656,32 @@ class MsfaBatchReconstructor:
             mosaic_init(c["y"], c["masks"], self.s, out=c["x"])
         return self
 
+    def _step_persistent(self, sigma_w: float, c_wnnm: float) -> None:
+        main = torch.cuda.current_stream()
+        P, K = self.P, self.K
+        for c in self.classes:  # key selection per class
+            d = c["den"]
+            select_keys(c["x"], P, c["N"], self.edge_th, keys=d.keys, n_found=d.n_found, n_corner=d.n_corner,
+                        ws=d.ws_select, stream=main)
+        # every image of the batch: one persistent tensor-core launch
+        match_topk_batch(self.x_flat, self.batch, self.keys_flat, self.nf_flat, K, idx=self.idx_flat,
+                         dist=self.dist_flat, ws=self.ws_batch, stream=main)
+        for c in self.classes:
+            c["stream"].wait_stream(main)
+        for c in self.classes:
+            st = c["stream"] if self.concurrent else main
+            with torch.cuda.stream(st):
+                d = c["den"]
+                lowrank_groups(c["x"], P, d.idx, d.n_found, sigma_w, c_wnnm, groups=d.groups, rank=d.rank,
+                               ws=d.ws_lowrank, stream=st)
+                aggregate(d.groups, d.idx, d.n_found, c["x"], P, out=c["v"], ws=d.ws_agg, stream=st)
+                gap_step(c["y"], c["masks"], c["v"], out=c["x"], stream=st)
+        for c in self.classes:
+            main.wait_stream(c["stream"])
+
     def step(self, sigma_w: float, c_wnnm: float) -> None:
+        if self.persistent:
+            return self._step_persistent(sigma_w, c_wnnm)
         main = torch.cuda.current_stream()
         if not self.concurrent:  # one class after the other on the current stream (for per-kernel timing)
             for c in self.classes:

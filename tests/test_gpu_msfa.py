@@ -148,3 +148,29 @@ def test_batch_bf16_matches_fp32_form():
         outs.append([t.cpu().numpy() for t in r.images()])
     for a, b, im in zip(outs[0], outs[1], imgs):
         assert abs(O.psnr(a, im.truth) - O.psnr(b, im.truth)) < 0.05
+
+
+def test_persistent_batch_matching_equals_class_path():
+    """The whole batch's matching as one persistent launch (glr_match_topk_batch) gives the same
+    matches as one launch per size class, so a full BF16 run of the schedule is identical bit for
+    bit; CUDA-graph replay of the persistent form equals its eager run."""
+    cfg = synth.MSFA_SMALL
+    imgs = synth.msfa_problem(cfg)
+    sides = [im.y.shape[0] for im in imgs]
+    masks = {im.y.shape[0]: cuda(im.masks) for im in imgs}
+    ys = [cuda(im.y) for im in imgs]
+    sig = cfg.sigma_schedule()
+    a = glr.MsfaBatchReconstructor(sides, [im.N for im in imgs], cfg.bands, cfg.P, cfg.K, mode="bf16")
+    b = glr.MsfaBatchReconstructor(sides, [im.N for im in imgs], cfg.bands, cfg.P, cfg.K, mode="bf16", persistent=True)
+    c = glr.MsfaBatchReconstructor(sides, [im.N for im in imgs], cfg.bands, cfg.P, cfg.K, mode="bf16", persistent=True)
+    for r in (a, b, c):
+        r.start(ys, masks)
+    c.capture(sig, cfg.c_wnnm)
+    for sw in sig:
+        a.step(sw, cfg.c_wnnm)
+        b.step(sw, cfg.c_wnnm)
+        c.step_graph(sw)
+    torch.cuda.synchronize()
+    for xa, xb, xc in zip(a.images(), b.images(), c.images()):
+        assert torch.equal(xa, xb)
+        assert torch.equal(xb, xc)
