@@ -42,12 +42,22 @@ UNIT = "iter/s"
 # with single-threaded BLAS so `cores` is exact.
 # ---------------------------------------------------------------------------
 def oracle_sample(n_keys: int = 24) -> dict:
-    import numpy as np
+    from paper_2301_03047_gb300 import synth
 
+    return _oracle_sample_sci(synth.SCI_LARGE, n_keys)
+
+
+def oracle_sample_huge(n_keys: int = 6) -> dict:
+    """The oracle on one 2048^2 frame of the 24-frame workload, extrapolated the same way."""
+    from paper_2301_03047_gb300 import synth
+
+    return _oracle_sample_sci(synth.SCI_HUGE, n_keys)
+
+
+def _oracle_sample_sci(cfg, n_keys: int) -> dict:
     from oracle import glr_oracle as O
     from paper_2301_03047_gb300 import synth
 
-    cfg = synth.SCI_LARGE
     prob = synth.sci_problem(synth.scaled(cfg, T=1))  # one frame of the same scene model and size
     sw = cfg.sigma_schedule()[0]
     x = O.gap_init(prob.y, prob.masks)[:, None]  # [1][1][H][W]
@@ -172,11 +182,26 @@ def run_oracle_child(n_keys: int, fn: str = "oracle_sample") -> dict:
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def run_oracle_all_cores(n_keys: int, fn: str = "oracle_sample", procs: int | None = None) -> dict:
+def _mem_available_gb() -> float:
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) / 2**20
+    except OSError:
+        pass
+    return 0.0
+
+
+def run_oracle_all_cores(n_keys: int, fn: str = "oracle_sample", procs: int | None = None,
+                         gb_per_proc: float = 0.0) -> dict:
     """The same sample on every host core at once: `procs` single-threaded children run side by
     side (their per-key and per-frame times include the contention for memory bandwidth), and the
-    full iteration's work is divided over them (frames and keys are independent units)."""
+    full iteration's work is divided over them (frames and keys are independent units).
+    gb_per_proc > 0: at most as many children as fit in half of the available host memory."""
     procs = procs or os.cpu_count() or 1
+    if gb_per_proc > 0:
+        procs = max(1, min(procs, int(0.5 * _mem_available_gb() / gb_per_proc)))
     cmd, env = _oracle_cmd(n_keys, fn)
     children = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT)
                 for _ in range(procs)]
@@ -197,10 +222,10 @@ def run_oracle_all_cores(n_keys: int, fn: str = "oracle_sample", procs: int | No
     return res
 
 
-def cpu_baseline_entry(n_keys: int, fn: str, unit: str = "iter/s") -> dict:
+def cpu_baseline_entry(n_keys: int, fn: str, unit: str = "iter/s", gb_per_proc: float = 0.0) -> dict:
     """cpu_baseline: the oracle on all host cores (value) and on one core (single_core), nproc recorded."""
     one = run_oracle_child(n_keys, fn)
-    allc = run_oracle_all_cores(max(4, n_keys // 4), fn)
+    allc = run_oracle_all_cores(max(4, n_keys // 4), fn, gb_per_proc=gb_per_proc)
     return {"value": round(allc["iters_per_s"], 8), "unit": unit, "cores": allc["procs"], "nproc": os.cpu_count(),
             "kind": "oracle", "sample": allc["sample"], "t_iter_s": round(allc["t_iter_s"], 1),
             "pair_dists_per_s": round(allc["pair_dists_per_s"], 1),
@@ -433,6 +458,10 @@ def workload(name: str):
 
     if name == "sci16":
         return synth.SCI_LARGE
+    if name == "sci24x2048":  # the learned-proposal workload: 24 frames of 2048^2, 16384 keys per frame
+        return synth.SCI_HUGE
+    if name == "sci2x2048":  # profiling case of the large frames
+        return synth.scaled(synth.SCI_HUGE, T=2, name="sci_2x2048x2048_P8_N16384_K64")
     if name == "sci4":  # profiling case: same frame size, 4 frames (operands still larger than L2)
         return synth.scaled(synth.SCI_LARGE, T=4, name="sci_4x512x512_P8_N4096_K64")
     if name == "sci8":
@@ -449,6 +478,81 @@ def workload(name: str):
     if name == "mri256":  # profiling case of the MRI path
         return synth.mri_scaled(synth.MRI_LARGE, H=256, W=256, N=2048, name="mri_256x256_P6_N2048_K48")
     raise ValueError(name)
+
+
+def run_learned(args, cfg, prob, y, masks, sched, dev, fpc, flush, x_final, chosen, plain) -> dict:
+    """The learned proposal: an encoder trained on pairs from the exhaustive matcher's own output on
+    two frames of the start image (set-up, untimed), then the GAP iterations with K' candidates per
+    key by embedding distance re-ranked exactly (timed like the other forms), its PSNR against the
+    chosen form, and the recall of the exhaustive top-K on frame 0 of the chosen form's final
+    estimate (trained and untrained encoder)."""
+    import torch
+
+    from paper_2301_03047_gb300 import glr
+
+    t0 = time.perf_counter()
+    x0 = glr.gap_step(y[None], masks, None).view(cfg.T, 1, cfg.H, cfg.W)
+    xt = x0[:2].contiguous()
+    kt, nt, _ = glr.select_keys(xt, cfg.P, cfg.N, cfg.edge_th)
+    it, _ = glr.match_topk(xt, cfg.P, kt, nt, cfg.K, "bf16")
+    enc = glr.Encoder(seed=0, device=dev)
+    hist = glr.train_encoder(enc, [(xt, cfg.P, kt, nt, it)], steps=args.learned_steps, batch_pairs=32768)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del x0, xt, kt, nt, it
+    torch.cuda.empty_cache()
+    kov = args.learned_k_over
+    rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode="learned", edge_th=cfg.edge_th,
+                               device=dev, k_over=kov, frames_per_call=fpc, encoder=enc.params)
+    rec.start(y, masks)
+    k = 0
+    for _ in range(args.warmup):
+        rec.step(sched[k % len(sched)], cfg.c_wnnm)
+        k += 1
+    torch.cuda.synchronize()
+    glr.profile_enable(True)
+    glr.profile_collect()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record()
+        rec.step(sched[k % len(sched)], cfg.c_wnnm)
+        ev[i][1].record()
+        k += 1
+    torch.cuda.synchronize()
+    prof = glr.profile_collect()
+    glr.profile_enable(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    psnr = psnr_framewise(rec.x.cpu().numpy()[0], prob.truth)
+    del rec
+    torch.cuda.empty_cache()
+
+    # recall of the exhaustive top-K among the learned proposal's K results, frame 0
+    x1 = x_final[0:1].reshape(1, 1, cfg.H, cfg.W).contiguous().to(dev)
+    k1, n1, _ = glr.select_keys(x1, cfg.P, cfg.N, cfg.edge_th)
+    n = int(n1[0].item())
+    ie, _ = glr.match_topk(x1, cfg.P, k1, n1, cfg.K, "bf16")
+    ie = ie[0, :n]
+
+    def recall(e, kv):
+        il, _ = glr.match_topk(x1, cfg.P, k1, n1, cfg.K, "learned", k_over=kv, encoder=e.params)
+        return round(float((il[0, :n, :, None] == ie[:, None, :]).any(-1).float().mean().item()), 4)
+
+    rec_tr = {str(kv): recall(enc, kv) for kv in sorted({kov // 2, kov})}
+    rec_un = recall(glr.Encoder(seed=0, device=dev), kov)
+    out = {"value": round(1e3 / ms, 4), "unit": UNIT, "ms_per_step": round(ms, 3), "steps": args.steps,
+           "k_over": kov, "psnr_db": round(psnr, 3), "delta_psnr_db_vs_chosen": round(psnr - chosen["psnr"], 4),
+           "speedup_vs_chosen": round(chosen["ms_per_step"] / ms, 3),
+           "recall_trained": rec_tr, "recall_untrained": rec_un,
+           "recall_of": f"exhaustive BF16 top-{cfg.K} of all {n} keys of frame 0 (chosen form's final estimate)",
+           "train": {"steps": args.learned_steps, "pairs_per_step": 32768, "frames": 2, "s": round(t_train, 2),
+                     "loss_first": round(hist[0], 4), "loss_last": round(hist[-1], 4)},
+           "kernels": {kn: {"ms_per_step": round(v[0] / args.steps, 3), "launches": v[1]}
+                       for kn, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
+    if plain is not None:
+        out["speedup_vs_plain"] = round(plain["ms_per_step"] / ms, 3)
+        out["delta_psnr_db_vs_plain"] = round(psnr - plain["psnr"], 4)
+    return out
 
 
 def run_glr(args) -> None:
@@ -484,28 +588,36 @@ def run_glr(args) -> None:
     stream_stats = None
     launches = 0
     tuned = {}
+    # frames of 2048^2: the denoiser works on 8 frames at a time (workspaces sized for 8); the
+    # plain form (about 6 s per iteration there) is timed over 3 iterations after 2 warm-ups
+    huge = cfg.H * cfg.W >= 2048 * 2048
+    fpc = 8 if huge else 0
     for form in forms:
+        headline = form == forms[0]
+        n_steps = args.steps if (headline or not huge) else min(args.steps, 3)
+        n_warm = args.warmup if (headline or not huge) else 2
         # autotune the matching schedule on the start image (set-up, untimed)
-        x0 = glr.gap_step(y[None], masks, None).view(cfg.T, 1, cfg.H, cfg.W).contiguous()
-        k0, n0, _ = glr.select_keys(x0, cfg.P, cfg.N, cfg.edge_th)
-        if args.match_schedule and form == forms[0]:
+        if args.match_schedule and headline:
             tuned[form] = sched_kw(args.match_schedule.split(","))
+        elif args.no_tune or huge:
+            tuned[form] = sched_kw(())
         else:
-            tuned[form] = sched_kw(glr.autotune_match(x0, cfg.P, k0, n0, cfg.K, form) if not args.no_tune else ())
-        del x0, k0, n0
+            x0 = glr.gap_step(y[None], masks, None).view(cfg.T, 1, cfg.H, cfg.W).contiguous()
+            k0, n0, _ = glr.select_keys(x0, cfg.P, cfg.N, cfg.edge_th)
+            tuned[form] = sched_kw(glr.autotune_match(x0, cfg.P, k0, n0, cfg.K, form))
+            del x0, k0, n0
         rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=form, edge_th=cfg.edge_th,
-                                   device=dev, **tuned[form])
+                                   device=dev, frames_per_call=fpc, **tuned[form])
         rec.start(y, masks)
         k = 0
-        for _ in range(args.warmup):
+        for _ in range(n_warm):
             rec.step(sched[k % len(sched)], cfg.c_wnnm)
             k += 1
         torch.cuda.synchronize()
-        headline = form == forms[0]
         if headline:
             glr.profile_enable(True)
             glr.profile_collect()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
@@ -513,7 +625,7 @@ def run_glr(args) -> None:
         clk = Clocks(local) if headline else None
         if clk:
             clk.__enter__()
-        for i in range(args.steps):
+        for i in range(n_steps):
             flush.zero_()
             ev[i][0].record()
             rec.step(sched[k % len(sched)], cfg.c_wnnm)
@@ -527,6 +639,11 @@ def run_glr(args) -> None:
             dist.barrier()
         step_ms = [a.elapsed_time(b) for a, b in ev]
         total_s = reduce_max(sum(step_ms) / 1e3, dist, dev)
+        if not headline:
+            # quality is compared at equal iteration counts: untimed steps up to the chosen form's count
+            while k < results[forms[0]]["iters"]:
+                rec.step(sched[k % len(sched)], cfg.c_wnnm)
+                k += 1
         if headline:
             launches = glr.launch_count() - l0
             prof = glr.profile_collect()
@@ -540,8 +657,8 @@ def run_glr(args) -> None:
         x = rec.x.cpu().numpy()[0]
         if headline:
             x_final = torch.from_numpy(x)
-        results[form] = {"total_s": total_s, "ms_per_step": total_s / args.steps * 1e3, "step_ms": step_ms,
-                         "psnr": psnr_framewise(x, prob.truth), "iters": k}
+        results[form] = {"total_s": total_s, "ms_per_step": total_s / n_steps * 1e3, "step_ms": step_ms,
+                         "psnr": psnr_framewise(x, prob.truth), "iters": k, "steps": n_steps}
         if headline and not args.no_graph:
             # the same noise levels as the eager timing, replayed from CUDA graphs (one per level)
             rec.capture(sched, cfg.c_wnnm)
@@ -562,6 +679,10 @@ def run_glr(args) -> None:
         del rec
         torch.cuda.empty_cache()
 
+    learned = None
+    if args.learned == 1 or (args.learned < 0 and huge):
+        learned = run_learned(args, cfg, prob, y, masks, sched, dev, fpc, flush, x_final, results[forms[0]],
+                              results.get("fp32"))
     head = results[forms[0]]
     value = ws * args.steps / head["total_s"]
     npos = (cfg.H - cfg.P + 1) * (cfg.W - cfg.P + 1)
@@ -574,7 +695,7 @@ def run_glr(args) -> None:
         m_h = torch.from_numpy(prob.masks).pin_memory()
         x_h = torch.empty((1, cfg.T, cfg.H, cfg.W), dtype=torch.float32).pin_memory()
         rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=forms[0], edge_th=cfg.edge_th,
-                                   device=dev, **tuned[forms[0]])
+                                   device=dev, frames_per_call=fpc, **tuned[forms[0]])
         y_d = torch.empty_like(y)
         m_d = torch.empty_like(masks)
         y_d.copy_(y_h, non_blocking=True)
@@ -626,7 +747,10 @@ def run_glr(args) -> None:
     cpu = None
     if not args.no_cpu:
         try:
-            cpu = cpu_baseline_entry(args.oracle_keys, "oracle_sample")
+            if huge:  # a 2048^2 frame: each key's scan is 16x longer, so fewer keys
+                cpu = cpu_baseline_entry(max(4, args.oracle_keys // 4), "oracle_sample_huge", gb_per_proc=8.0)
+            else:
+                cpu = cpu_baseline_entry(args.oracle_keys, "oracle_sample")
         except Exception as e:  # the CPU baseline must not hide the GPU result
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
         if oracle_inputs is not None:
@@ -635,7 +759,8 @@ def run_glr(args) -> None:
             except Exception as e:
                 cpu["oracle_error"] = {"failed": str(e)[-300:]}
             os.unlink(oracle_inputs)
-    rl = roofline(prof, cfg, sweeps, clocks_summary or {}, pk) if prof else None
+    # a launch covers frames_per_call frames when the frames are processed in groups
+    rl = roofline(prof, cfg, sweeps, clocks_summary or {}, pk, n_img=fpc or None) if prof else None
     kernels = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])} if prof else {}
     line = {
         "metric": METRIC,
@@ -666,15 +791,18 @@ def run_glr(args) -> None:
         "clocks": clocks_summary,
     }
     line["autotuned_match"] = tuned
+    if learned is not None:
+        line["learned"] = learned
     if "graph" in results:
         line["cuda_graph"] = {"value": round(results["graph"]["value"], 4), "unit": UNIT,
                               "ms_per_step": round(results["graph"]["ms_per_step"], 3)}
     if len(forms) > 1:
         pl = results["fp32"]
-        line["plain"] = {"value": round(ws * args.steps / pl["total_s"], 4), "unit": UNIT,
+        line["plain"] = {"value": round(ws * pl["steps"] / pl["total_s"], 4), "unit": UNIT,
                          "ms_per_step": round(pl["ms_per_step"], 3), "psnr_db": round(pl["psnr"], 3),
-                         "pair_dists_per_s": round(ws * pairs_per_iter * args.steps / pl["total_s"], 1)}
-        line["speedup_vs_plain"] = round(pl["total_s"] / head["total_s"], 3)
+                         "steps": pl["steps"],
+                         "pair_dists_per_s": round(ws * pairs_per_iter * pl["steps"] / pl["total_s"], 1)}
+        line["speedup_vs_plain"] = round(pl["ms_per_step"] / head["ms_per_step"], 3)
         line["delta_psnr_db"] = round(head["psnr"] - pl["psnr"], 4)
     print(json.dumps(line))
 
@@ -776,7 +904,7 @@ def run_mri(args, cfg, dev, dist) -> None:
         clk = Clocks(local) if headline else None
         if clk:
             clk.__enter__()
-        for i in range(args.steps):
+        for i in range(n_steps):
             flush.zero_()
             ev[i][0].record()
             rec.step(sched[k % len(sched)], cfg.c_wnnm)
@@ -820,6 +948,10 @@ def run_mri(args, cfg, dev, dist) -> None:
         del rec
         torch.cuda.empty_cache()
 
+    learned = None
+    if args.learned == 1 or (args.learned < 0 and huge):
+        learned = run_learned(args, cfg, prob, y, masks, sched, dev, fpc, flush, x_final, results[forms[0]],
+                              results.get("fp32"))
     head = results[forms[0]]
     e2e = None
     if not args.no_e2e:
@@ -1213,10 +1345,16 @@ def main() -> None:
                     help="matching form: bf16 (chosen), fp32 (plain), edge (the paper's heat map of Eq. 4)")
     ap.add_argument("--oracle-keys", type=int, default=96)
     ap.add_argument("--workload", default="sci16",
-                    choices=["sci16", "sci4", "sci8", "mri1024", "mri256", "msfa32", "msfa4", "msfa2"],
-                    help="sci16 = the headline workload; mri1024 = the MRI (ADMM) path on 1024^2 complex; "
-                    "msfa32 = MSFA demosaicing of 32 images of uneven sizes; sci4 / sci8 / mri256 / msfa4 are "
-                    "smaller cases for profiling")
+                    choices=["sci16", "sci4", "sci8", "sci24x2048", "sci2x2048", "mri1024", "mri256", "msfa32",
+                             "msfa4", "msfa2"],
+                    help="sci16 = the headline workload; sci24x2048 = 24 frames of 2048^2 with 16384 keys per "
+                    "frame (adds the learned proposal); mri1024 = the MRI (ADMM) path on 1024^2 complex; "
+                    "msfa32 = MSFA demosaicing of 32 images of uneven sizes; sci4 / sci8 / sci2x2048 / mri256 / "
+                    "msfa4 are smaller cases for profiling")
+    ap.add_argument("--learned", type=int, default=-1,
+                    help="1: also time the learned proposal (trained encoder); default on for 2048^2 frames")
+    ap.add_argument("--learned-k-over", type=int, default=256, help="candidates per key of the learned proposal")
+    ap.add_argument("--learned-steps", type=int, default=300, help="encoder training steps (32768 pairs each)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -400,13 +400,20 @@ class GlrDenoiser:
 
     def __init__(self, shape: GlrShape, mode: str = "bf16", edge_th: float = 0.1, k_over: int = 0, splits: int = 0,
                  device="cuda", cap: int = 0, epi_batch: int = 0, complex_: bool = False, n_uniform: int = 0,
-                 window: int = 20, fused: bool = False, bound_pass: int = 0):
+                 window: int = 20, fused: bool = False, bound_pass: int = 0, frames_per_call: int = 0,
+                 encoder: torch.Tensor | None = None):
         """fused (real images, d <= 64, K <= 64): grouping, WNNM and aggregation in one kernel pass
         (glr_lowrank_aggregate): no group buffer (1 GB less on the 16 x 512^2 workload) but slower
         there (27.7 ms against 23.5 ms for the separate kernels on the GAP start image: the fused
         kernel's per-lane patch gathers do not coalesce and its 12 warps per SM hide the atomics
-        poorly), so it is off by default."""
+        poorly), so it is off by default.
+
+        frames_per_call > 0: the steps run on that many images at a time (the images are independent),
+        so workspaces and the group buffer are sized for that many (large images, e.g. 24 frames of
+        2048 x 2048).  encoder: the encoder parameters for mode "learned"."""
         s = shape
+        self.fpc = frames_per_call if 0 < frames_per_call < s.n_img else s.n_img
+        self.encoder = encoder
         self.shape, self.mode, self.edge_th, self.complex_ = s, mode, edge_th, complex_
         self.n_uniform, self.window = n_uniform, window
         can_fuse = not complex_ and s.C * s.P * s.P <= 64 and s.K <= 64
@@ -414,7 +421,7 @@ class GlrDenoiser:
         self.opts = match_opts(mode, k_over, splits, cap, None, epi_batch, edge_th, window, bound_pass)
         self.k_over, self.splits, self.cap, self.epi_batch = k_over, splits, cap, epi_batch
         self.bound_pass = bound_pass
-        im = images(s.n_img, s.C, s.H, s.W, s.P)
+        im = images(self.fpc, s.C, s.H, s.W, s.P)
         dev = torch.device(device)
         d = s.C * s.P * s.P
         self.keys = torch.empty((s.n_img, s.N), dtype=torch.int32, device=dev)
@@ -422,9 +429,10 @@ class GlrDenoiser:
         self.n_corner = torch.empty(s.n_img, dtype=torch.int32, device=dev)
         self.idx = torch.empty((s.n_img, s.N, s.K), dtype=torch.int32, device=dev)
         self.dist = torch.empty((s.n_img, s.N, s.K), dtype=torch.float32, device=dev)
-        self.groups = None if self.fused else torch.empty((s.n_img, s.N, s.K, d), dtype=torch.float32, device=dev)
+        self.groups = None if self.fused else torch.empty((self.fpc, s.N, s.K, d), dtype=torch.float32, device=dev)
         self.rank = torch.empty((s.n_img, s.N), dtype=torch.int32, device=dev)
         self.ws_select = workspace(L.GLR_OP_SELECT, im, s.N, s.K, None, dev)
+        self.opts.encoder = _ptr(encoder) if encoder is not None else None
         self.ws_match = workspace(L.GLR_OP_MATCH, im, s.N, s.K, self.opts, dev)
         self.ws_lowrank = workspace(L.GLR_OP_LOWRANK, im, s.N, s.K, None, dev)
         self.ws_agg = workspace(L.GLR_OP_AGGREGATE, im, s.N, s.K, None, dev)
@@ -434,30 +442,44 @@ class GlrDenoiser:
     def __call__(self, x: torch.Tensor, sigma_w: float, c_wnnm: float, out: torch.Tensor | None = None,
                  stream=None) -> torch.Tensor:
         s = self.shape
-        select_keys(x, s.P, s.N, self.edge_th, n_uniform=self.n_uniform, keys=self.keys, n_found=self.n_found,
-                    n_corner=self.n_corner, ws=self.ws_select, stream=stream)
-        match_topk(x, s.P, self.keys, self.n_found, s.K, self.mode, k_over=self.k_over, splits=self.splits,
-                   cap=self.cap, epi_batch=self.epi_batch, edge_th=self.edge_th, window=self.window,
-                   bound_pass=self.bound_pass, idx=self.idx,
-                   dist=self.dist, ws=self.ws_match, stream=stream)
+        if out is None:
+            out = torch.empty_like(x)
+        for f0 in range(0, s.n_img, self.fpc):
+            f1 = min(s.n_img, f0 + self.fpc)
+            self._call_range(x[f0:f1], f0, f1, sigma_w, c_wnnm, out[f0:f1], stream)
+        return out
+
+    def _call_range(self, x, f0, f1, sigma_w, c_wnnm, out, stream):
+        s = self.shape
+        keys, nf, nc = self.keys[f0:f1], self.n_found[f0:f1], self.n_corner[f0:f1]
+        idx, dist, rank = self.idx[f0:f1], self.dist[f0:f1], self.rank[f0:f1]
+        select_keys(x, s.P, s.N, self.edge_th, n_uniform=self.n_uniform, keys=keys, n_found=nf,
+                    n_corner=nc, ws=self.ws_select, stream=stream)
+        match_topk(x, s.P, keys, nf, s.K, self.mode, k_over=self.k_over, splits=self.splits,
+                   cap=self.cap, encoder=self.encoder, epi_batch=self.epi_batch, edge_th=self.edge_th,
+                   window=self.window, bound_pass=self.bound_pass, idx=idx, dist=dist, ws=self.ws_match,
+                   stream=stream)
         if self.fused:
-            return lowrank_aggregate(x, s.P, self.idx, self.n_found, sigma_w, c_wnnm, out=out, rank=self.rank,
-                                     ws=self.ws_agg, stream=stream)
-        lowrank_groups(x, s.P, self.idx, self.n_found, sigma_w, c_wnnm, groups=self.groups, rank=self.rank,
-                       ws=self.ws_lowrank, stream=stream, complex_=self.complex_)
-        return aggregate(self.groups, self.idx, self.n_found, x, s.P, out=out, ws=self.ws_agg, stream=stream)
+            return lowrank_aggregate(x, s.P, idx, nf, sigma_w, c_wnnm, out=out, rank=rank, ws=self.ws_agg,
+                                     stream=stream)
+        groups = self.groups[: f1 - f0]
+        lowrank_groups(x, s.P, idx, nf, sigma_w, c_wnnm, groups=groups, rank=rank, ws=self.ws_lowrank,
+                       stream=stream, complex_=self.complex_)
+        return aggregate(groups, idx, nf, x, s.P, out=out, ws=self.ws_agg, stream=stream)
 
 
 class SciReconstructor:
     """GAP + GLR for one video snapshot y = sum_t M_t x_t (Eq. 6); frames are the images."""
 
     def __init__(self, T, H, W, P, N, K, mode="bf16", edge_th=0.1, accelerate=False, k_over=0, splits=0,
-                 device="cuda", cap=0, epi_batch=0, admm_rho=0.0, n_uniform=0, window=20, bound_pass=0):
+                 device="cuda", cap=0, epi_batch=0, admm_rho=0.0, n_uniform=0, window=20, bound_pass=0,
+                 frames_per_call=0, encoder=None):
         """admm_rho > 0: ADMM (z = D(x + u), u += x - z, x = the data step) instead of GAP;
-        n_uniform > 0: corner + uniform key mix."""
+        n_uniform > 0: corner + uniform key mix; frames_per_call, encoder: see GlrDenoiser."""
         self.T, self.H, self.W = T, H, W
         self.den = GlrDenoiser(GlrShape(T, 1, H, W, P, N, K), mode, edge_th, k_over, splits, device, cap, epi_batch,
-                               n_uniform=n_uniform, window=window, bound_pass=bound_pass)
+                               n_uniform=n_uniform, window=window, bound_pass=bound_pass,
+                               frames_per_call=frames_per_call, encoder=encoder)
         self.accelerate = accelerate
         self.rho = admm_rho
         self.x = torch.empty((1, T, H, W), dtype=torch.float32, device=device)
