@@ -482,10 +482,10 @@ def workload(name: str):
 
 def run_learned(args, cfg, prob, y, masks, sched, dev, fpc, flush, x_final, chosen, plain) -> dict:
     """The learned proposal: an encoder trained on pairs from the exhaustive matcher's own output on
-    two frames of the start image (set-up, untimed), then the GAP iterations with K' candidates per
-    key by embedding distance re-ranked exactly (timed like the other forms), its PSNR against the
-    chosen form, and the recall of the exhaustive top-K on frame 0 of the chosen form's final
-    estimate (trained and untrained encoder)."""
+    two frames of the start image (set-up, untimed), then for each embedding operand format (BF16,
+    FP8 E4M3) the GAP iterations with K' candidates per key by embedding score re-ranked exactly
+    (timed like the other forms), the PSNR against the chosen form, and the recall of the
+    exhaustive top-K on frame 0 of the chosen form's final estimate (trained and untrained)."""
     import torch
 
     from paper_2301_03047_gb300 import glr
@@ -502,31 +502,6 @@ def run_learned(args, cfg, prob, y, masks, sched, dev, fpc, flush, x_final, chos
     del x0, xt, kt, nt, it
     torch.cuda.empty_cache()
     kov = args.learned_k_over
-    rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode="learned", edge_th=cfg.edge_th,
-                               device=dev, k_over=kov, frames_per_call=fpc, encoder=enc.params)
-    rec.start(y, masks)
-    k = 0
-    for _ in range(args.warmup):
-        rec.step(sched[k % len(sched)], cfg.c_wnnm)
-        k += 1
-    torch.cuda.synchronize()
-    glr.profile_enable(True)
-    glr.profile_collect()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record()
-        rec.step(sched[k % len(sched)], cfg.c_wnnm)
-        ev[i][1].record()
-        k += 1
-    torch.cuda.synchronize()
-    prof = glr.profile_collect()
-    glr.profile_enable(False)
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    psnr = psnr_framewise(rec.x.cpu().numpy()[0], prob.truth)
-    del rec
-    torch.cuda.empty_cache()
-
     # recall of the exhaustive top-K among the learned proposal's K results, frame 0
     x1 = x_final[0:1].reshape(1, 1, cfg.H, cfg.W).contiguous().to(dev)
     k1, n1, _ = glr.select_keys(x1, cfg.P, cfg.N, cfg.edge_th)
@@ -534,24 +509,55 @@ def run_learned(args, cfg, prob, y, masks, sched, dev, fpc, flush, x_final, chos
     ie, _ = glr.match_topk(x1, cfg.P, k1, n1, cfg.K, "bf16")
     ie = ie[0, :n]
 
-    def recall(e, kv):
-        il, _ = glr.match_topk(x1, cfg.P, k1, n1, cfg.K, "learned", k_over=kv, encoder=e.params)
+    def recall(e, kv, fmt):
+        il, _ = glr.match_topk(x1, cfg.P, k1, n1, cfg.K, "learned", k_over=kv, encoder=e.params, emb_format=fmt)
         return round(float((il[0, :n, :, None] == ie[:, None, :]).any(-1).float().mean().item()), 4)
 
-    rec_tr = {str(kv): recall(enc, kv) for kv in sorted({kov // 2, kov})}
-    rec_un = recall(glr.Encoder(seed=0, device=dev), kov)
-    out = {"value": round(1e3 / ms, 4), "unit": UNIT, "ms_per_step": round(ms, 3), "steps": args.steps,
-           "k_over": kov, "psnr_db": round(psnr, 3), "delta_psnr_db_vs_chosen": round(psnr - chosen["psnr"], 4),
-           "speedup_vs_chosen": round(chosen["ms_per_step"] / ms, 3),
-           "recall_trained": rec_tr, "recall_untrained": rec_un,
+    enc0 = glr.Encoder(seed=0, device=dev)
+    out = {"k_over": kov, "steps": args.steps,
            "recall_of": f"exhaustive BF16 top-{cfg.K} of all {n} keys of frame 0 (chosen form's final estimate)",
            "train": {"steps": args.learned_steps, "pairs_per_step": 32768, "frames": 2, "s": round(t_train, 2),
-                     "loss_first": round(hist[0], 4), "loss_last": round(hist[-1], 4)},
-           "kernels": {kn: {"ms_per_step": round(v[0] / args.steps, 3), "launches": v[1]}
-                       for kn, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
-    if plain is not None:
-        out["speedup_vs_plain"] = round(plain["ms_per_step"] / ms, 3)
-        out["delta_psnr_db_vs_plain"] = round(psnr - plain["psnr"], 4)
+                     "loss_first": round(hist[0], 4), "loss_last": round(hist[-1], 4)}}
+    for fmt in ("bf16", "e4m3"):
+        rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode="learned", edge_th=cfg.edge_th,
+                                   device=dev, k_over=kov, frames_per_call=fpc, encoder=enc.params,
+                                   emb_format=fmt)
+        rec.start(y, masks)
+        k = 0
+        for _ in range(args.warmup):
+            rec.step(sched[k % len(sched)], cfg.c_wnnm)
+            k += 1
+        torch.cuda.synchronize()
+        glr.profile_enable(True)
+        glr.profile_collect()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record()
+            rec.step(sched[k % len(sched)], cfg.c_wnnm)
+            ev[i][1].record()
+            k += 1
+        torch.cuda.synchronize()
+        prof = glr.profile_collect()
+        glr.profile_enable(False)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        psnr = psnr_framewise(rec.x.cpu().numpy()[0], prob.truth)
+        _, mcnt = glr.poll_status(rec.den.ws_match)  # counters of the last call (frames_per_call frames)
+        cand = mcnt[4] / ((fpc or cfg.T) * cfg.N)
+        del rec
+        torch.cuda.empty_cache()
+        r = {"value": round(1e3 / ms, 4), "unit": UNIT, "ms_per_step": round(ms, 3), "psnr_db": round(psnr, 3),
+             "delta_psnr_db_vs_chosen": round(psnr - chosen["psnr"], 4),
+             "speedup_vs_chosen": round(chosen["ms_per_step"] / ms, 3),
+             "candidate_chunks_per_key": round(cand, 1),
+             "recall_trained": {str(kv): recall(enc, kv, fmt) for kv in sorted({kov // 2, kov})},
+             "recall_untrained": recall(enc0, kov, fmt),
+             "kernels": {kn: {"ms_per_step": round(v[0] / args.steps, 3), "launches": v[1]}
+                         for kn, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
+        if plain is not None:
+            r["speedup_vs_plain"] = round(plain["ms_per_step"] / ms, 3)
+            r["delta_psnr_db_vs_plain"] = round(psnr - plain["psnr"], 4)
+        out[fmt] = r
     return out
 
 

@@ -136,7 +136,16 @@ typedef struct glr_match_opts {
                              128-position half tile, and a candidate scan started from the
                              bound they give (same matches as -1);
                            -1 = one candidate scan;
-                           0 = automatic (2 where it applies, else 1 when d <= 74, else -1) */
+                           0 = automatic (2 where it applies, else 1 when d <= 74, else -1).
+                           GLR_MATCH_LEARNED: 2 or 0 = one scan over the embedding operands
+                             that records the minimum score of every 32-position chunk per
+                             key; the chunks at or below the key's K'-th smallest minimum are
+                             scored again in FP32 from the same operand values, and the K'
+                             best of those re-ranked exactly (positions < 2^24 - 64);
+                             1 or -1 = the candidate-stream scan over BF16 embeddings */
+  int32_t emb_format;   /* GLR_MATCH_LEARNED with bound_pass 2: the embedding operand of the
+                           proposal scan, 0 = BF16 (kind::f16), 1 = FP8 E4M3 with one
+                           power-of-two scale per call (kind::f8f6f4) */
 } glr_match_opts;
 
 /* Operation codes for glr_workspace_size. */
@@ -273,6 +282,21 @@ glr_status glr_encoder_train_step(const float* x, const glr_images* im, const in
 glr_status glr_debug_match_scores(const float* x, const glr_images* im, const int32_t* keys,
                                   const int32_t* n_found, int32_t N, int32_t K, float* scores, void* ws,
                                   size_t ws_bytes, void* stream);
+
+/*
+ * Testing aid for the learned proposal's scan: runs glr_match_topk in
+ * GLR_MATCH_LEARNED mode with bound_pass 2 (no idx / dist output) and also writes
+ * the raw scan scores of every key against the first 256 positions of its image,
+ * float32 [n_img][ceil(N/128)*128][256], to `scores` (device): the
+ * contraction over the 32 operand columns, ||a_q||^2 - 2 <a_p, a_q> + ||a_p||^2
+ * with both squared norms carried as three terms of the operand type, for the
+ * embedding operands a (BF16 roundings of the embeddings, or E4M3 roundings of
+ * s times them, s the per-call power-of-two scale; emb_format 0 or 1).  Exists to check the operand packing and the
+ * kind::f16 / kind::f8f6f4 contraction against a host computation.
+ */
+glr_status glr_debug_proposal_scores(const float* x, const glr_images* im, const int32_t* keys,
+                                     const int32_t* n_found, int32_t N, int32_t K, const float* encoder,
+                                     int32_t emb_format, float* scores, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * Testing aid for the bounded waits of the tensor-core scorer (BF16, LEARNED and

@@ -88,3 +88,44 @@ def adamw_step(params, grads, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, wd=1
         out_p[k] = p - lr * mh / (np.sqrt(vh) + eps)
         out_m[k], out_v[k] = m_k, v_k
     return out_p, out_m, out_v
+
+
+# ---------------------------------------------------------------------------
+# 8-bit proposal operands: FP8 E4M3 rounding (the OCP 8-bit floating-point
+# format's E4M3 encoding: 1 sign bit, 4 exponent bits with bias 7, 3 mantissa
+# bits, no infinities, largest finite magnitude 1.75 x 2^8 = 448, normals down
+# to 2^-6, subnormals m x 2^-9 for m = 1..7), written from that definition.
+# ---------------------------------------------------------------------------
+E4M3_MAX = 448.0
+
+
+def e4m3_round(x) -> np.ndarray:
+    """Round to the nearest E4M3 value, ties to even, saturating at +-448 (FP64 in and out)."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    with np.errstate(divide="ignore"):
+        e = np.floor(np.log2(np.where(a > 0, a, 1.0)))
+    e = np.clip(e, -6, 8)  # below 2^-6 the spacing stays at the subnormal 2^-9
+    quantum = np.exp2(e - 3)
+    q = np.round(a / quantum) * quantum  # numpy rounds halves to even
+    q = np.minimum(q, E4M3_MAX)
+    return np.where(x < 0, -q, q)
+
+
+def e4m3_decode(code: int) -> float:
+    """Value of an E4M3 byte (NaN for the two NaN codes)."""
+    s = -1.0 if code & 0x80 else 1.0
+    ex = (code >> 3) & 0xF
+    m = code & 0x7
+    if ex == 0xF and m == 0x7:
+        return float("nan")
+    if ex == 0:
+        return s * m * 2.0**-9
+    return s * (1.0 + m / 8.0) * 2.0 ** (ex - 7)
+
+
+def e4m3_scale(n2max: float, target: float = 384.0) -> float:
+    """The proposal's per-call scale: the largest power of two s with s^2 n2max <= target."""
+    if not n2max > 0:
+        return 1.0
+    return float(2.0 ** np.floor(np.log2(np.sqrt(target / n2max))))

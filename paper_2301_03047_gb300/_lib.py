@@ -27,7 +27,8 @@ class GlrImages(ctypes.Structure):
 
 class GlrMatchOpts(ctypes.Structure):
     _fields_ = [("mode", c_int32), ("k_over", c_int32), ("splits", c_int32), ("cap", c_int32), ("encoder", c_void_p),
-                ("epi_batch", c_int32), ("edge_th", c_float), ("window", c_int32), ("bound_pass", c_int32)]
+                ("epi_batch", c_int32), ("edge_th", c_float), ("window", c_int32), ("bound_pass", c_int32),
+                ("emb_format", c_int32)]
 
 
 class GlrBatch(ctypes.Structure):
@@ -46,6 +47,7 @@ PROTOTYPES = {
     "glr_admm_sci_step": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_float, c_void_p, c_void_p, c_void_p]),
     "glr_match_topk": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, ctypes.POINTER(GlrMatchOpts), c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_debug_match_scores": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "glr_debug_proposal_scores": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
     "glr_debug_wnnm_sweep_cap": (c_int32, [c_int32]),
     "glr_debug_match_wait_ns": (ctypes.c_uint64, [ctypes.c_uint64]),
     "glr_encoder_embed": (c_int32, [c_void_p, ctypes.POINTER(GlrImages), c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

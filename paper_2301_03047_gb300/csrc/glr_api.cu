@@ -258,6 +258,21 @@ glr_status glr_debug_match_scores(const float* x, const glr_images* im, const in
   return st;
 }
 
+glr_status glr_debug_proposal_scores(const float* x, const glr_images* im, const int32_t* keys,
+                                     const int32_t* n_found, int32_t N, int32_t K, const float* encoder,
+                                     int32_t emb_format, float* scores, void* ws, size_t ws_bytes, void* stream) {
+  if (!scores || !encoder || (emb_format != 0 && emb_format != 1)) return GLR_EINVAL;
+  glr_match_opts o{};
+  o.mode = GLR_MATCH_LEARNED;
+  o.encoder = encoder;
+  o.bound_pass = 2;
+  o.emb_format = emb_format;
+  g_tc_dump = scores;
+  glr_status st = glr_match_topk(x, im, keys, n_found, N, K, &o, nullptr, nullptr, ws, ws_bytes, stream);
+  g_tc_dump = nullptr;
+  return st;
+}
+
 glr_status glr_encoder_embed(const float* x, const glr_images* im, const float* params, float* emb, void* ws,
                              size_t ws_bytes, void* stream) {
   if (!images_ok(im) || !x || !params || !emb) return GLR_EINVAL;
@@ -272,7 +287,7 @@ glr_status glr_encoder_embed(const float* x, const glr_images* im, const float* 
   double* part = reinterpret_cast<double*>((char*)ws + L.take((size_t)im->n_img * kMeanMaxSlices * 8));
   st = launch_image_mean(x, *im, mean, part, s);
   if (st != GLR_OK) return st;
-  return launch_encode_positions(x, *im, mean, params, emb, s);
+  return launch_encode_positions(x, *im, mean, params, emb, nullptr, reinterpret_cast<StatusBlock*>(ws), s);
 }
 
 glr_status glr_encoder_train_step(const float* x, const glr_images* im, const int32_t* pairs, int32_t n_pairs,

@@ -46,7 +46,9 @@ struct MatchPlan {
   int bound_pass;       // tensor-core scorer: minima scan first (bound from half-tile minima)
   size_t mins_off;      // bound_pass 1: half-tile minima [n_img][Npad][2 pos_tiles] float32;
                         // bound_pass 2: 16-bit chunk minima [n_img][Npad][8 pos_tiles]
-  size_t ccnt_off, clist_off;  // bound_pass 2: candidate chunks per key (count, the first 256 ids)
+  size_t ccnt_off, clist_off;  // bound_pass 2: candidate chunks per key (count, the first ids)
+  int emb_fmt;                 // GLR_MATCH_LEARNED, bound_pass 2: proposal operand 0 = BF16, 1 = E4M3
+  size_t embq_off, n2_off;     // its position operand rows, the largest squared embedding norm
   size_t mean_off, meanp_off, qn_off, keyv_off, buf_off, bufcnt_off, taugl_off, qpack_off, kpack_off, embp_off, embk_off, total;
 };
 MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o);
@@ -56,13 +58,16 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
 // tensor-core scorer (k_match_tc.cu); returns GLR_ENOTSUP when the shape is not covered
 glr_status launch_match_tc(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found,
                            int N, const MatchPlan& plan, char* ws, cudaStream_t s);
+// learned proposal scan over the packed embedding operands (k_match_tc.cu)
+glr_status launch_match_emb(const glr_images& im, const int32_t* keys, const int32_t* n_found, int N,
+                            const MatchPlan& pl, char* ws, float* dump, cudaStream_t s);
 glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int32_t* n_found, const MatchPlan& pl,
                                 char* ws, float* dump, const int32_t* seed_keys, int seed_N, const float* emb_pos,
                                 const float* emb_keys, cudaStream_t s);
 
 // ---- learned proposal (k_encoder.cu)
 glr_status launch_encode_positions(const float* x, const glr_images& im, const float* mean, const float* params,
-                                   float* emb, cudaStream_t s);
+                                   float* emb, unsigned* n2max, StatusBlock* st, cudaStream_t s);
 glr_status launch_encode_vectors(const float* vecs, long long n, int d, const float* params, float* emb,
                                  cudaStream_t s);
 // image means: part = scratch of n_img x kMeanMaxSlices doubles

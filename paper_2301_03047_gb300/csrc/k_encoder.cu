@@ -5,8 +5,9 @@
 // Parameter buffer (FP32 master, 5200 floats): W1[64][64] (row = hidden unit),
 // b1[64], W2[16][64] (row = output), b2[16].
 //
-//  k_encode_positions  embedding of every patch position (mean-shifted patch),
-//                      weights rounded to FP16 in shared memory, FP32 math
+//  k_encode_tc         embedding of every patch position (mean-shifted patch) on the
+//                      tensor cores: FP16 patches, weights and hidden activations,
+//                      FP32 accumulation
 //  k_encode_vectors    embedding of given 64-vectors (the shifted key patches)
 //  k_enc_train         one block per 64 pairs: FP32 forward of both patches,
 //                      loss w (||f(p)-f(q)||^2 - d)^2 with w = 1/(d + 0.05)^2
@@ -17,6 +18,7 @@
 #include <cuda_fp16.h>
 
 #include "glr_kernels.cuh"
+#include "tc_ptx.cuh"
 
 namespace glr {
 
@@ -68,37 +70,185 @@ __device__ __forceinline__ void enc_forward(const float* w, const float (&p)[EI]
   }
 }
 
-__global__ void __launch_bounds__(128) k_encode_positions(const float* __restrict__ x, const float* __restrict__ mean,
-                                                          int n_img, int C, int H, int W, int P,
-                                                          const float* __restrict__ params, float* __restrict__ emb) {
-  extern __shared__ __align__(16) float wsm[];
-  load_weights(params, wsm, true);
+// ---- inference on the tensor cores: 128 positions per tile, two tcgen05.mma (kind::f16,
+// FP16 operands, FP32 accumulators in tensor memory).  A = the tile's mean-shifted patches
+// [128][64] and H = its hidden activations, both FP16 in the 128-byte swizzled K-major
+// layout; W1 [64][64] and W2 [16][64] (FP16) are the B operands.  Per tile:
+//   threads write their patch rows -> MMA1 (128 x 64 x 64) -> threads read their row of
+//   D1, add b1, apply the ReLU, write their FP16 row of H -> MMA2 (128 x 16 x 64) ->
+//   threads read D2, add b2 and store the FP32 embedding.
+// 128 threads (thread t owns row t, i.e. tensor-memory lane t); 128 tensor-memory columns
+// (D1: 0..63, D2: 64..79); at most four CTAs per SM (shared memory), so the columns of
+// all resident CTAs fit.  The largest squared embedding norm goes to *n2max (the scale of
+// the 8-bit proposal operand).
+constexpr int ENC_M = 128;
+constexpr uint32_t ENC_A = 0, ENC_H = 16384, ENC_W1 = 32768, ENC_W2 = 40960, ENC_B = 43008, ENC_BAR = 43520;
+constexpr uint32_t ENC_SMEM = 50 * 1024;  // > 228 KB / 5: at most four resident CTAs
+
+// Byte offset of 16-byte chunk c of row r in a [rows][128 B] tile with the 128-byte swizzle.
+__device__ __forceinline__ uint32_t sw128(int r, int c) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+}
+__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+template <int PT>
+__global__ void __launch_bounds__(ENC_M) k_encode_tc(const float* __restrict__ x, const float* __restrict__ mean,
+                                                     int n_img, int C, int H, int W, int P_,
+                                                     const float* __restrict__ params, float* __restrict__ emb,
+                                                     unsigned* __restrict__ n2max, StatusBlock* st) {
+  extern __shared__ uint8_t enc_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(enc_raw) + 1023) & ~(uintptr_t)1023);
+  const int P = PT ? PT : P_;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  float* bias = reinterpret_cast<float*>(sm + ENC_B);  // b1[64], b2[16]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + ENC_BAR);
+  uint32_t* tmem_s = reinterpret_cast<uint32_t*>(sm + ENC_BAR + 32);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(sm + ENC_BAR + 36);
+  // FP16 weights into the swizzled B tiles; biases stay FP32
+  for (int i = tid; i < (EH + EO) * 8; i += ENC_M) {
+    const int row = i >> 3, c = i & 7;
+    const float* src = params + (row < EH ? OFF_W1 + row * EI : OFF_W2 + (row - EH) * EH) + 8 * c;
+    const uint4 v = make_uint4(pack_h2(src[0], src[1]), pack_h2(src[2], src[3]), pack_h2(src[4], src[5]),
+                               pack_h2(src[6], src[7]));
+    *reinterpret_cast<uint4*>(sm + (row < EH ? ENC_W1 + sw128(row, c) : ENC_W2 + sw128(row - EH, c))) = v;
+  }
+  for (int i = tid; i < EH + EO; i += ENC_M) bias[i] = params[i < EH ? OFF_B1 + i : OFF_B2 + i - EH];
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    mbar_init(bar + 2, 1);
+    *abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_s, 128);
+    tmem_relinquish();
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
   __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_s;
+  const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
   const int Hq = H - P + 1, Wq = W - P + 1;
   const long long npos = (long long)Hq * Wq;
-  const long long total = (long long)n_img * npos;
+  const long long tiles_per_img = (npos + ENC_M - 1) / ENC_M;
   const int d = C * P * P;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long f = i / npos;
-    const int q = (int)(i - f * npos);
-    const int r = q / Wq, c = q - (q / Wq) * Wq;
-    const float mu = mean[f];
-    float p[EI];
+  const uint32_t sA = smem_u32(sm + ENC_A), sH = smem_u32(sm + ENC_H);
+  const uint32_t sW1 = smem_u32(sm + ENC_W1), sW2 = smem_u32(sm + ENC_W2);
+  float wmax = 0.f;
+  uint32_t phase = 0;
+  for (long long t = blockIdx.x; t < (long long)n_img * tiles_per_img; t += gridDim.x) {
+    const long long f = t / tiles_per_img;
+    const long long q = (t - f * tiles_per_img) * ENC_M + tid;
+    const bool valid = q < npos;
+    // this thread's mean-shifted patch (zeros past d and past the last position), FP16
+    {
+      const int r = valid ? (int)(q / Wq) : 0, c = valid ? (int)(q - (q / Wq) * Wq) : 0;
+      const float mu = mean[f];
+      const float* xf = x + (long long)f * C * H * W + (long long)r * W + c;
+      uint32_t w[32];
 #pragma unroll
-    for (int e = 0; e < EI; ++e) {
-      float v = 0.f;
-      if (e < d) {
-        const int ch = e / (P * P), dr = (e / P) % P, dc = e % P;
-        v = __ldg(x + (((long long)f * C + ch) * H + r + dr) * W + c + dc) - mu;
+      for (int e2 = 0; e2 < 32; ++e2) {
+        float v[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int e = 2 * e2 + u;
+          float val = 0.f;
+          if constexpr (PT > 0) {
+            const int ch = e / (PT * PT), dr = (e / PT) % PT, dc = e % PT;
+            if (valid && ch < C) val = __ldg(xf + ((long long)ch * H + dr) * W + dc) - mu;
+          } else if (valid && e < d) {
+            const int ch = e / (P * P), dr = (e / P) % P, dc = e % P;
+            val = __ldg(xf + ((long long)ch * H + dr) * W + dc) - mu;
+          }
+          v[u] = val;
+        }
+        w[e2] = pack_h2(v[0], v[1]);
       }
-      p[e] = v;
-    }
-    float out[EO];
-    enc_forward(wsm, p, out);
-    float4* dst = reinterpret_cast<float4*>(emb + i * EO);
 #pragma unroll
-    for (int k = 0; k < EO / 4; ++k) dst[k] = make_float4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
+      for (int c8 = 0; c8 < 8; ++c8)
+        *reinterpret_cast<uint4*>(sm + ENC_A + sw128(tid, c8)) =
+            make_uint4(w[4 * c8], w[4 * c8 + 1], w[4 * c8 + 2], w[4 * c8 + 3]);
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int k = 0; k < EI / 16; ++k)
+        mma_f16(tmem, smem_desc(sA + 32 * k, 1024, LAYOUT_SW128), smem_desc(sW1 + 32 * k, 1024, LAYOUT_SW128),
+                 idesc_f16(ENC_M, EH), k > 0 ? 1u : 0u);
+      mma_commit(bar);
+    }
+    if (__syncthreads_or(!mbar_wait(bar, phase, abort_s, st))) break;
+    tc_fence_after();
+    {
+      float z[2][32];
+      tmem_ld_32x32_nowait(lane_addr, z[0]);
+      tmem_ld_32x32_nowait(lane_addr + 32, z[1]);
+      tmem_ld_wait();
+#pragma unroll
+      for (int c8 = 0; c8 < 8; ++c8) {
+        uint32_t w4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = 8 * c8 + 2 * u;
+          w4[u] = pack_h2(fmaxf(z[j >> 5][j & 31] + bias[j], 0.f), fmaxf(z[(j + 1) >> 5][(j + 1) & 31] + bias[j + 1], 0.f));
+        }
+        *reinterpret_cast<uint4*>(sm + ENC_H + sw128(tid, c8)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+      }
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int k = 0; k < EH / 16; ++k)
+        mma_f16(tmem + 64, smem_desc(sH + 32 * k, 1024, LAYOUT_SW128), smem_desc(sW2 + 32 * k, 1024, LAYOUT_SW128),
+                 idesc_f16(ENC_M, EO), k > 0 ? 1u : 0u);
+      mma_commit(bar + 1);
+    }
+    if (__syncthreads_or(!mbar_wait(bar + 1, phase, abort_s, st))) break;
+    tc_fence_after();
+    {
+      float o[32];
+      tmem_ld_32x32_nowait(lane_addr + 64, o);
+      tmem_ld_wait();
+      float n2 = 0.f;
+#pragma unroll
+      for (int j = 0; j < EO; ++j) {
+        o[j] += bias[EH + j];
+        n2 = fmaf(o[j], o[j], n2);
+      }
+      if (valid) {
+        float4* dst = reinterpret_cast<float4*>(emb + (f * npos + q) * EO);
+#pragma unroll
+        for (int k = 0; k < EO / 4; ++k) dst[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+        wmax = fmaxf(wmax, n2);
+      }
+    }
+    tc_fence_before();
+    phase ^= 1u;
+  }
+  // teardown: every MMA issued has completed before tensor memory is freed
+  if (tid == 0) {
+    mma_commit(bar + 2);
+    mbar_wait(bar + 2, 0, abort_s, st, false);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  if (n2max != nullptr && (tid & 31) == 0) atomicMax(n2max, __float_as_uint(wmax));
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 128);
   }
 }
 
@@ -269,12 +419,28 @@ __global__ void k_adamw(float* __restrict__ params, const float* __restrict__ gr
 }  // namespace
 
 glr_status launch_encode_positions(const float* x, const glr_images& im, const float* mean, const float* params,
-                                   float* emb, cudaStream_t s) {
-  const long long total = (long long)im.n_img * (im.H - im.P + 1) * (im.W - im.P + 1);
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 128), (long long)num_sms() * 16));
-  const size_t smem = NPARAM * 4;
-  GLR_LAUNCH("k_encode_positions", s,
-             k_encode_positions<<<blocks, 128, smem, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, params, emb));
+                                   float* emb, unsigned* n2max, StatusBlock* st, cudaStream_t s) {
+  if (im.C * im.P * im.P > EI) return GLR_ENOTSUP;
+  const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
+  const long long tiles = (long long)im.n_img * ceil_div(npos, (long long)ENC_M);
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)num_sms() * 4));
+  if (n2max != nullptr && cudaMemsetAsync(n2max, 0, 4, s) != cudaSuccess) return GLR_ECUDA;
+#define GLR_ENC_CASE(PP)                                                                                       \
+  {                                                                                                            \
+    if (cudaFuncSetAttribute(k_encode_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ENC_SMEM) !=   \
+        cudaSuccess)                                                                                           \
+      return GLR_ECUDA;                                                                                        \
+    GLR_LAUNCH("k_encode_tc", s,                                                                               \
+               k_encode_tc<PP><<<blocks, ENC_M, ENC_SMEM, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, params, \
+                                                               emb, n2max, st));                               \
+  }
+  switch (im.P) {
+    case 4: GLR_ENC_CASE(4); break;
+    case 6: GLR_ENC_CASE(6); break;
+    case 8: GLR_ENC_CASE(8); break;
+    default: GLR_ENC_CASE(0); break;
+  }
+#undef GLR_ENC_CASE
   return GLR_OK;
 }
 

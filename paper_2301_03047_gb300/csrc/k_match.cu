@@ -14,6 +14,9 @@
 //   k_rerank       per key: the K' best stream scores over all the key's
 //                  streams (ties to smaller ids), their exact FP32
 //                  sum((p-q)^2), sort by (distance, id), emit the K best.
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "glr_kernels.cuh"
 #include "topk_stream.cuh"
 
@@ -508,22 +511,25 @@ __device__ int warp_keep_smallest_kth(unsigned long long* list, int n, int k, un
 
 // Bound and candidate chunks of every key for the exact evaluation (one warp per key, many
 // warps per SM to hide the memory latency).
-//  * Each lane keeps the 8 smallest of its share of the key's rounded-up 16-bit chunk minima
+//  * Each lane keeps the L smallest of its share of the key's rounded-up 16-bit chunk minima
 //    (pairs of adjacent chunks, interleaved over the lanes) in registers; the K'-th smallest of
-//    those 256 values is tau16.  It bounds the K'-th smallest of all the minima from above (the
+//    those 32 L values is tau16.  It bounds the K'-th smallest of all the minima from above (the
 //    K'-th smallest of a subset is never smaller), so every chunk that holds one of the key's K'
 //    smallest BF16 scores has its minimum at or below tau16; it equals the exact K'-th smallest
-//    unless a lane's share holds more than 8 of the K' smallest.
-//  * Then the ids of every chunk at or below tau16, ascending (the first CT_CL of them; ccount
+//    unless a lane's share holds more than L of the K' smallest.
+//  * Then the ids of every chunk at or below tau16, ascending (the first clcap of them; ccount
 //    receives the full count).
-constexpr int CT_CL = 256;
+constexpr int CT_CL = 256;   // listed candidate chunks per key (exact matching)
+constexpr int CT_CL_EMB = 512;  // listed candidate chunks per key (learned proposal, K' up to 256)
 
+// L = values each lane keeps (8 for K' <= 96; 24 for the learned proposal's K' up to 256)
+template <int L>
 __global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ mins16, const int32_t* __restrict__ n_found,
-                                                   int n_img, int N, int Npad, int nchunks, int kp,
+                                                   int n_img, int N, int Npad, int nchunks, int kp, int clcap,
                                                    uint32_t* __restrict__ tau16, int32_t* __restrict__ ccount,
                                                    uint32_t* __restrict__ clist, StatusBlock* st) {
   __shared__ unsigned hist_s[8][256];
-  __shared__ uint16_t vals_s[8][256];
+  __shared__ uint16_t vals_s[8][32 * L];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned* hist = hist_s[wid];
   uint16_t* vals = vals_s[wid];
@@ -537,17 +543,17 @@ __global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ 
     if (nchunks > kp) {
       // per-lane 8 smallest (sorted ascending)
       const uint32_t* m2 = reinterpret_cast<const uint32_t*>(mins16 + row * nchunks);
-      uint32_t t[8];
+      uint32_t t[L];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) t[j] = 0xffffu;
+      for (int j = 0; j < L; ++j) t[j] = 0xffffu;
       for (int i = lane; i < n2; i += 32) {
         const uint32_t w = __ldg(m2 + i);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           uint32_t v = (w >> (16 * h)) & 0xffffu;
-          if (v < t[7]) {
+          if (v < t[L - 1]) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {  // insertion: t stays sorted, the largest drops out
+            for (int j = 0; j < L; ++j) {  // insertion: t stays sorted, the largest drops out
               const uint32_t lo = min(t[j], v);
               v = max(t[j], v);
               t[j] = lo;
@@ -556,7 +562,7 @@ __global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ 
         }
       }
 #pragma unroll
-      for (int j = 0; j < 8; ++j) vals[lane * 8 + j] = (uint16_t)t[j];
+      for (int j = 0; j < L; ++j) vals[lane * L + j] = (uint16_t)t[j];
       __syncwarp();
       // the kp-th smallest of the 256 kept values: two 8-bit radix passes
       int rank = kp;
@@ -568,7 +574,7 @@ __global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ 
         for (int j = 0; j < 8; ++j) hist[lane * 8 + j] = 0;
         __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < L; ++j) {
           const uint32_t e = vals[j * 32 + lane];
           if (pass == 0 || (e >> 8) == prefix) atomicAdd(&hist[(e >> shift) & 255u], 1u);
         }
@@ -631,7 +637,7 @@ __global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ 
       while (bits) {
         const int j = __ffs(bits) - 1;
         bits &= bits - 1;
-        if (pos < CT_CL) clist[row * CT_CL + pos] = (uint32_t)(8 * i + j);
+        if (pos < clcap) clist[row * clcap + pos] = (uint32_t)(8 * i + j);
         ++pos;
       }
       total += __shfl_sync(0xffffffffu, incl, 31);
@@ -642,6 +648,61 @@ __global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ 
       atomicAdd(&st->cand_appends, (unsigned long long)total);  // candidate chunks (status counter 4)
     }
   }
+}
+
+// Exact distances sum((p - q)^2) of the cnt (score, position) entries of a warp's list (pv =
+// the key's raw patch, xf = its image; the re-rank's order of summation), then the K smallest
+// (distance, id) pairs written sorted to row gk of idx / dist.  list holds at least the next
+// power of two above max(cnt, K) entries.
+template <int PT>
+__device__ void exact_topk_finish(unsigned long long* list, int cnt, const float* pv, const float* xf, int C, int H,
+                                  int W, int P_, int Wq, int K, unsigned* hist, int lane, long long gk,
+                                  int32_t* __restrict__ idx, float* __restrict__ dist) {
+  const int P = PT ? PT : P_;
+  for (int i = lane; i < cnt; i += 32) {
+    const int q = (int)(unsigned)(list[i] & 0xffffffffull);
+    const int r = q / Wq, c = q - (q / Wq) * Wq;
+    float acc = 0.f;
+    for (int ch = 0; ch < C; ++ch)
+      for (int dr = 0; dr < P; ++dr) {
+        const float* rowp = xf + ((long long)ch * H + r + dr) * W + c;
+        const float* pp = pv + (ch * P + dr) * P;
+        for (int dc = 0; dc < P; ++dc) {
+          const float df = pp[dc] - __ldg(rowp + dc);
+          acc = fmaf(df, df, acc);
+        }
+      }
+    list[i] = ((unsigned long long)float_order_key(acc) << 32) | (unsigned)q;
+  }
+  __syncwarp();
+  int total = cnt;
+  if (total > K) total = warp_keep_smallest(list, total, K, hist, lane);
+  int p2 = 32;
+  while (p2 < total) p2 <<= 1;
+  for (int i = total + lane; i < p2; i += 32) list[i] = ~0ull;
+  __syncwarp();
+  for (int kk = 2; kk <= p2; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < p2; i += 32) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & kk) == 0;
+          const unsigned long long a = list[i], b = list[ixj];
+          if ((a > b) == up) {
+            list[i] = b;
+            list[ixj] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  for (int i = lane; i < K; i += 32) {
+    const unsigned long long e = list[i];
+    if (idx) idx[gk * K + i] = (int32_t)(e & 0xffffffffu);
+    if (dist) dist[gk * K + i] = float_from_order_key((uint32_t)(e >> 32));
+  }
+  __syncwarp();
 }
 
 // Candidate chunks of the chunk-minima scan, evaluated exactly.  One warp per key:
@@ -857,51 +918,145 @@ __global__ void __launch_bounds__(CT_WARPS * 32, 4)
       if (listed || scan >= nchunks) break;
     }
     if (cnt > Kp) cnt = warp_keep_smallest_kth(list, cnt, Kp, hist, lane, &kth);
-    // 3. exact distances of the K' best, in the re-rank's order of summation
-    for (int i = lane; i < cnt; i += 32) {
-      const int q = (int)(unsigned)(list[i] & 0xffffffffull);
-      const int r = q / Wq, c = q - (q / Wq) * Wq;
-      float acc = 0.f;
-      for (int ch = 0; ch < C; ++ch)
-        for (int dr = 0; dr < P; ++dr) {
-          const float* rowp = xf + ((long long)ch * H + r + dr) * W + c;
-          const float* pp = pv + (ch * P + dr) * P;
-          for (int dc = 0; dc < P; ++dc) {
-            const float df = pp[dc] - __ldg(rowp + dc);
-            acc = fmaf(df, df, acc);
-          }
-        }
-      list[i] = ((unsigned long long)float_order_key(acc) << 32) | (unsigned)q;
-    }
-    __syncwarp();
-    int total = cnt;
-    if (total > K) total = warp_keep_smallest(list, total, K, hist, lane);
-    int p2 = 32;
-    while (p2 < total) p2 <<= 1;
-    for (int i = total + lane; i < p2; i += 32) list[i] = ~0ull;
-    __syncwarp();
-    for (int kk = 2; kk <= p2; kk <<= 1) {
-      for (int j = kk >> 1; j > 0; j >>= 1) {
-        for (int i = lane; i < p2; i += 32) {
-          const int ixj = i ^ j;
-          if (ixj > i) {
-            const bool up = (i & kk) == 0;
-            const unsigned long long a = list[i], b = list[ixj];
-            if ((a > b) == up) {
-              list[i] = b;
-              list[ixj] = a;
-            }
-          }
-        }
-        __syncwarp();
+    // 3. exact distances of the K' best, the K smallest written sorted
+    exact_topk_finish<PT>(list, cnt, pv, xf, C, H, W, P, Wq, K, hist, lane, gk, idx, dist);
+  }
+}
+
+// Learned proposal, after the embedding scan: every chunk whose rounded-up minimum is at or
+// below the key's K'-th smallest (k_tau_chunk<24>; they hold the key's K' smallest scan
+// scores) is scored again in FP32 from the same operand values,
+//   sc = sum_j a_q,j (a_q,j + b_p,j) = ||a_p - a_q||^2 - ||a_p||^2   (the scan's score up to
+//                                                                    a constant of the key),
+// a running warp list keeps the K' smallest (score, id), and those K' get their exact
+// distance and the K smallest are written sorted (exact_topk_finish).  One warp per key,
+// four chunks per step (lane = position within each), their operand rows loaded together.
+constexpr int ET_WARPS = 4;
+constexpr size_t ET_WARP_BYTES = (size_t)CT_LCAP * 8 + CT_CCAP * 4 + 256 * 4 + 96 * 4;
+
+template <bool FP8>
+__device__ __forceinline__ void emb_row_values(const uint8_t* row, float (&a)[16]) {
+  if constexpr (FP8) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(row));
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const __half2_raw hr =
+            __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((u[k] >> (16 * h)) & 0xffffu), __NV_E4M3);
+        const float2 v = __half22float2(__half2(hr));
+        a[4 * k + 2 * h] = v.x;
+        a[4 * k + 2 * h + 1] = v.y;
       }
     }
-    for (int i = lane; i < K; i += 32) {
-      const unsigned long long e = list[i];
-      if (idx) idx[gk * K + i] = (int32_t)(e & 0xffffffffu);
-      if (dist) dist[gk * K + i] = float_from_order_key((uint32_t)(e >> 32));
+  } else {
+    const uint4* p = reinterpret_cast<const uint4*>(row);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const uint4 w = __ldg(p + k);
+      const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        a[8 * k + 2 * t] = __uint_as_float(u[t] << 16);
+        a[8 * k + 2 * t + 1] = __uint_as_float(u[t] & 0xffff0000u);
+      }
     }
-    __syncwarp();
+  }
+}
+
+template <bool FP8>
+__global__ void __launch_bounds__(ET_WARPS * 32)
+    k_emb_topk(const float* __restrict__ x, const int32_t* __restrict__ keys, const int32_t* __restrict__ n_found,
+               const uint8_t* __restrict__ qop, const uint8_t* __restrict__ kop, const uint16_t* __restrict__ mins16,
+               const uint32_t* __restrict__ tau16s, const int32_t* __restrict__ ccount,
+               const uint32_t* __restrict__ clist_g, int clcap, int n_img, int C, int H, int W, int P, int N, int Npad,
+               long long npos_pad, int nchunks, int K, int Kp, int32_t* __restrict__ idx, float* __restrict__ dist) {
+  constexpr int RB = FP8 ? 32 : 64;  // operand row bytes
+  extern __shared__ unsigned long long et_smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint8_t* wbase = reinterpret_cast<uint8_t*>(et_smem) + (size_t)wid * ET_WARP_BYTES;
+  unsigned long long* list = reinterpret_cast<unsigned long long*>(wbase);
+  uint32_t* clist = reinterpret_cast<uint32_t*>(wbase + CT_LCAP * 8);
+  unsigned* hist = reinterpret_cast<unsigned*>(wbase + CT_LCAP * 8 + CT_CCAP * 4);
+  float* pv = reinterpret_cast<float*>(wbase + CT_LCAP * 8 + CT_CCAP * 4 + 256 * 4);  // raw key patch
+  const int d = C * P * P;
+  const int Hq = H - P + 1, Wq = W - P + 1;
+  const long long npos = (long long)Hq * Wq;
+  const unsigned ltm = (1u << lane) - 1u;
+  const long long nkeys = (long long)n_img * N;
+  for (long long gk = blockIdx.x * (long long)ET_WARPS + wid; gk < nkeys; gk += (long long)gridDim.x * ET_WARPS) {
+    const int f = (int)(gk / N), k = (int)(gk - (long long)f * N);
+    if (k >= min(n_found[f], N)) continue;
+    const int kq = keys[gk];
+    if ((unsigned)kq >= (unsigned)npos) continue;  // flagged by k_key_vectors
+    const int kr = kq / Wq, kc = kq - (kq / Wq) * Wq;
+    const float* xf = x + (long long)f * C * H * W;
+    for (int e = lane; e < d; e += 32) {
+      const int ch = e / (P * P), dr = (e / P) % P, dc = e % P;
+      pv[e] = __ldg(xf + ((long long)ch * H + kr + dr) * W + kc + dc);
+    }
+    const long long row = (long long)f * Npad + k;
+    float b[16];
+    emb_row_values<FP8>(kop + row * RB, b);
+    const uint32_t tau16 = tau16s[row];
+    const int ctot = ccount[row];
+    const bool listed = ctot <= clcap;
+    const uint16_t* mk = mins16 + row * nchunks;
+    const uint8_t* qf = qop + (long long)f * npos_pad * RB;
+    int cnt = 0, scan = 0;
+    unsigned long long kth = ~0ull;
+    for (;;) {
+      int ncl = 0;
+      if (listed) {
+        for (int i = lane; i < ctot; i += 32) clist[i] = clist_g[row * clcap + i];
+        ncl = ctot;
+      } else {
+        // more candidates than the list holds: gather them from the minima, a batch at a time
+        while (scan < nchunks && ncl < CT_CCAP - 32) {
+          const int c = scan + lane;
+          const bool cand = c < nchunks && (uint32_t)__ldg(mk + c) <= tau16;
+          const unsigned m = __ballot_sync(0xffffffffu, cand);
+          if (cand) clist[ncl + __popc(m & ltm)] = (uint32_t)c;
+          ncl += __popc(m);
+          scan += 32;
+        }
+      }
+      __syncwarp();
+      for (int i0 = 0; i0 < ncl; i0 += 4) {
+        float a[4][16];
+        int q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int cid = i0 + u < ncl ? (int)clist[i0 + u] : -1;
+          q[u] = cid >= 0 && 32LL * cid + lane < npos ? 32 * cid + lane : -1;
+          if (q[u] >= 0) {
+            emb_row_values<FP8>(qf + (long long)q[u] * RB, a[u]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) a[u][j] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float sc = 0.f;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sc = fmaf(a[u][j], a[u][j] + b[j], sc);
+          const unsigned long long e =
+              q[u] >= 0 ? (((unsigned long long)float_order_key(sc) << 32) | (unsigned)q[u]) : ~0ull;
+          const bool keep = e < kth;
+          const unsigned m = __ballot_sync(0xffffffffu, keep);
+          if (keep) list[cnt + __popc(m & ltm)] = e;
+          cnt += __popc(m);
+        }
+        __syncwarp();
+        if (cnt > CT_LCAP - 128 && cnt > Kp) cnt = warp_keep_smallest_kth(list, cnt, Kp, hist, lane, &kth);
+      }
+      __syncwarp();
+      if (listed || scan >= nchunks) break;
+    }
+    if (cnt > Kp) cnt = warp_keep_smallest_kth(list, cnt, Kp, hist, lane, &kth);
+    exact_topk_finish<0>(list, cnt, pv, xf, C, H, W, P, Wq, K, hist, lane, gk, idx, dist);
   }
 }
 
@@ -956,6 +1111,36 @@ glr_status launch_rerank_streams(const float* x, const int32_t* keys, const int3
   return GLR_OK;
 }
 
+// Learned proposal after the embedding scan (bound_pass 2): the bound and candidate chunks of
+// every key, then their FP32 embedding scores, the exact distances of the K' best and the K
+// best written.
+glr_status launch_emb_topk(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found, int N,
+                           const MatchPlan& pl, char* ws, int32_t* idx, float* dist, cudaStream_t s) {
+  const long long nkeys = (long long)im.n_img * N;
+  const int nchunks = 8 * pl.pos_tiles;
+  const uint16_t* mins16 = reinterpret_cast<const uint16_t*>(ws + pl.mins_off);
+  uint32_t* tau16s = reinterpret_cast<uint32_t*>(ws + pl.taugl_off);
+  int32_t* ccount = reinterpret_cast<int32_t*>(ws + pl.ccnt_off);
+  uint32_t* clist_g = reinterpret_cast<uint32_t*>(ws + pl.clist_off);
+  {
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, 8), (long long)num_sms() * 16));
+    GLR_LAUNCH("k_tau_chunk", s, k_tau_chunk<24><<<blocks, 256, 0, s>>>(mins16, n_found, im.n_img, N, pl.Npad,
+                                                                         nchunks, pl.Kp, CT_CL_EMB, tau16s, ccount,
+                                                                         clist_g, reinterpret_cast<StatusBlock*>(ws)));
+  }
+  const size_t smem = (size_t)ET_WARPS * ET_WARP_BYTES;
+  auto kern = pl.emb_fmt == 1 ? k_emb_topk<true> : k_emb_topk<false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GLR_ECUDA;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, ET_WARPS), (long long)num_sms() * 8));
+  GLR_LAUNCH("k_emb_topk", s,
+             kern<<<blocks, ET_WARPS * 32, smem, s>>>(x, keys, n_found, reinterpret_cast<const uint8_t*>(ws + pl.embq_off),
+                                                      reinterpret_cast<const uint8_t*>(ws + pl.embk_off), mins16, tau16s,
+                                                      ccount, clist_g, CT_CL_EMB, im.n_img, im.C, im.H, im.W, im.P, N,
+                                                      pl.Npad, pl.npos_pad, nchunks, pl.K, pl.Kp, idx, dist));
+  return GLR_OK;
+}
+
 // Exact evaluation of the candidate chunks (bound_pass 2).
 glr_status launch_chunk_topk(const float* x, const glr_images& im, const int32_t* keys, const int32_t* n_found,
                              int N, const MatchPlan& pl, const float* mean, const float* qn, const float* keyv,
@@ -967,9 +1152,9 @@ glr_status launch_chunk_topk(const float* x, const glr_images& im, const int32_t
   uint32_t* clist_g = reinterpret_cast<uint32_t*>(ws + pl.clist_off);
   {
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, 8), (long long)num_sms() * 16));
-    GLR_LAUNCH("k_tau_chunk", s, k_tau_chunk<<<blocks, 256, 0, s>>>(mins16, n_found, im.n_img, N, pl.Npad, nchunks,
-                                                                     pl.Kp, tau16s, ccount, clist_g,
-                                                                     reinterpret_cast<StatusBlock*>(ws)));
+    GLR_LAUNCH("k_tau_chunk", s, k_tau_chunk<8><<<blocks, 256, 0, s>>>(mins16, n_found, im.n_img, N, pl.Npad,
+                                                                        nchunks, pl.Kp, CT_CL, tau16s, ccount, clist_g,
+                                                                        reinterpret_cast<StatusBlock*>(ws)));
   }
   const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, CT_WARPS), (long long)num_sms() * 8));
 #define GLR_CHUNK_CASE(PP, CM)                                                                                  \
@@ -1043,7 +1228,9 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   const int bp = o ? o->bound_pass : 0;
   const bool chunk_ok = pl.mode == GLR_MATCH_BF16 && d <= 74 && (im.P == 4 || im.P == 6 || im.P == 8) &&
                         im.C * im.P <= 16 && npos < (1LL << 24) - 64;  // position ids exact in FP32
-  const bool chunk = chunk_ok && (bp == 2 || bp == 0);
+  // the learned proposal's embedding scan takes the same chunk-minima form (bound_pass 2)
+  const bool emb_chunk = pl.mode == GLR_MATCH_LEARNED && (bp == 2 || bp == 0) && npos < (1LL << 24) - 64;
+  const bool chunk = (chunk_ok && (bp == 2 || bp == 0)) || emb_chunk;
   const long long nstreams = chunk ? 0 : (long long)im.n_img * pl.Npad * pl.streams_per_key;
   pl.buf_off = L.take((size_t)nstreams * (pl.cap + 32) * 8);
   pl.bufcnt_off = L.take((size_t)nstreams * 4);
@@ -1057,8 +1244,10 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
     const int dk = 64 * pl.nkc + 16;
     pl.dk = dk;
     pl.npos_pad = (long long)pl.pos_tiles * pl.pos_tile;
-    pl.qpack_off = L.take((size_t)im.n_img * pl.npos_pad * dk * 2);
-    pl.kpack_off = L.take((size_t)im.n_img * pl.Npad * dk * 2);
+    if (!emb_chunk) {
+      pl.qpack_off = L.take((size_t)im.n_img * pl.npos_pad * dk * 2);
+      pl.kpack_off = L.take((size_t)im.n_img * pl.Npad * dk * 2);
+    }
     // the bound of the minima scan needs Kp half tiles.  Automatic: on for one-chunk
     // rows, where the candidate appends cost more than a second contraction; off for
     // chunked rows (d > 74), where the contraction itself dominates
@@ -1066,7 +1255,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
       pl.bound_pass = 2;  // rounded-up 16-bit minima of every 32-position chunk
       pl.mins_off = L.take((size_t)im.n_img * pl.Npad * 8 * pl.pos_tiles * 2);
       pl.ccnt_off = L.take((size_t)im.n_img * pl.Npad * 4);
-      pl.clist_off = L.take((size_t)im.n_img * pl.Npad * CT_CL * 4);
+      pl.clist_off = L.take((size_t)im.n_img * pl.Npad * (emb_chunk ? CT_CL_EMB : CT_CL) * 4);
     } else {
       pl.bound_pass = ((bp == 1 || ((bp == 0 || bp == 2) && pl.nkc == 1)) && 2LL * pl.pos_tiles >= pl.Kp) ? 1 : 0;
       if (pl.bound_pass) pl.mins_off = L.take((size_t)im.n_img * pl.Npad * 2 * pl.pos_tiles * 4);
@@ -1074,8 +1263,16 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
   }
   if (edge) pl.edge_off = L.take((size_t)im.n_img * 4 * im.C * im.H * im.W * 4);
   if (pl.mode == GLR_MATCH_LEARNED) {
-    pl.embp_off = L.take((size_t)im.n_img * npos * 16 * 4);
-    pl.embk_off = L.take((size_t)im.n_img * pl.Npad * 16 * 4);
+    pl.embp_off = L.take((size_t)im.n_img * npos * 16 * 4);  // FP32 embeddings of every position
+    if (emb_chunk) {
+      pl.emb_fmt = (o && o->emb_format == 1) ? 1 : 0;
+      const size_t rb = pl.emb_fmt == 1 ? 32 : 64;  // operand row bytes
+      pl.n2_off = L.take(4);
+      pl.embq_off = L.take((size_t)im.n_img * pl.npos_pad * rb);
+      pl.embk_off = L.take((size_t)im.n_img * pl.Npad * rb);
+    } else {
+      pl.embk_off = L.take((size_t)im.n_img * pl.Npad * 16 * 4);
+    }
   }
   pl.total = L.off;
   return pl;
@@ -1131,7 +1328,8 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
     const glr_status st = launch_image_mean(x, im, mean, reinterpret_cast<double*>(ws + pl.meanp_off), s);
     if (st != GLR_OK) return st;
   }
-  if (!tc || pl.bound_pass == 2) {  // the FP32 scorers add ||q||^2 themselves; the tensor-core operands carry theirs
+  // the FP32 scorers add ||q||^2 themselves; the tensor-core operands carry theirs
+  if (!tc || (pl.bound_pass == 2 && pl.mode != GLR_MATCH_LEARNED)) {
     const long long total = (long long)im.n_img * npos;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)num_sms() * 32));
     GLR_LAUNCH("k_patch_norms", s, k_patch_norms<<<blocks, 256, 0, s>>>(x, mean, im.n_img, im.C, im.H, im.W, im.P, qn));
@@ -1145,9 +1343,17 @@ glr_status launch_match(const float* x, const glr_images& im, const int32_t* key
   StreamCfg cfg{pl.cap, pl.Kp, pl.finish};
   if (pl.mode == GLR_MATCH_LEARNED) {
     float* emb_p = reinterpret_cast<float*>(ws + pl.embp_off);
-    float* emb_k = reinterpret_cast<float*>(ws + pl.embk_off);
-    glr_status st = launch_encode_positions(x, im, mean, encoder, emb_p, s);
+    const bool emb_chunk = pl.bound_pass == 2;
+    glr_status st = launch_encode_positions(x, im, mean, encoder, emb_p,
+                                            emb_chunk ? reinterpret_cast<unsigned*>(ws + pl.n2_off) : nullptr,
+                                            reinterpret_cast<StatusBlock*>(ws), s);
     if (st != GLR_OK) return st;
+    if (emb_chunk) {
+      st = launch_match_emb(im, keys, n_found, N, pl, ws, g_tc_dump, s);
+      if (st != GLR_OK) return st;
+      return launch_emb_topk(x, im, keys, n_found, N, pl, ws, idx, dist, s);
+    }
+    float* emb_k = reinterpret_cast<float*>(ws + pl.embk_off);
     st = launch_encode_vectors(keyv, (long long)im.n_img * pl.Npad, d, encoder, emb_k, s);
     if (st != GLR_OK) return st;
   }

@@ -36,8 +36,11 @@
 // loads and MMAs are waited for (bounded) and TMEM is freed before exit.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "glr_kernels.cuh"
+#include "tc_ptx.cuh"
 #include "topk_stream.cuh"
 
 namespace glr {
@@ -86,115 +89,7 @@ constexpr uint32_t W_OFF_HIST = (W_OFF_MISC + 64 + 15) / 16 * 16;
 constexpr uint32_t W_OFF_TAU = W_OFF_HIST + TC_EPI_WARPS * 256 * 4;  // no append tile: rows go through shuffles
 constexpr uint32_t W_SMEM = W_OFF_TAU + TC_M * 4 + 1024;
 static_assert(W_SMEM <= 232448, "shared memory budget (wide)");
-constexpr unsigned long long kWaitNs = 1000000000ull;                   // 1 s
-
-// ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait.  Returns false if the CTA aborted or this wait timed out (then
-// it raises the abort flag and the device status bit).  The pipeline's waits take
-// the launch's limit (1 s unless a test shortens it); the teardown waits
-// (honour_abort = false), which only wait for copies and MMAs already issued,
-// always keep the full second.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, StatusBlock* st,
-                                          bool honour_abort = true, unsigned long long limit_ns = kWaitNs) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  const unsigned long long limit = honour_abort ? limit_ns : kWaitNs;
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    // the clock is read every 256 polls, or at every poll under a shortened (test) limit
-    if ((it & 255u) == 0 || limit < kWaitNs) {
-      if (honour_abort && *abort) return false;
-      if (globaltimer() - t0 > limit) {
-        *abort = 1;
-        status_set(st, GLR_DEV_TIMEOUT);
-        return false;
-      }
-    }
-  }
-}
-__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-// 32 lanes x 32 consecutive FP32 columns; the destination registers are valid after tmem_ld_wait().
-__device__ __forceinline__ void tmem_ld_32x32_nowait(uint32_t taddr, float (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
-      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
-        "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15]), "=f"(v[16]),
-        "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]), "=f"(v[22]), "=f"(v[23]), "=f"(v[24]),
-        "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31])
-      : "r"(taddr));
-}
-// Shared-memory matrix descriptor (K-major operand, swizzled): start address,
-// leading / stride byte offsets (>> 4), descriptor version 1, layout type.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo_bytes, uint32_t layout) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1u << 16;  // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1u << 46;
-  d |= (uint64_t)layout << 61;
-  return d;
-}
-constexpr uint32_t LAYOUT_SW128 = 2, LAYOUT_SW32 = 6;
-
-// Instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, N, M.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
+// (PTX helpers: tc_ptx.cuh)
 
 // ------------------------------------------------------------------- kernels
 __device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
@@ -648,6 +543,36 @@ __global__ void __launch_bounds__(256) k_seed_bounds(const __nv_bfloat16* __rest
   }
 }
 
+// One visit of an epilogue thread to its row's half tile in tensor memory (128 columns,
+// positions q0 ..): the minimum of every 32-position chunk as the upper 16 bits of its order
+// key rounded up (never below the true minimum; positions >= npos left out), four chunks
+// packed in 8 bytes at dst.  The accumulator buffer goes back to the MMA warp as soon as it
+// is read.  dump_row != nullptr: the 128 raw scores are copied there as well.
+__device__ __forceinline__ void chunk_minima_visit(uint32_t taddr, long long q0, long long npos, uint64_t* tempty_b,
+                                                   int lane, uint2* dst, float* dump_row) {
+  float w[4][32];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) tmem_ld_32x32_nowait(taddr + 32 * c, w[c]);
+  tmem_ld_wait();
+  tc_fence_before();
+  __syncwarp();
+  if (lane == 0) mbar_arrive(tempty_b);
+  if (dump_row != nullptr) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int j = 0; j < 32; ++j) dump_row[32 * c + j] = w[c][j];
+  }
+  uint32_t k16[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int nvalid = (int)max(0LL, min(32LL, npos - (q0 + 32 * c)));
+    const uint32_t k32 = float_order_key(stream_min(w[c], nvalid));
+    k16[c] = min((k32 >> 16) + ((k32 & 0xffffu) != 0u ? 1u : 0u), 0xffffu);
+  }
+  *dst = make_uint2(k16[0] | (k16[1] << 16), k16[2] | (k16[3] << 16));
+}
+
 template <int EB, bool WIDE, int MINS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_match_tc(const __grid_constant__ CUtensorMap tm_qmain, const __grid_constant__ CUtensorMap tm_qaux,
@@ -768,10 +693,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (kc < nkc) {
 #pragma unroll
             for (int k = 0; k < DK_MAIN / 16; ++k)
-              mma_bf16(d_tmem, smem_desc(sa + 32 * k, 1024, LAYOUT_SW128), smem_desc(sb + 32 * k, 1024, LAYOUT_SW128),
+              mma_f16(d_tmem, smem_desc(sa + 32 * k, 1024, LAYOUT_SW128), smem_desc(sb + 32 * k, 1024, LAYOUT_SW128),
                        idesc, (kc > 0 || k > 0) ? 1u : 0u);
           } else {
-            mma_bf16(d_tmem, smem_desc(sa, 256, LAYOUT_SW32), smem_desc(sb, 256, LAYOUT_SW32), idesc, 1u);
+            mma_f16(d_tmem, smem_desc(sa, 256, LAYOUT_SW32), smem_desc(sb, 256, LAYOUT_SW32), idesc, 1u);
           }
           mma_commit(empty + s);
           ++it;
@@ -825,9 +750,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t b_aux = smem_u32(smem + OFF_B_AUX + s * B_AUX_BYTES);
 #pragma unroll
         for (int k = 0; k < DK_MAIN / 16; ++k)
-          mma_bf16(d_tmem, smem_desc(a_main + 32 * k, 1024, LAYOUT_SW128), smem_desc(b_main + 32 * k, 1024, LAYOUT_SW128),
+          mma_f16(d_tmem, smem_desc(a_main + 32 * k, 1024, LAYOUT_SW128), smem_desc(b_main + 32 * k, 1024, LAYOUT_SW128),
                    idesc, k > 0 ? 1u : 0u);
-        mma_bf16(d_tmem, smem_desc(a_aux, 256, LAYOUT_SW32), smem_desc(b_aux, 256, LAYOUT_SW32), idesc, 1u);
+        mma_f16(d_tmem, smem_desc(a_aux, 256, LAYOUT_SW32), smem_desc(b_aux, 256, LAYOUT_SW32), idesc, 1u);
         mma_commit(empty + s);
         mma_commit(tfull + b);
       }
@@ -862,23 +787,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc_fence_after();
       const long long tile_q0 = (long long)(t_begin + i) * TC_N;
       if constexpr (MINS == 2) {
-        float w[4][32];
-        const uint32_t taddr = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) tmem_ld_32x32_nowait(taddr + 32 * c, w[c]);
-        tmem_ld_wait();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(tempty + b);
-        uint32_t k16[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int nvalid = (int)max(0LL, min(32LL, npos - (tile_q0 + h * 128 + 32 * c)));
-          const uint32_t k32 = float_order_key(stream_min(w[c], nvalid));
-          k16[c] = min((k32 >> 16) + ((k32 & 0xffffu) != 0u ? 1u : 0u), 0xffffu);
-        }
-        reinterpret_cast<uint2*>(mins)[(((long long)f * Npad + key) * ntiles + t_begin + i) * 2 + h] =
-            make_uint2(k16[0] | (k16[1] << 16), k16[2] | (k16[3] << 16));
+        chunk_minima_visit(tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128),
+                           tile_q0 + h * 128, npos, tempty + b, lane,
+                           reinterpret_cast<uint2*>(mins) + (((long long)f * Npad + key) * ntiles + t_begin + i) * 2 + h,
+                           nullptr);
         continue;
       } else if constexpr (MINS == 1) {
         float w[4][32], v[128];
@@ -1115,10 +1027,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (kc < nkc) {
 #pragma unroll
               for (int k = 0; k < DK_MAIN / 16; ++k)
-                mma_bf16(d_tmem, smem_desc(sa + 32 * k, 1024, LAYOUT_SW128), smem_desc(sb + 32 * k, 1024, LAYOUT_SW128),
+                mma_f16(d_tmem, smem_desc(sa + 32 * k, 1024, LAYOUT_SW128), smem_desc(sb + 32 * k, 1024, LAYOUT_SW128),
                          idesc, (kc > 0 || k > 0) ? 1u : 0u);
             } else {
-              mma_bf16(d_tmem, smem_desc(sa, 256, LAYOUT_SW32), smem_desc(sb, 256, LAYOUT_SW32), idesc, 1u);
+              mma_f16(d_tmem, smem_desc(sa, 256, LAYOUT_SW32), smem_desc(sb, 256, LAYOUT_SW32), idesc, 1u);
             }
             mma_commit(empty + s);
             ++it_ring;
@@ -1203,6 +1115,286 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
+// ------------------------------------------------------ learned proposal scan
+// The proposal contracts 16-value embeddings instead of patches.  Operand rows of 32
+// elements, one per position / key:
+//   BF16 (64-byte rows, two 32-byte swizzled chunks of 16 columns):
+//     positions [ a = e~ (16)            | qn_hi qn_mid qn_lo 1 1 1 0 .. ]
+//     keys      [ b = -2 e~ (16)         | 1 1 1 pn_hi pn_mid pn_lo 0 .. ]
+//   E4M3 (32-byte rows, one 32-byte swizzled chunk, kind::f8f6f4, K = 32 per MMA):
+//     positions [ a = e4m3(s e) (16)     | qn_hi qn_mid qn_lo 1 1 1 0 .. ]
+//     keys      [ b = e4m3(-2 a) (16)    | 1 1 1 pn_hi pn_mid pn_lo 0 .. ]
+// with e the FP32 embedding, e~ its BF16 rounding, qn = sum a^2 (FP32) of the position and
+// pn the same of the key's own position, each split into three terms of the operand type,
+// and s the per-tensor scale: the largest power of two with s^2 max ||e||^2 <= 384 (squared
+// norms stay below E4M3's largest finite 448; doubling is exact).  A tile product gives per
+// key p and position q the score
+//   ||a_q||^2 - 2 <a_p, a_q> + ||a_p||^2 = ||a_p - a_q||^2,
+// the squared distance of the rounded embeddings (scaled by s^2 for E4M3), so the 16-bit
+// chunk minima resolve it relative to the distance itself.
+constexpr int EMB_COLS = 32;
+constexpr int EMB_STAGES = 8;
+constexpr uint32_t EMB_A_BYTES = TC_M * 64;          // 8 KB: two 4 KB chunks (BF16) or one (E4M3)
+constexpr uint32_t EMB_STAGE_BYTES = TC_N * 64;      // 16 KB: two 8 KB chunks (BF16) or one (E4M3)
+constexpr uint32_t EMB_OFF_B = EMB_A_BYTES;
+constexpr uint32_t EMB_OFF_BAR = EMB_OFF_B + EMB_STAGES * EMB_STAGE_BYTES;
+constexpr int EMB_NBAR = 2 * EMB_STAGES + 4 + 2;
+constexpr uint32_t EMB_OFF_MISC = EMB_OFF_BAR + EMB_NBAR * 8;
+constexpr uint32_t EMB_SMEM = EMB_OFF_MISC + 64 + 1024;
+static_assert(EMB_SMEM <= 232448, "shared memory budget (proposal scan)");
+
+__device__ __forceinline__ float emb_scale(const unsigned* n2max) {
+  const float m = __uint_as_float(*n2max);
+  if (!(m > 0.f) || !(m < INFINITY)) return 1.f;
+  int ex;
+  frexpf(sqrtf(384.f / m), &ex);  // sqrt(384 / m) in [2^(ex-1), 2^ex)
+  return ldexpf(1.f, ex - 1);
+}
+__device__ __forceinline__ uint8_t to_e4m3(float v) {
+  return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float from_e4m3(uint8_t b) {
+  const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3);
+  return __half2float(__half(h));
+}
+
+// Position rows from the FP32 embeddings emb[img][npos][16]; rows past npos are zero.
+template <bool FP8>
+__global__ void __launch_bounds__(256) k_pack_emb_pos(const float* __restrict__ emb, int n_img, long long npos,
+                                                      long long npos_pad, const unsigned* __restrict__ n2max,
+                                                      uint8_t* __restrict__ out) {
+  constexpr int RB = FP8 ? 32 : 64;  // row bytes
+  const float s = FP8 ? emb_scale(n2max) : 1.f;
+  const long long total = (long long)n_img * npos_pad;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long f = i / npos_pad, q = i - f * npos_pad;
+    __align__(16) uint8_t row[RB];
+#pragma unroll
+    for (int k = 0; k < RB; ++k) row[k] = 0;
+    if (q < npos) {
+      const float4* src = reinterpret_cast<const float4*>(emb + (f * npos + q) * 16);
+      float e[16];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float4 v = __ldg(src + k);
+        e[4 * k] = v.x;
+        e[4 * k + 1] = v.y;
+        e[4 * k + 2] = v.z;
+        e[4 * k + 3] = v.w;
+      }
+      float n = 0.f;
+      if constexpr (FP8) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          row[j] = to_e4m3(s * e[j]);
+          const float a = from_e4m3(row[j]);
+          n = fmaf(a, a, n);
+        }
+        row[16] = to_e4m3(n);
+        const float r1 = n - from_e4m3(row[16]);
+        row[17] = to_e4m3(r1);
+        row[18] = to_e4m3(r1 - from_e4m3(row[17]));
+        row[19] = row[20] = row[21] = to_e4m3(1.f);
+      } else {
+        __nv_bfloat16* rb = reinterpret_cast<__nv_bfloat16*>(row);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          rb[j] = __float2bfloat16_rn(e[j]);
+          const float a = __bfloat162float(rb[j]);
+          n = fmaf(a, a, n);
+        }
+        split3(n, rb[16], rb[17], rb[18]);
+        rb[19] = rb[20] = rb[21] = __float2bfloat16_rn(1.f);
+      }
+    }
+    uint4* dst = reinterpret_cast<uint4*>(out + i * RB);
+#pragma unroll
+    for (int k = 0; k < RB / 16; ++k) dst[k] = reinterpret_cast<const uint4*>(row)[k];
+  }
+}
+
+// Key rows: the embedding of each key's own position (so a key scores its own position
+// like any other); rows of keys >= n_found and of the padding are zero.
+template <bool FP8>
+__global__ void __launch_bounds__(256) k_pack_emb_keys(const float* __restrict__ emb, const int32_t* __restrict__ keys,
+                                                       const int32_t* __restrict__ n_found, int n_img, int N, int Npad,
+                                                       long long npos, const unsigned* __restrict__ n2max,
+                                                       uint8_t* __restrict__ out) {
+  constexpr int RB = FP8 ? 32 : 64;
+  const float s = FP8 ? emb_scale(n2max) : 1.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)n_img * Npad;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(i / Npad), k = (int)(i - (long long)f * Npad);
+    __align__(16) uint8_t row[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) row[j] = 0;
+    const int kq = k < min(n_found[f], N) ? keys[(long long)f * N + k] : -1;
+    if (kq >= 0 && kq < npos) {
+      const float* src = emb + ((long long)f * npos + kq) * 16;
+      float n = 0.f;  // the key position's own squared norm, formed as for the position rows
+      if constexpr (FP8) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float a = from_e4m3(to_e4m3(s * __ldg(src + j)));
+          n = fmaf(a, a, n);
+          row[j] = to_e4m3(-2.f * a);
+        }
+        row[16] = row[17] = row[18] = to_e4m3(1.f);
+        row[19] = to_e4m3(n);
+        const float r1 = n - from_e4m3(row[19]);
+        row[20] = to_e4m3(r1);
+        row[21] = to_e4m3(r1 - from_e4m3(row[20]));
+      } else {
+        __nv_bfloat16* rb = reinterpret_cast<__nv_bfloat16*>(row);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float a = __bfloat162float(__float2bfloat16_rn(__ldg(src + j)));
+          n = fmaf(a, a, n);
+          rb[j] = __float2bfloat16_rn(-2.f * a);
+        }
+        rb[16] = rb[17] = rb[18] = __float2bfloat16_rn(1.f);
+        split3(n, rb[19], rb[20], rb[21]);
+      }
+    }
+    uint4* dst = reinterpret_cast<uint4*>(out + i * RB);
+#pragma unroll
+    for (int j = 0; j < RB / 16; ++j) dst[j] = reinterpret_cast<const uint4*>(row)[j];
+  }
+}
+
+// The proposal scan: CTA = 128 keys x one split of the positions, 320 threads as in
+// k_match_tc (producer, MMA issuer, 8 epilogue warps), an 8-stage ring of position tiles
+// (the contraction of a tile is one E4M3 or two BF16 instructions, so the ring is deeper),
+// and the chunk-minima epilogue: the minimum score of every 32-position chunk per key,
+// rounded up to 16 bits (mins viewed as uint16 [key][8 tile + 4 half + c]).
+template <bool FP8>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_match_emb(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_k, int Npad,
+                long long npos, long long npos_pad, int tiles_per_split, int ntiles, unsigned long long wait_ns,
+                StatusBlock* st, float* __restrict__ dump, uint2* __restrict__ mins) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr uint32_t kChunkA = TC_M * 32, kChunkB = TC_N * 32;  // one 32-byte column chunk of a tile
+  constexpr uint32_t kBytesA = FP8 ? kChunkA : 2 * kChunkA, kBytesB = FP8 ? kChunkB : 2 * kChunkB;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + EMB_OFF_BAR);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + EMB_STAGES;
+  uint64_t* tfull = bars + 2 * EMB_STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* a_full = tempty + 2;
+  uint64_t* mma_done = a_full + 1;
+  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(smem + EMB_OFF_MISC);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(smem + EMB_OFF_MISC + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kt = blockIdx.x, f = blockIdx.y, split = blockIdx.z;
+  const int t_begin = split * tiles_per_split;
+  const int nt = max(0, min(ntiles, t_begin + tiles_per_split) - t_begin);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < EMB_STAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);
+      mbar_init(tempty + b, TC_EPI_WARPS);
+    }
+    mbar_init(a_full, 1);
+    mbar_init(mma_done, 1);
+    *abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_base_s, 512);
+    tmem_relinquish();
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_base_s;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- producer
+      const int arow = f * Npad + kt * TC_M;
+      mbar_arrive_expect_tx(a_full, kBytesA);
+      tma_load_2d(&tm_k, a_full, smem, 0, arow);
+      if (!FP8) tma_load_2d(&tm_k, a_full, smem + kChunkA, 16, arow);
+      int issued = 0;
+      for (int i = 0; i < nt; ++i) {
+        const int s = i % EMB_STAGES;
+        const uint32_t ph = (uint32_t)(i / EMB_STAGES) & 1u;
+        if (!mbar_wait(empty + s, ph ^ 1u, abort_s, st, true, wait_ns)) break;
+        mbar_arrive_expect_tx(full + s, kBytesB);
+        const int brow = (int)(f * npos_pad + (long long)(t_begin + i) * TC_N);
+        uint8_t* sb = smem + EMB_OFF_B + s * EMB_STAGE_BYTES;
+        tma_load_2d(&tm_q, full + s, sb, 0, brow);
+        if (!FP8) tma_load_2d(&tm_q, full + s, sb + kChunkB, 16, brow);
+        issued = i + 1;
+      }
+      // teardown: every issued copy has landed before the CTA may exit
+      mbar_wait(a_full, 0, abort_s, st, false);
+      for (int i = max(0, issued - EMB_STAGES); i < issued; ++i)
+        mbar_wait(full + (i % EMB_STAGES), (uint32_t)(i / EMB_STAGES) & 1u, abort_s, st, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // --------------------------------------------------------- MMA issuer
+      constexpr uint32_t idesc = FP8 ? idesc_e4m3(TC_M, TC_N) : idesc_bf16(TC_M, TC_N);
+      const uint32_t sa = smem_u32(smem);
+      bool ok = mbar_wait(a_full, 0, abort_s, st, true, wait_ns);
+      tc_fence_after();
+      for (int i = 0; ok && i < nt; ++i) {
+        const int s = i % EMB_STAGES;
+        const uint32_t ph = (uint32_t)(i / EMB_STAGES) & 1u;
+        const int b = i & 1;
+        const uint32_t bph = (uint32_t)(i >> 1) & 1u;
+        if (!mbar_wait(full + s, ph, abort_s, st, true, wait_ns)) break;
+        if (!mbar_wait(tempty + b, bph ^ 1u, abort_s, st, true, wait_ns)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * TC_N);
+        const uint32_t sb = smem_u32(smem + EMB_OFF_B + s * EMB_STAGE_BYTES);
+        if constexpr (FP8) {
+          mma_e4m3(d_tmem, smem_desc(sa, 256, LAYOUT_SW32), smem_desc(sb, 256, LAYOUT_SW32), idesc, 0u);
+        } else {
+          mma_f16(d_tmem, smem_desc(sa, 256, LAYOUT_SW32), smem_desc(sb, 256, LAYOUT_SW32), idesc, 0u);
+          mma_f16(d_tmem, smem_desc(sa + kChunkA, 256, LAYOUT_SW32), smem_desc(sb + kChunkB, 256, LAYOUT_SW32), idesc,
+                  1u);
+        }
+        mma_commit(empty + s);
+        mma_commit(tfull + b);
+      }
+      // teardown: all issued MMAs have completed
+      mma_commit(mma_done);
+      mbar_wait(mma_done, 0, abort_s, st, false);
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    const int e = warp - 2;
+    const int quad = warp & 3;
+    const int h = e >> 2;
+    const int key = kt * TC_M + 32 * quad + lane;
+    for (int i = 0; i < nt; ++i) {
+      const int b = i & 1;
+      const uint32_t bph = (uint32_t)(i >> 1) & 1u;
+      if (!__all_sync(0xffffffffu, mbar_wait(tfull + b, bph, abort_s, st, true, wait_ns))) break;
+      tc_fence_after();
+      const long long tile_q0 = (long long)(t_begin + i) * TC_N;
+      float* dump_row = (dump != nullptr && i == 0 && t_begin == 0)
+                            ? dump + ((long long)f * Npad + key) * TC_N + h * 128
+                            : nullptr;
+      chunk_minima_visit(tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128),
+                         tile_q0 + h * 128, npos, tempty + b, lane,
+                         mins + (((long long)f * Npad + key) * ntiles + t_begin + i) * 2 + h, dump_row);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 512);
+  }
+}
+
 // ---------------------------------------------------------------- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -1222,14 +1414,14 @@ EncodeTiledFn encode_fn() {
 }
 
 bool make_map(CUtensorMap* m, void* base, uint64_t rows, uint32_t cols, uint32_t box_rows, CUtensorMapSwizzle sw,
-              uint32_t box_cols = 0) {
+              uint32_t box_cols = 0, CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, uint32_t esz = 2) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {cols, rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * esz};
   const cuuint32_t box[2] = {box_cols ? box_cols : cols, box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+  return fn(m, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -1487,6 +1679,57 @@ glr_status launch_match_tc(const float* x, const glr_images& im, const int32_t* 
   // seed bounds read the narrow operand layout only; the minima scan gives a tighter bound
   const int32_t* seed = (g_tc_dump || pl.nkc > 1 || pl.bound_pass) ? nullptr : keys;
   return launch_match_tc_impl(x, im, n_found, pl, ws, g_tc_dump, seed, N, ep, ek, s);
+}
+
+// Learned proposal (GLR_MATCH_LEARNED, bound_pass 2): pack the embedding operands (BF16 or
+// E4M3 with its per-tensor scale) and run the chunk-minima scan over them.  The FP32
+// embeddings and the largest squared norm are in the workspace (k_encode_tc).
+glr_status launch_match_emb(const glr_images& im, const int32_t* keys, const int32_t* n_found, int N,
+                            const MatchPlan& pl, char* ws, float* dump, cudaStream_t s) {
+  const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
+  const float* emb = reinterpret_cast<const float*>(ws + pl.embp_off);
+  const unsigned* n2 = reinterpret_cast<const unsigned*>(ws + pl.n2_off);
+  uint8_t* qop = reinterpret_cast<uint8_t*>(ws + pl.embq_off);
+  uint8_t* kop = reinterpret_cast<uint8_t*>(ws + pl.embk_off);
+  const bool fp8 = pl.emb_fmt == 1;
+  {
+    const long long total = (long long)im.n_img * pl.npos_pad;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)num_sms() * 32));
+    if (fp8)
+      GLR_LAUNCH("k_pack_emb_pos", s,
+                 k_pack_emb_pos<true><<<blocks, 256, 0, s>>>(emb, im.n_img, npos, pl.npos_pad, n2, qop));
+    else
+      GLR_LAUNCH("k_pack_emb_pos", s,
+                 k_pack_emb_pos<false><<<blocks, 256, 0, s>>>(emb, im.n_img, npos, pl.npos_pad, n2, qop));
+    const int kb = (int)std::max<long long>(1, ceil_div((long long)im.n_img * pl.Npad, 256));
+    if (fp8)
+      GLR_LAUNCH("k_pack_emb_keys", s,
+                 k_pack_emb_keys<true><<<kb, 256, 0, s>>>(emb, keys, n_found, im.n_img, N, pl.Npad, npos, n2, kop));
+    else
+      GLR_LAUNCH("k_pack_emb_keys", s,
+                 k_pack_emb_keys<false><<<kb, 256, 0, s>>>(emb, keys, n_found, im.n_img, N, pl.Npad, npos, n2, kop));
+  }
+  CUtensorMap tq, tk;
+  const uint64_t qrows = (uint64_t)im.n_img * pl.npos_pad, krows = (uint64_t)im.n_img * pl.Npad;
+  const CUtensorMapDataType dt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const uint32_t esz = fp8 ? 1 : 2, box_cols = fp8 ? 32 : 16;
+  if (!make_map(&tq, qop, qrows, EMB_COLS, TC_N, CU_TENSOR_MAP_SWIZZLE_32B, box_cols, dt, esz) ||
+      !make_map(&tk, kop, krows, EMB_COLS, TC_M, CU_TENSOR_MAP_SWIZZLE_32B, box_cols, dt, esz))
+    return GLR_ECUDA;
+  auto kern = fp8 ? k_match_emb<true> : k_match_emb<false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EMB_SMEM) != cudaSuccess)
+    return GLR_ECUDA;
+  int blocks_per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, TC_THREADS, EMB_SMEM) != cudaSuccess ||
+      blocks_per_sm != 1)  // all of TMEM: exactly one resident CTA per SM
+    return GLR_ENOTSUP;
+  dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
+  GLR_LAUNCH("k_match_emb", s,
+             kern<<<grid, TC_THREADS, EMB_SMEM, s>>>(tq, tk, pl.Npad, npos, pl.npos_pad, pl.tiles_per_split,
+                                                     pl.pos_tiles, g_match_wait_ns > 0 ? g_match_wait_ns : kWaitNs,
+                                                     reinterpret_cast<StatusBlock*>(ws), dump,
+                                                     reinterpret_cast<uint2*>(ws + pl.mins_off)));
+  return GLR_OK;
 }
 
 float* g_tc_dump = nullptr;

@@ -53,12 +53,13 @@ def images_of(x: torch.Tensor, P: int) -> L.GlrImages:
 
 def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0, cap: int = 0,
                encoder: torch.Tensor | None = None, epi_batch: int = 0, edge_th: float = 0.1,
-               window: int = 20, bound_pass: int = 0) -> L.GlrMatchOpts:
+               window: int = 20, bound_pass: int = 0, emb_format: str | int = "bf16") -> L.GlrMatchOpts:
     """mode: "fp32" (plain), "bf16" (chosen), "learned", "edge" (the paper's heat map of Eq. 4),
     or "window" (block matching within +-window of the key).  bound_pass (tensor-core modes):
     2 = chunk minima, then an exact FP32 evaluation of the candidate chunks; 1 = a minima scan
     gives each key its starting bound for the candidate scan; -1 = one candidate scan;
-    0 = automatic."""
+    0 = automatic.  emb_format (mode "learned", chunk minima): "bf16" or "e4m3" embedding
+    operands of the proposal scan."""
     m = {"fp32": L.GLR_MATCH_FP32, "bf16": L.GLR_MATCH_BF16, "learned": L.GLR_MATCH_LEARNED,
          "edge": L.GLR_MATCH_EDGE, "window": L.GLR_MATCH_WINDOW}.get(mode, mode)
     o = L.GlrMatchOpts()
@@ -68,6 +69,7 @@ def match_opts(mode: str | int = "fp32", k_over: int = 0, splits: int = 0, cap: 
     o.edge_th = float(edge_th)
     o.window = int(window)
     o.bound_pass = int(bound_pass)
+    o.emb_format = {"bf16": 0, "e4m3": 1, "fp8": 1}.get(emb_format, emb_format)
     return o
 
 
@@ -113,13 +115,13 @@ def select_keys(x, P, N, edge_th=0.1, *, n_uniform=0, keys=None, n_found=None, n
 
 
 def match_topk(x, P, keys, n_found, K, mode="fp32", *, k_over=0, splits=0, cap=0, encoder=None, epi_batch=0,
-               edge_th=0.1, window=20, bound_pass=0, idx=None, dist=None, ws=None, stream=None):
+               edge_th=0.1, window=20, bound_pass=0, emb_format="bf16", idx=None, dist=None, ws=None, stream=None):
     """Global matching with a fused running top-K (Eq. 1 over the whole image as a contraction).
     mode "edge": the paper's heat map (Eq. 4); dist then holds the heat-map values (descending)."""
     lib = L.load()
     im = images_of(x, P)
     N = keys.shape[1]
-    o = match_opts(mode, k_over, splits, cap, encoder, epi_batch, edge_th, window, bound_pass)
+    o = match_opts(mode, k_over, splits, cap, encoder, epi_batch, edge_th, window, bound_pass, emb_format)
     dev = x.device
     if idx is None:
         idx = torch.empty((x.shape[0], N, K), dtype=torch.int32, device=dev)
@@ -218,6 +220,25 @@ def debug_match_scores(x, P, keys, n_found, K, *, ws=None, stream=None):
     wp, wn = _ws(ws)
     _check("glr_debug_match_scores", lib.glr_debug_match_scores(_ptr(x), ctypes.byref(im), _ptr(keys), _ptr(n_found),
                                                                 int(N), int(K), _ptr(scores), wp, wn, _stream(stream)))
+    return scores
+
+
+def debug_proposal_scores(x, P, keys, n_found, K, encoder, emb_format="bf16", *, k_over=0, ws=None, stream=None):
+    """Raw scores of the learned proposal's scan (BF16 or E4M3 embedding operands) of every key
+    against the first 256 positions (testing aid)."""
+    lib = L.load()
+    im = images_of(x, P)
+    N = keys.shape[1]
+    npad = (N + 127) // 128 * 128
+    fmt = {"bf16": 0, "e4m3": 1, "fp8": 1}.get(emb_format, emb_format)
+    scores = torch.full((x.shape[0], npad, 256), float("nan"), dtype=torch.float32, device=x.device)
+    if ws is None:
+        ws = workspace(L.GLR_OP_MATCH, im, N, K, match_opts("learned", k_over, encoder=encoder, bound_pass=2,
+                                                           emb_format=fmt), x.device)
+    wp, wn = _ws(ws)
+    _check("glr_debug_proposal_scores", lib.glr_debug_proposal_scores(
+        _ptr(x), ctypes.byref(im), _ptr(keys), _ptr(n_found), int(N), int(K), _ptr(encoder), int(fmt), _ptr(scores),
+        wp, wn, _stream(stream)))
     return scores
 
 
@@ -401,7 +422,7 @@ class GlrDenoiser:
     def __init__(self, shape: GlrShape, mode: str = "bf16", edge_th: float = 0.1, k_over: int = 0, splits: int = 0,
                  device="cuda", cap: int = 0, epi_batch: int = 0, complex_: bool = False, n_uniform: int = 0,
                  window: int = 20, fused: bool = False, bound_pass: int = 0, frames_per_call: int = 0,
-                 encoder: torch.Tensor | None = None):
+                 encoder: torch.Tensor | None = None, emb_format: str = "bf16"):
         """fused (real images, d <= 64, K <= 64): grouping, WNNM and aggregation in one kernel pass
         (glr_lowrank_aggregate): no group buffer (1 GB less on the 16 x 512^2 workload) but slower
         there (27.7 ms against 23.5 ms for the separate kernels on the GAP start image: the fused
@@ -418,7 +439,8 @@ class GlrDenoiser:
         self.n_uniform, self.window = n_uniform, window
         can_fuse = not complex_ and s.C * s.P * s.P <= 64 and s.K <= 64
         self.fused = fused and can_fuse
-        self.opts = match_opts(mode, k_over, splits, cap, None, epi_batch, edge_th, window, bound_pass)
+        self.emb_format = emb_format
+        self.opts = match_opts(mode, k_over, splits, cap, None, epi_batch, edge_th, window, bound_pass, emb_format)
         self.k_over, self.splits, self.cap, self.epi_batch = k_over, splits, cap, epi_batch
         self.bound_pass = bound_pass
         im = images(self.fpc, s.C, s.H, s.W, s.P)
@@ -457,8 +479,8 @@ class GlrDenoiser:
                     n_corner=nc, ws=self.ws_select, stream=stream)
         match_topk(x, s.P, keys, nf, s.K, self.mode, k_over=self.k_over, splits=self.splits,
                    cap=self.cap, encoder=self.encoder, epi_batch=self.epi_batch, edge_th=self.edge_th,
-                   window=self.window, bound_pass=self.bound_pass, idx=idx, dist=dist, ws=self.ws_match,
-                   stream=stream)
+                   window=self.window, bound_pass=self.bound_pass, emb_format=self.emb_format, idx=idx, dist=dist,
+                   ws=self.ws_match, stream=stream)
         if self.fused:
             return lowrank_aggregate(x, s.P, idx, nf, sigma_w, c_wnnm, out=out, rank=rank, ws=self.ws_agg,
                                      stream=stream)
@@ -473,13 +495,13 @@ class SciReconstructor:
 
     def __init__(self, T, H, W, P, N, K, mode="bf16", edge_th=0.1, accelerate=False, k_over=0, splits=0,
                  device="cuda", cap=0, epi_batch=0, admm_rho=0.0, n_uniform=0, window=20, bound_pass=0,
-                 frames_per_call=0, encoder=None):
+                 frames_per_call=0, encoder=None, emb_format="bf16"):
         """admm_rho > 0: ADMM (z = D(x + u), u += x - z, x = the data step) instead of GAP;
         n_uniform > 0: corner + uniform key mix; frames_per_call, encoder: see GlrDenoiser."""
         self.T, self.H, self.W = T, H, W
         self.den = GlrDenoiser(GlrShape(T, 1, H, W, P, N, K), mode, edge_th, k_over, splits, device, cap, epi_batch,
                                n_uniform=n_uniform, window=window, bound_pass=bound_pass,
-                               frames_per_call=frames_per_call, encoder=encoder)
+                               frames_per_call=frames_per_call, encoder=encoder, emb_format=emb_format)
         self.accelerate = accelerate
         self.rho = admm_rho
         self.x = torch.empty((1, T, H, W), dtype=torch.float32, device=device)

@@ -65,3 +65,42 @@ def test_adamw_first_step_closed_form():
     want_b = params["b1"] - lr * grads["b1"] / (np.abs(grads["b1"]) + eps)
     assert np.allclose(p1["W1"], want_W) and np.allclose(p1["b1"], want_b)
     assert np.allclose(m1["W1"], 0.1 * grads["W1"]) and np.allclose(v1["b1"], 0.001 * grads["b1"] ** 2)
+
+
+# ---- E4M3 rounding of the 8-bit proposal operands (pinned to the format's definition)
+def _codes_positive():
+    return [c for c in range(0x00, 0x7F)]  # 0x7F is NaN
+
+
+def test_e4m3_every_finite_code_rounds_to_itself():
+    vals = np.array([E.e4m3_decode(c) for c in _codes_positive()] + [E.e4m3_decode(0x80 | c) for c in _codes_positive()])
+    np.testing.assert_array_equal(E.e4m3_round(vals), vals)
+    assert E.e4m3_decode(0x7E) == 448.0 and E.e4m3_decode(0x01) == 2.0**-9 and E.e4m3_decode(0x38) == 1.0
+    assert np.isnan(E.e4m3_decode(0x7F)) and np.isnan(E.e4m3_decode(0xFF))
+
+
+def test_e4m3_midpoints_round_to_the_even_code():
+    codes = _codes_positive()
+    vals = [E.e4m3_decode(c) for c in codes]
+    for c in range(len(codes) - 1):
+        lo, hi = vals[c], vals[c + 1]
+        mid = 0.5 * (lo + hi)
+        want = lo if codes[c] % 2 == 0 else hi  # the even mantissa (lowest code bit 0)
+        assert E.e4m3_round(mid) == want, (codes[c], lo, hi)
+        assert E.e4m3_round(-mid) == -want
+        # just off the midpoint: the nearer neighbour
+        assert E.e4m3_round(mid - 1e-6 * (hi - lo)) == lo
+        assert E.e4m3_round(mid + 1e-6 * (hi - lo)) == hi
+
+
+def test_e4m3_saturates_and_flushes_below_half_the_smallest_subnormal():
+    np.testing.assert_array_equal(E.e4m3_round([448.0, 464.0, 1e6, -1e6]), [448.0, 448.0, 448.0, -448.0])
+    np.testing.assert_array_equal(E.e4m3_round([2.0**-11, -(2.0**-11)]), [0.0, 0.0])
+
+
+def test_e4m3_scale_is_the_largest_fitting_power_of_two():
+    rng = np.random.default_rng(5)
+    for n2 in np.exp(rng.uniform(-10, 12, 200)):
+        s = E.e4m3_scale(n2)
+        assert np.log2(s) == np.round(np.log2(s))
+        assert s * s * n2 <= 384.0 < 4 * s * s * n2

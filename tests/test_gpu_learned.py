@@ -16,18 +16,139 @@ def _params_dict(flat):
     return {"W1": f[:4096].reshape(64, 64), "b1": f[4096:4160], "W2": f[4160:5184].reshape(16, 64), "b2": f[5184:5200]}
 
 
+def _bf16(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+
+
+def _f16(a):
+    return np.asarray(a, np.float64).astype(np.float16).astype(np.float64)
+
+
 def test_embed_matches_oracle_forward():
+    """The tensor-core encoder: FP16 patches, weights and hidden units, FP32 accumulation and
+    biases.  The oracle forward with the same roundings (patches and weights before, hidden
+    units after the ReLU) agrees to FP32 accumulation order, except where a hidden unit sits on
+    an FP16 rounding boundary (then one FP16 step of that unit)."""
     rng = synth.rng_for("enc-embed")
     x = synth.textured_frames(rng, 2, 40, 44)[:, None]
     enc = glr.Encoder(seed=3)
-    enc.params.add_(torch.randn_like(enc.params) * 0.05)  # non-zero biases too
+    noise = np.random.default_rng(3).standard_normal(enc.params.numel()).astype(np.float32) * 0.05
+    enc.params.add_(torch.from_numpy(noise).cuda())  # non-zero biases too
     emb = enc.embed(torch.from_numpy(x).cuda(), 8).cpu().numpy()
-    p16 = enc.params.cpu().numpy().astype(np.float16).astype(np.float64)  # inference rounds weights to FP16
+    pf = enc.params.cpu().numpy().astype(np.float64)
+    prm = _params_dict(pf)
+    prm["W1"], prm["W2"] = _f16(prm["W1"]), _f16(prm["W2"])
     for f in range(2):
         mu = np.float32(np.float64(x[f]).mean())
-        Q = O.patch_matrix((x[f] - mu).astype(np.float32), 8)
-        want, _ = E.forward(_params_dict(p16), Q)
-        np.testing.assert_allclose(emb[f], want, rtol=1e-4, atol=1e-4)
+        Q = _f16(O.patch_matrix((x[f] - mu).astype(np.float32), 8))
+        Z = Q @ prm["W1"].T + prm["b1"]
+        Hh = _f16(np.maximum(Z, 0.0))
+        want = Hh @ prm["W2"].T + prm["b2"]
+        err = np.abs(emb[f] - want)
+        tol = 2e-6 * (np.abs(Hh) @ np.abs(prm["W2"]).T + np.abs(prm["b2"])) + 1e-6
+        # a hidden unit on an FP16 rounding boundary may round the other way: at most one FP16
+        # step of each unit
+        step = np.spacing(np.maximum(Hh, 2.0**-14).astype(np.float16)).astype(np.float64) * (Hh > 0)
+        assert np.all(err <= tol + step @ np.abs(prm["W2"]).T), err.max()
+        assert np.mean(np.all(err <= tol, axis=1)) > 0.97, np.mean(np.all(err <= tol, axis=1))
+
+
+def _exact_encoder_case():
+    """An image and encoder weights for which every value the tensor-core encoder computes is
+    exact: pixels 0.5 + r/256 with the r summing to zero (the image mean is exactly 0.5), four
+    +-1 inputs per hidden unit (FP16-exact sums), four +-1/2 hidden units per output and
+    biases on a 1/512 grid (FP32-exact outputs).  The embeddings are then known exactly."""
+    rng = np.random.default_rng(11)
+    H, W, P = 40, 300, 8
+    half = rng.integers(1, 100, H * W // 2)
+    r = np.concatenate([half, -half])
+    rng.shuffle(r)
+    x = (0.5 + r / 256.0).reshape(1, 1, H, W).astype(np.float32)
+    W1 = np.zeros((64, 64))
+    for j in range(64):
+        W1[j, rng.choice(64, 4, replace=False)] = rng.choice([-1.0, 1.0], 4)
+    b1 = rng.integers(-8, 9, 64) / 256.0
+    W2 = np.zeros((16, 64))
+    for o in range(16):
+        W2[o, rng.choice(64, 4, replace=False)] = rng.choice([-0.5, 0.5], 4)
+    b2 = rng.integers(-64, 65, 16) / 512.0
+    flat = np.concatenate([W1.ravel(), b1, W2.ravel(), b2]).astype(np.float32)
+    Q = O.patch_matrix(x[0] - 0.5, P)  # exact
+    E_ = np.maximum(Q @ W1.T + b1, 0.0) @ W2.T + b2
+    npos = Q.shape[0]
+    keys = rng.choice(npos, 200, replace=False).astype(np.int32)
+    return x, P, flat, E_, keys
+
+
+def _f32_sumsq(A):
+    """sum_j a_j^2 as a chain of FP32 fused multiply-adds over j (each step rounded once)."""
+    n = np.zeros(A.shape[0], np.float32)
+    for j in range(A.shape[1]):
+        n = (A[:, j].astype(np.float64) ** 2 + n.astype(np.float64)).astype(np.float32)
+    return n.astype(np.float64)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_proposal_raw_scores_against_host(fmt):
+    """The proposal scan's raw scores (operand packing, per-call scale, norm terms, TMA layout and
+    the kind::f16 / kind::f8f6f4 contraction) against the same quantities formed on the host
+    from exactly known embeddings: sum_j a_q,j b_p,j + the three norm terms of q + those of p."""
+    x, P, flat, E_, keys = _exact_encoder_case()
+    N = len(keys)
+    if fmt == "e4m3":
+        n2 = _f32_sumsq(E_)
+        t = np.log2(np.sqrt(384.0 / n2.max()))
+        assert abs(t - np.round(t)) > 1e-4  # the scale does not sit on a rounding boundary
+        s = E.e4m3_scale(n2.max())
+        A = E.e4m3_round(s * E_)
+        Bk = E.e4m3_round(-2.0 * A[keys])
+        rnd = E.e4m3_round
+    else:
+        A = _bf16(E_)
+        Bk = -2.0 * A[keys]
+        rnd = _bf16
+    n = _f32_sumsq(A)
+    hi = rnd(n)
+    r1 = (n - hi).astype(np.float32).astype(np.float64)
+    mid = rnd(r1)
+    lo = rnd((r1 - mid).astype(np.float32).astype(np.float64))
+    sc = glr.debug_proposal_scores(torch.from_numpy(x).cuda(), P, torch.from_numpy(keys[None]).cuda(),
+                                   torch.tensor([N], dtype=torch.int32).cuda(), 16,
+                                   torch.from_numpy(flat).cuda(), fmt)
+    torch.cuda.synchronize()
+    sc = sc.cpu().numpy()[0, :N, :]
+    terms = Bk[:, None, :] * A[None, :256, :]
+    norms = hi + mid + lo  # ||a_q||^2 of every position; a key carries its own position's terms
+    want = terms.sum(2) + norms[None, :256] + norms[keys][:, None]
+    nmag = np.abs(hi) + np.abs(mid) + np.abs(lo)
+    mag = np.abs(terms).sum(2) + nmag[None, :256] + nmag[keys][:, None]
+    err = np.abs(sc - want)
+    assert np.all(err <= 4 * 2.0**-24 * mag + 1e-30), (err.max(), np.argmax(err))
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_learned_results_are_exact_distances(fmt):
+    """Whatever the proposal picks, the results are exact: every returned distance is the FP64
+    distance of its position within FP32 rounding, rows ascend without repeats, and each key
+    finds its own position (score -||a_p||^2, the smallest possible) at distance 0."""
+    rng = synth.rng_for("learned-exact")
+    F, H, W, P, N, K = 2, 72, 90, 8, 150, 24
+    x = synth.textured_frames(rng, F, H, W)[:, None].astype(np.float32)
+    npos = (H - P + 1) * (W - P + 1)
+    keys = np.stack([rng.choice(npos, size=N, replace=False) for _ in range(F)]).astype(np.int32)
+    enc = glr.Encoder(seed=2)
+    idx, dist = glr.match_topk(torch.from_numpy(x).cuda(), P, torch.from_numpy(keys).cuda(),
+                               torch.full((F,), N, dtype=torch.int32).cuda(), K, "learned", encoder=enc.params,
+                               emb_format=fmt)
+    torch.cuda.synchronize()
+    idx, dist = idx.cpu().numpy(), dist.cpu().numpy()
+    for f in range(F):
+        Q = O.patch_matrix(x[f], P)
+        for i in range(N):
+            d = ((Q[idx[f, i]] - Q[keys[f, i]]) ** 2).sum(1)
+            np.testing.assert_allclose(dist[f, i], d, rtol=2e-6, atol=1e-6)
+            assert np.all(np.diff(dist[f, i]) >= 0) and len(set(idx[f, i])) == K
+            assert dist[f, i, 0] == 0.0
 
 
 def test_train_step_loss_and_gradient_match_oracle():
