@@ -511,11 +511,14 @@ __device__ int warp_keep_smallest_kth(unsigned long long* list, int n, int k, un
 
 // Bound and candidate chunks of every key for the exact evaluation (one warp per key, many
 // warps per SM to hide the memory latency).
-//  * Each lane keeps the L smallest of its share of the key's rounded-up 16-bit chunk minima
-//    (pairs of adjacent chunks, interleaved over the lanes) in registers; the K'-th smallest of
-//    those 32 L values is tau16.  It bounds the K'-th smallest of all the minima from above (the
-//    K'-th smallest of a subset is never smaller), so every chunk that holds one of the key's K'
-//    smallest BF16 scores has its minimum at or below tau16; it equals the exact K'-th smallest
+//  * Each lane keeps the L smallest of its share of the key's 16-bit chunk minima (the upper
+//    half of each minimum's order key; pairs of adjacent chunks, interleaved over the lanes) in
+//    registers; the K'-th smallest of those 32 L values is tau16.  It bounds the K'-th smallest
+//    of all the 16-bit minima from above (the K'-th smallest of a subset is never smaller).  If
+//    M is the K'-th smallest chunk minimum, K' chunks have minima <= M, so at least K' scores
+//    are <= M and every chunk holding one of the key's K' smallest scores has its minimum <= M;
+//    truncating the keys keeps that order, so those chunks are at or below tau16, and M lies at
+//    or below the upper end of tau16's 2^16-key bucket.  tau16 equals the exact K'-th smallest
 //    unless a lane's share holds more than L of the K' smallest.
 //  * Then the ids of every chunk at or below tau16, ascending (the first clcap of them; ccount
 //    receives the full count).
@@ -706,8 +709,8 @@ __device__ void exact_topk_finish(unsigned long long* list, int cnt, const float
 }
 
 // Candidate chunks of the chunk-minima scan, evaluated exactly.  One warp per key:
-//  1. tau = the K'-th smallest rounded-up chunk minimum of the key (every chunk holding one of
-//     the key's K' smallest BF16 scores has its minimum at or below tau);
+//  1. tau = the upper end of the bucket of the key's K'-th smallest 16-bit chunk minimum (every
+//     chunk holding one of the key's K' smallest BF16 scores has its minimum at or below tau);
 //  2. every chunk with minimum <= tau (in position order, 4 chunks at a time: the image strips
 //     of the 4 chunks staged in shared memory, each lane scoring 4 adjacent positions from
 //     registers) gets the FP32 score ||q - mu||^2 - 2 <p - mu, q> (the squared distance of the
@@ -923,7 +926,7 @@ __global__ void __launch_bounds__(CT_WARPS * 32, 4)
   }
 }
 
-// Learned proposal, after the embedding scan: every chunk whose rounded-up minimum is at or
+// Learned proposal, after the embedding scan: every chunk whose 16-bit minimum is at or
 // below the key's K'-th smallest (k_tau_chunk<24>; they hold the key's K' smallest scan
 // scores) is scored again in FP32 from the same operand values,
 //   sc = sum_j a_q,j (a_q,j + b_p,j) = ||a_p - a_q||^2 - ||a_p||^2   (the scan's score up to
@@ -1252,7 +1255,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
     // rows, where the candidate appends cost more than a second contraction; off for
     // chunked rows (d > 74), where the contraction itself dominates
     if (chunk) {
-      pl.bound_pass = 2;  // rounded-up 16-bit minima of every 32-position chunk
+      pl.bound_pass = 2;  // 16-bit minima of every 32-position chunk
       pl.mins_off = L.take((size_t)im.n_img * pl.Npad * 8 * pl.pos_tiles * 2);
       pl.ccnt_off = L.take((size_t)im.n_img * pl.Npad * 4);
       pl.clist_off = L.take((size_t)im.n_img * pl.Npad * (emb_chunk ? CT_CL_EMB : CT_CL) * 4);

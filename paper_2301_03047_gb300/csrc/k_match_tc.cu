@@ -543,36 +543,6 @@ __global__ void __launch_bounds__(256) k_seed_bounds(const __nv_bfloat16* __rest
   }
 }
 
-// One visit of an epilogue thread to its row's half tile in tensor memory (128 columns,
-// positions q0 ..): the minimum of every 32-position chunk as the upper 16 bits of its order
-// key rounded up (never below the true minimum; positions >= npos left out), four chunks
-// packed in 8 bytes at dst.  The accumulator buffer goes back to the MMA warp as soon as it
-// is read.  dump_row != nullptr: the 128 raw scores are copied there as well.
-__device__ __forceinline__ void chunk_minima_visit(uint32_t taddr, long long q0, long long npos, uint64_t* tempty_b,
-                                                   int lane, uint2* dst, float* dump_row) {
-  float w[4][32];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) tmem_ld_32x32_nowait(taddr + 32 * c, w[c]);
-  tmem_ld_wait();
-  tc_fence_before();
-  __syncwarp();
-  if (lane == 0) mbar_arrive(tempty_b);
-  if (dump_row != nullptr) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int j = 0; j < 32; ++j) dump_row[32 * c + j] = w[c][j];
-  }
-  uint32_t k16[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int nvalid = (int)max(0LL, min(32LL, npos - (q0 + 32 * c)));
-    const uint32_t k32 = float_order_key(stream_min(w[c], nvalid));
-    k16[c] = min((k32 >> 16) + ((k32 & 0xffffu) != 0u ? 1u : 0u), 0xffffu);
-  }
-  *dst = make_uint2(k16[0] | (k16[1] << 16), k16[2] | (k16[3] << 16));
-}
-
 template <int EB, bool WIDE, int MINS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_match_tc(const __grid_constant__ CUtensorMap tm_qmain, const __grid_constant__ CUtensorMap tm_qaux,
@@ -584,9 +554,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // MINS = 1: bound pass.  No candidate is kept; each epilogue lane writes the minimum
   // score of its row over every half tile (128 positions) to mins[key][2 tile + half]
   // instead (all four 32-column chunks read from TMEM in one visit).
-  // MINS = 2: chunk-minima scan.  The minimum of every 32-position chunk, as the upper
-  // 16 bits of its order key rounded up (so it is never below the true minimum), four
-  // chunks of a half tile packed in 8 bytes: mins viewed as uint16 [key][8 tile + 4 half + c].
+  // (the chunk-minima scan of bound_pass 2 is k_match_chunk)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t kBar = WIDE ? W_OFF_BAR : OFF_BAR, kMisc = WIDE ? W_OFF_MISC : OFF_MISC;
@@ -786,13 +754,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) break;
       tc_fence_after();
       const long long tile_q0 = (long long)(t_begin + i) * TC_N;
-      if constexpr (MINS == 2) {
-        chunk_minima_visit(tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128),
-                           tile_q0 + h * 128, npos, tempty + b, lane,
-                           reinterpret_cast<uint2*>(mins) + (((long long)f * Npad + key) * ntiles + t_begin + i) * 2 + h,
-                           nullptr);
-        continue;
-      } else if constexpr (MINS == 1) {
+      if constexpr (MINS == 1) {
         float w[4][32], v[128];
         const uint32_t taddr = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128);
 #pragma unroll
@@ -1133,15 +1095,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // the squared distance of the rounded embeddings (scaled by s^2 for E4M3), so the 16-bit
 // chunk minima resolve it relative to the distance itself.
 constexpr int EMB_COLS = 32;
-constexpr int EMB_STAGES = 8;
-constexpr uint32_t EMB_A_BYTES = TC_M * 64;          // 8 KB: two 4 KB chunks (BF16) or one (E4M3)
-constexpr uint32_t EMB_STAGE_BYTES = TC_N * 64;      // 16 KB: two 8 KB chunks (BF16) or one (E4M3)
-constexpr uint32_t EMB_OFF_B = EMB_A_BYTES;
-constexpr uint32_t EMB_OFF_BAR = EMB_OFF_B + EMB_STAGES * EMB_STAGE_BYTES;
-constexpr int EMB_NBAR = 2 * EMB_STAGES + 4 + 2;
-constexpr uint32_t EMB_OFF_MISC = EMB_OFF_BAR + EMB_NBAR * 8;
-constexpr uint32_t EMB_SMEM = EMB_OFF_MISC + 64 + 1024;
-static_assert(EMB_SMEM <= 232448, "shared memory budget (proposal scan)");
 
 __device__ __forceinline__ float emb_scale(const unsigned* n2max) {
   const float m = __uint_as_float(*n2max);
@@ -1263,41 +1216,76 @@ __global__ void __launch_bounds__(256) k_pack_emb_keys(const float* __restrict__
   }
 }
 
-// The proposal scan: CTA = 128 keys x one split of the positions, 320 threads as in
-// k_match_tc (producer, MMA issuer, 8 epilogue warps), an 8-stage ring of position tiles
-// (the contraction of a tile is one E4M3 or two BF16 instructions, so the ring is deeper),
-// and the chunk-minima epilogue: the minimum score of every 32-position chunk per key,
-// rounded up to 16 bits (mins viewed as uint16 [key][8 tile + 4 half + c]).
-template <bool FP8>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_match_emb(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_k, int Npad,
-                long long npos, long long npos_pad, int tiles_per_split, int ntiles, unsigned long long wait_ns,
-                StatusBlock* st, float* __restrict__ dump, uint2* __restrict__ mins) {
+// Chunk-minima scans (bound_pass 2) of both the exact BF16 matcher and the learned proposal:
+// CTA = 128 keys x one split of the positions, 320 threads: warp 0 = TMA producer (one
+// thread), warp 1 = TMEM allocator and MMA issuer (one thread), warps 2-9 = epilogue (warps
+// w and w + 4 share a TMEM lane quadrant and take one column half each).  Position tiles are
+// NT wide and tensor memory holds 512 / NT accumulators: each tile's handshake (MMA commit ->
+// epilogue reads -> buffer released -> next MMA into it) is a chain of barrier wake-ups, and
+// more buffers in flight overlap more of those chains.  Operand forms:
+//   CF_PATCH      BF16 rows of 64 patch columns (128-byte swizzle) + 16 norm columns
+//                 (32-byte swizzle): 4 + 1 kind::f16 MMAs per tile
+//   CF_EMB_BF16   BF16 embedding rows of 32 columns as two 32-byte swizzled chunks:
+//                 2 kind::f16 MMAs per tile
+//   CF_EMB_E4M3   E4M3 embedding rows of 32 bytes: 1 kind::f8f6f4 MMA per tile
+// Minima: the upper 16 bits of the order key of each 32-position chunk minimum (the key
+// truncated), mins viewed as uint16 [key][chunk] (chunk = position / 32).
+constexpr int CF_PATCH = 0, CF_EMB_BF16 = 1, CF_EMB_E4M3 = 2;
+constexpr int kChunkNT = 256;  // position tile of the chunk-minima scans (128 measured slower)
+constexpr int CH_EPI_WARPS = 8;
+constexpr int CH_THREADS = 64 + CH_EPI_WARPS * 32;
+template <int FORM, int NT>
+struct ChunkForm {
+  static constexpr int nbuf = 512 / NT;  // accumulators in tensor memory
+  static constexpr uint32_t a_main = FORM == CF_PATCH ? A_MAIN_BYTES : (FORM == CF_EMB_BF16 ? 4096 : 4096);
+  static constexpr uint32_t a_bytes = FORM == CF_PATCH ? A_MAIN_BYTES + A_AUX_BYTES : (FORM == CF_EMB_BF16 ? 8192 : 4096);
+  static constexpr uint32_t b_main = FORM == CF_PATCH ? NT * 128 : NT * 32;  // first column chunk of a tile
+  static constexpr uint32_t b_bytes = FORM == CF_PATCH ? NT * 160 : (FORM == CF_EMB_BF16 ? NT * 64 : NT * 32);
+  static constexpr int stages = (FORM == CF_PATCH ? 160 * 1024 : 128 * 1024) / (int)b_bytes < 16
+                                    ? (FORM == CF_PATCH ? 160 * 1024 : 128 * 1024) / (int)b_bytes
+                                    : 16;
+  static constexpr uint32_t off_b = (a_bytes + 1023) / 1024 * 1024;
+  static constexpr uint32_t off_bar = off_b + stages * b_bytes;
+  static constexpr uint32_t off_misc = off_bar + (2 * stages + 2 * nbuf + 2) * 8;
+  static constexpr uint32_t smem = off_misc + 64 + 1024;
+};
+static_assert(ChunkForm<CF_PATCH, 128>::smem <= 232448 && ChunkForm<CF_PATCH, 256>::smem <= 232448, "smem budget");
+static_assert(ChunkForm<CF_EMB_BF16, 128>::smem <= 232448, "smem budget");
+
+template <int FORM, int NT>
+__global__ void __launch_bounds__(CH_THREADS, 1)
+    k_match_chunk(const __grid_constant__ CUtensorMap tm_qmain, const __grid_constant__ CUtensorMap tm_qaux,
+                  const __grid_constant__ CUtensorMap tm_kmain, const __grid_constant__ CUtensorMap tm_kaux,
+                  int Npad, long long npos, long long npos_pad, int tiles_per_split, int ntiles,
+                  unsigned long long wait_ns, StatusBlock* st, float* __restrict__ dump,
+                  uint16_t* __restrict__ mins) {
+  using CF = ChunkForm<FORM, NT>;
+  constexpr int NST = CF::stages, NB = CF::nbuf, CPW = NT / 64;  // chunks per epilogue thread and tile
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  constexpr uint32_t kChunkA = TC_M * 32, kChunkB = TC_N * 32;  // one 32-byte column chunk of a tile
-  constexpr uint32_t kBytesA = FP8 ? kChunkA : 2 * kChunkA, kBytesB = FP8 ? kChunkB : 2 * kChunkB;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + EMB_OFF_BAR);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CF::off_bar);
   uint64_t* full = bars;
-  uint64_t* empty = bars + EMB_STAGES;
-  uint64_t* tfull = bars + 2 * EMB_STAGES;
-  uint64_t* tempty = tfull + 2;
-  uint64_t* a_full = tempty + 2;
+  uint64_t* empty = bars + NST;
+  uint64_t* tfull = bars + 2 * NST;
+  uint64_t* tempty = tfull + NB;
+  uint64_t* a_full = tempty + NB;
   uint64_t* mma_done = a_full + 1;
-  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(smem + EMB_OFF_MISC);
-  volatile int* abort_s = reinterpret_cast<volatile int*>(smem + EMB_OFF_MISC + 4);
+  uint32_t* tmem_base_s = reinterpret_cast<uint32_t*>(smem + CF::off_misc);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(smem + CF::off_misc + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kt = blockIdx.x, f = blockIdx.y, split = blockIdx.z;
-  const int t_begin = split * tiles_per_split;
-  const int nt = max(0, min(ntiles, t_begin + tiles_per_split) - t_begin);
+  // tiles_per_split and ntiles count 256-position tiles; this kernel walks NT-position tiles
+  constexpr int R = 256 / NT;
+  const int t_begin = split * tiles_per_split * R;
+  const int nt = max(0, min(ntiles * R, t_begin + tiles_per_split * R) - t_begin);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < EMB_STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NB; ++b) {
       mbar_init(tfull + b, 1);
-      mbar_init(tempty + b, TC_EPI_WARPS);
+      mbar_init(tempty + b, CH_EPI_WARPS);
     }
     mbar_init(a_full, 1);
     mbar_init(mma_done, 1);
@@ -1316,49 +1304,58 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       // ---------------------------------------------------------- producer
       const int arow = f * Npad + kt * TC_M;
-      mbar_arrive_expect_tx(a_full, kBytesA);
-      tma_load_2d(&tm_k, a_full, smem, 0, arow);
-      if (!FP8) tma_load_2d(&tm_k, a_full, smem + kChunkA, 16, arow);
+      mbar_arrive_expect_tx(a_full, CF::a_bytes);
+      tma_load_2d(&tm_kmain, a_full, smem, 0, arow);
+      if constexpr (FORM == CF_PATCH) tma_load_2d(&tm_kaux, a_full, smem + CF::a_main, 0, arow);
+      if constexpr (FORM == CF_EMB_BF16) tma_load_2d(&tm_kmain, a_full, smem + CF::a_main, 16, arow);
       int issued = 0;
       for (int i = 0; i < nt; ++i) {
-        const int s = i % EMB_STAGES;
-        const uint32_t ph = (uint32_t)(i / EMB_STAGES) & 1u;
+        const int s = i % NST;
+        const uint32_t ph = (uint32_t)(i / NST) & 1u;
         if (!mbar_wait(empty + s, ph ^ 1u, abort_s, st, true, wait_ns)) break;
-        mbar_arrive_expect_tx(full + s, kBytesB);
-        const int brow = (int)(f * npos_pad + (long long)(t_begin + i) * TC_N);
-        uint8_t* sb = smem + EMB_OFF_B + s * EMB_STAGE_BYTES;
-        tma_load_2d(&tm_q, full + s, sb, 0, brow);
-        if (!FP8) tma_load_2d(&tm_q, full + s, sb + kChunkB, 16, brow);
+        mbar_arrive_expect_tx(full + s, CF::b_bytes);
+        const int brow = (int)(f * npos_pad + (long long)(t_begin + i) * NT);
+        uint8_t* sb = smem + CF::off_b + s * CF::b_bytes;
+        tma_load_2d(&tm_qmain, full + s, sb, 0, brow);
+        if constexpr (FORM == CF_PATCH) tma_load_2d(&tm_qaux, full + s, sb + CF::b_main, 0, brow);
+        if constexpr (FORM == CF_EMB_BF16) tma_load_2d(&tm_qmain, full + s, sb + CF::b_main, 16, brow);
         issued = i + 1;
       }
       // teardown: every issued copy has landed before the CTA may exit
       mbar_wait(a_full, 0, abort_s, st, false);
-      for (int i = max(0, issued - EMB_STAGES); i < issued; ++i)
-        mbar_wait(full + (i % EMB_STAGES), (uint32_t)(i / EMB_STAGES) & 1u, abort_s, st, false);
+      for (int i = max(0, issued - NST); i < issued; ++i)
+        mbar_wait(full + (i % NST), (uint32_t)(i / NST) & 1u, abort_s, st, false);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // --------------------------------------------------------- MMA issuer
-      constexpr uint32_t idesc = FP8 ? idesc_e4m3(TC_M, TC_N) : idesc_bf16(TC_M, TC_N);
+      constexpr uint32_t idesc = FORM == CF_EMB_E4M3 ? idesc_e4m3(TC_M, NT) : idesc_bf16(TC_M, NT);
       const uint32_t sa = smem_u32(smem);
       bool ok = mbar_wait(a_full, 0, abort_s, st, true, wait_ns);
       tc_fence_after();
       for (int i = 0; ok && i < nt; ++i) {
-        const int s = i % EMB_STAGES;
-        const uint32_t ph = (uint32_t)(i / EMB_STAGES) & 1u;
-        const int b = i & 1;
-        const uint32_t bph = (uint32_t)(i >> 1) & 1u;
+        const int s = i % NST;
+        const uint32_t ph = (uint32_t)(i / NST) & 1u;
+        const int b = i % NB;
+        const uint32_t bph = (uint32_t)(i / NB) & 1u;
         if (!mbar_wait(full + s, ph, abort_s, st, true, wait_ns)) break;
         if (!mbar_wait(tempty + b, bph ^ 1u, abort_s, st, true, wait_ns)) break;
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(b * TC_N);
-        const uint32_t sb = smem_u32(smem + EMB_OFF_B + s * EMB_STAGE_BYTES);
-        if constexpr (FP8) {
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * NT);
+        const uint32_t sb = smem_u32(smem + CF::off_b + s * CF::b_bytes);
+        if constexpr (FORM == CF_PATCH) {
+#pragma unroll
+          for (int k = 0; k < DK_MAIN / 16; ++k)
+            mma_f16(d_tmem, smem_desc(sa + 32 * k, 1024, LAYOUT_SW128), smem_desc(sb + 32 * k, 1024, LAYOUT_SW128),
+                    idesc, k > 0 ? 1u : 0u);
+          mma_f16(d_tmem, smem_desc(sa + CF::a_main, 256, LAYOUT_SW32), smem_desc(sb + CF::b_main, 256, LAYOUT_SW32),
+                  idesc, 1u);
+        } else if constexpr (FORM == CF_EMB_E4M3) {
           mma_e4m3(d_tmem, smem_desc(sa, 256, LAYOUT_SW32), smem_desc(sb, 256, LAYOUT_SW32), idesc, 0u);
         } else {
           mma_f16(d_tmem, smem_desc(sa, 256, LAYOUT_SW32), smem_desc(sb, 256, LAYOUT_SW32), idesc, 0u);
-          mma_f16(d_tmem, smem_desc(sa + kChunkA, 256, LAYOUT_SW32), smem_desc(sb + kChunkB, 256, LAYOUT_SW32), idesc,
-                  1u);
+          mma_f16(d_tmem, smem_desc(sa + CF::a_main, 256, LAYOUT_SW32), smem_desc(sb + CF::b_main, 256, LAYOUT_SW32),
+                  idesc, 1u);
         }
         mma_commit(empty + s);
         mma_commit(tfull + b);
@@ -1369,22 +1366,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else {
     // ------------------------------------------------------------- epilogue
-    const int e = warp - 2;
-    const int quad = warp & 3;
-    const int h = e >> 2;
+    const int quad = warp & 3;        // TMEM lane quadrant this warp may read
+    const int h = (warp - 2) >> 2;    // column half of the tile: NT / 2 positions, CPW chunks
     const int key = kt * TC_M + 32 * quad + lane;
+    const uint32_t taddr0 = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(h * (NT / 2));
+    uint16_t* mrow = mins + ((long long)f * Npad + key) * ntiles * 8 + h * CPW;
     for (int i = 0; i < nt; ++i) {
-      const int b = i & 1;
-      const uint32_t bph = (uint32_t)(i >> 1) & 1u;
+      const int b = i % NB;
+      const uint32_t bph = (uint32_t)(i / NB) & 1u;
       if (!__all_sync(0xffffffffu, mbar_wait(tfull + b, bph, abort_s, st, true, wait_ns))) break;
       tc_fence_after();
-      const long long tile_q0 = (long long)(t_begin + i) * TC_N;
-      float* dump_row = (dump != nullptr && i == 0 && t_begin == 0)
-                            ? dump + ((long long)f * Npad + key) * TC_N + h * 128
-                            : nullptr;
-      chunk_minima_visit(tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * TC_N + h * 128),
-                         tile_q0 + h * 128, npos, tempty + b, lane,
-                         mins + (((long long)f * Npad + key) * ntiles + t_begin + i) * 2 + h, dump_row);
+      float w[CPW][32];
+#pragma unroll
+      for (int c = 0; c < CPW; ++c) tmem_ld_32x32_nowait(taddr0 + (uint32_t)(b * NT + 32 * c), w[c]);
+      tmem_ld_wait();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty + b);
+      const long long q0 = (long long)(t_begin + i) * NT + h * (NT / 2);
+      if (dump != nullptr && q0 < TC_N) {  // raw scores of the first 256 positions
+        float* dr = dump + ((long long)f * Npad + key) * TC_N + q0;
+#pragma unroll
+        for (int c = 0; c < CPW; ++c)
+#pragma unroll
+          for (int j = 0; j < 32; ++j) dr[32 * c + j] = w[c][j];
+      }
+      // the upper 16 bits of each chunk minimum's order key (truncation: monotone, so a key's
+      // K'-th smallest truncated minimum still bounds its candidate chunks); positions past the
+      // grid only occur in the last tile
+      uint32_t k16[CPW];
+      if (q0 + NT / 2 <= npos) {
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) k16[c] = float_order_key(min_tree3(w[c])) >> 16;
+      } else {
+#pragma unroll
+        for (int c = 0; c < CPW; ++c) {
+          const int nvalid = (int)max(0LL, min(32LL, npos - (q0 + 32 * c)));
+          k16[c] = float_order_key(stream_min(w[c], nvalid)) >> 16;
+        }
+      }
+      uint16_t* dst = mrow + (long long)(t_begin + i) * (NT / 32);
+      if constexpr (CPW == 4) {
+        *reinterpret_cast<uint2*>(dst) = make_uint2(k16[0] | (k16[1] << 16), k16[2] | (k16[3] << 16));
+      } else {
+        *reinterpret_cast<uint32_t*>(dst) = k16[0] | (k16[1] << 16);
+      }
     }
   }
   tc_fence_before();
@@ -1561,16 +1587,24 @@ glr_status launch_match_tc_impl(const float* x, const glr_images& im, const int3
   auto kmin = k_match_tc<4, false, 1>;
   if (pl.bound_pass == 2) {
     // chunk-minima scan only; the exact evaluation of the candidate chunks follows (k_match.cu)
-    auto kch = k_match_tc<4, false, 2>;
-    if (cudaFuncSetAttribute(kch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM) != cudaSuccess)
+    auto kch = k_match_chunk<CF_PATCH, kChunkNT>;
+    constexpr uint32_t smem = ChunkForm<CF_PATCH, kChunkNT>::smem;
+    CUtensorMap cq, cqa;  // position tiles of kChunkNT rows
+    if (!make_map(&cq, qmain, qrows, DK_MAIN, kChunkNT, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map(&cqa, qaux, qrows, DK_AUX, kChunkNT, CU_TENSOR_MAP_SWIZZLE_32B))
       return GLR_ECUDA;
+    if (cudaFuncSetAttribute(kch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return GLR_ECUDA;
+    int blocks_per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kch, CH_THREADS, smem) != cudaSuccess ||
+        blocks_per_sm != 1)  // all of TMEM: exactly one resident CTA per SM
+      return GLR_ENOTSUP;
     const long long npos = (long long)(im.H - im.P + 1) * (im.W - im.P + 1);
-    const StreamCfg cfg{pl.cap, pl.Kp, pl.finish, g_match_wait_ns > 0 ? g_match_wait_ns : kWaitNs};
     dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
     GLR_LAUNCH("k_match_tc_chunk", s,
-               kch<<<grid, TC_THREADS, TC_SMEM, s>>>(tq, tqa, tk, tka, n_found, pl.Npad, npos, pl.npos_pad, pl.splits,
-                                                     pl.tiles_per_split, pl.pos_tiles, 1, cfg, bufs, bufcnt, taugl, st,
-                                                     nullptr, mins));
+               kch<<<grid, CH_THREADS, smem, s>>>(cq, cqa, tk, tka, pl.Npad, npos, pl.npos_pad, pl.tiles_per_split,
+                                                 pl.pos_tiles, g_match_wait_ns > 0 ? g_match_wait_ns : kWaitNs, st,
+                                                 dump, reinterpret_cast<uint16_t*>(mins)));
     return GLR_OK;
   }
   if (pl.bound_pass &&
@@ -1713,22 +1747,23 @@ glr_status launch_match_emb(const glr_images& im, const int32_t* keys, const int
   const uint64_t qrows = (uint64_t)im.n_img * pl.npos_pad, krows = (uint64_t)im.n_img * pl.Npad;
   const CUtensorMapDataType dt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const uint32_t esz = fp8 ? 1 : 2, box_cols = fp8 ? 32 : 16;
-  if (!make_map(&tq, qop, qrows, EMB_COLS, TC_N, CU_TENSOR_MAP_SWIZZLE_32B, box_cols, dt, esz) ||
+  if (!make_map(&tq, qop, qrows, EMB_COLS, kChunkNT, CU_TENSOR_MAP_SWIZZLE_32B, box_cols, dt, esz) ||
       !make_map(&tk, kop, krows, EMB_COLS, TC_M, CU_TENSOR_MAP_SWIZZLE_32B, box_cols, dt, esz))
     return GLR_ECUDA;
-  auto kern = fp8 ? k_match_emb<true> : k_match_emb<false>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EMB_SMEM) != cudaSuccess)
+  auto kern = fp8 ? k_match_chunk<CF_EMB_E4M3, kChunkNT> : k_match_chunk<CF_EMB_BF16, kChunkNT>;
+  const uint32_t smem = fp8 ? ChunkForm<CF_EMB_E4M3, kChunkNT>::smem : ChunkForm<CF_EMB_BF16, kChunkNT>::smem;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return GLR_ECUDA;
   int blocks_per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, TC_THREADS, EMB_SMEM) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, CH_THREADS, smem) != cudaSuccess ||
       blocks_per_sm != 1)  // all of TMEM: exactly one resident CTA per SM
     return GLR_ENOTSUP;
   dim3 grid((unsigned)(pl.Npad / TC_M), (unsigned)im.n_img, (unsigned)pl.splits);
   GLR_LAUNCH("k_match_emb", s,
-             kern<<<grid, TC_THREADS, EMB_SMEM, s>>>(tq, tk, pl.Npad, npos, pl.npos_pad, pl.tiles_per_split,
-                                                     pl.pos_tiles, g_match_wait_ns > 0 ? g_match_wait_ns : kWaitNs,
-                                                     reinterpret_cast<StatusBlock*>(ws), dump,
-                                                     reinterpret_cast<uint2*>(ws + pl.mins_off)));
+             kern<<<grid, CH_THREADS, smem, s>>>(tq, tq, tk, tk, pl.Npad, npos, pl.npos_pad, pl.tiles_per_split,
+                                                 pl.pos_tiles, g_match_wait_ns > 0 ? g_match_wait_ns : kWaitNs,
+                                                 reinterpret_cast<StatusBlock*>(ws), dump,
+                                                 reinterpret_cast<uint16_t*>(ws + pl.mins_off)));
   return GLR_OK;
 }
 
