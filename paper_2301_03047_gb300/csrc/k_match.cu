@@ -512,7 +512,7 @@ __device__ int warp_keep_smallest_kth(unsigned long long* list, int n, int k, un
 // Bound and candidate chunks of every key for the exact evaluation (one warp per key, many
 // warps per SM to hide the memory latency).
 //  * Each lane keeps the L smallest of its share of the key's 16-bit chunk minima (the upper
-//    half of each minimum's order key; pairs of adjacent chunks, interleaved over the lanes) in
+//    half of each minimum's order key; runs of 8 chunks, interleaved over the lanes) in
 //    registers; the K'-th smallest of those 32 L values is tau16.  It bounds the K'-th smallest
 //    of all the 16-bit minima from above (the K'-th smallest of a subset is never smaller).  If
 //    M is the K'-th smallest chunk minimum, K' chunks have minima <= M, so at least K' scores
@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ 
   unsigned* hist = hist_s[wid];
   uint16_t* vals = vals_s[wid];
   const long long nkeys = (long long)n_img * N;
-  const int n2 = nchunks / 2, n8 = nchunks / 8;  // nchunks is a multiple of 8
+  const int n8 = nchunks / 8;  // nchunks is a multiple of 8
   for (long long gk = blockIdx.x * 8LL + wid; gk < nkeys; gk += gridDim.x * 8LL) {
     const int f = (int)(gk / N), k = (int)(gk - (long long)f * N);
     if (k >= min(n_found[f], N)) continue;
@@ -545,15 +545,25 @@ __global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ 
     uint32_t prefix = 0xffffu;
     if (nchunks > kp) {
       // per-lane 8 smallest (sorted ascending)
-      const uint32_t* m2 = reinterpret_cast<const uint32_t*>(mins16 + row * nchunks);
+      // 8 minima (16 bytes) per lane and step, the next two steps' loads in flight; a step
+      // whose smallest value does not beat the lane's L-th is skipped after one compare
+      const uint4* m8r = reinterpret_cast<const uint4*>(mins16 + row * nchunks);
+      const uint4 none = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
       uint32_t t[L];
 #pragma unroll
       for (int j = 0; j < L; ++j) t[j] = 0xffffu;
-      for (int i = lane; i < n2; i += 32) {
-        const uint32_t w = __ldg(m2 + i);
+      uint4 nx1 = lane < n8 ? __ldg(m8r + lane) : none;
+      uint4 nx2 = lane + 32 < n8 ? __ldg(m8r + lane + 32) : none;
+      for (int i = lane; i < n8; i += 32) {
+        const uint4 cur = nx1;
+        nx1 = nx2;
+        nx2 = i + 64 < n8 ? __ldg(m8r + i + 64) : none;
+        const uint32_t m2 = __vminu2(__vminu2(cur.x, cur.y), __vminu2(cur.z, cur.w));
+        if (min(m2 & 0xffffu, m2 >> 16) >= t[L - 1]) continue;
+        const uint32_t w4[4] = {cur.x, cur.y, cur.z, cur.w};
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          uint32_t v = (w >> (16 * h)) & 0xffffu;
+        for (int h = 0; h < 8; ++h) {
+          uint32_t v = (w4[h >> 1] >> (16 * (h & 1))) & 0xffffu;
           if (v < t[L - 1]) {
 #pragma unroll
             for (int j = 0; j < L; ++j) {  // insertion: t stays sorted, the largest drops out
@@ -619,11 +629,13 @@ __global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ 
     // candidate chunks in ascending order
     const uint4* m8 = reinterpret_cast<const uint4*>(mins16 + row * nchunks);
     int total = 0;
+    uint4 nxt = lane < n8 ? __ldg(m8 + lane) : make_uint4(0u, 0u, 0u, 0u);
     for (int base = 0; base < n8; base += 32) {
       const int i = base + lane;
       uint32_t bits = 0;
+      const uint4 v = nxt;
+      if (i + 32 < n8) nxt = __ldg(m8 + i + 32);
       if (i < n8) {
-        const uint4 v = __ldg(m8 + i);
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int j = 0; j < 8; ++j)
