@@ -558,7 +558,33 @@ def run_learned(args, cfg, prob, y, masks, sched, dev, fpc, flush, x_final, chos
             r["speedup_vs_plain"] = round(plain["ms_per_step"] / ms, 3)
             r["delta_psnr_db_vs_plain"] = round(psnr - plain["psnr"], 4)
         out[fmt] = r
-    return out
+    return out, enc
+
+
+def run_quality(args, cfg, prob, y, masks, sched, dev, fpc, tuned, forms, enc) -> dict:
+    """PSNR after the workload's full iteration count (untimed), every form from the same start:
+    the exhaustive forms and, when an encoder was trained, the learned proposal in both formats."""
+    import torch
+
+    from paper_2301_03047_gb300 import glr
+
+    runs = [(f, dict(mode=f, **tuned[f])) for f in forms]
+    if enc is not None:
+        runs += [(f"learned_{fmt}", dict(mode="learned", k_over=args.learned_k_over, encoder=enc.params,
+                                         emb_format=fmt)) for fmt in ("bf16", "e4m3")]
+    psnr = {}
+    for name, kw in runs:
+        rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, edge_th=cfg.edge_th, device=dev,
+                                   frames_per_call=fpc, **kw)
+        rec.start(y, masks)
+        for k in range(cfg.iters):
+            rec.step(sched[k % len(sched)], cfg.c_wnnm)
+        torch.cuda.synchronize()
+        psnr[name] = round(psnr_framewise(rec.x.cpu().numpy()[0], prob.truth), 3)
+        del rec
+        torch.cuda.empty_cache()
+    base = psnr[forms[0]]
+    return {"iters": cfg.iters, "psnr_db": psnr, "delta_vs_chosen_db": {k: round(v - base, 3) for k, v in psnr.items()}}
 
 
 def run_glr(args) -> None:
@@ -685,10 +711,12 @@ def run_glr(args) -> None:
         del rec
         torch.cuda.empty_cache()
 
-    learned = None
+    learned = enc = quality = None
     if args.learned == 1 or (args.learned < 0 and huge):
-        learned = run_learned(args, cfg, prob, y, masks, sched, dev, fpc, flush, x_final, results[forms[0]],
-                              results.get("fp32"))
+        learned, enc = run_learned(args, cfg, prob, y, masks, sched, dev, fpc, flush, x_final, results[forms[0]],
+                                   results.get("fp32"))
+    if args.quality == 1 or (args.quality < 0 and huge):
+        quality = run_quality(args, cfg, prob, y, masks, sched, dev, fpc, tuned, forms, enc)
     head = results[forms[0]]
     value = ws * args.steps / head["total_s"]
     npos = (cfg.H - cfg.P + 1) * (cfg.W - cfg.P + 1)
@@ -799,6 +827,8 @@ def run_glr(args) -> None:
     line["autotuned_match"] = tuned
     if learned is not None:
         line["learned"] = learned
+    if quality is not None:
+        line["quality_full_iters"] = quality
     if "graph" in results:
         line["cuda_graph"] = {"value": round(results["graph"]["value"], 4), "unit": UNIT,
                               "ms_per_step": round(results["graph"]["ms_per_step"], 3)}
@@ -910,7 +940,7 @@ def run_mri(args, cfg, dev, dist) -> None:
         clk = Clocks(local) if headline else None
         if clk:
             clk.__enter__()
-        for i in range(n_steps):
+        for i in range(args.steps):
             flush.zero_()
             ev[i][0].record()
             rec.step(sched[k % len(sched)], cfg.c_wnnm)
@@ -954,10 +984,6 @@ def run_mri(args, cfg, dev, dist) -> None:
         del rec
         torch.cuda.empty_cache()
 
-    learned = None
-    if args.learned == 1 or (args.learned < 0 and huge):
-        learned = run_learned(args, cfg, prob, y, masks, sched, dev, fpc, flush, x_final, results[forms[0]],
-                              results.get("fp32"))
     head = results[forms[0]]
     e2e = None
     if not args.no_e2e:
@@ -1361,6 +1387,9 @@ def main() -> None:
                     help="1: also time the learned proposal (trained encoder); default on for 2048^2 frames")
     ap.add_argument("--learned-k-over", type=int, default=256, help="candidates per key of the learned proposal")
     ap.add_argument("--learned-steps", type=int, default=300, help="encoder training steps (32768 pairs each)")
+    ap.add_argument("--quality", type=int, default=-1,
+                    help="1: also report every form's PSNR after the workload's full iteration count (untimed); "
+                    "default on for 2048^2 frames")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
