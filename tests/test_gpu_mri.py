@@ -113,6 +113,18 @@ def resolvable_rank(Yg, sw, cw, fn):
     return int(np.count_nonzero((s_new > 0) & (s > tol)))
 
 
+def sv_entry_errors(Mg, Mo, s, s_new, sw, K):
+    """(worst singular-value error, worst entry error), both over s_1: the singular values of the
+    returned group Mg (FP64 SVD) against the oracle's shrunk values where the shrinkage is well
+    conditioned (s_hat >= s / 2), and the entries of Mg against the oracle's estimate Mo."""
+    sg = np.linalg.svd(Mg, compute_uv=False)
+    s_hat = np.sqrt(np.maximum(s * s - K * sw * sw, 0.0))
+    good = (s_new > 0) & (s_hat >= 0.5 * s)
+    n = min(len(sg), len(s_new))
+    ds = np.abs(sg[:n] - s_new[:n])[good[:n]]
+    return (float(ds.max()) if ds.size else 0.0) / s[0], float(np.abs(Mg - Mo).max()) / s[0]
+
+
 def complex_image(tag, H, W):
     return synth.complex_phantom(synth.rng_for(tag), H, W)
 
@@ -136,12 +148,18 @@ def test_lowrank_complex_parity(case):
     Xo, _ = MO.lowrank_groups_complex(Y, sw, cw, eps=1e-8)
     ro = [resolvable_rank(MO.group_to_complex(Y[i]), sw, cw, MO.wnnm_complex) for i in range(N)]
     d = 2 * P * P
+    worst = [0.0, 0.0]
     for i in range(N):
         scale = np.linalg.norm(Y[i]) / math.sqrt(d * K)
         err = g[i] - Xo[i]
         assert np.sqrt(np.mean(err ** 2)) <= 2e-4 * max(scale, 1e-3), i
         assert np.abs(err).max() <= 1e-3 * max(np.abs(Y[i]).max(), 1e-3), i
         assert abs(int(rk[i]) - int(ro[i])) <= 1
+        _, _, sv, s_new = MO.wnnm_complex(MO.group_to_complex(Y[i]), sw, cw, 1e-8)
+        e = sv_entry_errors(MO.group_to_complex(g[i].astype(np.float64)), MO.group_to_complex(Xo[i]), sv, s_new, sw, K)
+        worst = [max(worst[0], e[0]), max(worst[1], e[1])]
+    print(f"complex {tag}: worst singular-value error {worst[0]:.2e} s_1, worst entry error {worst[1]:.2e} s_1")
+    assert max(worst) <= 1e-5, worst  # the survey's bar (measured worst 6.7e-6, Gram path entries)
 
 
 @pytest.mark.parametrize("case", [("w1", 1, 4, 30, 32, 6, 20, 32, 0.1), ("w2", 1, 1, 30, 30, 8, 12, 96, 0.05),
@@ -163,6 +181,7 @@ def test_lowrank_wide_real_parity(case):
     Y = O.gather_groups(x[0], P, idx[0])
     Xo, _ = O.lowrank_groups(Y, sw, cw, eps=1e-8)
     d = C * P * P
+    worst = [0.0, 0.0]
     for i in range(N):
         scale = np.linalg.norm(Y[i]) / math.sqrt(d * K)
         err = g[i] - Xo[i]
@@ -176,6 +195,10 @@ def test_lowrank_wide_real_parity(case):
         lo = int(np.count_nonzero((s_new > 0) & (sv > tol_hi)))
         hi = int(np.count_nonzero(s_new > 0))
         assert lo - 1 <= int(rk[i]) <= hi + 1, (i, int(rk[i]), lo, hi)
+        e = sv_entry_errors(g[i].T.astype(np.float64), Xo[i].T, sv, s_new, sw, K)
+        worst = [max(worst[0], e[0]), max(worst[1], e[1])]
+    print(f"wide {tag} (d {d}, K {K}): worst singular-value error {worst[0]:.2e} s_1, worst entry error {worst[1]:.2e} s_1")
+    assert max(worst) <= 1e-5, worst  # the survey's bar (measured worst 6.7e-6, Gram path entries)
 
 
 def bf16(a):
