@@ -787,8 +787,10 @@ __global__ void __launch_bounds__(CT_WARPS * 32, 4)
     // the FP32 score sc = ||q'||^2 - 2 <p', q> is the squared distance of the mean-shifted
     // patches minus c_k = ||p'||^2 + 2 mu sum(p'); a position can only hold one of the key's K'
     // smallest BF16 scores if its distance is at most tau plus the BF16 error of that score,
-    // |s~ - d| <= 2^-8 S^2 + ... with S = ||p'|| + ||q'|| (BF16 rounds within 2^-9 per value),
-    // so only positions within that bound enter the list
+    // |s~ - d| <= 2 sqrt(d) delta + delta^2 + 2.02e-6 (||p'||^2 + ||q'||^2), delta = 2^-9 S,
+    // S = ||p'|| + ||q'|| (BF16 rounds within 2^-9 per value; the last term is the FP32
+    // accumulation of the scan), so only positions within that bound (and a margin for the
+    // FP32 rounding of the score here) enter the list
     float pn2 = 0.f, psum = 0.f;
 #pragma unroll
     for (int e = 0; e < DM; ++e) {
@@ -917,8 +919,11 @@ __global__ void __launch_bounds__(CT_WARPS * 32, 4)
             const float qq = __ldg(qf + q);
             const float sc = fmaf(-2.f, acc[i], qq);
             const float S = pn + sqrtf(qq);
-            const float thr = tau_f + 0.004f * S * S + 1e-4f * (1.f + fabsf(sc) + fabsf(c_k) + qq + pn2);
-            near = sc + c_k <= thr;
+            const float dl = 0.001953125f * S;  // 2^-9 (||p'|| + ||q'||)
+            const float dq = sc + c_k;           // the FP32 distance
+            const float thr = tau_f + fmaf(2.f * sqrtf(fmaxf(dq, 0.f)), dl, dl * dl) + 2.02e-6f * (pn2 + qq) +
+                              1e-4f * (1.f + fabsf(sc) + fabsf(c_k) + qq + pn2);
+            near = dq <= thr;
             e = ((unsigned long long)float_order_key(sc) << 32) | (unsigned)q;
           }
           const bool keep = valid && near && e < kth;
