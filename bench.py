@@ -396,7 +396,7 @@ def merge_scans(prof: dict) -> dict:
 
 
 def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict, n_img: int | None = None,
-             d: int | None = None) -> dict:
+             d: int | None = None, census: dict | None = None) -> dict:
     """Roofline entry of the kernel with the largest share of the timed region.  The matcher's two
     scans (minima, candidates) count as one unit: the pair FLOPs once, over their summed time."""
     scans = "k_match_tc_min" in prof
@@ -426,9 +426,17 @@ def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict, n
         units = T * N
         # complex columns: a complex multiply-add is 4 real ones on 2 real values, twice the real count per value
         work = units * sweeps_per_group * 6.0 * d * K * K * (2.0 if name == "k_jacobi_wnnm_c" else 1.0)
+        note = "work = 6 d K^2 per sweep x measured sweeps"
+        if census:
+            # the timed iterations' own counts: sweeps, power steps of the rank-1 certificate
+            # (4 d K each: Y v and Y^T y) and the certified groups' output (4 d K)
+            work = units * (census["sweeps_per_group"] * 6.0 * d * K * K
+                            + (census["power_steps_per_group"] + census["rank1_per_group"]) * 4.0 * d * K)
+            note = ("work = 6 d K^2 per sweep + 4 d K per power step and per rank-1 output, counts of the "
+                    "timed iterations")
         achieved = work / avg_s / 1e12
         out = {"bound": "alu", "peak": round(fp32_alu_peak_tflops(sm), 1), "unit": "TFLOP/s",
-               "peak_note": f"derived FP32 FMA peak {num_sms()}x128x2 at {sm:.0f} MHz; work = 6 d K^2 per sweep x measured sweeps"}
+               "peak_note": f"derived FP32 FMA peak {num_sms()}x128x2 at {sm:.0f} MHz; {note}"}
         unit_name = "groups"
     else:
         units = T * N
@@ -478,6 +486,29 @@ def workload(name: str):
     if name == "mri256":  # profiling case of the MRI path
         return synth.mri_scaled(synth.MRI_LARGE, H=256, W=256, N=2048, name="mri_256x256_P6_N2048_K48")
     raise ValueError(name)
+
+
+def lowrank_census(cfg, y, masks, sched, dev, form, sched_kw_form, n_warm, n_steps) -> dict:
+    """The low-rank step's work over the timed iterations (untimed replay of the same iterations
+    with the status block read after each): sweeps, rank-1 certificate power steps and certified
+    groups, per group."""
+    import torch
+
+    from paper_2301_03047_gb300 import glr
+
+    rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=form, edge_th=cfg.edge_th,
+                               device=dev, **sched_kw_form)
+    rec.start(y, masks)
+    tot = [0, 0, 0, 0]  # sweeps, groups, rank1, power steps
+    for k in range(n_warm + n_steps):
+        rec.step(sched[k % len(sched)], cfg.c_wnnm)
+        if k >= n_warm:
+            torch.cuda.synchronize()
+            _, cnt = glr.poll_status(rec.den.ws_lowrank_status)
+            tot = [tot[0] + cnt[2], tot[1] + cnt[3], tot[2] + cnt[7], tot[3] + cnt[8]]
+    del rec
+    g = max(tot[1], 1)
+    return {"sweeps_per_group": tot[0] / g, "rank1_per_group": tot[2] / g, "power_steps_per_group": tot[3] / g}
 
 
 def run_learned(args, cfg, prob, y, masks, sched, dev, fpc, flush, x_final, chosen, plain) -> dict:
@@ -616,6 +647,7 @@ def run_glr(args) -> None:
     prof = None
     clocks_summary = None
     sweeps = 0.0
+    census = None
     svd_noconv = None
     stream_stats = None
     launches = 0
@@ -683,6 +715,9 @@ def run_glr(args) -> None:
             bits, cnt = glr.poll_status(rec.den.ws_lowrank_status)
             sweeps = cnt[2] / max(cnt[3], 1)
             svd_noconv = cnt[1]
+            if not fpc:  # frames in one call: every iteration's counts can be read back
+                census = lowrank_census(cfg, y, masks, sched, dev, form, tuned[form], n_warm, n_steps)
+                sweeps = census["sweeps_per_group"]
             _, mcnt = glr.poll_status(rec.den.ws_match)
             stream_stats = {"appends_per_key": round(mcnt[4] / (cfg.T * cfg.N), 1),
                             "compactions_per_key": round(mcnt[5] / (cfg.T * cfg.N), 2)}
@@ -794,7 +829,7 @@ def run_glr(args) -> None:
                 cpu["oracle_error"] = {"failed": str(e)[-300:]}
             os.unlink(oracle_inputs)
     # a launch covers frames_per_call frames when the frames are processed in groups
-    rl = roofline(prof, cfg, sweeps, clocks_summary or {}, pk, n_img=fpc or None) if prof else None
+    rl = roofline(prof, cfg, sweeps, clocks_summary or {}, pk, n_img=fpc or None, census=census) if prof else None
     kernels = {k: {"ms_per_step": round(v[0] / args.steps, 3), "launches": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])} if prof else {}
     line = {
         "metric": METRIC,
@@ -817,6 +852,8 @@ def run_glr(args) -> None:
         "gpu_launches": launches,
         "kernels": kernels,
         "svd_sweeps_per_group": round(sweeps, 2),
+        "svd_rank1_certified": round(census["rank1_per_group"], 4) if census else None,
+        "svd_power_steps_per_group": round(census["power_steps_per_group"], 2) if census else None,
         "svd_groups_at_sweep_cap": svd_noconv,
         "topk_streams": stream_stats,
         "roofline": rl,

@@ -472,6 +472,8 @@ glr_status glr_poll_status(const void* ws, uint32_t* bits, uint32_t* counters, i
     counters[4] = (uint32_t)std::min<unsigned long long>(h.cand_appends, 0xffffffffull);
     counters[5] = (uint32_t)std::min<unsigned long long>(h.compactions, 0xffffffffull);
     counters[6] = h.fb_noconv;
+    counters[7] = h.rank1;
+    counters[8] = h.power_steps;
   }
   if (reset) {
     if (cudaMemsetAsync(const_cast<void*>(ws), 0, sizeof(StatusBlock), s) != cudaSuccess) return GLR_ECUDA;

@@ -21,7 +21,9 @@ struct StatusBlock {
   unsigned long long cand_appends;  // candidates appended by the top-K streams
   unsigned long long compactions;   // stream compactions
   uint32_t fb_noconv;      // groups the FP64 fallback did not converge within its sweep cap
-  uint32_t pad[53];
+  uint32_t rank1;          // groups settled by the rank-1 certificate (no Jacobi sweep)
+  uint32_t power_steps;    // power steps of the rank-1 certificate (all groups that tried it)
+  uint32_t pad[51];
 };
 static_assert(sizeof(StatusBlock) == 256, "status block is 256 bytes");
 

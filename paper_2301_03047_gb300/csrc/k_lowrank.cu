@@ -242,6 +242,85 @@ __device__ __forceinline__ float sq_norm(const float (&a)[DMAX]) {
   return (p[0] + p[1]) + (p[2] + p[3]);
 }
 
+// The rank-1 certificate of k_jacobi_wnnm (real groups of up to 64 rows).  WNNM removes
+// every component with s <= s_crit, s_crit^2 = sw^2 (K + sqrt(K^2 + 4 C^2)) / 2 (where
+// s = C sw^2 / sqrt(s^2 - K sw^2)).  Power steps on Y^T Y from the all-ones vector give the
+// dominant right singular vector v and mu = ||Y v||^2 <= s_1^2; ||Y||_F^2 - mu is then at least
+// sum_{i >= 2} s_i^2 >= s_2^2, so when it is at most s_crit^2 (less margins for the FP32
+// sums) WNNM keeps at most the first component and X^ = s_1' u u^T Y with u = Y v / ||Y v||.
+// y = Y v is summed through the warp's shared-memory slice buf (32 partial rows of 68
+// floats, then y at 32 x 68): every lane adds two rows of the 32 lane partials in lane
+// order.  Returns true with ylo, yhi = rows 2 lane, 2 lane + 1 of y and mu.
+constexpr int kPowerSteps = 12;
+constexpr int kPartLd = 68;  // partial-row stride (floats): 16-byte stores without bank conflicts
+__device__ __forceinline__ bool rank1_certificate(const float (&a)[64], const float (&b)[64], bool has_a,
+                                                  bool has_b, int K, float sigma_w, float c_wnnm, int lane,
+                                                  float* buf, float& ylo, float& yhi, float& mu, int& steps) {
+  const float sw2 = sigma_w * sigma_w;
+  const float scrit2 = 0.5f * sw2 * ((float)K + sqrtf((float)K * (float)K + 4.f * c_wnnm * c_wnnm));
+  float fro = sq_norm<64>(a) + sq_norm<64>(b);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+  float va = has_a ? rsqrtf((float)K) : 0.f, vb = has_b ? rsqrtf((float)K) : 0.f;
+  float* yv = buf + 32 * kPartLd;
+  mu = 0.f;
+  for (int it = 0; it < kPowerSteps; ++it) {
+    steps = it + 1;
+    // y = Y v: this lane's share (its two columns), then the 32 shares added
+    float4* pw = reinterpret_cast<float4*>(buf + lane * kPartLd);
+#pragma unroll
+    for (int r4 = 0; r4 < 16; ++r4)
+      pw[r4] = make_float4(fmaf(va, a[4 * r4], vb * b[4 * r4]), fmaf(va, a[4 * r4 + 1], vb * b[4 * r4 + 1]),
+                           fmaf(va, a[4 * r4 + 2], vb * b[4 * r4 + 2]), fmaf(va, a[4 * r4 + 3], vb * b[4 * r4 + 3]));
+    __syncwarp();
+    float sx = 0.f, sy = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float2 v = *reinterpret_cast<const float2*>(buf + k * kPartLd + 2 * lane);
+      sx += v.x;
+      sy += v.y;
+    }
+    ylo = sx;
+    yhi = sy;
+    *reinterpret_cast<float2*>(yv + 2 * lane) = make_float2(sx, sy);
+    __syncwarp();
+    float p[4] = {0.f, 0.f, 0.f, 0.f}, za[4] = {0.f, 0.f, 0.f, 0.f}, zb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int r4 = 0; r4 < 16; ++r4) {
+      const float4 t = reinterpret_cast<const float4*>(yv)[r4];
+      const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        p[u] = fmaf(tv[u], tv[u], p[u]);
+        za[u] = fmaf(a[4 * r4 + u], tv[u], za[u]);
+        zb[u] = fmaf(b[4 * r4 + u], tv[u], zb[u]);
+      }
+    }
+    __syncwarp();  // y and the partials are read before the next step rewrites them
+    const float mu_new = (p[0] + p[1]) + (p[2] + p[3]);  // ||Y v||^2, v of unit length
+    const float zA = (za[0] + za[1]) + (za[2] + za[3]), zB = (zb[0] + zb[1]) + (zb[2] + zb[3]);
+    const bool done = it > 0 && mu_new - mu <= 1e-7f * mu_new;
+    mu = mu_new;
+    if (!(mu > 0.f)) return fro <= 0.9999f * scrit2;  // Y = 0 (or below s_crit altogether)
+    // residual of the eigen-equation: r = Y^T Y v - mu v; v is within |r| / gap of the
+    // dominant vector, gap >= mu - (||Y||_F^2 - mu) once the energy test holds
+    const float ra = zA - mu * va, rb = zB - mu * vb;
+    float r2 = ra * ra + rb * rb, n2 = zA * zA + zB * zB;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+      n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    }
+    const float rest = fro - mu;  // >= sum_{i >= 2} s_i^2 (mu only grows)
+    if (rest <= 0.9999f * scrit2 - 4e-6f * fro && sqrtf(r2) <= 2e-6f * (mu - rest)) return true;
+    if (done && rest > 0.9999f * scrit2) return false;  // converged above the level: not rank 1
+    const float inv = rsqrtf(n2);
+    va = zA * inv;
+    vb = zB * inv;
+  }
+  return false;
+}
+
 // Columns at or above the skip level up to which a sweep is replaced by a direct test of
 // their pairs (each costs one broadcast column: DMAX shuffles and 2 DMAX FMAs per lane).
 constexpr int kDirectCheckCols = 4;
@@ -292,6 +371,17 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
     }
     int sweep = 0;
     bool converged = (m < 1);
+    // real groups of up to 64 rows: settle rank <= 1 without sweeps where the certificate holds
+    bool rank1 = false;
+    float ylo = 0.f, yhi = 0.f, mu1 = 0.f;
+    if constexpr (!CPLX && DMAX == 64) {
+      if (sigma_w > 0.f && !converged) {
+        int steps = 0;
+        rank1 = rank1_certificate(a, b, ja < K, jb < K, K, sigma_w, c_wnnm, lane, Ws, ylo, yhi, mu1, steps);
+        converged = converged || rank1;
+        if (lane == 0) atomicAdd(&st->power_steps, (unsigned)steps);
+      }
+    }
     // Components with s^2 < K sw^2 are always removed by the shrinkage.  When the
     // columns below that level carry less than K sw^2 in total, no combination of
     // them can reach it, so rotations among them cannot change X^ and are skipped
@@ -428,7 +518,24 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
     if (lane == 0) {
       atomicAdd(&st->sweeps, (unsigned)sweep);
       atomicAdd(&st->groups, 1u);
+      if (rank1) atomicAdd(&st->rank1, 1u);
     }
+    __shared__ float coef_s[WARPS][64];
+    int rnk;
+    if (rank1) {
+      // X^ = coef w (w^T Y) with w = Y v: coef = s' / (s ||w||^2), s = ||w|| (as below)
+      const float sw2 = sigma_w * sigma_w;
+      const float s1 = sqrtf(mu1);
+      const float h1 = sqrtf(fmaxf(mu1 - (float)K * sw2, 0.f));
+      const float p1 = fmaxf(s1 - c_wnnm * sw2 / (h1 + 1e-8f), 0.f);
+      const float coef = (p1 > 0.f && mu1 > 0.f) ? p1 / (s1 * mu1) : 0.f;
+      rnk = coef != 0.f ? 1 : 0;
+      if (rank && lane == 0) rank[g] = rnk;
+      __syncwarp();  // the certificate's last reads of Ws are done
+      Ws[2 * lane] = ylo;
+      Ws[2 * lane + 1] = yhi;
+      if (lane == 0) coef_s[wid][0] = coef;
+    } else {
     // singular values and WNNM shrinkage (reading: tau_i = C sw^2 / (sigma_hat_i + eps))
     float na2 = 0.f, nb2 = 0.f;
 #pragma unroll
@@ -456,10 +563,9 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
     const unsigned act_a = __ballot_sync(0xffffffffu, coef_a != 0.f);
     const unsigned act_b = __ballot_sync(0xffffffffu, coef_b != 0.f);
     const int ra = __popc(act_a), rb = __popc(act_b);
-    const int rnk = ra + rb;
+    rnk = ra + rb;
     if (rank && lane == 0) rank[g] = rnk;
     // stage the active columns w_i into shared memory (compacted) with coefficients
-    __shared__ float coef_s[WARPS][64];
     {
       const int pa = __popc(act_a & ((1u << lane) - 1u));
       const int pb = ra + __popc(act_b & ((1u << lane) - 1u));
@@ -474,6 +580,7 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
         coef_s[wid][pb] = coef_b;
       }
     }
+    }  // rank1
     __syncwarp();
     // X^ columns j = 2 lane, 2 lane + 1: x^_j = sum_i coef_i w_i (w_i . y_j)
 #pragma unroll 1

@@ -426,3 +426,42 @@ def test_lowrank_singular_values_and_estimate_tight_bar(case):
     print(f"worst singular-value error {worst_s:.2e} s_1, worst entry error {worst_x:.2e} s_1")
     assert worst_s <= 1e-5, worst_s
     assert worst_x <= 1e-5, worst_x
+
+
+@pytest.mark.parametrize("two_patterns", [False, True])
+def test_lowrank_rank1_certificate(two_patterns):
+    """Groups of near copies of one 8 x 8 pattern plus noise of std 0.01 at sigma_w = 0.1: the
+    residual energy (~64 K 1e-4) is below s_crit^2 = sw^2 (K + sqrt(K^2 + 4 C^2)) / 2, so the
+    register kernel settles them by the rank-1 certificate without sweeps (status counter 7)
+    and X^ must equal the oracle's within 1e-5 s_1.  With two patterns per group the certificate
+    fails and the Jacobi sweeps run: the same bar, and no group is counted."""
+    rng = np.random.default_rng(21)
+    H = W = 8 * 12
+    pa = rng.random((8, 8))
+    pb = rng.random((8, 8))
+    base = np.tile(pa, (12, 12))
+    if two_patterns:
+        base[:, 48:] = np.tile(pb, (12, 6))
+    x = (base + 0.01 * rng.standard_normal((H, W))).astype(np.float32)[None, None]
+    P, K, N = 8, 64, 40
+    Wq = W - P + 1
+    grid = [r * Wq + c for r in range(0, 89, 8) for c in range(0, 89, 8)]  # 12 x 12 aligned positions
+    idx = np.stack([rng.choice(grid, size=K, replace=False) for _ in range(N)]).astype(np.int32)[None]
+    sw, cw = 0.1, 2 * math.sqrt(K)
+    im = glr.images(1, 1, H, W, P)
+    ws = glr.workspace(glr.L.GLR_OP_LOWRANK, im, N, K)
+    groups, rank = glr.lowrank_groups(cuda(x), P, cuda(idx, torch.int32), cuda(np.array([N], np.int32), torch.int32),
+                                      sw, cw, ws=ws)
+    torch.cuda.synchronize()
+    _, cnt = glr.poll_status(ws)
+    g = groups.cpu().numpy()[0].astype(np.float64)
+    rk = rank.cpu().numpy()[0]
+    Y = O.gather_groups(x[0], P, idx[0])
+    for i in range(N):
+        Xo, ro, s, _ = O.wnnm(Y[i].T, sw, cw, eps=1e-8)
+        assert np.abs(g[i].T - Xo).max() <= 1e-5 * s[0], i
+        assert int(rk[i]) == ro, (i, int(rk[i]), ro)
+    if two_patterns:
+        assert cnt[7] < N and cnt[2] > 0  # the mixed groups needed sweeps
+    else:
+        assert cnt[7] == N and cnt[2] == 0, cnt  # every group settled without a sweep
