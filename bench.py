@@ -431,9 +431,10 @@ def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict, n
             # the timed iterations' own counts: sweeps, power steps of the rank-1 certificate
             # (4 d K each: Y v and Y^T y) and the certified groups' output (4 d K)
             work = units * (census["sweeps_per_group"] * 6.0 * d * K * K
-                            + (census["power_steps_per_group"] + census["rank1_per_group"]) * 4.0 * d * K)
-            note = ("work = 6 d K^2 per sweep + 4 d K per power step and per rank-1 output, counts of the "
-                    "timed iterations")
+                            + (census["power_steps_per_group"] + census["rank1_per_group"]) * 4.0 * d * K
+                            + census["gram_per_group"] * 2.0 * d * K * K)
+            note = ("work = 6 d K^2 per sweep + 4 d K per power step and per rank-1 output + 2 d K^2 per Gram "
+                    "bound, counts of the timed iterations")
         achieved = work / avg_s / 1e12
         out = {"bound": "alu", "peak": round(fp32_alu_peak_tflops(sm), 1), "unit": "TFLOP/s",
                "peak_note": f"derived FP32 FMA peak {num_sms()}x128x2 at {sm:.0f} MHz; {note}"}
@@ -499,16 +500,17 @@ def lowrank_census(cfg, y, masks, sched, dev, form, sched_kw_form, n_warm, n_ste
     rec = glr.SciReconstructor(cfg.T, cfg.H, cfg.W, cfg.P, cfg.N, cfg.K, mode=form, edge_th=cfg.edge_th,
                                device=dev, **sched_kw_form)
     rec.start(y, masks)
-    tot = [0, 0, 0, 0]  # sweeps, groups, rank1, power steps
+    tot = [0, 0, 0, 0, 0, 0]  # sweeps, groups, rank1, power steps, rank1 by the Gram bound, Gram bounds
     for k in range(n_warm + n_steps):
         rec.step(sched[k % len(sched)], cfg.c_wnnm)
         if k >= n_warm:
             torch.cuda.synchronize()
             _, cnt = glr.poll_status(rec.den.ws_lowrank_status)
-            tot = [tot[0] + cnt[2], tot[1] + cnt[3], tot[2] + cnt[7], tot[3] + cnt[8]]
+            tot = [t + c for t, c in zip(tot, (cnt[2], cnt[3], cnt[7], cnt[8], cnt[9], cnt[10]))]
     del rec
     g = max(tot[1], 1)
-    return {"sweeps_per_group": tot[0] / g, "rank1_per_group": tot[2] / g, "power_steps_per_group": tot[3] / g}
+    return {"sweeps_per_group": tot[0] / g, "rank1_per_group": tot[2] / g, "power_steps_per_group": tot[3] / g,
+            "rank1_gram_per_group": tot[4] / g, "gram_per_group": tot[5] / g}
 
 
 def run_learned(args, cfg, prob, y, masks, sched, dev, fpc, flush, x_final, chosen, plain) -> dict:
@@ -854,6 +856,7 @@ def run_glr(args) -> None:
         "svd_sweeps_per_group": round(sweeps, 2),
         "svd_rank1_certified": round(census["rank1_per_group"], 4) if census else None,
         "svd_power_steps_per_group": round(census["power_steps_per_group"], 2) if census else None,
+        "svd_rank1_by_gram_bound": round(census["rank1_gram_per_group"], 4) if census else None,
         "svd_groups_at_sweep_cap": svd_noconv,
         "topk_streams": stream_stats,
         "roofline": rl,

@@ -498,13 +498,15 @@ glr_status glr_admm_step(const float* y, const float* mask, const float* z, cons
  * Reads the status block of a workspace used by an earlier call (blocks on
  * `stream`).  ws == NULL reads the status block of glr_aggregate_noalloc's
  * scratch array on the current device instead.  bits = OR of GLR_DEV_*;
- * counters (may be NULL) receives 9 uint32 values: [0] keys whose candidate
+ * counters (may be NULL) receives 11 uint32 values: [0] keys whose candidate
  * buffer overflowed, [1] groups whose SVD hit the FP32 sweep cap, [2] total
  * Jacobi sweeps, [3] groups processed, [4] candidates appended by the matching
  * top-K streams or candidate chunks of the chunk form (saturating), [5] top-K
  * stream compactions (saturating), [6] groups whose FP64 fallback also reached
  * its sweep cap, [7] groups settled by the rank-1 certificate without sweeps,
- * [8] power steps the certificate took (over every group that tried it).
+ * [8] power steps the certificate took (over every group that tried it), [9]
+ * groups of [7] settled by its Gram bound (the energy bound did not hold),
+ * [10] Gram bounds evaluated.
  * Returns GLR_ETIMEDOUT if a bounded device wait expired (GLR_DEV_TIMEOUT),
  * else GLR_EDEVICE if another error bit (non-finite, bad index) is set.
  * Pass reset != 0 to clear the block afterwards.

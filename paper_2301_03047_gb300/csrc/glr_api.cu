@@ -474,6 +474,8 @@ glr_status glr_poll_status(const void* ws, uint32_t* bits, uint32_t* counters, i
     counters[6] = h.fb_noconv;
     counters[7] = h.rank1;
     counters[8] = h.power_steps;
+    counters[9] = h.rank1_gram;
+    counters[10] = h.gram_evals;
   }
   if (reset) {
     if (cudaMemsetAsync(const_cast<void*>(ws), 0, sizeof(StatusBlock), s) != cudaSuccess) return GLR_ECUDA;

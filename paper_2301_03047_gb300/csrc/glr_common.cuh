@@ -23,7 +23,9 @@ struct StatusBlock {
   uint32_t fb_noconv;      // groups the FP64 fallback did not converge within its sweep cap
   uint32_t rank1;          // groups settled by the rank-1 certificate (no Jacobi sweep)
   uint32_t power_steps;    // power steps of the rank-1 certificate (all groups that tried it)
-  uint32_t pad[51];
+  uint32_t rank1_gram;     // of rank1: settled by the Gram bound (the energy bound did not hold)
+  uint32_t gram_evals;     // Gram bounds evaluated
+  uint32_t pad[49];
 };
 static_assert(sizeof(StatusBlock) == 256, "status block is 256 bytes");
 

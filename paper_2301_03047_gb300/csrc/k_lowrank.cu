@@ -244,26 +244,44 @@ __device__ __forceinline__ float sq_norm(const float (&a)[DMAX]) {
 
 // The rank-1 certificate of k_jacobi_wnnm (real groups of up to 64 rows).  WNNM removes
 // every component with s <= s_crit, s_crit^2 = sw^2 (K + sqrt(K^2 + 4 C^2)) / 2 (where
-// s = C sw^2 / sqrt(s^2 - K sw^2)).  Power steps on Y^T Y from the all-ones vector give the
-// dominant right singular vector v and mu = ||Y v||^2 <= s_1^2; ||Y||_F^2 - mu is then at least
-// sum_{i >= 2} s_i^2 >= s_2^2, so when it is at most s_crit^2 (less margins for the FP32
-// sums) WNNM keeps at most the first component and X^ = s_1' u u^T Y with u = Y v / ||Y v||.
-// y = Y v is summed through the warp's shared-memory slice buf (32 partial rows of 68
-// floats, then y at 32 x 68): every lane adds two rows of the 32 lane partials in lane
-// order.  Returns true with ylo, yhi = rows 2 lane, 2 lane + 1 of y and mu.
+// s = C sw^2 / sqrt(s^2 - K sw^2)).  Power steps on Y^T Y from the all-ones vector give a unit
+// vector v near the dominant right singular vector and mu = ||Y v||^2 <= s_1^2.  Two upper
+// bounds on s_2^2 settle the group as rank <= 1:
+//  1. energy: ||Y||_F^2 - mu >= sum_{i >= 2} s_i^2 >= s_2^2;
+//  2. Gram: with R = Y (I - v v^T), R^T R is Y^T Y compressed to the complement of v, so by
+//     Cauchy interlacing s_2^2 <= lambda_max(R^T R) <= ||R^T R||_F.  Where the residual energy
+//     is spread over many small components (noise at the start of the schedule) this is up to
+//     sqrt(K - 1) times tighter than the energy bound.
+// Either bound at most s_crit^2 (less margins for the FP32 sums) means WNNM keeps at most the
+// first component; once the eigen-residual ||Y^T Y v - mu v|| is below 2e-6 (mu - bound) (v
+// within 2e-6 of the dominant vector) X^ = s_1' u u^T Y with u = Y v / ||Y v||.
+// y = Y v is summed through the warp's shared-memory slice buf (32 partial rows of 68 floats,
+// then y at 32 x 68): every lane adds two rows of the 32 lane partials in lane order.  The
+// Gram bound stores the columns of R in buf (slot l: lane l's first column, slot 32 + l: its
+// second; float4 r4 of slot s at 4 (r4 ^ (s & 15)), so that both the column stores and the
+// broadcast reads avoid bank conflicts) and the eigen-residual components in res[64].
+// Returns 0 (not certified), 1 (energy bound) or 2 (Gram bound), with ylo, yhi = rows
+// 2 lane, 2 lane + 1 of y, mu, and zA, zB = y . y_j of the lane's two columns (so that
+// x^_j = s_1' / (s_1 mu) (y . y_j) y); gram tells whether the Gram bound was evaluated.
 constexpr int kPowerSteps = 12;
 constexpr int kPartLd = 68;  // partial-row stride (floats): 16-byte stores without bank conflicts
-__device__ __forceinline__ bool rank1_certificate(const float (&a)[64], const float (&b)[64], bool has_a,
-                                                  bool has_b, int K, float sigma_w, float c_wnnm, int lane,
-                                                  float* buf, float& ylo, float& yhi, float& mu, int& steps) {
+__device__ __forceinline__ int rank1_certificate(const float (&a)[64], const float (&b)[64], bool has_a,
+                                                 bool has_b, int K, float sigma_w, float c_wnnm, int lane,
+                                                 float* buf, float* res, float& ylo, float& yhi, float& mu,
+                                                 float& zA, float& zB, int& steps, bool& gram) {
   const float sw2 = sigma_w * sigma_w;
   const float scrit2 = 0.5f * sw2 * ((float)K + sqrtf((float)K * (float)K + 4.f * c_wnnm * c_wnnm));
+  const float lim = 0.9999f * scrit2;
+  const float sqrt_m = sqrtf((float)max(K - 1, 1));  // R has rank <= K - 1
   float fro = sq_norm<64>(a) + sq_norm<64>(b);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
   float va = has_a ? rsqrtf((float)K) : 0.f, vb = has_b ? rsqrtf((float)K) : 0.f;
   float* yv = buf + 32 * kPartLd;
   mu = 0.f;
+  gram = false;
+  float ra = 0.f, rb = 0.f, res_n = 0.f, lim_g = 0.f;
+  bool try_gram = false;
   for (int it = 0; it < kPowerSteps; ++it) {
     steps = it + 1;
     // y = Y v: this lane's share (its two columns), then the 32 shares added
@@ -298,28 +316,100 @@ __device__ __forceinline__ bool rank1_certificate(const float (&a)[64], const fl
     }
     __syncwarp();  // y and the partials are read before the next step rewrites them
     const float mu_new = (p[0] + p[1]) + (p[2] + p[3]);  // ||Y v||^2, v of unit length
-    const float zA = (za[0] + za[1]) + (za[2] + za[3]), zB = (zb[0] + zb[1]) + (zb[2] + zb[3]);
+    zA = (za[0] + za[1]) + (za[2] + za[3]);
+    zB = (zb[0] + zb[1]) + (zb[2] + zb[3]);
     const bool done = it > 0 && mu_new - mu <= 1e-7f * mu_new;
     mu = mu_new;
-    if (!(mu > 0.f)) return fro <= 0.9999f * scrit2;  // Y = 0 (or below s_crit altogether)
+    if (!(mu > 0.f)) return fro <= lim ? 1 : 0;  // Y = 0 (or below s_crit altogether)
     // residual of the eigen-equation: r = Y^T Y v - mu v; v is within |r| / gap of the
-    // dominant vector, gap >= mu - (||Y||_F^2 - mu) once the energy test holds
-    const float ra = zA - mu * va, rb = zB - mu * vb;
+    // dominant vector, gap >= mu - (upper bound on s_2^2)
+    ra = zA - mu * va;
+    rb = zB - mu * vb;
     float r2 = ra * ra + rb * rb, n2 = zA * zA + zB * zB;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       r2 += __shfl_xor_sync(0xffffffffu, r2, o);
       n2 += __shfl_xor_sync(0xffffffffu, n2, o);
     }
-    const float rest = fro - mu;  // >= sum_{i >= 2} s_i^2 (mu only grows)
-    if (rest <= 0.9999f * scrit2 - 4e-6f * fro && sqrtf(r2) <= 2e-6f * (mu - rest)) return true;
-    if (done && rest > 0.9999f * scrit2) return false;  // converged above the level: not rank 1
+    res_n = sqrtf(r2);
+    const float rest = fro - mu;  // = ||R||_F^2 >= sum_{i >= 2} s_i^2 (mu only grows)
+    const bool energy_ok = rest <= lim - 4e-6f * fro;
+    if (energy_ok && res_n <= 2e-6f * (mu - rest)) return 1;
+    // the Gram bound's level, less its FP32 error (the products a.r_c and the residual terms
+    // below: about 4e-6 sqrt(||Y||_F^2 ||R||_F^2) and 4e-6 ||Y||_F^2 at worst, taken 10 and 2
+    // times); it can only hold when ||R||_F^2 / sqrt(K - 1) <= ||R^T R||_F is below it
+    lim_g = lim - 8e-6f * fro - 4e-5f * sqrtf(fro * fmaxf(rest, 0.f));
+    const bool gram_ok = lim_g > 0.f && rest <= lim_g * sqrt_m;
+    if (!energy_ok && gram_ok && res_n <= 2e-6f * (mu - lim_g)) {
+      try_gram = true;
+      break;
+    }
+    if (done && !energy_ok && !gram_ok) return 0;  // converged above both levels: not rank 1
     const float inv = rsqrtf(n2);
     va = zA * inv;
     vb = zB * inv;
   }
-  return false;
+  if (!try_gram) return 0;
+  // Gram bound: R columns r_j = y_j - v_j y into buf (y rows from the lanes that hold them),
+  // res_j = y . r_j = (Y^T y)_j - v_j ||y||^2 (the eigen-residual), then per lane the entries
+  // (R^T R)_{j s} = r_j . r_s = y_j . r_s - v_j res_s of its two rows j
+  gram = true;
+  res[lane] = ra;
+  res[32 + lane] = rb;
+  {
+    const int sw = lane & 15;
+    float4* ca = reinterpret_cast<float4*>(buf + lane * 64);
+    float4* cb = reinterpret_cast<float4*>(buf + (32 + lane) * 64);
+#pragma unroll
+    for (int r4 = 0; r4 < 16; ++r4) {
+      float yr[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = 4 * r4 + u;
+        yr[u] = __shfl_sync(0xffffffffu, (r & 1) ? yhi : ylo, r >> 1);
+      }
+      ca[r4 ^ sw] = make_float4(fmaf(-va, yr[0], a[4 * r4]), fmaf(-va, yr[1], a[4 * r4 + 1]),
+                                fmaf(-va, yr[2], a[4 * r4 + 2]), fmaf(-va, yr[3], a[4 * r4 + 3]));
+      cb[r4 ^ sw] = make_float4(fmaf(-vb, yr[0], b[4 * r4]), fmaf(-vb, yr[1], b[4 * r4 + 1]),
+                                fmaf(-vb, yr[2], b[4 * r4 + 2]), fmaf(-vb, yr[3], b[4 * r4 + 3]));
+    }
+  }
+  __syncwarp();
+  float gs = 0.f;
+#pragma unroll 1
+  for (int s = 0; s < 64; ++s) {
+    const float4* cs = reinterpret_cast<const float4*>(buf + s * 64);
+    const int sw = s & 15;
+    float da[4] = {0.f, 0.f, 0.f, 0.f}, db[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int r4 = 0; r4 < 16; ++r4) {
+      const float4 t = cs[r4 ^ sw];
+      da[0] = fmaf(a[4 * r4], t.x, da[0]);
+      da[1] = fmaf(a[4 * r4 + 1], t.y, da[1]);
+      da[2] = fmaf(a[4 * r4 + 2], t.z, da[2]);
+      da[3] = fmaf(a[4 * r4 + 3], t.w, da[3]);
+      db[0] = fmaf(b[4 * r4], t.x, db[0]);
+      db[1] = fmaf(b[4 * r4 + 1], t.y, db[1]);
+      db[2] = fmaf(b[4 * r4 + 2], t.z, db[2]);
+      db[3] = fmaf(b[4 * r4 + 3], t.w, db[3]);
+    }
+    const float rs = res[s];
+    const float ga = fmaf(-va, rs, (da[0] + da[1]) + (da[2] + da[3]));
+    const float gb = fmaf(-vb, rs, (db[0] + db[1]) + (db[2] + db[3]));
+    gs = fmaf(ga, ga, fmaf(gb, gb, gs));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gs += __shfl_xor_sync(0xffffffffu, gs, o);
+  __syncwarp();  // the R columns and res are read before the caller reuses buf
+  const float rho = sqrtf(gs);  // ||R^T R||_F >= s_2^2
+  return (rho <= lim_g && res_n <= 2e-6f * (mu - rho)) ? 2 : 0;
 }
+
+// Staging slice of a 64 x 64 group: float4 r4 (rows 4 r4 .. 4 r4 + 3) of column j at
+// 16 j + (r4 ^ ((j >> 1) & 15)).  Coalesced copies (8 consecutive float4 of one column per
+// quarter warp) and the lanes' reads of their own columns 2 lane, 2 lane + 1 both fall on 8
+// distinct 16-byte bank groups.
+__device__ __forceinline__ int stage_at(int j, int r4) { return 16 * j + (r4 ^ ((j >> 1) & 15)); }
 
 // Columns at or above the skip level up to which a sweep is replaced by a direct test of
 // their pairs (each costs one broadcast column: DMAX shuffles and 2 DMAX FMAs per lane).
@@ -334,6 +424,7 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
                                                             StatusBlock* st, FusedIO io,
                                                             int32_t* __restrict__ fb_queue) {
   extern __shared__ float wsm[];  // [WARPS][64][DMAX]: active columns of W
+  __shared__ float coef_s[WARPS][64];  // shrinkage coefficients (the certificate's scratch before)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float* Ws = wsm + (size_t)wid * 64 * DMAX;
   const long long ngroups = (long long)n_img * N;
@@ -343,6 +434,8 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
     const int f = (int)(g / N), k = (int)(g - (long long)f * N);
     if (k >= min(n_found[f], N)) continue;
     float* Y = FUSED ? nullptr : groups + g * (long long)K * d;
+    // real 64-row groups in memory move through the staging slice with 16-byte accesses
+    const bool stage_ok = !FUSED && !CPLX && DMAX == 64 && d == 64;
     float a[DMAX], b[DMAX];
     const int ja = 2 * lane, jb = 2 * lane + 1;
     int qa = -1, qb = -1;  // FUSED: patch positions of the two columns (-1: none / invalid)
@@ -356,6 +449,26 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
       if ((unsigned)qb >= (unsigned)npos) qb = -1;
       gather_col<DMAX>(a, io, f, qa, d, qa >= 0);
       gather_col<DMAX>(b, io, f, qb, d, qb >= 0);
+    } else if (stage_ok) {
+      // the group's K rows of 64 floats, coalesced through the warp's staging slice
+      const float4* src = reinterpret_cast<const float4*>(Y);
+      float4* W4 = reinterpret_cast<float4*>(Ws);
+      for (int t = lane; t < K * 16; t += 32) W4[stage_at(t >> 4, t & 15)] = src[t];
+      __syncwarp();
+#pragma unroll
+      for (int r4 = 0; r4 < 16; ++r4) {
+        const float4 ta = ja < K ? W4[stage_at(ja, r4)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 tb = jb < K ? W4[stage_at(jb, r4)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        a[4 * r4] = ta.x;
+        a[4 * r4 + 1] = ta.y;
+        a[4 * r4 + 2] = ta.z;
+        a[4 * r4 + 3] = ta.w;
+        b[4 * r4] = tb.x;
+        b[4 * r4 + 1] = tb.y;
+        b[4 * r4 + 2] = tb.z;
+        b[4 * r4 + 3] = tb.w;
+      }
+      __syncwarp();  // the slice is read before the certificate reuses it
     } else {
       load_col<DMAX, CPLX>(a, Y + (long long)ja * d, d, ja < K);
       load_col<DMAX, CPLX>(b, Y + (long long)jb * d, d, live && jb < K);
@@ -373,13 +486,20 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
     bool converged = (m < 1);
     // real groups of up to 64 rows: settle rank <= 1 without sweeps where the certificate holds
     bool rank1 = false;
-    float ylo = 0.f, yhi = 0.f, mu1 = 0.f;
+    float ylo = 0.f, yhi = 0.f, mu1 = 0.f, zA = 0.f, zB = 0.f;
     if constexpr (!CPLX && DMAX == 64) {
       if (sigma_w > 0.f && !converged) {
         int steps = 0;
-        rank1 = rank1_certificate(a, b, ja < K, jb < K, K, sigma_w, c_wnnm, lane, Ws, ylo, yhi, mu1, steps);
+        bool gram = false;
+        const int how = rank1_certificate(a, b, ja < K, jb < K, K, sigma_w, c_wnnm, lane, Ws, coef_s[wid], ylo,
+                                          yhi, mu1, zA, zB, steps, gram);
+        rank1 = how != 0;
         converged = converged || rank1;
-        if (lane == 0) atomicAdd(&st->power_steps, (unsigned)steps);
+        if (lane == 0) {
+          atomicAdd(&st->power_steps, (unsigned)steps);
+          if (gram) atomicAdd(&st->gram_evals, 1u);
+          if (how == 2) atomicAdd(&st->rank1_gram, 1u);
+        }
       }
     }
     // Components with s^2 < K sw^2 are always removed by the shrinkage.  When the
@@ -520,7 +640,6 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
       atomicAdd(&st->groups, 1u);
       if (rank1) atomicAdd(&st->rank1, 1u);
     }
-    __shared__ float coef_s[WARPS][64];
     int rnk;
     if (rank1) {
       // X^ = coef w (w^T Y) with w = Y v: coef = s' / (s ||w||^2), s = ||w|| (as below)
@@ -532,6 +651,27 @@ __global__ void __launch_bounds__(WARPS * 32, CPLX ? 2 : 3) k_jacobi_wnnm(int n_
       rnk = coef != 0.f ? 1 : 0;
       if (rank && lane == 0) rank[g] = rnk;
       __syncwarp();  // the certificate's last reads of Ws are done
+      if (stage_ok) {
+        // x^_j = coef (y . y_j) y from the certificate's own products: y to every lane through
+        // coef_s, the columns staged as they were loaded, stored with 16-byte accesses
+        float* yv = coef_s[wid];
+        yv[2 * lane] = ylo;
+        yv[2 * lane + 1] = yhi;
+        __syncwarp();
+        float4* W4 = reinterpret_cast<float4*>(Ws);
+        const float ka = zA * coef, kb = zB * coef;
+#pragma unroll
+        for (int r4 = 0; r4 < 16; ++r4) {
+          const float4 t = reinterpret_cast<const float4*>(yv)[r4];
+          W4[stage_at(ja, r4)] = make_float4(ka * t.x, ka * t.y, ka * t.z, ka * t.w);
+          W4[stage_at(jb, r4)] = make_float4(kb * t.x, kb * t.y, kb * t.z, kb * t.w);
+        }
+        __syncwarp();
+        float4* dst = reinterpret_cast<float4*>(Y);
+        for (int t = lane; t < K * 16; t += 32) dst[t] = W4[stage_at(t >> 4, t & 15)];
+        __syncwarp();
+        continue;
+      }
       Ws[2 * lane] = ylo;
       Ws[2 * lane + 1] = yhi;
       if (lane == 0) coef_s[wid][0] = coef;

@@ -365,12 +365,12 @@ def admm_sci_step(y, masks, z, x, u, rho, *, x_out=None, w_out=None, stream=None
 
 def poll_status(ws, reset=False, stream=None):
     """(bits, [cand_overflow, svd_noconv, sweeps, groups, cand_appends, compactions, fb_noconv, rank1,
-    power_steps]) of the last call that used ws.  ws=None reads the status block of
+    power_steps, rank1_gram, gram_evals]) of the last call that used ws.  ws=None reads the status block of
     glr_aggregate_noalloc's scratch array on the current device."""
     lib = L.load()
     wp = _ws(ws)[0] if ws is not None else None
     bits = ctypes.c_uint32(0)
-    cnt = (ctypes.c_uint32 * 9)()
+    cnt = (ctypes.c_uint32 * 11)()
     code = lib.glr_poll_status(wp, ctypes.byref(bits), cnt, 1 if reset else 0, _stream(stream))
     if code not in (L.GLR_OK, L.GLR_EDEVICE, L.GLR_ETIMEDOUT):
         raise GlrError("glr_poll_status", code)

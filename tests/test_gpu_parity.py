@@ -428,21 +428,26 @@ def test_lowrank_singular_values_and_estimate_tight_bar(case):
     assert worst_x <= 1e-5, worst_x
 
 
-@pytest.mark.parametrize("two_patterns", [False, True])
-def test_lowrank_rank1_certificate(two_patterns):
-    """Groups of near copies of one 8 x 8 pattern plus noise of std 0.01 at sigma_w = 0.1: the
-    residual energy (~64 K 1e-4) is below s_crit^2 = sw^2 (K + sqrt(K^2 + 4 C^2)) / 2, so the
-    register kernel settles them by the rank-1 certificate without sweeps (status counter 7)
-    and X^ must equal the oracle's within 1e-5 s_1.  With two patterns per group the certificate
-    fails and the Jacobi sweeps run: the same bar, and no group is counted."""
+@pytest.mark.parametrize("kind", ["one", "spread", "two"])
+def test_lowrank_rank1_certificate(kind):
+    """Groups of near copies of one 8 x 8 pattern plus noise at sigma_w = 0.1, where
+    s_crit^2 = sw^2 (K + sqrt(K^2 + 4 C^2)) / 2 = 0.678.
+    one: noise std 0.01, residual energy ~63 x 64 x 1e-4 = 0.40 below s_crit^2, so the energy
+    bound settles every group (status counter 7) without sweeps.
+    spread: noise std 0.02, residual energy ~1.6 above s_crit^2, but spread over 63 components:
+    ||R^T R||_F ~ sqrt(2 x 63) x 64 x 4e-4 = 0.29 is below it, so the Gram bound settles every
+    group (counter 9) without sweeps.
+    two: two patterns per group, s_2 far above s_crit: no group is certified, the sweeps run.
+    In every case X^ must equal the oracle's within 1e-5 s_1 and the rank the oracle's."""
     rng = np.random.default_rng(21)
     H = W = 8 * 12
     pa = rng.random((8, 8))
     pb = rng.random((8, 8))
     base = np.tile(pa, (12, 12))
-    if two_patterns:
+    if kind == "two":
         base[:, 48:] = np.tile(pb, (12, 6))
-    x = (base + 0.01 * rng.standard_normal((H, W))).astype(np.float32)[None, None]
+    noise = 0.02 if kind == "spread" else 0.01
+    x = (base + noise * rng.standard_normal((H, W))).astype(np.float32)[None, None]
     P, K, N = 8, 64, 40
     Wq = W - P + 1
     grid = [r * Wq + c for r in range(0, 89, 8) for c in range(0, 89, 8)]  # 12 x 12 aligned positions
@@ -457,11 +462,17 @@ def test_lowrank_rank1_certificate(two_patterns):
     g = groups.cpu().numpy()[0].astype(np.float64)
     rk = rank.cpu().numpy()[0]
     Y = O.gather_groups(x[0], P, idx[0])
+    scrit2 = sw * sw * (K + math.sqrt(K * K + 4 * cw * cw)) / 2
     for i in range(N):
         Xo, ro, s, _ = O.wnnm(Y[i].T, sw, cw, eps=1e-8)
         assert np.abs(g[i].T - Xo).max() <= 1e-5 * s[0], i
         assert int(rk[i]) == ro, (i, int(rk[i]), ro)
-    if two_patterns:
+        if kind == "spread":  # the case is what it claims: energy above s_crit^2, Gram bound below
+            s2 = s[1:] ** 2
+            assert s2.sum() > scrit2 and math.sqrt((s2 ** 2).sum()) < scrit2
+    if kind == "two":
         assert cnt[7] < N and cnt[2] > 0  # the mixed groups needed sweeps
+    elif kind == "one":
+        assert cnt[7] == N and cnt[9] == 0 and cnt[2] == 0, cnt  # the energy bound settled every group
     else:
-        assert cnt[7] == N and cnt[2] == 0, cnt  # every group settled without a sweep
+        assert cnt[7] == N and cnt[9] == N and cnt[10] == N and cnt[2] == 0, cnt  # the Gram bound did
