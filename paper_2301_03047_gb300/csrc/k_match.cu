@@ -635,6 +635,9 @@ __global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ 
       uint32_t bits = 0;
       const uint4 v = nxt;
       if (i + 32 < n8) nxt = __ldg(m8 + i + 32);
+      // most steps hold no candidate: the smallest of each lane's 8 minima decides that
+      const uint32_t m2 = __vminu2(__vminu2(v.x, v.y), __vminu2(v.z, v.w));
+      if (!__any_sync(0xffffffffu, i < n8 && min(m2 & 0xffffu, m2 >> 16) <= prefix)) continue;
       if (i < n8) {
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
