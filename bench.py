@@ -341,16 +341,18 @@ def fp32_alu_peak_tflops(sm_mhz: float) -> float:
     return num_sms() * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def kernel_hash(fname: str) -> str:
+def kernel_hash(fname) -> str:
+    """Hash of the kernel's source file(s) (a name or a tuple of names) and the shared headers."""
     h = hashlib.sha1()
-    for f in (fname, "glr_common.cuh", "topk_stream.cuh", "glr_kernels.cuh"):
+    names = tuple(fname) if isinstance(fname, (tuple, list)) else (fname,)
+    for f in names + ("glr_common.cuh", "topk_stream.cuh", "glr_kernels.cuh"):
         p = os.path.join(ROOT, "paper_2301_03047_gb300", "csrc", f)
         if os.path.exists(p):
             h.update(open(p, "rb").read())
     return h.hexdigest()[:12]
 
 
-KERNEL_FILE = {"k_match_tc": "k_match_tc.cu", "k_match_fp32": "k_match.cu", "k_jacobi_wnnm": "k_lowrank.cu",
+KERNEL_FILE = {"k_match_tc": ("k_match_tc.cu", "k_match.cu"), "k_match_fp32": "k_match.cu", "k_jacobi_wnnm": "k_lowrank.cu",
                "k_jacobi_smem": "k_lowrank_wide.cu", "k_jacobi_wnnm_c": "k_lowrank.cu", "k_fft_rows": "k_fft.cu",
                "k_match_tc_w": "k_match_tc.cu", "k_gram_wnnm": "k_lowrank_wide.cu",
                "k_jacobi_wnnm_fused": "k_lowrank.cu",
@@ -383,9 +385,9 @@ def merge_scans(prof: dict) -> dict:
     together they are one contraction of every key/position pair."""
     prof = dict(prof)
     if "k_match_tc_chunk" in prof:
-        # chunk minima (the contraction) + the exact evaluation of the candidate chunks
+        # chunk minima (the contraction), the bound and candidate list, the exact evaluation
         ms, n = prof.pop("k_match_tc_chunk")
-        extra = [prof.pop(k) for k in ("k_chunk_topk", "k_patch_norms") if k in prof]
+        extra = [prof.pop(k) for k in ("k_tau_chunk", "k_chunk_topk", "k_patch_norms") if k in prof]
         prof["k_match_tc"] = (ms + sum(e[0] for e in extra), n)
         return prof
     extra = [prof.pop(k) for k in ("k_match_tc_min", "k_tau_bound") if k in prof]
@@ -416,7 +418,8 @@ def roofline(prof: dict, cfg, sweeps_per_group: float, clocks: dict, pk: dict, n
             out = {"bound": "tensor", "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
                    "peak_note": f"of {pk['source']} cuBLAS bf16 sustained"
                                 + ("; time = minima scan + bound + candidate scan" if scans else "")
-                                + ("; time = chunk-minima scan + exact evaluation of the candidate chunks" if chunks else "")}
+                                + ("; time = chunk-minima scan + bound + exact evaluation of the candidate chunks"
+                                   if chunks else "")}
         else:
             out = {"bound": "alu", "peak": round(fp32_alu_peak_tflops(sm), 1), "unit": "TFLOP/s",
                    "peak_note": f"derived FP32 FMA peak {num_sms()}x128x2 at {sm:.0f} MHz"}
