@@ -47,6 +47,7 @@ struct MatchPlan {
   size_t mins_off;      // bound_pass 1: half-tile minima [n_img][Npad][2 pos_tiles] float32;
                         // bound_pass 2: 16-bit chunk minima [n_img][Npad][8 pos_tiles]
   size_t ccnt_off, clist_off;  // bound_pass 2: candidate chunks per key (count, the first ids)
+  size_t ticket_off;           // bound_pass 2: next key of the exact evaluation (int)
   int emb_fmt;                 // GLR_MATCH_LEARNED, bound_pass 2: proposal operand 0 = BF16, 1 = E4M3
   size_t embq_off, n2_off;     // its position operand rows, the largest squared embedding norm
   size_t mean_off, meanp_off, qn_off, keyv_off, buf_off, bufcnt_off, taugl_off, qpack_off, kpack_off, embp_off, embk_off, total;

@@ -530,7 +530,8 @@ template <int L>
 __global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ mins16, const int32_t* __restrict__ n_found,
                                                    int n_img, int N, int Npad, int nchunks, int kp, int clcap,
                                                    uint32_t* __restrict__ tau16, int32_t* __restrict__ ccount,
-                                                   uint32_t* __restrict__ clist, StatusBlock* st) {
+                                                   uint32_t* __restrict__ clist, StatusBlock* st,
+                                                   int* __restrict__ ticket = nullptr) {
   __shared__ unsigned hist_s[8][256];
   __shared__ uint16_t vals_s[8][32 * L];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -538,6 +539,7 @@ __global__ void __launch_bounds__(256) k_tau_chunk(const uint16_t* __restrict__ 
   uint16_t* vals = vals_s[wid];
   const long long nkeys = (long long)n_img * N;
   const int n8 = nchunks / 8;  // nchunks is a multiple of 8
+  if (ticket != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0;  // for k_chunk_topk
   for (long long gk = blockIdx.x * 8LL + wid; gk < nkeys; gk += gridDim.x * 8LL) {
     const int f = (int)(gk / N), k = (int)(gk - (long long)f * N);
     if (k >= min(n_found[f], N)) continue;
@@ -754,7 +756,7 @@ __global__ void __launch_bounds__(CT_WARPS * 32, 4)
                  const uint16_t* __restrict__ mins16, const uint32_t* __restrict__ tau16s,
                  const int32_t* __restrict__ ccount, const uint32_t* __restrict__ clist_g, int n_img, int C, int H,
                  int W, int N, int Npad, int nchunks, int K, int Kp, int32_t* __restrict__ idx,
-                 float* __restrict__ dist) {
+                 float* __restrict__ dist, int* __restrict__ ticket) {
   constexpr int P = PT, PP = P * P, CP = CMAX * P, DM = CMAX * PP, SW = 32 + P - 1;
   extern __shared__ unsigned long long ct_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -771,7 +773,13 @@ __global__ void __launch_bounds__(CT_WARPS * 32, 4)
   const int g = lane >> 3, l8 = lane & 7;
   const unsigned ltm = (1u << lane) - 1u;
   const long long nkeys = (long long)n_img * N;
-  for (long long gk = blockIdx.x * (long long)CT_WARPS + wid; gk < nkeys; gk += (long long)gridDim.x * CT_WARPS) {
+  // keys are taken one at a time from a shared ticket (zeroed by k_tau_chunk): the candidate
+  // counts differ from key to key, and every resident warp stays busy until the last key
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(ticket, 1);
+    const long long gk = __shfl_sync(0xffffffffu, t, 0);
+    if (gk >= nkeys) break;
     const int f = (int)(gk / N), k = (int)(gk - (long long)f * N);
     if (k >= min(n_found[f], N)) continue;
     const int kq = keys[gk];
@@ -1173,24 +1181,30 @@ glr_status launch_chunk_topk(const float* x, const glr_images& im, const int32_t
   uint32_t* tau16s = reinterpret_cast<uint32_t*>(ws + pl.taugl_off);
   int32_t* ccount = reinterpret_cast<int32_t*>(ws + pl.ccnt_off);
   uint32_t* clist_g = reinterpret_cast<uint32_t*>(ws + pl.clist_off);
+  int* ticket = reinterpret_cast<int*>(ws + pl.ticket_off);
   {
     const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, 8), (long long)num_sms() * 16));
     GLR_LAUNCH("k_tau_chunk", s, k_tau_chunk<8><<<blocks, 256, 0, s>>>(mins16, n_found, im.n_img, N, pl.Npad,
                                                                         nchunks, pl.Kp, CT_CL, tau16s, ccount, clist_g,
-                                                                        reinterpret_cast<StatusBlock*>(ws)));
+                                                                        reinterpret_cast<StatusBlock*>(ws), ticket));
   }
-  const int blocks = (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, CT_WARPS), (long long)num_sms() * 8));
 #define GLR_CHUNK_CASE(PP, CM)                                                                                  \
   {                                                                                                             \
     const size_t smem = (size_t)CT_WARPS * chunk_topk_warp_bytes<PP, CM>();                                     \
     if (cudaFuncSetAttribute(k_chunk_topk<PP, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=    \
         cudaSuccess)                                                                                            \
       return GLR_ECUDA;                                                                                         \
+    int per_sm = 0; /* resident CTAs: every warp of the grid is on an SM at once */                            \
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chunk_topk<PP, CM>, CT_WARPS * 32, smem) !=    \
+        cudaSuccess)                                                                                            \
+      return GLR_ECUDA;                                                                                         \
+    const int blocks =                                                                                          \
+        (int)std::max<long long>(1, std::min<long long>(ceil_div(nkeys, CT_WARPS), (long long)num_sms() * std::max(per_sm, 1))); \
     GLR_LAUNCH("k_chunk_topk", s,                                                                               \
                (k_chunk_topk<PP, CM><<<blocks, CT_WARPS * 32, smem, s>>>(x, mean, qn, keyv, keys, n_found, mins16, \
                                                                         tau16s, ccount, clist_g, im.n_img, im.C, \
                                                                         im.H, im.W, N, pl.Npad, nchunks, pl.K,   \
-                                                                        pl.Kp, idx, dist)));                     \
+                                                                        pl.Kp, idx, dist, ticket)));             \
   }
   if (im.P == 8 && im.C == 1) GLR_CHUNK_CASE(8, 1)
   else if (im.P == 6 && im.C <= 2) GLR_CHUNK_CASE(6, 2)
@@ -1278,6 +1292,7 @@ MatchPlan match_plan(const glr_images& im, int N, int K, const glr_match_opts* o
       pl.bound_pass = 2;  // 16-bit minima of every 32-position chunk
       pl.mins_off = L.take((size_t)im.n_img * pl.Npad * 8 * pl.pos_tiles * 2);
       pl.ccnt_off = L.take((size_t)im.n_img * pl.Npad * 4);
+      pl.ticket_off = L.take(4);
       pl.clist_off = L.take((size_t)im.n_img * pl.Npad * (emb_chunk ? CT_CL_EMB : CT_CL) * 4);
     } else {
       pl.bound_pass = ((bp == 1 || ((bp == 0 || bp == 2) && pl.nkc == 1)) && 2LL * pl.pos_tiles >= pl.Kp) ? 1 : 0;
